@@ -1,0 +1,458 @@
+"""Error tables, bound composition, max ordering and the retrieval planner
+(oracle).  Test infrastructure only.
+
+Sec. III-A: error-bound mode minimises the retrieved size S_tau subject to
+max|x - x'| <= tau; PSNR = 20 log10((max x - min x) / RMSE).  Sec. V-C: a
+level's maximum coefficient gives a bitplane -> absolute error map; with
+coefficient decomposition, the level's error is the maximum over regions, and
+"max ordering" merges the per-region loading orders by descending cumulative
+error, merging steps with equal error, into segments with an error list M_0.
+Sec. VI-B: the interpreter picks how many bitplanes to retrieve.
+
+Readings (the paper gives estimates; the benchmark spec asks for a guarantee):
+* L-infinity: per-level E_l = Lam^d E_{l+1} + e_l + rho_l; per-region
+  F_r = Lam max(E_{l+1}, F_1..F_{r-1}) + e_{l,r} + rho_l, E_l = max(E_{l+1}, F_r);
+  Lam = 1.25 (cubic: sum of |weights| of every boundary rule) or 1 (linear).
+  A decomposed region's coefficient error is e_1 + e_2 + e_3 (the bilinear
+  per-level predictions have unit weight sum).
+* L2 (PSNR): ||P e||_2 <= sqrt(||P^T P||_inf) ||e||_2 per 1-D pass, with the
+  row sum computed exactly for every line length; tensor passes multiply.
+* rho_l: rounding allowance (first-order error analysis of the canonical
+  expressions, times 1.01); fixed-point levels lose < one quantum per floor.
+* Greedy planner: take the step with the largest bound decrease per byte
+  until the bound meets the target (the paper uses greedy for PMGARD and a DP
+  / best-first search for its own modes; greedy is this build's reading).
+"""
+import math
+
+import numpy as np
+
+LAMBDA = {"linear": 1.0, "cubic": 1.25}
+KAPPA = {"linear": 1.0, "cubic": 3.625}
+U_W = {"f32": 2.0 ** -24, "f64": 2.0 ** -53}
+MARGIN = 1.000000001
+
+
+def _up(x):
+    """float(x) rounded up (x: python int or float)."""
+    f = float(x)
+    if isinstance(x, int) and int(f) < x:
+        f = math.nextafter(f, math.inf)
+    return f
+
+
+# --------------------------------------------------------------------------
+# per-stream tables
+# --------------------------------------------------------------------------
+
+def nb_dropped_max(k):
+    """Largest |value| of k negabinary digits: floor((2^(k+1) - 1) / 3)."""
+    return ((1 << (k + 1)) - 1) // 3
+
+
+def stream_tables(enc, n_real, is_int, B, encoding, h, psnr_mode, bytes_b):
+    """maxerr[b], sq[b] (rigorous upper bounds) and bytes[b], b = 0..B."""
+    qd = enc["quant"]
+    if is_int:
+        vmax_abs = _up(qd["vmax"]) * h
+        unit = math.ldexp(h, qd["sh"] + (3 if encoding == "negabinary" else 0))
+    else:
+        vmax_abs = qd["vmax"]
+        unit = math.ldexp(1.0, qd["E"] - B + (3 if encoding == "negabinary" else 0))
+    zero = qd["vmax"] == 0
+    maxerr = [0.0] * (B + 1)
+    sq = [0.0] * (B + 1)
+    for b in range(B + 1):
+        if zero:
+            continue
+        if b == 0:
+            maxerr[b] = vmax_abs
+        elif encoding == "generic":
+            maxerr[b] = math.ldexp(unit, B - b)
+        else:
+            maxerr[b] = _up(nb_dropped_max(B - b) + 1) * unit
+    if zero:
+        return dict(maxerr=maxerr, sq=sq, bytes=bytes_b, unit=unit)
+    if psnr_mode:
+        C = enc["pairs"]
+        for b in range(B + 1):
+            s2 = 0
+            s1 = 0
+            for j in range(b, B):
+                for jj in range(b, B):
+                    w = 2 * B - 2 - j - jj
+                    if encoding == "generic":
+                        s2 += C[j, jj] << w
+                    else:
+                        s2 += (-1) ** (j + jj) * (C[j, jj] << w)
+                if encoding == "generic":
+                    s1 += C[j, j] << (B - 1 - j)
+            if encoding != "generic":
+                s1 = math.isqrt(n_real * s2)
+                if s1 * s1 < n_real * s2:
+                    s1 += 1
+            total = s2 + 2 * s1 + n_real
+            sq[b] = _up(total) * unit * unit
+    else:
+        for b in range(B + 1):
+            sq[b] = n_real * maxerr[b] * maxerr[b]
+    return dict(maxerr=maxerr, sq=sq, bytes=bytes_b, unit=unit)
+
+
+# --------------------------------------------------------------------------
+# spectral factors of the 1-D upsampling operators (L2 composition)
+# --------------------------------------------------------------------------
+
+def pass_matrix(m, degree):
+    """P: (m//2) x ceil(m/2) weights mapping even-index values of a line of m
+    points to its odd indices (same boundary rules as interp.predict_line)."""
+    mc = (m + 1) // 2
+    P = np.zeros((m // 2, mc))
+    for t, j in enumerate(range(1, m, 2)):
+        p1, m3, p3 = j + 1 < m, j - 3 >= 0, j + 3 < m
+        if degree == "cubic" and p1 and m3 and p3:
+            w = {j - 3: -1 / 16, j - 1: 9 / 16, j + 1: 9 / 16, j + 3: -1 / 16}
+        elif degree == "cubic" and p1 and p3:
+            w = {j - 1: 3 / 8, j + 1: 6 / 8, j + 3: -1 / 8}
+        elif degree == "cubic" and p1 and m3:
+            w = {j - 3: -1 / 8, j - 1: 6 / 8, j + 1: 3 / 8}
+        elif p1:
+            w = {j - 1: 0.5, j + 1: 0.5}
+        else:
+            w = {j - 1: 1.0}
+        for src, val in w.items():
+            P[t, src // 2] += val
+    return P
+
+
+_RS_CACHE = {}
+
+
+def rowsum_ptp(m, degree):
+    """||P^T P||_inf (exact in float64: weights are dyadic)."""
+    key = (m, degree)
+    if key not in _RS_CACHE:
+        P = pass_matrix(m, degree)
+        _RS_CACHE[key] = float(np.abs(P.T @ P).sum(axis=1).max()) if P.size else 0.0
+    return _RS_CACHE[key]
+
+
+# --------------------------------------------------------------------------
+# composition
+# --------------------------------------------------------------------------
+
+class Composer:
+    """Bound composition for one refactored field (see module docstring)."""
+
+    def __init__(self, meta, streams):
+        self.m = meta
+        self.st = streams      # list of dict(level, region, sub, n_real, ...)
+        self.L = meta["L"]
+        self.d = meta["d"]
+        self.lam = LAMBDA[meta["degree"]]
+        self.uw = U_W[meta["dtype"]]
+        self.h = meta["h"]
+        self.M = meta["M"]
+        self.C0 = meta["C0"]
+        kap = KAPPA[meta["degree"]]
+        lam_d1 = 1.0
+        for _ in range(self.d - 1):
+            lam_d1 *= self.lam
+        self.lam_d = lam_d1 * self.lam
+        self.pf = (self.d * kap * lam_d1) if meta["interp"] == "level" else kap
+        self.rho_fix = (2.0 * self.d * lam_d1 + 2.0) * self.h
+        # stream groups
+        self.by_level = {}
+        for i, s in enumerate(streams):
+            self.by_level.setdefault(s["level"], []).append(i)
+
+    # ---- L-infinity -------------------------------------------------------
+    def rho0(self, E1, e0sum):
+        if self.L == 1:
+            return MARGIN * 1.01 * self.uw * self.C0
+        V = self.M + self.lam_d * E1 + e0sum
+        return 1.01 * self.uw * (2.0 * self.pf * V + self.lam_d * V + 2.0 * V
+                                 + 12.0 * self.C0)
+
+    def region_errors(self, level, err):
+        """e_{l,r} per region (sum of sub-streams); region 0 = whole level."""
+        out = {}
+        for i in self.by_level[level]:
+            r = self.st[i]["region"]
+            out[r] = out.get(r, 0.0) + err[i]
+        return out
+
+    def linf(self, err):
+        """Composed bound E_0 from per-stream errors ``err``."""
+        L = self.L
+        E = err[self.by_level[L - 1][0]] + (self.h if L - 1 >= 1 else 0.0)
+        if L == 1:
+            return (E + self.rho0(0.0, 0.0)) * MARGIN
+        for level in range(L - 2, -1, -1):
+            reg = self.region_errors(level, err)
+            if level == 0:
+                rho = self.rho0(E, sum(reg.values()))
+            else:
+                rho = self.rho_fix
+            if self.m["interp"] == "level":
+                e = max(reg.values())
+                E = self.lam_d * E + e + rho
+            else:
+                F = []
+                for r in sorted(reg):
+                    base = E
+                    for f in F:
+                        base = max(base, f)
+                    F.append(self.lam * base + reg[r] + rho)
+                for f in F:
+                    E = max(E, f)
+        return E * MARGIN
+
+    # ---- L2 ---------------------------------------------------------------
+    def _e1_and_e0(self, err):
+        """E_1 (composed bound of level 1) and the sum of level-0 region
+        errors: the magnitude terms of the level-0 rounding allowance."""
+        L = self.L
+        if L == 1:
+            return 0.0, 0.0
+        E = err[self.by_level[L - 1][0]] + (self.h if L - 1 >= 1 else 0.0)
+        for level in range(L - 2, 0, -1):
+            reg = self.region_errors(level, err)
+            if self.m["interp"] == "level":
+                E = self.lam_d * E + max(reg.values()) + self.rho_fix
+            else:
+                F = []
+                for r in sorted(reg):
+                    base = E
+                    for f in F:
+                        base = max(base, f)
+                    F.append(self.lam * base + reg[r] + self.rho_fix)
+                for f in F:
+                    E = max(E, f)
+        return E, sum(self.region_errors(0, err).values())
+
+    def l2(self, sq, err):
+        """Upper bound on the sum of squared errors (per-stream sq, and the
+        per-stream max errors of the same plan for the rounding terms)."""
+        m = self.m
+        L = self.L
+        cnt = m["level_counts"]
+        N = math.sqrt(sq[self.by_level[L - 1][0]])
+        if L == 1:
+            N += self.rho0(0.0, 0.0) * math.sqrt(cnt[0])
+            return (N * N) * MARGIN
+        N += self.h * math.sqrt(cnt[L - 1])
+        E1, e0 = self._e1_and_e0(err)
+        for level in range(L - 2, -1, -1):
+            rho = self.rho0(E1, e0) if level == 0 else self.rho_fix
+            groups = {}
+            for i in self.by_level[level]:
+                s = self.st[i]
+                groups.setdefault(s["region"], []).append((s["sub"], i))
+            cnorm = {}
+            for r, items in groups.items():
+                items.sort()
+                if items[0][0] == 0:
+                    cnorm[r] = math.sqrt(sq[items[0][1]])
+                else:
+                    a2, a3 = m["decomp_factors"][r]
+                    n1 = math.sqrt(sq[items[0][1]])
+                    n2 = math.sqrt(sq[items[1][1]]) + a2 * n1
+                    n3 = math.sqrt(sq[items[2][1]]) + a3 * math.sqrt(n1 * n1 + n2 * n2)
+                    cnorm[r] = math.sqrt(n1 * n1 + n2 * n2 + n3 * n3)
+            if m["interp"] == "level":
+                c = 0.0
+                for r in sorted(cnorm):
+                    c += cnorm[r] * cnorm[r]
+                t = m["level_factor"][level] * N + math.sqrt(c) + rho * math.sqrt(cnt[level])
+                N = math.sqrt(N * N + t * t)
+            else:
+                T = N * N
+                for r in sorted(cnorm):
+                    t = (m["region_factor"][(level, r)] * math.sqrt(T) + cnorm[r]
+                         + rho * math.sqrt(m["region_counts"][(level, r)]))
+                    T += t * t
+                N = math.sqrt(T)
+        return (N * N) * MARGIN
+
+
+# --------------------------------------------------------------------------
+# staircases, max ordering and the greedy planner
+# --------------------------------------------------------------------------
+
+def useful_steps(vals, bytes_b):
+    """Plane counts that strictly lower ``vals`` (from b = 0), with their byte
+    increments: [(b, vals[b], bytes[b] - bytes[prev])]."""
+    out = []
+    b = 0
+    B = len(vals) - 1
+    while True:
+        nb = b + 1
+        while nb <= B and not vals[nb] < vals[b]:
+            nb += 1
+        if nb > B:
+            return out
+        out.append((nb, vals[nb], bytes_b[nb] - bytes_b[b]))
+        b = nb
+
+
+def _region_sequence(ids, tabs):
+    """Greedy loading order inside one decomposed region: repeatedly add the
+    next useful plane step of the sub-stream with the largest decrease of
+    e_1 + e_2 + e_3 per byte (ties: lower sub-level)."""
+    b = {i: 0 for i in ids}
+    steps = {i: useful_steps(tabs[i]["maxerr"], tabs[i]["bytes"]) for i in ids}
+    pos = {i: 0 for i in ids}
+
+    def total():
+        t = 0.0
+        for i in ids:
+            t = t + tabs[i]["maxerr"][b[i]]
+        return t
+
+    cur = total()
+    seq = []
+    while True:
+        best = None
+        for i in ids:
+            if pos[i] >= len(steps[i]):
+                continue
+            nb, val, db = steps[i][pos[i]]
+            de = tabs[i]["maxerr"][b[i]] - val
+            ratio = math.inf if db == 0 else de / db
+            if best is None or ratio > best[0]:
+                best = (ratio, i, nb, db)
+        if best is None:
+            return seq
+        _, i, nb, db = best
+        b[i] = nb
+        pos[i] += 1
+        cur = total()
+        seq.append((cur, [(i, nb)], db))
+
+
+def max_ordering(level_ids_by_region, tabs):
+    """Sec. V-C max ordering: merge the per-region loading orders by
+    descending cumulative error; steps with equal error merge into one
+    segment.  Returns (initial level error, [(updates, bytes, level error)])."""
+    allsteps = []
+    cur = {}
+    for r, ids in sorted(level_ids_by_region.items()):
+        t = 0.0
+        for i in ids:
+            t = t + tabs[i]["maxerr"][0]
+        cur[r] = t
+        for k, (e, upd, db) in enumerate(_region_sequence(ids, tabs)):
+            allsteps.append((e, r, k, upd, db))
+    allsteps.sort(key=lambda s: (-s[0], s[1], s[2]))
+    init = max(cur.values())
+    segs = []
+    i = 0
+    while i < len(allsteps):
+        j = i
+        upd, db = [], 0
+        while j < len(allsteps) and allsteps[j][0] == allsteps[i][0]:
+            e, r, k, u, d = allsteps[j]
+            upd += u
+            db += d
+            cur[r] = e
+            j += 1
+        segs.append((upd, db, max(cur.values())))
+        i = j
+    return init, segs
+
+
+class Unit:
+    def __init__(self, ids, steps, weight):
+        self.ids = ids          # stream indices
+        self.steps = steps      # [(updates [(stream, b)], dbytes, unit value)]
+        self.weight = weight
+
+
+def _compress(init, segs):
+    """Merge segments that do not lower the unit value into the next one."""
+    out = []
+    upd, db, prev = [], 0, init
+    for u, d, v in segs:
+        upd = upd + u
+        db += d
+        if v < prev:
+            out.append((upd, db, v))
+            upd, db, prev = [], 0, v
+    return out
+
+
+def build_units(comp, tabs, kind):
+    """Planning units.  kind 'linf': per-level levels (max-ordered at a
+    decomposed level 0) or per-region streams; kind 'l2': every stream."""
+    units = []
+    d = comp.d
+    for level in range(comp.L - 1, -1, -1):
+        ids = comp.by_level[level]
+        w = float(2 ** (d * level))
+        if kind == "linf" and comp.m["interp"] == "level" and len(ids) > 1:
+            by_r = {}
+            for i in ids:
+                by_r.setdefault(comp.st[i]["region"], []).append(i)
+            init, segs = max_ordering(by_r, tabs)
+            units.append(Unit(ids, _compress(init, segs), w))
+        else:
+            key = "maxerr" if kind == "linf" else "sq"
+            for i in ids:
+                st = [([(i, nb)], db, v) for nb, v, db in useful_steps(tabs[i][key], tabs[i]["bytes"])]
+                units.append(Unit([i], st, w))
+    return units
+
+
+def greedy(comp, tabs, target, kind):
+    """Greedy interpreter: returns (planes per stream, bound, satisfied)."""
+    n = len(tabs)
+    b = [0] * n
+    units = build_units(comp, tabs, kind)
+    pos = [0] * len(units)
+
+    def evaluate(bb):
+        err = [tabs[i]["maxerr"][bb[i]] for i in range(n)]
+        if kind == "linf":
+            return comp.linf(err)
+        sq = [tabs[i]["sq"][bb[i]] for i in range(n)]
+        return comp.l2(sq, err)
+
+    def unit_value(u, bb):
+        key = "maxerr" if kind == "linf" else "sq"
+        if len(u.ids) == 1:
+            return tabs[u.ids[0]][key][bb[u.ids[0]]]
+        reg = {}
+        for i in u.ids:
+            r = comp.st[i]["region"]
+            reg[r] = reg.get(r, 0.0) + tabs[i]["maxerr"][bb[i]]
+        return max(reg.values())
+
+    bound = evaluate(b)
+    while bound > target:
+        best = None
+        fallback = None
+        for ui, u in enumerate(units):
+            if pos[ui] >= len(u.steps):
+                continue
+            upd, db, _ = u.steps[pos[ui]]
+            trial = list(b)
+            for i, nb in upd:
+                trial[i] = nb
+            nbnd = evaluate(trial)
+            gain = bound - nbnd
+            ratio = math.inf if db == 0 else gain / db
+            if gain > 0 or db == 0:
+                if best is None or ratio > best[0]:
+                    best = (ratio, ui, trial, nbnd)
+            own = (unit_value(u, b) - unit_value(u, trial)) * u.weight
+            fr = math.inf if db == 0 else own / db
+            if fallback is None or fr > fallback[0]:
+                fallback = (fr, ui, trial, nbnd)
+        if best is None:
+            best = fallback
+        if best is None:
+            return b, bound, False
+        _, ui, b, bound = best
+        pos[ui] += 1
+    return b, bound, True
