@@ -1,0 +1,198 @@
+/*
+ * pcr.h -- C ABI of the B300 progressive refactor / retrieve library.
+ *
+ * The library implements the data-parallel path of the adaptive progressive
+ * compressor of arXiv 2609.04573 ("ProAICD"): a 2-D or 3-D FP32/FP64 field is
+ * refactored into hierarchical coefficients by multilevel interpolation
+ * (per-level or per-region, linear or cubic; Sec. IV), the finest level's
+ * coefficients are further decomposed by 2-D per-level linear interpolation
+ * of each slice (Sec. V-B, Algorithm 1), and every stream is quantised and
+ * split into bitplanes with per-plane error tables (Sec. V-C).  Retrieval picks
+ * the planes that provably meet a max-abs-error or PSNR target (Sec. III-A,
+ * V-C) and reconstructs the field from them (Algorithm 2).
+ *
+ * Conventions shared by every entry point
+ *   - Status codes only: no exceptions cross the ABI, nothing aborts, no
+ *     device trap.  pcr_last_error() gives a thread-local message for the last
+ *     non-OK status of the calling thread.
+ *   - Device pointers are CUDA device addresses on the current device; the
+ *     caller owns them and must keep them alive until the work enqueued on
+ *     `cuda_stream` (a cudaStream_t, NULL = legacy default stream) completes.
+ *   - A pcr_handle owns its device buffers (allocated through the caller's
+ *     pcr_allocator, or cudaMallocAsync when that pointer is NULL) and its host
+ *     tables; pcr_free releases both.  Handles are immutable after
+ *     pcr_refactor / pcr_deserialize, so several threads may plan and retrieve
+ *     from one handle concurrently, each on its own stream.
+ *   - Fields are row-major (C order, last axis fastest).  ndim is 2 or 3 and
+ *     every dimension must be >= 2.
+ */
+#ifndef PCR_H
+#define PCR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PCR_OK = 0,
+  PCR_ERR_INVALID_ARG = 1,   /* bad pointer, size, enum or combination      */
+  PCR_ERR_UNSUPPORTED = 2,   /* valid request outside what is implemented   */
+  PCR_ERR_OOM = 3,           /* the allocator returned NULL                 */
+  PCR_ERR_CUDA = 4,          /* a CUDA runtime call failed (message given)  */
+  PCR_ERR_TIMEOUT = 5,       /* a bounded device wait gave up               */
+  PCR_ERR_UNSATISFIABLE = 6, /* even all planes cannot meet the target      */
+  PCR_ERR_CORRUPT = 7        /* container failed length / checksum checks   */
+} pcr_status;
+
+enum { PCR_F32 = 0, PCR_F64 = 1 };
+enum { PCR_MODE_EB = 0, PCR_MODE_PSNR = 1 };
+enum { PCR_INTERP_LEVEL = 0, PCR_INTERP_REGION = 1 };
+enum { PCR_LINEAR = 1, PCR_CUBIC = 3 };
+enum { PCR_ENC_DEFAULT = 0, PCR_ENC_GENERIC = 1, PCR_ENC_NEGABINARY = 2 };
+enum { PCR_TARGET_ABS = 0, PCR_TARGET_REL = 1, PCR_TARGET_PSNR = 2 };
+
+#define PCR_MAX_STREAMS 64
+
+/* Device memory provider.  alloc(ctx, bytes, stream) returns a device pointer
+ * usable in stream order on `stream` (NULL on failure -> PCR_ERR_OOM);
+ * free(ctx, p, stream) returns it.  Pass NULL for cudaMallocAsync/FreeAsync. */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*free)(void* ctx, void* p, void* stream);
+} pcr_allocator;
+
+/* Refactoring scheme (Sec. IV-VI; tuning table of Sec. VI-A).
+ *   mode        PCR_MODE_EB: error-bound mode, L-inf tables only (sq tables
+ *               are the L-inf bound times the count);
+ *               PCR_MODE_PSNR: also exact integer squared-error tables.
+ *   interp      per-level (pass order = natural axis order) or per-region.
+ *   degree      PCR_LINEAR or PCR_CUBIC.
+ *   order       per-region pass order: a permutation of the active axes
+ *               (3-D: 0,1,2; 2-D: 1,2 in order[0..1]); ignored per-level.
+ *   decomp_axis slice normal (0..2) of the level-0 coefficient decomposition
+ *               (Sec. V-B), or -1 for none; 3-D only.
+ *   encoding    PCR_ENC_DEFAULT picks generic for EB, negabinary+XOR for PSNR.
+ *   nlevels     L (0 = auto: coarsest grid keeps >= 3 points per axis).
+ *   nplanes     B (0 = auto: 32 for FP32, 64 for FP64; otherwise 1..B_auto). */
+typedef struct {
+  int mode;
+  int interp;
+  int degree;
+  int order[3];
+  int decomp_axis;
+  int encoding;
+  int nlevels;
+  int nplanes;
+} pcr_scheme;
+
+/* Retrieval target (Sec. III-A): PCR_TARGET_ABS max|x - x'| <= value;
+ * PCR_TARGET_REL max|x - x'| <= value * (max x - min x);
+ * PCR_TARGET_PSNR 20 log10((max x - min x) / RMSE) >= value (dB). */
+typedef struct {
+  int kind;
+  double value;
+} pcr_target;
+
+/* A retrieval plan: how many planes of every stream to read (host data). */
+typedef struct {
+  int nstreams;
+  int planes[PCR_MAX_STREAMS];
+  double bound;       /* a-priori L-inf bound (ABS/REL) or SSE bound (PSNR) */
+  double psnr_bound;  /* PSNR implied by the SSE bound (PSNR targets)       */
+  uint64_t bytes;     /* payload bytes read: plane words + sign words       */
+  int satisfied;      /* 1 when the bound meets the target                  */
+} pcr_retrieval_plan;
+
+/* Per-stream description (tests, tools, serialisation). */
+typedef struct {
+  int level, region, sub;      /* sub 0 = undecomposed, 1..3 = S1..S3        */
+  int is_fixed;                /* 1: 64-bit fixed point (levels >= 1)       */
+  int nplanes;                 /* B                                         */
+  int64_t n_real, n_pad, words;/* elements, padded elements, words / plane  */
+  int64_t nseg;                /* sign segments (generic encoding)          */
+  int exponent;                /* E (float streams) or bit length e (fixed) */
+  int shift;                   /* fixed streams: quantisation shift sh      */
+  double vmax;                 /* max |coefficient| (fixed: in quanta)      */
+} pcr_stream_info;
+
+typedef struct pcr_handle pcr_handle;
+
+/* ---- refactor (Algorithm 1) ------------------------------------------- */
+/* Refactor the device field `d_field` (dims[ndim], dtype PCR_F32/PCR_F64).
+ * Enqueues all work on `cuda_stream` and synchronises it once at the end to
+ * read the ~KB of tables.  On success *out owns the streams. */
+pcr_status pcr_refactor(const void* d_field, int ndim, const int64_t* dims, int dtype,
+                        const pcr_scheme* scheme, const pcr_allocator* alloc,
+                        void* cuda_stream, pcr_handle** out);
+
+/* Batched form: n independent fields refactored with one work list per
+ * kernel (one launch per pipeline stage for the whole batch).  Arrays are
+ * length n; fields may have different shapes and dtypes. */
+pcr_status pcr_refactor_batch(int n, const void* const* d_fields, const int* ndims,
+                              const int64_t* const* dims, const int* dtypes,
+                              const pcr_scheme* schemes, const pcr_allocator* alloc,
+                              void* cuda_stream, pcr_handle** outs);
+
+/* ---- plan (retrieval interpreter, Sec. V-C / VI-B) -------------------- */
+/* Host only.  Greedy selection of planes meeting `target`; returns
+ * PCR_ERR_UNSATISFIABLE (plan still filled with all planes) when the bound
+ * with every plane exceeds the target. */
+pcr_status pcr_plan(const pcr_handle* h, const pcr_target* target, pcr_retrieval_plan* out);
+
+/* ---- retrieve (Algorithm 2) ------------------------------------------- */
+/* Decode the planes of `plan` (from pcr_plan on the same handle), recompose
+ * and reconstruct into the caller's device buffer `d_out` (same shape and
+ * dtype as the refactored field).  Returns after enqueueing. */
+pcr_status pcr_retrieve(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out,
+                        void* cuda_stream);
+
+/* Batched retrieval: n (handle, plan, output) triples, one work list per
+ * stage.  Used by the serving loop. */
+pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
+                              void* const* d_outs, void* cuda_stream);
+
+/* ---- introspection / persistence -------------------------------------- */
+pcr_status pcr_num_streams(const pcr_handle* h, int* n);
+pcr_status pcr_stream_info_get(const pcr_handle* h, int i, pcr_stream_info* out);
+/* Error tables of stream i: maxerr[B+1], sq[B+1] (FP64) and bytes[B+1]. */
+pcr_status pcr_stream_tables(const pcr_handle* h, int i, double* maxerr, double* sq,
+                             uint64_t* bytes);
+/* Field statistics: min, max, fixed-point exponent G (max|x| < 2^G). */
+pcr_status pcr_field_stats(const pcr_handle* h, double* xmin, double* xmax, int* G);
+/* Copy stream i's plane words ([B][words] u32) and sign area to host. */
+pcr_status pcr_stream_copy(const pcr_handle* h, int i, uint32_t* planes_host,
+                           uint32_t* signs_host, uint32_t* sign_counts_host,
+                           uint64_t* pairs_host);
+/* Max-ordering segment errors of a per-level decomposed level 0 (M_0 of
+ * Algorithm 1); *n receives the count (0 when not applicable), errs may be
+ * NULL to query the count. */
+pcr_status pcr_max_ordering(const pcr_handle* h, double* errs, int* n);
+/* Container: header + tables + stream directory + payload, CRC32 per
+ * section.  *buf is malloc'ed; release with pcr_buffer_free. */
+pcr_status pcr_serialize(const pcr_handle* h, void** buf, size_t* len);
+pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_allocator* alloc,
+                           void* cuda_stream, pcr_handle** out);
+void pcr_buffer_free(void* buf);
+void pcr_free(pcr_handle* h);
+const char* pcr_last_error(void);
+
+/* ---- test entry: encode given coefficients ---------------------------- */
+/* Encode one stream of n_pad values already in canonical padded order
+ * (`d_vals`: float, double or int64 fixed point per `value_kind` 0/1/2)
+ * with B planes and `encoding`; writes plane words [B][n_pad/32], the sign
+ * area, sign counts, plane nonzero-word counts and (want_pairs) plane pair
+ * counts to host arrays.  Lets tests feed the oracle's own coefficients. */
+pcr_status pcr_debug_encode(const void* d_vals, int64_t n_pad, int value_kind, int B,
+                            int encoding, int want_pairs, void* cuda_stream,
+                            uint32_t* planes_host, uint32_t* signs_host,
+                            uint32_t* sign_counts_host, uint32_t* plane_nz_host,
+                            uint64_t* pairs_host, double* vmax_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCR_H */

@@ -1,0 +1,363 @@
+"""Python binding of the B300 progressive refactor / retrieve library.
+
+Argument marshalling only: every step of the refactor and retrieval path runs
+in the CUDA kernels of ``libpcr.so`` (C ABI in ``include/pcr.h``).  PyTorch
+provides device memory (its caching allocator, passed to the library as a
+``pcr_allocator``) and CUDA streams.  There is no CPU fallback: importing this
+package fails loudly when the library is missing.
+
+Method: arXiv 2609.04573 (ProAICD) -- adaptive multilevel interpolation
+(Sec. IV), coefficient decomposition (Sec. V), bitplane streams with error
+tables (Sec. V-C), bound-driven retrieval (Sec. III-A, Alg. 2).
+"""
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence, Tuple
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libpcr.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(
+        f"{_LIB_PATH} is missing: build it with `python -m paper_2609_04573_b300.build` "
+        "(nvcc, sm_103a).  There is no CPU fallback.")
+_lib = C.CDLL(_LIB_PATH)
+
+MAX_STREAMS = 64
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSAT, ERR_CORRUPT = range(8)
+_STATUS = ["OK", "INVALID_ARG", "UNSUPPORTED", "OOM", "CUDA", "TIMEOUT", "UNSATISFIABLE", "CORRUPT"]
+
+
+class PcrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"pcr {_STATUS[status] if status < len(_STATUS) else status}: {msg}")
+        self.status = status
+
+
+class Unsatisfiable(PcrError):
+    pass
+
+
+class _Scheme(C.Structure):
+    _fields_ = [("mode", C.c_int), ("interp", C.c_int), ("degree", C.c_int),
+                ("order", C.c_int * 3), ("decomp_axis", C.c_int), ("encoding", C.c_int),
+                ("nlevels", C.c_int), ("nplanes", C.c_int)]
+
+
+class _Target(C.Structure):
+    _fields_ = [("kind", C.c_int), ("value", C.c_double)]
+
+
+class _Plan(C.Structure):
+    _fields_ = [("nstreams", C.c_int), ("planes", C.c_int * MAX_STREAMS), ("bound", C.c_double),
+                ("psnr_bound", C.c_double), ("bytes", C.c_uint64), ("satisfied", C.c_int)]
+
+
+class _StreamInfo(C.Structure):
+    _fields_ = [("level", C.c_int), ("region", C.c_int), ("sub", C.c_int), ("is_fixed", C.c_int),
+                ("nplanes", C.c_int), ("n_real", C.c_int64), ("n_pad", C.c_int64),
+                ("words", C.c_int64), ("nseg", C.c_int64), ("exponent", C.c_int),
+                ("shift", C.c_int), ("vmax", C.c_double)]
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class _Allocator(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("alloc", _ALLOC_FN), ("free", _FREE_FN)]
+
+
+_vp, _i64p = C.c_void_p, C.POINTER(C.c_int64)
+_sigs = {
+    "pcr_refactor": [_vp, C.c_int, _i64p, C.c_int, C.POINTER(_Scheme), C.POINTER(_Allocator), _vp, C.POINTER(_vp)],
+    "pcr_refactor_batch": [C.c_int, C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(_i64p), C.POINTER(C.c_int),
+                           C.POINTER(_Scheme), C.POINTER(_Allocator), _vp, C.POINTER(_vp)],
+    "pcr_plan": [_vp, C.POINTER(_Target), C.POINTER(_Plan)],
+    "pcr_retrieve": [_vp, C.POINTER(_Plan), _vp, _vp],
+    "pcr_retrieve_batch": [C.c_int, C.POINTER(_vp), C.POINTER(_Plan), C.POINTER(_vp), _vp],
+    "pcr_num_streams": [_vp, C.POINTER(C.c_int)],
+    "pcr_stream_info_get": [_vp, C.c_int, C.POINTER(_StreamInfo)],
+    "pcr_stream_tables": [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_uint64)],
+    "pcr_field_stats": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)],
+    "pcr_stream_copy": [_vp, C.c_int, _vp, _vp, _vp, _vp],
+    "pcr_max_ordering": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int)],
+    "pcr_serialize": [_vp, C.POINTER(_vp), C.POINTER(C.c_size_t)],
+    "pcr_deserialize": [_vp, C.c_size_t, C.POINTER(_Allocator), _vp, C.POINTER(_vp)],
+    "pcr_debug_encode": [_vp, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
+                         C.POINTER(C.c_double)],
+}
+for _name, _args in _sigs.items():
+    fn = getattr(_lib, _name)
+    fn.argtypes = _args
+    fn.restype = C.c_int
+_lib.pcr_free.argtypes = [_vp]
+_lib.pcr_free.restype = None
+_lib.pcr_buffer_free.argtypes = [_vp]
+_lib.pcr_buffer_free.restype = None
+_lib.pcr_last_error.argtypes = []
+_lib.pcr_last_error.restype = C.c_char_p
+
+# exported symbols (checked by the CPU tests against include/pcr.h)
+EXPORTS = sorted(list(_sigs) + ["pcr_free", "pcr_buffer_free", "pcr_last_error"])
+
+
+def _check(st):
+    if st != OK:
+        msg = _lib.pcr_last_error().decode()
+        raise (Unsatisfiable if st == ERR_UNSAT else PcrError)(st, msg)
+
+
+# ---- torch-backed allocator (the library allocates through torch) --------
+_live = {}
+
+
+def _torch_alloc(ctx, nbytes, stream):
+    try:
+        dev = torch.cuda.current_device()
+        ptr = torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
+        return ptr
+    except Exception:  # out of memory -> NULL -> PCR_ERR_OOM
+        return None
+
+
+def _torch_free(ctx, ptr, stream):
+    if ptr:
+        torch.cuda.caching_allocator_delete(ptr)
+
+
+_ALLOC_CB = _ALLOC_FN(_torch_alloc)
+_FREE_CB = _FREE_FN(_torch_free)
+_ALLOCATOR = _Allocator(None, _ALLOC_CB, _FREE_CB)
+
+EB, PSNR = 0, 1
+LEVEL, REGION = 0, 1
+LINEAR, CUBIC = 1, 3
+GENERIC, NEGABINARY = 1, 2
+_DT = {torch.float32: 0, torch.float64: 1}
+
+
+@dataclass
+class Scheme:
+    """Refactoring scheme (Sec. IV-VI, tuning table of Sec. VI-A)."""
+    mode: str = "eb"                 # "eb" | "psnr"
+    interp: str = "level"            # "level" | "region"
+    degree: str = "cubic"            # "linear" | "cubic"
+    order: Optional[Tuple[int, ...]] = None
+    decomp_axis: int = -1
+    encoding: Optional[str] = None   # None = generic (eb) / negabinary (psnr)
+    nlevels: int = 0
+    nplanes: int = 0
+
+    @classmethod
+    def for_target(cls, kind, **kw):
+        """The paper's adaptive choice (Sec. IV, VI-A): error-bound targets use
+        per-level interpolation with generic bitplanes; PSNR targets use
+        per-region interpolation with negabinary + XOR."""
+        if kind == "psnr":
+            return cls(mode="psnr", interp="region", **kw)
+        return cls(mode="eb", interp="level", **kw)
+
+    def c(self, ndim):
+        s = _Scheme()
+        s.mode = PSNR if self.mode == "psnr" else EB
+        s.interp = REGION if self.interp == "region" else LEVEL
+        s.degree = CUBIC if self.degree == "cubic" else LINEAR
+        order = self.order or tuple(range(ndim))
+        for i in range(3):
+            s.order[i] = order[i] if i < len(order) else 0
+        s.decomp_axis = self.decomp_axis
+        s.encoding = {None: 0, "generic": GENERIC, "negabinary": NEGABINARY}[self.encoding]
+        s.nlevels = self.nlevels
+        s.nplanes = self.nplanes
+        return s
+
+
+@dataclass
+class Target:
+    kind: str      # "abs" | "rel" | "psnr"
+    value: float
+
+    def c(self):
+        return _Target({"abs": 0, "rel": 1, "psnr": 2}[self.kind], float(self.value))
+
+
+@dataclass
+class Plan:
+    planes: list
+    bound: float
+    psnr_bound: float
+    bytes: int
+    satisfied: bool
+    _c: object = field(default=None, repr=False)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Handle:
+    """Refactored field: device streams + host tables (owned by the library)."""
+
+    def __init__(self, ptr, shape, dtype, device):
+        self._p = C.c_void_p(ptr)
+        self.shape = tuple(shape)
+        self.dtype = dtype
+        self.device = device
+
+    def __del__(self):
+        if getattr(self, "_p", None) and self._p.value:
+            _lib.pcr_free(self._p)
+            self._p = C.c_void_p(None)
+
+    @property
+    def nstreams(self):
+        n = C.c_int()
+        _check(_lib.pcr_num_streams(self._p, C.byref(n)))
+        return n.value
+
+    def stream_info(self, i):
+        s = _StreamInfo()
+        _check(_lib.pcr_stream_info_get(self._p, i, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in _StreamInfo._fields_}
+
+    def tables(self, i):
+        B = self.stream_info(i)["nplanes"]
+        me = (C.c_double * (B + 1))()
+        sq = (C.c_double * (B + 1))()
+        by = (C.c_uint64 * (B + 1))()
+        _check(_lib.pcr_stream_tables(self._p, i, me, sq, by))
+        return dict(maxerr=list(me), sq=list(sq), bytes=list(by))
+
+    def field_stats(self):
+        a, b, g = C.c_double(), C.c_double(), C.c_int()
+        _check(_lib.pcr_field_stats(self._p, C.byref(a), C.byref(b), C.byref(g)))
+        return a.value, b.value, g.value
+
+    def stream_copy(self, i):
+        """Plane words [B, words], sign area, sign counts [nseg, B], pairs."""
+        import numpy as np
+        info = self.stream_info(i)
+        B, words, nseg = info["nplanes"], info["words"], info["nseg"]
+        planes = np.zeros((B, words), np.uint32)
+        signs = np.zeros((nseg, 128 + B), np.uint32)
+        scnt = np.zeros((nseg, B), np.uint32)
+        pairs = np.zeros((B, B), np.uint64)
+        _check(_lib.pcr_stream_copy(self._p, i, planes.ctypes.data, signs.ctypes.data,
+                                    scnt.ctypes.data, pairs.ctypes.data))
+        return planes, signs, scnt, pairs
+
+    def max_ordering(self):
+        n = C.c_int()
+        _check(_lib.pcr_max_ordering(self._p, None, C.byref(n)))
+        if n.value == 0:
+            return []
+        arr = (C.c_double * n.value)()
+        _check(_lib.pcr_max_ordering(self._p, arr, C.byref(n)))
+        return list(arr)
+
+    def plan(self, target, allow_unsat=False):
+        p = _Plan()
+        st = _lib.pcr_plan(self._p, C.byref(target.c()), C.byref(p))
+        if st != OK and not (st == ERR_UNSAT and allow_unsat):
+            _check(st)
+        return Plan(list(p.planes[:p.nstreams]), p.bound, p.psnr_bound, p.bytes, bool(p.satisfied), p)
+
+    def plan_from_planes(self, planes):
+        p = _Plan()
+        p.nstreams = len(planes)
+        for i, b in enumerate(planes):
+            p.planes[i] = int(b)
+        return Plan(list(planes), 0.0, 0.0, 0, True, p)
+
+    def retrieve(self, target_or_plan, out=None, stream=None):
+        """Reconstruct into ``out`` (allocated when None).  Returns (out, plan)."""
+        plan = target_or_plan if isinstance(target_or_plan, Plan) else self.plan(target_or_plan)
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device=self.device)
+        assert out.is_contiguous() and tuple(out.shape) == self.shape and out.dtype == self.dtype
+        _check(_lib.pcr_retrieve(self._p, C.byref(plan._c), C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out, plan
+
+    def serialize(self):
+        buf, n = C.c_void_p(), C.c_size_t()
+        _check(_lib.pcr_serialize(self._p, C.byref(buf), C.byref(n)))
+        data = C.string_at(buf, n.value)
+        _lib.pcr_buffer_free(buf)
+        return data
+
+
+def refactor(x, scheme=None, stream=None):
+    """Refactor a contiguous CUDA float32/float64 tensor (2-D or 3-D)."""
+    scheme = scheme or Scheme()
+    if not (x.is_cuda and x.is_contiguous() and x.dtype in _DT and x.dim() in (2, 3)):
+        raise ValueError("refactor expects a contiguous 2-D/3-D float32/float64 CUDA tensor")
+    dims = (C.c_int64 * x.dim())(*x.shape)
+    out = C.c_void_p()
+    _check(_lib.pcr_refactor(C.c_void_p(x.data_ptr()), x.dim(), dims, _DT[x.dtype],
+                             C.byref(scheme.c(x.dim())), C.byref(_ALLOCATOR), _stream_ptr(stream),
+                             C.byref(out)))
+    return Handle(out.value, x.shape, x.dtype, x.device)
+
+
+def refactor_batch(xs: Sequence[torch.Tensor], schemes, stream=None):
+    """One work list per pipeline stage for all fields (batched form)."""
+    n = len(xs)
+    if not isinstance(schemes, (list, tuple)):
+        schemes = [schemes] * n
+    ptrs = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    nd = (C.c_int * n)(*[x.dim() for x in xs])
+    dim_arrs = [(C.c_int64 * x.dim())(*x.shape) for x in xs]
+    dims = (_i64p * n)(*[C.cast(d, _i64p) for d in dim_arrs])
+    dts = (C.c_int * n)(*[_DT[x.dtype] for x in xs])
+    sch = (_Scheme * n)(*[s.c(x.dim()) for s, x in zip(schemes, xs)])
+    outs = (C.c_void_p * n)()
+    _check(_lib.pcr_refactor_batch(n, ptrs, nd, dims, dts, sch, C.byref(_ALLOCATOR),
+                                   _stream_ptr(stream), outs))
+    return [Handle(outs[i], x.shape, x.dtype, x.device) for i, x in enumerate(xs)]
+
+
+def retrieve_batch(handles, plans, outs, stream=None):
+    n = len(handles)
+    hp = (C.c_void_p * n)(*[h._p.value for h in handles])
+    pl = (_Plan * n)(*[p._c for p in plans])
+    op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    _check(_lib.pcr_retrieve_batch(n, hp, pl, op, _stream_ptr(stream)))
+    return outs
+
+
+def deserialize(data: bytes, device=None, stream=None):
+    import struct
+    out = C.c_void_p()
+    buf = C.create_string_buffer(data, len(data))
+    _check(_lib.pcr_deserialize(buf, len(data), C.byref(_ALLOCATOR), _stream_ptr(stream), C.byref(out)))
+    # header: magic, hdr len, crc, then ndim, dims[3], dtype
+    ndim = struct.unpack_from("<i", data, 20)[0]
+    dims = struct.unpack_from("<3q", data, 24)[:ndim]
+    dtype = torch.float32 if struct.unpack_from("<i", data, 48)[0] == 0 else torch.float64
+    return Handle(out.value, dims, dtype, device or torch.device("cuda", torch.cuda.current_device()))
+
+
+def debug_encode(vals: torch.Tensor, value_kind: int, B: int, encoding: int, want_pairs: bool, stream=None):
+    """Test entry: encode already-ordered padded values (see pcr_debug_encode)."""
+    import numpy as np
+    n = vals.numel()
+    words, nseg = n // 32, -(-n // 4096)
+    planes = np.zeros((B, words), np.uint32)
+    signs = np.zeros((nseg, 128 + B), np.uint32)
+    scnt = np.zeros((nseg, B), np.uint32)
+    pnz = np.zeros(B, np.uint32)
+    pairs = np.zeros((B, B), np.uint64)
+    vmax = C.c_double()
+    _check(_lib.pcr_debug_encode(C.c_void_p(vals.data_ptr()), n, value_kind, B, encoding, int(want_pairs),
+                                 _stream_ptr(stream), planes.ctypes.data, signs.ctypes.data,
+                                 scnt.ctypes.data, pnz.ctypes.data, pairs.ctypes.data, C.byref(vmax)))
+    return dict(planes=planes, signs=signs, sign_counts=scnt, plane_nz=pnz, pairs=pairs, vmax=vmax.value)
+
+
+def library_path():
+    return _LIB_PATH

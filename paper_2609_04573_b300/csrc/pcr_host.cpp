@@ -1,0 +1,1950 @@
+// Host side of the progressive refactor / retrieve library: geometry,
+// error tables, bound composition, max ordering, the greedy planner, the
+// container and the C ABI (include/pcr.h).  Section references are to
+// arXiv 2609.04573 (ProAICD).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/pcr.h"
+#include "pcr_internal.h"
+
+namespace pcr {
+// kernels (pcr_kernels.cu)
+void launch_minmax(int vk, const void* x, int64_t n, FieldStats* st, cudaStream_t s);
+void launch_to_fixed(int vk, const void* x, const FieldD& f, const FieldStats* st, int64_t* xc, cudaStream_t s);
+void launch_coef_fixed(const FieldD& f, int level, int raw, const LatD& lat, const int64_t* xc, int64_t* out,
+                       unsigned long long* vmax, cudaStream_t s);
+void launch_coef_l0(int vk, const FieldD& f, const LatD& lat, int compact, const void* x, void* out,
+                    unsigned long long* vmax, unsigned long long* c0, cudaStream_t s);
+void launch_raw_stage(int vk, const FieldD& f, const LatD& lat, const void* x, void* out,
+                      unsigned long long* vmax, cudaStream_t s);
+void launch_decompose(int vk, const DecompGeo& dg, const LatD& sl, const void* comp, void* out,
+                      unsigned long long* vmax, cudaStream_t s);
+void launch_recompose(int vk, const DecompGeo& dg, const LatD& sl, const void* dec, void* comp, cudaStream_t s);
+void launch_recon_fixed(const FieldD& f, int level, int raw, const LatD& lat, const int64_t* chat, int64_t* xc,
+                        cudaStream_t s);
+void launch_coarse_out(int vk, const FieldD& f, const int64_t* xc, double scale, void* out, cudaStream_t s);
+void launch_recon_l0(int vk, const FieldD& f, const LatD& lat, int compact, const void* chat, void* out,
+                     cudaStream_t s);
+void launch_copy_raw(int vk, const FieldD& f, const LatD& lat, const void* vals, void* out, cudaStream_t s);
+void launch_encode(int vk, int w64, int pairs, const StreamD* d_streams, const WorkItem* d_items, int nitems,
+                   cudaStream_t s);
+void launch_decode(int vk, int w64, const StreamD* d_streams, const WorkItem* d_items, int nitems,
+                   cudaStream_t s);
+}  // namespace pcr
+
+using namespace pcr;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static pcr_status fail(pcr_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                                \
+  do {                                                                                \
+    cudaError_t _e = (expr);                                                          \
+    if (_e != cudaSuccess)                                                            \
+      return fail(PCR_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+extern "C" const char* pcr_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// memory
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Mem {
+  pcr_allocator a{};
+  bool user = false;
+  void* alloc(size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    if (user) return a.alloc(a.ctx, bytes, (void*)s);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void free(void* p, cudaStream_t s) {
+    if (!p) return;
+    if (user) a.free(a.ctx, p, (void*)s);
+    else cudaFreeAsync(p, s);
+  }
+};
+
+Mem make_mem(const pcr_allocator* a) {
+  Mem m;
+  if (a && a->alloc && a->free) {
+    m.a = *a;
+    m.user = true;
+  }
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// geometry (Sec. IV, V-B, V-C): levels, regions, decomposition sub-levels,
+// streams as concatenated lattices with rows padded to 32 elements
+// ---------------------------------------------------------------------------
+int64_t count_from(int64_t n, int64_t start, int64_t step) {
+  if (n - 1 < start) return 0;
+  return (n - 1 - start) / step + 1;
+}
+
+struct Lat {
+  int64_t start[3] = {0, 0, 0}, step[3] = {1, 1, 1}, count[3] = {1, 1, 1};
+  int64_t row_pad() const { return (count[2] + 31) / 32 * 32; }
+  int64_t n_real() const { return count[0] * count[1] * count[2]; }
+  int64_t n_pad() const { return count[0] * count[1] * row_pad(); }
+};
+
+struct SGeo {
+  int level = 0, region = 0, sub = 0;
+  bool is_fix = false;
+  std::vector<Lat> lats;
+  int64_t n_real() const {
+    int64_t t = 0;
+    for (auto& l : lats) t += l.n_real();
+    return t;
+  }
+  int64_t n_pad() const {
+    int64_t t = 0;
+    for (auto& l : lats) t += l.n_pad();
+    return t;
+  }
+};
+
+Lat region_lat(const int64_t* n3, int level, const std::vector<int>& order, int r) {
+  const int64_t s = int64_t(1) << level;
+  Lat l;
+  const int a = order[r - 1];
+  l.start[a] = s;
+  l.step[a] = 2 * s;
+  l.count[a] = count_from(n3[a], s, 2 * s);
+  for (size_t i = r; i < order.size(); i++) {
+    const int b = order[i];
+    l.step[b] = 2 * s;
+    l.count[b] = count_from(n3[b], 0, 2 * s);
+  }
+  for (int i = 0; i < r - 1; i++) {
+    const int b = order[i];
+    l.step[b] = s;
+    l.count[b] = count_from(n3[b], 0, s);
+  }
+  return l;
+}
+
+Lat coarse_lat(const int64_t* n3, int L) {
+  const int64_t S = int64_t(1) << (L - 1);
+  Lat l;
+  for (int a = 0; a < 3; a++)
+    if (n3[a] > 1) {
+      l.step[a] = S;
+      l.count[a] = count_from(n3[a], 0, S);
+    }
+  return l;
+}
+
+Lat sub_lat(const Lat& R, int u, int v, int su, int tu, int sv, int tv) {
+  Lat l = R;
+  const int ax[2] = {u, v};
+  const int s0[2] = {su, sv}, t0[2] = {tu, tv};
+  for (int i = 0; i < 2; i++) {
+    const int a = ax[i];
+    l.start[a] = R.start[a] + R.step[a] * s0[i];
+    l.step[a] = R.step[a] * t0[i];
+    l.count[a] = count_from(R.count[a], s0[i], t0[i]);
+  }
+  return l;
+}
+
+// S1 = 4-grid, S2 = 2-grid minus 4-grid, S3 = the rest; each made of the
+// regions of a 2-D per-level hierarchy (odd along u first, then v)
+const int kSub[3][2][4] = {{{0, 4, 0, 4}, {-1, 0, 0, 0}},
+                           {{2, 4, 0, 4}, {0, 2, 2, 4}},
+                           {{1, 2, 0, 2}, {0, 1, 1, 2}}};
+
+std::vector<SGeo> build_streams(const int64_t* n3, int L, int interp, const std::vector<int>& order, int dax) {
+  std::vector<SGeo> out;
+  SGeo c;
+  c.level = L - 1;
+  c.is_fix = L - 1 >= 1;
+  c.lats.push_back(coarse_lat(n3, L));
+  out.push_back(c);
+  const int d = (int)order.size();
+  for (int level = L - 2; level >= 0; level--) {
+    std::vector<Lat> regs;
+    for (int r = 1; r <= d; r++) regs.push_back(region_lat(n3, level, order, r));
+    if (level == 0 && dax >= 0) {
+      int u = -1, v = -1;
+      for (int a = 0; a < 3; a++)
+        if (a != dax) (u < 0 ? u : v) = a;
+      for (int r = 1; r <= d; r++)
+        for (int k = 0; k < 3; k++) {
+          SGeo g;
+          g.level = 0;
+          g.region = r;
+          g.sub = k + 1;
+          for (int part = 0; part < 2; part++) {
+            if (kSub[k][part][0] < 0) continue;
+            const int* p = kSub[k][part];
+            g.lats.push_back(sub_lat(regs[r - 1], u, v, p[0], p[1], p[2], p[3]));
+          }
+          out.push_back(g);
+        }
+    } else if (interp == 0) {
+      SGeo g;
+      g.level = level;
+      g.is_fix = level >= 1;
+      g.lats = regs;
+      out.push_back(g);
+    } else {
+      for (int r = 1; r <= d; r++) {
+        SGeo g;
+        g.level = level;
+        g.region = r;
+        g.is_fix = level >= 1;
+        g.lats.push_back(regs[r - 1]);
+        out.push_back(g);
+      }
+    }
+  }
+  return out;
+}
+
+int auto_levels(const int64_t* n3) {
+  int64_t m = INT64_MAX;
+  for (int a = 0; a < 3; a++)
+    if (n3[a] > 1) m = std::min(m, n3[a]);
+  int L = 0;
+  while ((int64_t(1) << (L + 1)) <= m - 1) L++;
+  return std::max(1, L);
+}
+
+int max_levels(const int64_t* n3) {
+  int64_t m = INT64_MAX;
+  for (int a = 0; a < 3; a++)
+    if (n3[a] > 1) m = std::min(m, n3[a]);
+  int L = 1;
+  while ((int64_t(1) << L) <= m - 1) L++;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// exact integers for the squared-error tables (up to 384 bits)
+// ---------------------------------------------------------------------------
+struct Big {
+  static constexpr int N = 6;
+  uint64_t w[N] = {0, 0, 0, 0, 0, 0};
+  static Big from(uint64_t v) {
+    Big b;
+    b.w[0] = v;
+    return b;
+  }
+  void add(const Big& o) {
+    unsigned __int128 c = 0;
+    for (int i = 0; i < N; i++) {
+      c += (unsigned __int128)w[i] + o.w[i];
+      w[i] = (uint64_t)c;
+      c >>= 64;
+    }
+  }
+  void sub(const Big& o) {  // requires *this >= o
+    unsigned __int128 br = 0;
+    for (int i = 0; i < N; i++) {
+      unsigned __int128 t = (unsigned __int128)w[i] - o.w[i] - br;
+      w[i] = (uint64_t)t;
+      br = (t >> 127) & 1;
+    }
+  }
+  static Big shl(uint64_t v, int s) {  // v << s
+    Big b;
+    const int q = s / 64, r = s % 64;
+    if (q < N) b.w[q] = v << r;
+    if (r && q + 1 < N) b.w[q + 1] = v >> (64 - r);
+    return b;
+  }
+  Big mul(uint64_t m) const {
+    Big b;
+    unsigned __int128 c = 0;
+    for (int i = 0; i < N; i++) {
+      c += (unsigned __int128)w[i] * m;
+      b.w[i] = (uint64_t)c;
+      c >>= 64;
+    }
+    return b;
+  }
+  Big mulb(const Big& o) const {
+    Big b;
+    for (int i = 0; i < N; i++) {
+      unsigned __int128 c = 0;
+      for (int j = 0; i + j < N; j++) {
+        c += (unsigned __int128)w[i] * o.w[j] + b.w[i + j];
+        b.w[i + j] = (uint64_t)c;
+        c >>= 64;
+      }
+    }
+    return b;
+  }
+  int cmp(const Big& o) const {
+    for (int i = N - 1; i >= 0; i--)
+      if (w[i] != o.w[i]) return w[i] < o.w[i] ? -1 : 1;
+    return 0;
+  }
+  int bitlen() const {
+    for (int i = N - 1; i >= 0; i--)
+      if (w[i]) return 64 * i + 64 - __builtin_clzll(w[i]);
+    return 0;
+  }
+  bool bit(int i) const { return (w[i / 64] >> (i % 64)) & 1; }
+  void setbit(int i) { w[i / 64] |= uint64_t(1) << (i % 64); }
+  // smallest double >= value
+  double to_double_up() const {
+    const int t = bitlen();
+    if (t <= 53) {
+      uint64_t v = w[0];
+      return (double)v;
+    }
+    const int drop = t - 53;
+    uint64_t m = 0;
+    for (int i = t - 1; i >= drop; i--) m = (m << 1) | (uint64_t)bit(i);
+    bool rest = false;
+    for (int i = 0; i < drop && !rest; i++) rest = bit(i);
+    if (rest) m += 1;
+    return std::ldexp((double)m, drop);
+  }
+  Big isqrt_ceil() const {
+    Big r;
+    const int t = (bitlen() + 1) / 2 + 1;
+    for (int i = t; i >= 0; i--) {
+      Big c = r;
+      c.setbit(i);
+      if (c.mulb(c).cmp(*this) <= 0) r = c;
+    }
+    if (r.mulb(r).cmp(*this) < 0) r.add(Big::from(1));
+    return r;
+  }
+};
+
+double up_u64(uint64_t v) { return Big::from(v).to_double_up(); }
+
+// ---------------------------------------------------------------------------
+// ||P^T P||_inf of the 1-D odd-point operator of a line of m points
+// (L2 composition); weights are dyadic so every sum is exact
+// ---------------------------------------------------------------------------
+double rowsum_ptp(int64_t m, int degree) {
+  static std::map<std::pair<int64_t, int>, double> cache;
+  auto key = std::make_pair(m, degree);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  const int64_t mc = (m + 1) / 2;
+  // rows of P: list of (column, weight)
+  std::vector<std::vector<std::pair<int64_t, double>>> cols(mc);  // column -> (row, weight)
+  std::vector<std::vector<std::pair<int64_t, double>>> rows(m / 2);
+  for (int64_t t = 0, j = 1; j < m; j += 2, t++) {
+    const bool p1 = j + 1 < m, m3 = j - 3 >= 0, p3 = j + 3 < m;
+    std::vector<std::pair<int64_t, double>> w;
+    if (degree == 3 && p1 && m3 && p3) w = {{j - 3, -1.0 / 16}, {j - 1, 9.0 / 16}, {j + 1, 9.0 / 16}, {j + 3, -1.0 / 16}};
+    else if (degree == 3 && p1 && p3) w = {{j - 1, 3.0 / 8}, {j + 1, 6.0 / 8}, {j + 3, -1.0 / 8}};
+    else if (degree == 3 && p1 && m3) w = {{j - 3, -1.0 / 8}, {j - 1, 6.0 / 8}, {j + 1, 3.0 / 8}};
+    else if (p1) w = {{j - 1, 0.5}, {j + 1, 0.5}};
+    else w = {{j - 1, 1.0}};
+    for (auto& pr : w) {
+      rows[t].push_back({pr.first / 2, pr.second});
+      cols[pr.first / 2].push_back({t, pr.second});
+    }
+  }
+  double best = 0.0;
+  for (int64_t a = 0; a < mc; a++) {
+    std::map<int64_t, double> acc;
+    for (auto& rw : cols[a])
+      for (auto& cw : rows[rw.first]) acc[cw.first] += rw.second * cw.second;
+    double s = 0.0;
+    for (auto& kv : acc) s += std::fabs(kv.second);
+    best = std::max(best, s);
+  }
+  cache[key] = best;
+  return best;
+}
+
+// ---------------------------------------------------------------------------
+// tables, composition and planning
+// ---------------------------------------------------------------------------
+struct Tab {
+  std::vector<double> maxerr, sq;
+  std::vector<uint64_t> bytes;
+};
+
+constexpr double kMargin = 1.000000001;
+
+struct Meta {
+  int L = 1, d = 1, degree = 3, interp = 0, dtype = 0, decomp = -1;
+  double h = 0, M = 0, C0 = 0, R = 0;
+  int64_t n = 0;
+  std::map<int, int64_t> level_counts;
+  std::map<std::pair<int, int>, int64_t> region_counts;
+  std::map<int, double> level_factor;
+  std::map<std::pair<int, int>, double> region_factor;
+  std::map<int, std::pair<double, double>> decomp_factors;
+};
+
+struct SRef {
+  int level, region, sub;
+};
+
+struct Composer {
+  Meta m;
+  std::vector<SRef> st;
+  std::map<int, std::vector<int>> by_level;
+  double lam, uw, lam_d, pf, rho_fix;
+
+  void init(const Meta& meta, const std::vector<SRef>& streams) {
+    m = meta;
+    st = streams;
+    lam = m.degree == 3 ? 1.25 : 1.0;
+    uw = m.dtype == PCR_F32 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+    const double kap = m.degree == 3 ? 3.625 : 1.0;
+    double lam_d1 = 1.0;
+    for (int i = 0; i < m.d - 1; i++) lam_d1 *= lam;
+    lam_d = lam_d1 * lam;
+    pf = m.interp == 0 ? ((double)m.d * kap * lam_d1) : kap;
+    rho_fix = (2.0 * (double)m.d * lam_d1 + 2.0) * m.h;
+    by_level.clear();
+    for (size_t i = 0; i < st.size(); i++) by_level[st[i].level].push_back((int)i);
+  }
+
+  double rho0(double E1, double e0sum) const {
+    if (m.L == 1) return kMargin * 1.01 * uw * m.C0;
+    const double V = m.M + lam_d * E1 + e0sum;
+    return 1.01 * uw * (2.0 * pf * V + lam_d * V + 2.0 * V + 12.0 * m.C0);
+  }
+
+  // region -> summed error, in order of first appearance (stream order)
+  std::vector<std::pair<int, double>> region_errors(int level, const std::vector<double>& err) const {
+    std::vector<std::pair<int, double>> out;
+    for (int i : by_level.at(level)) {
+      const int r = st[i].region;
+      bool found = false;
+      for (auto& pr : out)
+        if (pr.first == r) {
+          pr.second = pr.second + err[i];
+          found = true;
+        }
+      if (!found) out.push_back({r, 0.0 + err[i]});
+    }
+    return out;
+  }
+
+  double level_step(double E, const std::vector<std::pair<int, double>>& reg, double rho) const {
+    if (m.interp == 0) {
+      double e = reg[0].second;
+      for (auto& pr : reg) e = std::max(e, pr.second);
+      return lam_d * E + e + rho;
+    }
+    auto sorted = reg;
+    std::sort(sorted.begin(), sorted.end());
+    std::vector<double> F;
+    for (auto& pr : sorted) {
+      double base = E;
+      for (double f : F) base = std::max(base, f);
+      F.push_back(lam * base + pr.second + rho);
+    }
+    for (double f : F) E = std::max(E, f);
+    return E;
+  }
+
+  static double sum_vals(const std::vector<std::pair<int, double>>& reg) {
+    double s = 0.0;
+    for (auto& pr : reg) s += pr.second;
+    return s;
+  }
+
+  double linf(const std::vector<double>& err) const {
+    const int L = m.L;
+    double E = err[by_level.at(L - 1)[0]] + (L - 1 >= 1 ? m.h : 0.0);
+    if (L == 1) return (E + rho0(0.0, 0.0)) * kMargin;
+    for (int level = L - 2; level >= 0; level--) {
+      auto reg = region_errors(level, err);
+      const double rho = level == 0 ? rho0(E, sum_vals(reg)) : rho_fix;
+      E = level_step(E, reg, rho);
+    }
+    return E * kMargin;
+  }
+
+  void e1_e0(const std::vector<double>& err, double& E1, double& e0) const {
+    const int L = m.L;
+    if (L == 1) {
+      E1 = e0 = 0.0;
+      return;
+    }
+    double E = err[by_level.at(L - 1)[0]] + (L - 1 >= 1 ? m.h : 0.0);
+    for (int level = L - 2; level >= 1; level--) E = level_step(E, region_errors(level, err), rho_fix);
+    E1 = E;
+    e0 = sum_vals(region_errors(0, err));
+  }
+
+  double l2(const std::vector<double>& sq, const std::vector<double>& err) const {
+    const int L = m.L;
+    double N = std::sqrt(sq[by_level.at(L - 1)[0]]);
+    if (L == 1) {
+      N += rho0(0.0, 0.0) * std::sqrt((double)m.level_counts.at(0));
+      return (N * N) * kMargin;
+    }
+    N += m.h * std::sqrt((double)m.level_counts.at(L - 1));
+    double E1, e0;
+    e1_e0(err, E1, e0);
+    for (int level = L - 2; level >= 0; level--) {
+      const double rho = level == 0 ? rho0(E1, e0) : rho_fix;
+      std::map<int, std::vector<std::pair<int, int>>> groups;
+      for (int i : by_level.at(level)) groups[st[i].region].push_back({st[i].sub, i});
+      std::map<int, double> cnorm;
+      for (auto& g : groups) {
+        auto items = g.second;
+        std::sort(items.begin(), items.end());
+        if (items[0].first == 0) {
+          cnorm[g.first] = std::sqrt(sq[items[0].second]);
+        } else {
+          const auto f = m.decomp_factors.at(g.first);
+          const double n1 = std::sqrt(sq[items[0].second]);
+          const double n2 = std::sqrt(sq[items[1].second]) + f.first * n1;
+          const double n3 = std::sqrt(sq[items[2].second]) + f.second * std::sqrt(n1 * n1 + n2 * n2);
+          cnorm[g.first] = std::sqrt(n1 * n1 + n2 * n2 + n3 * n3);
+        }
+      }
+      if (m.interp == 0) {
+        double c = 0.0;
+        for (auto& kv : cnorm) c += kv.second * kv.second;
+        const double t = m.level_factor.at(level) * N + std::sqrt(c) +
+                         rho * std::sqrt((double)m.level_counts.at(level));
+        N = std::sqrt(N * N + t * t);
+      } else {
+        double T = N * N;
+        for (auto& kv : cnorm) {
+          const double t = m.region_factor.at({level, kv.first}) * std::sqrt(T) + kv.second +
+                           rho * std::sqrt((double)m.region_counts.at({level, kv.first}));
+          T += t * t;
+        }
+        N = std::sqrt(T);
+      }
+    }
+    return (N * N) * kMargin;
+  }
+};
+
+struct Step {
+  std::vector<std::pair<int, int>> upd;  // (stream, new planes)
+  uint64_t db;
+  double val;
+};
+
+std::vector<std::tuple<int, double, uint64_t>> useful_steps(const std::vector<double>& vals,
+                                                             const std::vector<uint64_t>& bytes) {
+  std::vector<std::tuple<int, double, uint64_t>> out;
+  const int B = (int)vals.size() - 1;
+  int b = 0;
+  while (true) {
+    int nb = b + 1;
+    while (nb <= B && !(vals[nb] < vals[b])) nb++;
+    if (nb > B) return out;
+    out.push_back({nb, vals[nb], bytes[nb] - bytes[b]});
+    b = nb;
+  }
+}
+
+// greedy order inside one decomposed region (Sec. V-C)
+std::vector<Step> region_sequence(const std::vector<int>& ids, const std::vector<Tab>& tabs) {
+  std::map<int, int> b, pos;
+  std::map<int, std::vector<std::tuple<int, double, uint64_t>>> steps;
+  for (int i : ids) {
+    b[i] = 0;
+    pos[i] = 0;
+    steps[i] = useful_steps(tabs[i].maxerr, tabs[i].bytes);
+  }
+  auto total = [&]() {
+    double t = 0.0;
+    for (int i : ids) t = t + tabs[i].maxerr[b[i]];
+    return t;
+  };
+  std::vector<Step> seq;
+  while (true) {
+    bool have = false;
+    double br = 0;
+    int bi = -1, bnb = 0;
+    uint64_t bdb = 0;
+    for (int i : ids) {
+      if (pos[i] >= (int)steps[i].size()) continue;
+      const auto& stp = steps[i][pos[i]];
+      const double de = tabs[i].maxerr[b[i]] - std::get<1>(stp);
+      const uint64_t db = std::get<2>(stp);
+      const double ratio = db == 0 ? std::numeric_limits<double>::infinity() : de / (double)db;
+      if (!have || ratio > br) {
+        have = true;
+        br = ratio;
+        bi = i;
+        bnb = std::get<0>(stp);
+        bdb = db;
+      }
+    }
+    if (!have) return seq;
+    b[bi] = bnb;
+    pos[bi]++;
+    seq.push_back({{{bi, bnb}}, bdb, total()});
+  }
+}
+
+// Sec. V-C max ordering: (initial level error, segments)
+std::pair<double, std::vector<Step>> max_ordering(const std::map<int, std::vector<int>>& by_region,
+                                                  const std::vector<Tab>& tabs) {
+  struct S {
+    double e;
+    int r, k;
+    Step st;
+  };
+  std::vector<S> all;
+  std::map<int, double> cur;
+  for (auto& kv : by_region) {
+    double t = 0.0;
+    for (int i : kv.second) t = t + tabs[i].maxerr[0];
+    cur[kv.first] = t;
+    auto seq = region_sequence(kv.second, tabs);
+    for (size_t k = 0; k < seq.size(); k++) all.push_back({seq[k].val, kv.first, (int)k, seq[k]});
+  }
+  std::sort(all.begin(), all.end(), [](const S& a, const S& b) {
+    if (a.e != b.e) return a.e > b.e;
+    if (a.r != b.r) return a.r < b.r;
+    return a.k < b.k;
+  });
+  double init = -std::numeric_limits<double>::infinity();
+  for (auto& kv : cur) init = std::max(init, kv.second);
+  std::vector<Step> segs;
+  size_t i = 0;
+  while (i < all.size()) {
+    size_t j = i;
+    Step sg;
+    sg.db = 0;
+    while (j < all.size() && all[j].e == all[i].e) {
+      for (auto& u : all[j].st.upd) sg.upd.push_back(u);
+      sg.db += all[j].st.db;
+      cur[all[j].r] = all[j].e;
+      j++;
+    }
+    double mx = -std::numeric_limits<double>::infinity();
+    for (auto& kv : cur) mx = std::max(mx, kv.second);
+    sg.val = mx;
+    segs.push_back(sg);
+    i = j;
+  }
+  return {init, segs};
+}
+
+std::vector<Step> compress(double init, const std::vector<Step>& segs) {
+  std::vector<Step> out;
+  Step acc;
+  acc.db = 0;
+  double prev = init;
+  for (auto& s : segs) {
+    for (auto& u : s.upd) acc.upd.push_back(u);
+    acc.db += s.db;
+    if (s.val < prev) {
+      acc.val = s.val;
+      out.push_back(acc);
+      acc = Step();
+      acc.db = 0;
+      prev = s.val;
+    }
+  }
+  return out;
+}
+
+struct Unit {
+  std::vector<int> ids;
+  std::vector<Step> steps;
+  double weight;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the handle
+// ---------------------------------------------------------------------------
+struct pcr_handle {
+  int ndim = 3;
+  int64_t dims[3] = {0, 0, 0};
+  int64_t n3[3] = {1, 1, 1};
+  int dtype = PCR_F32;
+  int vk = VK_F32;
+  int w64 = 0;
+  pcr_scheme sch{};
+  std::vector<int> order;
+  int L = 1, B = 32, enc = 1, decomp = -1;
+  double xmin = 0, xmax = 0, M = 0, h = 0, C0 = 0;
+  int G = 0;
+  std::vector<SGeo> geo;
+  std::vector<int> E, sh;
+  std::vector<double> vmax;
+  std::vector<Tab> tabs;
+  std::vector<std::vector<uint32_t>> sign_counts;   // host copy per stream
+  std::vector<std::vector<uint32_t>> plane_nz;
+  std::vector<std::vector<uint64_t>> pairs;
+  std::vector<int64_t> plane_off, sign_off, scnt_off, nz_off;
+  int slot_words = 0;
+  Mem mem;
+  uint32_t* d_planes = nullptr;
+  uint32_t* d_signs = nullptr;
+  uint32_t* d_scnt = nullptr;
+  uint32_t* d_nz = nullptr;
+  Meta meta;
+  Composer comp;
+  bool has_m0 = false;
+  double m0_init = 0;
+  std::vector<Step> m0;
+  size_t plane_words = 0, sign_words = 0, scnt_words = 0, nz_words = 0;
+  ~pcr_handle() {
+    cudaStream_t s = 0;
+    mem.free(d_planes, s);
+    mem.free(d_signs, s);
+    mem.free(d_scnt, s);
+    mem.free(d_nz, s);
+  }
+};
+
+namespace {
+
+LatD to_latd(const Lat& l, int64_t base) {
+  LatD d;
+  for (int a = 0; a < 3; a++) {
+    d.start[a] = l.start[a];
+    d.step[a] = l.step[a];
+    d.count[a] = l.count[a];
+  }
+  d.row_pad = l.row_pad();
+  d.base = base;
+  return d;
+}
+
+FieldD field_desc(const pcr_handle* h) {
+  FieldD f{};
+  for (int a = 0; a < 3; a++) {
+    f.n[a] = h->n3[a];
+    f.nc[a] = h->n3[a] > 1 ? (h->n3[a] - 1) / 2 + 1 : 1;
+  }
+  f.d = (int)h->order.size();
+  for (int i = 0; i < 3; i++) f.order[i] = i < f.d ? h->order[i] : 0;
+  f.interp = h->sch.interp;
+  f.degree = h->sch.degree;
+  f.L = h->L;
+  return f;
+}
+
+StreamD stream_desc(const pcr_handle* h, int i) {
+  StreamD s{};
+  const SGeo& g = h->geo[i];
+  s.nlat = (int)g.lats.size();
+  int64_t base = 0;
+  for (int k = 0; k < s.nlat; k++) {
+    s.lat[k] = to_latd(g.lats[k], base);
+    base += g.lats[k].n_pad();
+  }
+  s.n_pad = g.n_pad();
+  s.words = s.n_pad / 32;
+  s.nseg = (s.n_pad + kSegElems - 1) / kSegElems;
+  s.level = g.level;
+  s.region = g.region;
+  s.sub = g.sub;
+  s.is_fix = g.is_fix;
+  s.B = h->B;
+  s.enc = h->enc;
+  s.vk = g.is_fix ? VK_FIX : h->vk;
+  s.slot_words = h->slot_words;
+  s.planes = h->d_planes + h->plane_off[i];
+  s.signs = h->d_signs + h->sign_off[i];
+  s.sign_counts = h->d_scnt + h->scnt_off[i];
+  s.plane_nz = h->d_nz + h->nz_off[i];
+  s.pairs = nullptr;
+  s.vmax = nullptr;
+  s.stage = nullptr;
+  s.b = 0;
+  s.E = h->E.empty() ? 0 : h->E[i];
+  s.sh = h->sh.empty() ? 0 : h->sh[i];
+  return s;
+}
+
+void compute_tables(pcr_handle* h, int i, const std::vector<uint64_t>* pairs, bool psnr) {
+  const SGeo& g = h->geo[i];
+  const int B = h->B;
+  const int64_t words = g.n_pad() / 32;
+  const bool nb = h->enc == 2;
+  Tab t;
+  t.maxerr.assign(B + 1, 0.0);
+  t.sq.assign(B + 1, 0.0);
+  t.bytes.assign(B + 1, 0);
+  uint64_t acc = 0;
+  const int64_t nseg = (g.n_pad() + kSegElems - 1) / kSegElems;
+  for (int k = 0; k < B; k++) {
+    if (h->plane_nz[i][k]) acc += 4 * (uint64_t)words;
+    if (!nb)
+      for (int64_t sg = 0; sg < nseg; sg++) acc += 4 * (uint64_t)((h->sign_counts[i][sg * B + k] + 31) / 32);
+    t.bytes[k + 1] = acc;
+  }
+  double unit, vmax_abs;
+  const bool zero = h->vmax[i] == 0;
+  if (g.is_fix) {
+    vmax_abs = up_u64((uint64_t)h->vmax[i]) * h->h;
+    unit = std::ldexp(h->h, h->sh[i] + (nb ? 3 : 0));
+  } else {
+    vmax_abs = h->vmax[i];
+    unit = std::ldexp(1.0, h->E[i] - B + (nb ? 3 : 0));
+  }
+  if (!zero) {
+    for (int b = 0; b <= B; b++) {
+      if (b == 0) t.maxerr[b] = vmax_abs;
+      else if (!nb) t.maxerr[b] = std::ldexp(unit, B - b);
+      else {
+        const int k = B - b;
+        const uint64_t dm = (k == 64 ? ~uint64_t(0) : ((uint64_t(1) << (k + 1)) - 1)) / 3;
+        t.maxerr[b] = up_u64(dm + 1) * unit;
+      }
+    }
+    const int64_t n_real = g.n_real();
+    if (psnr && pairs) {
+      const auto& C = *pairs;
+      for (int b = 0; b <= B; b++) {
+        Big pos, neg, s1;
+        for (int j = b; j < B; j++)
+          for (int jj = b; jj < B; jj++) {
+            const uint64_t c = C[std::min(j, jj) * B + std::max(j, jj)];
+            if (!c) continue;
+            const int w = 2 * B - 2 - j - jj;
+            Big term = Big::shl(c, w);
+            if (!nb || ((j + jj) % 2 == 0)) pos.add(term);
+            else neg.add(term);
+          }
+        Big s2 = pos;
+        s2.sub(neg);
+        if (!nb) {
+          for (int j = b; j < B; j++) s1.add(Big::shl(C[j * B + j], B - 1 - j));
+        } else {
+          s1 = s2.mul((uint64_t)n_real).isqrt_ceil();
+        }
+        Big total = s2;
+        Big s1x2 = s1;
+        s1x2.add(s1);
+        total.add(s1x2);
+        total.add(Big::from((uint64_t)n_real));
+        t.sq[b] = total.to_double_up() * unit * unit;
+      }
+    } else {
+      for (int b = 0; b <= B; b++) t.sq[b] = (double)n_real * t.maxerr[b] * t.maxerr[b];
+    }
+  }
+  h->tabs[i] = t;
+}
+
+void build_meta(pcr_handle* h) {
+  Meta& m = h->meta;
+  m.L = h->L;
+  m.d = (int)h->order.size();
+  m.degree = h->sch.degree;
+  m.interp = h->sch.interp;
+  m.dtype = h->dtype;
+  m.decomp = h->decomp;
+  m.h = h->h;
+  m.M = h->M;
+  m.C0 = h->C0;
+  m.R = h->xmax - h->xmin;
+  m.n = h->n3[0] * h->n3[1] * h->n3[2];
+  m.level_counts.clear();
+  m.region_counts.clear();
+  for (int l = 0; l < h->L; l++) m.level_counts[l] = 0;
+  for (auto& g : h->geo) {
+    m.level_counts[g.level] += g.n_real();
+    m.region_counts[{g.level, g.region}] += g.n_real();
+  }
+  for (int level = 0; level < h->L - 1; level++) {
+    const int64_t s = int64_t(1) << level;
+    double prod = 1.0;
+    for (int a : h->order) prod *= 1.0 + rowsum_ptp(count_from(h->n3[a], 0, s), m.degree);
+    m.level_factor[level] = std::sqrt(prod - 1.0);
+    for (int r = 1; r <= m.d; r++)
+      m.region_factor[{level, r}] = std::sqrt(rowsum_ptp(count_from(h->n3[h->order[r - 1]], 0, s), m.degree));
+  }
+  if (h->decomp >= 0) {
+    int u = -1, v = -1;
+    for (int a = 0; a < 3; a++)
+      if (a != h->decomp) (u < 0 ? u : v) = a;
+    for (int r = 1; r <= m.d; r++) {
+      const Lat R = region_lat(h->n3, 0, h->order, r);
+      double p2 = 1.0, p3 = 1.0;
+      for (int ax : {u, v}) {
+        const int64_t c = R.count[ax];
+        p3 *= 1.0 + rowsum_ptp(c, 1);
+        p2 *= 1.0 + rowsum_ptp(count_from(c, 0, 2), 1);
+      }
+      m.decomp_factors[r] = {std::sqrt(p2 - 1.0), std::sqrt(p3 - 1.0)};
+    }
+  }
+  std::vector<SRef> refs;
+  for (auto& g : h->geo) refs.push_back({g.level, g.region, g.sub});
+  h->comp.init(m, refs);
+  h->has_m0 = false;
+  h->m0.clear();
+  if (h->sch.interp == 0 && h->decomp >= 0) {
+    std::map<int, std::vector<int>> by_r;
+    for (int i : h->comp.by_level.at(0)) by_r[h->geo[i].region].push_back(i);
+    auto mo = max_ordering(by_r, h->tabs);
+    h->has_m0 = true;
+    h->m0_init = mo.first;
+    h->m0 = mo.second;
+  }
+}
+
+std::vector<Unit> build_units(const pcr_handle* h, bool linf) {
+  std::vector<Unit> units;
+  const Composer& c = h->comp;
+  for (int level = h->L - 1; level >= 0; level--) {
+    const auto& ids = c.by_level.at(level);
+    const double w = std::ldexp(1.0, c.m.d * level);
+    if (linf && h->sch.interp == 0 && ids.size() > 1) {
+      std::map<int, std::vector<int>> by_r;
+      for (int i : ids) by_r[h->geo[i].region].push_back(i);
+      auto mo = max_ordering(by_r, h->tabs);
+      units.push_back({ids, compress(mo.first, mo.second), w});
+    } else {
+      for (int i : ids) {
+        Unit u;
+        u.ids = {i};
+        u.weight = w;
+        for (auto& st : useful_steps(linf ? h->tabs[i].maxerr : h->tabs[i].sq, h->tabs[i].bytes))
+          u.steps.push_back({{{i, std::get<0>(st)}}, std::get<2>(st), std::get<1>(st)});
+        units.push_back(u);
+      }
+    }
+  }
+  return units;
+}
+
+// greedy interpreter: largest bound decrease per byte until the target holds
+bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, double& bound) {
+  const int n = (int)h->tabs.size();
+  b.assign(n, 0);
+  auto units = build_units(h, linf);
+  std::vector<size_t> pos(units.size(), 0);
+  auto evaluate = [&](const std::vector<int>& bb) {
+    std::vector<double> err(n), sq(n);
+    for (int i = 0; i < n; i++) err[i] = h->tabs[i].maxerr[bb[i]];
+    if (linf) return h->comp.linf(err);
+    for (int i = 0; i < n; i++) sq[i] = h->tabs[i].sq[bb[i]];
+    return h->comp.l2(sq, err);
+  };
+  auto unit_value = [&](const Unit& u, const std::vector<int>& bb) {
+    if (u.ids.size() == 1) return linf ? h->tabs[u.ids[0]].maxerr[bb[u.ids[0]]] : h->tabs[u.ids[0]].sq[bb[u.ids[0]]];
+    std::vector<std::pair<int, double>> reg;
+    for (int i : u.ids) {
+      const int r = h->geo[i].region;
+      bool found = false;
+      for (auto& pr : reg)
+        if (pr.first == r) {
+          pr.second = pr.second + h->tabs[i].maxerr[bb[i]];
+          found = true;
+        }
+      if (!found) reg.push_back({r, 0.0 + h->tabs[i].maxerr[bb[i]]});
+    }
+    double mx = reg[0].second;
+    for (auto& pr : reg) mx = std::max(mx, pr.second);
+    return mx;
+  };
+  bound = evaluate(b);
+  while (bound > target) {
+    bool have_best = false, have_fb = false;
+    double best_r = 0, fb_r = 0, best_bnd = 0, fb_bnd = 0;
+    size_t best_u = 0, fb_u = 0;
+    std::vector<int> best_b, fb_b;
+    for (size_t ui = 0; ui < units.size(); ui++) {
+      const Unit& u = units[ui];
+      if (pos[ui] >= u.steps.size()) continue;
+      const Step& st = u.steps[pos[ui]];
+      std::vector<int> trial = b;
+      for (auto& up : st.upd) trial[up.first] = up.second;
+      const double nb = evaluate(trial);
+      const double gain = bound - nb;
+      const double inf = std::numeric_limits<double>::infinity();
+      const double ratio = st.db == 0 ? inf : gain / (double)st.db;
+      if (gain > 0 || st.db == 0) {
+        if (!have_best || ratio > best_r) {
+          have_best = true;
+          best_r = ratio;
+          best_u = ui;
+          best_b = trial;
+          best_bnd = nb;
+        }
+      }
+      const double own = (unit_value(u, b) - unit_value(u, trial)) * u.weight;
+      const double fr = st.db == 0 ? inf : own / (double)st.db;
+      if (!have_fb || fr > fb_r) {
+        have_fb = true;
+        fb_r = fr;
+        fb_u = ui;
+        fb_b = trial;
+        fb_bnd = nb;
+      }
+    }
+    if (!have_best) {
+      if (!have_fb) return false;
+      best_u = fb_u;
+      best_b = fb_b;
+      best_bnd = fb_bnd;
+    }
+    b = best_b;
+    bound = best_bnd;
+    pos[best_u]++;
+  }
+  return true;
+}
+
+size_t vsize(int vk) { return vk == VK_F32 ? 4 : 8; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// refactor
+// ---------------------------------------------------------------------------
+static pcr_status validate(const void* d_field, int ndim, const int64_t* dims, int dtype, const pcr_scheme* sch) {
+  if (!d_field || !dims || !sch) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  if (ndim != 2 && ndim != 3) return fail(PCR_ERR_INVALID_ARG, "ndim must be 2 or 3");
+  for (int i = 0; i < ndim; i++)
+    if (dims[i] < 2) return fail(PCR_ERR_INVALID_ARG, "every dimension must be >= 2");
+  if (dtype != PCR_F32 && dtype != PCR_F64) return fail(PCR_ERR_INVALID_ARG, "dtype must be PCR_F32 or PCR_F64");
+  if (sch->mode != PCR_MODE_EB && sch->mode != PCR_MODE_PSNR) return fail(PCR_ERR_INVALID_ARG, "bad mode");
+  if (sch->interp != 0 && sch->interp != 1) return fail(PCR_ERR_INVALID_ARG, "bad interp");
+  if (sch->degree != 1 && sch->degree != 3) return fail(PCR_ERR_INVALID_ARG, "degree must be 1 or 3");
+  if (sch->encoding < 0 || sch->encoding > 2) return fail(PCR_ERR_INVALID_ARG, "bad encoding");
+  return PCR_OK;
+}
+
+static pcr_status setup_handle(pcr_handle* h, int ndim, const int64_t* dims, int dtype, const pcr_scheme* sch) {
+  h->ndim = ndim;
+  for (int i = 0; i < 3; i++) h->dims[i] = 0;
+  for (int i = 0; i < ndim; i++) h->dims[i] = dims[i];
+  if (ndim == 2) {
+    h->n3[0] = 1;
+    h->n3[1] = dims[0];
+    h->n3[2] = dims[1];
+  } else {
+    for (int i = 0; i < 3; i++) h->n3[i] = dims[i];
+  }
+  h->dtype = dtype;
+  h->vk = dtype == PCR_F32 ? VK_F32 : VK_F64;
+  h->w64 = dtype == PCR_F64;
+  h->sch = *sch;
+  std::vector<int> act;
+  for (int a = 0; a < 3; a++)
+    if (h->n3[a] > 1) act.push_back(a);
+  const int d = (int)act.size();
+  if (sch->interp == 1) {
+    // user axes: 0..ndim-1; 2-D fields are stored as (1, n0, n1)
+    std::vector<int> ord;
+    for (int i = 0; i < d; i++) ord.push_back(sch->order[i] + (ndim == 2 ? 1 : 0));
+    std::vector<int> s = ord;
+    std::sort(s.begin(), s.end());
+    if (s != act) return fail(PCR_ERR_INVALID_ARG, "order must be a permutation of the active axes");
+    h->order = ord;
+  } else {
+    h->order = act;
+  }
+  const int Bmax = dtype == PCR_F32 ? 32 : 64;
+  h->B = sch->nplanes ? sch->nplanes : Bmax;
+  if (h->B < 1 || h->B > Bmax) return fail(PCR_ERR_INVALID_ARG, "nplanes out of range");
+  h->L = sch->nlevels ? sch->nlevels : auto_levels(h->n3);
+  if (h->L < 1 || h->L > max_levels(h->n3)) return fail(PCR_ERR_INVALID_ARG, "nlevels out of range");
+  h->enc = sch->encoding == PCR_ENC_DEFAULT ? (sch->mode == PCR_MODE_EB ? 1 : 2) : sch->encoding;
+  if (sch->decomp_axis < -1 || sch->decomp_axis > 2) return fail(PCR_ERR_INVALID_ARG, "decomp_axis must be -1..2");
+  h->decomp = (d == 3 && h->L >= 2) ? sch->decomp_axis : -1;
+  h->geo = build_streams(h->n3, h->L, sch->interp, h->order, h->decomp);
+  if ((int)h->geo.size() > PCR_MAX_STREAMS) return fail(PCR_ERR_UNSUPPORTED, "too many streams");
+  for (auto& g : h->geo)
+    if (g.n_pad() >= (int64_t(1) << 31)) return fail(PCR_ERR_UNSUPPORTED, "stream longer than 2^31 elements");
+  h->slot_words = kSegWords + h->B;
+  // offsets of the device tables
+  const int ns = (int)h->geo.size();
+  h->plane_off.resize(ns);
+  h->sign_off.resize(ns);
+  h->scnt_off.resize(ns);
+  h->nz_off.resize(ns);
+  size_t po = 0, so = 0, co = 0, zo = 0;
+  for (int i = 0; i < ns; i++) {
+    const int64_t np = h->geo[i].n_pad();
+    const int64_t nseg = (np + kSegElems - 1) / kSegElems;
+    h->plane_off[i] = po;
+    po += (size_t)h->B * (np / 32);
+    h->sign_off[i] = so;
+    if (h->enc == 1) so += (size_t)nseg * h->slot_words;
+    h->scnt_off[i] = co;
+    co += (size_t)nseg * h->B;
+    h->nz_off[i] = zo;
+    zo += h->B;
+  }
+  h->plane_words = po;
+  h->sign_words = so;
+  h->scnt_words = co;
+  h->nz_words = zo;
+  return PCR_OK;
+}
+
+struct Scratch {
+  Mem* mem;
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  void* get(size_t bytes) {
+    void* p = mem->alloc(bytes, s);
+    if (p) ptrs.push_back(p);
+    return p;
+  }
+  ~Scratch() {
+    for (void* p : ptrs) mem->free(p, s);
+  }
+};
+
+// Enqueue the whole refactor of one handle (geometry already set up) with its
+// device outputs allocated; `st` receives field stats, `vmax` per-stream maxima.
+static pcr_status enqueue_refactor(pcr_handle* h, const void* d_field, cudaStream_t s, Scratch& sc,
+                                   FieldStats* d_st, unsigned long long* d_vmax, unsigned long long* d_pairs,
+                                   std::vector<StreamD>& sds) {
+  const int ns = (int)h->geo.size();
+  const int64_t n = h->n3[0] * h->n3[1] * h->n3[2];
+  const FieldD f = field_desc(h);
+  const size_t w = vsize(h->vk);
+  // staging
+  size_t fix_elems = 0, flt_elems = 0;
+  std::vector<size_t> soff(ns);
+  for (int i = 0; i < ns; i++) {
+    if (h->geo[i].is_fix) {
+      soff[i] = fix_elems;
+      fix_elems += h->geo[i].n_pad();
+    } else {
+      soff[i] = flt_elems;
+      flt_elems += h->geo[i].n_pad();
+    }
+  }
+  int64_t* st_fix = (int64_t*)sc.get(fix_elems * 8);
+  char* st_flt = (char*)sc.get(flt_elems * w);
+  if (!st_fix || !st_flt) return fail(PCR_ERR_OOM, "staging allocation failed");
+  launch_minmax(h->vk, d_field, n, d_st, s);
+  int64_t* xc = nullptr;
+  if (h->L >= 2) {
+    xc = (int64_t*)sc.get((size_t)f.nc[0] * f.nc[1] * f.nc[2] * 8);
+    if (!xc) return fail(PCR_ERR_OOM, "staging allocation failed");
+    launch_to_fixed(h->vk, d_field, f, d_st, xc, s);
+  }
+  // region compact arrays for the decomposition
+  std::vector<void*> comp(4, nullptr);
+  if (h->decomp >= 0)
+    for (int r = 1; r <= f.d; r++) {
+      const Lat R = region_lat(h->n3, 0, h->order, r);
+      comp[r] = sc.get((size_t)R.n_real() * w);
+      if (!comp[r]) return fail(PCR_ERR_OOM, "staging allocation failed");
+    }
+  unsigned long long* c0 = &d_st->c0;
+  for (int i = 0; i < ns; i++) {
+    const SGeo& g = h->geo[i];
+    sds[i] = stream_desc(h, i);
+    sds[i].vmax = d_vmax + i;
+    sds[i].pairs = d_pairs ? d_pairs + (size_t)i * h->B * h->B : nullptr;
+    sds[i].stage = g.is_fix ? (void*)(st_fix + soff[i]) : (void*)(st_flt + soff[i] * w);
+    int64_t base = 0;
+    for (size_t k = 0; k < g.lats.size(); k++) {
+      const LatD ld = to_latd(g.lats[k], base);
+      base += g.lats[k].n_pad();
+      if (g.is_fix) {
+        launch_coef_fixed(f, g.level, g.level == h->L - 1, ld, xc, (int64_t*)sds[i].stage, sds[i].vmax, s);
+      } else if (h->L == 1) {
+        launch_raw_stage(h->vk, f, ld, d_field, sds[i].stage, sds[i].vmax, s);
+      } else if (g.sub == 0) {
+        launch_coef_l0(h->vk, f, ld, 0, d_field, (char*)sds[i].stage, sds[i].vmax, c0, s);
+      }
+    }
+  }
+  if (h->decomp >= 0) {
+    int u = -1, v = -1;
+    for (int a = 0; a < 3; a++)
+      if (a != h->decomp) (u < 0 ? u : v) = a;
+    for (int r = 1; r <= f.d; r++) {
+      const Lat R = region_lat(h->n3, 0, h->order, r);
+      launch_coef_l0(h->vk, f, to_latd(R, 0), 1, d_field, comp[r], nullptr, c0, s);
+    }
+    for (int i = 0; i < ns; i++) {
+      const SGeo& g = h->geo[i];
+      if (g.sub == 0) continue;
+      DecompGeo dg;
+      dg.region = to_latd(region_lat(h->n3, 0, h->order, g.region), 0);
+      dg.u = u;
+      dg.v = v;
+      dg.sub = g.sub;
+      int64_t base = 0;
+      for (auto& l : g.lats) {
+        launch_decompose(h->vk, dg, to_latd(l, base), comp[g.region], sds[i].stage, sds[i].vmax, s);
+        base += l.n_pad();
+      }
+    }
+  }
+  return PCR_OK;
+}
+
+static pcr_status finish_refactor(pcr_handle* h, const FieldStats& st, const std::vector<unsigned long long>& vm,
+                                  const std::vector<uint32_t>& scnt, const std::vector<uint32_t>& nz,
+                                  const std::vector<uint64_t>* pairs) {
+  if (st.bad) return fail(PCR_ERR_INVALID_ARG, "field contains NaN or Inf");
+  auto inv = [](unsigned long long k) {
+    unsigned long long u = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+    double d;
+    std::memcpy(&d, &u, 8);
+    return d;
+  };
+  h->xmin = inv(st.xmin_key);
+  h->xmax = inv(st.xmax_key);
+  h->M = std::max(std::fabs(h->xmin), std::fabs(h->xmax));
+  h->G = st.G;
+  h->h = std::ldexp(1.0, h->G - kFixBits);
+  const int ns = (int)h->geo.size();
+  h->E.assign(ns, 0);
+  h->sh.assign(ns, 0);
+  h->vmax.assign(ns, 0);
+  h->tabs.assign(ns, Tab());
+  h->sign_counts.assign(ns, {});
+  h->plane_nz.assign(ns, {});
+  h->pairs.assign(ns, {});
+  double c0;
+  std::memcpy(&c0, &st.c0, 8);
+  h->C0 = h->L == 1 ? h->M : c0;
+  for (int i = 0; i < ns; i++) {
+    const SGeo& g = h->geo[i];
+    const unsigned long long v = vm[i];
+    if (g.is_fix) {
+      h->vmax[i] = (double)v;
+      h->E[i] = v ? 64 - __builtin_clzll(v) : 0;
+      const int lim = h->enc == 2 ? h->B - 3 : h->B;
+      h->sh[i] = h->E[i] > lim ? h->E[i] - lim : 0;
+    } else {
+      double dv;
+      if (h->vk == VK_F32) {
+        float fv;
+        const uint32_t b32 = (uint32_t)v;
+        std::memcpy(&fv, &b32, 4);
+        dv = fv;
+      } else {
+        std::memcpy(&dv, &v, 8);
+      }
+      h->vmax[i] = dv;
+      int E = 0;
+      if (dv > 0) std::frexp(dv, &E);
+      h->E[i] = E;
+      if (g.level == 0 && h->L >= 2) h->C0 = std::max(h->C0, dv);
+    }
+    const int64_t nseg = (g.n_pad() + kSegElems - 1) / kSegElems;
+    h->sign_counts[i].assign(scnt.begin() + h->scnt_off[i], scnt.begin() + h->scnt_off[i] + nseg * h->B);
+    h->plane_nz[i].assign(nz.begin() + h->nz_off[i], nz.begin() + h->nz_off[i] + h->B);
+    if (pairs) h->pairs[i].assign(pairs->begin() + (size_t)i * h->B * h->B, pairs->begin() + (size_t)(i + 1) * h->B * h->B);
+  }
+  for (int i = 0; i < ns; i++) compute_tables(h, i, pairs ? &h->pairs[i] : nullptr, h->sch.mode == PCR_MODE_PSNR);
+  build_meta(h);
+  return PCR_OK;
+}
+
+static pcr_status alloc_handle_buffers(pcr_handle* h, cudaStream_t s) {
+  h->d_planes = (uint32_t*)h->mem.alloc(h->plane_words * 4, s);
+  h->d_signs = (uint32_t*)h->mem.alloc(std::max<size_t>(h->sign_words, 1) * 4, s);
+  h->d_scnt = (uint32_t*)h->mem.alloc(std::max<size_t>(h->scnt_words, 1) * 4, s);
+  h->d_nz = (uint32_t*)h->mem.alloc(h->nz_words * 4, s);
+  if (!h->d_planes || !h->d_signs || !h->d_scnt || !h->d_nz) return fail(PCR_ERR_OOM, "handle allocation failed");
+  return PCR_OK;
+}
+
+struct BatchDev {
+  FieldStats* st;
+  unsigned long long* vmax;
+  unsigned long long* pairs;
+};
+
+extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, const int* ndims,
+                                         const int64_t* const* dims, const int* dtypes, const pcr_scheme* schemes,
+                                         const pcr_allocator* alloc, void* cuda_stream, pcr_handle** outs) {
+  if (n <= 0 || !d_fields || !ndims || !dims || !dtypes || !schemes || !outs)
+    return fail(PCR_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  std::vector<std::unique_ptr<pcr_handle>> hs(n);
+  Mem mem = make_mem(alloc);
+  for (int k = 0; k < n; k++) {
+    pcr_status e = validate(d_fields[k], ndims[k], dims[k], dtypes[k], &schemes[k]);
+    if (e) return e;
+    hs[k].reset(new pcr_handle());
+    hs[k]->mem = mem;
+    e = setup_handle(hs[k].get(), ndims[k], dims[k], dtypes[k], &schemes[k]);
+    if (e) return e;
+    e = alloc_handle_buffers(hs[k].get(), s);
+    if (e) return e;
+  }
+  Scratch sc{&mem, s, {}};
+  // one block of device statistics for the whole batch
+  std::vector<size_t> vm_off(n), pr_off(n);
+  size_t nv = 0, npairs = 0;
+  for (int k = 0; k < n; k++) {
+    vm_off[k] = nv;
+    nv += hs[k]->geo.size();
+    pr_off[k] = npairs;
+    if (hs[k]->sch.mode == PCR_MODE_PSNR) npairs += hs[k]->geo.size() * hs[k]->B * hs[k]->B;
+  }
+  FieldStats* d_st = (FieldStats*)sc.get(sizeof(FieldStats) * n);
+  unsigned long long* d_vm = (unsigned long long*)sc.get(nv * 8);
+  unsigned long long* d_pairs = npairs ? (unsigned long long*)sc.get(npairs * 8) : nullptr;
+  if (!d_st || !d_vm || (npairs && !d_pairs)) return fail(PCR_ERR_OOM, "statistics allocation failed");
+  std::vector<FieldStats> init(n);
+  for (auto& x : init) {
+    x.xmin_key = ~0ull;
+    x.xmax_key = 0;
+    x.c0 = 0;
+    x.G = 0;
+    x.bad = 0;
+  }
+  CUDA_TRY(cudaMemcpyAsync(d_st, init.data(), sizeof(FieldStats) * n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(d_vm, 0, nv * 8, s));
+  if (npairs) CUDA_TRY(cudaMemsetAsync(d_pairs, 0, npairs * 8, s));
+  for (int k = 0; k < n; k++) CUDA_TRY(cudaMemsetAsync(hs[k]->d_nz, 0, hs[k]->nz_words * 4, s));
+  // coefficient stages per field; encode work lists for the whole batch
+  std::vector<StreamD> all;
+  std::vector<WorkItem> items[2][2];  // [w64][fixed?]
+  int pairs_mode[2][2] = {{-1, -1}, {-1, -1}};
+  for (int k = 0; k < n; k++) {
+    pcr_handle* h = hs[k].get();
+    std::vector<StreamD> sds(h->geo.size());
+    pcr_status e = enqueue_refactor(h, d_fields[k], s, sc, d_st + k, d_vm + vm_off[k],
+                                    h->sch.mode == PCR_MODE_PSNR ? d_pairs + pr_off[k] : nullptr, sds);
+    if (e) return e;
+    for (size_t i = 0; i < sds.size(); i++) {
+      const int idx = (int)all.size();
+      all.push_back(sds[i]);
+      const int fx = sds[i].is_fix;
+      const int pm = h->sch.mode == PCR_MODE_PSNR;
+      if (pairs_mode[h->w64][fx] < 0) pairs_mode[h->w64][fx] = pm;
+      else if (pairs_mode[h->w64][fx] != pm) return fail(PCR_ERR_UNSUPPORTED, "mixed EB/PSNR modes in one batch");
+      for (int64_t g = 0; g < sds[i].nseg; g++) items[h->w64][fx].push_back({idx, (int)g});
+    }
+  }
+  StreamD* d_sd = (StreamD*)sc.get(all.size() * sizeof(StreamD));
+  size_t nit = 0;
+  for (int a = 0; a < 2; a++)
+    for (int b = 0; b < 2; b++) nit += items[a][b].size();
+  WorkItem* d_items = (WorkItem*)sc.get(std::max<size_t>(nit, 1) * sizeof(WorkItem));
+  if (!d_sd || !d_items) return fail(PCR_ERR_OOM, "work list allocation failed");
+  CUDA_TRY(cudaMemcpyAsync(d_sd, all.data(), all.size() * sizeof(StreamD), cudaMemcpyHostToDevice, s));
+  size_t off = 0;
+  for (int a = 0; a < 2; a++)
+    for (int b = 0; b < 2; b++) {
+      if (items[a][b].empty()) continue;
+      CUDA_TRY(cudaMemcpyAsync(d_items + off, items[a][b].data(), items[a][b].size() * sizeof(WorkItem),
+                               cudaMemcpyHostToDevice, s));
+      const int vk = b ? VK_FIX : (a ? VK_F64 : VK_F32);
+      launch_encode(vk, a, pairs_mode[a][b] > 0, d_sd, d_items + off, (int)items[a][b].size(), s);
+      off += items[a][b].size();
+    }
+  CUDA_TRY(cudaGetLastError());
+  // read back the tables (one synchronisation)
+  std::vector<FieldStats> st(n);
+  std::vector<unsigned long long> vm(nv);
+  std::vector<uint64_t> pairs(npairs);
+  CUDA_TRY(cudaMemcpyAsync(st.data(), d_st, sizeof(FieldStats) * n, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(vm.data(), d_vm, nv * 8, cudaMemcpyDeviceToHost, s));
+  if (npairs) CUDA_TRY(cudaMemcpyAsync(pairs.data(), d_pairs, npairs * 8, cudaMemcpyDeviceToHost, s));
+  std::vector<std::vector<uint32_t>> scnt(n), nz(n);
+  for (int k = 0; k < n; k++) {
+    scnt[k].resize(hs[k]->scnt_words);
+    nz[k].resize(hs[k]->nz_words);
+    if (hs[k]->scnt_words)
+      CUDA_TRY(cudaMemcpyAsync(scnt[k].data(), hs[k]->d_scnt, hs[k]->scnt_words * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(nz[k].data(), hs[k]->d_nz, hs[k]->nz_words * 4, cudaMemcpyDeviceToHost, s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (int k = 0; k < n; k++) {
+    pcr_handle* h = hs[k].get();
+    std::vector<unsigned long long> v(vm.begin() + vm_off[k], vm.begin() + vm_off[k] + h->geo.size());
+    std::vector<uint64_t> pk;
+    if (h->sch.mode == PCR_MODE_PSNR)
+      pk.assign(pairs.begin() + pr_off[k], pairs.begin() + pr_off[k] + h->geo.size() * h->B * h->B);
+    pcr_status e = finish_refactor(h, st[k], v, scnt[k], nz[k], h->sch.mode == PCR_MODE_PSNR ? &pk : nullptr);
+    if (e) return e;
+  }
+  for (int k = 0; k < n; k++) outs[k] = hs[k].release();
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_refactor(const void* d_field, int ndim, const int64_t* dims, int dtype,
+                                   const pcr_scheme* scheme, const pcr_allocator* alloc, void* cuda_stream,
+                                   pcr_handle** out) {
+  if (!out) return fail(PCR_ERR_INVALID_ARG, "null output");
+  const void* f[1] = {d_field};
+  const int nd[1] = {ndim};
+  const int64_t* dm[1] = {dims};
+  const int dt[1] = {dtype};
+  return pcr_refactor_batch(1, f, nd, dm, dt, scheme, alloc, cuda_stream, out);
+}
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+extern "C" pcr_status pcr_plan(const pcr_handle* h, const pcr_target* t, pcr_retrieval_plan* out) {
+  if (!h || !t || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  if (!(t->value >= 0) || !std::isfinite(t->value)) return fail(PCR_ERR_INVALID_ARG, "bad target value");
+  std::vector<int> b;
+  double bound = 0;
+  bool ok;
+  const double R = h->xmax - h->xmin;
+  std::memset(out, 0, sizeof(*out));
+  if (t->kind == PCR_TARGET_ABS || t->kind == PCR_TARGET_REL) {
+    const double tau = t->value * (t->kind == PCR_TARGET_REL ? R : 1.0);
+    ok = greedy(h, tau, true, b, bound);
+    out->psnr_bound = 0;
+  } else if (t->kind == PCR_TARGET_PSNR) {
+    const double ratio = R / std::pow(10.0, t->value / 20.0);
+    const double sse_max = (double)h->meta.n * ratio * ratio;
+    ok = greedy(h, sse_max, false, b, bound);
+    const double rmse = std::sqrt(bound / (double)h->meta.n);
+    out->psnr_bound = rmse > 0 ? 20.0 * std::log10(R / rmse) : std::numeric_limits<double>::infinity();
+  } else {
+    return fail(PCR_ERR_INVALID_ARG, "bad target kind");
+  }
+  out->nstreams = (int)b.size();
+  uint64_t bytes = 0;
+  for (size_t i = 0; i < b.size(); i++) {
+    out->planes[i] = b[i];
+    bytes += h->tabs[i].bytes[b[i]];
+  }
+  out->bytes = bytes;
+  out->bound = bound;
+  out->satisfied = ok ? 1 : 0;
+  if (!ok) return fail(PCR_ERR_UNSATISFIABLE, "target tighter than the all-planes bound");
+  return PCR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// retrieve
+// ---------------------------------------------------------------------------
+static pcr_status enqueue_retrieve_one(const pcr_handle* h, const pcr_retrieval_plan* p, void* d_out, cudaStream_t s,
+                                       Scratch& sc, std::vector<StreamD>& sds, std::vector<int>& stage_kind) {
+  const int ns = (int)h->geo.size();
+  if (!p || p->nstreams != ns) return fail(PCR_ERR_INVALID_ARG, "plan does not match the handle");
+  for (int i = 0; i < ns; i++)
+    if (p->planes[i] < 0 || p->planes[i] > h->B) return fail(PCR_ERR_INVALID_ARG, "plan plane count out of range");
+  const size_t w = vsize(h->vk);
+  size_t fix_elems = 0, flt_elems = 0;
+  std::vector<size_t> soff(ns);
+  for (int i = 0; i < ns; i++) {
+    if (h->geo[i].is_fix) {
+      soff[i] = fix_elems;
+      fix_elems += h->geo[i].n_pad();
+    } else {
+      soff[i] = flt_elems;
+      flt_elems += h->geo[i].n_pad();
+    }
+  }
+  int64_t* st_fix = (int64_t*)sc.get(fix_elems * 8);
+  char* st_flt = (char*)sc.get(flt_elems * w);
+  if (!st_fix || !st_flt) return fail(PCR_ERR_OOM, "staging allocation failed");
+  sds.resize(ns);
+  stage_kind.resize(ns);
+  for (int i = 0; i < ns; i++) {
+    sds[i] = stream_desc(h, i);
+    sds[i].b = p->planes[i];
+    sds[i].stage = h->geo[i].is_fix ? (void*)(st_fix + soff[i]) : (void*)(st_flt + soff[i] * w);
+    stage_kind[i] = h->geo[i].is_fix ? VK_FIX : h->vk;
+  }
+  return PCR_OK;
+}
+
+static pcr_status enqueue_reconstruct(const pcr_handle* h, const std::vector<StreamD>& sds, void* d_out,
+                                      cudaStream_t s, Scratch& sc) {
+  const FieldD f = field_desc(h);
+  const size_t w = vsize(h->vk);
+  const int ns = (int)h->geo.size();
+  if (h->L == 1) {
+    launch_copy_raw(h->vk, f, to_latd(h->geo[0].lats[0], 0), sds[0].stage, d_out, s);
+    return PCR_OK;
+  }
+  // level-0 recomposition (Alg. 2)
+  std::vector<void*> comp(4, nullptr);
+  if (h->decomp >= 0) {
+    int u = -1, v = -1;
+    for (int a = 0; a < 3; a++)
+      if (a != h->decomp) (u < 0 ? u : v) = a;
+    for (int r = 1; r <= f.d; r++) {
+      const Lat R = region_lat(h->n3, 0, h->order, r);
+      comp[r] = sc.get((size_t)R.n_real() * w);
+      if (!comp[r]) return fail(PCR_ERR_OOM, "staging allocation failed");
+    }
+    for (int i = 0; i < ns; i++) {  // stream order: S1, S2, S3 of each region
+      const SGeo& g = h->geo[i];
+      if (g.sub == 0) continue;
+      DecompGeo dg;
+      dg.region = to_latd(region_lat(h->n3, 0, h->order, g.region), 0);
+      dg.u = u;
+      dg.v = v;
+      dg.sub = g.sub;
+      int64_t base = 0;
+      for (auto& l : g.lats) {
+        launch_recompose(h->vk, dg, to_latd(l, base), sds[i].stage, comp[g.region], s);
+        base += l.n_pad();
+      }
+    }
+  }
+  // coarse levels in fixed point
+  int64_t* xc = (int64_t*)sc.get((size_t)f.nc[0] * f.nc[1] * f.nc[2] * 8);
+  if (!xc) return fail(PCR_ERR_OOM, "staging allocation failed");
+  for (int i = 0; i < ns; i++) {
+    const SGeo& g = h->geo[i];
+    if (!g.is_fix) continue;
+    int64_t base = 0;
+    for (auto& l : g.lats) {
+      launch_recon_fixed(f, g.level, g.level == h->L - 1, to_latd(l, base), (const int64_t*)sds[i].stage, xc, s);
+      base += l.n_pad();
+    }
+  }
+  launch_coarse_out(h->vk, f, xc, std::ldexp(1.0, h->G - kFixBits), d_out, s);
+  // level 0
+  if (h->decomp >= 0) {
+    for (int r = 1; r <= f.d; r++) {
+      const Lat R = region_lat(h->n3, 0, h->order, r);
+      launch_recon_l0(h->vk, f, to_latd(R, 0), 1, comp[r], d_out, s);
+    }
+  } else {
+    for (int i = 0; i < ns; i++) {
+      const SGeo& g = h->geo[i];
+      if (g.level != 0) continue;
+      int64_t base = 0;
+      for (auto& l : g.lats) {
+        launch_recon_l0(h->vk, f, to_latd(l, base), 0, sds[i].stage, d_out, s);
+        base += l.n_pad();
+      }
+    }
+  }
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
+                                         void* const* d_outs, void* cuda_stream) {
+  if (n <= 0 || !hs || !plans || !d_outs) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  for (int k = 0; k < n; k++)
+    if (!hs[k] || !d_outs[k]) return fail(PCR_ERR_INVALID_ARG, "null handle or output");
+  Mem mem = hs[0]->mem;
+  Scratch sc{&mem, s, {}};
+  std::vector<std::vector<StreamD>> sds(n);
+  std::vector<StreamD> all;
+  std::vector<WorkItem> items[2][2];
+  for (int k = 0; k < n; k++) {
+    std::vector<int> kinds;
+    pcr_status e = enqueue_retrieve_one(hs[k], &plans[k], d_outs[k], s, sc, sds[k], kinds);
+    if (e) return e;
+    for (size_t i = 0; i < sds[k].size(); i++) {
+      const int idx = (int)all.size();
+      all.push_back(sds[k][i]);
+      const int fx = sds[k][i].is_fix;
+      for (int64_t g = 0; g < sds[k][i].nseg; g++) items[hs[k]->w64][fx].push_back({idx, (int)g});
+    }
+  }
+  StreamD* d_sd = (StreamD*)sc.get(all.size() * sizeof(StreamD));
+  size_t nit = 0;
+  for (int a = 0; a < 2; a++)
+    for (int b = 0; b < 2; b++) nit += items[a][b].size();
+  WorkItem* d_items = (WorkItem*)sc.get(std::max<size_t>(nit, 1) * sizeof(WorkItem));
+  if (!d_sd || !d_items) return fail(PCR_ERR_OOM, "work list allocation failed");
+  CUDA_TRY(cudaMemcpyAsync(d_sd, all.data(), all.size() * sizeof(StreamD), cudaMemcpyHostToDevice, s));
+  size_t off = 0;
+  for (int a = 0; a < 2; a++)
+    for (int b = 0; b < 2; b++) {
+      if (items[a][b].empty()) continue;
+      CUDA_TRY(cudaMemcpyAsync(d_items + off, items[a][b].data(), items[a][b].size() * sizeof(WorkItem),
+                               cudaMemcpyHostToDevice, s));
+      const int vk = b ? VK_FIX : (a ? VK_F64 : VK_F32);
+      launch_decode(vk, a, d_sd, d_items + off, (int)items[a][b].size(), s);
+      off += items[a][b].size();
+    }
+  for (int k = 0; k < n; k++) {
+    pcr_status e = enqueue_reconstruct(hs[k], sds[k], d_outs[k], s, sc);
+    if (e) return e;
+  }
+  CUDA_TRY(cudaGetLastError());
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_retrieve(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out, void* cuda_stream) {
+  if (!h || !plan || !d_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  return pcr_retrieve_batch(1, &h, plan, &d_out, cuda_stream);
+}
+
+// ---------------------------------------------------------------------------
+// introspection
+// ---------------------------------------------------------------------------
+extern "C" pcr_status pcr_num_streams(const pcr_handle* h, int* n) {
+  if (!h || !n) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  *n = (int)h->geo.size();
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_stream_info_get(const pcr_handle* h, int i, pcr_stream_info* o) {
+  if (!h || !o || i < 0 || i >= (int)h->geo.size()) return fail(PCR_ERR_INVALID_ARG, "bad stream index");
+  const SGeo& g = h->geo[i];
+  o->level = g.level;
+  o->region = g.region;
+  o->sub = g.sub;
+  o->is_fixed = g.is_fix;
+  o->nplanes = h->B;
+  o->n_real = g.n_real();
+  o->n_pad = g.n_pad();
+  o->words = g.n_pad() / 32;
+  o->nseg = (g.n_pad() + kSegElems - 1) / kSegElems;
+  o->exponent = h->E[i];
+  o->shift = h->sh[i];
+  o->vmax = h->vmax[i];
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_stream_tables(const pcr_handle* h, int i, double* maxerr, double* sq, uint64_t* bytes) {
+  if (!h || i < 0 || i >= (int)h->geo.size()) return fail(PCR_ERR_INVALID_ARG, "bad stream index");
+  const Tab& t = h->tabs[i];
+  for (int b = 0; b <= h->B; b++) {
+    if (maxerr) maxerr[b] = t.maxerr[b];
+    if (sq) sq[b] = t.sq[b];
+    if (bytes) bytes[b] = t.bytes[b];
+  }
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_field_stats(const pcr_handle* h, double* xmin, double* xmax, int* G) {
+  if (!h) return fail(PCR_ERR_INVALID_ARG, "null handle");
+  if (xmin) *xmin = h->xmin;
+  if (xmax) *xmax = h->xmax;
+  if (G) *G = h->G;
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_stream_copy(const pcr_handle* h, int i, uint32_t* planes_host, uint32_t* signs_host,
+                                      uint32_t* sign_counts_host, uint64_t* pairs_host) {
+  if (!h || i < 0 || i >= (int)h->geo.size()) return fail(PCR_ERR_INVALID_ARG, "bad stream index");
+  const int64_t words = h->geo[i].n_pad() / 32;
+  const int64_t nseg = (h->geo[i].n_pad() + kSegElems - 1) / kSegElems;
+  if (planes_host) CUDA_TRY(cudaMemcpy(planes_host, h->d_planes + h->plane_off[i], (size_t)h->B * words * 4, cudaMemcpyDeviceToHost));
+  if (signs_host && h->enc == 1)
+    CUDA_TRY(cudaMemcpy(signs_host, h->d_signs + h->sign_off[i], (size_t)nseg * h->slot_words * 4, cudaMemcpyDeviceToHost));
+  if (sign_counts_host) std::memcpy(sign_counts_host, h->sign_counts[i].data(), h->sign_counts[i].size() * 4);
+  if (pairs_host && !h->pairs[i].empty()) std::memcpy(pairs_host, h->pairs[i].data(), h->pairs[i].size() * 8);
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_max_ordering(const pcr_handle* h, double* errs, int* n) {
+  if (!h || !n) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  if (!h->has_m0) {
+    *n = 0;
+    return PCR_OK;
+  }
+  *n = (int)h->m0.size() + 1;
+  if (errs) {
+    errs[0] = h->m0_init;
+    for (size_t k = 0; k < h->m0.size(); k++) errs[k + 1] = h->m0[k].val;
+  }
+  return PCR_OK;
+}
+
+extern "C" void pcr_free(pcr_handle* h) { delete h; }
+extern "C" void pcr_buffer_free(void* p) { std::free(p); }
+
+// ---------------------------------------------------------------------------
+// container: magic, version, header, tables, directory, payload; CRC32 of
+// each section (Sec. III-A: the refactored segments are the stored artifact)
+// ---------------------------------------------------------------------------
+namespace {
+uint32_t crc32(const void* data, size_t n, uint32_t c = 0) {
+  static uint32_t table[256];
+  static bool init = false;
+  if (!init) {
+    for (uint32_t i = 0; i < 256; i++) {
+      uint32_t r = i;
+      for (int k = 0; k < 8; k++) r = (r >> 1) ^ (0xEDB88320u & (0u - (r & 1u)));
+      table[i] = r;
+    }
+    init = true;
+  }
+  c = ~c;
+  const uint8_t* p = (const uint8_t*)data;
+  for (size_t i = 0; i < n; i++) c = table[(c ^ p[i]) & 0xFF] ^ (c >> 8);
+  return ~c;
+}
+
+struct Writer {
+  std::vector<uint8_t> buf;
+  template <class T> void put(const T& v) {
+    const uint8_t* p = (const uint8_t*)&v;
+    buf.insert(buf.end(), p, p + sizeof(T));
+  }
+  void raw(const void* p, size_t n) { buf.insert(buf.end(), (const uint8_t*)p, (const uint8_t*)p + n); }
+};
+
+struct Reader {
+  const uint8_t* p;
+  size_t n, o = 0;
+  bool ok = true;
+  template <class T> T get() {
+    T v{};
+    if (o + sizeof(T) > n) {
+      ok = false;
+      return v;
+    }
+    std::memcpy(&v, p + o, sizeof(T));
+    o += sizeof(T);
+    return v;
+  }
+  const uint8_t* take(size_t k) {
+    if (o + k > n) {
+      ok = false;
+      return nullptr;
+    }
+    const uint8_t* q = p + o;
+    o += k;
+    return q;
+  }
+};
+const uint64_t kMagic = 0x3130524350ull;  // "PCR01"
+}  // namespace
+
+extern "C" pcr_status pcr_serialize(const pcr_handle* h, void** buf, size_t* len) {
+  if (!h || !buf || !len) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  Writer w;
+  w.put(kMagic);
+  // header section
+  Writer hd;
+  hd.put(h->ndim);
+  for (int i = 0; i < 3; i++) hd.put(h->dims[i]);
+  hd.put(h->dtype);
+  hd.put(h->sch);
+  hd.put(h->xmin);
+  hd.put(h->xmax);
+  hd.put(h->G);
+  hd.put(h->C0);
+  const int ns = (int)h->geo.size();
+  for (int i = 0; i < ns; i++) {
+    hd.put(h->vmax[i]);
+    hd.put(h->E[i]);
+    hd.put(h->sh[i]);
+    hd.raw(h->plane_nz[i].data(), h->plane_nz[i].size() * 4);
+    hd.raw(h->sign_counts[i].data(), h->sign_counts[i].size() * 4);
+    const uint64_t np = h->pairs[i].size();
+    hd.put(np);
+    hd.raw(h->pairs[i].data(), np * 8);
+  }
+  w.put((uint64_t)hd.buf.size());
+  w.put(crc32(hd.buf.data(), hd.buf.size()));
+  w.raw(hd.buf.data(), hd.buf.size());
+  // payload: planes then signs
+  std::vector<uint32_t> planes(h->plane_words), signs(h->sign_words);
+  CUDA_TRY(cudaMemcpy(planes.data(), h->d_planes, h->plane_words * 4, cudaMemcpyDeviceToHost));
+  if (h->sign_words) CUDA_TRY(cudaMemcpy(signs.data(), h->d_signs, h->sign_words * 4, cudaMemcpyDeviceToHost));
+  w.put((uint64_t)planes.size());
+  w.put(crc32(planes.data(), planes.size() * 4));
+  w.raw(planes.data(), planes.size() * 4);
+  w.put((uint64_t)signs.size());
+  w.put(crc32(signs.data(), signs.size() * 4));
+  w.raw(signs.data(), signs.size() * 4);
+  void* out = std::malloc(w.buf.size());
+  if (!out) return fail(PCR_ERR_OOM, "host allocation failed");
+  std::memcpy(out, w.buf.data(), w.buf.size());
+  *buf = out;
+  *len = w.buf.size();
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_allocator* alloc, void* cuda_stream,
+                                      pcr_handle** out) {
+  if (!buf || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Reader r{(const uint8_t*)buf, len};
+  if (r.get<uint64_t>() != kMagic || !r.ok) return fail(PCR_ERR_CORRUPT, "bad magic");
+  const uint64_t hl = r.get<uint64_t>();
+  const uint32_t hc = r.get<uint32_t>();
+  const uint8_t* hp = r.take(hl);
+  if (!r.ok || crc32(hp, hl) != hc) return fail(PCR_ERR_CORRUPT, "header checksum or length mismatch");
+  Reader hr{hp, hl};
+  std::unique_ptr<pcr_handle> h(new pcr_handle());
+  h->mem = make_mem(alloc);
+  const int ndim = hr.get<int>();
+  int64_t dims[3];
+  for (int i = 0; i < 3; i++) dims[i] = hr.get<int64_t>();
+  const int dtype = hr.get<int>();
+  const pcr_scheme sch = hr.get<pcr_scheme>();
+  if (!hr.ok) return fail(PCR_ERR_CORRUPT, "truncated header");
+  pcr_status e = validate((const void*)1, ndim, dims, dtype, &sch);
+  if (e) return fail(PCR_ERR_CORRUPT, std::string("invalid header: ") + g_err);
+  e = setup_handle(h.get(), ndim, dims, dtype, &sch);
+  if (e) return fail(PCR_ERR_CORRUPT, std::string("invalid header: ") + g_err);
+  h->xmin = hr.get<double>();
+  h->xmax = hr.get<double>();
+  h->G = hr.get<int>();
+  h->C0 = hr.get<double>();
+  h->M = std::max(std::fabs(h->xmin), std::fabs(h->xmax));
+  h->h = std::ldexp(1.0, h->G - kFixBits);
+  const int ns = (int)h->geo.size();
+  h->vmax.resize(ns);
+  h->E.resize(ns);
+  h->sh.resize(ns);
+  h->plane_nz.resize(ns);
+  h->sign_counts.resize(ns);
+  h->pairs.resize(ns);
+  h->tabs.resize(ns);
+  for (int i = 0; i < ns; i++) {
+    h->vmax[i] = hr.get<double>();
+    h->E[i] = hr.get<int>();
+    h->sh[i] = hr.get<int>();
+    h->plane_nz[i].resize(h->B);
+    for (int k = 0; k < h->B; k++) h->plane_nz[i][k] = hr.get<uint32_t>();
+    const int64_t nseg = (h->geo[i].n_pad() + kSegElems - 1) / kSegElems;
+    h->sign_counts[i].resize(nseg * h->B);
+    for (auto& x : h->sign_counts[i]) x = hr.get<uint32_t>();
+    const uint64_t np = hr.get<uint64_t>();
+    if (!hr.ok || (np != 0 && np != (uint64_t)h->B * h->B)) return fail(PCR_ERR_CORRUPT, "bad table section");
+    h->pairs[i].resize(np);
+    for (auto& x : h->pairs[i]) x = hr.get<uint64_t>();
+  }
+  if (!hr.ok || hr.o != hl) return fail(PCR_ERR_CORRUPT, "header length mismatch");
+  const uint64_t npw = r.get<uint64_t>();
+  const uint32_t pc = r.get<uint32_t>();
+  const uint8_t* pp = r.take(npw * 4);
+  if (!r.ok || npw != h->plane_words || crc32(pp, npw * 4) != pc) return fail(PCR_ERR_CORRUPT, "plane section mismatch");
+  const uint64_t nsw = r.get<uint64_t>();
+  const uint32_t sgc = r.get<uint32_t>();
+  const uint8_t* sp = r.take(nsw * 4);
+  if (!r.ok || nsw != h->sign_words || crc32(sp, nsw * 4) != sgc) return fail(PCR_ERR_CORRUPT, "sign section mismatch");
+  if (r.o != len) return fail(PCR_ERR_CORRUPT, "trailing bytes");
+  e = alloc_handle_buffers(h.get(), s);
+  if (e) return e;
+  CUDA_TRY(cudaMemcpyAsync(h->d_planes, pp, npw * 4, cudaMemcpyHostToDevice, s));
+  if (nsw) CUDA_TRY(cudaMemcpyAsync(h->d_signs, sp, nsw * 4, cudaMemcpyHostToDevice, s));
+  std::vector<uint32_t> scnt, nz;
+  for (int i = 0; i < ns; i++) {
+    scnt.insert(scnt.end(), h->sign_counts[i].begin(), h->sign_counts[i].end());
+    nz.insert(nz.end(), h->plane_nz[i].begin(), h->plane_nz[i].end());
+  }
+  if (!scnt.empty()) CUDA_TRY(cudaMemcpyAsync(h->d_scnt, scnt.data(), scnt.size() * 4, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(h->d_nz, nz.data(), nz.size() * 4, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (int i = 0; i < ns; i++)
+    compute_tables(h.get(), i, h->pairs[i].empty() ? nullptr : &h->pairs[i], h->sch.mode == PCR_MODE_PSNR);
+  build_meta(h.get());
+  *out = h.release();
+  return PCR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// test entry: encode given values
+// ---------------------------------------------------------------------------
+extern "C" pcr_status pcr_debug_encode(const void* d_vals, int64_t n_pad, int value_kind, int B, int encoding,
+                                       int want_pairs, void* cuda_stream, uint32_t* planes_host,
+                                       uint32_t* signs_host, uint32_t* sign_counts_host, uint32_t* plane_nz_host,
+                                       uint64_t* pairs_host, double* vmax_host) {
+  if (!d_vals || n_pad <= 0 || n_pad % 32) return fail(PCR_ERR_INVALID_ARG, "n_pad must be a positive multiple of 32");
+  if (value_kind < 0 || value_kind > 2 || encoding < 1 || encoding > 2) return fail(PCR_ERR_INVALID_ARG, "bad kind");
+  const int w64 = value_kind == VK_F64 ? 1 : (value_kind == VK_FIX && B > 32 ? 1 : 0);
+  if (B < 1 || B > (w64 ? 64 : 32)) return fail(PCR_ERR_INVALID_ARG, "bad B");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Mem mem = make_mem(nullptr);
+  Scratch sc{&mem, s, {}};
+  const int64_t words = n_pad / 32, nseg = (n_pad + kSegElems - 1) / kSegElems;
+  const int slot = kSegWords + B;
+  uint32_t* d_planes = (uint32_t*)sc.get(words * B * 4);
+  uint32_t* d_signs = (uint32_t*)sc.get(nseg * slot * 4);
+  uint32_t* d_scnt = (uint32_t*)sc.get(nseg * B * 4);
+  uint32_t* d_nz = (uint32_t*)sc.get(B * 4);
+  unsigned long long* d_pairs = (unsigned long long*)sc.get((size_t)B * B * 8);
+  unsigned long long* d_vmax = (unsigned long long*)sc.get(8);
+  StreamD* d_sd = (StreamD*)sc.get(sizeof(StreamD));
+  WorkItem* d_it = (WorkItem*)sc.get(nseg * sizeof(WorkItem));
+  if (!d_planes || !d_signs || !d_scnt || !d_nz || !d_pairs || !d_vmax || !d_sd || !d_it)
+    return fail(PCR_ERR_OOM, "allocation failed");
+  CUDA_TRY(cudaMemsetAsync(d_nz, 0, B * 4, s));
+  CUDA_TRY(cudaMemsetAsync(d_pairs, 0, (size_t)B * B * 8, s));
+  CUDA_TRY(cudaMemsetAsync(d_signs, 0, nseg * slot * 4, s));
+  // maximum |value| on the host side of the test entry: read back values
+  std::vector<uint8_t> hv(n_pad * (value_kind == VK_F32 ? 4 : 8));
+  CUDA_TRY(cudaMemcpyAsync(hv.data(), d_vals, hv.size(), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  unsigned long long vm = 0;
+  double vmd = 0;
+  for (int64_t i = 0; i < n_pad; i++) {
+    if (value_kind == VK_F32) {
+      float f;
+      std::memcpy(&f, &hv[i * 4], 4);
+      f = std::fabs(f);
+      uint32_t b;
+      std::memcpy(&b, &f, 4);
+      vm = std::max<unsigned long long>(vm, b);
+      vmd = std::max(vmd, (double)f);
+    } else if (value_kind == VK_F64) {
+      double f;
+      std::memcpy(&f, &hv[i * 8], 8);
+      f = std::fabs(f);
+      unsigned long long b;
+      std::memcpy(&b, &f, 8);
+      vm = std::max(vm, b);
+      vmd = std::max(vmd, f);
+    } else {
+      int64_t v;
+      std::memcpy(&v, &hv[i * 8], 8);
+      const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
+      vm = std::max(vm, a);
+      vmd = std::max(vmd, (double)a);
+    }
+  }
+  CUDA_TRY(cudaMemcpyAsync(d_vmax, &vm, 8, cudaMemcpyHostToDevice, s));
+  StreamD sd{};
+  sd.nlat = 0;
+  sd.n_pad = n_pad;
+  sd.words = words;
+  sd.nseg = nseg;
+  sd.B = B;
+  sd.enc = encoding;
+  sd.vk = value_kind;
+  sd.is_fix = value_kind == VK_FIX;
+  sd.slot_words = slot;
+  sd.planes = d_planes;
+  sd.signs = d_signs;
+  sd.sign_counts = d_scnt;
+  sd.plane_nz = d_nz;
+  sd.pairs = want_pairs ? d_pairs : nullptr;
+  sd.vmax = d_vmax;
+  sd.stage = (void*)d_vals;
+  std::vector<WorkItem> it(nseg);
+  for (int64_t g = 0; g < nseg; g++) it[g] = {0, (int)g};
+  CUDA_TRY(cudaMemcpyAsync(d_sd, &sd, sizeof(sd), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(d_it, it.data(), nseg * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+  launch_encode(value_kind, w64, want_pairs, d_sd, d_it, (int)nseg, s);
+  CUDA_TRY(cudaGetLastError());
+  if (planes_host) CUDA_TRY(cudaMemcpyAsync(planes_host, d_planes, words * B * 4, cudaMemcpyDeviceToHost, s));
+  if (signs_host) CUDA_TRY(cudaMemcpyAsync(signs_host, d_signs, nseg * slot * 4, cudaMemcpyDeviceToHost, s));
+  if (sign_counts_host) CUDA_TRY(cudaMemcpyAsync(sign_counts_host, d_scnt, nseg * B * 4, cudaMemcpyDeviceToHost, s));
+  if (plane_nz_host) CUDA_TRY(cudaMemcpyAsync(plane_nz_host, d_nz, B * 4, cudaMemcpyDeviceToHost, s));
+  if (pairs_host) CUDA_TRY(cudaMemcpyAsync(pairs_host, d_pairs, (size_t)B * B * 8, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (vmax_host) *vmax_host = vmd;
+  return PCR_OK;
+}

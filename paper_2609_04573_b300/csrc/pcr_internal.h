@@ -1,0 +1,78 @@
+// Internal types shared by the CUDA kernels (pcr_kernels.cu) and the host
+// library (pcr_host.cpp).  Not part of the ABI.
+#pragma once
+#include <cstdint>
+
+namespace pcr {
+
+constexpr int kWord = 32;          // elements per plane word
+constexpr int kSegElems = 4096;    // elements per sign segment / encode CTA
+constexpr int kSegWords = kSegElems / kWord;
+constexpr int kFixBits = 40;       // fixed point: x_int = floor(x 2^(40-G))
+constexpr int kMaxLat = 3;
+
+enum ValueKind { VK_F32 = 0, VK_F64 = 1, VK_FIX = 2 };
+
+// One lattice of a stream: field coordinates start + step * k, k < count,
+// row-major with every row (fixed k0, k1) padded to row_pad elements.
+struct LatD {
+  int64_t start[3], step[3], count[3];
+  int64_t row_pad;
+  int64_t base;        // padded element offset of this lattice in its stream
+};
+
+// Field description for the coefficient kernels.
+struct FieldD {
+  int64_t n[3];        // 3-D shape (2-D fields: n[0] = 1)
+  int64_t nc[3];       // shape of the 2-grid (fixed-point copy of the coarse points)
+  int order[3];        // pass order over active axes (d entries)
+  int d;               // number of active axes
+  int interp;          // 0 per-level, 1 per-region
+  int degree;          // 1 linear, 3 cubic
+  int L;
+};
+
+// Per-stream device descriptor; holds raw device pointers so kernels can run
+// over work lists that mix streams of different handles (batched forms).
+struct StreamD {
+  int nlat;
+  LatD lat[kMaxLat];
+  int64_t n_pad, words, nseg;
+  int level, region, sub, is_fix;
+  int B, enc;          // planes; 1 generic, 2 negabinary
+  int vk;              // value kind of the staged values (ValueKind)
+  int slot_words;      // sign slot capacity (u32) per segment
+  uint32_t* planes;    // [B][words]
+  uint32_t* signs;     // [nseg][slot_words]
+  uint32_t* sign_counts;   // [nseg][B]
+  uint32_t* plane_nz;      // [B] nonzero words per plane
+  unsigned long long* pairs; // [B][B] (PSNR mode) or nullptr
+  unsigned long long* vmax;  // max |value| (float bits / double bits / u64)
+  void* stage;         // staged values, padded canonical order
+  int b;               // planes to decode (retrieval)
+  int E;               // float streams: exponent; fixed: bit length e
+  int sh;              // fixed streams: quantisation shift
+};
+
+// coefficient decomposition of one region (Sec. V-B): in-slice axes u, v and
+// the sub-level (1 = raw 4-grid, 2 = 2-grid, 3 = full grid)
+struct DecompGeo {
+  LatD region;
+  int u, v;
+  int sub;
+};
+
+struct WorkItem {
+  int stream;          // index into the StreamD array of the launch
+  int seg;
+};
+
+// Device statistics of one field.
+struct FieldStats {
+  unsigned long long xmin_key, xmax_key;   // order-preserving keys of doubles
+  unsigned long long c0;                   // max |c| at level 0 (double bits)
+  int G;                                   // max|x| < 2^G
+  int bad;                                 // non-finite input seen
+};
+
+}  // namespace pcr

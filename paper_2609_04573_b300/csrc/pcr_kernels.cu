@@ -1,0 +1,1107 @@
+// CUDA kernels of the progressive refactor / retrieve path (sm_103a).
+//
+// Section references are to arXiv 2609.04573 (ProAICD).  Arithmetic follows
+// fixed expression trees (compiled with -fmad=false and written with _rn
+// intrinsics) so that results are reproducible bit for bit:
+//   level 0 and its coefficient decomposition in the field dtype;
+//   levels >= 1 in exact 64-bit fixed point (quantum 2^(G-40)).
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <type_traits>
+
+#include "pcr_internal.h"
+
+namespace pcr {
+
+#define FULL 0xFFFFFFFFu
+
+// --------------------------------------------------------------------------
+// 1-D interpolation rules (Sec. IV): cubic in the interior, 3-point Lagrange
+// at either edge, 2-point mean, and the left neighbour when the line ends.
+// --------------------------------------------------------------------------
+template <typename T> struct Ar;
+
+template <> struct Ar<float> {
+  __device__ static float lin(float a, float b) { return __fmul_rn(__fadd_rn(a, b), 0.5f); }
+  __device__ static float cub(float m3, float m1, float p1, float p3) {
+    return __fmul_rn(__fsub_rn(__fmul_rn(__fadd_rn(m1, p1), 9.0f), __fadd_rn(m3, p3)), 0.0625f);
+  }
+  __device__ static float lft(float m1, float p1, float p3) {
+    return __fmul_rn(__fsub_rn(__fadd_rn(__fmul_rn(3.0f, m1), __fmul_rn(6.0f, p1)), p3), 0.125f);
+  }
+  __device__ static float rgt(float m3, float m1, float p1) {
+    return __fmul_rn(__fsub_rn(__fadd_rn(__fmul_rn(6.0f, m1), __fmul_rn(3.0f, p1)), m3), 0.125f);
+  }
+  __device__ static float add(float a, float b) { return __fadd_rn(a, b); }
+  __device__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+};
+
+template <> struct Ar<double> {
+  __device__ static double lin(double a, double b) { return __dmul_rn(__dadd_rn(a, b), 0.5); }
+  __device__ static double cub(double m3, double m1, double p1, double p3) {
+    return __dmul_rn(__dsub_rn(__dmul_rn(__dadd_rn(m1, p1), 9.0), __dadd_rn(m3, p3)), 0.0625);
+  }
+  __device__ static double lft(double m1, double p1, double p3) {
+    return __dmul_rn(__dsub_rn(__dadd_rn(__dmul_rn(3.0, m1), __dmul_rn(6.0, p1)), p3), 0.125);
+  }
+  __device__ static double rgt(double m3, double m1, double p1) {
+    return __dmul_rn(__dsub_rn(__dadd_rn(__dmul_rn(6.0, m1), __dmul_rn(3.0, p1)), m3), 0.125);
+  }
+  __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
+  __device__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+};
+
+template <> struct Ar<int64_t> {
+  __device__ static int64_t lin(int64_t a, int64_t b) { return (a + b) >> 1; }
+  __device__ static int64_t cub(int64_t m3, int64_t m1, int64_t p1, int64_t p3) {
+    return (9 * (m1 + p1) - (m3 + p3)) >> 4;
+  }
+  __device__ static int64_t lft(int64_t m1, int64_t p1, int64_t p3) { return (3 * m1 + 6 * p1 - p3) >> 3; }
+  __device__ static int64_t rgt(int64_t m3, int64_t m1, int64_t p1) { return (6 * m1 + 3 * p1 - m3) >> 3; }
+  __device__ static int64_t add(int64_t a, int64_t b) { return a + b; }
+  __device__ static int64_t sub(int64_t a, int64_t b) { return a - b; }
+};
+
+template <typename T, class F>
+__device__ __forceinline__ T rule1d(int64_t j, int64_t m, int degree, const F& at) {
+  const bool p1 = j + 1 < m, m3 = j - 3 >= 0, p3 = j + 3 < m;
+  if (degree == 3 && p1 && m3 && p3) return Ar<T>::cub(at(j - 3), at(j - 1), at(j + 1), at(j + 3));
+  if (degree == 3 && p1 && p3) return Ar<T>::lft(at(j - 1), at(j + 1), at(j + 3));
+  if (degree == 3 && p1 && m3) return Ar<T>::rgt(at(j - 3), at(j - 1), at(j + 1));
+  if (p1) return Ar<T>::lin(at(j - 1), at(j + 1));
+  return at(j - 1);
+}
+
+// Tensor recursion of the per-level scheme: the rule along odd[I] applied to
+// values that are themselves predictions along odd[0..I-1] (Sec. VI-C: the
+// per-level interpolant equals sequential passes that read predictions).
+template <typename T, int I, class G>
+__device__ __forceinline__ T wrec(int64_t q0, int64_t q1, int64_t q2, const int* odd,
+                                  const int64_t* m, int degree, const G& get) {
+  if constexpr (I < 0) {
+    return get(q0, q1, q2);
+  } else {
+    const int a = odd[I];
+    const int64_t j = a == 0 ? q0 : (a == 1 ? q1 : q2);
+    auto at = [&](int64_t t) -> T {
+      return wrec<T, I - 1>(a == 0 ? t : q0, a == 1 ? t : q1, a == 2 ? t : q2, odd, m, degree, get);
+    };
+    return rule1d<T>(j, m[a], degree, at);
+  }
+}
+
+// Prediction at level-grid coordinates q (some coordinate odd along a pass
+// axis).  per-level: rules along every odd axis in pass order, innermost
+// first; per-region: one rule along the last odd pass axis reading `get`.
+template <typename T, class G>
+__device__ __forceinline__ T predict(const int64_t* q, const int64_t* m, const int* order, int d,
+                                     int interp, int degree, const G& get) {
+  int odd[3];
+  int k = 0;
+  for (int i = 0; i < d; i++)
+    if (q[order[i]] & 1) odd[k++] = order[i];
+  if (interp == 1 && k > 1) {
+    odd[0] = odd[k - 1];
+    k = 1;
+  }
+  switch (k) {
+    case 1: return wrec<T, 0>(q[0], q[1], q[2], odd, m, degree, get);
+    case 2: return wrec<T, 1>(q[0], q[1], q[2], odd, m, degree, get);
+    case 3: return wrec<T, 2>(q[0], q[1], q[2], odd, m, degree, get);
+    default: return get(q[0], q[1], q[2]);
+  }
+}
+
+// --------------------------------------------------------------------------
+// helpers
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long dkey(double x) {
+  unsigned long long u = __double_as_longlong(x);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+template <typename T> __device__ __forceinline__ unsigned long long absbits(T v);
+template <> __device__ __forceinline__ unsigned long long absbits<float>(float v) {
+  return __float_as_uint(fabsf(v));
+}
+template <> __device__ __forceinline__ unsigned long long absbits<double>(double v) {
+  return (unsigned long long)__double_as_longlong(fabs(v));
+}
+template <> __device__ __forceinline__ unsigned long long absbits<int64_t>(int64_t v) {
+  return (unsigned long long)(v < 0 ? -v : v);
+}
+
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    unsigned long long t = __shfl_xor_sync(FULL, v, o);
+    v = t > v ? t : v;
+  }
+  return v;
+}
+
+// floor(x 2^(40-G)) for finite x with |x| < 2^G (exact bit manipulation).
+template <typename T> __device__ __forceinline__ int64_t fix_from(T x, int G);
+template <> __device__ __forceinline__ int64_t fix_from<float>(float x, int G) {
+  const uint32_t u = __float_as_uint(x);
+  const int e = (u >> 23) & 0xFF;
+  const int64_t val = e ? (int64_t)((u & 0x7FFFFFu) | 0x800000u) : (int64_t)(u & 0x7FFFFFu);
+  if (val == 0) return 0;
+  const int sh = (e ? e - 150 : -149) + kFixBits - G;
+  const bool neg = u >> 31;
+  if (sh >= 0) { const int64_t r = val << sh; return neg ? -r : r; }
+  const int k = -sh;
+  if (k >= 62) return neg ? -1 : 0;
+  if (!neg) return val >> k;
+  return -((val + ((int64_t(1) << k) - 1)) >> k);
+}
+template <> __device__ __forceinline__ int64_t fix_from<double>(double x, int G) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7FF);
+  const int64_t val = e ? (int64_t)((u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull)
+                        : (int64_t)(u & 0xFFFFFFFFFFFFFull);
+  if (val == 0) return 0;
+  const int sh = (e ? e - 1075 : -1074) + kFixBits - G;
+  const bool neg = u >> 63;
+  if (sh >= 0) { const int64_t r = val << sh; return neg ? -r : r; }
+  const int k = -sh;
+  if (k >= 62) return neg ? -1 : 0;
+  if (!neg) return val >> k;
+  return -((val + ((int64_t(1) << k) - 1)) >> k);
+}
+
+template <typename T> __device__ __forceinline__ T from_fix(int64_t v, T scale);
+template <> __device__ __forceinline__ float from_fix<float>(int64_t v, float scale) {
+  return __fmul_rn(__ll2float_rn(v), scale);
+}
+template <> __device__ __forceinline__ double from_fix<double>(int64_t v, double scale) {
+  return __dmul_rn(__ll2double_rn(v), scale);
+}
+
+// lattice element -> field coordinates; returns false for row padding
+__device__ __forceinline__ bool lat_coords(const LatD& l, int64_t idx, int64_t* p) {
+  const int64_t col = idx % l.row_pad;
+  if (col >= l.count[2]) return false;
+  const int64_t row = idx / l.row_pad;
+  const int64_t k1 = row % l.count[1], k0 = row / l.count[1];
+  p[0] = l.start[0] + l.step[0] * k0;
+  p[1] = l.start[1] + l.step[1] * k1;
+  p[2] = l.start[2] + l.step[2] * col;
+  return true;
+}
+
+__device__ __forceinline__ int64_t lat_padded_index(const LatD& l, const int64_t* p) {
+  const int64_t k0 = (p[0] - l.start[0]) / l.step[0];
+  const int64_t k1 = (p[1] - l.start[1]) / l.step[1];
+  const int64_t k2 = (p[2] - l.start[2]) / l.step[2];
+  return l.base + (k0 * l.count[1] + k1) * l.row_pad + k2;
+}
+
+// --------------------------------------------------------------------------
+// a1: field statistics
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void k_minmax(const T* __restrict__ x, int64_t n, FieldStats* st) {
+  T lo = x[0], hi = x[0];
+  int bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T v = x[i];
+    if (!isfinite(v)) bad = 1;
+    lo = v < lo ? v : lo;
+    hi = v > hi ? v : hi;
+  }
+  unsigned long long klo = dkey((double)lo), khi = dkey((double)hi);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    unsigned long long a = __shfl_xor_sync(FULL, klo, o), b = __shfl_xor_sync(FULL, khi, o);
+    klo = a < klo ? a : klo;
+    khi = b > khi ? b : khi;
+  }
+  bad = __any_sync(FULL, bad);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&st->xmin_key, klo);
+    atomicMax(&st->xmax_key, khi);
+    if (bad) st->bad = 1;
+  }
+}
+
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+  unsigned long long u = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  return __longlong_as_double((long long)u);
+}
+
+__global__ void k_stats_finalize(FieldStats* st) {
+  const double lo = dkey_inv(st->xmin_key), hi = dkey_inv(st->xmax_key);
+  const double M = fmax(fabs(lo), fabs(hi));
+  int G = 0;
+  if (M > 0) frexp(M, &G);
+  st->G = G;
+}
+
+// fixed-point copy of the 2-grid (coarse points of level 0)
+template <typename T>
+__global__ void k_to_fixed(const T* __restrict__ x, FieldD f, const FieldStats* st,
+                           int64_t* __restrict__ xc) {
+  const int G = st->G;
+  const int64_t n = f.nc[0] * f.nc[1] * f.nc[2];
+  const int s0 = f.n[0] > 1 ? 2 : 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c2 = i % f.nc[2], t = i / f.nc[2];
+    const int64_t c1 = t % f.nc[1], c0 = t / f.nc[1];
+    xc[i] = fix_from<T>(x[((c0 * s0) * f.n[1] + 2 * c1) * f.n[2] + 2 * c2], G);
+  }
+}
+
+// --------------------------------------------------------------------------
+// coefficients (Alg. 1): c = x - P(x) at the points of one lattice
+// --------------------------------------------------------------------------
+struct LevelGrid {
+  int64_t m[3];     // level-grid lengths
+  int64_t s;        // stride of the level in field units
+};
+
+__device__ __forceinline__ LevelGrid level_grid(const FieldD& f, int level) {
+  LevelGrid g;
+  g.s = int64_t(1) << level;
+  for (int a = 0; a < 3; a++) g.m[a] = f.n[a] > 1 ? (f.n[a] - 1) / g.s + 1 : 1;
+  return g;
+}
+
+// fixed-point levels >= 1: values from the 2-grid copy; raw = coarsest level
+__global__ void k_coef_fixed(FieldD f, int level, int raw, LatD lat, const int64_t* __restrict__ xc,
+                             int64_t* __restrict__ out, unsigned long long* vmax) {
+  const LevelGrid g = level_grid(f, level);
+  const int64_t half = g.s >> 1;
+  const int64_t n = lat.count[0] * lat.count[1] * lat.row_pad;
+  auto get = [&](int64_t a0, int64_t a1, int64_t a2) -> int64_t {
+    return xc[((a0 * (f.n[0] > 1 ? half : 0)) * f.nc[1] + a1 * half) * f.nc[2] + a2 * half];
+  };
+  unsigned long long mx = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p[3];
+    int64_t c = 0;
+    if (lat_coords(lat, i, p)) {
+      int64_t q[3] = {p[0] / g.s, p[1] / g.s, p[2] / g.s};
+      const int64_t v = get(q[0], q[1], q[2]);
+      c = raw ? v : v - predict<int64_t>(q, g.m, f.order, f.d, f.interp, f.degree, get);
+    }
+    out[lat.base + i] = c;
+    const unsigned long long a = absbits<int64_t>(c);
+    mx = a > mx ? a : mx;
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(vmax, mx);
+}
+
+// level 0 in the field dtype.  compact != 0: write the region's compact
+// (unpadded) array for the decomposition; else the padded stream layout.
+template <typename T>
+__global__ void k_coef_l0(FieldD f, LatD lat, int compact, const T* __restrict__ x,
+                          T* __restrict__ out, unsigned long long* vmax, unsigned long long* c0) {
+  const LevelGrid g = level_grid(f, 0);
+  const int64_t n = compact ? lat.count[0] * lat.count[1] * lat.count[2]
+                            : lat.count[0] * lat.count[1] * lat.row_pad;
+  auto get = [&](int64_t a0, int64_t a1, int64_t a2) -> T { return x[(a0 * f.n[1] + a1) * f.n[2] + a2]; };
+  unsigned long long mx = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p[3];
+    bool real;
+    if (compact) {
+      const int64_t k2 = i % lat.count[2], t = i / lat.count[2];
+      p[0] = lat.start[0] + lat.step[0] * (t / lat.count[1]);
+      p[1] = lat.start[1] + lat.step[1] * (t % lat.count[1]);
+      p[2] = lat.start[2] + lat.step[2] * k2;
+      real = true;
+    } else {
+      real = lat_coords(lat, i, p);
+    }
+    T c = T(0);
+    if (real) c = Ar<T>::sub(get(p[0], p[1], p[2]),
+                             predict<T>(p, g.m, f.order, f.d, f.interp, f.degree, get));
+    out[(compact ? 0 : lat.base) + i] = c;
+    const unsigned long long a = absbits<T>(c);
+    mx = a > mx ? a : mx;
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0 && mx) {
+    if (vmax) {
+      if (sizeof(T) == 4) atomicMax((unsigned int*)vmax, (unsigned int)mx);
+      else atomicMax(vmax, mx);
+    }
+    if (c0) {
+      double dv = sizeof(T) == 4 ? (double)__uint_as_float((unsigned int)mx)
+                                 : __longlong_as_double((long long)mx);
+      atomicMax(c0, (unsigned long long)__double_as_longlong(dv));
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// coefficient decomposition (Sec. V-B, Alg. 1): 2-D per-level linear
+// hierarchy on every slice normal to axis `nrm` of a region's compact array.
+// sub 1: raw 4-grid; sub 2: predicted on the 2-grid from the 4-grid; sub 3:
+// predicted on the full grid from the 2-grid (originals in both).
+// --------------------------------------------------------------------------
+template <typename T, class G>
+__device__ __forceinline__ T decomp_predict(const DecompGeo& dg, const int64_t* kc, const G& getc) {
+  // getc(k0, k1, k2) reads the region compact array
+  const int64_t cu = dg.region.count[dg.u], cv = dg.region.count[dg.v];
+  const int ord[2] = {dg.u, dg.v};
+  if (dg.sub == 2) {
+    int64_t m[3] = {1, 1, 1};
+    m[dg.u] = (cu + 1) / 2;
+    m[dg.v] = (cv + 1) / 2;
+    int64_t q[3] = {kc[0], kc[1], kc[2]};
+    q[dg.u] >>= 1;
+    q[dg.v] >>= 1;
+    const int u = dg.u, v = dg.v;
+    auto get2 = [&](int64_t a0, int64_t a1, int64_t a2) -> T {
+      int64_t k[3] = {a0, a1, a2};
+      k[u] *= 2;
+      k[v] *= 2;
+      return getc(k[0], k[1], k[2]);
+    };
+    return predict<T>(q, m, ord, 2, 0, 1, get2);
+  }
+  int64_t m[3] = {1, 1, 1};
+  m[dg.u] = cu;
+  m[dg.v] = cv;
+  return predict<T>(kc, m, ord, 2, 0, 1, getc);
+}
+
+template <typename T>
+__global__ void k_decompose(DecompGeo dg, LatD sl, const T* __restrict__ comp, T* __restrict__ out,
+                            unsigned long long* vmax) {
+  const LatD& R = dg.region;
+  const int64_t n = sl.count[0] * sl.count[1] * sl.row_pad;
+  auto getc = [&](int64_t a0, int64_t a1, int64_t a2) -> T {
+    return comp[(a0 * R.count[1] + a1) * R.count[2] + a2];
+  };
+  unsigned long long mx = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p[3];
+    T dv = T(0);
+    if (lat_coords(sl, i, p)) {
+      const int64_t kc[3] = {(p[0] - R.start[0]) / R.step[0], (p[1] - R.start[1]) / R.step[1],
+                             (p[2] - R.start[2]) / R.step[2]};
+      const T c = getc(kc[0], kc[1], kc[2]);
+      dv = dg.sub == 1 ? c : Ar<T>::sub(c, decomp_predict<T>(dg, kc, getc));
+    }
+    out[sl.base + i] = dv;
+    const unsigned long long a = absbits<T>(dv);
+    mx = a > mx ? a : mx;
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0 && mx) {
+    if (sizeof(T) == 4) atomicMax((unsigned int*)vmax, (unsigned int)mx);
+    else atomicMax(vmax, mx);
+  }
+}
+
+// inverse (Alg. 2): comp[k] = d_hat (S1) or d_hat + prediction (S2, S3)
+template <typename T>
+__global__ void k_recompose(DecompGeo dg, LatD sl, const T* __restrict__ dec, T* __restrict__ comp) {
+  const LatD& R = dg.region;
+  const int64_t n = sl.count[0] * sl.count[1] * sl.count[2];
+  auto getc = [&](int64_t a0, int64_t a1, int64_t a2) -> T {
+    return comp[(a0 * R.count[1] + a1) * R.count[2] + a2];
+  };
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k2 = i % sl.count[2], t = i / sl.count[2];
+    const int64_t p[3] = {sl.start[0] + sl.step[0] * (t / sl.count[1]),
+                          sl.start[1] + sl.step[1] * (t % sl.count[1]), sl.start[2] + sl.step[2] * k2};
+    const int64_t kc[3] = {(p[0] - R.start[0]) / R.step[0], (p[1] - R.start[1]) / R.step[1],
+                           (p[2] - R.start[2]) / R.step[2]};
+    const T d = dec[sl.base + (t * sl.row_pad) + k2];
+    const T r = dg.sub == 1 ? d : Ar<T>::add(decomp_predict<T>(dg, kc, getc), d);
+    comp[(kc[0] * R.count[1] + kc[1]) * R.count[2] + kc[2]] = r;
+  }
+}
+
+// --------------------------------------------------------------------------
+// reconstruction (Alg. 2)
+// --------------------------------------------------------------------------
+// fixed-point levels >= 1: xc[p/2] = P(xc) + c_hat (raw: = c_hat)
+__global__ void k_recon_fixed(FieldD f, int level, int raw, LatD lat, const int64_t* __restrict__ chat,
+                              int64_t* __restrict__ xc) {
+  const LevelGrid g = level_grid(f, level);
+  const int64_t half = g.s >> 1;
+  const int64_t n = lat.count[0] * lat.count[1] * lat.count[2];
+  auto idx = [&](int64_t a0, int64_t a1, int64_t a2) -> int64_t {
+    return ((a0 * (f.n[0] > 1 ? half : 0)) * f.nc[1] + a1 * half) * f.nc[2] + a2 * half;
+  };
+  auto get = [&](int64_t a0, int64_t a1, int64_t a2) -> int64_t { return xc[idx(a0, a1, a2)]; };
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k2 = i % lat.count[2], t = i / lat.count[2];
+    const int64_t p[3] = {lat.start[0] + lat.step[0] * (t / lat.count[1]),
+                          lat.start[1] + lat.step[1] * (t % lat.count[1]), lat.start[2] + lat.step[2] * k2};
+    int64_t q[3] = {p[0] / g.s, p[1] / g.s, p[2] / g.s};
+    const int64_t ch = chat[lat.base + t * lat.row_pad + k2];
+    const int64_t v = raw ? ch : predict<int64_t>(q, g.m, f.order, f.d, f.interp, f.degree, get) + ch;
+    xc[idx(q[0], q[1], q[2])] = v;
+  }
+}
+
+// coarse points of level 0: out[2-grid] = x_int h rounded once
+template <typename T>
+__global__ void k_coarse_out(FieldD f, const int64_t* __restrict__ xc, T scale, T* __restrict__ out) {
+  const int64_t n = f.nc[0] * f.nc[1] * f.nc[2];
+  const int s0 = f.n[0] > 1 ? 2 : 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c2 = i % f.nc[2], t = i / f.nc[2];
+    const int64_t c1 = t % f.nc[1], c0 = t / f.nc[1];
+    out[((c0 * s0) * f.n[1] + 2 * c1) * f.n[2] + 2 * c2] = from_fix<T>(xc[i], scale);
+  }
+}
+
+// level 0: out[p] = P(out) + c_hat; c_hat from the padded stream layout of
+// `lat` (compact == 0) or from the region's recomposed compact array.
+template <typename T>
+__global__ void k_recon_l0(FieldD f, LatD lat, int compact, const T* __restrict__ chat, T* __restrict__ out) {
+  const LevelGrid g = level_grid(f, 0);
+  const int64_t n = lat.count[0] * lat.count[1] * lat.count[2];
+  auto get = [&](int64_t a0, int64_t a1, int64_t a2) -> T { return out[(a0 * f.n[1] + a1) * f.n[2] + a2]; };
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k2 = i % lat.count[2], t = i / lat.count[2];
+    const int64_t p[3] = {lat.start[0] + lat.step[0] * (t / lat.count[1]),
+                          lat.start[1] + lat.step[1] * (t % lat.count[1]), lat.start[2] + lat.step[2] * k2};
+    const T ch = compact ? chat[i] : chat[lat.base + t * lat.row_pad + k2];
+    out[(p[0] * f.n[1] + p[1]) * f.n[2] + p[2]] =
+        Ar<T>::add(predict<T>(p, g.m, f.order, f.d, f.interp, f.degree, get), ch);
+  }
+}
+
+// L == 1: the whole field is the raw coarse stream
+template <typename T>
+__global__ void k_copy_raw(FieldD f, LatD lat, const T* __restrict__ vals, T* __restrict__ out) {
+  const int64_t n = lat.count[0] * lat.count[1] * lat.count[2];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k2 = i % lat.count[2], t = i / lat.count[2];
+    const int64_t p0 = t / lat.count[1], p1 = t % lat.count[1];
+    out[(p0 * f.n[1] + p1) * f.n[2] + k2] = vals[t * lat.row_pad + k2];
+  }
+}
+
+template <typename T>
+__global__ void k_raw_stage(FieldD f, LatD lat, const T* __restrict__ x, T* __restrict__ out,
+                            unsigned long long* vmax) {
+  const int64_t n = lat.count[0] * lat.count[1] * lat.row_pad;
+  unsigned long long mx = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p[3];
+    T v = T(0);
+    if (lat_coords(lat, i, p)) v = x[(p[0] * f.n[1] + p[1]) * f.n[2] + p[2]];
+    out[i] = v;
+    const unsigned long long a = absbits<T>(v);
+    mx = a > mx ? a : mx;
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0 && mx) {
+    if (sizeof(T) == 4) atomicMax((unsigned int*)vmax, (unsigned int)mx);
+    else atomicMax(vmax, mx);
+  }
+}
+
+// --------------------------------------------------------------------------
+// bitplanes (Sec. V-C; Sec. VI-A encodings)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+#pragma unroll
+  for (int j = 16; j >= 1; j >>= 1) {
+    const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
+                     : j == 2 ? 0x33333333u : 0x55555555u;
+    const uint32_t y = __shfl_xor_sync(FULL, x, j);
+    x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
+  }
+  return x;
+}
+
+__host__ __device__ __forceinline__ uint64_t nb_mask(int B) {
+  uint64_t m = 0;
+  for (int i = 1; i < B; i += 2) m |= uint64_t(1) << i;
+  return m;
+}
+
+// quantisation parameters of one stream from its maximum
+struct QParams {
+  int E;      // float exponent, or fixed bit length
+  int sh;     // fixed shift
+  bool zero;
+};
+
+__device__ __forceinline__ QParams qparams(const StreamD& s) {
+  QParams q;
+  const unsigned long long vm = *s.vmax;
+  q.zero = vm == 0;
+  q.E = 0;
+  q.sh = 0;
+  if (s.vk == VK_F32) {
+    if (vm) frexpf(__uint_as_float((unsigned)vm), &q.E);
+  } else if (s.vk == VK_F64) {
+    if (vm) frexp(__longlong_as_double((long long)vm), &q.E);
+  } else {
+    q.E = vm ? 64 - __clzll((long long)vm) : 0;
+    const int lim = s.enc == 2 ? s.B - 3 : s.B;
+    q.sh = q.E > lim ? q.E - lim : 0;
+  }
+  return q;
+}
+
+template <typename VT, int W> struct Code;  // W-bit code of one value
+
+template <int W>
+using code_t = typename std::conditional<W == 32, uint32_t, uint64_t>::type;
+
+template <typename VT, int W>
+__device__ __forceinline__ code_t<W> quantize(VT v, const StreamD& s, const QParams& qp, bool& neg) {
+  using C = code_t<W>;
+  const int B = s.B;
+  const C M = (C)nb_mask(B);
+  if constexpr (std::is_same<VT, int64_t>::value) {
+    const uint64_t a = (uint64_t)(v < 0 ? -v : v);
+    neg = v < 0;
+    const uint64_t mag = a >> qp.sh;
+    if (s.enc == 1) return (C)mag;
+    const int64_t sv = neg ? -(int64_t)mag : (int64_t)mag;
+    return (C)(((C)sv + M) ^ M);
+  } else if constexpr (std::is_same<VT, float>::value) {
+    neg = v < 0.0f;
+    if (s.enc == 1) return (C)__float2uint_rz(ldexpf(fabsf(v), B - qp.E));
+    const int sv = __float2int_rz(ldexpf(v, B - 3 - qp.E));
+    return (C)(((C)(int64_t)sv + M) ^ M);
+  } else {
+    neg = v < 0.0;
+    if (s.enc == 1) return (C)__double2ull_rz(ldexp(fabs(v), B - qp.E));
+    const long long sv = __double2ll_rz(ldexp(v, B - 3 - qp.E));
+    return (C)(((C)sv + M) ^ M);
+  }
+}
+
+template <typename VT, int W>
+__device__ __forceinline__ VT dequantize(code_t<W> q, bool neg, const StreamD& s) {
+  const int B = s.B;
+  if (s.enc == 1) {
+    if constexpr (std::is_same<VT, int64_t>::value) {
+      const int64_t mag = (int64_t)((uint64_t)q << s.sh);
+      return neg ? -mag : mag;
+    } else if constexpr (std::is_same<VT, float>::value) {
+      const float mag = ldexpf(__uint2float_rn((uint32_t)q), s.E - B);
+      return neg ? -mag : mag;
+    } else {
+      const double mag = ldexp(__ull2double_rn((unsigned long long)q), s.E - B);
+      return neg ? -mag : mag;
+    }
+  }
+  const uint64_t M = nb_mask(B);
+  int64_t val;
+  if (W == 32) val = (int64_t)((uint64_t)(q ^ (code_t<W>)M)) - (int64_t)M;
+  else val = (int64_t)(((uint64_t)q ^ M) - M);
+  if constexpr (std::is_same<VT, int64_t>::value) {
+    return (int64_t)((uint64_t)val << s.sh);
+  } else if constexpr (std::is_same<VT, float>::value) {
+    return ldexpf(__ll2float_rn(val), s.E - B + 3);
+  } else {
+    return ldexp(__ll2double_rn(val), s.E - B + 3);
+  }
+}
+
+template <int NP>
+__device__ __forceinline__ int tri(int a, int b) {  // a <= b
+  return a * NP - (a * (a - 1)) / 2 + (b - a);
+}
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kWordsPerWarp = kSegWords / kWarps;   // 16
+
+// Encode one (stream, segment) per CTA.  W = 32 (FP32 fields) or 64 (FP64).
+template <typename VT, int W, bool PAIRS>
+__global__ void __launch_bounds__(kThreads) k_encode(const StreamD* __restrict__ streams,
+                                                     const WorkItem* __restrict__ items) {
+  constexpr int NP = W;                       // max planes held per lane pair
+  __shared__ uint32_t pbuf[NP][kSegWords + 1];
+  __shared__ uint32_t sbuf[kSegWords + 64];
+  __shared__ uint32_t wcnt[kWarps][NP];
+  __shared__ uint32_t woff[kWarps][NP];
+  __shared__ uint32_t poff[NP + 1];
+  __shared__ uint32_t pnz[NP];
+  __shared__ uint32_t pairs_s[PAIRS ? NP * (NP + 1) / 2 : 1];
+
+  const WorkItem it = items[blockIdx.x];
+  const StreamD& s = streams[it.stream];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int B = s.B;
+  const int64_t e0 = (int64_t)it.seg * kSegElems;
+  const int nw = (int)min((int64_t)kSegWords, (s.n_pad - e0) / 32);
+  const QParams qp = qparams(s);
+  const VT* vals = (const VT*)s.stage;
+  const bool generic = s.enc == 1;
+
+  for (int i = threadIdx.x; i < kSegWords + 64; i += kThreads) sbuf[i] = 0;
+  if (threadIdx.x < NP) pnz[threadIdx.x] = 0;
+  if (PAIRS)
+    for (int i = threadIdx.x; i < NP * (NP + 1) / 2; i += kThreads) pairs_s[i] = 0;
+  __syncthreads();
+
+  uint32_t rec[kWordsPerWarp];
+  uint32_t run_lo = 0, run_hi = 0, nz_lo = 0, nz_hi = 0;
+  uint32_t acc_ll[PAIRS ? 17 : 1], acc_hh[PAIRS && W == 64 ? 17 : 1], acc_lh[PAIRS && W == 64 ? 32 : 1];
+  if (PAIRS) {
+#pragma unroll
+    for (int t = 0; t < 17; t++) acc_ll[t] = 0;
+    if (W == 64) {
+#pragma unroll
+      for (int t = 0; t < 17; t++) acc_hh[t] = 0;
+#pragma unroll
+      for (int t = 0; t < 32; t++) acc_lh[t] = 0;
+    }
+  }
+  const uint32_t lt = (1u << lane) - 1u;
+
+#pragma unroll
+  for (int jj = 0; jj < kWordsPerWarp; jj++) {
+    rec[jj] = 0xFFFFFFFFu;
+    const int j = warp * kWordsPerWarp + jj;
+    if (j >= nw) continue;
+    const VT v = vals[e0 + (int64_t)j * 32 + lane];
+    bool neg;
+    code_t<W> q = qp.zero ? code_t<W>(0) : quantize<VT, W>(v, s, qp, neg);
+    if (qp.zero) neg = false;
+    uint32_t dlo, dhi = 0;
+    if (W == 32) {
+      dlo = transpose32(__brev((uint32_t)q << (32 - B)), lane);
+    } else {
+      const uint64_t r = __brevll((unsigned long long)((uint64_t)q << (64 - B)));
+      dlo = transpose32((uint32_t)r, lane);
+      dhi = transpose32((uint32_t)(r >> 32), lane);
+    }
+    // stored planes (negabinary: XOR with the previous digit plane)
+    uint32_t slo = dlo, shi = dhi;
+    if (!generic) {
+      const uint32_t up = __shfl_up_sync(FULL, dlo, 1);
+      slo = lane ? dlo ^ up : dlo;
+      if (W == 64) {
+        const uint32_t uph = __shfl_up_sync(FULL, dhi, 1);
+        const uint32_t l31 = __shfl_sync(FULL, dlo, 31);
+        shi = dhi ^ (lane ? uph : l31);
+      }
+    }
+    if (lane < B) pbuf[lane][j] = slo;
+    if (W == 64 && lane + 32 < B) pbuf[lane + 32][j] = shi;
+    nz_lo += slo != 0;
+    nz_hi += shi != 0;
+    if (generic) {
+      // first-significance masks: digit plane & ~(OR of earlier planes)
+      uint32_t inc = dlo;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc |= t;
+      }
+      uint32_t exc = __shfl_up_sync(FULL, inc, 1);
+      if (lane == 0) exc = 0;
+      const uint32_t nlo = dlo & ~exc;
+      uint32_t nhi = 0;
+      if (W == 64) {
+        const uint32_t tot = __shfl_sync(FULL, inc, 31);
+        uint32_t inh = dhi;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(FULL, inh, o);
+          if (lane >= o) inh |= t;
+        }
+        inh |= tot;
+        uint32_t exh = __shfl_up_sync(FULL, inh, 1);
+        if (lane == 0) exh = tot;
+        nhi = dhi & ~exh;
+      }
+      // this element's plane and rank among the word's elements of that plane
+      int p = B;
+      if (q) p = (W == 32) ? __clz((uint32_t)q << (32 - B)) : __clzll((long long)((uint64_t)q << (64 - B)));
+      const int pl = p & 31;
+      const uint32_t nml = __shfl_sync(FULL, nlo, pl), nmh = __shfl_sync(FULL, nhi, pl);
+      const uint32_t bl = __shfl_sync(FULL, run_lo, pl), bh = __shfl_sync(FULL, run_hi, pl);
+      const uint32_t nm = p < 32 ? nml : nmh;
+      const uint32_t base = p < 32 ? bl : bh;
+      if (p < B) rec[jj] = (uint32_t)p | ((base + __popc(nm & lt)) << 7) | ((uint32_t)neg << 20);
+      run_lo += __popc(nlo);
+      run_hi += __popc(nhi);
+    }
+    if (PAIRS) {
+#pragma unroll
+      for (int t = 0; t < 17; t++) {
+        const uint32_t o = __shfl_sync(FULL, dlo, (lane + t) & 31);
+        acc_ll[t] += __popc(dlo & o);
+      }
+      if (W == 64) {
+#pragma unroll
+        for (int t = 0; t < 17; t++) {
+          const uint32_t o = __shfl_sync(FULL, dhi, (lane + t) & 31);
+          acc_hh[t] += __popc(dhi & o);
+        }
+#pragma unroll
+        for (int t = 0; t < 32; t++) {
+          const uint32_t o = __shfl_sync(FULL, dhi, (lane + t) & 31);
+          acc_lh[t] += __popc(dlo & o);
+        }
+      }
+    }
+  }
+  // plane nonzero-word counts
+  if (lane < B && nz_lo) atomicAdd(&pnz[lane], nz_lo);
+  if (W == 64 && lane + 32 < B && nz_hi) atomicAdd(&pnz[lane + 32], nz_hi);
+  if (generic) {
+    wcnt[warp][lane] = run_lo;
+    if (W == 64) wcnt[warp][lane + 32] = run_hi;
+  }
+  if (PAIRS) {
+    // pair (a, b) counts of digit planes, plane index a = lane (+32 for hi)
+#pragma unroll
+    for (int t = 0; t < 17; t++) {
+      const int b = (lane + t) & 31;
+      if ((t < 16 || lane < 16) && acc_ll[t]) {
+        const int a0 = min(lane, b), b0 = max(lane, b);
+        atomicAdd(&pairs_s[tri<NP>(a0, b0)], acc_ll[t]);
+      }
+      if (W == 64 && (t < 16 || lane < 16) && acc_hh[t]) {
+        const int a0 = min(lane, b) + 32, b0 = max(lane, b) + 32;
+        atomicAdd(&pairs_s[tri<NP>(a0, b0)], acc_hh[t]);
+      }
+    }
+    if (W == 64) {
+#pragma unroll
+      for (int t = 0; t < 32; t++)
+        if (acc_lh[t]) atomicAdd(&pairs_s[tri<NP>(lane, 32 + ((lane + t) & 31))], acc_lh[t]);
+    }
+  }
+  __syncthreads();
+  if (generic) {
+    if (threadIdx.x < NP) {
+      const int k = threadIdx.x;
+      uint32_t acc = 0;
+      for (int w = 0; w < kWarps; w++) {
+        woff[w][k] = acc;
+        acc += wcnt[w][k];
+      }
+      wcnt[0][k] = acc;   // segment total of plane k
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t o = 0;
+      for (int k = 0; k < B; k++) {
+        poff[k] = o;
+        o += (wcnt[0][k] + 31) >> 5;
+      }
+      poff[B] = o;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < kWordsPerWarp; jj++) {
+      const uint32_t r = rec[jj];
+      if (r != 0xFFFFFFFFu && (r >> 20)) {
+        const int p = r & 127;
+        const uint32_t pos = (r >> 7) & 8191;
+        const uint32_t bit = poff[p] * 32 + woff[warp][p] + pos;
+        atomicOr(&sbuf[bit >> 5], 1u << (bit & 31));
+      }
+    }
+    __syncthreads();
+    uint32_t* dst = s.signs + (int64_t)it.seg * s.slot_words;
+    for (int i = threadIdx.x; i < (int)poff[B]; i += kThreads) dst[i] = sbuf[i];
+    if (threadIdx.x < B) s.sign_counts[(int64_t)it.seg * B + threadIdx.x] = wcnt[0][threadIdx.x];
+  }
+  // plane words: coalesced per plane
+  const int64_t w0 = (int64_t)it.seg * kSegWords;
+  for (int i = threadIdx.x; i < B * nw; i += kThreads) {
+    const int k = i / nw, j = i - k * nw;
+    s.planes[(int64_t)k * s.words + w0 + j] = pbuf[k][j];
+  }
+  if (threadIdx.x < B && pnz[threadIdx.x]) atomicAdd(&s.plane_nz[threadIdx.x], pnz[threadIdx.x]);
+  if (PAIRS) {
+    for (int i = threadIdx.x; i < NP * NP; i += kThreads) {
+      const int a = i / NP, c = i % NP;
+      if (a <= c && c < B && pairs_s[tri<NP>(a, c)])
+        atomicAdd(&s.pairs[a * B + c], (unsigned long long)pairs_s[tri<NP>(a, c)]);
+    }
+  }
+}
+
+// Decode one (stream, segment) per CTA: planes < b (zero-fill below).
+template <typename VT, int W>
+__global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__ streams,
+                                                     const WorkItem* __restrict__ items) {
+  constexpr int NP = W;
+  __shared__ uint32_t pbuf[NP][kSegWords + 1];
+  __shared__ uint32_t sbuf[kSegWords + 64];
+  __shared__ uint32_t wcnt[kWarps][NP];
+  __shared__ uint32_t woff[kWarps][NP];
+  __shared__ uint32_t poff[NP + 1];
+
+  const WorkItem it = items[blockIdx.x];
+  const StreamD& s = streams[it.stream];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int B = s.B, b = s.b;
+  const int64_t e0 = (int64_t)it.seg * kSegElems;
+  const int nw = (int)min((int64_t)kSegWords, (s.n_pad - e0) / 32);
+  const bool generic = s.enc == 1;
+  const int64_t w0 = (int64_t)it.seg * kSegWords;
+  VT* out = (VT*)s.stage;
+
+  for (int i = threadIdx.x; i < b * nw; i += kThreads) {
+    const int k = i / nw, j = i - k * nw;
+    pbuf[k][j] = s.plane_nz[k] ? s.planes[(int64_t)k * s.words + w0 + j] : 0u;
+  }
+  if (generic) {
+    if (threadIdx.x == 0) {
+      uint32_t o = 0;
+      for (int k = 0; k < B; k++) {
+        poff[k] = o;
+        o += (s.sign_counts[(int64_t)it.seg * B + k] + 31) >> 5;
+      }
+      poff[B] = o;
+    }
+    __syncthreads();
+    const uint32_t* src = s.signs + (int64_t)it.seg * s.slot_words;
+    for (int i = threadIdx.x; i < (int)poff[b]; i += kThreads) sbuf[i] = src[i];
+  }
+  __syncthreads();
+
+  auto load_digits = [&](int j, uint32_t& dlo, uint32_t& dhi) {
+    uint32_t xl = lane < b ? pbuf[lane][j] : 0u;
+    uint32_t xh = (W == 64 && lane + 32 < b) ? pbuf[lane + 32][j] : 0u;
+    if (!generic) {
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, xl, o);
+        if (lane >= o) xl ^= t;
+      }
+      if (W == 64) {
+        const uint32_t tot = __shfl_sync(FULL, xl, 31);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(FULL, xh, o);
+          if (lane >= o) xh ^= t;
+        }
+        xh ^= tot;
+      }
+      if (lane >= b) xl = 0;
+      if (lane + 32 >= b) xh = 0;
+    }
+    dlo = xl;
+    dhi = xh;
+  };
+  auto new_masks = [&](uint32_t dlo, uint32_t dhi, uint32_t& nlo, uint32_t& nhi) {
+    uint32_t inc = dlo;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc |= t;
+    }
+    uint32_t exc = __shfl_up_sync(FULL, inc, 1);
+    if (lane == 0) exc = 0;
+    nlo = dlo & ~exc;
+    nhi = 0;
+    if (W == 64) {
+      const uint32_t tot = __shfl_sync(FULL, inc, 31);
+      uint32_t inh = dhi;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, inh, o);
+        if (lane >= o) inh |= t;
+      }
+      inh |= tot;
+      uint32_t exh = __shfl_up_sync(FULL, inh, 1);
+      if (lane == 0) exh = tot;
+      nhi = dhi & ~exh;
+    }
+  };
+
+  if (generic) {
+    uint32_t run_lo = 0, run_hi = 0;
+    for (int jj = 0; jj < kWordsPerWarp; jj++) {
+      const int j = warp * kWordsPerWarp + jj;
+      if (j >= nw) break;
+      uint32_t dlo, dhi, nlo, nhi;
+      load_digits(j, dlo, dhi);
+      new_masks(dlo, dhi, nlo, nhi);
+      run_lo += __popc(nlo);
+      run_hi += __popc(nhi);
+    }
+    wcnt[warp][lane] = run_lo;
+    if (W == 64) wcnt[warp][lane + 32] = run_hi;
+    __syncthreads();
+    if (threadIdx.x < NP) {
+      uint32_t acc = 0;
+      for (int w = 0; w < kWarps; w++) {
+        woff[w][threadIdx.x] = acc;
+        acc += wcnt[w][threadIdx.x];
+      }
+    }
+    __syncthreads();
+  }
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t run_lo = 0, run_hi = 0;
+  for (int jj = 0; jj < kWordsPerWarp; jj++) {
+    const int j = warp * kWordsPerWarp + jj;
+    if (j >= nw) break;
+    uint32_t dlo, dhi;
+    load_digits(j, dlo, dhi);
+    code_t<W> q;
+    if (W == 32) {
+      q = (code_t<W>)(__brev(transpose32(dlo, lane)) >> (32 - B));
+    } else {
+      const uint64_t lo = transpose32(dlo, lane), hi = transpose32(dhi, lane);
+      q = (code_t<W>)(__brevll((unsigned long long)(lo | (hi << 32))) >> (64 - B));
+    }
+    bool neg = false;
+    if (generic) {
+      uint32_t nlo, nhi;
+      new_masks(dlo, dhi, nlo, nhi);
+      int p = B;
+      if (q) p = (W == 32) ? __clz((uint32_t)q << (32 - B)) : __clzll((long long)((uint64_t)q << (64 - B)));
+      const int pl = p & 31;
+      const uint32_t nml = __shfl_sync(FULL, nlo, pl), nmh = __shfl_sync(FULL, nhi, pl);
+      const uint32_t bl = __shfl_sync(FULL, run_lo, pl), bh = __shfl_sync(FULL, run_hi, pl);
+      if (p < B) {
+        const uint32_t nm = p < 32 ? nml : nmh;
+        const uint32_t base = p < 32 ? bl : bh;
+        const uint32_t bit = poff[p] * 32 + woff[warp][p] + base + __popc(nm & lt);
+        neg = (sbuf[bit >> 5] >> (bit & 31)) & 1u;
+      }
+      run_lo += __popc(nlo);
+      run_hi += __popc(nhi);
+    }
+    out[e0 + (int64_t)j * 32 + lane] = dequantize<VT, W>(q, neg, s);
+  }
+}
+
+// --------------------------------------------------------------------------
+// host-callable launchers
+// --------------------------------------------------------------------------
+static int grid_for(int64_t n, int threads = 256) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > 148 * 64) g = 148 * 64;
+  return (int)(g < 1 ? 1 : g);
+}
+
+void launch_minmax(int vk, const void* x, int64_t n, FieldStats* st, cudaStream_t s) {
+  if (vk == VK_F32) k_minmax<float><<<grid_for(n), 256, 0, s>>>((const float*)x, n, st);
+  else k_minmax<double><<<grid_for(n), 256, 0, s>>>((const double*)x, n, st);
+  k_stats_finalize<<<1, 1, 0, s>>>(st);
+}
+
+void launch_to_fixed(int vk, const void* x, const FieldD& f, const FieldStats* st, int64_t* xc,
+                     cudaStream_t s) {
+  const int64_t n = f.nc[0] * f.nc[1] * f.nc[2];
+  if (vk == VK_F32) k_to_fixed<float><<<grid_for(n), 256, 0, s>>>((const float*)x, f, st, xc);
+  else k_to_fixed<double><<<grid_for(n), 256, 0, s>>>((const double*)x, f, st, xc);
+}
+
+void launch_coef_fixed(const FieldD& f, int level, int raw, const LatD& lat, const int64_t* xc,
+                       int64_t* out, unsigned long long* vmax, cudaStream_t s) {
+  const int64_t n = lat.count[0] * lat.count[1] * lat.row_pad;
+  if (n == 0) return;
+  k_coef_fixed<<<grid_for(n), 256, 0, s>>>(f, level, raw, lat, xc, out, vmax);
+}
+
+void launch_coef_l0(int vk, const FieldD& f, const LatD& lat, int compact, const void* x, void* out,
+                    unsigned long long* vmax, unsigned long long* c0, cudaStream_t s) {
+  const int64_t n = lat.count[0] * lat.count[1] * (compact ? lat.count[2] : lat.row_pad);
+  if (n == 0) return;
+  if (vk == VK_F32)
+    k_coef_l0<float><<<grid_for(n), 256, 0, s>>>(f, lat, compact, (const float*)x, (float*)out, vmax, c0);
+  else
+    k_coef_l0<double><<<grid_for(n), 256, 0, s>>>(f, lat, compact, (const double*)x, (double*)out, vmax, c0);
+}
+
+void launch_raw_stage(int vk, const FieldD& f, const LatD& lat, const void* x, void* out,
+                      unsigned long long* vmax, cudaStream_t s) {
+  const int64_t n = lat.count[0] * lat.count[1] * lat.row_pad;
+  if (vk == VK_F32) k_raw_stage<float><<<grid_for(n), 256, 0, s>>>(f, lat, (const float*)x, (float*)out, vmax);
+  else k_raw_stage<double><<<grid_for(n), 256, 0, s>>>(f, lat, (const double*)x, (double*)out, vmax);
+}
+
+void launch_decompose(int vk, const DecompGeo& dg, const LatD& sl, const void* comp, void* out,
+                      unsigned long long* vmax, cudaStream_t s) {
+  const int64_t n = sl.count[0] * sl.count[1] * sl.row_pad;
+  if (n == 0) return;
+  if (vk == VK_F32)
+    k_decompose<float><<<grid_for(n), 256, 0, s>>>(dg, sl, (const float*)comp, (float*)out, vmax);
+  else
+    k_decompose<double><<<grid_for(n), 256, 0, s>>>(dg, sl, (const double*)comp, (double*)out, vmax);
+}
+
+void launch_recompose(int vk, const DecompGeo& dg, const LatD& sl, const void* dec, void* comp,
+                      cudaStream_t s) {
+  const int64_t n = sl.count[0] * sl.count[1] * sl.count[2];
+  if (n == 0) return;
+  if (vk == VK_F32) k_recompose<float><<<grid_for(n), 256, 0, s>>>(dg, sl, (const float*)dec, (float*)comp);
+  else k_recompose<double><<<grid_for(n), 256, 0, s>>>(dg, sl, (const double*)dec, (double*)comp);
+}
+
+void launch_recon_fixed(const FieldD& f, int level, int raw, const LatD& lat, const int64_t* chat,
+                        int64_t* xc, cudaStream_t s) {
+  const int64_t n = lat.count[0] * lat.count[1] * lat.count[2];
+  if (n == 0) return;
+  k_recon_fixed<<<grid_for(n), 256, 0, s>>>(f, level, raw, lat, chat, xc);
+}
+
+void launch_coarse_out(int vk, const FieldD& f, const int64_t* xc, double scale, void* out, cudaStream_t s) {
+  const int64_t n = f.nc[0] * f.nc[1] * f.nc[2];
+  if (vk == VK_F32) k_coarse_out<float><<<grid_for(n), 256, 0, s>>>(f, xc, (float)scale, (float*)out);
+  else k_coarse_out<double><<<grid_for(n), 256, 0, s>>>(f, xc, scale, (double*)out);
+}
+
+void launch_recon_l0(int vk, const FieldD& f, const LatD& lat, int compact, const void* chat, void* out,
+                     cudaStream_t s) {
+  const int64_t n = lat.count[0] * lat.count[1] * lat.count[2];
+  if (n == 0) return;
+  if (vk == VK_F32) k_recon_l0<float><<<grid_for(n), 256, 0, s>>>(f, lat, compact, (const float*)chat, (float*)out);
+  else k_recon_l0<double><<<grid_for(n), 256, 0, s>>>(f, lat, compact, (const double*)chat, (double*)out);
+}
+
+void launch_copy_raw(int vk, const FieldD& f, const LatD& lat, const void* vals, void* out, cudaStream_t s) {
+  const int64_t n = lat.count[0] * lat.count[1] * lat.count[2];
+  if (vk == VK_F32) k_copy_raw<float><<<grid_for(n), 256, 0, s>>>(f, lat, (const float*)vals, (float*)out);
+  else k_copy_raw<double><<<grid_for(n), 256, 0, s>>>(f, lat, (const double*)vals, (double*)out);
+}
+
+// vk: value kind of the streams in this work list; w64: FP64-field word path
+void launch_encode(int vk, int w64, int pairs, const StreamD* d_streams, const WorkItem* d_items,
+                   int nitems, cudaStream_t s) {
+  if (nitems == 0) return;
+#define ENC(VT, W, P) k_encode<VT, W, P><<<nitems, kThreads, 0, s>>>(d_streams, d_items)
+  if (!w64) {
+    if (vk == VK_F32) { if (pairs) ENC(float, 32, true); else ENC(float, 32, false); }
+    else { if (pairs) ENC(int64_t, 32, true); else ENC(int64_t, 32, false); }
+  } else {
+    if (vk == VK_F64) { if (pairs) ENC(double, 64, true); else ENC(double, 64, false); }
+    else { if (pairs) ENC(int64_t, 64, true); else ENC(int64_t, 64, false); }
+  }
+#undef ENC
+}
+
+void launch_decode(int vk, int w64, const StreamD* d_streams, const WorkItem* d_items, int nitems,
+                   cudaStream_t s) {
+  if (nitems == 0) return;
+  if (!w64) {
+    if (vk == VK_F32) k_decode<float, 32><<<nitems, kThreads, 0, s>>>(d_streams, d_items);
+    else k_decode<int64_t, 32><<<nitems, kThreads, 0, s>>>(d_streams, d_items);
+  } else {
+    if (vk == VK_F64) k_decode<double, 64><<<nitems, kThreads, 0, s>>>(d_streams, d_items);
+    else k_decode<int64_t, 64><<<nitems, kThreads, 0, s>>>(d_streams, d_items);
+  }
+}
+
+}  // namespace pcr
