@@ -1,0 +1,335 @@
+"""Benchmark of the B300 progressive refactor / retrieve path (one JSON line).
+
+Workload (default): the 512^3 FP32 turbulence-like field (spectral Gaussian
+random field, |u_hat| ~ k^-11/6, rescaled to [-1, 1], seed 2), refactored with
+per-level cubic interpolation plus coefficient decomposition (slices normal to
+the fastest axis) and generic bitplanes, then retrieved at a relative error
+bound of 1e-4 (the tolerance of the paper's transfer use case).  One step =
+refactor + plan + retrieve of that field.  value = field bytes processed per
+second (refactor input + retrieve output) over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pcr|reference]
+
+Multi-GPU (torchrun): every rank refactors and retrieves its own independent
+field (the paper's block-parallel scaling: no data-path collective), so the
+run is weak scaling; the max over ranks of the timed region defines the time.
+--impl reference times the CPU oracle (test infrastructure) on a bounded
+block of the same workload, on the host cores.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FIELD_SHAPE = (512, 512, 512)
+SEED = 2
+TARGET = ("rel", 1e-4)
+WORKLOAD = "grf_k-5/3_512^3_f32"
+METRIC = "refactor & retrieve GB/s (fraction of HBM roofline) at stated eb/PSNR vs CPU oracle"
+
+# DRAM traffic per launch of the dominant kernel, from the committed ncu
+# summary (profiles/); None when the kernel changed after that capture.
+TRAFFIC_PER_LAUNCH = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pcr", choices=["pcr", "reference"])
+    ap.add_argument("--size", type=int, default=512, help="cube edge (default 512)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for n, v in zip(names, s[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6400.0, "fallback": True}
+
+
+def make_field(shape, device):
+    import numpy as np
+    import torch
+    from synth import grf
+    X = grf(shape, SEED, np.float32)
+    return torch.from_numpy(X).to(device), X
+
+
+def run_pcr(args):
+    import numpy as np
+    import torch
+    import paper_2609_04573_b300 as pcr
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    shape = (args.size,) * 3
+    x, X = make_field(shape, dev)
+    nbytes = x.numel() * x.element_size()
+    scheme = pcr.Scheme(mode="eb", interp="level", degree="cubic", decomp_axis=2)
+    target = pcr.Target(*TARGET)
+    out = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h = pcr.refactor(x, scheme)
+        pl = h.plan(target)
+        h.retrieve(pl, out=out)
+        return h, pl
+
+    for _ in range(args.warmup):
+        h, pl = step()
+    torch.cuda.synchronize()
+    # correctness of the timed configuration: bound respected at full size
+    err = (out.double() - x.double()).abs().max().item()
+    xmin, xmax, _ = h.field_stats()
+    bound_ok = err <= TARGET[1] * (xmax - xmin)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    pcr.profile_enable(True)
+    pcr.profile_read(reset=True)
+    launches0 = pcr.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            h, pl = step()
+        ev1.record(stream)
+        barrier()
+    launches = pcr.launch_count() - launches0
+    prof = pcr.profile_read(reset=True)
+    pcr.profile_enable(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+
+    # e2e through the public API with host buffers (pinned), copies inside
+    xh = torch.from_numpy(X).pin_memory()
+    oh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(x)
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        h2 = pcr.refactor(xd, scheme)
+        h2.retrieve(h2.plan(target), out=out)
+        oh.copy_(out, non_blocking=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        xd.copy_(xh, non_blocking=True)
+        h2 = pcr.refactor(xd, scheme)
+        h2.retrieve(h2.plan(target), out=out)
+        oh.copy_(out, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6400.0)
+    value = world * 2 * nbytes / (ms * 1e-3) / 1e9
+    # per-stage shares and the dominant stage's roofline
+    total_prof = sum(v[0] for v in prof.values()) or 1.0
+    stages = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                  "share": v[0] / total_prof} for k, v in prof.items()}
+    dom = max(prof, key=lambda k: prof[k][0])
+    n = x.numel()
+    algo = algorithmic_bytes(dom, h, n, x.element_size(), pl)
+    dom_ms = prof[dom][0] / max(prof[dom][1], 1)         # per launch
+    achieved = algo["per_launch"] / (dom_ms * 1e-3) / 1e9 if algo["per_launch"] else None
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": (achieved / hbm) if achieved else None, "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+            "algorithmic_bytes_per_launch": algo["per_launch"], "ms_per_launch": dom_ms,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not pk.get("fallback") else "fallback"}
+    refactor_ms = sum(v[0] for k, v in prof.items() if k in REFACTOR_STAGES) / args.steps
+    retrieve_ms = sum(v[0] for k, v in prof.items() if k in RETRIEVE_STAGES) / args.steps
+    strict = 8.1 * n / 1e9 / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shape": list(shape), "scheme": "per-level cubic + "
+                   "coefficient decomposition (axis 2) + generic bitplanes, B=32",
+                   "target": f"{TARGET[0]} {TARGET[1]}", "l2": "inputs larger than L2 (512 MB field)",
+                   "parallelism": f"replicas x{world}"},
+        "refactor_gbs": nbytes / (refactor_ms * 1e-3) / 1e9 if refactor_ms else None,
+        "retrieve_gbs": nbytes / (retrieve_ms * 1e-3) / 1e9 if retrieve_ms else None,
+        "strict_roofline_frac": {"refactor": (8.1 * n / (refactor_ms * 1e-3) / 1e9) / hbm if refactor_ms else None,
+                                 "retrieve": ((pl.bytes + 4 * n) / (retrieve_ms * 1e-3) / 1e9) / hbm
+                                 if retrieve_ms else None},
+        "retrieve_bytes_per_elem": pl.bytes / n, "bound_respected_full_size": bool(bound_ok),
+        "max_err": err, "roofline": roof, "stages": stages,
+        "e2e": {"value": world * 2 * nbytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu_baseline(),
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+REFACTOR_STAGES = {"stats", "to_fixed", "coarsest", "interp_level0", "interp_fixed_levels", "zero_pads",
+                   "absmax", "decompose", "encode_float", "encode_fixed"}
+RETRIEVE_STAGES = {"decode_float", "decode_fixed", "recompose", "recon_coarsest", "recon_fixed_levels",
+                   "coarse_out", "recon_level0", "copy_raw"}
+
+
+def algorithmic_bytes(stage, h, n, w, pl):
+    """Algorithmic DRAM bytes of one launch of a stage (defined in the design doc):
+    interp_level0 (refactor): read the field, write level-0 coefficients;
+    recon_level0: read coarse values and level-0 coefficients, write field;
+    decompose / recompose: read and write the decomposed region values;
+    encode_float: read level-0 stream values, write B planes + signs;
+    decode_float: read the planned planes + signs, write stream values."""
+    n0 = n - math.prod((s + 1) // 2 for s in FIELD_SHAPE)  # level-0 points (odd somewhere)
+    table = {
+        "interp_level0": (n * w + n0 * w) / 1,
+        "recon_level0": (n0 * w + n * w) / 1,
+        "decompose": 2 * n0 * w / 3,          # three launches (regions) per step
+        "recompose": 2 * n0 * w / 3,
+        "encode_float": n0 * w + n0 * 4 + n0 / 8,
+        "decode_float": pl.bytes + n0 * w,
+    }
+    return {"per_launch": table.get(stage)}
+
+
+def cpu_baseline():
+    """The oracle on a bounded block of the same workload (host cores)."""
+    import numpy as np
+    import oracle
+    from synth import grf
+    edge = 256
+    X = grf((edge,) * 3, SEED, np.float32)
+    t0 = time.perf_counter()
+    h = oracle.refactor(X, oracle.Scheme(mode="eb", interp="level", degree="cubic", decomp_axis=2))
+    oracle.retrieve(h, oracle.Target(*TARGET))
+    dt = time.perf_counter() - t0
+    return {"value": 2 * X.nbytes / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"one {edge}^3 block of the same recipe (refactor + retrieve at rel 1e-4), "
+                      f"{dt:.1f} s single-threaded numpy"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from synth import grf
+    edge = 128
+    X = grf((edge,) * 3, SEED, np.float32)
+    sch = oracle.Scheme(mode="eb", interp="level", degree="cubic", decomp_axis=2)
+    for _ in range(args.warmup):
+        h = oracle.refactor(X, sch)
+        oracle.retrieve(h, oracle.Target(*TARGET))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        h = oracle.refactor(X, sch)
+        oracle.retrieve(h, oracle.Target(*TARGET))
+    dt = (time.perf_counter() - t0) / args.steps
+    v = 2 * X.nbytes / dt / 1e9
+    sample = f"one {edge}^3 block of the same recipe per step (refactor + retrieve at rel 1e-4)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shape": list(FIELD_SHAPE), "sample_shape": [edge] * 3},
+        "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_pcr(a)

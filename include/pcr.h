@@ -71,8 +71,8 @@ typedef struct {
  *               PCR_MODE_PSNR: also exact integer squared-error tables.
  *   interp      per-level (pass order = natural axis order) or per-region.
  *   degree      PCR_LINEAR or PCR_CUBIC.
- *   order       per-region pass order: a permutation of the active axes
- *               (3-D: 0,1,2; 2-D: 1,2 in order[0..1]); ignored per-level.
+ *   order       per-region pass order: a permutation of the field's axes
+ *               (3-D: of 0,1,2; 2-D: of 0,1 in order[0..1]); ignored per-level.
  *   decomp_axis slice normal (0..2) of the level-0 coefficient decomposition
  *               (Sec. V-B), or -1 for none; 3-D only.
  *   encoding    PCR_ENC_DEFAULT picks generic for EB, negabinary+XOR for PSNR.
@@ -179,6 +179,19 @@ pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_allocator* all
 void pcr_buffer_free(void* buf);
 void pcr_free(pcr_handle* h);
 const char* pcr_last_error(void);
+
+/* ---- tracing ------------------------------------------------------------ */
+/* enable != 0: every pipeline stage enqueued afterwards records a pair of
+ * CUDA events on its stream.  pcr_profile_read synchronises the recorded
+ * events and returns, per stage name (48-byte NUL-terminated slots of
+ * `names`), the summed milliseconds and kernel launches; *n_out receives the
+ * number of stages (entries beyond max_entries are counted, not written);
+ * reset != 0 clears the totals.  Not for use inside stream capture. */
+pcr_status pcr_profile_enable(int enable);
+pcr_status pcr_profile_read(int max_entries, char* names, double* ms, int64_t* launches, int* n_out,
+                            int reset);
+/* Kernels this library has launched since it was loaded (all threads). */
+int64_t pcr_launch_count(void);
 
 /* ---- test entry: encode given coefficients ---------------------------- */
 /* Encode one stream of n_pad values already in canonical padded order

@@ -93,6 +93,13 @@ for _name, _args in _sigs.items():
     fn = getattr(_lib, _name)
     fn.argtypes = _args
     fn.restype = C.c_int
+_lib.pcr_profile_enable.argtypes = [C.c_int]
+_lib.pcr_profile_enable.restype = C.c_int
+_lib.pcr_profile_read.argtypes = [C.c_int, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_int), C.c_int]
+_lib.pcr_profile_read.restype = C.c_int
+_lib.pcr_launch_count.argtypes = []
+_lib.pcr_launch_count.restype = C.c_int64
 _lib.pcr_free.argtypes = [_vp]
 _lib.pcr_free.restype = None
 _lib.pcr_buffer_free.argtypes = [_vp]
@@ -101,7 +108,8 @@ _lib.pcr_last_error.argtypes = []
 _lib.pcr_last_error.restype = C.c_char_p
 
 # exported symbols (checked by the CPU tests against include/pcr.h)
-EXPORTS = sorted(list(_sigs) + ["pcr_free", "pcr_buffer_free", "pcr_last_error"])
+EXPORTS = sorted(list(_sigs) + ["pcr_free", "pcr_buffer_free", "pcr_last_error", "pcr_profile_enable",
+                                "pcr_profile_read", "pcr_launch_count"])
 
 
 def _check(st):
@@ -357,6 +365,31 @@ def debug_encode(vals: torch.Tensor, value_kind: int, B: int, encoding: int, wan
                                  _stream_ptr(stream), planes.ctypes.data, signs.ctypes.data,
                                  scnt.ctypes.data, pnz.ctypes.data, pairs.ctypes.data, C.byref(vmax)))
     return dict(planes=planes, signs=signs, sign_counts=scnt, plane_nz=pnz, pairs=pairs, vmax=vmax.value)
+
+
+def profile_enable(on=True):
+    """Per-stage CUDA-event timing inside the library (tracing)."""
+    _check(_lib.pcr_profile_enable(int(on)))
+
+
+def profile_read(reset=True):
+    """{stage: (milliseconds, kernel launches)} since the last reset."""
+    cap = 64
+    names = C.create_string_buffer(48 * cap)
+    ms = (C.c_double * cap)()
+    ln = (C.c_int64 * cap)()
+    n = C.c_int()
+    _check(_lib.pcr_profile_read(cap, names, ms, ln, C.byref(n), int(reset)))
+    out = {}
+    for k in range(min(n.value, cap)):
+        nm = names.raw[48 * k:48 * (k + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (ms[k], ln[k])
+    return out
+
+
+def launch_count():
+    """Kernels launched by libpcr since it was loaded."""
+    return int(_lib.pcr_launch_count())
 
 
 def library_path():

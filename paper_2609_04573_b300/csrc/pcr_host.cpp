@@ -12,6 +12,7 @@
 #include <limits>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -42,6 +43,10 @@ void launch_encode(int vk, int w64, int pairs, const StreamD* d_streams, const W
                    cudaStream_t s);
 void launch_decode(int vk, int w64, const StreamD* d_streams, const WorkItem* d_items, int nitems,
                    cudaStream_t s);
+void launch_tile_interp(int vk, const TileArgs& a, cudaStream_t s);
+void launch_tile_decomp(int vk, const DecompArgs& a, cudaStream_t s);
+void launch_zero_pads(int vk, const LatD& lat, void* stage, cudaStream_t s);
+void launch_absmax(int vk, const void* v, int64_t n, unsigned long long* slot, cudaStream_t s);
 }  // namespace pcr
 
 using namespace pcr;
@@ -64,6 +69,75 @@ static pcr_status fail(pcr_status st, const std::string& msg) {
   } while (0)
 
 extern "C" const char* pcr_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// tracing: per-stage CUDA-event timing and kernel launch counts
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+struct ProfRec {
+  std::string name;
+  cudaEvent_t a, b;
+  long long launches;
+};
+std::vector<ProfRec> g_prof_recs;
+std::map<std::string, std::pair<double, long long>> g_prof_tot;
+
+struct Prof {
+  const char* name;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  long long c0;
+  Prof(const char* n, cudaStream_t st) : name(n), s(st), c0(launch_count()) {
+    if (g_prof_on && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
+  }
+  ~Prof() {
+    const long long dl = launch_count() - c0;
+    if (!a) return;
+    cudaEvent_t b;
+    if (cudaEventCreate(&b) != cudaSuccess) return;
+    cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof_recs.push_back({name, a, b, dl});
+  }
+};
+}  // namespace
+
+extern "C" pcr_status pcr_profile_enable(int enable) {
+  g_prof_on = enable != 0;
+  return PCR_OK;
+}
+
+extern "C" int64_t pcr_launch_count(void) { return launch_count(); }
+
+extern "C" pcr_status pcr_profile_read(int max_entries, char* names, double* ms, int64_t* launches, int* n_out,
+                                       int reset) {
+  if (!n_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  for (auto& r : g_prof_recs) {
+    float t = 0.0f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess) cudaEventElapsedTime(&t, r.a, r.b);
+    auto& acc = g_prof_tot[r.name];
+    acc.first += t;
+    acc.second += r.launches;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_prof_recs.clear();
+  int k = 0;
+  for (auto& kv : g_prof_tot) {
+    if (k < max_entries) {
+      if (names) std::snprintf(names + 48 * k, 48, "%s", kv.first.c_str());
+      if (ms) ms[k] = kv.second.first;
+      if (launches) launches[k] = kv.second.second;
+    }
+    k++;
+  }
+  *n_out = k;
+  if (reset) g_prof_tot.clear();
+  return PCR_OK;
+}
 
 // ---------------------------------------------------------------------------
 // memory
@@ -786,6 +860,114 @@ StreamD stream_desc(const pcr_handle* h, int i) {
   return s;
 }
 
+// tiled-kernel arguments of one level (grid = the level's s-grid)
+TileArgs level_args(const pcr_handle* h, int level, int retrieve, const void* src, void* dst) {
+  TileArgs a{};
+  const int64_t s = int64_t(1) << level;
+  for (int k = 0; k < 3; k++) a.m[k] = h->n3[k] > 1 ? count_from(h->n3[k], 0, s) : 1;
+  if (level == 0) {
+    a.stride[0] = h->n3[1] * h->n3[2];
+    a.stride[1] = h->n3[2];
+    a.stride[2] = 1;
+  } else {
+    int64_t nc[3];
+    for (int k = 0; k < 3; k++) nc[k] = h->n3[k] > 1 ? (h->n3[k] - 1) / 2 + 1 : 1;
+    const int64_t xs[3] = {nc[1] * nc[2], nc[2], 1};
+    for (int k = 0; k < 3; k++) a.stride[k] = (h->n3[k] > 1 ? s / 2 : 0) * xs[k];
+  }
+  a.d = (int)h->order.size();
+  for (int i = 0; i < 3; i++) a.order[i] = i < a.d ? h->order[i] : 0;
+  a.interp = h->sch.interp;
+  a.degree = h->sch.degree;
+  a.retrieve = retrieve;
+  a.src = src;
+  a.dst = dst;
+  return a;
+}
+
+TileRegion tile_region(const pcr_handle* h, const Lat& l, int level, int64_t row_pad, int64_t base, void* stage,
+                       unsigned long long* vmax) {
+  TileRegion r{};
+  const int64_t s = int64_t(1) << level;
+  for (int k = 0; k < 3; k++) {
+    if (h->n3[k] > 1) {
+      r.start[k] = l.start[k] / s;
+      r.step[k] = l.step[k] / s;
+    } else {
+      r.start[k] = 0;
+      r.step[k] = 1;
+    }
+    r.count[k] = l.count[k];
+  }
+  r.row_pad = row_pad;
+  r.base = base;
+  r.stage = stage;
+  r.vmax = vmax;
+  return r;
+}
+
+// region lattices of `level` with the stream staging that holds them
+void level_regions(const pcr_handle* h, int level, const std::vector<StreamD>& sds, TileArgs& a) {
+  const int d = (int)h->order.size();
+  for (size_t i = 0; i < h->geo.size(); i++) {
+    const SGeo& g = h->geo[i];
+    if (g.level != level || g.sub != 0) continue;
+    int64_t base = 0;
+    for (size_t k = 0; k < g.lats.size(); k++) {
+      const int r = g.region == 0 ? (int)k : g.region - 1;
+      if (r < d)
+        a.reg[r] = tile_region(h, g.lats[k], level, g.lats[k].row_pad(), base, sds[i].stage, sds[i].vmax);
+      base += g.lats[k].n_pad();
+    }
+  }
+}
+
+void zero_stream_pads(const pcr_handle* h, const StreamD& sd, int kind, cudaStream_t s) {
+  for (int k = 0; k < sd.nlat; k++)
+    if (sd.lat[k].row_pad > sd.lat[k].count[2]) launch_zero_pads(kind, sd.lat[k], sd.stage, s);
+}
+
+// sub-level lattices of a decomposed region in its compact coordinates
+void decomp_subs(const pcr_handle* h, int region, const std::vector<StreamD>& sds, DecompArgs& a) {
+  int u = -1, v = -1;
+  for (int ax = 0; ax < 3; ax++)
+    if (ax != h->decomp) (u < 0 ? u : v) = ax;
+  const Lat R = region_lat(h->n3, 0, h->order, region);
+  for (int k = 0; k < 3; k++) a.cnt[k] = R.count[k];
+  a.u = u;
+  a.v = v;
+  a.n = h->decomp;
+  Lat C;  // compact grid of the region
+  for (int k = 0; k < 3; k++) {
+    C.start[k] = 0;
+    C.step[k] = 1;
+    C.count[k] = R.count[k];
+  }
+  int slot = 0;
+  for (size_t i = 0; i < h->geo.size(); i++) {
+    const SGeo& g = h->geo[i];
+    if (g.level != 0 || g.region != region || g.sub == 0) continue;
+    const int sub = g.sub - 1;
+    int64_t base = 0;
+    for (int part = 0; part < 2; part++) {
+      if (kSub[sub][part][0] < 0) continue;
+      const int* p = kSub[sub][part];
+      const Lat L = sub_lat(C, u, v, p[0], p[1], p[2], p[3]);
+      DecompSub& ds = a.subs[slot++];
+      for (int k = 0; k < 3; k++) {
+        ds.start[k] = L.start[k];
+        ds.step[k] = L.step[k];
+        ds.count[k] = L.count[k];
+      }
+      ds.row_pad = L.row_pad();
+      ds.base = base;
+      ds.stage = sds[i].stage;
+      ds.vmax = sds[i].vmax;
+      base += L.n_pad();
+    }
+  }
+}
+
 void compute_tables(pcr_handle* h, int i, const std::vector<uint64_t>* pairs, bool psnr) {
   const SGeo& g = h->geo[i];
   const int B = h->B;
@@ -818,7 +1000,8 @@ void compute_tables(pcr_handle* h, int i, const std::vector<uint64_t>* pairs, bo
       else if (!nb) t.maxerr[b] = std::ldexp(unit, B - b);
       else {
         const int k = B - b;
-        const uint64_t dm = (k == 64 ? ~uint64_t(0) : ((uint64_t(1) << (k + 1)) - 1)) / 3;
+        const uint64_t full = k + 1 >= 64 ? ~uint64_t(0) : ((uint64_t(1) << (k + 1)) - 1);
+        const uint64_t dm = full / 3;   // largest |value| of k negabinary digits
         t.maxerr[b] = up_u64(dm + 1) * unit;
       }
     }
@@ -1145,12 +1328,18 @@ static pcr_status enqueue_refactor(pcr_handle* h, const void* d_field, cudaStrea
   int64_t* st_fix = (int64_t*)sc.get(fix_elems * 8);
   char* st_flt = (char*)sc.get(flt_elems * w);
   if (!st_fix || !st_flt) return fail(PCR_ERR_OOM, "staging allocation failed");
-  launch_minmax(h->vk, d_field, n, d_st, s);
+  {
+    Prof pf("stats", s);
+    launch_minmax(h->vk, d_field, n, d_st, s);
+  }
   int64_t* xc = nullptr;
   if (h->L >= 2) {
     xc = (int64_t*)sc.get((size_t)f.nc[0] * f.nc[1] * f.nc[2] * 8);
     if (!xc) return fail(PCR_ERR_OOM, "staging allocation failed");
-    launch_to_fixed(h->vk, d_field, f, d_st, xc, s);
+    {
+      Prof pf("to_fixed", s);
+      launch_to_fixed(h->vk, d_field, f, d_st, xc, s);
+    }
   }
   // region compact arrays for the decomposition
   std::vector<void*> comp(4, nullptr);
@@ -1167,41 +1356,55 @@ static pcr_status enqueue_refactor(pcr_handle* h, const void* d_field, cudaStrea
     sds[i].vmax = d_vmax + i;
     sds[i].pairs = d_pairs ? d_pairs + (size_t)i * h->B * h->B : nullptr;
     sds[i].stage = g.is_fix ? (void*)(st_fix + soff[i]) : (void*)(st_flt + soff[i] * w);
-    int64_t base = 0;
-    for (size_t k = 0; k < g.lats.size(); k++) {
-      const LatD ld = to_latd(g.lats[k], base);
-      base += g.lats[k].n_pad();
-      if (g.is_fix) {
-        launch_coef_fixed(f, g.level, g.level == h->L - 1, ld, xc, (int64_t*)sds[i].stage, sds[i].vmax, s);
-      } else if (h->L == 1) {
-        launch_raw_stage(h->vk, f, ld, d_field, sds[i].stage, sds[i].vmax, s);
-      } else if (g.sub == 0) {
-        launch_coef_l0(h->vk, f, ld, 0, d_field, (char*)sds[i].stage, sds[i].vmax, c0, s);
+  }
+  // coarsest level (raw) and the L = 1 case
+  {
+    const SGeo& g = h->geo[0];
+    const LatD ld = to_latd(g.lats[0], 0);
+    Prof pf("coarsest", s);
+    if (g.is_fix) launch_coef_fixed(f, g.level, 1, ld, xc, (int64_t*)sds[0].stage, sds[0].vmax, s);
+    else launch_raw_stage(h->vk, f, ld, d_field, sds[0].stage, sds[0].vmax, s);
+  }
+  // levels L-2 .. 1 in fixed point (Alg. 1 loop), level 0 in the field dtype
+  for (int level = h->L - 2; level >= 0; level--) {
+    TileArgs a = level_args(h, level, 0, level == 0 ? d_field : (const void*)xc, nullptr);
+    if (level == 0 && h->decomp >= 0) {
+      for (int r = 1; r <= f.d; r++) {
+        const Lat R = region_lat(h->n3, 0, h->order, r);
+        a.reg[r - 1] = tile_region(h, R, 0, R.count[2], 0, comp[r], nullptr);
       }
+    } else {
+      level_regions(h, level, sds, a);
+    }
+    {
+      Prof pf(level == 0 ? "interp_level0" : "interp_fixed_levels", s);
+      launch_tile_interp(level == 0 ? h->vk : VK_FIX, a, s);
     }
   }
+  {
+    Prof pf("zero_pads", s);
+    for (int i = 1; i < ns; i++)
+      if (h->geo[i].sub == 0) zero_stream_pads(h, sds[i], h->geo[i].is_fix ? VK_FIX : h->vk, s);
+  }
   if (h->decomp >= 0) {
-    int u = -1, v = -1;
-    for (int a = 0; a < 3; a++)
-      if (a != h->decomp) (u < 0 ? u : v) = a;
     for (int r = 1; r <= f.d; r++) {
       const Lat R = region_lat(h->n3, 0, h->order, r);
-      launch_coef_l0(h->vk, f, to_latd(R, 0), 1, d_field, comp[r], nullptr, c0, s);
-    }
-    for (int i = 0; i < ns; i++) {
-      const SGeo& g = h->geo[i];
-      if (g.sub == 0) continue;
-      DecompGeo dg;
-      dg.region = to_latd(region_lat(h->n3, 0, h->order, g.region), 0);
-      dg.u = u;
-      dg.v = v;
-      dg.sub = g.sub;
-      int64_t base = 0;
-      for (auto& l : g.lats) {
-        launch_decompose(h->vk, dg, to_latd(l, base), comp[g.region], sds[i].stage, sds[i].vmax, s);
-        base += l.n_pad();
+      {
+        Prof pf("absmax", s);
+        launch_absmax(h->vk, comp[r], R.n_real(), c0, s);
+      }
+      DecompArgs da{};
+      decomp_subs(h, r, sds, da);
+      da.retrieve = 0;
+      da.comp = comp[r];
+      {
+        Prof pf(da.retrieve ? "recompose" : "decompose", s);
+        launch_tile_decomp(h->vk, da, s);
       }
     }
+    Prof pf("zero_pads", s);
+    for (int i = 1; i < ns; i++)
+      if (h->geo[i].sub != 0) zero_stream_pads(h, sds[i], h->vk, s);
   }
   return PCR_OK;
 }
@@ -1359,7 +1562,10 @@ extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, con
       CUDA_TRY(cudaMemcpyAsync(d_items + off, items[a][b].data(), items[a][b].size() * sizeof(WorkItem),
                                cudaMemcpyHostToDevice, s));
       const int vk = b ? VK_FIX : (a ? VK_F64 : VK_F32);
-      launch_encode(vk, a, pairs_mode[a][b] > 0, d_sd, d_items + off, (int)items[a][b].size(), s);
+      {
+        Prof pf(b ? "encode_fixed" : "encode_float", s);
+        launch_encode(vk, a, pairs_mode[a][b] > 0, d_sd, d_items + off, (int)items[a][b].size(), s);
+      }
       off += items[a][b].size();
     }
   CUDA_TRY(cudaGetLastError());
@@ -1479,66 +1685,62 @@ static pcr_status enqueue_reconstruct(const pcr_handle* h, const std::vector<Str
                                       cudaStream_t s, Scratch& sc) {
   const FieldD f = field_desc(h);
   const size_t w = vsize(h->vk);
-  const int ns = (int)h->geo.size();
   if (h->L == 1) {
-    launch_copy_raw(h->vk, f, to_latd(h->geo[0].lats[0], 0), sds[0].stage, d_out, s);
+    {
+      Prof pf("copy_raw", s);
+      launch_copy_raw(h->vk, f, to_latd(h->geo[0].lats[0], 0), sds[0].stage, d_out, s);
+    }
     return PCR_OK;
   }
   // level-0 recomposition (Alg. 2)
   std::vector<void*> comp(4, nullptr);
   if (h->decomp >= 0) {
-    int u = -1, v = -1;
-    for (int a = 0; a < 3; a++)
-      if (a != h->decomp) (u < 0 ? u : v) = a;
     for (int r = 1; r <= f.d; r++) {
       const Lat R = region_lat(h->n3, 0, h->order, r);
       comp[r] = sc.get((size_t)R.n_real() * w);
       if (!comp[r]) return fail(PCR_ERR_OOM, "staging allocation failed");
-    }
-    for (int i = 0; i < ns; i++) {  // stream order: S1, S2, S3 of each region
-      const SGeo& g = h->geo[i];
-      if (g.sub == 0) continue;
-      DecompGeo dg;
-      dg.region = to_latd(region_lat(h->n3, 0, h->order, g.region), 0);
-      dg.u = u;
-      dg.v = v;
-      dg.sub = g.sub;
-      int64_t base = 0;
-      for (auto& l : g.lats) {
-        launch_recompose(h->vk, dg, to_latd(l, base), sds[i].stage, comp[g.region], s);
-        base += l.n_pad();
+      DecompArgs da{};
+      decomp_subs(h, r, sds, da);
+      da.retrieve = 1;
+      da.comp = comp[r];
+      {
+        Prof pf(da.retrieve ? "recompose" : "decompose", s);
+        launch_tile_decomp(h->vk, da, s);
       }
     }
   }
-  // coarse levels in fixed point
+  // coarse levels in fixed point: raw coarsest, then L-2 .. 1
   int64_t* xc = (int64_t*)sc.get((size_t)f.nc[0] * f.nc[1] * f.nc[2] * 8);
   if (!xc) return fail(PCR_ERR_OOM, "staging allocation failed");
-  for (int i = 0; i < ns; i++) {
-    const SGeo& g = h->geo[i];
-    if (!g.is_fix) continue;
-    int64_t base = 0;
-    for (auto& l : g.lats) {
-      launch_recon_fixed(f, g.level, g.level == h->L - 1, to_latd(l, base), (const int64_t*)sds[i].stage, xc, s);
-      base += l.n_pad();
+  {
+    Prof pf("recon_coarsest", s);
+    launch_recon_fixed(f, h->L - 1, 1, to_latd(h->geo[0].lats[0], 0), (const int64_t*)sds[0].stage, xc, s);
+  }
+  for (int level = h->L - 2; level >= 1; level--) {
+    TileArgs a = level_args(h, level, 1, xc, xc);
+    level_regions(h, level, sds, a);
+    {
+      Prof pf("recon_fixed_levels", s);
+      launch_tile_interp(VK_FIX, a, s);
     }
   }
-  launch_coarse_out(h->vk, f, xc, std::ldexp(1.0, h->G - kFixBits), d_out, s);
+  {
+    Prof pf("coarse_out", s);
+    launch_coarse_out(h->vk, f, xc, std::ldexp(1.0, h->G - kFixBits), d_out, s);
+  }
   // level 0
+  TileArgs a = level_args(h, 0, 1, d_out, d_out);
   if (h->decomp >= 0) {
     for (int r = 1; r <= f.d; r++) {
       const Lat R = region_lat(h->n3, 0, h->order, r);
-      launch_recon_l0(h->vk, f, to_latd(R, 0), 1, comp[r], d_out, s);
+      a.reg[r - 1] = tile_region(h, R, 0, R.count[2], 0, comp[r], nullptr);
     }
   } else {
-    for (int i = 0; i < ns; i++) {
-      const SGeo& g = h->geo[i];
-      if (g.level != 0) continue;
-      int64_t base = 0;
-      for (auto& l : g.lats) {
-        launch_recon_l0(h->vk, f, to_latd(l, base), 0, sds[i].stage, d_out, s);
-        base += l.n_pad();
-      }
-    }
+    level_regions(h, 0, sds, a);
+  }
+  {
+    Prof pf("recon_level0", s);
+    launch_tile_interp(h->vk, a, s);
   }
   return PCR_OK;
 }
@@ -1579,7 +1781,10 @@ extern "C" pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, con
       CUDA_TRY(cudaMemcpyAsync(d_items + off, items[a][b].data(), items[a][b].size() * sizeof(WorkItem),
                                cudaMemcpyHostToDevice, s));
       const int vk = b ? VK_FIX : (a ? VK_F64 : VK_F32);
-      launch_decode(vk, a, d_sd, d_items + off, (int)items[a][b].size(), s);
+      {
+        Prof pf(b ? "decode_fixed" : "decode_float", s);
+        launch_decode(vk, a, d_sd, d_items + off, (int)items[a][b].size(), s);
+      }
       off += items[a][b].size();
     }
   for (int k = 0; k < n; k++) {

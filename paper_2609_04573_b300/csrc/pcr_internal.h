@@ -62,6 +62,48 @@ struct DecompGeo {
   int sub;
 };
 
+// one region of a level in level-grid coordinates, with the staging it
+// writes (refactor: coefficients) or reads (retrieve: decoded coefficients)
+struct TileRegion {
+  int64_t start[3], step[3], count[3];
+  int64_t row_pad;     // padded row length, or count[2] for compact arrays
+  int64_t base;        // element offset of the region's lattice in `stage`
+  void* stage;
+  unsigned long long* vmax;   // refactor: stream maximum slot (may be null)
+};
+
+// arguments of the tiled interpolation kernel (one level, all regions)
+struct TileArgs {
+  int64_t m[3];        // level-grid lengths (1 along an inactive axis)
+  int64_t stride[3];   // element strides of src / dst per level-grid step
+  int64_t ntiles[3];
+  int d;
+  int order[3];
+  int interp, degree;
+  int retrieve;
+  const void* src;     // refactor: field (level 0) or fixed-point 2-grid copy
+  void* dst;           // retrieve: same view as src
+  TileRegion reg[3];
+};
+
+// one sub-level lattice part of a decomposed region, in the region's compact
+// coordinates, with its padded stream staging
+struct DecompSub {
+  int64_t start[3], step[3], count[3];
+  int64_t row_pad, base;
+  void* stage;
+  unsigned long long* vmax;
+};
+
+struct DecompArgs {
+  int64_t cnt[3];      // compact region dims
+  int64_t ntiles[3];
+  int u, v, n;         // in-slice axes and slice normal
+  int retrieve;        // 0 decompose, 1 recompose
+  void* comp;          // region compact array (c, or recomposed c_hat)
+  DecompSub subs[5];   // S1, S2a, S2b, S3a, S3b
+};
+
 struct WorkItem {
   int stream;          // index into the StreamD array of the launch
   int seg;
@@ -74,5 +116,10 @@ struct FieldStats {
   int G;                                   // max|x| < 2^G
   int bad;                                 // non-finite input seen
 };
+
+// kernels launched by this library since load (tracing); every launcher
+// increments it right before its <<<...>>>
+void count_launch();
+long long launch_count();
 
 }  // namespace pcr

@@ -7,11 +7,16 @@
 //   levels >= 1 in exact 64-bit fixed point (quantum 2^(G-40)).
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <atomic>
 #include <type_traits>
 
 #include "pcr_internal.h"
 
 namespace pcr {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(); }
 
 #define FULL 0xFFFFFFFFu
 
@@ -202,12 +207,15 @@ __device__ __forceinline__ int64_t lat_padded_index(const LatD& l, const int64_t
 // --------------------------------------------------------------------------
 template <typename T>
 __global__ void k_minmax(const T* __restrict__ x, int64_t n, FieldStats* st) {
+  __shared__ unsigned long long rlo[32], rhi[32];
+  __shared__ int rbad;
+  if (threadIdx.x == 0) rbad = 0;
   T lo = x[0], hi = x[0];
   int bad = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const T v = x[i];
-    if (!isfinite(v)) bad = 1;
+    bad |= !isfinite(v);
     lo = v < lo ? v : lo;
     hi = v > hi ? v : hi;
   }
@@ -219,10 +227,28 @@ __global__ void k_minmax(const T* __restrict__ x, int64_t n, FieldStats* st) {
     khi = b > khi ? b : khi;
   }
   bad = __any_sync(FULL, bad);
+  __syncthreads();
   if ((threadIdx.x & 31) == 0) {
-    atomicMin(&st->xmin_key, klo);
-    atomicMax(&st->xmax_key, khi);
-    if (bad) st->bad = 1;
+    rlo[threadIdx.x >> 5] = klo;
+    rhi[threadIdx.x >> 5] = khi;
+    if (bad) rbad = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x >> 5;
+    klo = threadIdx.x < nw ? rlo[threadIdx.x] : ~0ull;
+    khi = threadIdx.x < nw ? rhi[threadIdx.x] : 0ull;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      unsigned long long a = __shfl_xor_sync(FULL, klo, o), b = __shfl_xor_sync(FULL, khi, o);
+      klo = a < klo ? a : klo;
+      khi = b > khi ? b : khi;
+    }
+    if (threadIdx.x == 0) {
+      atomicMin(&st->xmin_key, klo);
+      atomicMax(&st->xmax_key, khi);
+      if (rbad) st->bad = 1;
+    }
   }
 }
 
@@ -563,6 +589,16 @@ template <typename VT, int W> struct Code;  // W-bit code of one value
 template <int W>
 using code_t = typename std::conditional<W == 32, uint32_t, uint64_t>::type;
 
+// exact power-of-two scaling: x * 2^k through one multiply when 2^k is a
+// normal number (then the product is exact whenever it is >= 1 or a normal
+// number), else through ldexp
+__device__ __forceinline__ float scale2f(float x, int k) {
+  return (k >= -126 && k <= 127) ? __fmul_rn(x, __int_as_float((k + 127) << 23)) : ldexpf(x, k);
+}
+__device__ __forceinline__ double scale2d(double x, int k) {
+  return (k >= -1022 && k <= 1023) ? __dmul_rn(x, __longlong_as_double((long long)(k + 1023) << 52)) : ldexp(x, k);
+}
+
 template <typename VT, int W>
 __device__ __forceinline__ code_t<W> quantize(VT v, const StreamD& s, const QParams& qp, bool& neg) {
   using C = code_t<W>;
@@ -577,13 +613,13 @@ __device__ __forceinline__ code_t<W> quantize(VT v, const StreamD& s, const QPar
     return (C)(((C)sv + M) ^ M);
   } else if constexpr (std::is_same<VT, float>::value) {
     neg = v < 0.0f;
-    if (s.enc == 1) return (C)__float2uint_rz(ldexpf(fabsf(v), B - qp.E));
-    const int sv = __float2int_rz(ldexpf(v, B - 3 - qp.E));
+    if (s.enc == 1) return (C)__float2uint_rz(scale2f(fabsf(v), B - qp.E));
+    const int sv = __float2int_rz(scale2f(v, B - 3 - qp.E));
     return (C)(((C)(int64_t)sv + M) ^ M);
   } else {
     neg = v < 0.0;
-    if (s.enc == 1) return (C)__double2ull_rz(ldexp(fabs(v), B - qp.E));
-    const long long sv = __double2ll_rz(ldexp(v, B - 3 - qp.E));
+    if (s.enc == 1) return (C)__double2ull_rz(scale2d(fabs(v), B - qp.E));
+    const long long sv = __double2ll_rz(scale2d(v, B - 3 - qp.E));
     return (C)(((C)sv + M) ^ M);
   }
 }
@@ -596,10 +632,10 @@ __device__ __forceinline__ VT dequantize(code_t<W> q, bool neg, const StreamD& s
       const int64_t mag = (int64_t)((uint64_t)q << s.sh);
       return neg ? -mag : mag;
     } else if constexpr (std::is_same<VT, float>::value) {
-      const float mag = ldexpf(__uint2float_rn((uint32_t)q), s.E - B);
+      const float mag = scale2f(__uint2float_rn((uint32_t)q), s.E - B);
       return neg ? -mag : mag;
     } else {
-      const double mag = ldexp(__ull2double_rn((unsigned long long)q), s.E - B);
+      const double mag = scale2d(__ull2double_rn((unsigned long long)q), s.E - B);
       return neg ? -mag : mag;
     }
   }
@@ -610,9 +646,9 @@ __device__ __forceinline__ VT dequantize(code_t<W> q, bool neg, const StreamD& s
   if constexpr (std::is_same<VT, int64_t>::value) {
     return (int64_t)((uint64_t)val << s.sh);
   } else if constexpr (std::is_same<VT, float>::value) {
-    return ldexpf(__ll2float_rn(val), s.E - B + 3);
+    return scale2f(__ll2float_rn(val), s.E - B + 3);
   } else {
-    return ldexp(__ll2double_rn(val), s.E - B + 3);
+    return scale2d(__ll2double_rn(val), s.E - B + 3);
   }
 }
 
@@ -625,11 +661,36 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kWordsPerWarp = kSegWords / kWarps;   // 16
 
+// most significant plane of code q (B for q == 0)
+template <int W>
+__device__ __forceinline__ int msb_plane(code_t<W> q, int B) {
+  if (!q) return B;
+  return W == 32 ? __clz((uint32_t)q << (32 - B)) : __clzll((long long)((uint64_t)q << (64 - B)));
+}
+
+// Generic-encoding sign bookkeeping for one word: the element's plane p and
+// its rank among this warp's earlier elements of plane p (running per-warp
+// counters in shared memory; match.any groups lanes of equal plane).
+__device__ __forceinline__ uint32_t sign_record(int p, bool neg, int B, uint32_t* wc, int lane) {
+  const unsigned grp = __match_any_sync(FULL, p);
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t rec = 0xFFFFFFFFu;
+  uint32_t base = 0;
+  if (p < B) base = wc[p];
+  __syncwarp();
+  if (p < B) {
+    rec = (uint32_t)p | ((base + __popc(grp & lt)) << 7) | ((uint32_t)neg << 20);
+    if ((grp & lt) == 0) wc[p] = base + __popc(grp);
+  }
+  __syncwarp();
+  return rec;
+}
+
 // Encode one (stream, segment) per CTA.  W = 32 (FP32 fields) or 64 (FP64).
 template <typename VT, int W, bool PAIRS>
 __global__ void __launch_bounds__(kThreads) k_encode(const StreamD* __restrict__ streams,
                                                      const WorkItem* __restrict__ items) {
-  constexpr int NP = W;                       // max planes held per lane pair
+  constexpr int NP = W;
   __shared__ uint32_t pbuf[NP][kSegWords + 1];
   __shared__ uint32_t sbuf[kSegWords + 64];
   __shared__ uint32_t wcnt[kWarps][NP];
@@ -650,12 +711,13 @@ __global__ void __launch_bounds__(kThreads) k_encode(const StreamD* __restrict__
 
   for (int i = threadIdx.x; i < kSegWords + 64; i += kThreads) sbuf[i] = 0;
   if (threadIdx.x < NP) pnz[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < kWarps * NP; i += kThreads) (&wcnt[0][0])[i] = 0;
   if (PAIRS)
     for (int i = threadIdx.x; i < NP * (NP + 1) / 2; i += kThreads) pairs_s[i] = 0;
   __syncthreads();
 
   uint32_t rec[kWordsPerWarp];
-  uint32_t run_lo = 0, run_hi = 0, nz_lo = 0, nz_hi = 0;
+  uint32_t nz_lo = 0, nz_hi = 0;
   uint32_t acc_ll[PAIRS ? 17 : 1], acc_hh[PAIRS && W == 64 ? 17 : 1], acc_lh[PAIRS && W == 64 ? 32 : 1];
   if (PAIRS) {
 #pragma unroll
@@ -667,7 +729,6 @@ __global__ void __launch_bounds__(kThreads) k_encode(const StreamD* __restrict__
       for (int t = 0; t < 32; t++) acc_lh[t] = 0;
     }
   }
-  const uint32_t lt = (1u << lane) - 1u;
 
 #pragma unroll
   for (int jj = 0; jj < kWordsPerWarp; jj++) {
@@ -675,9 +736,9 @@ __global__ void __launch_bounds__(kThreads) k_encode(const StreamD* __restrict__
     const int j = warp * kWordsPerWarp + jj;
     if (j >= nw) continue;
     const VT v = vals[e0 + (int64_t)j * 32 + lane];
-    bool neg;
-    code_t<W> q = qp.zero ? code_t<W>(0) : quantize<VT, W>(v, s, qp, neg);
-    if (qp.zero) neg = false;
+    bool neg = false;
+    code_t<W> q = 0;
+    if (!qp.zero) q = quantize<VT, W>(v, s, qp, neg);
     uint32_t dlo, dhi = 0;
     if (W == 32) {
       dlo = transpose32(__brev((uint32_t)q << (32 - B)), lane);
@@ -686,7 +747,6 @@ __global__ void __launch_bounds__(kThreads) k_encode(const StreamD* __restrict__
       dlo = transpose32((uint32_t)r, lane);
       dhi = transpose32((uint32_t)(r >> 32), lane);
     }
-    // stored planes (negabinary: XOR with the previous digit plane)
     uint32_t slo = dlo, shi = dhi;
     if (!generic) {
       const uint32_t up = __shfl_up_sync(FULL, dlo, 1);
@@ -701,43 +761,7 @@ __global__ void __launch_bounds__(kThreads) k_encode(const StreamD* __restrict__
     if (W == 64 && lane + 32 < B) pbuf[lane + 32][j] = shi;
     nz_lo += slo != 0;
     nz_hi += shi != 0;
-    if (generic) {
-      // first-significance masks: digit plane & ~(OR of earlier planes)
-      uint32_t inc = dlo;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(FULL, inc, o);
-        if (lane >= o) inc |= t;
-      }
-      uint32_t exc = __shfl_up_sync(FULL, inc, 1);
-      if (lane == 0) exc = 0;
-      const uint32_t nlo = dlo & ~exc;
-      uint32_t nhi = 0;
-      if (W == 64) {
-        const uint32_t tot = __shfl_sync(FULL, inc, 31);
-        uint32_t inh = dhi;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t t = __shfl_up_sync(FULL, inh, o);
-          if (lane >= o) inh |= t;
-        }
-        inh |= tot;
-        uint32_t exh = __shfl_up_sync(FULL, inh, 1);
-        if (lane == 0) exh = tot;
-        nhi = dhi & ~exh;
-      }
-      // this element's plane and rank among the word's elements of that plane
-      int p = B;
-      if (q) p = (W == 32) ? __clz((uint32_t)q << (32 - B)) : __clzll((long long)((uint64_t)q << (64 - B)));
-      const int pl = p & 31;
-      const uint32_t nml = __shfl_sync(FULL, nlo, pl), nmh = __shfl_sync(FULL, nhi, pl);
-      const uint32_t bl = __shfl_sync(FULL, run_lo, pl), bh = __shfl_sync(FULL, run_hi, pl);
-      const uint32_t nm = p < 32 ? nml : nmh;
-      const uint32_t base = p < 32 ? bl : bh;
-      if (p < B) rec[jj] = (uint32_t)p | ((base + __popc(nm & lt)) << 7) | ((uint32_t)neg << 20);
-      run_lo += __popc(nlo);
-      run_hi += __popc(nhi);
-    }
+    if (generic) rec[jj] = sign_record(msb_plane<W>(q, B), neg, B, wcnt[warp], lane);
     if (PAIRS) {
 #pragma unroll
       for (int t = 0; t < 17; t++) {
@@ -758,26 +782,15 @@ __global__ void __launch_bounds__(kThreads) k_encode(const StreamD* __restrict__
       }
     }
   }
-  // plane nonzero-word counts
   if (lane < B && nz_lo) atomicAdd(&pnz[lane], nz_lo);
   if (W == 64 && lane + 32 < B && nz_hi) atomicAdd(&pnz[lane + 32], nz_hi);
-  if (generic) {
-    wcnt[warp][lane] = run_lo;
-    if (W == 64) wcnt[warp][lane + 32] = run_hi;
-  }
   if (PAIRS) {
-    // pair (a, b) counts of digit planes, plane index a = lane (+32 for hi)
 #pragma unroll
     for (int t = 0; t < 17; t++) {
       const int b = (lane + t) & 31;
-      if ((t < 16 || lane < 16) && acc_ll[t]) {
-        const int a0 = min(lane, b), b0 = max(lane, b);
-        atomicAdd(&pairs_s[tri<NP>(a0, b0)], acc_ll[t]);
-      }
-      if (W == 64 && (t < 16 || lane < 16) && acc_hh[t]) {
-        const int a0 = min(lane, b) + 32, b0 = max(lane, b) + 32;
-        atomicAdd(&pairs_s[tri<NP>(a0, b0)], acc_hh[t]);
-      }
+      if ((t < 16 || lane < 16) && acc_ll[t]) atomicAdd(&pairs_s[tri<NP>(min(lane, b), max(lane, b))], acc_ll[t]);
+      if (W == 64 && (t < 16 || lane < 16) && acc_hh[t])
+        atomicAdd(&pairs_s[tri<NP>(min(lane, b) + 32, max(lane, b) + 32)], acc_hh[t]);
     }
     if (W == 64) {
 #pragma unroll
@@ -823,9 +836,14 @@ __global__ void __launch_bounds__(kThreads) k_encode(const StreamD* __restrict__
   }
   // plane words: coalesced per plane
   const int64_t w0 = (int64_t)it.seg * kSegWords;
-  for (int i = threadIdx.x; i < B * nw; i += kThreads) {
-    const int k = i / nw, j = i - k * nw;
-    s.planes[(int64_t)k * s.words + w0 + j] = pbuf[k][j];
+  if (nw == kSegWords) {
+    for (int i = threadIdx.x; i < B * kSegWords; i += kThreads)
+      s.planes[(int64_t)(i >> 7) * s.words + w0 + (i & 127)] = pbuf[i >> 7][i & 127];
+  } else {
+    for (int i = threadIdx.x; i < B * nw; i += kThreads) {
+      const int k = i / nw, j = i - k * nw;
+      s.planes[(int64_t)k * s.words + w0 + j] = pbuf[k][j];
+    }
   }
   if (threadIdx.x < B && pnz[threadIdx.x]) atomicAdd(&s.plane_nz[threadIdx.x], pnz[threadIdx.x]);
   if (PAIRS) {
@@ -858,10 +876,18 @@ __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__
   const int64_t w0 = (int64_t)it.seg * kSegWords;
   VT* out = (VT*)s.stage;
 
-  for (int i = threadIdx.x; i < b * nw; i += kThreads) {
-    const int k = i / nw, j = i - k * nw;
-    pbuf[k][j] = s.plane_nz[k] ? s.planes[(int64_t)k * s.words + w0 + j] : 0u;
+  if (nw == kSegWords) {
+    for (int i = threadIdx.x; i < b * kSegWords; i += kThreads) {
+      const int k = i >> 7, j = i & 127;
+      pbuf[k][j] = s.plane_nz[k] ? s.planes[(int64_t)k * s.words + w0 + j] : 0u;
+    }
+  } else {
+    for (int i = threadIdx.x; i < b * nw; i += kThreads) {
+      const int k = i / nw, j = i - k * nw;
+      pbuf[k][j] = s.plane_nz[k] ? s.planes[(int64_t)k * s.words + w0 + j] : 0u;
+    }
   }
+  for (int i = threadIdx.x; i < kWarps * NP; i += kThreads) (&wcnt[0][0])[i] = 0;
   if (generic) {
     if (threadIdx.x == 0) {
       uint32_t o = 0;
@@ -877,7 +903,14 @@ __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__
   }
   __syncthreads();
 
-  auto load_digits = [&](int j, uint32_t& dlo, uint32_t& dhi) {
+  code_t<W> qs[kWordsPerWarp];
+  uint32_t rec[kWordsPerWarp];
+#pragma unroll
+  for (int jj = 0; jj < kWordsPerWarp; jj++) {
+    const int j = warp * kWordsPerWarp + jj;
+    qs[jj] = 0;
+    rec[jj] = 0xFFFFFFFFu;
+    if (j >= nw) continue;
     uint32_t xl = lane < b ? pbuf[lane][j] : 0u;
     uint32_t xh = (W == 64 && lane + 32 < b) ? pbuf[lane + 32][j] : 0u;
     if (!generic) {
@@ -898,48 +931,17 @@ __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__
       if (lane >= b) xl = 0;
       if (lane + 32 >= b) xh = 0;
     }
-    dlo = xl;
-    dhi = xh;
-  };
-  auto new_masks = [&](uint32_t dlo, uint32_t dhi, uint32_t& nlo, uint32_t& nhi) {
-    uint32_t inc = dlo;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(FULL, inc, o);
-      if (lane >= o) inc |= t;
+    code_t<W> q;
+    if (W == 32) {
+      q = (code_t<W>)(__brev(transpose32(xl, lane)) >> (32 - B));
+    } else {
+      const uint64_t lo = transpose32(xl, lane), hi = transpose32(xh, lane);
+      q = (code_t<W>)(__brevll((unsigned long long)(lo | (hi << 32))) >> (64 - B));
     }
-    uint32_t exc = __shfl_up_sync(FULL, inc, 1);
-    if (lane == 0) exc = 0;
-    nlo = dlo & ~exc;
-    nhi = 0;
-    if (W == 64) {
-      const uint32_t tot = __shfl_sync(FULL, inc, 31);
-      uint32_t inh = dhi;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(FULL, inh, o);
-        if (lane >= o) inh |= t;
-      }
-      inh |= tot;
-      uint32_t exh = __shfl_up_sync(FULL, inh, 1);
-      if (lane == 0) exh = tot;
-      nhi = dhi & ~exh;
-    }
-  };
-
+    qs[jj] = q;
+    if (generic) rec[jj] = sign_record(msb_plane<W>(q, B), false, B, wcnt[warp], lane);
+  }
   if (generic) {
-    uint32_t run_lo = 0, run_hi = 0;
-    for (int jj = 0; jj < kWordsPerWarp; jj++) {
-      const int j = warp * kWordsPerWarp + jj;
-      if (j >= nw) break;
-      uint32_t dlo, dhi, nlo, nhi;
-      load_digits(j, dlo, dhi);
-      new_masks(dlo, dhi, nlo, nhi);
-      run_lo += __popc(nlo);
-      run_hi += __popc(nhi);
-    }
-    wcnt[warp][lane] = run_lo;
-    if (W == 64) wcnt[warp][lane + 32] = run_hi;
     __syncthreads();
     if (threadIdx.x < NP) {
       uint32_t acc = 0;
@@ -950,39 +952,18 @@ __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__
     }
     __syncthreads();
   }
-  const uint32_t lt = (1u << lane) - 1u;
-  uint32_t run_lo = 0, run_hi = 0;
+#pragma unroll
   for (int jj = 0; jj < kWordsPerWarp; jj++) {
     const int j = warp * kWordsPerWarp + jj;
-    if (j >= nw) break;
-    uint32_t dlo, dhi;
-    load_digits(j, dlo, dhi);
-    code_t<W> q;
-    if (W == 32) {
-      q = (code_t<W>)(__brev(transpose32(dlo, lane)) >> (32 - B));
-    } else {
-      const uint64_t lo = transpose32(dlo, lane), hi = transpose32(dhi, lane);
-      q = (code_t<W>)(__brevll((unsigned long long)(lo | (hi << 32))) >> (64 - B));
-    }
+    if (j >= nw) continue;
     bool neg = false;
-    if (generic) {
-      uint32_t nlo, nhi;
-      new_masks(dlo, dhi, nlo, nhi);
-      int p = B;
-      if (q) p = (W == 32) ? __clz((uint32_t)q << (32 - B)) : __clzll((long long)((uint64_t)q << (64 - B)));
-      const int pl = p & 31;
-      const uint32_t nml = __shfl_sync(FULL, nlo, pl), nmh = __shfl_sync(FULL, nhi, pl);
-      const uint32_t bl = __shfl_sync(FULL, run_lo, pl), bh = __shfl_sync(FULL, run_hi, pl);
-      if (p < B) {
-        const uint32_t nm = p < 32 ? nml : nmh;
-        const uint32_t base = p < 32 ? bl : bh;
-        const uint32_t bit = poff[p] * 32 + woff[warp][p] + base + __popc(nm & lt);
-        neg = (sbuf[bit >> 5] >> (bit & 31)) & 1u;
-      }
-      run_lo += __popc(nlo);
-      run_hi += __popc(nhi);
+    const uint32_t r = rec[jj];
+    if (generic && r != 0xFFFFFFFFu) {
+      const int p = r & 127;
+      const uint32_t bit = poff[p] * 32 + woff[warp][p] + ((r >> 7) & 8191);
+      neg = (sbuf[bit >> 5] >> (bit & 31)) & 1u;
     }
-    out[e0 + (int64_t)j * 32 + lane] = dequantize<VT, W>(q, neg, s);
+    out[e0 + (int64_t)j * 32 + lane] = dequantize<VT, W>(qs[jj], neg, s);
   }
 }
 
@@ -996,13 +977,18 @@ static int grid_for(int64_t n, int threads = 256) {
 }
 
 void launch_minmax(int vk, const void* x, int64_t n, FieldStats* st, cudaStream_t s) {
-  if (vk == VK_F32) k_minmax<float><<<grid_for(n), 256, 0, s>>>((const float*)x, n, st);
-  else k_minmax<double><<<grid_for(n), 256, 0, s>>>((const double*)x, n, st);
+  count_launch();
+  count_launch();
+  int g = grid_for(n, 512);
+  if (g > 148 * 4) g = 148 * 4;
+  if (vk == VK_F32) k_minmax<float><<<g, 512, 0, s>>>((const float*)x, n, st);
+  else k_minmax<double><<<g, 512, 0, s>>>((const double*)x, n, st);
   k_stats_finalize<<<1, 1, 0, s>>>(st);
 }
 
 void launch_to_fixed(int vk, const void* x, const FieldD& f, const FieldStats* st, int64_t* xc,
                      cudaStream_t s) {
+  count_launch();
   const int64_t n = f.nc[0] * f.nc[1] * f.nc[2];
   if (vk == VK_F32) k_to_fixed<float><<<grid_for(n), 256, 0, s>>>((const float*)x, f, st, xc);
   else k_to_fixed<double><<<grid_for(n), 256, 0, s>>>((const double*)x, f, st, xc);
@@ -1012,6 +998,7 @@ void launch_coef_fixed(const FieldD& f, int level, int raw, const LatD& lat, con
                        int64_t* out, unsigned long long* vmax, cudaStream_t s) {
   const int64_t n = lat.count[0] * lat.count[1] * lat.row_pad;
   if (n == 0) return;
+  count_launch();
   k_coef_fixed<<<grid_for(n), 256, 0, s>>>(f, level, raw, lat, xc, out, vmax);
 }
 
@@ -1019,6 +1006,7 @@ void launch_coef_l0(int vk, const FieldD& f, const LatD& lat, int compact, const
                     unsigned long long* vmax, unsigned long long* c0, cudaStream_t s) {
   const int64_t n = lat.count[0] * lat.count[1] * (compact ? lat.count[2] : lat.row_pad);
   if (n == 0) return;
+  count_launch();
   if (vk == VK_F32)
     k_coef_l0<float><<<grid_for(n), 256, 0, s>>>(f, lat, compact, (const float*)x, (float*)out, vmax, c0);
   else
@@ -1027,6 +1015,7 @@ void launch_coef_l0(int vk, const FieldD& f, const LatD& lat, int compact, const
 
 void launch_raw_stage(int vk, const FieldD& f, const LatD& lat, const void* x, void* out,
                       unsigned long long* vmax, cudaStream_t s) {
+  count_launch();
   const int64_t n = lat.count[0] * lat.count[1] * lat.row_pad;
   if (vk == VK_F32) k_raw_stage<float><<<grid_for(n), 256, 0, s>>>(f, lat, (const float*)x, (float*)out, vmax);
   else k_raw_stage<double><<<grid_for(n), 256, 0, s>>>(f, lat, (const double*)x, (double*)out, vmax);
@@ -1036,6 +1025,7 @@ void launch_decompose(int vk, const DecompGeo& dg, const LatD& sl, const void* c
                       unsigned long long* vmax, cudaStream_t s) {
   const int64_t n = sl.count[0] * sl.count[1] * sl.row_pad;
   if (n == 0) return;
+  count_launch();
   if (vk == VK_F32)
     k_decompose<float><<<grid_for(n), 256, 0, s>>>(dg, sl, (const float*)comp, (float*)out, vmax);
   else
@@ -1046,6 +1036,7 @@ void launch_recompose(int vk, const DecompGeo& dg, const LatD& sl, const void* d
                       cudaStream_t s) {
   const int64_t n = sl.count[0] * sl.count[1] * sl.count[2];
   if (n == 0) return;
+  count_launch();
   if (vk == VK_F32) k_recompose<float><<<grid_for(n), 256, 0, s>>>(dg, sl, (const float*)dec, (float*)comp);
   else k_recompose<double><<<grid_for(n), 256, 0, s>>>(dg, sl, (const double*)dec, (double*)comp);
 }
@@ -1054,10 +1045,12 @@ void launch_recon_fixed(const FieldD& f, int level, int raw, const LatD& lat, co
                         int64_t* xc, cudaStream_t s) {
   const int64_t n = lat.count[0] * lat.count[1] * lat.count[2];
   if (n == 0) return;
+  count_launch();
   k_recon_fixed<<<grid_for(n), 256, 0, s>>>(f, level, raw, lat, chat, xc);
 }
 
 void launch_coarse_out(int vk, const FieldD& f, const int64_t* xc, double scale, void* out, cudaStream_t s) {
+  count_launch();
   const int64_t n = f.nc[0] * f.nc[1] * f.nc[2];
   if (vk == VK_F32) k_coarse_out<float><<<grid_for(n), 256, 0, s>>>(f, xc, (float)scale, (float*)out);
   else k_coarse_out<double><<<grid_for(n), 256, 0, s>>>(f, xc, scale, (double*)out);
@@ -1067,11 +1060,13 @@ void launch_recon_l0(int vk, const FieldD& f, const LatD& lat, int compact, cons
                      cudaStream_t s) {
   const int64_t n = lat.count[0] * lat.count[1] * lat.count[2];
   if (n == 0) return;
+  count_launch();
   if (vk == VK_F32) k_recon_l0<float><<<grid_for(n), 256, 0, s>>>(f, lat, compact, (const float*)chat, (float*)out);
   else k_recon_l0<double><<<grid_for(n), 256, 0, s>>>(f, lat, compact, (const double*)chat, (double*)out);
 }
 
 void launch_copy_raw(int vk, const FieldD& f, const LatD& lat, const void* vals, void* out, cudaStream_t s) {
+  count_launch();
   const int64_t n = lat.count[0] * lat.count[1] * lat.count[2];
   if (vk == VK_F32) k_copy_raw<float><<<grid_for(n), 256, 0, s>>>(f, lat, (const float*)vals, (float*)out);
   else k_copy_raw<double><<<grid_for(n), 256, 0, s>>>(f, lat, (const double*)vals, (double*)out);
@@ -1081,6 +1076,7 @@ void launch_copy_raw(int vk, const FieldD& f, const LatD& lat, const void* vals,
 void launch_encode(int vk, int w64, int pairs, const StreamD* d_streams, const WorkItem* d_items,
                    int nitems, cudaStream_t s) {
   if (nitems == 0) return;
+  count_launch();
 #define ENC(VT, W, P) k_encode<VT, W, P><<<nitems, kThreads, 0, s>>>(d_streams, d_items)
   if (!w64) {
     if (vk == VK_F32) { if (pairs) ENC(float, 32, true); else ENC(float, 32, false); }
@@ -1095,6 +1091,7 @@ void launch_encode(int vk, int w64, int pairs, const StreamD* d_streams, const W
 void launch_decode(int vk, int w64, const StreamD* d_streams, const WorkItem* d_items, int nitems,
                    cudaStream_t s) {
   if (nitems == 0) return;
+  count_launch();
   if (!w64) {
     if (vk == VK_F32) k_decode<float, 32><<<nitems, kThreads, 0, s>>>(d_streams, d_items);
     else k_decode<int64_t, 32><<<nitems, kThreads, 0, s>>>(d_streams, d_items);

@@ -1,0 +1,517 @@
+// Tiled interpolation and coefficient-decomposition kernels (sm_103a).
+//
+// One CTA owns a box of one level's grid, stages the box plus a halo in
+// shared memory with coalesced row loads along the fastest axis, and runs
+// the level's region passes there (Sec. VI-C "fastest direction
+// interpolation": region r is predicted along its pass axis from the points
+// that are even along it).  Every prediction is evaluated once per tile, so
+// the per-level tensor interpolant costs about one 1-D rule per point.
+//
+// The same kernel serves the four directions of the method:
+//   refactor, per-level  : c = x - W, shared memory keeps predictions W
+//   refactor, per-region : c = x - W, W from original values only
+//   retrieve, per-level  : x' = W + c_hat, W from reconstructed coarse values
+//   retrieve, per-region : x' = W + c_hat, earlier regions reconstructed in
+//                          the tile (halo points recomputed, not exchanged)
+// Arithmetic: the rules of pcr_kernels.cu (identical expression trees).
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <type_traits>
+
+#include "pcr_internal.h"
+
+namespace pcr {
+
+#define FULLMASK 0xFFFFFFFFu
+
+template <typename T> struct TAr;
+template <> struct TAr<float> {
+  __device__ static float lin(float a, float b) { return __fmul_rn(__fadd_rn(a, b), 0.5f); }
+  __device__ static float cub(float m3, float m1, float p1, float p3) {
+    return __fmul_rn(__fsub_rn(__fmul_rn(__fadd_rn(m1, p1), 9.0f), __fadd_rn(m3, p3)), 0.0625f);
+  }
+  __device__ static float lft(float m1, float p1, float p3) {
+    return __fmul_rn(__fsub_rn(__fadd_rn(__fmul_rn(3.0f, m1), __fmul_rn(6.0f, p1)), p3), 0.125f);
+  }
+  __device__ static float rgt(float m3, float m1, float p1) {
+    return __fmul_rn(__fsub_rn(__fadd_rn(__fmul_rn(6.0f, m1), __fmul_rn(3.0f, p1)), m3), 0.125f);
+  }
+  __device__ static float add(float a, float b) { return __fadd_rn(a, b); }
+  __device__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+  __device__ static unsigned long long mag(float v) { return __float_as_uint(fabsf(v)); }
+};
+template <> struct TAr<double> {
+  __device__ static double lin(double a, double b) { return __dmul_rn(__dadd_rn(a, b), 0.5); }
+  __device__ static double cub(double m3, double m1, double p1, double p3) {
+    return __dmul_rn(__dsub_rn(__dmul_rn(__dadd_rn(m1, p1), 9.0), __dadd_rn(m3, p3)), 0.0625);
+  }
+  __device__ static double lft(double m1, double p1, double p3) {
+    return __dmul_rn(__dsub_rn(__dadd_rn(__dmul_rn(3.0, m1), __dmul_rn(6.0, p1)), p3), 0.125);
+  }
+  __device__ static double rgt(double m3, double m1, double p1) {
+    return __dmul_rn(__dsub_rn(__dadd_rn(__dmul_rn(6.0, m1), __dmul_rn(3.0, p1)), m3), 0.125);
+  }
+  __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
+  __device__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+  __device__ static unsigned long long mag(double v) { return (unsigned long long)__double_as_longlong(fabs(v)); }
+};
+template <> struct TAr<int64_t> {
+  __device__ static int64_t lin(int64_t a, int64_t b) { return (a + b) >> 1; }
+  __device__ static int64_t cub(int64_t m3, int64_t m1, int64_t p1, int64_t p3) { return (9 * (m1 + p1) - (m3 + p3)) >> 4; }
+  __device__ static int64_t lft(int64_t m1, int64_t p1, int64_t p3) { return (3 * m1 + 6 * p1 - p3) >> 3; }
+  __device__ static int64_t rgt(int64_t m3, int64_t m1, int64_t p1) { return (6 * m1 + 3 * p1 - m3) >> 3; }
+  __device__ static int64_t add(int64_t a, int64_t b) { return a + b; }
+  __device__ static int64_t sub(int64_t a, int64_t b) { return a - b; }
+  __device__ static unsigned long long mag(int64_t v) { return (unsigned long long)(v < 0 ? -v : v); }
+};
+
+// one 1-D rule at odd index j of a line of m points; at(k) reads index k
+template <typename T, class F>
+__device__ __forceinline__ T rule(int j, int m, int degree, const F& at) {
+  const bool p1 = j + 1 < m;
+  if (degree == 3) {
+    const bool m3 = j >= 3, p3 = j + 3 < m;
+    if (p1 && m3 && p3) return TAr<T>::cub(at(j - 3), at(j - 1), at(j + 1), at(j + 3));
+    if (p1 && p3) return TAr<T>::lft(at(j - 1), at(j + 1), at(j + 3));
+    if (p1 && m3) return TAr<T>::rgt(at(j - 3), at(j - 1), at(j + 1));
+  }
+  if (p1) return TAr<T>::lin(at(j - 1), at(j + 1));
+  return at(j - 1);
+}
+
+__device__ __forceinline__ unsigned long long wmax(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(FULLMASK, v, o);
+    v = t > v ? t : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ void push_max(unsigned long long* slot, unsigned long long v, int bytes) {
+  v = wmax(v);
+  if ((threadIdx.x & 31) == 0 && v && slot) {
+    if (bytes == 4) atomicMax((unsigned int*)slot, (unsigned int)v);
+    else atomicMax(slot, v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// interpolation tile kernel
+// ---------------------------------------------------------------------------
+template <typename A, int T0, int T1, int T2, int H0, int H>
+__global__ void __launch_bounds__(256) k_tile_interp(TileArgs a) {
+  constexpr int S0 = T0 + 2 * H0, S1 = T1 + 2 * H, S2 = T2 + 2 * H;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  A* S = reinterpret_cast<A*>(smem_raw);
+
+  int64_t bid = blockIdx.x;
+  const int64_t tb2 = (bid % a.ntiles[2]) * T2;
+  bid /= a.ntiles[2];
+  const int64_t tb1 = (bid % a.ntiles[1]) * T1;
+  const int64_t tb0 = (bid / a.ntiles[1]) * T0;
+  const int64_t org[3] = {tb0 - H0, tb1 - H, tb2 - H};
+  const A* __restrict__ src = reinterpret_cast<const A*>(a.src);
+  A* __restrict__ dst = reinterpret_cast<A*>(a.dst);
+
+  {
+    // warp per smem row, lanes along the fastest axis (coalesced row loads)
+    const int lane0 = threadIdx.x & 31, warp0 = threadIdx.x >> 5;
+    const int om0 = (int)org[0], om1 = (int)org[1], om2 = (int)org[2];
+    const int mm0 = (int)a.m[0], mm1 = (int)a.m[1], mm2 = (int)a.m[2];
+    const int64_t st2 = a.stride[2];
+#pragma unroll 2
+    for (int row = warp0; row < S0 * S1; row += (int)(blockDim.x >> 5)) {
+      const int i0 = row / S1, i1 = row - (row / S1) * S1;
+      const int q0 = om0 + i0, q1 = om1 + i1;
+      const bool rok = q0 >= 0 && q0 < mm0 && q1 >= 0 && q1 < mm1;
+      const A* rowp = src + (rok ? (int64_t)q0 * a.stride[0] + (int64_t)q1 * a.stride[1] : 0);
+      A* srow = S + row * S2;
+#pragma unroll
+      for (int c = 0; c < (S2 + 31) / 32; c++) {
+        const int i2 = lane0 + 32 * c;
+        if (i2 < S2) {
+          const int q2 = om2 + i2;
+          A v = A(0);
+          if (rok && q2 >= 0 && q2 < mm2) v = rowp[(int64_t)q2 * st2];
+          srow[i2] = v;
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  const bool per_level = a.interp == 0;
+  const bool retrieve = a.retrieve != 0;
+  // halo points along later pass axes are needed unless refactoring per-region
+  const bool halo = retrieve || per_level;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int m0 = (int)a.m[0], m1 = (int)a.m[1], m2 = (int)a.m[2];
+  const int b0 = (int)tb0, b1 = (int)tb1, b2 = (int)tb2;
+  const int o0 = (int)org[0], o1 = (int)org[1], o2 = (int)org[2];
+  const int64_t ds0 = a.stride[0], ds1 = a.stride[1], ds2 = a.stride[2];
+  constexpr int DEG = H == 3 ? 3 : 1;
+  for (int r = 0; r < a.d; r++) {
+    const int ax = r == 0 ? a.order[0] : (r == 1 ? a.order[1] : a.order[2]);
+    // pass range: odd along ax in the tile; even along later pass axes with
+    // the halo (when needed); the tile along earlier axes
+    bool later0 = false, later1 = false, later2 = false;
+    for (int k = r + 1; k < a.d; k++) {
+      const int bx = k == 1 ? a.order[1] : a.order[2];
+      later0 |= bx == 0;
+      later1 |= bx == 1;
+      later2 |= bx == 2;
+    }
+    auto range = [&](int axis, int tb, int T, int Hx, int m, bool later, int& lo, int& n, int& st) {
+      if (axis == ax) {
+        lo = tb + 1;
+        st = 2;
+        const int hi = min(tb + T, m);
+        n = hi > lo ? (hi - lo + 1) / 2 : 0;
+      } else if (later) {
+        const int l = halo ? max(tb - Hx, 0) : tb;
+        lo = (l + 1) & ~1;
+        st = 2;
+        const int hi = halo ? min(tb + T + Hx, m) : min(tb + T, m);
+        n = hi > lo ? (hi - lo + 1) / 2 : 0;
+      } else {
+        lo = tb;
+        st = 1;
+        const int hi = min(tb + T, m);
+        n = hi > lo ? hi - lo : 0;
+      }
+    };
+    int lo0, n0, st0, lo1, n1, st1, lo2, n2, st2;
+    range(0, b0, T0, H0, m0, later0, lo0, n0, st0);
+    range(1, b1, T1, H, m1, later1, lo1, n1, st1);
+    range(2, b2, T2, H, m2, later2, lo2, n2, st2);
+    const TileRegion R = r == 0 ? a.reg[0] : (r == 1 ? a.reg[1] : a.reg[2]);
+    const int mlen = ax == 0 ? m0 : (ax == 1 ? m1 : m2);
+    const int sstep = ax == 0 ? S1 * S2 : (ax == 1 ? S2 : 1);
+    // region lattice steps are 1 or 2 in level-grid units
+    const int sh0 = R.step[0] == 2, sh1 = R.step[1] == 2, sh2 = R.step[2] == 2;
+    const int rs0 = (int)R.start[0], rs1 = (int)R.start[1], rs2 = (int)R.start[2];
+    const int64_t rc1 = R.count[1], rpad = R.row_pad, rbase = R.base;
+    A* __restrict__ stg = reinterpret_cast<A*>(R.stage);
+    unsigned long long mx = 0;
+    // one warp per row of the pass range, lanes along the fastest axis
+    for (int row = warp; row < n0 * n1; row += nwarp) {
+      const int i0 = row / n1, i1 = row - (row / n1) * n1;
+      const int q0 = lo0 + st0 * i0, q1 = lo1 + st1 * i1;
+      const bool row_in = q0 >= b0 && q0 < b0 + T0 && q1 >= b1 && q1 < b1 + T1;
+      const int sp_row = ((q0 - o0) * S1 + (q1 - o1)) * S2 - o2;
+      const int64_t srow = rbase + ((int64_t)((q0 - rs0) >> sh0) * rc1 + ((q1 - rs1) >> sh1)) * rpad;
+      const int64_t drow = (int64_t)q0 * ds0 + (int64_t)q1 * ds1;
+      for (int i2 = lane; i2 < n2; i2 += 32) {
+        const int q2 = lo2 + st2 * i2;
+        const int sp = sp_row + q2;
+        const int j = ax == 0 ? q0 : (ax == 1 ? q1 : q2);
+        auto at = [&](int k) -> A { return S[sp + (k - j) * sstep]; };
+        const A W = rule<A>(j, mlen, DEG, at);
+        const bool in_tile = row_in && q2 >= b2 && q2 < b2 + T2;
+        const int64_t si = srow + ((q2 - rs2) >> sh2);
+        if (!retrieve) {
+          if (in_tile) {
+            const A c = TAr<A>::sub(S[sp], W);
+            stg[si] = c;
+            const unsigned long long mg = TAr<A>::mag(c);
+            mx = mg > mx ? mg : mx;
+          }
+          if (per_level) S[sp] = W;
+        } else if (per_level) {
+          S[sp] = W;
+          if (in_tile) dst[drow + (int64_t)q2 * ds2] = TAr<A>::add(W, stg[si]);
+        } else {
+          const A xv = TAr<A>::add(W, stg[si]);
+          S[sp] = xv;
+          if (in_tile) dst[drow + (int64_t)q2 * ds2] = xv;
+        }
+      }
+    }
+    if (!retrieve) push_max(R.vmax, mx, sizeof(A));
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// coefficient decomposition tile kernel (Sec. V-B, Alg. 1 / Alg. 2)
+// ---------------------------------------------------------------------------
+// Works on one region's compact array (dims cnt, row-major) with slices
+// normal to axis N; in-slice axes U < V.  The tile covers T[k] compact points
+// per axis plus one extra point at the high end of each in-slice axis (the
+// next 4-grid line), so every prediction is local.  Sub-level slots:
+// 0 S1 (4-grid), 1 S2a (u = 2 mod 4, v = 0 mod 4), 2 S2b (u even, v = 2 mod
+// 4), 3 S3a (u odd, v even), 4 S3b (v odd).
+template <int N> struct Axes;
+template <> struct Axes<0> { static constexpr int U = 1, V = 2; };
+template <> struct Axes<1> { static constexpr int U = 0, V = 2; };
+template <> struct Axes<2> { static constexpr int U = 0, V = 1; };
+
+__device__ __forceinline__ int slot_of(int ku, int kv) {
+  if (((ku | kv) & 3) == 0) return 0;
+  if (((ku | kv) & 1) == 0) return (kv & 3) == 0 ? 1 : 2;
+  return (kv & 1) == 0 ? 3 : 4;
+}
+
+// log2 of the sub-lattice steps along (u, v) and starts, per slot
+__device__ __forceinline__ void slot_geom(int sl, int& su, int& lu, int& sv, int& lv) {
+  switch (sl) {
+    case 0: su = 0; lu = 2; sv = 0; lv = 2; break;
+    case 1: su = 2; lu = 2; sv = 0; lv = 2; break;
+    case 2: su = 0; lu = 1; sv = 2; lv = 2; break;
+    case 3: su = 1; lu = 1; sv = 0; lv = 1; break;
+    default: su = 0; lu = 0; sv = 1; lv = 1; break;
+  }
+}
+
+template <typename A, int N, int T0, int T1, int T2>
+__global__ void __launch_bounds__(256) k_tile_decomp(DecompArgs a) {
+  constexpr int U = Axes<N>::U, V = Axes<N>::V;
+  constexpr int S0 = T0 + (N != 0), S1 = T1 + (N != 1), S2 = T2 + (N != 2);
+  constexpr int TS[3] = {T0, T1, T2};
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  A* S = reinterpret_cast<A*>(smem_raw);
+  int64_t bid = blockIdx.x;
+  const int tb2 = (int)((bid % a.ntiles[2]) * T2);
+  bid /= a.ntiles[2];
+  const int tb1 = (int)((bid % a.ntiles[1]) * T1);
+  const int tb0 = (int)((bid / a.ntiles[1]) * T0);
+  const int cnt0 = (int)a.cnt[0], cnt1 = (int)a.cnt[1], cnt2 = (int)a.cnt[2];
+  const int cu = (int)a.cnt[U], cv = (int)a.cnt[V];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  A* __restrict__ comp = reinterpret_cast<A*>(a.comp);
+  (void)TS;
+
+  auto pick = [](int k0, int k1, int k2, int ax) { return ax == 0 ? k0 : (ax == 1 ? k1 : k2); };
+  auto stage_index = [&](int sl, int k0, int k1, int k2) -> int64_t {
+    int su, lu, sv, lv;
+    slot_geom(sl, su, lu, sv, lv);
+    const DecompSub& sb = a.subs[sl];
+    int l[3] = {k0, k1, k2};
+    l[U] = (pick(k0, k1, k2, U) - su) >> lu;
+    l[V] = (pick(k0, k1, k2, V) - sv) >> lv;
+    return sb.base + ((int64_t)l[0] * sb.count[1] + l[1]) * sb.row_pad + l[2];
+  };
+  auto sidx = [&](int k0, int k1, int k2) { return ((k0 - tb0) * S1 + (k1 - tb1)) * S2 + (k2 - tb2); };
+  constexpr int dU = U == 0 ? S1 * S2 : (U == 1 ? S2 : 1);
+  constexpr int dV = V == 0 ? S1 * S2 : (V == 1 ? S2 : 1);
+
+  for (int row = warp; row < S0 * S1; row += nwarp) {
+    const int k0 = tb0 + row / S1, k1 = tb1 + row % S1;
+#pragma unroll 2
+    for (int i2 = lane; i2 < S2; i2 += 32) {
+      const int k2 = tb2 + i2;
+      A val = A(0);
+      if (k0 < cnt0 && k1 < cnt1 && k2 < cnt2) {
+        if (!a.retrieve) {
+          val = comp[((int64_t)k0 * cnt1 + k1) * cnt2 + k2];
+        } else {
+          const int sl = slot_of(pick(k0, k1, k2, U), pick(k0, k1, k2, V));
+          val = reinterpret_cast<const A*>(a.subs[sl].stage)[stage_index(sl, k0, k1, k2)];
+        }
+      }
+      S[row * S2 + i2] = val;
+    }
+  }
+  __syncthreads();
+
+  // per-level linear prediction (Alg. 1 Pi_2: t = 2 from the 4-grid;
+  // Pi_1: t = 1 from the 2-grid); the v pass reads u-pass predictions
+  auto predict = [&](int sp, int ku, int kv, int t) -> A {
+    auto pass_u = [&](int p) -> A {
+      if (ku + t < cu) return TAr<A>::lin(S[p - t * dU], S[p + t * dU]);
+      return S[p - t * dU];
+    };
+    if ((kv & (2 * t - 1)) == 0) return pass_u(sp);
+    const bool u_coarse = (ku & (2 * t - 1)) == 0;
+    auto src = [&](int p) -> A { return u_coarse ? S[p] : pass_u(p); };
+    if (kv + t < cv) return TAr<A>::lin(src(sp - t * dV), src(sp + t * dV));
+    return src(sp - t * dV);
+  };
+
+  if (!a.retrieve) {
+    unsigned long long m0 = 0, m1 = 0, m2 = 0, m3 = 0, m4 = 0;
+    for (int row = warp; row < T0 * T1; row += nwarp) {
+      const int k0 = tb0 + row / T1, k1 = tb1 + row % T1;
+      if (k0 >= cnt0 || k1 >= cnt1) continue;
+      for (int i2 = lane; i2 < T2; i2 += 32) {
+        const int k2 = tb2 + i2;
+        if (k2 >= cnt2) continue;
+        const int ku = pick(k0, k1, k2, U), kv = pick(k0, k1, k2, V);
+        const int sl = slot_of(ku, kv);
+        const int sp = sidx(k0, k1, k2);
+        const A c = S[sp];
+        const A dv = sl == 0 ? c : TAr<A>::sub(c, predict(sp, ku, kv, sl <= 2 ? 2 : 1));
+        reinterpret_cast<A*>(a.subs[sl].stage)[stage_index(sl, k0, k1, k2)] = dv;
+        const unsigned long long mg = TAr<A>::mag(dv);
+        if (sl == 0) m0 = mg > m0 ? mg : m0;
+        else if (sl == 1) m1 = mg > m1 ? mg : m1;
+        else if (sl == 2) m2 = mg > m2 ? mg : m2;
+        else if (sl == 3) m3 = mg > m3 ? mg : m3;
+        else m4 = mg > m4 ? mg : m4;
+      }
+    }
+    push_max(a.subs[0].vmax, m0, sizeof(A));
+    push_max(a.subs[1].vmax, m1, sizeof(A));
+    push_max(a.subs[2].vmax, m2, sizeof(A));
+    push_max(a.subs[3].vmax, m3, sizeof(A));
+    push_max(a.subs[4].vmax, m4, sizeof(A));
+    return;
+  }
+  // recompose: S1 as decoded; S2 (tile + high halo) from S1; then S3 (tile)
+  for (int row = warp; row < S0 * S1; row += nwarp) {
+    const int k0 = tb0 + row / S1, k1 = tb1 + row % S1;
+    if (k0 >= cnt0 || k1 >= cnt1) continue;
+    for (int i2 = lane; i2 < S2; i2 += 32) {
+      const int k2 = tb2 + i2;
+      if (k2 >= cnt2) continue;
+      const int ku = pick(k0, k1, k2, U), kv = pick(k0, k1, k2, V);
+      const int sl = slot_of(ku, kv);
+      if (sl != 1 && sl != 2) continue;
+      const int sp = row * S2 + i2;
+      S[sp] = TAr<A>::add(predict(sp, ku, kv, 2), S[sp]);
+    }
+  }
+  __syncthreads();
+  for (int row = warp; row < T0 * T1; row += nwarp) {
+    const int k0 = tb0 + row / T1, k1 = tb1 + row % T1;
+    if (k0 >= cnt0 || k1 >= cnt1) continue;
+    for (int i2 = lane; i2 < T2; i2 += 32) {
+      const int k2 = tb2 + i2;
+      if (k2 >= cnt2) continue;
+      const int ku = pick(k0, k1, k2, U), kv = pick(k0, k1, k2, V);
+      const int sp = sidx(k0, k1, k2);
+      A r = S[sp];
+      if (slot_of(ku, kv) >= 3) r = TAr<A>::add(predict(sp, ku, kv, 1), r);
+      comp[((int64_t)k0 * cnt1 + k1) * cnt2 + k2] = r;
+    }
+  }
+}
+
+// zero the padding of every row of a padded lattice in a staging buffer
+template <typename A>
+__global__ void k_zero_pads(LatD lat, A* stage) {
+  const int64_t padw = lat.row_pad - lat.count[2];
+  const int64_t rows = lat.count[0] * lat.count[1];
+  const int64_t n = rows * padw;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / padw, c = i % padw;
+    stage[lat.base + r * lat.row_pad + lat.count[2] + c] = A(0);
+  }
+}
+
+// max |c| over a region's compact array (level-0 rounding term)
+template <typename A>
+__global__ void k_absmax(const A* v, int64_t n, unsigned long long* slot_double_bits) {
+  __shared__ unsigned long long red[32];
+  unsigned long long mx = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long m = TAr<A>::mag(v[i]);
+    mx = m > mx ? m : mx;
+  }
+  mx = wmax(mx);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+    mx = wmax(mx);
+    if (threadIdx.x == 0 && mx) {
+      const double d = sizeof(A) == 4 ? (double)__uint_as_float((unsigned)mx) : __longlong_as_double((long long)mx);
+      atomicMax(slot_double_bits, (unsigned long long)__double_as_longlong(d));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename A, int T0, int T1, int T2, int H0, int H>
+static void run_tile(const TileArgs& a0, cudaStream_t s) {
+  count_launch();
+  TileArgs a = a0;
+  a.ntiles[0] = (a.m[0] + T0 - 1) / T0;
+  a.ntiles[1] = (a.m[1] + T1 - 1) / T1;
+  a.ntiles[2] = (a.m[2] + T2 - 1) / T2;
+  const size_t smem = sizeof(A) * (T0 + 2 * H0) * (T1 + 2 * H) * (T2 + 2 * H);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tile_interp<A, T0, T1, T2, H0, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  const int64_t nb = a.ntiles[0] * a.ntiles[1] * a.ntiles[2];
+  k_tile_interp<A, T0, T1, T2, H0, H><<<(unsigned)nb, 256, smem, s>>>(a);
+}
+
+template <typename A>
+static void run_tile_kind(const TileArgs& a, cudaStream_t s) {
+  const bool is3 = a.m[0] > 1;
+  const bool cubic = a.degree == 3;
+  constexpr bool wide = sizeof(A) == 4;
+  if (is3) {
+    if (cubic) {
+      if (wide) run_tile<A, 8, 8, 64, 3, 3>(a, s); else run_tile<A, 4, 4, 64, 3, 3>(a, s);
+    } else {
+      if (wide) run_tile<A, 8, 8, 64, 1, 1>(a, s); else run_tile<A, 4, 4, 64, 1, 1>(a, s);
+    }
+  } else {
+    if (cubic) run_tile<A, 1, 32, 64, 0, 3>(a, s); else run_tile<A, 1, 32, 64, 0, 1>(a, s);
+  }
+}
+
+void launch_tile_interp(int vk, const TileArgs& a, cudaStream_t s) {
+  if (vk == VK_F32) run_tile_kind<float>(a, s);
+  else if (vk == VK_F64) run_tile_kind<double>(a, s);
+  else run_tile_kind<int64_t>(a, s);
+}
+
+template <typename A, int N, int T0, int T1, int T2>
+static void run_decomp(const DecompArgs& a0, cudaStream_t s) {
+  count_launch();
+  DecompArgs a = a0;
+  a.ntiles[0] = (a.cnt[0] + T0 - 1) / T0;
+  a.ntiles[1] = (a.cnt[1] + T1 - 1) / T1;
+  a.ntiles[2] = (a.cnt[2] + T2 - 1) / T2;
+  const size_t smem = sizeof(A) * (T0 + (N != 0)) * (T1 + (N != 1)) * (T2 + (N != 2));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tile_decomp<A, N, T0, T1, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  const int64_t nb = a.ntiles[0] * a.ntiles[1] * a.ntiles[2];
+  k_tile_decomp<A, N, T0, T1, T2><<<(unsigned)nb, 256, smem, s>>>(a);
+}
+
+void launch_tile_decomp(int vk, const DecompArgs& a, cudaStream_t s) {
+  // tiles are multiples of 4 along the in-slice axes
+  if (vk == VK_F32) {
+    if (a.n == 2) run_decomp<float, 2, 16, 16, 32>(a, s);
+    else if (a.n == 1) run_decomp<float, 1, 16, 4, 64>(a, s);
+    else run_decomp<float, 0, 4, 16, 64>(a, s);
+  } else {
+    if (a.n == 2) run_decomp<double, 2, 16, 16, 32>(a, s);
+    else if (a.n == 1) run_decomp<double, 1, 16, 4, 64>(a, s);
+    else run_decomp<double, 0, 4, 16, 64>(a, s);
+  }
+}
+
+void launch_zero_pads(int vk, const LatD& lat, void* stage, cudaStream_t s) {
+  const int64_t n = lat.count[0] * lat.count[1] * (lat.row_pad - lat.count[2]);
+  if (n <= 0) return;
+  count_launch();
+  int g = (int)((n + 255) / 256);
+  if (g > 148 * 16) g = 148 * 16;
+  if (vk == VK_F32) k_zero_pads<float><<<g, 256, 0, s>>>(lat, (float*)stage);
+  else if (vk == VK_F64) k_zero_pads<double><<<g, 256, 0, s>>>(lat, (double*)stage);
+  else k_zero_pads<int64_t><<<g, 256, 0, s>>>(lat, (int64_t*)stage);
+}
+
+void launch_absmax(int vk, const void* v, int64_t n, unsigned long long* slot, cudaStream_t s) {
+  if (n <= 0) return;
+  count_launch();
+  int g = (int)((n + 255) / 256);
+  if (g > 148 * 4) g = 148 * 4;
+  if (vk == VK_F32) k_absmax<float><<<g, 256, 0, s>>>((const float*)v, n, slot);
+  else k_absmax<double><<<g, 256, 0, s>>>((const double*)v, n, slot);
+}
+
+}  // namespace pcr
