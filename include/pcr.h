@@ -155,6 +155,32 @@ pcr_status pcr_retrieve(const pcr_handle* h, const pcr_retrieval_plan* plan, voi
 pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
                               void* const* d_outs, void* cuda_stream);
 
+/* ---- retrieval without device allocation -------------------------------- */
+/* Same plans, same kernels and the same output as pcr_retrieve, for callers
+ * that must not allocate device memory: code that enqueues work while a
+ * stream is being captured into a CUDA graph (cudaMalloc is not permitted
+ * there), applications whose own pool or arena owns all device memory, and
+ * latency-bound loops where cudaMalloc / cudaFree would synchronise the device.
+ * Every temporary buffer of the call is carved out of one fixed 32 MiB array
+ * compiled into the library (PCR_STATIC_SCRATCH_BYTES); each GPU that loads
+ * the library holds that array until the process exits.  Nothing is
+ * allocated: no cudaMalloc / cudaMallocAsync / cudaFree and no call to the
+ * handle's allocator.  Every byte of the array that a call reads is written
+ * earlier in the same call, so nothing needs clearing between calls.
+ *   - A retrieval needing more scratch than the array holds returns
+ *     PCR_ERR_UNSUPPORTED with the required size in pcr_last_error() (with
+ *     FP32 and coefficient decomposition the limit is about 3.5 M points).
+ *   - The first call on a device looks the array's device address up with
+ *     cudaGetSymbolAddress (device-wide set-up): make that first call on each
+ *     device before any stream capture begins.
+ *   - All calls share the one array, so calls that can run at the same time
+ *     on the GPU (different streams, or host threads without ordering) race
+ *     and corrupt each other; calls enqueued on one stream are ordered.
+ * The paper has no counterpart: this is an interface for such callers. */
+#define PCR_STATIC_SCRATCH_BYTES (32u << 20)
+pcr_status pcr_retrieve_static(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out,
+                               void* cuda_stream);
+
 /* ---- introspection / persistence -------------------------------------- */
 pcr_status pcr_num_streams(const pcr_handle* h, int* n);
 pcr_status pcr_stream_info_get(const pcr_handle* h, int i, pcr_stream_info* out);

@@ -78,6 +78,7 @@ _sigs = {
     "pcr_plan": [_vp, C.POINTER(_Target), C.POINTER(_Plan)],
     "pcr_retrieve": [_vp, C.POINTER(_Plan), _vp, _vp],
     "pcr_retrieve_batch": [C.c_int, C.POINTER(_vp), C.POINTER(_Plan), C.POINTER(_vp), _vp],
+    "pcr_retrieve_static": [_vp, C.POINTER(_Plan), _vp, _vp],
     "pcr_num_streams": [_vp, C.POINTER(C.c_int)],
     "pcr_stream_info_get": [_vp, C.c_int, C.POINTER(_StreamInfo)],
     "pcr_stream_tables": [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_uint64)],
@@ -290,6 +291,15 @@ class Handle:
         assert out.is_contiguous() and tuple(out.shape) == self.shape and out.dtype == self.dtype
         _check(_lib.pcr_retrieve(self._p, C.byref(plan._c), C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out, plan
+
+    def retrieve_static(self, plan, out, stream=None):
+        """pcr_retrieve_static: the same result as retrieve() with every
+        temporary buffer in the library's fixed device array (no device
+        allocation), for callers that cannot allocate.  ``out`` must be given."""
+        assert out.is_contiguous() and tuple(out.shape) == self.shape and out.dtype == self.dtype
+        _check(_lib.pcr_retrieve_static(self._p, C.byref(plan._c), C.c_void_p(out.data_ptr()),
+                                        _stream_ptr(stream)))
+        return out
 
     def serialize(self):
         buf, n = C.c_void_p(), C.c_size_t()

@@ -1290,11 +1290,22 @@ static pcr_status setup_handle(pcr_handle* h, int ndim, const int64_t* dims, int
   return PCR_OK;
 }
 
+// Temporary device buffers of one call: from the caller's allocator, or
+// carved (256-byte aligned, never freed) out of a fixed region when `bump`
+// is set.
 struct Scratch {
   Mem* mem;
   cudaStream_t s;
   std::vector<void*> ptrs;
+  char* bump = nullptr;
+  size_t cap = 0, off = 0;
   void* get(size_t bytes) {
+    if (bump) {
+      const size_t o = (off + 255) & ~size_t(255);
+      if (o + bytes > cap) return nullptr;
+      off = o + bytes;
+      return bump + o;
+    }
     void* p = mem->alloc(bytes, s);
     if (p) ptrs.push_back(p);
     return p;
@@ -1745,14 +1756,8 @@ static pcr_status enqueue_reconstruct(const pcr_handle* h, const std::vector<Str
   return PCR_OK;
 }
 
-extern "C" pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
-                                         void* const* d_outs, void* cuda_stream) {
-  if (n <= 0 || !hs || !plans || !d_outs) return fail(PCR_ERR_INVALID_ARG, "null argument");
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  for (int k = 0; k < n; k++)
-    if (!hs[k] || !d_outs[k]) return fail(PCR_ERR_INVALID_ARG, "null handle or output");
-  Mem mem = hs[0]->mem;
-  Scratch sc{&mem, s, {}};
+static pcr_status retrieve_batch_impl(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
+                                      void* const* d_outs, cudaStream_t s, Scratch& sc) {
   std::vector<std::vector<StreamD>> sds(n);
   std::vector<StreamD> all;
   std::vector<WorkItem> items[2][2];
@@ -1793,6 +1798,59 @@ extern "C" pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, con
   }
   CUDA_TRY(cudaGetLastError());
   return PCR_OK;
+}
+
+extern "C" pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
+                                         void* const* d_outs, void* cuda_stream) {
+  if (n <= 0 || !hs || !plans || !d_outs) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  for (int k = 0; k < n; k++)
+    if (!hs[k] || !d_outs[k]) return fail(PCR_ERR_INVALID_ARG, "null handle or output");
+  Mem mem = hs[0]->mem;
+  Scratch sc{&mem, s, {}};
+  return retrieve_batch_impl(n, hs, plans, d_outs, s, sc);
+}
+
+// bytes of temporary device memory one retrieval of `h` uses (upper bound,
+// including 256-byte alignment of every piece)
+static size_t retrieve_scratch_bytes(const pcr_handle* h) {
+  const size_t w = vsize(h->vk);
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  size_t fix = 0, flt = 0, items = 0;
+  for (auto& g : h->geo) {
+    (g.is_fix ? fix : flt) += g.n_pad();
+    items += (g.n_pad() + kSegElems - 1) / kSegElems;
+  }
+  size_t t = al(fix * 8) + al(flt * w) + al(h->geo.size() * sizeof(StreamD)) + al(std::max<size_t>(items, 1) * sizeof(WorkItem));
+  if (h->L >= 2) {
+    size_t nc = 1;
+    for (int a = 0; a < 3; a++) nc *= h->n3[a] > 1 ? (h->n3[a] - 1) / 2 + 1 : 1;
+    t += al(nc * 8);
+  }
+  if (h->decomp >= 0)
+    for (int r = 1; r <= (int)h->order.size(); r++) t += al((size_t)region_lat(h->n3, 0, h->order, r).n_real() * w);
+  return t + 256;
+}
+
+// Retrieval whose temporary buffers live in the library's fixed device array
+// (pcr_static.cu); see pcr_retrieve_static in include/pcr.h.
+extern "C" pcr_status pcr_retrieve_static(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out,
+                                          void* cuda_stream) {
+  if (!h || !plan || !d_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  size_t cap = 0;
+  std::string why;
+  char* base = (char*)static_scratch(&cap, &why);
+  if (!base) return fail(PCR_ERR_CUDA, "static scratch set-up failed: " + why);
+  const size_t need = retrieve_scratch_bytes(h);
+  if (need > cap)
+    return fail(PCR_ERR_UNSUPPORTED, "retrieval needs " + std::to_string(need) +
+                                         " bytes of scratch; the static array holds " + std::to_string(cap));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Mem mem = h->mem;
+  Scratch sc{&mem, s, {}};
+  sc.bump = base;
+  sc.cap = cap;
+  return retrieve_batch_impl(1, &h, plan, &d_out, s, sc);
 }
 
 extern "C" pcr_status pcr_retrieve(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out, void* cuda_stream) {

@@ -2,6 +2,7 @@
 // library (pcr_host.cpp).  Not part of the ABI.
 #pragma once
 #include <cstdint>
+#include <string>
 
 namespace pcr {
 
@@ -116,6 +117,11 @@ struct FieldStats {
   int G;                                   // max|x| < 2^G
   int bad;                                 // non-finite input seen
 };
+
+// Device address of the library's fixed scratch array on the current device
+// (looked up once per device with cudaGetSymbolAddress); nullptr and a
+// reason on failure.  *cap receives its size in bytes.
+void* static_scratch(size_t* cap, std::string* why);
 
 // kernels launched by this library since load (tracing); every launcher
 // increments it right before its <<<...>>>
