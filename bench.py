@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pcr", choices=["pcr", "reference"])
     ap.add_argument("--size", type=int, default=512, help="cube edge (default 512)")
+    ap.add_argument("--mode", default="headline", choices=["headline", "batch", "serve"],
+                    help="headline (default): the 512^3 step; batch: 96 uneven fields, one "
+                         "batched refactor vs sequential calls; serve: continuous-batching server")
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the batch/serve workload")
     return ap.parse_args()
 
 
@@ -327,9 +331,105 @@ def run_reference(args):
     }))
 
 
+def run_batch(args):
+    """96 independent fields of uneven shapes (32 x 100x500x500, 32 x
+    64x256x1024, 32 x 2-D 1800x3600): one batched refactor (one work list per
+    stage, one synchronisation) against the same fields refactored one call
+    at a time."""
+    import torch
+    import paper_2609_04573_b300 as pcr
+    from synth.device import grf_torch
+    torch.cuda.set_device(0)
+    per = max(1, int(round(32 * args.scale)))
+    shapes = [(100, 500, 500)] * per + [(64, 256, 1024)] * per + [(1800, 3600)] * per
+    xs = [grf_torch(s, 1000 + i) for i, s in enumerate(shapes)]
+    nbytes = sum(x.numel() * 4 for x in xs)
+    schemes = [pcr.Scheme(interp="level", degree="cubic", decomp_axis=2 if x.dim() == 3 else -1) for x in xs]
+    torch.cuda.synchronize()
+    hb = pcr.refactor_batch(xs, schemes)          # warm-up
+    del hb
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, r
+    tb, hb = timed(lambda: pcr.refactor_batch(xs, schemes))
+    ts, hs = timed(lambda: [pcr.refactor(x, s) for x, s in zip(xs, schemes)])
+    same = all(a.stream_copy(i)[0].tobytes() == b.stream_copy(i)[0].tobytes()
+               for a, b in zip(hb[:3], hs[:3]) for i in range(a.nstreams))
+    print(json.dumps({"mode": "batch", "fields": len(xs), "bytes": nbytes,
+                      "batched_gbs": nbytes / tb / 1e9, "sequential_gbs": nbytes / ts / 1e9,
+                      "batched_s": tb, "sequential_s": ts, "speedup": ts / tb,
+                      "first_fields_identical": same}))
+
+
+def run_serve(args):
+    """Resident refactored fields, Poisson arrivals of mixed-tolerance
+    requests (half whole-field, half 128^3 boxes), continuous batching with
+    memory admission, against a one-at-a-time server."""
+    import random
+    import torch
+    import paper_2609_04573_b300 as pcr
+    from paper_2609_04573_b300.serve import Server, percentile
+    from synth.device import grf_torch
+    torch.cuda.set_device(0)
+    n512 = max(1, int(round(48 * args.scale)))
+    n256 = max(1, int(round(192 * args.scale)))
+    shapes = [(512,) * 3] * n512 + [(256,) * 3] * n256
+    handles = []
+    for i, s in enumerate(shapes):
+        x = grf_torch(s, 2000 + i)
+        handles.append(pcr.refactor(x, pcr.Scheme(interp="level", degree="cubic", decomp_axis=2)))
+        del x
+    torch.cuda.synchronize()
+    resident = sum(sum(h.stream_info(i)["words"] * 4 * h.stream_info(i)["nplanes"] for i in range(h.nstreams))
+                   for h in handles)
+    rng = random.Random(7)
+    nreq = max(50, int(400 * min(1.0, args.scale * 4)))
+    reqs, t = [], 0.0
+    for _ in range(nreq):
+        t += rng.expovariate(2000.0)
+        f = rng.randrange(len(handles))
+        if rng.random() < 0.5:
+            tg = pcr.Target("rel", 10.0 ** -rng.randint(2, 6))
+        else:
+            tg = pcr.Target("psnr", float(rng.choice(range(50, 111, 10))))
+        box = None
+        if rng.random() < 0.5:
+            box = tuple((lo, lo + 128) for lo in (rng.randrange(0, s - 127) for s in shapes[f]))
+        reqs.append((t, f, tg, box))
+
+    def serve(batch, streams, budget):
+        srv = Server(handles, mem_budget=budget, max_batch=batch, streams=streams)
+        t0 = time.perf_counter()
+        live = []
+        for ta, f, tg, box in reqs:
+            while time.perf_counter() - t0 < ta:
+                time.sleep(0.00005)
+            live.append(srv.submit(f, tg, box))
+        for r in live:
+            r.future.result(timeout=600)
+        wall = time.perf_counter() - t0
+        srv.close()
+        lat = [r.latency * 1e3 for r in live]
+        out_bytes = sum(handles[r.field_id].out_bytes for r in live)
+        return {"p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99), "wall_s": wall,
+                "field_gbs": out_bytes / wall / 1e9, "read_gbs": sum(r.bytes_read for r in live) / wall / 1e9,
+                "batches": srv.batches}
+    cont = serve(16, 2, 24 << 30)
+    seq = serve(1, 1, 24 << 30)
+    print(json.dumps({"mode": "serve", "fields": len(handles), "resident_plane_bytes": resident,
+                      "requests": nreq, "arrival_rate_per_s": 2000, "continuous": cont, "sequential": seq}))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.mode == "batch":
+        run_batch(a)
+    elif a.mode == "serve":
+        run_serve(a)
     else:
         run_pcr(a)

@@ -155,6 +155,10 @@ pcr_status pcr_retrieve(const pcr_handle* h, const pcr_retrieval_plan* plan, voi
 pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
                               void* const* d_outs, void* cuda_stream);
 
+/* Upper bound on the temporary device memory one pcr_retrieve of `h` takes
+ * (staging, work lists, recomposition); used for memory-based admission. */
+pcr_status pcr_retrieve_scratch_bytes(const pcr_handle* h, size_t* bytes);
+
 /* ---- retrieval without device allocation -------------------------------- */
 /* Same plans, same kernels and the same output as pcr_retrieve, for callers
  * that must not allocate device memory: code that enqueues work while a

@@ -79,6 +79,7 @@ _sigs = {
     "pcr_retrieve": [_vp, C.POINTER(_Plan), _vp, _vp],
     "pcr_retrieve_batch": [C.c_int, C.POINTER(_vp), C.POINTER(_Plan), C.POINTER(_vp), _vp],
     "pcr_retrieve_static": [_vp, C.POINTER(_Plan), _vp, _vp],
+    "pcr_retrieve_scratch_bytes": [_vp, C.POINTER(C.c_size_t)],
     "pcr_num_streams": [_vp, C.POINTER(C.c_int)],
     "pcr_stream_info_get": [_vp, C.c_int, C.POINTER(_StreamInfo)],
     "pcr_stream_tables": [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_uint64)],
@@ -291,6 +292,19 @@ class Handle:
         assert out.is_contiguous() and tuple(out.shape) == self.shape and out.dtype == self.dtype
         _check(_lib.pcr_retrieve(self._p, C.byref(plan._c), C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out, plan
+
+    @property
+    def out_bytes(self):
+        n = 1
+        for s in self.shape:
+            n *= s
+        return n * (4 if self.dtype == torch.float32 else 8)
+
+    def retrieve_scratch_bytes(self):
+        """Temporary device memory one retrieval of this handle takes."""
+        v = C.c_size_t()
+        _check(_lib.pcr_retrieve_scratch_bytes(self._p, C.byref(v)))
+        return v.value
 
     def retrieve_static(self, plan, out, stream=None):
         """pcr_retrieve_static: the same result as retrieve() with every

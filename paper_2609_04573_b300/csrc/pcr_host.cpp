@@ -774,7 +774,7 @@ struct pcr_handle {
   std::vector<int> E, sh;
   std::vector<double> vmax;
   std::vector<Tab> tabs;
-  std::vector<std::vector<uint32_t>> sign_counts;   // host copy per stream
+  std::vector<std::vector<uint32_t>> sign_words;    // per stream: sign words per plane (all segments)
   std::vector<std::vector<uint32_t>> plane_nz;
   std::vector<std::vector<uint64_t>> pairs;
   std::vector<int64_t> plane_off, sign_off, scnt_off, nz_off;
@@ -789,7 +789,7 @@ struct pcr_handle {
   bool has_m0 = false;
   double m0_init = 0;
   std::vector<Step> m0;
-  size_t plane_words = 0, sign_words = 0, scnt_words = 0, nz_words = 0;
+  size_t plane_words = 0, sign_area_words = 0, scnt_words = 0, nz_words = 0;
   ~pcr_handle() {
     cudaStream_t s = 0;
     mem.free(d_planes, s);
@@ -981,8 +981,7 @@ void compute_tables(pcr_handle* h, int i, const std::vector<uint64_t>* pairs, bo
   const int64_t nseg = (g.n_pad() + kSegElems - 1) / kSegElems;
   for (int k = 0; k < B; k++) {
     if (h->plane_nz[i][k]) acc += 4 * (uint64_t)words;
-    if (!nb)
-      for (int64_t sg = 0; sg < nseg; sg++) acc += 4 * (uint64_t)((h->sign_counts[i][sg * B + k] + 31) / 32);
+    if (!nb) acc += 4 * (uint64_t)h->sign_words[i][k];
     t.bytes[k + 1] = acc;
   }
   double unit, vmax_abs;
@@ -1281,10 +1280,10 @@ static pcr_status setup_handle(pcr_handle* h, int ndim, const int64_t* dims, int
     h->scnt_off[i] = co;
     co += (size_t)nseg * h->B;
     h->nz_off[i] = zo;
-    zo += h->B;
+    zo += 2 * (size_t)h->B;
   }
   h->plane_words = po;
-  h->sign_words = so;
+  h->sign_area_words = so;
   h->scnt_words = co;
   h->nz_words = zo;
   return PCR_OK;
@@ -1421,7 +1420,7 @@ static pcr_status enqueue_refactor(pcr_handle* h, const void* d_field, cudaStrea
 }
 
 static pcr_status finish_refactor(pcr_handle* h, const FieldStats& st, const std::vector<unsigned long long>& vm,
-                                  const std::vector<uint32_t>& scnt, const std::vector<uint32_t>& nz,
+                                  const std::vector<uint32_t>& nz,
                                   const std::vector<uint64_t>* pairs) {
   if (st.bad) return fail(PCR_ERR_INVALID_ARG, "field contains NaN or Inf");
   auto inv = [](unsigned long long k) {
@@ -1440,7 +1439,7 @@ static pcr_status finish_refactor(pcr_handle* h, const FieldStats& st, const std
   h->sh.assign(ns, 0);
   h->vmax.assign(ns, 0);
   h->tabs.assign(ns, Tab());
-  h->sign_counts.assign(ns, {});
+  h->sign_words.assign(ns, {});
   h->plane_nz.assign(ns, {});
   h->pairs.assign(ns, {});
   double c0;
@@ -1471,8 +1470,8 @@ static pcr_status finish_refactor(pcr_handle* h, const FieldStats& st, const std
       if (g.level == 0 && h->L >= 2) h->C0 = std::max(h->C0, dv);
     }
     const int64_t nseg = (g.n_pad() + kSegElems - 1) / kSegElems;
-    h->sign_counts[i].assign(scnt.begin() + h->scnt_off[i], scnt.begin() + h->scnt_off[i] + nseg * h->B);
     h->plane_nz[i].assign(nz.begin() + h->nz_off[i], nz.begin() + h->nz_off[i] + h->B);
+    h->sign_words[i].assign(nz.begin() + h->nz_off[i] + h->B, nz.begin() + h->nz_off[i] + 2 * h->B);
     if (pairs) h->pairs[i].assign(pairs->begin() + (size_t)i * h->B * h->B, pairs->begin() + (size_t)(i + 1) * h->B * h->B);
   }
   for (int i = 0; i < ns; i++) compute_tables(h, i, pairs ? &h->pairs[i] : nullptr, h->sch.mode == PCR_MODE_PSNR);
@@ -1482,10 +1481,12 @@ static pcr_status finish_refactor(pcr_handle* h, const FieldStats& st, const std
 
 static pcr_status alloc_handle_buffers(pcr_handle* h, cudaStream_t s) {
   h->d_planes = (uint32_t*)h->mem.alloc(h->plane_words * 4, s);
-  h->d_signs = (uint32_t*)h->mem.alloc(std::max<size_t>(h->sign_words, 1) * 4, s);
+  h->d_signs = (uint32_t*)h->mem.alloc(std::max<size_t>(h->sign_area_words, 1) * 4, s);
   h->d_scnt = (uint32_t*)h->mem.alloc(std::max<size_t>(h->scnt_words, 1) * 4, s);
   h->d_nz = (uint32_t*)h->mem.alloc(h->nz_words * 4, s);
   if (!h->d_planes || !h->d_signs || !h->d_scnt || !h->d_nz) return fail(PCR_ERR_OOM, "handle allocation failed");
+  // unused tails of sign slots stay zero, so containers are deterministic
+  if (h->sign_area_words) CUDA_TRY(cudaMemsetAsync(h->d_signs, 0, h->sign_area_words * 4, s));
   return PCR_OK;
 }
 
@@ -1587,12 +1588,9 @@ extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, con
   CUDA_TRY(cudaMemcpyAsync(st.data(), d_st, sizeof(FieldStats) * n, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(vm.data(), d_vm, nv * 8, cudaMemcpyDeviceToHost, s));
   if (npairs) CUDA_TRY(cudaMemcpyAsync(pairs.data(), d_pairs, npairs * 8, cudaMemcpyDeviceToHost, s));
-  std::vector<std::vector<uint32_t>> scnt(n), nz(n);
+  std::vector<std::vector<uint32_t>> nz(n);
   for (int k = 0; k < n; k++) {
-    scnt[k].resize(hs[k]->scnt_words);
     nz[k].resize(hs[k]->nz_words);
-    if (hs[k]->scnt_words)
-      CUDA_TRY(cudaMemcpyAsync(scnt[k].data(), hs[k]->d_scnt, hs[k]->scnt_words * 4, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(nz[k].data(), hs[k]->d_nz, hs[k]->nz_words * 4, cudaMemcpyDeviceToHost, s));
   }
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -1602,7 +1600,7 @@ extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, con
     std::vector<uint64_t> pk;
     if (h->sch.mode == PCR_MODE_PSNR)
       pk.assign(pairs.begin() + pr_off[k], pairs.begin() + pr_off[k] + h->geo.size() * h->B * h->B);
-    pcr_status e = finish_refactor(h, st[k], v, scnt[k], nz[k], h->sch.mode == PCR_MODE_PSNR ? &pk : nullptr);
+    pcr_status e = finish_refactor(h, st[k], v, nz[k], h->sch.mode == PCR_MODE_PSNR ? &pk : nullptr);
     if (e) return e;
   }
   for (int k = 0; k < n; k++) outs[k] = hs[k].release();
@@ -1832,6 +1830,12 @@ static size_t retrieve_scratch_bytes(const pcr_handle* h) {
   return t + 256;
 }
 
+extern "C" pcr_status pcr_retrieve_scratch_bytes(const pcr_handle* h, size_t* bytes) {
+  if (!h || !bytes) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  *bytes = retrieve_scratch_bytes(h);
+  return PCR_OK;
+}
+
 // Retrieval whose temporary buffers live in the library's fixed device array
 // (pcr_static.cu); see pcr_retrieve_static in include/pcr.h.
 extern "C" pcr_status pcr_retrieve_static(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out,
@@ -1912,7 +1916,8 @@ extern "C" pcr_status pcr_stream_copy(const pcr_handle* h, int i, uint32_t* plan
   if (planes_host) CUDA_TRY(cudaMemcpy(planes_host, h->d_planes + h->plane_off[i], (size_t)h->B * words * 4, cudaMemcpyDeviceToHost));
   if (signs_host && h->enc == 1)
     CUDA_TRY(cudaMemcpy(signs_host, h->d_signs + h->sign_off[i], (size_t)nseg * h->slot_words * 4, cudaMemcpyDeviceToHost));
-  if (sign_counts_host) std::memcpy(sign_counts_host, h->sign_counts[i].data(), h->sign_counts[i].size() * 4);
+  if (sign_counts_host)
+    CUDA_TRY(cudaMemcpy(sign_counts_host, h->d_scnt + h->scnt_off[i], (size_t)nseg * h->B * 4, cudaMemcpyDeviceToHost));
   if (pairs_host && !h->pairs[i].empty()) std::memcpy(pairs_host, h->pairs[i].data(), h->pairs[i].size() * 8);
   return PCR_OK;
 }
@@ -2012,7 +2017,12 @@ extern "C" pcr_status pcr_serialize(const pcr_handle* h, void** buf, size_t* len
     hd.put(h->E[i]);
     hd.put(h->sh[i]);
     hd.raw(h->plane_nz[i].data(), h->plane_nz[i].size() * 4);
-    hd.raw(h->sign_counts[i].data(), h->sign_counts[i].size() * 4);
+    {
+      const int64_t nseg = (h->geo[i].n_pad() + kSegElems - 1) / kSegElems;
+      std::vector<uint32_t> sc((size_t)nseg * h->B);
+      CUDA_TRY(cudaMemcpy(sc.data(), h->d_scnt + h->scnt_off[i], sc.size() * 4, cudaMemcpyDeviceToHost));
+      hd.raw(sc.data(), sc.size() * 4);
+    }
     const uint64_t np = h->pairs[i].size();
     hd.put(np);
     hd.raw(h->pairs[i].data(), np * 8);
@@ -2021,9 +2031,10 @@ extern "C" pcr_status pcr_serialize(const pcr_handle* h, void** buf, size_t* len
   w.put(crc32(hd.buf.data(), hd.buf.size()));
   w.raw(hd.buf.data(), hd.buf.size());
   // payload: planes then signs
-  std::vector<uint32_t> planes(h->plane_words), signs(h->sign_words);
+  std::vector<uint32_t> planes(h->plane_words), signs(h->sign_area_words);
   CUDA_TRY(cudaMemcpy(planes.data(), h->d_planes, h->plane_words * 4, cudaMemcpyDeviceToHost));
-  if (h->sign_words) CUDA_TRY(cudaMemcpy(signs.data(), h->d_signs, h->sign_words * 4, cudaMemcpyDeviceToHost));
+  if (h->sign_area_words)
+    CUDA_TRY(cudaMemcpy(signs.data(), h->d_signs, h->sign_area_words * 4, cudaMemcpyDeviceToHost));
   w.put((uint64_t)planes.size());
   w.put(crc32(planes.data(), planes.size() * 4));
   w.raw(planes.data(), planes.size() * 4);
@@ -2072,7 +2083,8 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
   h->E.resize(ns);
   h->sh.resize(ns);
   h->plane_nz.resize(ns);
-  h->sign_counts.resize(ns);
+  std::vector<std::vector<uint32_t>> scnts(ns);
+  h->sign_words.assign(ns, std::vector<uint32_t>(h->B, 0));
   h->pairs.resize(ns);
   h->tabs.resize(ns);
   for (int i = 0; i < ns; i++) {
@@ -2082,8 +2094,10 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
     h->plane_nz[i].resize(h->B);
     for (int k = 0; k < h->B; k++) h->plane_nz[i][k] = hr.get<uint32_t>();
     const int64_t nseg = (h->geo[i].n_pad() + kSegElems - 1) / kSegElems;
-    h->sign_counts[i].resize(nseg * h->B);
-    for (auto& x : h->sign_counts[i]) x = hr.get<uint32_t>();
+    scnts[i].resize(nseg * h->B);
+    for (auto& x : scnts[i]) x = hr.get<uint32_t>();
+    for (int64_t sg = 0; sg < nseg; sg++)
+      for (int k = 0; k < h->B; k++) h->sign_words[i][k] += (scnts[i][sg * h->B + k] + 31) / 32;
     const uint64_t np = hr.get<uint64_t>();
     if (!hr.ok || (np != 0 && np != (uint64_t)h->B * h->B)) return fail(PCR_ERR_CORRUPT, "bad table section");
     h->pairs[i].resize(np);
@@ -2097,7 +2111,8 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
   const uint64_t nsw = r.get<uint64_t>();
   const uint32_t sgc = r.get<uint32_t>();
   const uint8_t* sp = r.take(nsw * 4);
-  if (!r.ok || nsw != h->sign_words || crc32(sp, nsw * 4) != sgc) return fail(PCR_ERR_CORRUPT, "sign section mismatch");
+  if (!r.ok || nsw != h->sign_area_words || crc32(sp, nsw * 4) != sgc)
+    return fail(PCR_ERR_CORRUPT, "sign section mismatch");
   if (r.o != len) return fail(PCR_ERR_CORRUPT, "trailing bytes");
   e = alloc_handle_buffers(h.get(), s);
   if (e) return e;
@@ -2105,8 +2120,9 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
   if (nsw) CUDA_TRY(cudaMemcpyAsync(h->d_signs, sp, nsw * 4, cudaMemcpyHostToDevice, s));
   std::vector<uint32_t> scnt, nz;
   for (int i = 0; i < ns; i++) {
-    scnt.insert(scnt.end(), h->sign_counts[i].begin(), h->sign_counts[i].end());
+    scnt.insert(scnt.end(), scnts[i].begin(), scnts[i].end());
     nz.insert(nz.end(), h->plane_nz[i].begin(), h->plane_nz[i].end());
+    nz.insert(nz.end(), h->sign_words[i].begin(), h->sign_words[i].end());
   }
   if (!scnt.empty()) CUDA_TRY(cudaMemcpyAsync(h->d_scnt, scnt.data(), scnt.size() * 4, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(h->d_nz, nz.data(), nz.size() * 4, cudaMemcpyHostToDevice, s));
@@ -2137,14 +2153,14 @@ extern "C" pcr_status pcr_debug_encode(const void* d_vals, int64_t n_pad, int va
   uint32_t* d_planes = (uint32_t*)sc.get(words * B * 4);
   uint32_t* d_signs = (uint32_t*)sc.get(nseg * slot * 4);
   uint32_t* d_scnt = (uint32_t*)sc.get(nseg * B * 4);
-  uint32_t* d_nz = (uint32_t*)sc.get(B * 4);
+  uint32_t* d_nz = (uint32_t*)sc.get(2 * B * 4);
   unsigned long long* d_pairs = (unsigned long long*)sc.get((size_t)B * B * 8);
   unsigned long long* d_vmax = (unsigned long long*)sc.get(8);
   StreamD* d_sd = (StreamD*)sc.get(sizeof(StreamD));
   WorkItem* d_it = (WorkItem*)sc.get(nseg * sizeof(WorkItem));
   if (!d_planes || !d_signs || !d_scnt || !d_nz || !d_pairs || !d_vmax || !d_sd || !d_it)
     return fail(PCR_ERR_OOM, "allocation failed");
-  CUDA_TRY(cudaMemsetAsync(d_nz, 0, B * 4, s));
+  CUDA_TRY(cudaMemsetAsync(d_nz, 0, 2 * B * 4, s));
   CUDA_TRY(cudaMemsetAsync(d_pairs, 0, (size_t)B * B * 8, s));
   CUDA_TRY(cudaMemsetAsync(d_signs, 0, nseg * slot * 4, s));
   // maximum |value| on the host side of the test entry: read back values

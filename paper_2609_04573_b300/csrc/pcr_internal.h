@@ -46,7 +46,7 @@ struct StreamD {
   uint32_t* planes;    // [B][words]
   uint32_t* signs;     // [nseg][slot_words]
   uint32_t* sign_counts;   // [nseg][B]
-  uint32_t* plane_nz;      // [B] nonzero words per plane
+  uint32_t* plane_nz;      // [2B]: nonzero words per plane, then sign words per plane
   unsigned long long* pairs; // [B][B] (PSNR mode) or nullptr
   unsigned long long* vmax;  // max |value| (float bits / double bits / u64)
   void* stage;         // staged values, padded canonical order

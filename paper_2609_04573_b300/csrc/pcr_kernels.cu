@@ -832,7 +832,11 @@ __global__ void __launch_bounds__(kThreads) k_encode(const StreamD* __restrict__
     __syncthreads();
     uint32_t* dst = s.signs + (int64_t)it.seg * s.slot_words;
     for (int i = threadIdx.x; i < (int)poff[B]; i += kThreads) dst[i] = sbuf[i];
-    if (threadIdx.x < B) s.sign_counts[(int64_t)it.seg * B + threadIdx.x] = wcnt[0][threadIdx.x];
+    if (threadIdx.x < B) {
+      const uint32_t c = wcnt[0][threadIdx.x];
+      s.sign_counts[(int64_t)it.seg * B + threadIdx.x] = c;
+      if (c) atomicAdd(&s.plane_nz[B + threadIdx.x], (c + 31) >> 5);   // sign words of plane k
+    }
   }
   // plane words: coalesced per plane
   const int64_t w0 = (int64_t)it.seg * kSegWords;

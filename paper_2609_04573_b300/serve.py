@@ -1,0 +1,159 @@
+"""Serving loop for progressive retrieval (continuous batching).
+
+Refactored fields stay resident on the device (their handles own the plane
+streams).  Requests -- (field, target[, box]) -- arrive at any time; a worker
+thread admits them while the memory the in-flight retrievals need (output +
+scratch, from pcr_retrieve_scratch_bytes) stays under a budget, groups the
+admitted requests into one pcr_retrieve_batch call (one decode work list for
+the whole group), and keeps up to `streams` groups on the GPU at once on
+separate CUDA streams.  Requests that arrive while groups are running join the
+next group as soon as memory frees up; results complete out of order through
+CUDA events.  Every result is the same field a single pcr_retrieve of that
+request produces (the kernels are deterministic and share no state between
+requests).
+
+Box requests return the requested sub-box of the retrieved field.
+"""
+import queue
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+from typing import Optional, Tuple
+
+import torch
+
+from . import Target, retrieve_batch
+
+
+@dataclass
+class Request:
+    field_id: int
+    target: Target
+    box: Optional[Tuple[Tuple[int, int], ...]] = None   # ((lo, hi), ...) per axis
+    t_submit: float = 0.0
+    t_done: float = 0.0
+    future: Future = field(default_factory=Future)
+    plan: object = None
+    bytes_read: int = 0
+
+    @property
+    def latency(self):
+        return self.t_done - self.t_submit
+
+
+class Server:
+    """Continuous-batching retrieval server over resident handles."""
+
+    def __init__(self, handles, mem_budget=8 << 30, max_batch=32, streams=2, device=None):
+        self.handles = list(handles)
+        self.budget = int(mem_budget)
+        self.max_batch = max_batch
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        self.q = queue.Queue()
+        self.inflight = []            # (event, stream, [requests], [outs], mem)
+        self.mem_in_use = 0
+        self.done = []
+        self._stop = False
+        self._need = [h.retrieve_scratch_bytes() + h.out_bytes for h in self.handles]
+        self._worker = threading.Thread(target=self._run, daemon=True)
+        self._worker.start()
+        self.batches = 0
+
+    def submit(self, field_id, target, box=None):
+        r = Request(field_id, target, box, t_submit=time.perf_counter())
+        self.q.put(r)
+        return r
+
+    def close(self):
+        self._stop = True
+        self._worker.join()
+
+    # ---- worker -----------------------------------------------------------
+    def _run(self):
+        torch.cuda.set_device(self.device)
+        pending = []
+        sidx = 0
+        while True:
+            try:
+                while True:
+                    pending.append(self.q.get_nowait())
+            except queue.Empty:
+                pass
+            self._poll()
+            if self._stop and not pending and not self.inflight and self.q.empty():
+                return
+            free_stream = len(self.inflight) < len(self.streams)
+            if pending and free_stream:
+                group, mem = [], 0
+                rest = []
+                for r in pending:
+                    need = self._need[r.field_id]
+                    if len(group) < self.max_batch and self.mem_in_use + mem + need <= self.budget:
+                        group.append(r)
+                        mem += need
+                    else:
+                        rest.append(r)
+                if not group and not self.inflight and pending:
+                    # a single request larger than the budget runs alone
+                    group, rest = [pending[0]], pending[1:]
+                    mem = self._need[pending[0].field_id]
+                pending = rest
+                if group:
+                    self._launch(group, mem, self.streams[sidx % len(self.streams)])
+                    sidx += 1
+                    continue
+            time.sleep(0.0002)
+
+    def _launch(self, group, mem, stream):
+        hs, plans, outs = [], [], []
+        for r in group:
+            h = self.handles[r.field_id]
+            try:
+                p = h.plan(r.target, allow_unsat=True)
+            except Exception as e:  # isolate a failed request, keep the others
+                r.t_done = time.perf_counter()
+                r.future.set_exception(e)
+                continue
+            r.plan = p
+            r.bytes_read = p.bytes
+            hs.append(h)
+            plans.append(p)
+            with torch.cuda.stream(stream):
+                outs.append(torch.empty(h.shape, dtype=h.dtype, device=self.device))
+        live = [r for r in group if r.plan is not None]
+        if not live:
+            return
+        with torch.cuda.stream(stream):
+            retrieve_batch(hs, plans, outs, stream=stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        self.mem_in_use += mem
+        self.inflight.append((ev, stream, live, outs, mem))
+        self.batches += 1
+
+    def _poll(self):
+        keep = []
+        for ev, stream, reqs, outs, mem in self.inflight:
+            if ev.query():
+                now = time.perf_counter()
+                for r, o in zip(reqs, outs):
+                    res = o
+                    if r.box is not None:
+                        res = o[tuple(slice(lo, hi) for lo, hi in r.box)]
+                    r.t_done = now
+                    r.future.set_result(res)
+                    self.done.append(r)
+                self.mem_in_use -= mem
+            else:
+                keep.append((ev, stream, reqs, outs, mem))
+        self.inflight = keep
+
+
+def percentile(xs, p):
+    if not xs:
+        return None
+    s = sorted(xs)
+    k = min(len(s) - 1, max(0, int(round(p / 100.0 * (len(s) - 1)))))
+    return s[k]
