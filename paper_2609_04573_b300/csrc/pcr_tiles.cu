@@ -99,136 +99,218 @@ __device__ __forceinline__ void push_max(unsigned long long* slot, unsigned long
 // ---------------------------------------------------------------------------
 // interpolation tile kernel
 // ---------------------------------------------------------------------------
-template <typename A, int T0, int T1, int T2, int H0, int H>
-__global__ void __launch_bounds__(256) k_tile_interp(TileArgs a) {
-  constexpr int S0 = T0 + 2 * H0, S1 = T1 + 2 * H, S2 = T2 + 2 * H;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  A* S = reinterpret_cast<A*>(smem_raw);
-
-  int64_t bid = blockIdx.x;
-  const int64_t tb2 = (bid % a.ntiles[2]) * T2;
-  bid /= a.ntiles[2];
-  const int64_t tb1 = (bid % a.ntiles[1]) * T1;
-  const int64_t tb0 = (bid / a.ntiles[1]) * T0;
-  const int64_t org[3] = {tb0 - H0, tb1 - H, tb2 - H};
-  const A* __restrict__ src = reinterpret_cast<const A*>(a.src);
-  A* __restrict__ dst = reinterpret_cast<A*>(a.dst);
-
-  {
-    // warp per smem row, lanes along the fastest axis (coalesced row loads)
-    const int lane0 = threadIdx.x & 31, warp0 = threadIdx.x >> 5;
-    const int om0 = (int)org[0], om1 = (int)org[1], om2 = (int)org[2];
-    const int mm0 = (int)a.m[0], mm1 = (int)a.m[1], mm2 = (int)a.m[2];
-    const int64_t st2 = a.stride[2];
-#pragma unroll 2
-    for (int row = warp0; row < S0 * S1; row += (int)(blockDim.x >> 5)) {
-      const int i0 = row / S1, i1 = row - (row / S1) * S1;
-      const int q0 = om0 + i0, q1 = om1 + i1;
-      const bool rok = q0 >= 0 && q0 < mm0 && q1 >= 0 && q1 < mm1;
-      const A* rowp = src + (rok ? (int64_t)q0 * a.stride[0] + (int64_t)q1 * a.stride[1] : 0);
-      A* srow = S + row * S2;
+// asynchronous global -> shared copies (zero-filled when !valid)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 8 : 0));
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+// One region pass of one staged tile along compile-time axis AX.
+// Range: odd along AX inside the tile; even along later pass axes (with the
+// halo when `halo`); the tile along earlier axes.  Shared-memory neighbours
+// along AX are at compile-time offsets; interior lines skip the boundary
+// checks of the 1-D rule.
+template <typename A, int AX, int T0, int T1, int T2, int H0, int H, int S1, int S2>
+__device__ __forceinline__ void tile_pass(const TileArgs& a, A* __restrict__ S, const TileRegion& R, int b0, int b1,
+                                          int b2, int o0, int o1, int o2, bool later0, bool later1, bool later2,
+                                          bool halo, bool per_level, bool retrieve, A* __restrict__ dst) {
+  constexpr int DEG = H == 3 ? 3 : 1;
+  constexpr int SSTEP = AX == 0 ? S1 * S2 : (AX == 1 ? S2 : 1);
+  const int m[3] = {(int)a.m[0], (int)a.m[1], (int)a.m[2]};
+  const int b[3] = {b0, b1, b2};
+  const int Tt[3] = {T0, T1, T2};
+  const int Hh[3] = {H0, H, H};
+  const bool later[3] = {later0, later1, later2};
+  int lo[3], n[3], st[3];
 #pragma unroll
-      for (int c = 0; c < (S2 + 31) / 32; c++) {
-        const int i2 = lane0 + 32 * c;
-        if (i2 < S2) {
-          const int q2 = om2 + i2;
-          A v = A(0);
-          if (rok && q2 >= 0 && q2 < mm2) v = rowp[(int64_t)q2 * st2];
-          srow[i2] = v;
+  for (int k = 0; k < 3; k++) {
+    int l, hi;
+    if (k == AX) {
+      l = b[k] + 1;
+      hi = min(b[k] + Tt[k], m[k]);
+      st[k] = 2;
+    } else if (later[k]) {
+      l = (halo ? max(b[k] - Hh[k], 0) : b[k]);
+      l = (l + 1) & ~1;
+      hi = halo ? min(b[k] + Tt[k] + Hh[k], m[k]) : min(b[k] + Tt[k], m[k]);
+      st[k] = 2;
+    } else {
+      l = b[k];
+      hi = min(b[k] + Tt[k], m[k]);
+      st[k] = 1;
+    }
+    lo[k] = l;
+    n[k] = hi > l ? (hi - l + st[k] - 1) / st[k] : 0;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int sh0 = R.step[0] == 2, sh1 = R.step[1] == 2, sh2 = R.step[2] == 2;
+  const int rs0 = (int)R.start[0], rs1 = (int)R.start[1], rs2 = (int)R.start[2];
+  // streams hold fewer than 2^31 elements, so staging offsets fit in 32 bits
+  const int rc1 = (int)R.count[1], rpad = (int)R.row_pad, rbase = (int)R.base;
+  A* __restrict__ stg = reinterpret_cast<A*>(R.stage);
+  const int mlen = m[AX];
+  const int rows = n[0] * n[1];
+  const unsigned inv = n[1] ? ((1u << 20) + n[1] - 1) / n[1] : 0;   // row / n1 without a division
+  float fmx = 0.0f;
+  unsigned long long imx = 0;
+  const int total = rows * n[2];
+  const unsigned inv2 = n[2] ? ((1u << 20) + n[2] - 1) / n[2] : 0;   // idx / n2 (idx < 2^14)
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int row = (int)(((unsigned)idx * inv2) >> 20), i2 = idx - row * n[2];
+    const int i0 = (int)(((unsigned)row * inv) >> 20), i1 = row - i0 * n[1];
+    const int q0 = lo[0] + st[0] * i0, q1 = lo[1] + st[1] * i1, q2 = lo[2] + st[2] * i2;
+    const int sp = ((q0 - o0) * S1 + (q1 - o1)) * S2 + (q2 - o2);
+    A W;
+    const int jj = AX == 0 ? q0 : (AX == 1 ? q1 : q2);
+    if (DEG == 3 && jj >= 3 && jj + 3 < mlen) {
+      W = TAr<A>::cub(S[sp - 3 * SSTEP], S[sp - SSTEP], S[sp + SSTEP], S[sp + 3 * SSTEP]);
+    } else {
+      auto at = [&](int k) -> A { return S[sp + (k - jj) * SSTEP]; };
+      W = rule<A>(jj, mlen, DEG, at);
+    }
+    const bool in_tile = q0 >= b0 && q0 < b0 + T0 && q1 >= b1 && q1 < b1 + T1 && q2 >= b2 && q2 < b2 + T2;
+    const int si = rbase + (((q0 - rs0) >> sh0) * rc1 + ((q1 - rs1) >> sh1)) * rpad + ((q2 - rs2) >> sh2);
+    if (!retrieve) {
+      if (in_tile) {
+        const A c = TAr<A>::sub(S[sp], W);
+        stg[si] = c;
+        if constexpr (std::is_same<A, float>::value) fmx = fmaxf(fmx, fabsf(c));
+        else {
+          const unsigned long long mg = TAr<A>::mag(c);
+          imx = mg > imx ? mg : imx;
         }
+      }
+      if (per_level) S[sp] = W;
+    } else {
+      const int64_t di = (int64_t)q0 * a.stride[0] + (int64_t)q1 * a.stride[1] + (int64_t)q2 * a.stride[2];
+      if (per_level) {
+        S[sp] = W;
+        if (in_tile) dst[di] = TAr<A>::add(W, stg[si]);
+      } else {
+        const A xv = TAr<A>::add(W, stg[si]);
+        S[sp] = xv;
+        if (in_tile) dst[di] = xv;
       }
     }
   }
+  (void)lane;
+  (void)warp;
+  (void)nwarp;
+  if (!retrieve) {
+    if constexpr (std::is_same<A, float>::value) imx = __float_as_uint(fmx);
+    push_max(R.vmax, imx, sizeof(A));
+  }
+}
+
+template <typename A, int T0, int T1, int T2, int H0, int H>
+__global__ void __launch_bounds__(256) k_tile_interp(TileArgs a) {
+  // the x extent of the staged box starts 4 points (not H) before the tile so
+  // that, for float fields whose rows are 16-byte multiples, every staged row
+  // is loaded with aligned 16-byte vectors
+  constexpr int XL = 4;
+  constexpr int S0 = T0 + 2 * H0, S1 = T1 + 2 * H, S2 = T2 + 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  A* S = reinterpret_cast<A*>(smem_raw);
+
+  unsigned bid = blockIdx.x;
+  const unsigned nt2 = (unsigned)a.ntiles[2], nt1 = (unsigned)a.ntiles[1];
+  const int b2 = (int)(bid % nt2) * T2;
+  bid /= nt2;
+  const int b1 = (int)(bid % nt1) * T1;
+  const int b0 = (int)(bid / nt1) * T0;
+  const int o0 = b0 - H0, o1 = b1 - H, o2 = b2 - XL;
+  const A* __restrict__ src = reinterpret_cast<const A*>(a.src);
+  A* __restrict__ dst = reinterpret_cast<A*>(a.dst);
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int m0 = (int)a.m[0], m1 = (int)a.m[1], m2 = (int)a.m[2];
+    const int64_t st2 = a.stride[2];
+    // 16-byte vectors: float rows of unit x-stride, 16-byte aligned row starts
+    const bool vec = sizeof(A) == 4 && st2 == 1 && (a.stride[1] % 4) == 0 && (a.stride[0] % 4) == 0 &&
+                     ((uintptr_t)src % 16) == 0;
+    // rows needed along an axis: the tile, plus the halo points that are
+    // even (every 1-D rule reads points even along its axis)
+    constexpr int HL0 = H0 == 0 ? 0 : H0 / 2, HR0 = H0 == 0 ? 0 : (H0 + 1) / 2;
+    constexpr int HL = H / 2, HR = (H + 1) / 2;
+    constexpr int R0 = T0 + HL0 + HR0, R1 = T1 + HL + HR;
+    auto rowpos = [](int c, int b, int T, int hl) -> int {   // compact row -> coordinate
+      if (c < hl) return b - 2 * (hl - c);
+      if (c < hl + T) return b + (c - hl);
+      return b + T + 2 * (c - hl - T);
+    };
+    if (vec) {
+      constexpr int NV = S2 / 4;
+      for (int idx = threadIdx.x; idx < R0 * R1 * NV; idx += blockDim.x) {
+        const int rr = idx / NV, v = idx - rr * NV;
+        const int c0 = rr / R1, c1 = rr - c0 * R1;
+        const int q0 = rowpos(c0, b0, T0, HL0), q1 = rowpos(c1, b1, T1, HL);
+        const bool rok = q0 >= 0 && q0 < m0 && q1 >= 0 && q1 < m1;
+        const float* rp = reinterpret_cast<const float*>(src) + (rok ? (int64_t)q0 * a.stride[0] + (int64_t)q1 * a.stride[1] : 0);
+        float* d = reinterpret_cast<float*>(S) + ((q0 - o0) * S1 + (q1 - o1)) * S2 + 4 * v;
+        const int x = o2 + 4 * v;
+        if (rok && x >= 0 && x + 3 < m2) {
+          cp_async16(d, rp + x);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            const bool ok = rok && x + e >= 0 && x + e < m2;
+            cp_async4(d + e, ok ? (const void*)(rp + x + e) : (const void*)src, ok);
+          }
+        }
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < R0 * R1 * S2; idx += blockDim.x) {
+        const int rr = idx / S2, i2 = idx - rr * S2;
+        const int c0 = rr / R1, c1 = rr - c0 * R1;
+        const int q0 = rowpos(c0, b0, T0, HL0), q1 = rowpos(c1, b1, T1, HL);
+        const int q2 = o2 + i2;
+        const bool ok = q0 >= 0 && q0 < m0 && q1 >= 0 && q1 < m1 && q2 >= 0 && q2 < m2;
+        A* d = S + ((q0 - o0) * S1 + (q1 - o1)) * S2 + i2;
+        const A* g = ok ? src + (int64_t)q0 * a.stride[0] + (int64_t)q1 * a.stride[1] + (int64_t)q2 * st2 : src;
+        if (sizeof(A) == 4) cp_async4(d, g, ok);
+        else cp_async8(d, g, ok);
+      }
+    }
+    (void)lane;
+    (void)warp;
+    (void)nwarp;
+  }
+  cp_async_wait_all();
   __syncthreads();
 
   const bool per_level = a.interp == 0;
   const bool retrieve = a.retrieve != 0;
-  // halo points along later pass axes are needed unless refactoring per-region
   const bool halo = retrieve || per_level;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int m0 = (int)a.m[0], m1 = (int)a.m[1], m2 = (int)a.m[2];
-  const int b0 = (int)tb0, b1 = (int)tb1, b2 = (int)tb2;
-  const int o0 = (int)org[0], o1 = (int)org[1], o2 = (int)org[2];
-  const int64_t ds0 = a.stride[0], ds1 = a.stride[1], ds2 = a.stride[2];
-  constexpr int DEG = H == 3 ? 3 : 1;
   for (int r = 0; r < a.d; r++) {
     const int ax = r == 0 ? a.order[0] : (r == 1 ? a.order[1] : a.order[2]);
-    // pass range: odd along ax in the tile; even along later pass axes with
-    // the halo (when needed); the tile along earlier axes
-    bool later0 = false, later1 = false, later2 = false;
+    bool l0 = false, l1 = false, l2 = false;
     for (int k = r + 1; k < a.d; k++) {
       const int bx = k == 1 ? a.order[1] : a.order[2];
-      later0 |= bx == 0;
-      later1 |= bx == 1;
-      later2 |= bx == 2;
+      l0 |= bx == 0;
+      l1 |= bx == 1;
+      l2 |= bx == 2;
     }
-    auto range = [&](int axis, int tb, int T, int Hx, int m, bool later, int& lo, int& n, int& st) {
-      if (axis == ax) {
-        lo = tb + 1;
-        st = 2;
-        const int hi = min(tb + T, m);
-        n = hi > lo ? (hi - lo + 1) / 2 : 0;
-      } else if (later) {
-        const int l = halo ? max(tb - Hx, 0) : tb;
-        lo = (l + 1) & ~1;
-        st = 2;
-        const int hi = halo ? min(tb + T + Hx, m) : min(tb + T, m);
-        n = hi > lo ? (hi - lo + 1) / 2 : 0;
-      } else {
-        lo = tb;
-        st = 1;
-        const int hi = min(tb + T, m);
-        n = hi > lo ? hi - lo : 0;
-      }
-    };
-    int lo0, n0, st0, lo1, n1, st1, lo2, n2, st2;
-    range(0, b0, T0, H0, m0, later0, lo0, n0, st0);
-    range(1, b1, T1, H, m1, later1, lo1, n1, st1);
-    range(2, b2, T2, H, m2, later2, lo2, n2, st2);
     const TileRegion R = r == 0 ? a.reg[0] : (r == 1 ? a.reg[1] : a.reg[2]);
-    const int mlen = ax == 0 ? m0 : (ax == 1 ? m1 : m2);
-    const int sstep = ax == 0 ? S1 * S2 : (ax == 1 ? S2 : 1);
-    // region lattice steps are 1 or 2 in level-grid units
-    const int sh0 = R.step[0] == 2, sh1 = R.step[1] == 2, sh2 = R.step[2] == 2;
-    const int rs0 = (int)R.start[0], rs1 = (int)R.start[1], rs2 = (int)R.start[2];
-    const int64_t rc1 = R.count[1], rpad = R.row_pad, rbase = R.base;
-    A* __restrict__ stg = reinterpret_cast<A*>(R.stage);
-    unsigned long long mx = 0;
-    // one warp per row of the pass range, lanes along the fastest axis
-    for (int row = warp; row < n0 * n1; row += nwarp) {
-      const int i0 = row / n1, i1 = row - (row / n1) * n1;
-      const int q0 = lo0 + st0 * i0, q1 = lo1 + st1 * i1;
-      const bool row_in = q0 >= b0 && q0 < b0 + T0 && q1 >= b1 && q1 < b1 + T1;
-      const int sp_row = ((q0 - o0) * S1 + (q1 - o1)) * S2 - o2;
-      const int64_t srow = rbase + ((int64_t)((q0 - rs0) >> sh0) * rc1 + ((q1 - rs1) >> sh1)) * rpad;
-      const int64_t drow = (int64_t)q0 * ds0 + (int64_t)q1 * ds1;
-      for (int i2 = lane; i2 < n2; i2 += 32) {
-        const int q2 = lo2 + st2 * i2;
-        const int sp = sp_row + q2;
-        const int j = ax == 0 ? q0 : (ax == 1 ? q1 : q2);
-        auto at = [&](int k) -> A { return S[sp + (k - j) * sstep]; };
-        const A W = rule<A>(j, mlen, DEG, at);
-        const bool in_tile = row_in && q2 >= b2 && q2 < b2 + T2;
-        const int64_t si = srow + ((q2 - rs2) >> sh2);
-        if (!retrieve) {
-          if (in_tile) {
-            const A c = TAr<A>::sub(S[sp], W);
-            stg[si] = c;
-            const unsigned long long mg = TAr<A>::mag(c);
-            mx = mg > mx ? mg : mx;
-          }
-          if (per_level) S[sp] = W;
-        } else if (per_level) {
-          S[sp] = W;
-          if (in_tile) dst[drow + (int64_t)q2 * ds2] = TAr<A>::add(W, stg[si]);
-        } else {
-          const A xv = TAr<A>::add(W, stg[si]);
-          S[sp] = xv;
-          if (in_tile) dst[drow + (int64_t)q2 * ds2] = xv;
-        }
-      }
-    }
-    if (!retrieve) push_max(R.vmax, mx, sizeof(A));
+    if (ax == 0)
+      tile_pass<A, 0, T0, T1, T2, H0, H, S1, S2>(a, S, R, b0, b1, b2, o0, o1, o2, l0, l1, l2, halo, per_level,
+                                                 retrieve, dst);
+    else if (ax == 1)
+      tile_pass<A, 1, T0, T1, T2, H0, H, S1, S2>(a, S, R, b0, b1, b2, o0, o1, o2, l0, l1, l2, halo, per_level,
+                                                 retrieve, dst);
+    else
+      tile_pass<A, 2, T0, T1, T2, H0, H, S1, S2>(a, S, R, b0, b1, b2, o0, o1, o2, l0, l1, l2, halo, per_level,
+                                                 retrieve, dst);
     __syncthreads();
   }
 }
@@ -432,7 +514,7 @@ static void run_tile(const TileArgs& a0, cudaStream_t s) {
   a.ntiles[0] = (a.m[0] + T0 - 1) / T0;
   a.ntiles[1] = (a.m[1] + T1 - 1) / T1;
   a.ntiles[2] = (a.m[2] + T2 - 1) / T2;
-  const size_t smem = sizeof(A) * (T0 + 2 * H0) * (T1 + 2 * H) * (T2 + 2 * H);
+  const size_t smem = sizeof(A) * (T0 + 2 * H0) * (T1 + 2 * H) * (T2 + 8);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_tile_interp<A, T0, T1, T2, H0, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
