@@ -46,7 +46,6 @@ void launch_decode(int vk, int w64, const StreamD* d_streams, const WorkItem* d_
 void launch_tile_interp(int vk, const TileArgs& a, cudaStream_t s);
 void launch_tile_decomp(int vk, const DecompArgs& a, cudaStream_t s);
 void launch_zero_pads(int vk, const LatD& lat, void* stage, cudaStream_t s);
-void launch_absmax(int vk, const void* v, int64_t n, unsigned long long* slot, cudaStream_t s);
 }  // namespace pcr
 
 using namespace pcr;
@@ -1398,15 +1397,11 @@ static pcr_status enqueue_refactor(pcr_handle* h, const void* d_field, cudaStrea
   }
   if (h->decomp >= 0) {
     for (int r = 1; r <= f.d; r++) {
-      const Lat R = region_lat(h->n3, 0, h->order, r);
-      {
-        Prof pf("absmax", s);
-        launch_absmax(h->vk, comp[r], R.n_real(), c0, s);
-      }
       DecompArgs da{};
       decomp_subs(h, r, sds, da);
       da.retrieve = 0;
       da.comp = comp[r];
+      da.c0 = c0;     // max |c| over the region, for the rounding allowance
       {
         Prof pf(da.retrieve ? "recompose" : "decompose", s);
         launch_tile_decomp(h->vk, da, s);

@@ -103,6 +103,7 @@ struct DecompArgs {
   int retrieve;        // 0 decompose, 1 recompose
   void* comp;          // region compact array (c, or recomposed c_hat)
   DecompSub subs[5];   // S1, S2a, S2b, S3a, S3b
+  unsigned long long* c0;  // decompose: running max |c| (bits of a double)
 };
 
 struct WorkItem {

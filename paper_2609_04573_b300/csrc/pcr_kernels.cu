@@ -542,6 +542,7 @@ __global__ void k_raw_stage(FieldD f, LatD lat, const T* __restrict__ x, T* __re
 // --------------------------------------------------------------------------
 // bitplanes (Sec. V-C; Sec. VI-A encodings)
 // --------------------------------------------------------------------------
+// 32 x 32 bit transpose across a warp: bit k of lane e <-> bit e of lane k
 __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 #pragma unroll
   for (int j = 16; j >= 1; j >>= 1) {
@@ -646,6 +647,10 @@ __device__ __forceinline__ VT dequantize(code_t<W> q, bool neg, const StreamD& s
   if constexpr (std::is_same<VT, int64_t>::value) {
     return (int64_t)((uint64_t)val << s.sh);
   } else if constexpr (std::is_same<VT, float>::value) {
+    // |val| < 2^31 here: the quantised value is below 2^(B-3) <= 2^29 and the
+    // digits dropped below plane b are worth less than (2/3) 2^31, so the
+    // 32-bit conversion rounds the same integer as a 64-bit one would
+    if (W == 32) return scale2f(__int2float_rn((int)val), s.E - B + 3);
     return scale2f(__ll2float_rn(val), s.E - B + 3);
   } else {
     return scale2d(__ll2double_rn(val), s.E - B + 3);
@@ -864,7 +869,9 @@ template <typename VT, int W>
 __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__ streams,
                                                      const WorkItem* __restrict__ items) {
   constexpr int NP = W;
-  __shared__ uint32_t pbuf[NP][kSegWords + 1];
+  // plane rows padded to 132 words: 16-byte aligned rows, and the 16-byte
+  // reads of 8 lanes from 8 rows fall on distinct banks
+  __shared__ __align__(16) uint32_t pbuf[NP][kSegWords + 4];
   __shared__ uint32_t sbuf[kSegWords + 64];
   __shared__ uint32_t wcnt[kWarps][NP];
   __shared__ uint32_t woff[kWarps][NP];
@@ -880,7 +887,14 @@ __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__
   const int64_t w0 = (int64_t)it.seg * kSegWords;
   VT* out = (VT*)s.stage;
 
-  if (nw == kSegWords) {
+  if (nw == kSegWords && (s.words & 3) == 0) {
+    for (int i = threadIdx.x; i < b * (kSegWords / 4); i += kThreads) {
+      const int k = i >> 5, c = i & 31;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (s.plane_nz[k]) v = *reinterpret_cast<const uint4*>(s.planes + (int64_t)k * s.words + w0 + 4 * c);
+      *reinterpret_cast<uint4*>(&pbuf[k][4 * c]) = v;
+    }
+  } else if (nw == kSegWords) {
     for (int i = threadIdx.x; i < b * kSegWords; i += kThreads) {
       const int k = i >> 7, j = i & 127;
       pbuf[k][j] = s.plane_nz[k] ? s.planes[(int64_t)k * s.words + w0 + j] : 0u;
@@ -909,14 +923,20 @@ __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__
 
   code_t<W> qs[kWordsPerWarp];
   uint32_t rec[kWordsPerWarp];
+  uint4 gl = make_uint4(0u, 0u, 0u, 0u), gh = gl;   // plane words of 4 consecutive words
 #pragma unroll
   for (int jj = 0; jj < kWordsPerWarp; jj++) {
     const int j = warp * kWordsPerWarp + jj;
     qs[jj] = 0;
     rec[jj] = 0xFFFFFFFFu;
     if (j >= nw) continue;
-    uint32_t xl = lane < b ? pbuf[lane][j] : 0u;
-    uint32_t xh = (W == 64 && lane + 32 < b) ? pbuf[lane + 32][j] : 0u;
+    if ((jj & 3) == 0) {
+      if (lane < b) gl = *reinterpret_cast<const uint4*>(&pbuf[lane][j]);
+      if (W == 64 && lane + 32 < b) gh = *reinterpret_cast<const uint4*>(&pbuf[lane + 32][j]);
+    }
+    const int e4 = jj & 3;
+    uint32_t xl = lane < b ? (e4 == 0 ? gl.x : e4 == 1 ? gl.y : e4 == 2 ? gl.z : gl.w) : 0u;
+    uint32_t xh = (W == 64 && lane + 32 < b) ? (e4 == 0 ? gh.x : e4 == 1 ? gh.y : e4 == 2 ? gh.z : gh.w) : 0u;
     if (!generic) {
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {

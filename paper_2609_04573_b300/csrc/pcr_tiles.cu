@@ -96,6 +96,17 @@ __device__ __forceinline__ void push_max(unsigned long long* slot, unsigned long
   }
 }
 
+// warp maximum of |values| given as bit patterns of A, merged into a slot
+// holding the bits of a non-negative double
+template <typename A>
+__device__ __forceinline__ void push_max_double(unsigned long long* slot, unsigned long long v) {
+  v = wmax(v);
+  if ((threadIdx.x & 31) == 0 && v && slot) {
+    const double d = sizeof(A) == 4 ? (double)__uint_as_float((unsigned)v) : __longlong_as_double((long long)v);
+    atomicMax(slot, (unsigned long long)__double_as_longlong(d));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // interpolation tile kernel
 // ---------------------------------------------------------------------------
@@ -412,7 +423,7 @@ __global__ void __launch_bounds__(256) k_tile_decomp(DecompArgs a) {
   };
 
   if (!a.retrieve) {
-    unsigned long long m0 = 0, m1 = 0, m2 = 0, m3 = 0, m4 = 0;
+    unsigned long long m0 = 0, m1 = 0, m2 = 0, m3 = 0, m4 = 0, cm = 0;
     for (int row = warp; row < T0 * T1; row += nwarp) {
       const int k0 = tb0 + row / T1, k1 = tb1 + row % T1;
       if (k0 >= cnt0 || k1 >= cnt1) continue;
@@ -423,6 +434,8 @@ __global__ void __launch_bounds__(256) k_tile_decomp(DecompArgs a) {
         const int sl = slot_of(ku, kv);
         const int sp = sidx(k0, k1, k2);
         const A c = S[sp];
+        const unsigned long long cg = TAr<A>::mag(c);
+        cm = cg > cm ? cg : cm;
         const A dv = sl == 0 ? c : TAr<A>::sub(c, predict(sp, ku, kv, sl <= 2 ? 2 : 1));
         reinterpret_cast<A*>(a.subs[sl].stage)[stage_index(sl, k0, k1, k2)] = dv;
         const unsigned long long mg = TAr<A>::mag(dv);
@@ -438,6 +451,7 @@ __global__ void __launch_bounds__(256) k_tile_decomp(DecompArgs a) {
     push_max(a.subs[2].vmax, m2, sizeof(A));
     push_max(a.subs[3].vmax, m3, sizeof(A));
     push_max(a.subs[4].vmax, m4, sizeof(A));
+    push_max_double<A>(a.c0, cm);
     return;
   }
   // recompose: S1 as decoded; S2 (tile + high halo) from S1; then S3 (tile)
@@ -470,6 +484,173 @@ __global__ void __launch_bounds__(256) k_tile_decomp(DecompArgs a) {
   }
 }
 
+// Slices normal to the fastest axis (N = 2, in-slice axes u = 0, v = 1).
+// One thread owns the 4 x 4 block (4a.., 4b..) of in-slice points for one
+// vector of VEC consecutive points along the normal axis, and holds the
+// block's 5 x 5 neighbourhood (the next 4-grid lines included) in registers.
+// Within a block the sub-level of point (du, dv) and its prediction rule are
+// compile-time constants; the lines shared with the next blocks are read
+// again by those blocks (from L2).  Loads and stores are VEC-wide along the
+// contiguous normal axis.
+template <typename A, int VEC> struct VecT { A v[VEC]; };
+template <typename A, int VEC>
+__device__ __forceinline__ void vld(VecT<A, VEC>& d, const A* p) {
+  if constexpr (VEC * sizeof(A) == 16) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    static_assert(sizeof(VecT<A, VEC>) == 16, "vector size");
+    d = *reinterpret_cast<const VecT<A, VEC>*>(&t);
+  } else if constexpr (VEC * sizeof(A) == 8) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    d = *reinterpret_cast<const VecT<A, VEC>*>(&t);
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; e++) d.v[e] = p[e];
+  }
+}
+template <typename A, int VEC>
+__device__ __forceinline__ void vst(A* p, const VecT<A, VEC>& d) {
+  if constexpr (VEC * sizeof(A) == 16) {
+    *reinterpret_cast<float4*>(p) = *reinterpret_cast<const float4*>(&d);
+  } else if constexpr (VEC * sizeof(A) == 8) {
+    *reinterpret_cast<float2*>(p) = *reinterpret_cast<const float2*>(&d);
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; e++) p[e] = d.v[e];
+  }
+}
+
+// sub-level slot of in-block offsets (du, dv) (both taken mod 4)
+__host__ __device__ constexpr int blk_slot(int du, int dv) {
+  return ((du | dv) & 3) == 0 ? 0 : (((du | dv) & 1) == 0 ? ((dv & 3) == 0 ? 1 : 2) : ((dv & 1) == 0 ? 3 : 4));
+}
+__host__ __device__ constexpr int blk_su(int sl) { return sl == 1 ? 2 : (sl == 3 ? 1 : 0); }
+__host__ __device__ constexpr int blk_lu(int sl) { return sl <= 1 ? 2 : (sl <= 3 ? 1 : 0); }
+__host__ __device__ constexpr int blk_sv(int sl) { return sl == 2 ? 2 : (sl == 4 ? 1 : 0); }
+__host__ __device__ constexpr int blk_lv(int sl) { return sl <= 2 ? 2 : 1; }
+
+template <typename A, int VEC>
+__global__ void __launch_bounds__(128) k_decomp_blk(DecompArgs a) {
+  using V = VecT<A, VEC>;
+  const unsigned nvec = (unsigned)a.ntiles[2], nbb = (unsigned)a.ntiles[1], nab = (unsigned)a.ntiles[0];
+  const unsigned item = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned iv = item % nvec, rest = item / nvec;
+  const unsigned bb = rest % nbb, ab = rest / nbb;
+  const bool live = ab < nab;
+  const int cu = (int)a.cnt[0], cv = (int)a.cnt[1];
+  const int64_t cw = a.cnt[2];
+  const int u0 = 4 * (int)ab, v0 = 4 * (int)bb;
+  const int64_t k2 = (int64_t)iv * VEC;
+  A* __restrict__ comp = reinterpret_cast<A*>(a.comp);
+  bool vu[5], vv[5];
+#pragma unroll
+  for (int d = 0; d < 5; d++) {
+    vu[d] = live && u0 + d < cu;
+    vv[d] = live && v0 + d < cv;
+  }
+  // row of slot sl holding in-block offsets (du, dv), this thread's vector
+  auto srow = [&](int sl, int du, int dv) -> A* {
+    const DecompSub& sb = a.subs[sl];
+    const int64_t ui = ((int64_t)ab << (2 - blk_lu(sl))) + ((du - blk_su(sl)) >> blk_lu(sl));
+    const int64_t vi = ((int64_t)bb << (2 - blk_lv(sl))) + ((dv - blk_sv(sl)) >> blk_lv(sl));
+    return reinterpret_cast<A*>(sb.stage) + sb.base + (ui * sb.count[1] + vi) * sb.row_pad + k2;
+  };
+  V x[5][5];
+  auto lin = [](const V& p, const V& q) {
+    V r;
+#pragma unroll
+    for (int e = 0; e < VEC; e++) r.v[e] = TAr<A>::lin(p.v[e], q.v[e]);
+    return r;
+  };
+  // per-level linear prediction with step t (Alg. 1: t = 2 from the 4-grid,
+  // t = 1 from the 2-grid); the v pass reads u-pass predictions
+  auto pass_u = [&](int du, int dv, int t) -> V { return vu[du + t] ? lin(x[du - t][dv], x[du + t][dv]) : x[du - t][dv]; };
+  auto predict = [&](int du, int dv, int t) -> V {
+    if (dv % (2 * t) == 0) return pass_u(du, dv, t);
+    const bool uc = du % (2 * t) == 0;
+    const V lo = uc ? x[du][dv - t] : pass_u(du, dv - t, t);
+    if (!vv[dv + t]) return lo;
+    const V hi = uc ? x[du][dv + t] : pass_u(du, dv + t, t);
+    return lin(lo, hi);
+  };
+
+  if (!a.retrieve) {
+#pragma unroll
+    for (int du = 0; du < 5; du++)
+#pragma unroll
+      for (int dv = 0; dv < 5; dv++) {
+        if (vu[du] && vv[dv]) vld<A, VEC>(x[du][dv], comp + ((int64_t)(u0 + du) * cv + (v0 + dv)) * cw + k2);
+        else
+#pragma unroll
+          for (int e = 0; e < VEC; e++) x[du][dv].v[e] = A(0);
+      }
+    // magnitudes as order-preserving bit patterns (|v| of an IEEE value)
+    using M = std::conditional_t<sizeof(A) == 4, unsigned, unsigned long long>;
+    M mx[5] = {0, 0, 0, 0, 0}, cm = 0;
+#pragma unroll
+    for (int du = 0; du < 4; du++)
+#pragma unroll
+      for (int dv = 0; dv < 4; dv++) {
+        if (!(vu[du] && vv[dv])) continue;
+        const int sl = blk_slot(du, dv);
+        V d = x[du][dv];
+#pragma unroll
+        for (int e = 0; e < VEC; e++) {
+          const M cg = (M)TAr<A>::mag(d.v[e]);
+          cm = cg > cm ? cg : cm;
+        }
+        if (sl != 0) {
+          const V w = predict(du, dv, sl <= 2 ? 2 : 1);
+#pragma unroll
+          for (int e = 0; e < VEC; e++) d.v[e] = TAr<A>::sub(d.v[e], w.v[e]);
+        }
+        vst<A, VEC>(srow(sl, du, dv), d);
+#pragma unroll
+        for (int e = 0; e < VEC; e++) {
+          const M mg = (M)TAr<A>::mag(d.v[e]);
+          mx[sl] = mg > mx[sl] ? mg : mx[sl];
+        }
+      }
+#pragma unroll
+    for (int q = 0; q < 5; q++) push_max(a.subs[q].vmax, mx[q], sizeof(A));
+    push_max_double<A>(a.c0, cm);
+    return;
+  }
+  // recompose: decoded sub-level values of the block and of the next 4-grid
+  // lines' 2-grid points; S2 from S1, then S3 from the 2-grid (Alg. 2)
+#pragma unroll
+  for (int du = 0; du < 5; du++)
+#pragma unroll
+    for (int dv = 0; dv < 5; dv++) {
+      const bool need = (du < 4 && dv < 4) || ((du | dv) & 1) == 0;
+      if (need && vu[du] && vv[dv]) vld<A, VEC>(x[du][dv], srow(blk_slot(du, dv), du, dv));
+      else
+#pragma unroll
+        for (int e = 0; e < VEC; e++) x[du][dv].v[e] = A(0);
+    }
+#pragma unroll
+  for (int du = 0; du < 5; du += 2)
+#pragma unroll
+    for (int dv = 0; dv < 5; dv += 2) {
+      if (((du | dv) & 3) == 0 || !(vu[du] && vv[dv])) continue;
+      const V w = predict(du, dv, 2);
+#pragma unroll
+      for (int e = 0; e < VEC; e++) x[du][dv].v[e] = TAr<A>::add(w.v[e], x[du][dv].v[e]);
+    }
+#pragma unroll
+  for (int du = 0; du < 4; du++)
+#pragma unroll
+    for (int dv = 0; dv < 4; dv++) {
+      if (!(vu[du] && vv[dv])) continue;
+      V r = x[du][dv];
+      if (((du | dv) & 1) != 0) {
+        const V w = predict(du, dv, 1);
+#pragma unroll
+        for (int e = 0; e < VEC; e++) r.v[e] = TAr<A>::add(w.v[e], r.v[e]);
+      }
+      vst<A, VEC>(comp + ((int64_t)(u0 + du) * cv + (v0 + dv)) * cw + k2, r);
+    }
+}
+
 // zero the padding of every row of a padded lattice in a staging buffer
 template <typename A>
 __global__ void k_zero_pads(LatD lat, A* stage) {
@@ -483,27 +664,6 @@ __global__ void k_zero_pads(LatD lat, A* stage) {
 }
 
 // max |c| over a region's compact array (level-0 rounding term)
-template <typename A>
-__global__ void k_absmax(const A* v, int64_t n, unsigned long long* slot_double_bits) {
-  __shared__ unsigned long long red[32];
-  unsigned long long mx = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long m = TAr<A>::mag(v[i]);
-    mx = m > mx ? m : mx;
-  }
-  mx = wmax(mx);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
-    mx = wmax(mx);
-    if (threadIdx.x == 0 && mx) {
-      const double d = sizeof(A) == 4 ? (double)__uint_as_float((unsigned)mx) : __longlong_as_double((long long)mx);
-      atomicMax(slot_double_bits, (unsigned long long)__double_as_longlong(d));
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -563,14 +723,28 @@ static void run_decomp(const DecompArgs& a0, cudaStream_t s) {
   k_tile_decomp<A, N, T0, T1, T2><<<(unsigned)nb, 256, smem, s>>>(a);
 }
 
+template <typename A, int VEC>
+static void run_decomp_blk(const DecompArgs& a0, cudaStream_t s) {
+  count_launch();
+  DecompArgs a = a0;
+  a.ntiles[0] = (a.cnt[0] + 3) / 4;
+  a.ntiles[1] = (a.cnt[1] + 3) / 4;
+  a.ntiles[2] = a.cnt[2] / VEC;
+  const int64_t items = a.ntiles[0] * a.ntiles[1] * a.ntiles[2];
+  if (items == 0) return;
+  k_decomp_blk<A, VEC><<<(unsigned)((items + 127) / 128), 128, 0, s>>>(a);
+}
+
 void launch_tile_decomp(int vk, const DecompArgs& a, cudaStream_t s) {
   // tiles are multiples of 4 along the in-slice axes
   if (vk == VK_F32) {
-    if (a.n == 2) run_decomp<float, 2, 16, 16, 32>(a, s);
+    if (a.n == 2 && a.cnt[2] % 4 == 0) run_decomp_blk<float, 4>(a, s);
+    else if (a.n == 2) run_decomp_blk<float, 1>(a, s);
     else if (a.n == 1) run_decomp<float, 1, 16, 4, 64>(a, s);
     else run_decomp<float, 0, 4, 16, 64>(a, s);
   } else {
-    if (a.n == 2) run_decomp<double, 2, 16, 16, 32>(a, s);
+    if (a.n == 2 && a.cnt[2] % 2 == 0) run_decomp_blk<double, 2>(a, s);
+    else if (a.n == 2) run_decomp_blk<double, 1>(a, s);
     else if (a.n == 1) run_decomp<double, 1, 16, 4, 64>(a, s);
     else run_decomp<double, 0, 4, 16, 64>(a, s);
   }
@@ -587,13 +761,5 @@ void launch_zero_pads(int vk, const LatD& lat, void* stage, cudaStream_t s) {
   else k_zero_pads<int64_t><<<g, 256, 0, s>>>(lat, (int64_t*)stage);
 }
 
-void launch_absmax(int vk, const void* v, int64_t n, unsigned long long* slot, cudaStream_t s) {
-  if (n <= 0) return;
-  count_launch();
-  int g = (int)((n + 255) / 256);
-  if (g > 148 * 4) g = 148 * 4;
-  if (vk == VK_F32) k_absmax<float><<<g, 256, 0, s>>>((const float*)v, n, slot);
-  else k_absmax<double><<<g, 256, 0, s>>>((const double*)v, n, slot);
-}
 
 }  // namespace pcr
