@@ -15,6 +15,7 @@
 //                          the tile (halo points recomputed, not exchanged)
 // Arithmetic: the rules of pcr_kernels.cu (identical expression trees).
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -664,6 +665,359 @@ __global__ void k_zero_pads(LatD lat, A* stage) {
 }
 
 // max |c| over a region's compact array (level-0 rounding term)
+__device__ __forceinline__ float fmax_abs(float m, float c) { return fmaxf(m, fabsf(c)); }
+__device__ __forceinline__ double fmax_abs(double m, double c) { return fmax(m, fabs(c)); }
+
+// ---------------------------------------------------------------------------
+// level-0 per-level interpolation, 3-D, pass order (0, 1, 2): plane marching
+// ---------------------------------------------------------------------------
+// Alg. 1 (per-level) at level 0 predicts region 1 (odd i0, even i1, even i2)
+// along axis 0 from the coarse grid, region 2 (odd i1, even i2) along axis 1
+// and region 3 (odd i2) along axis 2, each pass reading the earlier passes'
+// predictions.  Passes 2 and 3 stay inside one plane i0, and pass 1 reads
+// only the coarse points (even i0, i1, i2) of planes i0 +- 1, +- 3.  One CTA
+// owns a T1 x T2 column of the field and a chunk of planes, and walks the
+// planes in order:
+//   ring  : coarse values of the last four even planes over the column and
+//           its halo (the inputs of pass 1)
+//   Pe/Po : the current plane's values at even / odd i2 (tile + halo rows;
+//           even i2 values are replaced by predictions as the passes run)
+// The next plane's inputs (refactor: field rows and the coarse plane the
+// ring needs next; retrieve: decoded coefficients of every point) are
+// fetched into registers while the current plane's passes run.
+// Refactor: c = x - W is stored to each region's staging as it is computed.
+// Retrieve: the plane's reconstruction W + c_hat (coarse points: the ring)
+// is assembled in Xo and written back with full-row vector stores.
+// Region staging offsets use the level-0 lattices of this pass order:
+// region 1 starts (1,0,0) step (2,2,2), region 2 (0,1,0) step (1,2,2),
+// region 3 (0,0,1) step (1,1,2) (checked by the launcher).
+// Arithmetic: the 1-D rules of the general tile kernel (same expressions).
+template <typename A, int DEG, bool RET, int T1, int T2>
+__global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
+  constexpr int NT = 256;
+  constexpr int HR = DEG - 1;            // reach beyond the tile along i1, i2
+  constexpr int PR = T1 + 2 * HR + 1;    // Pe rows: i1 in [b1 - HR, b1 + T1 + HR]
+  constexpr int CE = T2 / 2 + DEG;       // even i2 in [b2 - HR, b2 + T2 + HR]
+  constexpr int PAD = (HR / 2) & 1;      // Pe column pad: 16-byte vectors land on aligned pairs
+  constexpr int CEP = (CE + PAD + 3) & ~3;
+  constexpr int CR = T1 / 2 + DEG;       // even i1 rows of the ring
+  constexpr int CO = T2 / 2;             // odd i2 in the tile (a power of two)
+  constexpr int VEC = 16 / sizeof(A);
+  constexpr int XL = 4;                  // loaded rows start 4 points before the tile (16-byte aligned)
+  constexpr int NV = (T2 + 2 * XL) / VEC;
+  constexpr int NLV = (PR * NV + NT - 1) / NT;        // plane vectors per thread
+  constexpr int N1 = (CR * CE + NT - 1) / NT;         // ring / pass-1 points per thread
+  constexpr int N2 = ((T1 / 2) * CE + NT - 1) / NT;   // pass-2 points per thread
+  constexpr int N3 = (T1 * CO) / NT;                  // pass-3 points per thread
+  static_assert((T1 * CO) % NT == 0 && (CO & (CO - 1)) == 0, "tile shape");
+
+  __shared__ __align__(16) A Pe[PR][CEP];
+  __shared__ __align__(16) A Po[RET ? 1 : T1][CO];
+  __shared__ __align__(16) A ring[4][CR][CE];
+  __shared__ __align__(16) A Xo[RET ? T1 : 1][RET ? T2 : 4];
+
+  const int m0 = (int)a.m[0], m1 = (int)a.m[1], m2 = (int)a.m[2];
+  const int64_t s0 = a.stride[0], s1 = a.stride[1];
+  unsigned bid = blockIdx.x;
+  const unsigned nt2 = (unsigned)a.ntiles[2], nt1 = (unsigned)a.ntiles[1];
+  const int b2 = (int)(bid % nt2) * T2;
+  bid /= nt2;
+  const int b1 = (int)(bid % nt1) * T1;
+  const int z0 = (int)(bid / nt1) * zc;
+  const int z1 = min(z0 + zc, m0);
+  const A* __restrict__ src = reinterpret_cast<const A*>(a.src);
+  A* __restrict__ dst = reinterpret_cast<A*>(a.dst);
+  const int tid = threadIdx.x;
+
+  A* __restrict__ g1 = reinterpret_cast<A*>(a.reg[0].stage);
+  A* __restrict__ g2 = reinterpret_cast<A*>(a.reg[1].stage);
+  A* __restrict__ g3 = reinterpret_cast<A*>(a.reg[2].stage);
+  const int64_t rp1 = a.reg[0].row_pad, rp2 = a.reg[1].row_pad, rp3 = a.reg[2].row_pad;
+  auto base1 = [&](int i0) { return a.reg[0].base + (int64_t)(i0 >> 1) * a.reg[0].count[1] * rp1; };
+  auto base2 = [&](int i0) { return a.reg[1].base + (int64_t)i0 * a.reg[1].count[1] * rp2; };
+  auto base3 = [&](int i0) { return a.reg[2].base + (int64_t)i0 * a.reg[2].count[1] * rp3; };
+  A mx1 = A(0), mx2 = A(0), mx3 = A(0);
+
+  // point sets of the passes (thread-strided)
+  auto p1pt = [&](int it, int& ci, int& cj, int& r, int& c) {
+    const int i = tid + NT * it;
+    ci = i / CE;
+    cj = i - ci * CE;
+    r = b1 - HR + 2 * ci;
+    c = b2 - HR + 2 * cj;
+    return i < CR * CE;
+  };
+  auto p2pt = [&](int it, int& ri, int& cj, int& r, int& c) {
+    const int i = tid + NT * it;
+    ri = i / CE;
+    cj = i - ri * CE;
+    r = b1 + 1 + 2 * ri;
+    c = b2 - HR + 2 * cj;
+    return i < (T1 / 2) * CE;
+  };
+  auto p3pt = [&](int it, int& ri, int& oj, int& r, int& c) {
+    const int i = tid + NT * it;
+    ri = i / CO;
+    oj = i & (CO - 1);
+    r = b1 + ri;
+    c = b2 + 1 + 2 * oj;
+  };
+  auto in_tile = [&](int r, int c) { return r >= b1 && r < b1 + T1 && c >= b2 && c < b2 + T2; };
+
+  // ---- prefetch registers
+  A rg[N1];                     // coarse values of one even plane (ring points)
+  VecT<A, VEC> pv[RET ? 1 : NLV];   // refactor: field rows of one plane
+  A h1[RET ? N1 : 1], h2[RET ? N2 : 1], h3[RET ? N3 : 1];   // retrieve: c_hat of one plane
+
+  auto fetch_ring = [&](int p) {
+#pragma unroll
+    for (int it = 0; it < N1; it++) {
+      int ci, cj, r, c;
+      const bool ok = p1pt(it, ci, cj, r, c) && p >= 0 && p < m0 && r >= 0 && r < m1 && c >= 0 && c < m2;
+      rg[it] = ok ? src[(int64_t)p * s0 + (int64_t)r * s1 + c] : A(0);
+    }
+  };
+  auto store_ring = [&](int p) {
+    if (p < 0 || p >= m0) return;
+    A(*rs)[CE] = ring[(p >> 1) & 3];
+#pragma unroll
+    for (int it = 0; it < N1; it++) {
+      int ci, cj, r, c;
+      if (p1pt(it, ci, cj, r, c)) rs[ci][cj] = rg[it];
+    }
+  };
+  auto fetch_plane = [&](int i0) {
+#pragma unroll
+    for (int it = 0; it < NLV; it++) {
+      const int i = tid + NT * it;
+      const int pr = i / NV, v = i - pr * NV;
+      const int r = b1 - HR + pr, c0 = b2 - XL + v * VEC;
+      const bool need = i < PR * NV && ((pr >= HR && pr < HR + T1) || !(r & 1)) && r >= 0 && r < m1 && i0 < m0;
+      if (need && c0 >= 0 && c0 + VEC <= m2) {
+        const A* gp = src + (int64_t)i0 * s0 + (int64_t)r * s1 + c0;
+        if constexpr (VEC == 4) {
+          const float4 t = __ldg(reinterpret_cast<const float4*>(gp));
+          pv[it].v[0] = t.x; pv[it].v[1] = t.y; pv[it].v[2] = t.z; pv[it].v[3] = t.w;
+        } else {
+          const double2 t = __ldg(reinterpret_cast<const double2*>(gp));
+          pv[it].v[0] = t.x; pv[it].v[1] = t.y;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < VEC; k++) {
+          const int c = c0 + k;
+          pv[it].v[k] = (need && c >= 0 && c < m2) ? src[(int64_t)i0 * s0 + (int64_t)r * s1 + c] : A(0);
+        }
+      }
+    }
+  };
+  auto store_plane = [&]() {
+#pragma unroll
+    for (int it = 0; it < NLV; it++) {
+      const int i = tid + NT * it;
+      const int pr = i / NV, v = i - pr * NV;
+      if (i >= PR * NV) continue;
+      const int r = b1 - HR + pr;
+      const bool rows = pr >= HR && pr < HR + T1;
+      if (!rows && (r & 1)) continue;
+      // element k sits at i2 = b2 - XL + VEC v + k: even k -> Pe, odd k -> Po
+      if constexpr (VEC == 4) {
+        const int ce = 2 * v - (XL - HR) / 2 + PAD;   // Pe column of element 0 (element 2: ce + 1)
+        if (ce >= 0 && ce + 1 < CE + PAD) {
+          *reinterpret_cast<float2*>(&Pe[pr][ce]) = make_float2(pv[it].v[0], pv[it].v[2]);
+        } else {
+          if (ce >= PAD && ce < CE + PAD) Pe[pr][ce] = pv[it].v[0];
+          if (ce + 1 >= PAD && ce + 1 < CE + PAD) Pe[pr][ce + 1] = pv[it].v[2];
+        }
+        const int co = 2 * v - XL / 2;                 // Po column of element 1 (element 3: co + 1)
+        if (rows && co >= 0 && co + 1 < CO) *reinterpret_cast<float2*>(&Po[pr - HR][co]) = make_float2(pv[it].v[1], pv[it].v[3]);
+      } else {
+        const int ce = v - (XL - HR) / 2 + PAD;       // element 0 (even)
+        if (ce >= PAD && ce < CE + PAD) Pe[pr][ce] = pv[it].v[0];
+        const int co = v - XL / 2;                    // element 1 (odd)
+        if (rows && co >= 0 && co < CO) Po[pr - HR][co] = pv[it].v[1];
+      }
+    }
+  };
+  auto fetch_chat = [&](int i0) {
+    if (i0 >= z1) return;
+    if (i0 & 1) {
+      const int64_t B1 = base1(i0);
+#pragma unroll
+      for (int it = 0; it < N1; it++) {
+        int ci, cj, r, c;
+        const bool ok = p1pt(it, ci, cj, r, c) && in_tile(r, c) && r < m1 && c < m2;
+        h1[it] = ok ? g1[B1 + (int64_t)(r >> 1) * rp1 + (c >> 1)] : A(0);
+      }
+    }
+    const int64_t B2 = base2(i0), B3 = base3(i0);
+#pragma unroll
+    for (int it = 0; it < N2; it++) {
+      int ri, cj, r, c;
+      const bool ok = p2pt(it, ri, cj, r, c) && in_tile(r, c) && r < m1 && c < m2;
+      h2[it] = ok ? g2[B2 + (int64_t)(r >> 1) * rp2 + (c >> 1)] : A(0);
+    }
+#pragma unroll
+    for (int it = 0; it < N3; it++) {
+      int ri, oj, r, c;
+      p3pt(it, ri, oj, r, c);
+      const bool ok = r < m1 && c < m2;
+      h3[it] = ok ? g3[B3 + (int64_t)r * rp3 + (c >> 1)] : A(0);
+    }
+  };
+
+  // warm-up: the ring holds planes z0 - 2, z0, z0 + 2 before the first odd
+  // plane; the first plane's inputs are in registers
+  fetch_ring(z0 - 2);
+  store_ring(z0 - 2);
+  fetch_ring(z0);
+  store_ring(z0);
+  fetch_ring(z0 + 2);
+  store_ring(z0 + 2);
+  if (!RET) fetch_plane(z0);
+  else fetch_chat(z0);
+
+  for (int i0 = z0; i0 < z1; i0++) {
+    const bool odd = i0 & 1;
+    // registers -> shared memory: this plane's rows, and (odd planes) the
+    // coarse plane i0 + 3 (the slot of plane i0 - 5)
+    if (!RET) store_plane();
+    if (odd) store_ring(i0 + 3);
+    A c1[RET ? N1 : 1], c2[RET ? N2 : 1], c3[RET ? N3 : 1];
+    if (RET) {
+#pragma unroll
+      for (int it = 0; it < N1; it++) c1[it] = h1[it];
+#pragma unroll
+      for (int it = 0; it < N2; it++) c2[it] = h2[it];
+#pragma unroll
+      for (int it = 0; it < N3; it++) c3[it] = h3[it];
+    }
+    __syncthreads();
+    // the next plane's inputs, in flight during this plane's passes
+    if (i0 + 1 < z1) {
+      if (!RET) fetch_plane(i0 + 1);
+      else fetch_chat(i0 + 1);
+      if (!odd) fetch_ring(i0 + 4);       // needed by plane i0 + 1
+    }
+    if (!odd && RET) {
+      // even plane: the coarse points are the reconstruction already
+      const A(*rs)[CE] = ring[(i0 >> 1) & 3];
+#pragma unroll
+      for (int it = 0; it < N1; it++) {
+        int ci, cj, r, c;
+        if (!p1pt(it, ci, cj, r, c)) continue;
+        Pe[2 * ci][cj + PAD] = rs[ci][cj];
+        if (in_tile(r, c)) Xo[r - b1][c - b2] = rs[ci][cj];
+      }
+      __syncthreads();
+    }
+    if (odd) {
+      // pass 1 along axis 0 over the even (i1, i2) points of tile + halo
+      const int64_t B1 = base1(i0);
+      const int sm3 = ((i0 - 3) >> 1) & 3, sm1 = ((i0 - 1) >> 1) & 3, sp1 = ((i0 + 1) >> 1) & 3,
+                sp3 = ((i0 + 3) >> 1) & 3;
+      const bool fast = DEG == 3 && i0 >= 3 && i0 + 3 < m0;
+#pragma unroll
+      for (int it = 0; it < N1; it++) {
+        int ci, cj, r, c;
+        if (!p1pt(it, ci, cj, r, c) || r < 0 || r >= m1 || c < 0 || c >= m2) continue;
+        A W;
+        if (fast) {
+          W = TAr<A>::cub(ring[sm3][ci][cj], ring[sm1][ci][cj], ring[sp1][ci][cj], ring[sp3][ci][cj]);
+        } else {
+          auto at = [&](int p) -> A { return ring[(p >> 1) & 3][ci][cj]; };
+          W = rule<A>(i0, m0, DEG, at);
+        }
+        if (in_tile(r, c)) {
+          if (!RET) {
+            const A cv = TAr<A>::sub(Pe[2 * ci][cj + PAD], W);
+            g1[B1 + (int64_t)(r >> 1) * rp1 + (c >> 1)] = cv;
+            mx1 = fmax_abs(mx1, cv);
+          } else {
+            Xo[r - b1][c - b2] = TAr<A>::add(W, c1[it]);
+          }
+        }
+        Pe[2 * ci][cj + PAD] = W;
+      }
+      __syncthreads();
+    }
+    // pass 2 along axis 1: odd i1 in the tile, even i2 over tile + halo
+    {
+      const int64_t B2 = base2(i0);
+#pragma unroll
+      for (int it = 0; it < N2; it++) {
+        int ri, cj, r, c;
+        if (!p2pt(it, ri, cj, r, c) || r >= m1 || c < 0 || c >= m2) continue;
+        const int pr = r - (b1 - HR);
+        A W;
+        if (DEG == 3 && r >= 3 && r + 3 < m1) {
+          W = TAr<A>::cub(Pe[pr - 3][cj + PAD], Pe[pr - 1][cj + PAD], Pe[pr + 1][cj + PAD], Pe[pr + 3][cj + PAD]);
+        } else {
+          auto at = [&](int k) -> A { return Pe[pr + (k - r)][cj + PAD]; };
+          W = rule<A>(r, m1, DEG, at);
+        }
+        if (c >= b2 && c < b2 + T2) {
+          if (!RET) {
+            const A cv = TAr<A>::sub(Pe[pr][cj + PAD], W);
+            g2[B2 + (int64_t)(r >> 1) * rp2 + (c >> 1)] = cv;
+            mx2 = fmax_abs(mx2, cv);
+          } else {
+            Xo[r - b1][c - b2] = TAr<A>::add(W, c2[it]);
+          }
+        }
+        Pe[pr][cj + PAD] = W;
+      }
+    }
+    __syncthreads();
+    // pass 3 along axis 2: odd i2 of the tile rows
+    {
+      const int64_t B3 = base3(i0);
+#pragma unroll
+      for (int it = 0; it < N3; it++) {
+        int ri, oj, r, c;
+        p3pt(it, ri, oj, r, c);
+        if (r >= m1 || c >= m2) continue;
+        const int pr = ri + HR;
+        const int cj = oj + HR / 2 + PAD;           // Pe column of c - 1
+        A W;
+        if (DEG == 3 && c >= 3 && c + 3 < m2) {
+          W = TAr<A>::cub(Pe[pr][cj - 1], Pe[pr][cj], Pe[pr][cj + 1], Pe[pr][cj + 2]);
+        } else {
+          auto at = [&](int k) -> A { return Pe[pr][cj + ((k - (c - 1)) >> 1)]; };
+          W = rule<A>(c, m2, DEG, at);
+        }
+        if (!RET) {
+          const A cv = TAr<A>::sub(Po[ri][oj], W);
+          g3[B3 + (int64_t)r * rp3 + (c >> 1)] = cv;
+          mx3 = fmax_abs(mx3, cv);
+        } else {
+          Xo[ri][c - b2] = TAr<A>::add(W, c3[it]);
+        }
+      }
+    }
+    if (RET) {
+      __syncthreads();
+      // full tile rows of the reconstructed plane
+      for (int i = tid; i < T1 * (T2 / VEC); i += NT) {
+        const int ri = i / (T2 / VEC), v = i - ri * (T2 / VEC);
+        const int r = b1 + ri, c0 = b2 + v * VEC;
+        if (r >= m1) continue;
+        A* gp = dst + (int64_t)i0 * s0 + (int64_t)r * s1 + c0;
+        const VecT<A, VEC> xv = *reinterpret_cast<const VecT<A, VEC>*>(&Xo[ri][v * VEC]);
+        if (c0 + VEC <= m2) vst<A, VEC>(gp, xv);
+        else
+          for (int k = 0; k < VEC && c0 + k < m2; k++) gp[k] = xv.v[k];
+      }
+    }
+    __syncthreads();
+  }
+  if (!RET) {
+    push_max(a.reg[0].vmax, TAr<A>::mag(mx1), sizeof(A));
+    push_max(a.reg[1].vmax, TAr<A>::mag(mx2), sizeof(A));
+    push_max(a.reg[2].vmax, TAr<A>::mag(mx3), sizeof(A));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -700,7 +1054,57 @@ static void run_tile_kind(const TileArgs& a, cudaStream_t s) {
   }
 }
 
+template <typename A, int DEG, bool RET, int T1, int T2>
+static void run_level0_march(const TileArgs& a0, cudaStream_t s) {
+  count_launch();
+  TileArgs a = a0;
+  a.ntiles[1] = (a.m[1] + T1 - 1) / T1;
+  a.ntiles[2] = (a.m[2] + T2 - 1) / T2;
+  // plane chunks: about eight full waves of 4 CTAs per SM, so the last wave
+  // is not a sparse tail; at least 8 planes so the ring warm-up (three
+  // coarse-plane loads) stays a small share of a chunk
+  const int64_t cols = a.ntiles[1] * a.ntiles[2];
+  const int64_t want = (148 * 4 * 8 + cols - 1) / cols;
+  int64_t zc = (a.m[0] + want - 1) / want;
+  zc = std::max<int64_t>(8, (zc + 1) & ~int64_t(1));
+  a.ntiles[0] = (a.m[0] + zc - 1) / zc;
+  static bool attr = false;
+  if (!attr) {   // shared memory for several CTAs per SM
+    cudaFuncSetAttribute(k_level0_march<A, DEG, RET, T1, T2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    attr = true;
+  }
+  k_level0_march<A, DEG, RET, T1, T2><<<(unsigned)(a.ntiles[0] * cols), 256, 0, s>>>(a, (int)zc);
+}
+
+// the plane-marching kernel covers level 0 of 3-D per-level schemes in a
+// contiguous field whose rows hold whole 16-byte vectors
+template <typename A>
+static bool level0_march(const TileArgs& a, cudaStream_t s) {
+  constexpr int VEC = 16 / sizeof(A);
+  if (a.d != 3 || a.interp != 0 || a.order[0] != 0 || a.order[1] != 1 || a.order[2] != 2) return false;
+  if (a.degree != 1 && a.degree != 3) return false;
+  if (a.stride[2] != 1 || a.stride[1] != a.m[2] || a.stride[0] != a.m[1] * a.m[2]) return false;
+  if (a.m[2] % VEC != 0 || ((uintptr_t)a.src % 16) != 0 || ((uintptr_t)a.dst % 16) != 0) return false;
+  // level-0 region lattices of pass order (0, 1, 2)
+  static const int64_t st[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  static const int64_t sp[3][3] = {{2, 2, 2}, {1, 2, 2}, {1, 1, 2}};
+  for (int r = 0; r < 3; r++)
+    for (int k = 0; k < 3; k++)
+      if (a.reg[r].start[k] != st[r][k] || a.reg[r].step[k] != sp[r][k]) return false;
+  constexpr int T1 = 16, T2 = sizeof(A) == 4 ? 128 : 64;
+  if (a.retrieve) {
+    if (a.degree == 3) run_level0_march<A, 3, true, T1, T2>(a, s);
+    else run_level0_march<A, 1, true, T1, T2>(a, s);
+  } else {
+    if (a.degree == 3) run_level0_march<A, 3, false, T1, T2>(a, s);
+    else run_level0_march<A, 1, false, T1, T2>(a, s);
+  }
+  return true;
+}
+
 void launch_tile_interp(int vk, const TileArgs& a, cudaStream_t s) {
+  if (vk == VK_F32 && level0_march<float>(a, s)) return;
+  if (vk == VK_F64 && level0_march<double>(a, s)) return;
   if (vk == VK_F32) run_tile_kind<float>(a, s);
   else if (vk == VK_F64) run_tile_kind<double>(a, s);
   else run_tile_kind<int64_t>(a, s);

@@ -39,6 +39,12 @@ CASES = [
     ((2, 3, 2), np.float32, dict(interp="level", degree="linear")),
     ((5, 5, 5), np.float32, dict(interp="region", degree="cubic", nlevels=1)),
     ((12, 10, 9), np.float32, dict(interp="level", degree="cubic", nplanes=6, nlevels=3)),
+    # rows of whole 16-byte vectors: level 0 runs the plane-marching kernel
+    # (ragged column tiles along both in-plane axes, several plane chunks)
+    ((37, 45, 260), np.float32, dict(interp="level", degree="cubic", decomp_axis=2)),
+    ((36, 33, 132), np.float32, dict(interp="level", degree="linear")),
+    ((18, 20, 66), np.float64, dict(interp="level", degree="cubic", decomp_axis=1)),
+    ((24, 17, 40), np.float32, dict(mode="psnr", interp="level", degree="cubic")),
 ]
 
 
