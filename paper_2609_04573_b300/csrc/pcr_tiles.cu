@@ -665,8 +665,26 @@ __global__ void k_zero_pads(LatD lat, A* stage) {
 }
 
 // max |c| over a region's compact array (level-0 rounding term)
-__device__ __forceinline__ float fmax_abs(float m, float c) { return fmaxf(m, fabsf(c)); }
-__device__ __forceinline__ double fmax_abs(double m, double c) { return fmax(m, fabs(c)); }
+// running maximum of |c|: floating point in the value type, fixed point as
+// an unsigned magnitude
+template <typename A> struct MaxAbs {
+  using T = A;
+  __device__ static T upd(T m, A c) { return fmax(m, fabs(c)); }
+  __device__ static unsigned long long bits(T m) { return TAr<A>::mag(m); }
+};
+template <> struct MaxAbs<float> {
+  using T = float;
+  __device__ static T upd(T m, float c) { return fmaxf(m, fabsf(c)); }
+  __device__ static unsigned long long bits(T m) { return TAr<float>::mag(m); }
+};
+template <> struct MaxAbs<int64_t> {
+  using T = unsigned long long;
+  __device__ static T upd(T m, int64_t c) {
+    const T g = TAr<int64_t>::mag(c);
+    return g > m ? g : m;
+  }
+  __device__ static unsigned long long bits(T m) { return m; }
+};
 
 // ---------------------------------------------------------------------------
 // level-0 per-level interpolation, 3-D, pass order (0, 1, 2): plane marching
@@ -736,7 +754,8 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
   auto base1 = [&](int i0) { return a.reg[0].base + (int64_t)(i0 >> 1) * a.reg[0].count[1] * rp1; };
   auto base2 = [&](int i0) { return a.reg[1].base + (int64_t)i0 * a.reg[1].count[1] * rp2; };
   auto base3 = [&](int i0) { return a.reg[2].base + (int64_t)i0 * a.reg[2].count[1] * rp3; };
-  A mx1 = A(0), mx2 = A(0), mx3 = A(0);
+  using MX = MaxAbs<A>;
+  typename MX::T mx1 = 0, mx2 = 0, mx3 = 0;
 
   // point sets of the passes (thread-strided)
   auto p1pt = [&](int it, int& ci, int& cj, int& r, int& c) {
@@ -795,13 +814,7 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
       const bool need = i < PR * NV && ((pr >= HR && pr < HR + T1) || !(r & 1)) && r >= 0 && r < m1 && i0 < m0;
       if (need && c0 >= 0 && c0 + VEC <= m2) {
         const A* gp = src + (int64_t)i0 * s0 + (int64_t)r * s1 + c0;
-        if constexpr (VEC == 4) {
-          const float4 t = __ldg(reinterpret_cast<const float4*>(gp));
-          pv[it].v[0] = t.x; pv[it].v[1] = t.y; pv[it].v[2] = t.z; pv[it].v[3] = t.w;
-        } else {
-          const double2 t = __ldg(reinterpret_cast<const double2*>(gp));
-          pv[it].v[0] = t.x; pv[it].v[1] = t.y;
-        }
+        vld<A, VEC>(pv[it], gp);
       } else {
 #pragma unroll
         for (int k = 0; k < VEC; k++) {
@@ -932,7 +945,7 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
           if (!RET) {
             const A cv = TAr<A>::sub(Pe[2 * ci][cj + PAD], W);
             g1[B1 + (int64_t)(r >> 1) * rp1 + (c >> 1)] = cv;
-            mx1 = fmax_abs(mx1, cv);
+            mx1 = MX::upd(mx1, cv);
           } else {
             Xo[r - b1][c - b2] = TAr<A>::add(W, c1[it]);
           }
@@ -960,7 +973,7 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
           if (!RET) {
             const A cv = TAr<A>::sub(Pe[pr][cj + PAD], W);
             g2[B2 + (int64_t)(r >> 1) * rp2 + (c >> 1)] = cv;
-            mx2 = fmax_abs(mx2, cv);
+            mx2 = MX::upd(mx2, cv);
           } else {
             Xo[r - b1][c - b2] = TAr<A>::add(W, c2[it]);
           }
@@ -989,7 +1002,7 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
         if (!RET) {
           const A cv = TAr<A>::sub(Po[ri][oj], W);
           g3[B3 + (int64_t)r * rp3 + (c >> 1)] = cv;
-          mx3 = fmax_abs(mx3, cv);
+          mx3 = MX::upd(mx3, cv);
         } else {
           Xo[ri][c - b2] = TAr<A>::add(W, c3[it]);
         }
@@ -1012,9 +1025,9 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
     __syncthreads();
   }
   if (!RET) {
-    push_max(a.reg[0].vmax, TAr<A>::mag(mx1), sizeof(A));
-    push_max(a.reg[1].vmax, TAr<A>::mag(mx2), sizeof(A));
-    push_max(a.reg[2].vmax, TAr<A>::mag(mx3), sizeof(A));
+    push_max(a.reg[0].vmax, MX::bits(mx1), sizeof(A));
+    push_max(a.reg[1].vmax, MX::bits(mx2), sizeof(A));
+    push_max(a.reg[2].vmax, MX::bits(mx3), sizeof(A));
   }
 }
 
@@ -1105,6 +1118,7 @@ static bool level0_march(const TileArgs& a, cudaStream_t s) {
 void launch_tile_interp(int vk, const TileArgs& a, cudaStream_t s) {
   if (vk == VK_F32 && level0_march<float>(a, s)) return;
   if (vk == VK_F64 && level0_march<double>(a, s)) return;
+  if (vk == VK_FIX && level0_march<int64_t>(a, s)) return;   // a contiguous fixed-point level (level 1)
   if (vk == VK_F32) run_tile_kind<float>(a, s);
   else if (vk == VK_F64) run_tile_kind<double>(a, s);
   else run_tile_kind<int64_t>(a, s);
