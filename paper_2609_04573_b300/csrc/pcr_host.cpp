@@ -789,6 +789,10 @@ struct pcr_handle {
   double m0_init = 0;
   std::vector<Step> m0;
   size_t plane_words = 0, sign_area_words = 0, scnt_words = 0, nz_words = 0;
+  // planner units ([0] l2, [1] L-infinity), built on first use from the tables
+  mutable std::mutex plan_mu;
+  mutable bool units_ok[2] = {false, false};
+  mutable std::vector<Unit> units[2];
   ~pcr_handle() {
     cudaStream_t s = 0;
     mem.free(d_planes, s);
@@ -1121,49 +1125,135 @@ std::vector<Unit> build_units(const pcr_handle* h, bool linf) {
   return units;
 }
 
+// planner units of a handle (the tables never change after construction)
+const std::vector<Unit>& cached_units(const pcr_handle* h, bool linf) {
+  std::lock_guard<std::mutex> lk(h->plan_mu);
+  if (!h->units_ok[linf]) {
+    h->units[linf] = build_units(h, linf);
+    h->units_ok[linf] = true;
+  }
+  return h->units[linf];
+}
+
+// L-infinity composition (Composer::linf) with the partial results of the
+// coarser levels kept: a step that changes streams of level l only needs
+// levels l .. 0 again.  Same operations in the same order as linf().
+struct LinfEval {
+  const Composer& c;
+  int L;
+  std::vector<std::vector<int>> ids;         // stream ids per level (stream order)
+  std::vector<double> E_in;                  // E entering each level for the current errors
+  mutable std::vector<std::pair<int, double>> reg;
+  explicit LinfEval(const Composer& comp) : c(comp), L(comp.m.L) {
+    ids.resize(L);
+    for (int l = 0; l < L; l++) ids[l] = c.by_level.at(l);
+    E_in.assign(L, 0.0);
+  }
+  void region_errors(int level, const std::vector<double>& err) const {
+    reg.clear();
+    for (int i : ids[level]) {
+      const int r = c.st[i].region;
+      bool found = false;
+      for (auto& pr : reg)
+        if (pr.first == r) {
+          pr.second = pr.second + err[i];
+          found = true;
+        }
+      if (!found) reg.push_back({r, 0.0 + err[i]});
+    }
+  }
+  double top(const std::vector<double>& err) const { return err[ids[L - 1][0]] + (L - 1 >= 1 ? c.m.h : 0.0); }
+  // bound with levels >= `from` as in E_in, levels < `from` from err;
+  // `keep` stores the E entering each recomputed level
+  double eval_from(int from, const std::vector<double>& err, bool keep) {
+    if (L == 1) return (top(err) + c.rho0(0.0, 0.0)) * kMargin;
+    double E;
+    int level;
+    if (from >= L - 1) {
+      E = top(err);
+      level = L - 2;
+    } else {
+      E = E_in[from];
+      level = from;
+    }
+    for (; level >= 0; level--) {
+      if (keep) E_in[level] = E;
+      region_errors(level, err);
+      const double rho = level == 0 ? c.rho0(E, Composer::sum_vals(reg)) : c.rho_fix;
+      E = c.level_step(E, reg, rho);
+    }
+    return E * kMargin;
+  }
+};
+
 // greedy interpreter: largest bound decrease per byte until the target holds
 bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, double& bound) {
   const int n = (int)h->tabs.size();
   b.assign(n, 0);
-  auto units = build_units(h, linf);
+  const std::vector<Unit>& units = cached_units(h, linf);
   std::vector<size_t> pos(units.size(), 0);
-  auto evaluate = [&](const std::vector<int>& bb) {
-    std::vector<double> err(n), sq(n);
-    for (int i = 0; i < n; i++) err[i] = h->tabs[i].maxerr[bb[i]];
-    if (linf) return h->comp.linf(err);
-    for (int i = 0; i < n; i++) sq[i] = h->tabs[i].sq[bb[i]];
+  std::vector<double> err(n), sq(n);
+  for (int i = 0; i < n; i++) {
+    err[i] = h->tabs[i].maxerr[0];
+    sq[i] = h->tabs[i].sq[0];
+  }
+  LinfEval le(h->comp);
+  std::vector<int> unit_level(units.size());
+  for (size_t ui = 0; ui < units.size(); ui++) unit_level[ui] = h->geo[units[ui].ids[0]].level;
+  auto evaluate = [&](int level, bool keep) {
+    if (linf) return le.eval_from(level, err, keep);
     return h->comp.l2(sq, err);
   };
-  auto unit_value = [&](const Unit& u, const std::vector<int>& bb) {
-    if (u.ids.size() == 1) return linf ? h->tabs[u.ids[0]].maxerr[bb[u.ids[0]]] : h->tabs[u.ids[0]].sq[bb[u.ids[0]]];
-    std::vector<std::pair<int, double>> reg;
+  std::vector<std::pair<int, double>> reg;
+  auto unit_value = [&](const Unit& u) {
+    if (u.ids.size() == 1) return linf ? err[u.ids[0]] : sq[u.ids[0]];
+    reg.clear();
     for (int i : u.ids) {
       const int r = h->geo[i].region;
       bool found = false;
       for (auto& pr : reg)
         if (pr.first == r) {
-          pr.second = pr.second + h->tabs[i].maxerr[bb[i]];
+          pr.second = pr.second + err[i];
           found = true;
         }
-      if (!found) reg.push_back({r, 0.0 + h->tabs[i].maxerr[bb[i]]});
+      if (!found) reg.push_back({r, 0.0 + err[i]});
     }
     double mx = reg[0].second;
     for (auto& pr : reg) mx = std::max(mx, pr.second);
     return mx;
   };
-  bound = evaluate(b);
+  // set the errors of one step's streams (returns the previous planes)
+  std::vector<std::pair<int, int>> saved;
+  auto apply = [&](const Step& st) {
+    saved.clear();
+    for (auto& up : st.upd) {
+      saved.push_back({up.first, b[up.first]});
+      b[up.first] = up.second;
+      err[up.first] = h->tabs[up.first].maxerr[up.second];
+      sq[up.first] = h->tabs[up.first].sq[up.second];
+    }
+  };
+  auto undo = [&]() {
+    for (auto it = saved.rbegin(); it != saved.rend(); ++it) {
+      b[it->first] = it->second;
+      err[it->first] = h->tabs[it->first].maxerr[it->second];
+      sq[it->first] = h->tabs[it->first].sq[it->second];
+    }
+  };
+  bound = evaluate(h->L - 1, true);
   while (bound > target) {
     bool have_best = false, have_fb = false;
     double best_r = 0, fb_r = 0, best_bnd = 0, fb_bnd = 0;
     size_t best_u = 0, fb_u = 0;
-    std::vector<int> best_b, fb_b;
     for (size_t ui = 0; ui < units.size(); ui++) {
       const Unit& u = units[ui];
       if (pos[ui] >= u.steps.size()) continue;
       const Step& st = u.steps[pos[ui]];
-      std::vector<int> trial = b;
-      for (auto& up : st.upd) trial[up.first] = up.second;
-      const double nb = evaluate(trial);
+      const double own0 = unit_value(u);
+      apply(st);
+      const double nb = evaluate(unit_level[ui], false);
+      const double own1 = unit_value(u);
+      undo();
       const double gain = bound - nb;
       const double inf = std::numeric_limits<double>::infinity();
       const double ratio = st.db == 0 ? inf : gain / (double)st.db;
@@ -1172,27 +1262,25 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
           have_best = true;
           best_r = ratio;
           best_u = ui;
-          best_b = trial;
           best_bnd = nb;
         }
       }
-      const double own = (unit_value(u, b) - unit_value(u, trial)) * u.weight;
+      const double own = (own0 - own1) * u.weight;
       const double fr = st.db == 0 ? inf : own / (double)st.db;
       if (!have_fb || fr > fb_r) {
         have_fb = true;
         fb_r = fr;
         fb_u = ui;
-        fb_b = trial;
         fb_bnd = nb;
       }
     }
     if (!have_best) {
       if (!have_fb) return false;
       best_u = fb_u;
-      best_b = fb_b;
       best_bnd = fb_bnd;
     }
-    b = best_b;
+    apply(units[best_u].steps[pos[best_u]]);
+    if (linf) le.eval_from(unit_level[best_u], err, true);   // refresh the kept partial results
     bound = best_bnd;
     pos[best_u]++;
   }
