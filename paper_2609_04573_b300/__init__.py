@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libpcr.so")
 if not os.path.exists(_LIB_PATH):
     raise ImportError(
-        f"{_LIB_PATH} is missing: build it with `python -m paper_2609_04573_b300.build` "
+        f"{_LIB_PATH} is missing: build it with `python paper_2609_04573_b300/build.py` "
         "(nvcc, sm_103a).  There is no CPU fallback.")
 _lib = C.CDLL(_LIB_PATH)
 

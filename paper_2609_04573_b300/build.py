@@ -33,17 +33,20 @@ def needs_build():
 def build(force=False, verbose=False):
     if not force and not needs_build():
         return LIB
-    objs = []
+    objs, procs = [], []
     builddir = os.path.join(HERE, "_build")
     os.makedirs(builddir, exist_ok=True)
-    for src in SOURCES:
+    for src in SOURCES:   # the sources compile independently: run them side by side
         obj = os.path.join(builddir, src + ".o")
         cmd = [_nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.append("-Xptxas=-v") if src.endswith(".cu") else None
             print(" ".join(cmd))
-        subprocess.run(cmd, check=True)
+        procs.append((src, subprocess.Popen(cmd)))
         objs.append(obj)
+    failed = [src for src, p in procs if p.wait() != 0]
+    if failed:
+        raise RuntimeError(f"nvcc failed on {', '.join(failed)}")
     tmp = LIB + ".tmp"
     subprocess.run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], check=True)
     os.replace(tmp, LIB)
