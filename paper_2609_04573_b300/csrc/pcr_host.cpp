@@ -82,6 +82,21 @@ struct ProfRec {
 };
 std::vector<ProfRec> g_prof_recs;
 std::map<std::string, std::pair<double, long long>> g_prof_tot;
+std::vector<cudaEvent_t> g_prof_pool;   // events returned by pcr_profile_read, reused
+
+cudaEvent_t prof_event() {
+  {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    if (!g_prof_pool.empty()) {
+      cudaEvent_t e = g_prof_pool.back();
+      g_prof_pool.pop_back();
+      return e;
+    }
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
 
 struct Prof {
   const char* name;
@@ -89,13 +104,13 @@ struct Prof {
   cudaEvent_t a = nullptr;
   long long c0;
   Prof(const char* n, cudaStream_t st) : name(n), s(st), c0(launch_count()) {
-    if (g_prof_on && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
+    if (g_prof_on && (a = prof_event())) cudaEventRecord(a, s);
   }
   ~Prof() {
     const long long dl = launch_count() - c0;
     if (!a) return;
-    cudaEvent_t b;
-    if (cudaEventCreate(&b) != cudaSuccess) return;
+    cudaEvent_t b = prof_event();
+    if (!b) return;
     cudaEventRecord(b, s);
     std::lock_guard<std::mutex> g(g_prof_mu);
     g_prof_recs.push_back({name, a, b, dl});
@@ -120,8 +135,8 @@ extern "C" pcr_status pcr_profile_read(int max_entries, char* names, double* ms,
     auto& acc = g_prof_tot[r.name];
     acc.first += t;
     acc.second += r.launches;
-    cudaEventDestroy(r.a);
-    cudaEventDestroy(r.b);
+    g_prof_pool.push_back(r.a);
+    g_prof_pool.push_back(r.b);
   }
   g_prof_recs.clear();
   int k = 0;
