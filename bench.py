@@ -43,7 +43,7 @@ TRAFFIC_PER_LAUNCH = {}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pcr", choices=["pcr", "reference"])
     ap.add_argument("--size", type=int, default=512, help="cube edge (default 512)")
@@ -62,7 +62,11 @@ def dist_env():
 
 
 class Clocks:
-    """nvidia-smi samples during the timed region."""
+    """nvidia-smi samples during the timed region.
+
+    Each query stalls this process's CUDA calls for tens of milliseconds, so
+    the sampler polls every 500 ms and the default timed region (200 steps,
+    about a second) holds a few samples at a few percent of its time."""
 
     def __init__(self, index):
         self.index = index
@@ -76,7 +80,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "500"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
