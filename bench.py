@@ -36,8 +36,10 @@ WORKLOAD = "grf_k-5/3_512^3_f32"
 METRIC = "refactor & retrieve GB/s (fraction of HBM roofline) at stated eb/PSNR vs CPU oracle"
 
 # DRAM traffic per launch of the dominant kernel, from the committed ncu
-# summary (profiles/); None when the kernel changed after that capture.
-TRAFFIC_PER_LAUNCH = {}
+# summary (profiles/encode_float_grf384.md: 357.9 MB at 384^3, scaled by the
+# level-0 value count to 512^3); absent when the kernel changed after that
+# capture or the run's size differs.
+TRAFFIC_PER_LAUNCH = {("encode_float", 512): 849.0e6}
 
 
 def parse():
@@ -237,7 +239,7 @@ def run_pcr(args):
     dom_ms = prof[dom][0] / max(prof[dom][1], 1)         # per launch
     achieved = algo["per_launch"] / (dom_ms * 1e-3) / 1e9 if algo["per_launch"] else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": (achieved / hbm) if achieved else None, "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+            "frac": (achieved / hbm) if achieved else None, "traffic": TRAFFIC_PER_LAUNCH.get((dom, args.size)),
             "algorithmic_bytes_per_launch": algo["per_launch"], "ms_per_launch": dom_ms,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not pk.get("fallback") else "fallback"}
     refactor_ms = sum(v[0] for k, v in prof.items() if k in REFACTOR_STAGES) / psteps
