@@ -864,6 +864,65 @@ __global__ void __launch_bounds__(kThreads) k_encode(const StreamD* __restrict__
   }
 }
 
+// per-lane constants of the warp bit transpose (hoisted out of word loops):
+// byte permutes for the 16- and 8-bit stages, and for the 4-, 2- and 1-bit
+// stages a rotation of the partner's word plus one masked merge
+struct TrC {
+  uint32_t sel16, sel8;
+  uint32_t ml[3], sh[3];
+};
+__device__ __forceinline__ TrC tr_consts(int lane) {
+  TrC c;
+  c.sel16 = (lane & 16) ? 0x3276u : 0x5410u;
+  c.sel8 = (lane & 8) ? 0x3715u : 0x6240u;
+#pragma unroll
+  for (int s = 0; s < 3; s++) {
+    const int j = 4 >> s;
+    const uint32_t m = j == 4 ? 0x0F0F0F0Fu : j == 2 ? 0x33333333u : 0x55555555u;
+    const bool lower = (lane & j) == 0;
+    c.ml[s] = lower ? m : ~m;
+    c.sh[s] = lower ? j : 32 - j;
+  }
+  return c;
+}
+// the same transpose as transpose32 (bit k of lane e <-> bit e of lane k)
+__device__ __forceinline__ uint32_t transpose32c(uint32_t x, const TrC& c) {
+  uint32_t y = __shfl_xor_sync(FULL, x, 16);
+  x = __byte_perm(x, y, c.sel16);
+  y = __shfl_xor_sync(FULL, x, 8);
+  x = __byte_perm(x, y, c.sel8);
+#pragma unroll
+  for (int s = 0; s < 3; s++) {
+    y = __shfl_xor_sync(FULL, x, 4 >> s);
+    const uint32_t yy = __funnelshift_l(y, y, c.sh[s]);
+    x = (x & c.ml[s]) | (yy & ~c.ml[s]);
+  }
+  return x;
+}
+
+// Generic-encoding sign rank of one word from its plane words (lane k holds
+// plane k): F_k = the elements whose leading one is in plane k (plane bits
+// not covered by a more significant plane, an exclusive prefix OR over the
+// lanes).  The element's rank within its plane is the warp's count of
+// earlier words' elements of that plane (ctr, held by the plane's lane) plus
+// the lanes below it in F_p.  Same ranks as sign_record, without match.any
+// (used by the decoder; the encoder measured faster with sign_record).
+__device__ __forceinline__ uint32_t sign_rank32(uint32_t d, int p, bool neg, int B, uint32_t& ctr, int lane,
+                                                uint32_t lt) {
+  uint32_t incl = d;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(FULL, incl, o);
+    incl |= lane >= o ? t : 0u;
+  }
+  uint32_t excl = __shfl_up_sync(FULL, incl, 1);
+  excl = lane ? excl : 0u;
+  const uint32_t F = d & ~excl;
+  const uint32_t fp = __shfl_sync(FULL, F, p & 31), cp = __shfl_sync(FULL, ctr, p & 31);
+  ctr += __popc(F);
+  return p < B ? ((uint32_t)p | ((cp + __popc(fp & lt)) << 7) | ((uint32_t)neg << 20)) : 0xFFFFFFFFu;
+}
+
 // Decode one (stream, segment) per CTA: planes < b (zero-fill below).
 template <typename VT, int W>
 __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__ streams,
@@ -905,9 +964,23 @@ __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__
       pbuf[k][j] = s.plane_nz[k] ? s.planes[(int64_t)k * s.words + w0 + j] : 0u;
     }
   }
-  for (int i = threadIdx.x; i < kWarps * NP; i += kThreads) (&wcnt[0][0])[i] = 0;
+  if (W == 64)
+    for (int i = threadIdx.x; i < kWarps * NP; i += kThreads) (&wcnt[0][0])[i] = 0;
   if (generic) {
-    if (threadIdx.x == 0) {
+    if (W == 32) {
+      if (threadIdx.x < 32) {   // first sign word of each plane: prefix of the planes' word counts
+        const int k = threadIdx.x;
+        const uint32_t words = k < B ? (s.sign_counts[(int64_t)it.seg * B + k] + 31) >> 5 : 0u;
+        uint32_t inc = words;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(FULL, inc, o);
+          inc += k >= o ? t : 0u;
+        }
+        poff[k] = inc - words;
+        if (k == 31) poff[32] = inc;
+      }
+    } else if (threadIdx.x == 0) {
       uint32_t o = 0;
       for (int k = 0; k < B; k++) {
         poff[k] = o;
@@ -923,6 +996,9 @@ __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__
 
   code_t<W> qs[kWordsPerWarp];
   uint32_t rec[kWordsPerWarp];
+  const TrC tc = tr_consts(lane);
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t ctr = 0;
   uint4 gl = make_uint4(0u, 0u, 0u, 0u), gh = gl;   // plane words of 4 consecutive words
 #pragma unroll
   for (int jj = 0; jj < kWordsPerWarp; jj++) {
@@ -957,15 +1033,19 @@ __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__
     }
     code_t<W> q;
     if (W == 32) {
-      q = (code_t<W>)(__brev(transpose32(xl, lane)) >> (32 - B));
+      q = (code_t<W>)(__brev(transpose32c(xl, tc)) >> (32 - B));
     } else {
       const uint64_t lo = transpose32(xl, lane), hi = transpose32(xh, lane);
       q = (code_t<W>)(__brevll((unsigned long long)(lo | (hi << 32))) >> (64 - B));
     }
     qs[jj] = q;
-    if (generic) rec[jj] = sign_record(msb_plane<W>(q, B), false, B, wcnt[warp], lane);
+    if (generic) {
+      if constexpr (W == 32) rec[jj] = sign_rank32(xl, msb_plane<W>(q, B), false, B, ctr, lane, lt);
+      else rec[jj] = sign_record(msb_plane<W>(q, B), false, B, wcnt[warp], lane);
+    }
   }
   if (generic) {
+    if (W == 32) wcnt[warp][lane] = ctr;
     __syncthreads();
     if (threadIdx.x < NP) {
       uint32_t acc = 0;
