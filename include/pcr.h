@@ -137,6 +137,52 @@ pcr_status pcr_refactor_batch(int n, const void* const* d_fields, const int* ndi
                               const pcr_scheme* schemes, const pcr_allocator* alloc,
                               void* cuda_stream, pcr_handle** outs);
 
+/* ---- batched refactor captured in one CUDA graph (spec batching) --
+ * For batches refactored again and again with the same shapes (variables of
+ * successive timesteps): the whole batch -- every kernel, memset and the
+ * small uploads and read-backs -- is captured once into one CUDA graph and
+ * each run is one graph launch plus the host finish of the tables.
+ * create: arguments as pcr_refactor_batch.  The fields stay at these device
+ *   addresses for the graph's lifetime; the caller refills them between
+ *   runs.  Creation refactors the batch once uncaptured (with the level
+ *   autotuner on, see pcr_autotune_enable, and measuring the scratch it
+ *   needs), allocates one scratch arena through `alloc` and pinned host
+ *   staging, captures on a stream of its own and instantiates; it
+ *   synchronises `cuda_stream`.  The handles are valid after create.
+ * run: launches the graph on `cuda_stream`, synchronises it and rebuilds
+ *   every handle's tables from the new data.
+ * handle: the k-th handle, owned by the graph (do not pcr_free it); valid
+ *   until pcr_refactor_graph_free, its contents replaced by every run.
+ * info: graph nodes, kernels per run, scratch arena bytes (any may be NULL).
+ * Errors: as pcr_refactor_batch; PCR_ERR_CUDA when capture or instantiation
+ *   fails. */
+typedef struct pcr_refactor_graph pcr_refactor_graph;
+pcr_status pcr_refactor_graph_create(int n, const void* const* d_fields, const int* ndims,
+                                     const int64_t* const* dims, const int* dtypes,
+                                     const pcr_scheme* schemes, const pcr_allocator* alloc,
+                                     void* cuda_stream, pcr_refactor_graph** out);
+pcr_status pcr_refactor_graph_run(pcr_refactor_graph* g, void* cuda_stream);
+pcr_status pcr_refactor_graph_handle(const pcr_refactor_graph* g, int k, const pcr_handle** out);
+pcr_status pcr_refactor_graph_info(const pcr_refactor_graph* g, int64_t* nodes, int64_t* kernels,
+                                   int64_t* arena_bytes);
+void pcr_refactor_graph_free(pcr_refactor_graph* g);
+
+/* ---- autotuner of the level-interpolation schedule (spec tuning;
+ * the paper tunes its interpolation choices, Sec. VI-A, but not GPU tiles) -
+ * Where a level can run either the general tile kernel or the plane-marching
+ * kernel, and the marching kernel's plane chunk sets its grid, all choices
+ * compute identical values.  enable(1): the first launch of an untuned
+ * (value kind, direction, degree, level grid) on a stream that is not being
+ * captured times every candidate with CUDA events and keeps the fastest;
+ * later launches use the table (enable(0) keeps using it without adding).
+ * read: up to max_entries entries, keys = 6 int64 per entry (value kind
+ * PCR-internal 0 f32 / 1 f64 / 2 fixed point, retrieve 0/1, degree, level
+ * grid lengths m0, m1, m2), choice (0 general tile kernel, -1 marching with
+ * the default chunk, k > 0 marching with k-plane chunks), ms (the winner's
+ * time); *n_out = entries in the table; reset clears it afterwards. */
+pcr_status pcr_autotune_enable(int enable);
+pcr_status pcr_autotune_read(int max_entries, int64_t* keys, int* choice, double* ms, int* n_out, int reset);
+
 /* ---- plan (retrieval interpreter, Sec. V-C / VI-B) -------------------- */
 /* Host only.  Greedy selection of planes meeting `target`; returns
  * PCR_ERR_UNSATISFIABLE (plan still filled with all planes) when the bound

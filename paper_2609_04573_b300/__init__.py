@@ -90,6 +90,14 @@ _sigs = {
     "pcr_deserialize": [_vp, C.c_size_t, C.POINTER(_Allocator), _vp, C.POINTER(_vp)],
     "pcr_debug_encode": [_vp, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
                          C.POINTER(C.c_double)],
+    "pcr_refactor_graph_create": [C.c_int, C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(_i64p),
+                                  C.POINTER(C.c_int), C.POINTER(_Scheme), C.POINTER(_Allocator), _vp,
+                                  C.POINTER(_vp)],
+    "pcr_refactor_graph_run": [_vp, _vp],
+    "pcr_refactor_graph_handle": [_vp, C.c_int, C.POINTER(_vp)],
+    "pcr_refactor_graph_info": [_vp, _i64p, _i64p, _i64p],
+    "pcr_autotune_enable": [C.c_int],
+    "pcr_autotune_read": [C.c_int, _i64p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int],
 }
 for _name, _args in _sigs.items():
     fn = getattr(_lib, _name)
@@ -104,6 +112,8 @@ _lib.pcr_launch_count.argtypes = []
 _lib.pcr_launch_count.restype = C.c_int64
 _lib.pcr_free.argtypes = [_vp]
 _lib.pcr_free.restype = None
+_lib.pcr_refactor_graph_free.argtypes = [_vp]
+_lib.pcr_refactor_graph_free.restype = None
 _lib.pcr_buffer_free.argtypes = [_vp]
 _lib.pcr_buffer_free.restype = None
 _lib.pcr_last_error.argtypes = []
@@ -111,7 +121,7 @@ _lib.pcr_last_error.restype = C.c_char_p
 
 # exported symbols (checked by the CPU tests against include/pcr.h)
 EXPORTS = sorted(list(_sigs) + ["pcr_free", "pcr_buffer_free", "pcr_last_error", "pcr_profile_enable",
-                                "pcr_profile_read", "pcr_launch_count"])
+                                "pcr_profile_read", "pcr_launch_count", "pcr_refactor_graph_free"])
 
 
 def _check(st):
@@ -213,14 +223,15 @@ def _stream_ptr(stream):
 class Handle:
     """Refactored field: device streams + host tables (owned by the library)."""
 
-    def __init__(self, ptr, shape, dtype, device):
+    def __init__(self, ptr, shape, dtype, device, owner=None):
         self._p = C.c_void_p(ptr)
         self.shape = tuple(shape)
         self.dtype = dtype
         self.device = device
+        self._owner = owner   # a RefactorGraph owns its handles; keep it alive
 
     def __del__(self):
-        if getattr(self, "_p", None) and self._p.value:
+        if getattr(self, "_owner", None) is None and getattr(self, "_p", None) and self._p.value:
             _lib.pcr_free(self._p)
             self._p = C.c_void_p(None)
 
@@ -351,6 +362,73 @@ def refactor_batch(xs: Sequence[torch.Tensor], schemes, stream=None):
     _check(_lib.pcr_refactor_batch(n, ptrs, nd, dims, dts, sch, C.byref(_ALLOCATOR),
                                    _stream_ptr(stream), outs))
     return [Handle(outs[i], x.shape, x.dtype, x.device) for i, x in enumerate(xs)]
+
+
+def _batch_args(xs, schemes):
+    n = len(xs)
+    if not isinstance(schemes, (list, tuple)):
+        schemes = [schemes] * n
+    ptrs = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    nd = (C.c_int * n)(*[x.dim() for x in xs])
+    dim_arrs = [(C.c_int64 * x.dim())(*x.shape) for x in xs]
+    dims = (_i64p * n)(*[C.cast(d, _i64p) for d in dim_arrs])
+    dts = (C.c_int * n)(*[_DT[x.dtype] for x in xs])
+    sch = (_Scheme * n)(*[s.c(x.dim()) for s, x in zip(schemes, xs)])
+    return n, ptrs, nd, dims, dim_arrs, dts, sch
+
+
+class RefactorGraph:
+    """A batch refactored again and again with the same shapes, captured in
+    one CUDA graph (pcr_refactor_graph_*).  The tensors `xs` stay where they
+    are for the graph's lifetime: refill them in place, then call run().
+    Creation refactors once (autotuning the level schedule) so `handles` are
+    valid right away; every run replaces their contents."""
+
+    def __init__(self, xs: Sequence[torch.Tensor], schemes, stream=None):
+        for x in xs:
+            if not (x.is_cuda and x.is_contiguous() and x.dtype in _DT and x.dim() in (2, 3)):
+                raise ValueError("RefactorGraph expects contiguous 2-D/3-D float32/float64 CUDA tensors")
+        self._xs = list(xs)
+        n, ptrs, nd, dims, _keep, dts, sch = _batch_args(xs, schemes)
+        self._g = C.c_void_p()
+        _check(_lib.pcr_refactor_graph_create(n, ptrs, nd, dims, dts, sch, C.byref(_ALLOCATOR),
+                                              _stream_ptr(stream), C.byref(self._g)))
+        self.handles = []
+        for i, x in enumerate(xs):
+            hp = C.c_void_p()
+            _check(_lib.pcr_refactor_graph_handle(self._g, i, C.byref(hp)))
+            self.handles.append(Handle(hp.value, x.shape, x.dtype, x.device, owner=self))
+
+    def run(self, stream=None):
+        _check(_lib.pcr_refactor_graph_run(self._g, _stream_ptr(stream)))
+        return self.handles
+
+    def info(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(_lib.pcr_refactor_graph_info(self._g, C.byref(a), C.byref(b), C.byref(c)))
+        return {"nodes": a.value, "kernels": b.value, "arena_bytes": c.value}
+
+    def __del__(self):
+        if getattr(self, "_g", None) and self._g.value:
+            _lib.pcr_refactor_graph_free(self._g)
+            self._g = C.c_void_p(None)
+
+
+def autotune(enable=True):
+    """Level-schedule autotuner on/off (pcr_autotune_enable)."""
+    _check(_lib.pcr_autotune_enable(1 if enable else 0))
+
+
+def autotune_table(reset=False):
+    """Tuned entries: {(kind, retrieve, degree, m0, m1, m2): (choice, ms)}."""
+    n = C.c_int()
+    _check(_lib.pcr_autotune_read(0, None, None, None, C.byref(n), 0))
+    k = n.value
+    keys = (C.c_int64 * (6 * max(k, 1)))()
+    ch = (C.c_int * max(k, 1))()
+    ms = (C.c_double * max(k, 1))()
+    _check(_lib.pcr_autotune_read(k, keys, ch, ms, C.byref(n), 1 if reset else 0))
+    return {tuple(keys[6 * i:6 * i + 6]): (ch[i], ms[i]) for i in range(min(k, n.value))}
 
 
 def retrieve_batch(handles, plans, outs, stream=None):

@@ -1400,7 +1400,9 @@ struct Scratch {
   std::vector<void*> ptrs;
   char* bump = nullptr;
   size_t cap = 0, off = 0;
+  size_t* measure = nullptr;   // when set: bytes a bump carve of the same requests would need
   void* get(size_t bytes) {
+    if (measure) *measure = ((*measure + 255) & ~size_t(255)) + bytes;
     if (bump) {
       const size_t o = (off + 255) & ~size_t(255);
       if (o + bytes > cap) return nullptr;
@@ -1594,59 +1596,84 @@ struct BatchDev {
   unsigned long long* pairs;
 };
 
-extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, const int* ndims,
-                                         const int64_t* const* dims, const int* dtypes, const pcr_scheme* schemes,
-                                         const pcr_allocator* alloc, void* cuda_stream, pcr_handle** outs) {
-  if (n <= 0 || !d_fields || !ndims || !dims || !dtypes || !schemes || !outs)
-    return fail(PCR_ERR_INVALID_ARG, "null argument");
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  std::vector<std::unique_ptr<pcr_handle>> hs(n);
-  Mem mem = make_mem(alloc);
-  for (int k = 0; k < n; k++) {
-    pcr_status e = validate(d_fields[k], ndims[k], dims[k], dtypes[k], &schemes[k]);
-    if (e) return e;
-    hs[k].reset(new pcr_handle());
-    hs[k]->mem = mem;
-    e = setup_handle(hs[k].get(), ndims[k], dims[k], dtypes[k], &schemes[k]);
-    if (e) return e;
-    e = alloc_handle_buffers(hs[k].get(), s);
-    if (e) return e;
+// ---------------------------------------------------------------------------
+// batched refactor: one work list per encode kind for the whole batch
+// ---------------------------------------------------------------------------
+// Offsets of each field's statistics in the batch's device blocks.
+struct BatchLayout {
+  std::vector<size_t> vm_off, pr_off, nz_off;
+  size_t nv = 0, npairs = 0, nnz = 0;
+  explicit BatchLayout(const std::vector<pcr_handle*>& hs) {
+    for (pcr_handle* h : hs) {
+      vm_off.push_back(nv);
+      nv += h->geo.size();
+      pr_off.push_back(npairs);
+      if (h->sch.mode == PCR_MODE_PSNR) npairs += h->geo.size() * h->B * h->B;
+      nz_off.push_back(nnz);
+      nnz += h->nz_words;
+    }
   }
-  Scratch sc{&mem, s, {}};
-  // one block of device statistics for the whole batch
-  std::vector<size_t> vm_off(n), pr_off(n);
-  size_t nv = 0, npairs = 0;
-  for (int k = 0; k < n; k++) {
-    vm_off[k] = nv;
-    nv += hs[k]->geo.size();
-    pr_off[k] = npairs;
-    if (hs[k]->sch.mode == PCR_MODE_PSNR) npairs += hs[k]->geo.size() * hs[k]->B * hs[k]->B;
-  }
+};
+
+// Host side of the batch's copies: the sources of the uploads (statistics
+// initialisers, stream descriptors, work items) and the destinations of the
+// read-backs.  Pageable vectors for a one-off call; for a captured graph the
+// same roles are played by pinned buffers that outlive the graph (`pinned`).
+struct BatchStage {
+  bool pinned = false;
+  FieldStats* st_init = nullptr;
+  StreamD* sd = nullptr;
+  WorkItem* items = nullptr;
+  size_t cap_sd = 0, cap_items = 0;
+  FieldStats* st = nullptr;
+  unsigned long long* vm = nullptr;
+  uint64_t* pairs = nullptr;
+  uint32_t* nz = nullptr;
+  // pageable storage
+  std::vector<FieldStats> v_init, v_st;
+  std::vector<StreamD> v_sd;
+  std::vector<WorkItem> v_items;
+  std::vector<unsigned long long> v_vm;
+  std::vector<uint64_t> v_pairs;
+  std::vector<uint32_t> v_nz;
+  size_t used_sd = 0, used_items = 0;   // descriptors and items the batch needed
+};
+
+// Enqueue the refactor of every handle of a batch (buffers allocated) and the
+// read-back of its statistics; no synchronisation.  `clear_signs` zeroes the
+// sign slots first (a replayed graph must not keep an earlier run's tails).
+static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* const* d_fields, cudaStream_t s,
+                                Scratch& sc, const BatchLayout& L, BatchStage& io, bool clear_signs) {
+  const int n = (int)hs.size();
   FieldStats* d_st = (FieldStats*)sc.get(sizeof(FieldStats) * n);
-  unsigned long long* d_vm = (unsigned long long*)sc.get(nv * 8);
-  unsigned long long* d_pairs = npairs ? (unsigned long long*)sc.get(npairs * 8) : nullptr;
-  if (!d_st || !d_vm || (npairs && !d_pairs)) return fail(PCR_ERR_OOM, "statistics allocation failed");
-  std::vector<FieldStats> init(n);
-  for (auto& x : init) {
-    x.xmin_key = ~0ull;
-    x.xmax_key = 0;
-    x.c0 = 0;
-    x.G = 0;
-    x.bad = 0;
+  unsigned long long* d_vm = (unsigned long long*)sc.get(L.nv * 8);
+  unsigned long long* d_pairs = L.npairs ? (unsigned long long*)sc.get(L.npairs * 8) : nullptr;
+  if (!d_st || !d_vm || (L.npairs && !d_pairs)) return fail(PCR_ERR_OOM, "statistics allocation failed");
+  if (!io.pinned) {
+    io.v_init.resize(n);
+    io.st_init = io.v_init.data();
   }
-  CUDA_TRY(cudaMemcpyAsync(d_st, init.data(), sizeof(FieldStats) * n, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemsetAsync(d_vm, 0, nv * 8, s));
-  if (npairs) CUDA_TRY(cudaMemsetAsync(d_pairs, 0, npairs * 8, s));
-  for (int k = 0; k < n; k++) CUDA_TRY(cudaMemsetAsync(hs[k]->d_nz, 0, hs[k]->nz_words * 4, s));
+  for (int k = 0; k < n; k++) {
+    FieldStats& x = io.st_init[k];
+    std::memset(&x, 0, sizeof(x));
+    x.xmin_key = ~0ull;
+  }
+  CUDA_TRY(cudaMemcpyAsync(d_st, io.st_init, sizeof(FieldStats) * n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(d_vm, 0, L.nv * 8, s));
+  if (L.npairs) CUDA_TRY(cudaMemsetAsync(d_pairs, 0, L.npairs * 8, s));
+  for (int k = 0; k < n; k++) {
+    CUDA_TRY(cudaMemsetAsync(hs[k]->d_nz, 0, hs[k]->nz_words * 4, s));
+    if (clear_signs && hs[k]->sign_area_words) CUDA_TRY(cudaMemsetAsync(hs[k]->d_signs, 0, hs[k]->sign_area_words * 4, s));
+  }
   // coefficient stages per field; encode work lists for the whole batch
   std::vector<StreamD> all;
   std::vector<WorkItem> items[2][2];  // [w64][fixed?]
   int pairs_mode[2][2] = {{-1, -1}, {-1, -1}};
   for (int k = 0; k < n; k++) {
-    pcr_handle* h = hs[k].get();
+    pcr_handle* h = hs[k];
     std::vector<StreamD> sds(h->geo.size());
-    pcr_status e = enqueue_refactor(h, d_fields[k], s, sc, d_st + k, d_vm + vm_off[k],
-                                    h->sch.mode == PCR_MODE_PSNR ? d_pairs + pr_off[k] : nullptr, sds);
+    pcr_status e = enqueue_refactor(h, d_fields[k], s, sc, d_st + k, d_vm + L.vm_off[k],
+                                    h->sch.mode == PCR_MODE_PSNR ? d_pairs + L.pr_off[k] : nullptr, sds);
     if (e) return e;
     for (size_t i = 0; i < sds.size(); i++) {
       const int idx = (int)all.size();
@@ -1658,19 +1685,37 @@ extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, con
       for (int64_t g = 0; g < sds[i].nseg; g++) items[h->w64][fx].push_back({idx, (int)g});
     }
   }
-  StreamD* d_sd = (StreamD*)sc.get(all.size() * sizeof(StreamD));
   size_t nit = 0;
   for (int a = 0; a < 2; a++)
     for (int b = 0; b < 2; b++) nit += items[a][b].size();
+  io.used_sd = all.size();
+  io.used_items = nit;
+  StreamD* d_sd = (StreamD*)sc.get(all.size() * sizeof(StreamD));
   WorkItem* d_items = (WorkItem*)sc.get(std::max<size_t>(nit, 1) * sizeof(WorkItem));
   if (!d_sd || !d_items) return fail(PCR_ERR_OOM, "work list allocation failed");
-  CUDA_TRY(cudaMemcpyAsync(d_sd, all.data(), all.size() * sizeof(StreamD), cudaMemcpyHostToDevice, s));
+  if (!io.pinned) {
+    io.v_sd = all;
+    io.sd = io.v_sd.data();
+    io.v_items.resize(std::max<size_t>(nit, 1));
+    io.items = io.v_items.data();
+  } else if (all.size() > io.cap_sd || nit > io.cap_items) {
+    return fail(PCR_ERR_INVALID_ARG, "batch work list larger than its staging");
+  } else {
+    std::memcpy(io.sd, all.data(), all.size() * sizeof(StreamD));
+  }
   size_t off = 0;
   for (int a = 0; a < 2; a++)
     for (int b = 0; b < 2; b++) {
       if (items[a][b].empty()) continue;
-      CUDA_TRY(cudaMemcpyAsync(d_items + off, items[a][b].data(), items[a][b].size() * sizeof(WorkItem),
-                               cudaMemcpyHostToDevice, s));
+      std::memcpy(io.items + off, items[a][b].data(), items[a][b].size() * sizeof(WorkItem));
+      off += items[a][b].size();
+    }
+  CUDA_TRY(cudaMemcpyAsync(d_sd, io.sd, all.size() * sizeof(StreamD), cudaMemcpyHostToDevice, s));
+  if (nit) CUDA_TRY(cudaMemcpyAsync(d_items, io.items, nit * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+  off = 0;
+  for (int a = 0; a < 2; a++)
+    for (int b = 0; b < 2; b++) {
+      if (items[a][b].empty()) continue;
       const int vk = b ? VK_FIX : (a ? VK_F64 : VK_F32);
       {
         Prof pf(b ? "encode_fixed" : "encode_float", s);
@@ -1679,29 +1724,234 @@ extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, con
       off += items[a][b].size();
     }
   CUDA_TRY(cudaGetLastError());
-  // read back the tables (one synchronisation)
-  std::vector<FieldStats> st(n);
-  std::vector<unsigned long long> vm(nv);
-  std::vector<uint64_t> pairs(npairs);
-  CUDA_TRY(cudaMemcpyAsync(st.data(), d_st, sizeof(FieldStats) * n, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaMemcpyAsync(vm.data(), d_vm, nv * 8, cudaMemcpyDeviceToHost, s));
-  if (npairs) CUDA_TRY(cudaMemcpyAsync(pairs.data(), d_pairs, npairs * 8, cudaMemcpyDeviceToHost, s));
-  std::vector<std::vector<uint32_t>> nz(n);
-  for (int k = 0; k < n; k++) {
-    nz[k].resize(hs[k]->nz_words);
-    CUDA_TRY(cudaMemcpyAsync(nz[k].data(), hs[k]->d_nz, hs[k]->nz_words * 4, cudaMemcpyDeviceToHost, s));
+  // read-back of the statistics the host tables need
+  if (!io.pinned) {
+    io.v_st.resize(n);
+    io.st = io.v_st.data();
+    io.v_vm.resize(std::max<size_t>(L.nv, 1));
+    io.vm = io.v_vm.data();
+    io.v_pairs.resize(std::max<size_t>(L.npairs, 1));
+    io.pairs = io.v_pairs.data();
+    io.v_nz.resize(std::max<size_t>(L.nnz, 1));
+    io.nz = io.v_nz.data();
   }
-  CUDA_TRY(cudaStreamSynchronize(s));
-  for (int k = 0; k < n; k++) {
-    pcr_handle* h = hs[k].get();
-    std::vector<unsigned long long> v(vm.begin() + vm_off[k], vm.begin() + vm_off[k] + h->geo.size());
+  CUDA_TRY(cudaMemcpyAsync(io.st, d_st, sizeof(FieldStats) * n, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(io.vm, d_vm, L.nv * 8, cudaMemcpyDeviceToHost, s));
+  if (L.npairs) CUDA_TRY(cudaMemcpyAsync(io.pairs, d_pairs, L.npairs * 8, cudaMemcpyDeviceToHost, s));
+  for (int k = 0; k < n; k++)
+    CUDA_TRY(cudaMemcpyAsync(io.nz + L.nz_off[k], hs[k]->d_nz, hs[k]->nz_words * 4, cudaMemcpyDeviceToHost, s));
+  return PCR_OK;
+}
+
+// host tables of every handle from a completed batch's read-backs
+static pcr_status finish_batch(const std::vector<pcr_handle*>& hs, const BatchLayout& L, const BatchStage& io) {
+  for (size_t k = 0; k < hs.size(); k++) {
+    pcr_handle* h = hs[k];
+    std::vector<unsigned long long> v(io.vm + L.vm_off[k], io.vm + L.vm_off[k] + h->geo.size());
+    std::vector<uint32_t> nz(io.nz + L.nz_off[k], io.nz + L.nz_off[k] + h->nz_words);
     std::vector<uint64_t> pk;
     if (h->sch.mode == PCR_MODE_PSNR)
-      pk.assign(pairs.begin() + pr_off[k], pairs.begin() + pr_off[k] + h->geo.size() * h->B * h->B);
-    pcr_status e = finish_refactor(h, st[k], v, nz[k], h->sch.mode == PCR_MODE_PSNR ? &pk : nullptr);
+      pk.assign(io.pairs + L.pr_off[k], io.pairs + L.pr_off[k] + h->geo.size() * h->B * h->B);
+    pcr_status e = finish_refactor(h, io.st[k], v, nz, h->sch.mode == PCR_MODE_PSNR ? &pk : nullptr);
+    if (e) return e;
+    std::lock_guard<std::mutex> lk(h->plan_mu);   // planner units follow the new tables
+    h->units_ok[0] = h->units_ok[1] = false;
+  }
+  return PCR_OK;
+}
+
+static pcr_status make_batch_handles(int n, const void* const* d_fields, const int* ndims,
+                                     const int64_t* const* dims, const int* dtypes, const pcr_scheme* schemes,
+                                     const Mem& mem, cudaStream_t s, std::vector<std::unique_ptr<pcr_handle>>& hs) {
+  hs.resize(n);
+  for (int k = 0; k < n; k++) {
+    pcr_status e = validate(d_fields[k], ndims[k], dims[k], dtypes[k], &schemes[k]);
+    if (e) return e;
+    hs[k].reset(new pcr_handle());
+    hs[k]->mem = mem;
+    e = setup_handle(hs[k].get(), ndims[k], dims[k], dtypes[k], &schemes[k]);
+    if (e) return e;
+    e = alloc_handle_buffers(hs[k].get(), s);
     if (e) return e;
   }
-  for (int k = 0; k < n; k++) outs[k] = hs[k].release();
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, const int* ndims,
+                                         const int64_t* const* dims, const int* dtypes, const pcr_scheme* schemes,
+                                         const pcr_allocator* alloc, void* cuda_stream, pcr_handle** outs) {
+  if (n <= 0 || !d_fields || !ndims || !dims || !dtypes || !schemes || !outs)
+    return fail(PCR_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Mem mem = make_mem(alloc);
+  std::vector<std::unique_ptr<pcr_handle>> own;
+  pcr_status e = make_batch_handles(n, d_fields, ndims, dims, dtypes, schemes, mem, s, own);
+  if (e) return e;
+  std::vector<pcr_handle*> hs;
+  for (auto& h : own) hs.push_back(h.get());
+  const BatchLayout L(hs);
+  BatchStage io;
+  {
+    Scratch sc{&mem, s, {}};
+    e = enqueue_batch(hs, d_fields, s, sc, L, io, false);
+    if (e) return e;
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  e = finish_batch(hs, L, io);
+  if (e) return e;
+  for (int k = 0; k < n; k++) outs[k] = own[k].release();
+  return PCR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched refactor captured in one CUDA graph
+// ---------------------------------------------------------------------------
+struct pcr_refactor_graph {
+  Mem mem;
+  std::vector<std::unique_ptr<pcr_handle>> own;
+  std::vector<pcr_handle*> hs;
+  std::vector<const void*> fields;
+  std::unique_ptr<BatchLayout> layout;
+  BatchStage io;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  void* pinned = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+  size_t nodes = 0;
+  ~pcr_refactor_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    if (pinned) cudaFreeHost(pinned);
+    if (arena) mem.free(arena, nullptr);
+  }
+};
+
+extern "C" pcr_status pcr_refactor_graph_create(int n, const void* const* d_fields, const int* ndims,
+                                                const int64_t* const* dims, const int* dtypes,
+                                                const pcr_scheme* schemes, const pcr_allocator* alloc,
+                                                void* cuda_stream, pcr_refactor_graph** out) {
+  if (n <= 0 || !d_fields || !ndims || !dims || !dtypes || !schemes || !out)
+    return fail(PCR_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  std::unique_ptr<pcr_refactor_graph> g(new pcr_refactor_graph());
+  g->mem = make_mem(alloc);
+  pcr_status e = make_batch_handles(n, d_fields, ndims, dims, dtypes, schemes, g->mem, s, g->own);
+  if (e) return e;
+  for (auto& h : g->own) g->hs.push_back(h.get());
+  g->fields.assign(d_fields, d_fields + n);
+  g->layout.reset(new BatchLayout(g->hs));
+  const BatchLayout& L = *g->layout;
+  // 1. one uncaptured run: autotunes the level schedule of these shapes,
+  //    measures the scratch the batch needs and leaves valid handles
+  size_t need = 0;
+  {
+    Scratch sc{&g->mem, s, {}};
+    sc.measure = &need;
+    BatchStage io;
+    const int was = set_autotune(1);
+    e = enqueue_batch(g->hs, d_fields, s, sc, L, io, false);
+    set_autotune(was);
+    if (e) return e;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    e = finish_batch(g->hs, L, io);
+    if (e) return e;
+    g->io.cap_sd = io.used_sd;
+    g->io.cap_items = std::max<size_t>(io.used_items, 1);
+  }
+  // 2. one scratch arena and pinned staging that live as long as the graph
+  g->arena_bytes = need + 256;
+  g->arena = g->mem.alloc(g->arena_bytes, s);
+  if (!g->arena) return fail(PCR_ERR_OOM, "graph scratch arena allocation failed");
+  const size_t b_init = sizeof(FieldStats) * n, b_sd = sizeof(StreamD) * g->io.cap_sd,
+               b_it = sizeof(WorkItem) * g->io.cap_items, b_st = sizeof(FieldStats) * n,
+               b_vm = 8 * std::max<size_t>(L.nv, 1), b_pr = 8 * std::max<size_t>(L.npairs, 1),
+               b_nz = 4 * std::max<size_t>(L.nnz, 1);
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t total = al(b_init) + al(b_sd) + al(b_it) + al(b_st) + al(b_vm) + al(b_pr) + al(b_nz);
+  CUDA_TRY(cudaMallocHost(&g->pinned, total));
+  char* p = (char*)g->pinned;
+  g->io.pinned = true;
+  g->io.st_init = (FieldStats*)p;
+  p += al(b_init);
+  g->io.sd = (StreamD*)p;
+  p += al(b_sd);
+  g->io.items = (WorkItem*)p;
+  p += al(b_it);
+  g->io.st = (FieldStats*)p;
+  p += al(b_st);
+  g->io.vm = (unsigned long long*)p;
+  p += al(b_vm);
+  g->io.pairs = (uint64_t*)p;
+  p += al(b_pr);
+  g->io.nz = (uint32_t*)p;
+  // 3. capture the whole batch on a stream of its own (tracing off while capturing)
+  CUDA_TRY(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const bool prof = g_prof_on;
+  g_prof_on = false;
+  const long long k0 = launch_count();
+  CUDA_TRY(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+  {
+    Scratch sc{&g->mem, g->cap, {}};
+    sc.bump = (char*)(((uintptr_t)g->arena + 255) & ~uintptr_t(255));
+    sc.cap = need;
+    e = enqueue_batch(g->hs, d_fields, g->cap, sc, L, g->io, true);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(g->cap, &graph);
+  g_prof_on = prof;
+  g->graph = graph;
+  if (e) return e;
+  if (ce != cudaSuccess) return fail(PCR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  g->kernels = launch_count() - k0;
+  add_launches(-g->kernels);   // recorded, not launched
+  CUDA_TRY(cudaGraphGetNodes(g->graph, nullptr, &g->nodes));
+  CUDA_TRY(cudaGraphInstantiate(&g->exec, g->graph, 0));
+  *out = g.release();
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_refactor_graph_run(pcr_refactor_graph* g, void* cuda_stream) {
+  if (!g) return fail(PCR_ERR_INVALID_ARG, "null graph");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  CUDA_TRY(cudaGraphLaunch(g->exec, s));
+  add_launches(g->kernels);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return finish_batch(g->hs, *g->layout, g->io);
+}
+
+extern "C" pcr_status pcr_refactor_graph_handle(const pcr_refactor_graph* g, int k, const pcr_handle** out) {
+  if (!g || !out || k < 0 || k >= (int)g->hs.size()) return fail(PCR_ERR_INVALID_ARG, "bad graph or index");
+  *out = g->hs[k];
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_refactor_graph_info(const pcr_refactor_graph* g, int64_t* nodes, int64_t* kernels,
+                                              int64_t* arena_bytes) {
+  if (!g) return fail(PCR_ERR_INVALID_ARG, "null graph");
+  if (nodes) *nodes = (int64_t)g->nodes;
+  if (kernels) *kernels = g->kernels;
+  if (arena_bytes) *arena_bytes = (int64_t)g->arena_bytes;
+  return PCR_OK;
+}
+
+extern "C" void pcr_refactor_graph_free(pcr_refactor_graph* g) { delete g; }
+
+extern "C" pcr_status pcr_autotune_enable(int enable) {
+  set_autotune(enable);
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_autotune_read(int max_entries, int64_t* keys, int* choice, double* ms, int* n_out,
+                                        int reset) {
+  if (!n_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  *n_out = autotune_entries(max_entries, keys, choice, ms);
+  if (reset) clear_autotune();
   return PCR_OK;
 }
 

@@ -128,5 +128,10 @@ void* static_scratch(size_t* cap, std::string* why);
 // increments it right before its <<<...>>>
 void count_launch();
 long long launch_count();
+void add_launches(long long n);
+// autotuner of the level-interpolation schedule (pcr_tiles.cu)
+int set_autotune(int on);   // returns the previous setting
+int autotune_entries(int max_entries, int64_t* keys, int* choice, double* ms);
+void clear_autotune();
 
 }  // namespace pcr

@@ -16,6 +16,9 @@
 // Arithmetic: the rules of pcr_kernels.cu (identical expression trees).
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <map>
 #include <cstdint>
 #include <type_traits>
 
@@ -1068,18 +1071,23 @@ static void run_tile_kind(const TileArgs& a, cudaStream_t s) {
 }
 
 template <typename A, int DEG, bool RET, int T1, int T2>
-static void run_level0_march(const TileArgs& a0, cudaStream_t s) {
+static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force) {
   count_launch();
   TileArgs a = a0;
   a.ntiles[1] = (a.m[1] + T1 - 1) / T1;
   a.ntiles[2] = (a.m[2] + T2 - 1) / T2;
-  // plane chunks: about eight full waves of 4 CTAs per SM, so the last wave
-  // is not a sparse tail; at least 8 planes so the ring warm-up (three
-  // coarse-plane loads) stays a small share of a chunk
+  // plane chunks (default): about eight full waves of 4 CTAs per SM, so the
+  // last wave is not a sparse tail; at least 8 planes so the ring warm-up
+  // (three coarse-plane loads) stays a small share of a chunk
   const int64_t cols = a.ntiles[1] * a.ntiles[2];
-  const int64_t want = (148 * 4 * 8 + cols - 1) / cols;
-  int64_t zc = (a.m[0] + want - 1) / want;
-  zc = std::max<int64_t>(8, (zc + 1) & ~int64_t(1));
+  int64_t zc;
+  if (zc_force > 0) {
+    zc = zc_force;
+  } else {
+    const int64_t want = (148 * 4 * 8 + cols - 1) / cols;
+    zc = (a.m[0] + want - 1) / want;
+    zc = std::max<int64_t>(8, (zc + 1) & ~int64_t(1));
+  }
   a.ntiles[0] = (a.m[0] + zc - 1) / zc;
   static bool attr = false;
   if (!attr) {   // shared memory for several CTAs per SM
@@ -1092,7 +1100,7 @@ static void run_level0_march(const TileArgs& a0, cudaStream_t s) {
 // the plane-marching kernel covers level 0 of 3-D per-level schemes in a
 // contiguous field whose rows hold whole 16-byte vectors
 template <typename A>
-static bool level0_march(const TileArgs& a, cudaStream_t s) {
+static bool march_applies(const TileArgs& a) {
   constexpr int VEC = 16 / sizeof(A);
   if (a.d != 3 || a.interp != 0 || a.order[0] != 0 || a.order[1] != 1 || a.order[2] != 2) return false;
   if (a.degree != 1 && a.degree != 3) return false;
@@ -1104,21 +1112,149 @@ static bool level0_march(const TileArgs& a, cudaStream_t s) {
   for (int r = 0; r < 3; r++)
     for (int k = 0; k < 3; k++)
       if (a.reg[r].start[k] != st[r][k] || a.reg[r].step[k] != sp[r][k]) return false;
-  constexpr int T1 = 16, T2 = sizeof(A) == 4 ? 128 : 64;
-  if (a.retrieve) {
-    if (a.degree == 3) run_level0_march<A, 3, true, T1, T2>(a, s);
-    else run_level0_march<A, 1, true, T1, T2>(a, s);
-  } else {
-    if (a.degree == 3) run_level0_march<A, 3, false, T1, T2>(a, s);
-    else run_level0_march<A, 1, false, T1, T2>(a, s);
-  }
   return true;
 }
 
+// zc > 0: chunks of zc planes; otherwise the default chunking
+template <typename A>
+static void march_launch(const TileArgs& a, cudaStream_t s, int zc) {
+  constexpr int T1 = 16, T2 = sizeof(A) == 4 ? 128 : 64;
+  if (a.retrieve) {
+    if (a.degree == 3) run_level0_march<A, 3, true, T1, T2>(a, s, zc);
+    else run_level0_march<A, 1, true, T1, T2>(a, s, zc);
+  } else {
+    if (a.degree == 3) run_level0_march<A, 3, false, T1, T2>(a, s, zc);
+    else run_level0_march<A, 1, false, T1, T2>(a, s, zc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// autotuner of the level-interpolation schedule
+// ---------------------------------------------------------------------------
+// Where the marching kernel applies, a level can also run the general tile
+// kernel, and the marching kernel's plane chunk sets its grid; all choices
+// compute the same values (same expression trees).  Choice 0 = general tile
+// kernel, -1 = marching with the default chunking, k > 0 = marching with
+// chunks of k planes.  With tuning on, the first launch of an untuned (value
+// kind, direction, degree, level grid) on a stream that is not being
+// captured times every candidate (CUDA events, the best of two runs after a
+// warm-up) and keeps the fastest; later launches, captured ones included,
+// use the table.  A level runs the same points however often it is
+// repeated, so the timing runs leave the same outputs behind.
+namespace {
+struct TuneKey {
+  int vk, ret, deg;
+  int64_t m0, m1, m2;
+  bool operator<(const TuneKey& o) const {
+    if (vk != o.vk) return vk < o.vk;
+    if (ret != o.ret) return ret < o.ret;
+    if (deg != o.deg) return deg < o.deg;
+    if (m0 != o.m0) return m0 < o.m0;
+    if (m1 != o.m1) return m1 < o.m1;
+    return m2 < o.m2;
+  }
+};
+struct TuneVal {
+  int choice;
+  float ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+std::atomic<int> g_tune_on{0};
+constexpr int kTuneCand[] = {0, 8, 16, 32, 64, -1};
+
+template <typename A>
+void run_choice(const TileArgs& a, cudaStream_t s, int choice) {
+  if (choice == 0) run_tile_kind<A>(a, s);
+  else march_launch<A>(a, s, choice);
+}
+
+template <typename A>
+TuneVal tune(const TileArgs& a, cudaStream_t s) {
+  TuneVal best{-1, -1.0f};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return best;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return best;
+  }
+  for (int c : kTuneCand) {
+    if (c > 0 && c >= 2 * a.m[0] && c != 8) continue;   // larger chunks than the field: same grid as a smaller one
+    run_choice<A>(a, s, c);                            // warm-up
+    float t = 1e30f;
+    for (int r = 0; r < 2; r++) {
+      cudaEventRecord(e0, s);
+      run_choice<A>(a, s, c);
+      cudaEventRecord(e1, s);
+      float ms = 0.0f;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        t = std::min(t, ms);
+    }
+    if (best.ms < 0.0f || t < best.ms) best = {c, t};
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+template <typename A>
+bool launch_tuned(int vk, const TileArgs& a, cudaStream_t s) {
+  if (!march_applies<A>(a)) return false;
+  const TuneKey key{vk, a.retrieve, a.degree, a.m[0], a.m[1], a.m[2]};
+  int choice = -1;
+  bool have = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      choice = it->second.choice;
+      have = true;
+    }
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!have && g_tune_on.load() && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+      cs == cudaStreamCaptureStatusNone) {
+    const TuneVal v = tune<A>(a, s);
+    if (v.ms >= 0.0f) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[key] = v;
+      choice = v.choice;
+    }
+  }
+  run_choice<A>(a, s, choice);
+  return true;
+}
+}  // namespace
+
+int set_autotune(int on) { return g_tune_on.exchange(on ? 1 : 0); }
+
+int autotune_entries(int max_entries, int64_t* keys, int* choice, double* ms) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  int k = 0;
+  for (auto& kv : g_tune) {
+    if (k < max_entries) {
+      const TuneKey& t = kv.first;
+      if (keys) {
+        const int64_t v[6] = {t.vk, t.ret, t.deg, t.m0, t.m1, t.m2};
+        for (int i = 0; i < 6; i++) keys[6 * k + i] = v[i];
+      }
+      if (choice) choice[k] = kv.second.choice;
+      if (ms) ms[k] = kv.second.ms;
+    }
+    k++;
+  }
+  return k;
+}
+
+void clear_autotune() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+}
+
 void launch_tile_interp(int vk, const TileArgs& a, cudaStream_t s) {
-  if (vk == VK_F32 && level0_march<float>(a, s)) return;
-  if (vk == VK_F64 && level0_march<double>(a, s)) return;
-  if (vk == VK_FIX && level0_march<int64_t>(a, s)) return;   // a contiguous fixed-point level (level 1)
+  if (vk == VK_F32 && launch_tuned<float>(vk, a, s)) return;
+  if (vk == VK_F64 && launch_tuned<double>(vk, a, s)) return;
+  if (vk == VK_FIX && launch_tuned<int64_t>(vk, a, s)) return;   // a contiguous fixed-point level (level 1)
   if (vk == VK_F32) run_tile_kind<float>(a, s);
   else if (vk == VK_F64) run_tile_kind<double>(a, s);
   else run_tile_kind<int64_t>(a, s);
