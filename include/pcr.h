@@ -201,6 +201,19 @@ pcr_status pcr_retrieve(const pcr_handle* h, const pcr_retrieval_plan* plan, voi
 pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
                               void* const* d_outs, void* cuda_stream);
 
+/* Retrieval of a box [lo, hi) of the field (user axes, 0 <= lo < hi <= dims)
+ * under `plan` (from pcr_plan: the bound holds at every point, so inside the
+ * box too).  d_out: device buffer of the box, row-major, prod(hi - lo)
+ * values of the field dtype.  Returns exactly the box of what pcr_retrieve
+ * with the same plan returns.  A point at level l depends on the coarser
+ * grid and on level l's coefficients within 3 * 2^l field points per axis
+ * (Alg. 2's rules), so only the stream segments meeting the box's
+ * dependency region are decoded and only the tiles meeting it are
+ * reconstructed.  Temporary device memory as pcr_retrieve plus one field.
+ * Enqueue only; errors: PCR_ERR_INVALID_ARG for a box outside the field. */
+pcr_status pcr_retrieve_box(const pcr_handle* h, const pcr_retrieval_plan* plan, const int64_t* lo,
+                            const int64_t* hi, void* d_out, void* cuda_stream);
+
 /* Upper bound on the temporary device memory one pcr_retrieve of `h` takes
  * (staging, work lists, recomposition); used for memory-based admission. */
 pcr_status pcr_retrieve_scratch_bytes(const pcr_handle* h, size_t* bytes);

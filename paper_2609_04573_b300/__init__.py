@@ -79,6 +79,7 @@ _sigs = {
     "pcr_retrieve": [_vp, C.POINTER(_Plan), _vp, _vp],
     "pcr_retrieve_batch": [C.c_int, C.POINTER(_vp), C.POINTER(_Plan), C.POINTER(_vp), _vp],
     "pcr_retrieve_static": [_vp, C.POINTER(_Plan), _vp, _vp],
+    "pcr_retrieve_box": [_vp, C.POINTER(_Plan), _i64p, _i64p, _vp, _vp],
     "pcr_retrieve_scratch_bytes": [_vp, C.POINTER(C.c_size_t)],
     "pcr_num_streams": [_vp, C.POINTER(C.c_int)],
     "pcr_stream_info_get": [_vp, C.c_int, C.POINTER(_StreamInfo)],
@@ -302,6 +303,23 @@ class Handle:
             out = torch.empty(self.shape, dtype=self.dtype, device=self.device)
         assert out.is_contiguous() and tuple(out.shape) == self.shape and out.dtype == self.dtype
         _check(_lib.pcr_retrieve(self._p, C.byref(plan._c), C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out, plan
+
+    def retrieve_box(self, target_or_plan, box, out=None, stream=None):
+        """Reconstruct only the box ((lo, hi) per axis) of the field: the same
+        values as retrieve() gives there, decoding and reconstructing only
+        the box's dependency region.  Returns (out, plan)."""
+        plan = target_or_plan if isinstance(target_or_plan, Plan) else self.plan(target_or_plan)
+        lo = [int(a) for a, _ in box]
+        hi = [int(b) for _, b in box]
+        if len(lo) != len(self.shape):
+            raise ValueError("box needs one (lo, hi) pair per axis")
+        shp = tuple(b - a for a, b in zip(lo, hi))
+        if out is None:
+            out = torch.empty(shp, dtype=self.dtype, device=self.device)
+        assert out.is_contiguous() and tuple(out.shape) == shp and out.dtype == self.dtype
+        _check(_lib.pcr_retrieve_box(self._p, C.byref(plan._c), (C.c_int64 * len(lo))(*lo),
+                                     (C.c_int64 * len(hi))(*hi), C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out, plan
 
     @property

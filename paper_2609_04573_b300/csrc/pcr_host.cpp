@@ -35,7 +35,9 @@ void launch_decompose(int vk, const DecompGeo& dg, const LatD& sl, const void* c
 void launch_recompose(int vk, const DecompGeo& dg, const LatD& sl, const void* dec, void* comp, cudaStream_t s);
 void launch_recon_fixed(const FieldD& f, int level, int raw, const LatD& lat, const int64_t* chat, int64_t* xc,
                         cudaStream_t s);
-void launch_coarse_out(int vk, const FieldD& f, const int64_t* xc, double scale, void* out, cudaStream_t s);
+void launch_coarse_out(int vk, const FieldD& f, const int64_t* xc, double scale, void* out, cudaStream_t s,
+                       const Box3* box = nullptr);
+void launch_copy_box(int vk, const FieldD& f, const void* src, void* dst, const Box3& b, cudaStream_t s);
 void launch_recon_l0(int vk, const FieldD& f, const LatD& lat, int compact, const void* chat, void* out,
                      cudaStream_t s);
 void launch_copy_raw(int vk, const FieldD& f, const LatD& lat, const void* vals, void* out, cudaStream_t s);
@@ -2141,6 +2143,218 @@ static pcr_status retrieve_batch_impl(int n, const pcr_handle* const* hs, const 
   for (int k = 0; k < n; k++) {
     pcr_status e = enqueue_reconstruct(hs[k], sds[k], d_outs[k], s, sc);
     if (e) return e;
+  }
+  CUDA_TRY(cudaGetLastError());
+  return PCR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// retrieval of a box of the field
+// ---------------------------------------------------------------------------
+// A reconstructed point at level l depends on the coarser grid and on level
+// l's decoded coefficients within 3 points of the level grid per axis (the
+// cubic rules; every region pass reads one axis once), i.e. 3 * 2^l field
+// points.  So with B_0 = the box and B_(l+1) = B_l grown by 3 * 2^l, level l
+// is reconstructed over B_l from coefficients decoded over B_l grown by
+// 3 * 2^l (level 0 with decomposition: grown further by the recomposition's
+// reach, 2 sub-level lines of 4 compact points, at most 16 field points).
+// Only the stream segments meeting those boxes are decoded and only the
+// tiles meeting B_l are run; values the kernels produce outside B_l (tile
+// rounding) may use undecoded inputs but are never read by a point inside.
+namespace {
+struct FBox {
+  int64_t lo[3], hi[3];   // field coordinates, [lo, hi)
+};
+int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+int64_t ceildiv(int64_t a, int64_t b) { return -floordiv(-a, b); }
+
+FBox grow(const FBox& b, int64_t r, const int64_t* n3) {
+  FBox o = b;
+  for (int k = 0; k < 3; k++)
+    if (n3[k] > 1) {
+      o.lo[k] = std::max<int64_t>(0, b.lo[k] - r);
+      o.hi[k] = std::min<int64_t>(n3[k], b.hi[k] + r);
+    }
+  return o;
+}
+
+// lattice index ranges [k0, k1) of the lattice points inside box b
+bool lat_range(const Lat& L, const FBox& b, int64_t* k0, int64_t* k1) {
+  for (int a = 0; a < 3; a++) {
+    k0[a] = std::max<int64_t>(0, ceildiv(b.lo[a] - L.start[a], L.step[a]));
+    k1[a] = std::min<int64_t>(L.count[a], floordiv(b.hi[a] - 1 - L.start[a], L.step[a]) + 1);
+    if (k1[a] <= k0[a]) return false;
+  }
+  return true;
+}
+}  // namespace
+
+// decode only the segments of stream i that hold lattice points of box b
+static void mark_segments(const SGeo& g, const FBox& b, std::vector<char>& mark) {
+  const int64_t nseg = (g.n_pad() + kSegElems - 1) / kSegElems;
+  mark.assign(nseg, 0);
+  int64_t base = 0;
+  for (const Lat& L : g.lats) {
+    int64_t k0[3], k1[3];
+    if (lat_range(L, b, k0, k1)) {
+      const int64_t rp = L.row_pad();
+      for (int64_t a = k0[0]; a < k1[0]; a++)
+        for (int64_t c = k0[1]; c < k1[1]; c++) {
+          const int64_t row = base + (a * L.count[1] + c) * rp;
+          for (int64_t sg = (row + k0[2]) / kSegElems; sg <= (row + k1[2] - 1) / kSegElems; sg++) mark[sg] = 1;
+        }
+    }
+    base += L.n_pad();
+  }
+}
+
+// level-grid box of a field box at level l (points q with q 2^l in [lo, hi))
+static void level_box(const pcr_handle* h, const FBox& b, int level, int64_t* lo, int64_t* hi) {
+  for (int k = 0; k < 3; k++) {
+    if (h->n3[k] > 1) {
+      lo[k] = ceildiv(b.lo[k], int64_t(1) << level);
+      hi[k] = ceildiv(b.hi[k], int64_t(1) << level);
+    } else {
+      lo[k] = 0;
+      hi[k] = 1;
+    }
+  }
+}
+
+static pcr_status enqueue_reconstruct_box(const pcr_handle* h, const std::vector<StreamD>& sds, void* d_full,
+                                          const std::vector<FBox>& B, cudaStream_t s, Scratch& sc) {
+  const FieldD f = field_desc(h);
+  const size_t w = vsize(h->vk);
+  if (h->L == 1) {
+    Prof pf("copy_raw", s);
+    launch_copy_raw(h->vk, f, to_latd(h->geo[0].lats[0], 0), sds[0].stage, d_full, s);
+    return PCR_OK;
+  }
+  std::vector<void*> comp(4, nullptr);
+  if (h->decomp >= 0) {
+    const FBox rb = grow(B[0], 3, h->n3);   // level-0 coefficients the level-0 pass reads
+    for (int r = 1; r <= f.d; r++) {
+      const Lat R = region_lat(h->n3, 0, h->order, r);
+      comp[r] = sc.get((size_t)R.n_real() * w);
+      if (!comp[r]) return fail(PCR_ERR_OOM, "staging allocation failed");
+      DecompArgs da{};
+      decomp_subs(h, r, sds, da);
+      da.retrieve = 1;
+      da.comp = comp[r];
+      int64_t k0[3], k1[3];
+      if (!lat_range(R, rb, k0, k1)) continue;
+      for (int k = 0; k < 3; k++) {
+        da.blo[k] = k0[k];
+        da.bhi[k] = k1[k];
+      }
+      Prof pf("recompose", s);
+      launch_tile_decomp(h->vk, da, s);
+    }
+  }
+  int64_t* xc = (int64_t*)sc.get((size_t)f.nc[0] * f.nc[1] * f.nc[2] * 8);
+  if (!xc) return fail(PCR_ERR_OOM, "staging allocation failed");
+  {
+    Prof pf("recon_coarsest", s);
+    launch_recon_fixed(f, h->L - 1, 1, to_latd(h->geo[0].lats[0], 0), (const int64_t*)sds[0].stage, xc, s);
+  }
+  for (int level = h->L - 2; level >= 1; level--) {
+    TileArgs a = level_args(h, level, 1, xc, xc);
+    level_regions(h, level, sds, a);
+    level_box(h, B[level], level, a.blo, a.bhi);
+    if (a.bhi[0] <= a.blo[0] || a.bhi[1] <= a.blo[1] || a.bhi[2] <= a.blo[2]) continue;
+    Prof pf("recon_fixed_levels", s);
+    launch_tile_interp(VK_FIX, a, s);
+  }
+  {
+    int64_t lo[3], hi[3];
+    level_box(h, B[1], 1, lo, hi);   // the 2-grid points level 0 reads
+    Box3 cb;
+    for (int k = 0; k < 3; k++) {
+      cb.lo[k] = lo[k];
+      cb.cnt[k] = std::max<int64_t>(0, hi[k] - lo[k]);
+    }
+    Prof pf("coarse_out", s);
+    launch_coarse_out(h->vk, f, xc, std::ldexp(1.0, h->G - kFixBits), d_full, s, &cb);
+  }
+  TileArgs a = level_args(h, 0, 1, d_full, d_full);
+  if (h->decomp >= 0) {
+    for (int r = 1; r <= f.d; r++) {
+      const Lat R = region_lat(h->n3, 0, h->order, r);
+      a.reg[r - 1] = tile_region(h, R, 0, R.count[2], 0, comp[r], nullptr);
+    }
+  } else {
+    level_regions(h, 0, sds, a);
+  }
+  level_box(h, B[0], 0, a.blo, a.bhi);
+  Prof pf("recon_level0", s);
+  launch_tile_interp(h->vk, a, s);
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_retrieve_box(const pcr_handle* h, const pcr_retrieval_plan* plan, const int64_t* lo,
+                                       const int64_t* hi, void* d_out, void* cuda_stream) {
+  if (!h || !plan || !lo || !hi || !d_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // user axes -> the internal 3-D view (2-D fields are 1 x n0 x n1)
+  FBox B0{{0, 0, 0}, {1, 1, 1}};
+  const int off = 3 - h->ndim;
+  for (int k = 0; k < h->ndim; k++) {
+    if (lo[k] < 0 || hi[k] > h->dims[k] || lo[k] >= hi[k]) return fail(PCR_ERR_INVALID_ARG, "box outside the field");
+    B0.lo[off + k] = lo[k];
+    B0.hi[off + k] = hi[k];
+  }
+  Mem mem = h->mem;
+  Scratch sc{&mem, s, {}};
+  std::vector<StreamD> sds;
+  std::vector<int> kinds;
+  pcr_status e = enqueue_retrieve_one(h, plan, d_out, s, sc, sds, kinds);
+  if (e) return e;
+  // level boxes and the decode work list
+  std::vector<FBox> B(h->L);
+  B[0] = B0;
+  for (int l = 0; l + 1 < h->L; l++) B[l + 1] = grow(B[l], int64_t(3) << l, h->n3);
+  std::vector<WorkItem> items[2];
+  std::vector<char> mark;
+  for (int i = 0; i < (int)h->geo.size(); i++) {
+    const SGeo& g = h->geo[i];
+    const int l = g.level;
+    FBox need;
+    if (l == h->L - 1) {
+      need = FBox{{0, 0, 0}, {h->n3[0], h->n3[1], h->n3[2]}};
+    } else {
+      const int64_t r = (int64_t(3) << l) + (l == 0 && h->decomp >= 0 ? 16 : 0);
+      need = grow(B[l], r, h->n3);
+    }
+    mark_segments(g, need, mark);
+    for (int64_t sg = 0; sg < (int64_t)mark.size(); sg++)
+      if (mark[sg]) items[g.is_fix].push_back({i, (int)sg});
+  }
+  StreamD* d_sd = (StreamD*)sc.get(sds.size() * sizeof(StreamD));
+  WorkItem* d_items = (WorkItem*)sc.get(std::max<size_t>(items[0].size() + items[1].size(), 1) * sizeof(WorkItem));
+  void* d_full = sc.get((size_t)h->n3[0] * h->n3[1] * h->n3[2] * vsize(h->vk));
+  if (!d_sd || !d_items || !d_full) return fail(PCR_ERR_OOM, "box retrieval allocation failed");
+  CUDA_TRY(cudaMemcpyAsync(d_sd, sds.data(), sds.size() * sizeof(StreamD), cudaMemcpyHostToDevice, s));
+  size_t o = 0;
+  for (int fx = 0; fx < 2; fx++) {
+    if (items[fx].empty()) continue;
+    CUDA_TRY(cudaMemcpyAsync(d_items + o, items[fx].data(), items[fx].size() * sizeof(WorkItem),
+                             cudaMemcpyHostToDevice, s));
+    {
+      Prof pf(fx ? "decode_fixed" : "decode_float", s);
+      launch_decode(fx ? VK_FIX : h->vk, h->w64, d_sd, d_items + o, (int)items[fx].size(), s);
+    }
+    o += items[fx].size();
+  }
+  e = enqueue_reconstruct_box(h, sds, d_full, B, s, sc);
+  if (e) return e;
+  Box3 ob;
+  for (int k = 0; k < 3; k++) {
+    ob.lo[k] = B0.lo[k];
+    ob.cnt[k] = B0.hi[k] - B0.lo[k];
+  }
+  {
+    Prof pf("copy_box", s);
+    launch_copy_box(h->vk, field_desc(h), d_full, d_out, ob, s);
   }
   CUDA_TRY(cudaGetLastError());
   return PCR_OK;

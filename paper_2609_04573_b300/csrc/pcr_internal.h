@@ -85,6 +85,11 @@ struct TileArgs {
   const void* src;     // refactor: field (level 0) or fixed-point 2-grid copy
   void* dst;           // retrieve: same view as src
   TileRegion reg[3];
+  // box retrieval: level-grid box [blo, bhi) whose values must be exact
+  // (bhi[0] == 0: the whole grid); set by the host
+  int64_t blo[3], bhi[3];
+  // set by the launchers: first tile per axis (plane-marching: first plane)
+  int64_t tlo[3];
 };
 
 // one sub-level lattice part of a decomposed region, in the region's compact
@@ -103,7 +108,15 @@ struct DecompArgs {
   int retrieve;        // 0 decompose, 1 recompose
   void* comp;          // region compact array (c, or recomposed c_hat)
   DecompSub subs[5];   // S1, S2a, S2b, S3a, S3b
+  // recompose of a box of the compact array [blo, bhi) (bhi[0] == 0: all);
+  // first block per axis set by the launcher
+  int64_t blo[3], bhi[3], tlo[3];
   unsigned long long* c0;  // decompose: running max |c| (bits of a double)
+};
+
+// an index box: points lo + [0, cnt) per axis
+struct Box3 {
+  int64_t lo[3], cnt[3];
 };
 
 struct WorkItem {

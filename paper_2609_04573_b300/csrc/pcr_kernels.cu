@@ -476,16 +476,29 @@ __global__ void k_recon_fixed(FieldD f, int level, int raw, LatD lat, const int6
   }
 }
 
-// coarse points of level 0: out[2-grid] = x_int h rounded once
+// coarse points of level 0: out[2-grid] = x_int h rounded once, over the
+// 2-grid box [lo, lo + cnt)
 template <typename T>
-__global__ void k_coarse_out(FieldD f, const int64_t* __restrict__ xc, T scale, T* __restrict__ out) {
-  const int64_t n = f.nc[0] * f.nc[1] * f.nc[2];
+__global__ void k_coarse_out(FieldD f, const int64_t* __restrict__ xc, T scale, T* __restrict__ out, Box3 b) {
+  const int64_t n = b.cnt[0] * b.cnt[1] * b.cnt[2];
   const int s0 = f.n[0] > 1 ? 2 : 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c2 = i % f.nc[2], t = i / f.nc[2];
-    const int64_t c1 = t % f.nc[1], c0 = t / f.nc[1];
-    out[((c0 * s0) * f.n[1] + 2 * c1) * f.n[2] + 2 * c2] = from_fix<T>(xc[i], scale);
+    const int64_t c2 = i % b.cnt[2] + b.lo[2], t = i / b.cnt[2];
+    const int64_t c1 = t % b.cnt[1] + b.lo[1], c0 = t / b.cnt[1] + b.lo[0];
+    out[((c0 * s0) * f.n[1] + 2 * c1) * f.n[2] + 2 * c2] = from_fix<T>(xc[(c0 * f.nc[1] + c1) * f.nc[2] + c2], scale);
+  }
+}
+
+// out[box] = field[lo + box] (row-major box of cnt points)
+template <typename T>
+__global__ void k_copy_box(FieldD f, const T* __restrict__ src, T* __restrict__ dst, Box3 b) {
+  const int64_t n = b.cnt[0] * b.cnt[1] * b.cnt[2];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c2 = i % b.cnt[2], t = i / b.cnt[2];
+    const int64_t c1 = t % b.cnt[1], c0 = t / b.cnt[1];
+    dst[i] = src[((c0 + b.lo[0]) * f.n[1] + c1 + b.lo[1]) * f.n[2] + c2 + b.lo[2]];
   }
 }
 
@@ -1154,11 +1167,26 @@ void launch_recon_fixed(const FieldD& f, int level, int raw, const LatD& lat, co
   k_recon_fixed<<<grid_for(n), 256, 0, s>>>(f, level, raw, lat, chat, xc);
 }
 
-void launch_coarse_out(int vk, const FieldD& f, const int64_t* xc, double scale, void* out, cudaStream_t s) {
+void launch_coarse_out(int vk, const FieldD& f, const int64_t* xc, double scale, void* out, cudaStream_t s,
+                       const Box3* box) {
+  Box3 b;
+  for (int k = 0; k < 3; k++) {
+    b.lo[k] = box ? box->lo[k] : 0;
+    b.cnt[k] = box ? box->cnt[k] : f.nc[k];
+  }
+  const int64_t n = b.cnt[0] * b.cnt[1] * b.cnt[2];
+  if (n <= 0) return;
   count_launch();
-  const int64_t n = f.nc[0] * f.nc[1] * f.nc[2];
-  if (vk == VK_F32) k_coarse_out<float><<<grid_for(n), 256, 0, s>>>(f, xc, (float)scale, (float*)out);
-  else k_coarse_out<double><<<grid_for(n), 256, 0, s>>>(f, xc, scale, (double*)out);
+  if (vk == VK_F32) k_coarse_out<float><<<grid_for(n), 256, 0, s>>>(f, xc, (float)scale, (float*)out, b);
+  else k_coarse_out<double><<<grid_for(n), 256, 0, s>>>(f, xc, scale, (double*)out, b);
+}
+
+void launch_copy_box(int vk, const FieldD& f, const void* src, void* dst, const Box3& b, cudaStream_t s) {
+  const int64_t n = b.cnt[0] * b.cnt[1] * b.cnt[2];
+  if (n <= 0) return;
+  count_launch();
+  if (vk == VK_F32) k_copy_box<float><<<grid_for(n), 256, 0, s>>>(f, (const float*)src, (float*)dst, b);
+  else k_copy_box<double><<<grid_for(n), 256, 0, s>>>(f, (const double*)src, (double*)dst, b);
 }
 
 void launch_recon_l0(int vk, const FieldD& f, const LatD& lat, int compact, const void* chat, void* out,

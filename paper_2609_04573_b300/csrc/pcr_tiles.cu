@@ -240,10 +240,10 @@ __global__ void __launch_bounds__(256) k_tile_interp(TileArgs a) {
 
   unsigned bid = blockIdx.x;
   const unsigned nt2 = (unsigned)a.ntiles[2], nt1 = (unsigned)a.ntiles[1];
-  const int b2 = (int)(bid % nt2) * T2;
+  const int b2 = (int)(bid % nt2 + a.tlo[2]) * T2;
   bid /= nt2;
-  const int b1 = (int)(bid % nt1) * T1;
-  const int b0 = (int)(bid / nt1) * T0;
+  const int b1 = (int)(bid % nt1 + a.tlo[1]) * T1;
+  const int b0 = (int)(bid / nt1 + a.tlo[0]) * T0;
   const int o0 = b0 - H0, o1 = b1 - H, o2 = b2 - XL;
   const A* __restrict__ src = reinterpret_cast<const A*>(a.src);
   A* __restrict__ dst = reinterpret_cast<A*>(a.dst);
@@ -537,9 +537,9 @@ __global__ void __launch_bounds__(128) k_decomp_blk(DecompArgs a) {
   using V = VecT<A, VEC>;
   const unsigned nvec = (unsigned)a.ntiles[2], nbb = (unsigned)a.ntiles[1], nab = (unsigned)a.ntiles[0];
   const unsigned item = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned iv = item % nvec, rest = item / nvec;
-  const unsigned bb = rest % nbb, ab = rest / nbb;
-  const bool live = ab < nab;
+  const unsigned iv = item % nvec + (unsigned)a.tlo[2], rest = item / nvec;
+  const unsigned bb = rest % nbb + (unsigned)a.tlo[1], ab = rest / nbb + (unsigned)a.tlo[0];
+  const bool live = rest / nbb < nab;
   const int cu = (int)a.cnt[0], cv = (int)a.cnt[1];
   const int64_t cw = a.cnt[2];
   const int u0 = 4 * (int)ab, v0 = 4 * (int)bb;
@@ -741,11 +741,11 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
   const int64_t s0 = a.stride[0], s1 = a.stride[1];
   unsigned bid = blockIdx.x;
   const unsigned nt2 = (unsigned)a.ntiles[2], nt1 = (unsigned)a.ntiles[1];
-  const int b2 = (int)(bid % nt2) * T2;
+  const int b2 = (int)(bid % nt2 + a.tlo[2]) * T2;
   bid /= nt2;
-  const int b1 = (int)(bid % nt1) * T1;
-  const int z0 = (int)(bid / nt1) * zc;
-  const int z1 = min(z0 + zc, m0);
+  const int b1 = (int)(bid % nt1 + a.tlo[1]) * T1;
+  const int z0 = (int)a.tlo[0] + (int)(bid / nt1) * zc;          // even
+  const int z1 = min(z0 + zc, a.bhi[0] ? (int)a.bhi[0] : m0);
   const A* __restrict__ src = reinterpret_cast<const A*>(a.src);
   A* __restrict__ dst = reinterpret_cast<A*>(a.dst);
   const int tid = threadIdx.x;
@@ -1039,11 +1039,15 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
 // ---------------------------------------------------------------------------
 template <typename A, int T0, int T1, int T2, int H0, int H>
 static void run_tile(const TileArgs& a0, cudaStream_t s) {
-  count_launch();
   TileArgs a = a0;
-  a.ntiles[0] = (a.m[0] + T0 - 1) / T0;
-  a.ntiles[1] = (a.m[1] + T1 - 1) / T1;
-  a.ntiles[2] = (a.m[2] + T2 - 1) / T2;
+  const int64_t T[3] = {T0, T1, T2};
+  for (int k = 0; k < 3; k++) {   // tiles covering the box (or the grid)
+    const int64_t lo = a.bhi[0] ? a.blo[k] : 0, hi = a.bhi[0] ? a.bhi[k] : a.m[k];
+    a.tlo[k] = lo / T[k];
+    a.ntiles[k] = hi > lo ? (hi + T[k] - 1) / T[k] - a.tlo[k] : 0;
+  }
+  if (!a.ntiles[0] || !a.ntiles[1] || !a.ntiles[2]) return;
+  count_launch();
   const size_t smem = sizeof(A) * (T0 + 2 * H0) * (T1 + 2 * H) * (T2 + 8);
   static bool attr = false;
   if (!attr) {
@@ -1072,10 +1076,20 @@ static void run_tile_kind(const TileArgs& a, cudaStream_t s) {
 
 template <typename A, int DEG, bool RET, int T1, int T2>
 static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force) {
-  count_launch();
   TileArgs a = a0;
-  a.ntiles[1] = (a.m[1] + T1 - 1) / T1;
-  a.ntiles[2] = (a.m[2] + T2 - 1) / T2;
+  const bool box = a.bhi[0] != 0;
+  const int64_t T[3] = {1, T1, T2};
+  for (int k = 1; k < 3; k++) {   // column tiles covering the box (or the grid)
+    const int64_t lo = box ? a.blo[k] : 0, hi = box ? a.bhi[k] : a.m[k];
+    a.tlo[k] = lo / T[k];
+    a.ntiles[k] = hi > lo ? (hi + T[k] - 1) / T[k] - a.tlo[k] : 0;
+  }
+  // planes [z_lo, z_end): chunks start on even planes (the ring holds even
+  // planes)
+  const int64_t zlo = box ? (a.blo[0] & ~int64_t(1)) : 0, zend = box ? a.bhi[0] : a.m[0];
+  a.tlo[0] = zlo;
+  if (zend <= zlo || !a.ntiles[1] || !a.ntiles[2]) return;
+  count_launch();
   // plane chunks (default): about eight full waves of 4 CTAs per SM, so the
   // last wave is not a sparse tail; at least 8 planes so the ring warm-up
   // (three coarse-plane loads) stays a small share of a chunk
@@ -1085,10 +1099,10 @@ static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force) {
     zc = zc_force;
   } else {
     const int64_t want = (148 * 4 * 8 + cols - 1) / cols;
-    zc = (a.m[0] + want - 1) / want;
+    zc = (zend - zlo + want - 1) / want;
     zc = std::max<int64_t>(8, (zc + 1) & ~int64_t(1));
   }
-  a.ntiles[0] = (a.m[0] + zc - 1) / zc;
+  a.ntiles[0] = (zend - zlo + zc - 1) / zc;
   static bool attr = false;
   if (!attr) {   // shared memory for several CTAs per SM
     cudaFuncSetAttribute(k_level0_march<A, DEG, RET, T1, T2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -1212,7 +1226,7 @@ bool launch_tuned(int vk, const TileArgs& a, cudaStream_t s) {
     }
   }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  if (!have && g_tune_on.load() && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+  if (!have && !a.bhi[0] && g_tune_on.load() && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
       cs == cudaStreamCaptureStatusNone) {
     const TuneVal v = tune<A>(a, s);
     if (v.ms >= 0.0f) {
@@ -1279,13 +1293,17 @@ static void run_decomp(const DecompArgs& a0, cudaStream_t s) {
 
 template <typename A, int VEC>
 static void run_decomp_blk(const DecompArgs& a0, cudaStream_t s) {
-  count_launch();
   DecompArgs a = a0;
-  a.ntiles[0] = (a.cnt[0] + 3) / 4;
-  a.ntiles[1] = (a.cnt[1] + 3) / 4;
-  a.ntiles[2] = a.cnt[2] / VEC;
+  const bool box = a.bhi[0] != 0;
+  const int64_t T[3] = {4, 4, VEC};
+  for (int k = 0; k < 3; k++) {   // 4 x 4 blocks and vectors covering the box (or the array)
+    const int64_t lo = box ? a.blo[k] : 0, hi = box ? std::min(a.bhi[k], a.cnt[k]) : a.cnt[k];
+    a.tlo[k] = lo / T[k];
+    a.ntiles[k] = hi > lo ? (k == 2 ? hi / T[k] + (hi % T[k] != 0) : (hi + T[k] - 1) / T[k]) - a.tlo[k] : 0;
+  }
   const int64_t items = a.ntiles[0] * a.ntiles[1] * a.ntiles[2];
   if (items == 0) return;
+  count_launch();
   k_decomp_blk<A, VEC><<<(unsigned)((items + 127) / 128), 128, 0, s>>>(a);
 }
 
