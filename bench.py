@@ -439,7 +439,9 @@ def run_serve(args):
         wall = time.perf_counter() - t0
         srv.close()
         lat = [r.latency * 1e3 for r in live]
-        out_bytes = sum(handles[r.field_id].out_bytes for r in live)
+        # bytes delivered: the field, or the box of a box request
+        out_bytes = sum(handles[r.field_id].out_bytes if r.box is None else
+                        math.prod(b - a for a, b in r.box) * 4 for r in live)
         return {"p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99), "wall_s": wall,
                 "field_gbs": out_bytes / wall / 1e9, "read_gbs": sum(r.bytes_read for r in live) / wall / 1e9,
                 "batches": srv.batches}

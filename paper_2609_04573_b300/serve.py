@@ -12,7 +12,9 @@ CUDA events.  Every result is the same field a single pcr_retrieve of that
 request produces (the kernels are deterministic and share no state between
 requests).
 
-Box requests return the requested sub-box of the retrieved field.
+Box requests are retrieved with pcr_retrieve_box on the group's stream: only
+the box's dependency region is decoded and reconstructed, and the result is
+the box of the whole-field retrieval under the same plan.
 """
 import queue
 import threading
@@ -57,6 +59,7 @@ class Server:
         self.done = []
         self._stop = False
         self._need = [h.retrieve_scratch_bytes() + h.out_bytes for h in self.handles]
+        # a box retrieval reconstructs into a field-sized buffer before copying the box
         self._worker = threading.Thread(target=self._run, daemon=True)
         self._worker.start()
         self.batches = 0
@@ -89,7 +92,7 @@ class Server:
                 group, mem = [], 0
                 rest = []
                 for r in pending:
-                    need = self._need[r.field_id]
+                    need = self._need_of(r)
                     if len(group) < self.max_batch and self.mem_in_use + mem + need <= self.budget:
                         group.append(r)
                         mem += need
@@ -98,7 +101,7 @@ class Server:
                 if not group and not self.inflight and pending:
                     # a single request larger than the budget runs alone
                     group, rest = [pending[0]], pending[1:]
-                    mem = self._need[pending[0].field_id]
+                    mem = self._need_of(pending[0])
                 pending = rest
                 if group:
                     self._launch(group, mem, self.streams[sidx % len(self.streams)])
@@ -106,8 +109,16 @@ class Server:
                     continue
             time.sleep(0.0002)
 
+    def _need_of(self, r):
+        n = self._need[r.field_id]
+        if r.box is not None:
+            h = self.handles[r.field_id]
+            n += h.out_bytes   # the field-sized reconstruction buffer of the box path
+        return n
+
     def _launch(self, group, mem, stream):
-        hs, plans, outs = [], [], []
+        hs, plans, outs, boxes = [], [], [], []
+        live = []
         for r in group:
             h = self.handles[r.field_id]
             try:
@@ -118,19 +129,28 @@ class Server:
                 continue
             r.plan = p
             r.bytes_read = p.bytes
-            hs.append(h)
-            plans.append(p)
-            with torch.cuda.stream(stream):
-                outs.append(torch.empty(h.shape, dtype=h.dtype, device=self.device))
-        live = [r for r in group if r.plan is not None]
+            live.append(r)
+            if r.box is None:
+                hs.append(h)
+                plans.append(p)
+                with torch.cuda.stream(stream):
+                    outs.append(torch.empty(h.shape, dtype=h.dtype, device=self.device))
+            else:
+                boxes.append((r, h, p))
         if not live:
             return
         with torch.cuda.stream(stream):
-            retrieve_batch(hs, plans, outs, stream=stream)
+            if hs:
+                retrieve_batch(hs, plans, outs, stream=stream)
+            res = {}
+            for r, h, p in boxes:
+                res[id(r)] = h.retrieve_box(p, r.box, stream=stream)[0]
+            it = iter(outs)
+            results = [res[id(r)] if r.box is not None else next(it) for r in live]
             ev = torch.cuda.Event()
             ev.record(stream)
         self.mem_in_use += mem
-        self.inflight.append((ev, stream, live, outs, mem))
+        self.inflight.append((ev, stream, live, results, mem))
         self.batches += 1
 
     def _poll(self):
@@ -139,11 +159,8 @@ class Server:
             if ev.query():
                 now = time.perf_counter()
                 for r, o in zip(reqs, outs):
-                    res = o
-                    if r.box is not None:
-                        res = o[tuple(slice(lo, hi) for lo, hi in r.box)]
                     r.t_done = now
-                    r.future.set_result(res)
+                    r.future.set_result(o)
                     self.done.append(r)
                 self.mem_in_use -= mem
             else:
