@@ -1779,6 +1779,50 @@ static pcr_status make_batch_handles(int n, const void* const* d_fields, const i
   return PCR_OK;
 }
 
+// bytes of temporary device memory the refactor of `h` takes inside a batch
+// (upper bound with the 256-byte alignment of every piece): stream staging,
+// the fixed-point 2-grid, the decomposed regions' compact arrays, and its
+// share of the batch's statistics, descriptors and work items
+static size_t refactor_scratch_bytes(const pcr_handle* h) {
+  const size_t w = vsize(h->vk);
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  size_t fix = 0, flt = 0, items = 0;
+  for (auto& g : h->geo) {
+    (g.is_fix ? fix : flt) += g.n_pad();
+    items += (g.n_pad() + kSegElems - 1) / kSegElems;
+  }
+  const size_t ns = h->geo.size();
+  size_t t = al(fix * 8) + al(flt * w) + al(ns * sizeof(StreamD)) + al(std::max<size_t>(items, 1) * sizeof(WorkItem)) +
+             al(sizeof(FieldStats)) + al(ns * 8);
+  if (h->sch.mode == PCR_MODE_PSNR) t += al(ns * h->B * h->B * 8);
+  if (h->L >= 2) {
+    size_t nc = 1;
+    for (int a = 0; a < 3; a++) nc *= h->n3[a] > 1 ? (h->n3[a] - 1) / 2 + 1 : 1;
+    t += al(nc * 8);
+  }
+  if (h->decomp >= 0)
+    for (int r = 1; r <= (int)h->order.size(); r++) t += al((size_t)region_lat(h->n3, 0, h->order, r).n_real() * w);
+  return t + 256;
+}
+
+// one device block for all of a call's temporary buffers, carved in order:
+// a single trip through the caller's allocator instead of one per buffer
+struct ScratchBlock {
+  Mem* mem;
+  cudaStream_t s;
+  void* p = nullptr;
+  ScratchBlock(Mem* m, cudaStream_t st, size_t bytes, Scratch& sc) : mem(m), s(st) {
+    p = mem->alloc(bytes + 256, s);
+    if (p) {
+      sc.bump = (char*)(((uintptr_t)p + 255) & ~uintptr_t(255));
+      sc.cap = bytes;
+    }
+  }
+  ~ScratchBlock() {
+    if (p) mem->free(p, s);
+  }
+};
+
 extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, const int* ndims,
                                          const int64_t* const* dims, const int* dtypes, const pcr_scheme* schemes,
                                          const pcr_allocator* alloc, void* cuda_stream, pcr_handle** outs) {
@@ -1794,7 +1838,11 @@ extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, con
   const BatchLayout L(hs);
   BatchStage io;
   {
+    size_t need = 256 * 8;   // slack: the batch-level pieces are aligned once each
+    for (pcr_handle* h : hs) need += refactor_scratch_bytes(h);
     Scratch sc{&mem, s, {}};
+    ScratchBlock blk(&mem, s, need, sc);
+    if (!blk.p) return fail(PCR_ERR_OOM, "scratch allocation failed");
     e = enqueue_batch(hs, d_fields, s, sc, L, io, false);
     if (e) return e;
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -2360,6 +2408,8 @@ extern "C" pcr_status pcr_retrieve_box(const pcr_handle* h, const pcr_retrieval_
   return PCR_OK;
 }
 
+static size_t retrieve_scratch_bytes(const pcr_handle* h);
+
 extern "C" pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
                                          void* const* d_outs, void* cuda_stream) {
   if (n <= 0 || !hs || !plans || !d_outs) return fail(PCR_ERR_INVALID_ARG, "null argument");
@@ -2367,7 +2417,11 @@ extern "C" pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, con
   for (int k = 0; k < n; k++)
     if (!hs[k] || !d_outs[k]) return fail(PCR_ERR_INVALID_ARG, "null handle or output");
   Mem mem = hs[0]->mem;
+  size_t need = 256 * 4;
+  for (int k = 0; k < n; k++) need += retrieve_scratch_bytes(hs[k]);
   Scratch sc{&mem, s, {}};
+  ScratchBlock blk(&mem, s, need, sc);
+  if (!blk.p) return fail(PCR_ERR_OOM, "scratch allocation failed");
   return retrieve_batch_impl(n, hs, plans, d_outs, s, sc);
 }
 
