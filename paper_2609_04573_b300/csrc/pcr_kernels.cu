@@ -213,13 +213,29 @@ __global__ void k_minmax(const T* __restrict__ x, int64_t n, FieldStats* st) {
   if (threadIdx.x == 0) rbad = 0;
   T lo = x[0], hi = x[0];
   int bad = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const T v = x[i];
+  auto take = [&](T v) {
     bad |= !isfinite(v);
     lo = v < lo ? v : lo;
     hi = v > hi ? v : hi;
+  };
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  int64_t tail = 0;
+  if (((uintptr_t)x & 15) == 0) {   // 16-byte vectors, four loads in flight
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const V* xv = reinterpret_cast<const V*>(x);
+    const int64_t nv = n / (16 / (int64_t)sizeof(T));
+#pragma unroll 4
+    for (int64_t i = tid; i < nv; i += nth) {
+      const V t = __ldg(xv + i);
+      if constexpr (sizeof(T) == 4) {
+        take(t.x); take(t.y); take(t.z); take(t.w);
+      } else {
+        take(t.x); take(t.y);
+      }
+    }
+    tail = nv * (16 / (int64_t)sizeof(T));
   }
+  for (int64_t i = tail + tid; i < n; i += nth) take(x[i]);
   unsigned long long klo = dkey((double)lo), khi = dkey((double)hi);
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
@@ -705,6 +721,32 @@ __device__ __forceinline__ uint32_t sign_record(int p, bool neg, int B, uint32_t
   return rec;
 }
 
+// per-plane sign layout of a segment (32-bit codes): woff[w][k] = elements
+// of plane k in warps before w, poff[k] = first sign word of plane k (an
+// exclusive prefix of the planes' word counts over the lanes), poff[32] =
+// the segment's sign words; wcnt[0][k] becomes the segment total of plane k.
+// Run by warp 0.
+__device__ __forceinline__ void sign_layout32(uint32_t (*wcnt)[32], uint32_t (*woff)[32], uint32_t* poff, int B,
+                                              int lane) {
+  uint32_t acc = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; w++) {
+    const uint32_t c = wcnt[w][lane];
+    woff[w][lane] = acc;
+    acc += c;
+  }
+  wcnt[0][lane] = acc;
+  const uint32_t words = lane < B ? (acc + 31) >> 5 : 0u;
+  uint32_t inc = words;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(FULL, inc, o);
+    inc += lane >= o ? t : 0u;
+  }
+  poff[lane] = inc - words;
+  if (lane == 31) poff[32] = inc;
+}
+
 // Encode one (stream, segment) per CTA.  W = 32 (FP32 fields) or 64 (FP64).
 template <typename VT, int W, bool PAIRS>
 __global__ void __launch_bounds__(kThreads) k_encode(const StreamD* __restrict__ streams,
@@ -819,23 +861,27 @@ __global__ void __launch_bounds__(kThreads) k_encode(const StreamD* __restrict__
   }
   __syncthreads();
   if (generic) {
-    if (threadIdx.x < NP) {
-      const int k = threadIdx.x;
-      uint32_t acc = 0;
-      for (int w = 0; w < kWarps; w++) {
-        woff[w][k] = acc;
-        acc += wcnt[w][k];
+    if constexpr (W == 32) {
+      if (warp == 0) sign_layout32(wcnt, woff, poff, B, lane);
+    } else {
+      if (threadIdx.x < NP) {
+        const int k = threadIdx.x;
+        uint32_t acc = 0;
+        for (int w = 0; w < kWarps; w++) {
+          woff[w][k] = acc;
+          acc += wcnt[w][k];
+        }
+        wcnt[0][k] = acc;   // segment total of plane k
       }
-      wcnt[0][k] = acc;   // segment total of plane k
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t o = 0;
-      for (int k = 0; k < B; k++) {
-        poff[k] = o;
-        o += (wcnt[0][k] + 31) >> 5;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint32_t o = 0;
+        for (int k = 0; k < B; k++) {
+          poff[k] = o;
+          o += (wcnt[0][k] + 31) >> 5;
+        }
+        poff[B] = o;
       }
-      poff[B] = o;
     }
     __syncthreads();
 #pragma unroll
