@@ -1487,7 +1487,10 @@ static pcr_status enqueue_refactor(pcr_handle* h, const void* d_field, cudaStrea
     if (level == 0 && h->decomp >= 0) {
       for (int r = 1; r <= f.d; r++) {
         const Lat R = region_lat(h->n3, 0, h->order, r);
-        a.reg[r - 1] = tile_region(h, R, 0, R.count[2], 0, comp[r], nullptr);
+        // max |c| over level 0 for the rounding allowance, taken while the
+        // coefficients are formed
+        a.reg[r - 1] = tile_region(h, R, 0, R.count[2], 0, comp[r], c0);
+        a.reg[r - 1].vmax_double = 1;
       }
     } else {
       level_regions(h, level, sds, a);
@@ -1508,7 +1511,7 @@ static pcr_status enqueue_refactor(pcr_handle* h, const void* d_field, cudaStrea
       decomp_subs(h, r, sds, da);
       da.retrieve = 0;
       da.comp = comp[r];
-      da.c0 = c0;     // max |c| over the region, for the rounding allowance
+      da.c0 = nullptr;   // max |c| taken by the level-0 prediction
       {
         Prof pf(da.retrieve ? "recompose" : "decompose", s);
         launch_tile_decomp(h->vk, da, s);

@@ -71,6 +71,7 @@ struct TileRegion {
   int64_t base;        // element offset of the region's lattice in `stage`
   void* stage;
   unsigned long long* vmax;   // refactor: stream maximum slot (may be null)
+  int vmax_double;            // 1: the slot holds the bits of a double (field statistics' max |c|)
 };
 
 // arguments of the tiled interpolation kernel (one level, all regions)

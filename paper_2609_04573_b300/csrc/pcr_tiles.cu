@@ -224,7 +224,8 @@ __device__ __forceinline__ void tile_pass(const TileArgs& a, A* __restrict__ S, 
   (void)nwarp;
   if (!retrieve) {
     if constexpr (std::is_same<A, float>::value) imx = __float_as_uint(fmx);
-    push_max(R.vmax, imx, sizeof(A));
+    if (R.vmax_double) push_max_double<A>(R.vmax, imx);
+    else push_max(R.vmax, imx, sizeof(A));
   }
 }
 
@@ -587,9 +588,7 @@ __global__ void __launch_bounds__(128) k_decomp_blk(DecompArgs a) {
 #pragma unroll
           for (int e = 0; e < VEC; e++) x[du][dv].v[e] = A(0);
       }
-    // magnitudes as order-preserving bit patterns (|v| of an IEEE value)
-    using M = std::conditional_t<sizeof(A) == 4, unsigned, unsigned long long>;
-    M mx[5] = {0, 0, 0, 0, 0}, cm = 0;
+    A mx[5] = {A(0), A(0), A(0), A(0), A(0)};   // max |value| per sub-level
 #pragma unroll
     for (int du = 0; du < 4; du++)
 #pragma unroll
@@ -597,11 +596,6 @@ __global__ void __launch_bounds__(128) k_decomp_blk(DecompArgs a) {
         if (!(vu[du] && vv[dv])) continue;
         const int sl = blk_slot(du, dv);
         V d = x[du][dv];
-#pragma unroll
-        for (int e = 0; e < VEC; e++) {
-          const M cg = (M)TAr<A>::mag(d.v[e]);
-          cm = cg > cm ? cg : cm;
-        }
         if (sl != 0) {
           const V w = predict(du, dv, sl <= 2 ? 2 : 1);
 #pragma unroll
@@ -609,14 +603,10 @@ __global__ void __launch_bounds__(128) k_decomp_blk(DecompArgs a) {
         }
         vst<A, VEC>(srow(sl, du, dv), d);
 #pragma unroll
-        for (int e = 0; e < VEC; e++) {
-          const M mg = (M)TAr<A>::mag(d.v[e]);
-          mx[sl] = mg > mx[sl] ? mg : mx[sl];
-        }
+        for (int e = 0; e < VEC; e++) mx[sl] = fmax(mx[sl], fabs(d.v[e]));
       }
 #pragma unroll
-    for (int q = 0; q < 5; q++) push_max(a.subs[q].vmax, mx[q], sizeof(A));
-    push_max_double<A>(a.c0, cm);
+    for (int q = 0; q < 5; q++) push_max(a.subs[q].vmax, TAr<A>::mag(mx[q]), sizeof(A));
     return;
   }
   // recompose: decoded sub-level values of the block and of the next 4-grid
@@ -1028,9 +1018,12 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
     __syncthreads();
   }
   if (!RET) {
-    push_max(a.reg[0].vmax, MX::bits(mx1), sizeof(A));
-    push_max(a.reg[1].vmax, MX::bits(mx2), sizeof(A));
-    push_max(a.reg[2].vmax, MX::bits(mx3), sizeof(A));
+    const unsigned long long m[3] = {MX::bits(mx1), MX::bits(mx2), MX::bits(mx3)};
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+      if (a.reg[r].vmax_double) push_max_double<A>(a.reg[r].vmax, m[r]);
+      else push_max(a.reg[r].vmax, m[r], sizeof(A));
+    }
   }
 }
 
