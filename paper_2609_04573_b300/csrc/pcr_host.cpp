@@ -810,8 +810,15 @@ struct pcr_handle {
   mutable std::mutex plan_mu;
   mutable bool units_ok[2] = {false, false};
   mutable std::vector<Unit> units[2];
+  // work list of a whole retrieval (every segment of every stream; stream
+  // numbers local to the handle), float streams then fixed-point streams;
+  // built by the refactor while its kernels run, reused by every
+  // single-handle retrieval
+  WorkItem* d_items_all = nullptr;
+  size_t items_n[2] = {0, 0};
   ~pcr_handle() {
     cudaStream_t s = 0;
+    if (d_items_all) mem.free(d_items_all, s);
     mem.free(d_planes, s);
     mem.free(d_signs, s);
     mem.free(d_scnt, s);
@@ -1690,6 +1697,25 @@ static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* 
       for (int64_t g = 0; g < sds[i].nseg; g++) items[h->w64][fx].push_back({idx, (int)g});
     }
   }
+  // each handle's whole-retrieval work list, kept on the device
+  for (int k = 0; k < n; k++) {
+    pcr_handle* h = hs[k];
+    if (h->d_items_all) continue;
+    std::vector<WorkItem> li;
+    for (int fx = 0; fx < 2; fx++) {
+      h->items_n[fx] = 0;
+      for (int i = 0; i < (int)h->geo.size(); i++) {
+        if ((int)h->geo[i].is_fix != fx) continue;
+        const int64_t nseg = (h->geo[i].n_pad() + kSegElems - 1) / kSegElems;
+        for (int64_t g = 0; g < nseg; g++) li.push_back({i, (int)g});
+        h->items_n[fx] += nseg;
+      }
+    }
+    if (li.empty()) continue;
+    h->d_items_all = (WorkItem*)h->mem.alloc(li.size() * sizeof(WorkItem), s);
+    if (!h->d_items_all) return fail(PCR_ERR_OOM, "work list allocation failed");
+    CUDA_TRY(cudaMemcpyAsync(h->d_items_all, li.data(), li.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+  }
   size_t nit = 0;
   for (int a = 0; a < 2; a++)
     for (int b = 0; b < 2; b++) nit += items[a][b].size();
@@ -2160,6 +2186,29 @@ static pcr_status retrieve_batch_impl(int n, const pcr_handle* const* hs, const 
   std::vector<std::vector<StreamD>> sds(n);
   std::vector<StreamD> all;
   std::vector<WorkItem> items[2][2];
+  if (n == 1 && hs[0]->d_items_all) {   // one handle: its kept work list
+    const pcr_handle* h = hs[0];
+    std::vector<int> kinds;
+    pcr_status e = enqueue_retrieve_one(h, &plans[0], d_outs[0], s, sc, sds[0], kinds);
+    if (e) return e;
+    StreamD* d_sd = (StreamD*)sc.get(sds[0].size() * sizeof(StreamD));
+    if (!d_sd) return fail(PCR_ERR_OOM, "work list allocation failed");
+    CUDA_TRY(cudaMemcpyAsync(d_sd, sds[0].data(), sds[0].size() * sizeof(StreamD), cudaMemcpyHostToDevice, s));
+    size_t off = 0;
+    for (int fx = 0; fx < 2; fx++) {
+      if (!h->items_n[fx]) continue;
+      const int vk = fx ? VK_FIX : h->vk;
+      {
+        Prof pf(fx ? "decode_fixed" : "decode_float", s);
+        launch_decode(vk, h->w64, d_sd, h->d_items_all + off, (int)h->items_n[fx], s);
+      }
+      off += h->items_n[fx];
+    }
+    e = enqueue_reconstruct(h, sds[0], d_outs[0], s, sc);
+    if (e) return e;
+    CUDA_TRY(cudaGetLastError());
+    return PCR_OK;
+  }
   for (int k = 0; k < n; k++) {
     std::vector<int> kinds;
     pcr_status e = enqueue_retrieve_one(hs[k], &plans[k], d_outs[k], s, sc, sds[k], kinds);
