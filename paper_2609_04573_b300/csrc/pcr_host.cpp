@@ -1167,28 +1167,32 @@ struct LinfEval {
   int L;
   std::vector<std::vector<int>> ids;         // stream ids per level (stream order)
   std::vector<double> E_in;                  // E entering each level for the current errors
+  // each level's region sums for the current errors: a step changes one
+  // level's streams, so the other levels' sums are reused as they are
+  std::vector<std::vector<std::pair<int, double>>> reg_cur;
   mutable std::vector<std::pair<int, double>> reg;
   explicit LinfEval(const Composer& comp) : c(comp), L(comp.m.L) {
     ids.resize(L);
     for (int l = 0; l < L; l++) ids[l] = c.by_level.at(l);
     E_in.assign(L, 0.0);
+    reg_cur.resize(L);
   }
-  void region_errors(int level, const std::vector<double>& err) const {
-    reg.clear();
+  void region_errors(int level, const std::vector<double>& err, std::vector<std::pair<int, double>>& out) const {
+    out.clear();
     for (int i : ids[level]) {
       const int r = c.st[i].region;
       bool found = false;
-      for (auto& pr : reg)
+      for (auto& pr : out)
         if (pr.first == r) {
           pr.second = pr.second + err[i];
           found = true;
         }
-      if (!found) reg.push_back({r, 0.0 + err[i]});
+      if (!found) out.push_back({r, 0.0 + err[i]});
     }
   }
   double top(const std::vector<double>& err) const { return err[ids[L - 1][0]] + (L - 1 >= 1 ? c.m.h : 0.0); }
-  // bound with levels >= `from` as in E_in, levels < `from` from err;
-  // `keep` stores the E entering each recomputed level
+  // bound with the errors `err`, of which only level `from`'s streams may
+  // differ from the kept state; `keep` makes `err` the kept state
   double eval_from(int from, const std::vector<double>& err, bool keep) {
     if (L == 1) return (top(err) + c.rho0(0.0, 0.0)) * kMargin;
     double E;
@@ -1201,10 +1205,16 @@ struct LinfEval {
       level = from;
     }
     for (; level >= 0; level--) {
+      const std::vector<std::pair<int, double>>* rg;
+      if (level == from || reg_cur[level].empty()) {
+        region_errors(level, err, keep ? reg_cur[level] : reg);
+        rg = keep ? &reg_cur[level] : &reg;
+      } else {
+        rg = &reg_cur[level];
+      }
       if (keep) E_in[level] = E;
-      region_errors(level, err);
-      const double rho = level == 0 ? c.rho0(E, Composer::sum_vals(reg)) : c.rho_fix;
-      E = c.level_step(E, reg, rho);
+      const double rho = level == 0 ? c.rho0(E, Composer::sum_vals(*rg)) : c.rho_fix;
+      E = c.level_step(E, *rg, rho);
     }
     return E * kMargin;
   }
