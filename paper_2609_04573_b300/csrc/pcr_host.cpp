@@ -816,13 +816,10 @@ struct pcr_handle {
   // single-handle retrieval
   WorkItem* d_items_all = nullptr;
   size_t items_n[2] = {0, 0};
+  bool items_ready = false;
+  void* d_block = nullptr;   // one allocation holding planes, signs, counts and the work list
   ~pcr_handle() {
-    cudaStream_t s = 0;
-    if (d_items_all) mem.free(d_items_all, s);
-    mem.free(d_planes, s);
-    mem.free(d_signs, s);
-    mem.free(d_scnt, s);
-    mem.free(d_nz, s);
+    if (d_block) mem.free(d_block, 0);
   }
 };
 
@@ -1602,11 +1599,26 @@ static pcr_status finish_refactor(pcr_handle* h, const FieldStats& st, const std
 }
 
 static pcr_status alloc_handle_buffers(pcr_handle* h, cudaStream_t s) {
-  h->d_planes = (uint32_t*)h->mem.alloc(h->plane_words * 4, s);
-  h->d_signs = (uint32_t*)h->mem.alloc(std::max<size_t>(h->sign_area_words, 1) * 4, s);
-  h->d_scnt = (uint32_t*)h->mem.alloc(std::max<size_t>(h->scnt_words, 1) * 4, s);
-  h->d_nz = (uint32_t*)h->mem.alloc(h->nz_words * 4, s);
-  if (!h->d_planes || !h->d_signs || !h->d_scnt || !h->d_nz) return fail(PCR_ERR_OOM, "handle allocation failed");
+  // one allocation, carved in 256-byte aligned pieces
+  size_t items = 0;
+  for (auto& g : h->geo) items += (g.n_pad() + kSegElems - 1) / kSegElems;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t b_pl = al(h->plane_words * 4), b_sg = al(std::max<size_t>(h->sign_area_words, 1) * 4),
+               b_sc = al(std::max<size_t>(h->scnt_words, 1) * 4), b_nz = al(h->nz_words * 4),
+               b_it = al(std::max<size_t>(items, 1) * sizeof(WorkItem));
+  h->d_block = h->mem.alloc(b_pl + b_sg + b_sc + b_nz + b_it + 256, s);
+  if (!h->d_block) return fail(PCR_ERR_OOM, "handle allocation failed");
+  char* p = (char*)(((uintptr_t)h->d_block + 255) & ~uintptr_t(255));
+  h->d_planes = (uint32_t*)p;
+  p += b_pl;
+  h->d_signs = (uint32_t*)p;
+  p += b_sg;
+  h->d_scnt = (uint32_t*)p;
+  p += b_sc;
+  h->d_nz = (uint32_t*)p;
+  p += b_nz;
+  h->d_items_all = (WorkItem*)p;
+  h->items_ready = false;
   // unused tails of sign slots stay zero, so containers are deterministic
   if (h->sign_area_words) CUDA_TRY(cudaMemsetAsync(h->d_signs, 0, h->sign_area_words * 4, s));
   return PCR_OK;
@@ -1710,7 +1722,7 @@ static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* 
   // each handle's whole-retrieval work list, kept on the device
   for (int k = 0; k < n; k++) {
     pcr_handle* h = hs[k];
-    if (h->d_items_all) continue;
+    if (h->items_ready) continue;
     std::vector<WorkItem> li;
     for (int fx = 0; fx < 2; fx++) {
       h->items_n[fx] = 0;
@@ -1722,9 +1734,8 @@ static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* 
       }
     }
     if (li.empty()) continue;
-    h->d_items_all = (WorkItem*)h->mem.alloc(li.size() * sizeof(WorkItem), s);
-    if (!h->d_items_all) return fail(PCR_ERR_OOM, "work list allocation failed");
     CUDA_TRY(cudaMemcpyAsync(h->d_items_all, li.data(), li.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+    h->items_ready = true;
   }
   size_t nit = 0;
   for (int a = 0; a < 2; a++)
@@ -2196,7 +2207,7 @@ static pcr_status retrieve_batch_impl(int n, const pcr_handle* const* hs, const 
   std::vector<std::vector<StreamD>> sds(n);
   std::vector<StreamD> all;
   std::vector<WorkItem> items[2][2];
-  if (n == 1 && hs[0]->d_items_all) {   // one handle: its kept work list
+  if (n == 1 && hs[0]->items_ready) {   // one handle: its kept work list
     const pcr_handle* h = hs[0];
     std::vector<int> kinds;
     pcr_status e = enqueue_retrieve_one(h, &plans[0], d_outs[0], s, sc, sds[0], kinds);

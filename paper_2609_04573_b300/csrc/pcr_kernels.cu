@@ -1006,7 +1006,10 @@ __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__
   const int64_t w0 = (int64_t)it.seg * kSegWords;
   VT* out = (VT*)s.stage;
 
-  if (nw == kSegWords && (s.words & 3) == 0) {
+  // 16-byte loads need 16-byte aligned plane rows: a whole number of
+  // 4-word groups per plane and an aligned stream base (streams before this
+  // one with B * words not a multiple of 4 shift it)
+  if (nw == kSegWords && (s.words & 3) == 0 && ((uintptr_t)s.planes & 15) == 0) {
     for (int i = threadIdx.x; i < b * (kSegWords / 4); i += kThreads) {
       const int k = i >> 5, c = i & 31;
       uint4 v = make_uint4(0u, 0u, 0u, 0u);

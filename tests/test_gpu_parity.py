@@ -45,6 +45,9 @@ CASES = [
     ((36, 33, 132), np.float32, dict(interp="level", degree="linear")),
     ((18, 20, 66), np.float64, dict(interp="level", degree="cubic", decomp_axis=1)),
     ((24, 17, 40), np.float32, dict(mode="psnr", interp="level", degree="cubic")),
+    # B not a multiple of 4 with whole 4096-value segments: plane rows of
+    # later streams start off 16-byte boundaries
+    ((40, 52, 70), np.float32, dict(interp="level", degree="cubic", decomp_axis=2, nplanes=6)),
 ]
 
 
