@@ -1119,18 +1119,31 @@ __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__
     }
     __syncthreads();
   }
+  // 32-bit codes: lane k holds the first sign bit of plane k for this warp,
+  // fetched by each element with one shuffle
+  uint32_t pbase = 0;
+  if (W == 32 && generic && lane < B) pbase = poff[lane] * 32 + woff[warp][lane];
+  VT* op = out + e0 + (int64_t)warp * kWordsPerWarp * 32 + lane;
 #pragma unroll
   for (int jj = 0; jj < kWordsPerWarp; jj++) {
     const int j = warp * kWordsPerWarp + jj;
     if (j >= nw) continue;
     bool neg = false;
     const uint32_t r = rec[jj];
-    if (generic && r != 0xFFFFFFFFu) {
+    if (W == 32) {
+      if (generic) {
+        const uint32_t base = __shfl_sync(FULL, pbase, r & 31);
+        if (r != 0xFFFFFFFFu) {
+          const uint32_t bit = base + ((r >> 7) & 8191);
+          neg = (sbuf[bit >> 5] >> (bit & 31)) & 1u;
+        }
+      }
+    } else if (generic && r != 0xFFFFFFFFu) {
       const int p = r & 127;
       const uint32_t bit = poff[p] * 32 + woff[warp][p] + ((r >> 7) & 8191);
       neg = (sbuf[bit >> 5] >> (bit & 31)) & 1u;
     }
-    out[e0 + (int64_t)j * 32 + lane] = dequantize<VT, W>(qs[jj], neg, s);
+    op[jj * 32] = dequantize<VT, W>(qs[jj], neg, s);
   }
 }
 

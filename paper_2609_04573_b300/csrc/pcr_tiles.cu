@@ -774,6 +774,17 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
     r = b1 + ri;
     c = b2 + 1 + 2 * oj;
   };
+  // FP32 cubic: pass 3 takes pairs of adjacent odd columns (c, c + 2), which
+  // share their even neighbours and whose coefficients are adjacent
+  constexpr bool PAIR = sizeof(A) == 4 && DEG == 3;
+  static_assert(!PAIR || (N3 % 2 == 0), "pairs");
+  auto p3pair = [&](int pi, int& ri, int& oj, int& r, int& c) {
+    const int q = tid + NT * pi;
+    ri = q / (CO / 2);
+    oj = 2 * (q & (CO / 2 - 1));
+    r = b1 + ri;
+    c = b2 + 1 + 2 * oj;
+  };
   auto in_tile = [&](int r, int c) { return r >= b1 && r < b1 + T1 && c >= b2 && c < b2 + T2; };
 
   // ---- prefetch registers
@@ -863,12 +874,24 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
       const bool ok = p2pt(it, ri, cj, r, c) && in_tile(r, c) && r < m1 && c < m2;
       h2[it] = ok ? g2[B2 + (int64_t)(r >> 1) * rp2 + (c >> 1)] : A(0);
     }
+    if constexpr (PAIR) {
 #pragma unroll
-    for (int it = 0; it < N3; it++) {
-      int ri, oj, r, c;
-      p3pt(it, ri, oj, r, c);
-      const bool ok = r < m1 && c < m2;
-      h3[it] = ok ? g3[B3 + (int64_t)r * rp3 + (c >> 1)] : A(0);
+      for (int pi = 0; pi < N3 / 2; pi++) {
+        int ri, oj, r, c;
+        p3pair(pi, ri, oj, r, c);
+        float2 t = make_float2(0.0f, 0.0f);
+        if (r < m1 && c < m2) t = *reinterpret_cast<const float2*>(g3 + B3 + (int64_t)r * rp3 + (c >> 1));
+        h3[2 * pi] = t.x;
+        h3[2 * pi + 1] = t.y;
+      }
+    } else {
+#pragma unroll
+      for (int it = 0; it < N3; it++) {
+        int ri, oj, r, c;
+        p3pt(it, ri, oj, r, c);
+        const bool ok = r < m1 && c < m2;
+        h3[it] = ok ? g3[B3 + (int64_t)r * rp3 + (c >> 1)] : A(0);
+      }
     }
   };
 
@@ -976,7 +999,39 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
     }
     __syncthreads();
     // pass 3 along axis 2: odd i2 of the tile rows
-    {
+    if constexpr (PAIR) {
+      const int64_t B3 = base3(i0);
+#pragma unroll
+      for (int pi = 0; pi < N3 / 2; pi++) {
+        int ri, oj, r, c;
+        p3pair(pi, ri, oj, r, c);
+        if (r >= m1 || c >= m2) continue;   // c + 2 < m2 too: m2 is a multiple of 4
+        const int pr = ri + HR;
+        const int cj = oj + HR / 2 + PAD;   // Pe column of c - 1 (even)
+        A W0, W1;
+        if (c >= 3 && c + 5 < m2) {
+          const A e0 = Pe[pr][cj - 1];
+          const float2 e12 = *reinterpret_cast<const float2*>(&Pe[pr][cj]);
+          const float2 e34 = *reinterpret_cast<const float2*>(&Pe[pr][cj + 2]);
+          W0 = TAr<A>::cub(e0, e12.x, e12.y, e34.x);
+          W1 = TAr<A>::cub(e12.x, e12.y, e34.x, e34.y);
+        } else {
+          auto at0 = [&](int k) -> A { return Pe[pr][cj + ((k - (c - 1)) >> 1)]; };
+          auto at1 = [&](int k) -> A { return Pe[pr][cj + 1 + ((k - (c + 1)) >> 1)]; };
+          W0 = rule<A>(c, m2, DEG, at0);
+          W1 = rule<A>(c + 2, m2, DEG, at1);
+        }
+        if (!RET) {
+          const float2 x = *reinterpret_cast<const float2*>(&Po[ri][oj]);
+          const A c0v = TAr<A>::sub(x.x, W0), c1v = TAr<A>::sub(x.y, W1);
+          *reinterpret_cast<float2*>(g3 + B3 + (int64_t)r * rp3 + (c >> 1)) = make_float2(c0v, c1v);
+          mx3 = MX::upd(MX::upd(mx3, c0v), c1v);
+        } else {
+          Xo[ri][c - b2] = TAr<A>::add(W0, c3[2 * pi]);
+          Xo[ri][c + 2 - b2] = TAr<A>::add(W1, c3[2 * pi + 1]);
+        }
+      }
+    } else {
       const int64_t B3 = base3(i0);
 #pragma unroll
       for (int it = 0; it < N3; it++) {
