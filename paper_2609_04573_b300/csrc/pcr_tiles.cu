@@ -719,6 +719,13 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
   constexpr int NLV = (PR * NV + NT - 1) / NT;        // plane vectors per thread
   constexpr int N1 = (CR * CE + NT - 1) / NT;         // ring / pass-1 points per thread
   constexpr int N2 = ((T1 / 2) * CE + NT - 1) / NT;   // pass-2 points per thread
+  // FP32 cubic refactor: pass 2 in pairs of even columns (2k-1, 2k),
+  // k = 1..CE/2, with column 0 alone: K2 items per row (the retrieval
+  // measured faster with single points here)
+  constexpr bool PAIR2 = sizeof(A) == 4 && DEG == 3 && !RET;
+  constexpr int K2 = (CE + 1) / 2;
+  constexpr int N2P = ((T1 / 2) * K2 + NT - 1) / NT;
+  constexpr int N2V = PAIR2 ? 2 * N2P : N2;              // pass-2 values per thread
   constexpr int N3 = (T1 * CO) / NT;                  // pass-3 points per thread
   static_assert((T1 * CO) % NT == 0 && (CO & (CO - 1)) == 0, "tile shape");
 
@@ -767,6 +774,17 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
     c = b2 - HR + 2 * cj;
     return i < (T1 / 2) * CE;
   };
+  // pair item: column cj (and cj + 1 when pair), row r; false past the end
+  auto p2pair = [&](int it, int& ri, int& cj, int& r, int& c, bool& pair) {
+    const int i = tid + NT * it;
+    ri = i / K2;
+    const int k = i - ri * K2;
+    pair = k > 0;
+    cj = pair ? 2 * k - 1 : 0;
+    r = b1 + 1 + 2 * ri;
+    c = b2 - HR + 2 * cj;
+    return i < (T1 / 2) * K2;
+  };
   auto p3pt = [&](int it, int& ri, int& oj, int& r, int& c) {
     const int i = tid + NT * it;
     ri = i / CO;
@@ -790,7 +808,7 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
   // ---- prefetch registers
   A rg[N1];                     // coarse values of one even plane (ring points)
   VecT<A, VEC> pv[RET ? 1 : NLV];   // refactor: field rows of one plane
-  A h1[RET ? N1 : 1], h2[RET ? N2 : 1], h3[RET ? N3 : 1];   // retrieve: c_hat of one plane
+  A h1[RET ? N1 : 1], h2[RET ? N2V : 1], h3[RET ? N3 : 1];   // retrieve: c_hat of one plane
 
   auto fetch_ring = [&](int p) {
 #pragma unroll
@@ -868,11 +886,25 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
       }
     }
     const int64_t B2 = base2(i0), B3 = base3(i0);
+    if constexpr (PAIR2) {
 #pragma unroll
-    for (int it = 0; it < N2; it++) {
-      int ri, cj, r, c;
-      const bool ok = p2pt(it, ri, cj, r, c) && in_tile(r, c) && r < m1 && c < m2;
-      h2[it] = ok ? g2[B2 + (int64_t)(r >> 1) * rp2 + (c >> 1)] : A(0);
+      for (int it = 0; it < N2P; it++) {
+        int ri, cj, r, c;
+        bool pair;
+        float2 t = make_float2(0.0f, 0.0f);
+        // pairs inside the tile: both points (c + 2 < m2 when c < m2)
+        if (p2pair(it, ri, cj, r, c, pair) && pair && in_tile(r, c) && in_tile(r, c + 2) && r < m1 && c < m2)
+          t = *reinterpret_cast<const float2*>(g2 + B2 + (int64_t)(r >> 1) * rp2 + (c >> 1));
+        h2[2 * it] = t.x;
+        h2[2 * it + 1] = t.y;
+      }
+    } else {
+#pragma unroll
+      for (int it = 0; it < N2; it++) {
+        int ri, cj, r, c;
+        const bool ok = p2pt(it, ri, cj, r, c) && in_tile(r, c) && r < m1 && c < m2;
+        h2[it] = ok ? g2[B2 + (int64_t)(r >> 1) * rp2 + (c >> 1)] : A(0);
+      }
     }
     if constexpr (PAIR) {
 #pragma unroll
@@ -912,12 +944,12 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
     // coarse plane i0 + 3 (the slot of plane i0 - 5)
     if (!RET) store_plane();
     if (odd) store_ring(i0 + 3);
-    A c1[RET ? N1 : 1], c2[RET ? N2 : 1], c3[RET ? N3 : 1];
+    A c1[RET ? N1 : 1], c2[RET ? N2V : 1], c3[RET ? N3 : 1];
     if (RET) {
 #pragma unroll
       for (int it = 0; it < N1; it++) c1[it] = h1[it];
 #pragma unroll
-      for (int it = 0; it < N2; it++) c2[it] = h2[it];
+      for (int it = 0; it < N2V; it++) c2[it] = h2[it];
 #pragma unroll
       for (int it = 0; it < N3; it++) c3[it] = h3[it];
     }
@@ -971,7 +1003,54 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
       __syncthreads();
     }
     // pass 2 along axis 1: odd i1 in the tile, even i2 over tile + halo
-    {
+    if constexpr (PAIR2) {
+      const int64_t B2 = base2(i0);
+#pragma unroll
+      for (int it = 0; it < N2P; it++) {
+        int ri, cj, r, c;
+        bool pair;
+        if (!p2pair(it, ri, cj, r, c, pair) || r >= m1 || c < 0 || c >= m2) continue;
+        const int pr = r - (b1 - HR);
+        const int pc = cj + PAD;
+        if (!pair) {   // column 0: the left halo column alone
+          A W;
+          if (r >= 3 && r + 3 < m1) {
+            W = TAr<A>::cub(Pe[pr - 3][pc], Pe[pr - 1][pc], Pe[pr + 1][pc], Pe[pr + 3][pc]);
+          } else {
+            auto at = [&](int k) -> A { return Pe[pr + (k - r)][pc]; };
+            W = rule<A>(r, m1, DEG, at);
+          }
+          Pe[pr][pc] = W;
+          continue;
+        }
+        float2 W;   // columns pc, pc + 1 (pc even)
+        if (r >= 3 && r + 3 < m1) {
+          const float2 a3 = *reinterpret_cast<const float2*>(&Pe[pr - 3][pc]);
+          const float2 a1 = *reinterpret_cast<const float2*>(&Pe[pr - 1][pc]);
+          const float2 p1 = *reinterpret_cast<const float2*>(&Pe[pr + 1][pc]);
+          const float2 p3 = *reinterpret_cast<const float2*>(&Pe[pr + 3][pc]);
+          W.x = TAr<A>::cub(a3.x, a1.x, p1.x, p3.x);
+          W.y = TAr<A>::cub(a3.y, a1.y, p1.y, p3.y);
+        } else {
+          auto at0 = [&](int k) -> A { return Pe[pr + (k - r)][pc]; };
+          auto at1 = [&](int k) -> A { return Pe[pr + (k - r)][pc + 1]; };
+          W.x = rule<A>(r, m1, DEG, at0);
+          W.y = rule<A>(r, m1, DEG, at1);
+        }
+        if (in_tile(r, c) && in_tile(r, c + 2)) {
+          if (!RET) {
+            const float2 x = *reinterpret_cast<const float2*>(&Pe[pr][pc]);
+            const A c0v = TAr<A>::sub(x.x, W.x), c1v = TAr<A>::sub(x.y, W.y);
+            *reinterpret_cast<float2*>(g2 + B2 + (int64_t)(r >> 1) * rp2 + (c >> 1)) = make_float2(c0v, c1v);
+            mx2 = MX::upd(MX::upd(mx2, c0v), c1v);
+          } else {
+            Xo[r - b1][c - b2] = TAr<A>::add(W.x, c2[2 * it]);
+            Xo[r - b1][c + 2 - b2] = TAr<A>::add(W.y, c2[2 * it + 1]);
+          }
+        }
+        *reinterpret_cast<float2*>(&Pe[pr][pc]) = W;
+      }
+    } else {
       const int64_t B2 = base2(i0);
 #pragma unroll
       for (int it = 0; it < N2; it++) {
