@@ -645,6 +645,102 @@ __global__ void __launch_bounds__(128) k_decomp_blk(DecompArgs a) {
     }
 }
 
+// Decomposition only (same values as k_decomp_blk's forward direction):
+// the 2-grid of the block's neighbourhood stays in registers while S1/S2 are
+// written, then each S3 point is loaded and predicted on its own, so fewer
+// vectors are live at once and more CTAs fit on an SM.
+template <typename A, int VEC>
+__global__ void __launch_bounds__(128, 6) k_decomp_fwd(DecompArgs a) {
+  using V = VecT<A, VEC>;
+  const unsigned nvec = (unsigned)a.ntiles[2], nbb = (unsigned)a.ntiles[1], nab = (unsigned)a.ntiles[0];
+  const unsigned item = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned iv = item % nvec + (unsigned)a.tlo[2], rest = item / nvec;
+  const unsigned bb = rest % nbb + (unsigned)a.tlo[1], ab = rest / nbb + (unsigned)a.tlo[0];
+  const bool live = rest / nbb < nab;
+  const int cu = (int)a.cnt[0], cv = (int)a.cnt[1];
+  const int64_t cw = a.cnt[2];
+  const int u0 = 4 * (int)ab, v0 = 4 * (int)bb;
+  const int64_t k2 = (int64_t)iv * VEC;
+  const A* __restrict__ comp = reinterpret_cast<const A*>(a.comp);
+  bool vu[5], vv[5];
+#pragma unroll
+  for (int d = 0; d < 5; d++) {
+    vu[d] = live && u0 + d < cu;
+    vv[d] = live && v0 + d < cv;
+  }
+  auto srow = [&](int sl, int du, int dv) -> A* {
+    const DecompSub& sb = a.subs[sl];
+    const int64_t ui = ((int64_t)ab << (2 - blk_lu(sl))) + ((du - blk_su(sl)) >> blk_lu(sl));
+    const int64_t vi = ((int64_t)bb << (2 - blk_lv(sl))) + ((dv - blk_sv(sl)) >> blk_lv(sl));
+    return reinterpret_cast<A*>(sb.stage) + sb.base + (ui * sb.count[1] + vi) * sb.row_pad + k2;
+  };
+  auto ld = [&](int du, int dv) {
+    V r;
+    if (vu[du] && vv[dv]) vld<A, VEC>(r, comp + ((int64_t)(u0 + du) * cv + (v0 + dv)) * cw + k2);
+    else
+#pragma unroll
+      for (int e = 0; e < VEC; e++) r.v[e] = A(0);
+    return r;
+  };
+  auto lin = [](const V& p, const V& q) {
+    V r;
+#pragma unroll
+    for (int e = 0; e < VEC; e++) r.v[e] = TAr<A>::lin(p.v[e], q.v[e]);
+    return r;
+  };
+  // 2-grid values g[i][j] = c at (2i, 2j), i, j in 0..2
+  V g[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) g[i][j] = ld(2 * i, 2 * j);
+  A mx[5] = {A(0), A(0), A(0), A(0), A(0)};
+  auto emit = [&](int sl, int du, int dv, const V& x, const V& w, bool sub) {
+    V d = x;
+    if (sub)
+#pragma unroll
+      for (int e = 0; e < VEC; e++) d.v[e] = TAr<A>::sub(d.v[e], w.v[e]);
+    vst<A, VEC>(srow(sl, du, dv), d);
+#pragma unroll
+    for (int e = 0; e < VEC; e++) mx[sl] = fmax(mx[sl], fabs(d.v[e]));
+  };
+  // the per-level predictions of Alg. 1 (as in k_decomp_blk): t = 2 from the
+  // 4-grid, t = 1 from the 2-grid; the v pass reads u-pass predictions
+  // S1 (0,0)
+  if (vu[0] && vv[0]) emit(0, 0, 0, g[0][0], g[0][0], false);
+  // S2a (2,0): along u from the 4-grid
+  if (vu[2] && vv[0]) emit(1, 2, 0, g[1][0], vu[4] ? lin(g[0][0], g[2][0]) : g[0][0], true);
+  // S2b (0,2): u on the 4-grid, along v
+  if (vu[0] && vv[2]) emit(2, 0, 2, g[0][1], vv[4] ? lin(g[0][0], g[0][2]) : g[0][0], true);
+  // S2b (2,2): u pass at v = 0 and v = 4, then along v
+  if (vu[2] && vv[2]) {
+    const V lo = vu[4] ? lin(g[0][0], g[2][0]) : g[0][0];
+    const V w = vv[4] ? lin(lo, vu[4] ? lin(g[0][2], g[2][2]) : g[0][2]) : lo;
+    emit(2, 2, 2, g[1][1], w, true);
+  }
+  // S3 from the 2-grid (t = 1): value at 2-grid point (du, dv) even
+  auto G = [&](int du, int dv) -> const V& { return g[du >> 1][dv >> 1]; };
+  auto pass_u1 = [&](int du, int dv) -> V { return vu[du + 1] ? lin(G(du - 1, dv), G(du + 1, dv)) : G(du - 1, dv); };
+#pragma unroll
+  for (int du = 0; du < 4; du++)
+#pragma unroll
+    for (int dv = 0; dv < 4; dv++) {
+      if (((du | dv) & 1) == 0 || !(vu[du] && vv[dv])) continue;
+      V w;
+      if ((dv & 1) == 0) {
+        w = pass_u1(du, dv);
+      } else {
+        const bool uc = (du & 1) == 0;
+        const V lo = uc ? G(du, dv - 1) : pass_u1(du, dv - 1);
+        if (!vv[dv + 1]) w = lo;
+        else w = lin(lo, uc ? G(du, dv + 1) : pass_u1(du, dv + 1));
+      }
+      emit(blk_slot(du, dv), du, dv, ld(du, dv), w, true);
+    }
+#pragma unroll
+  for (int q = 0; q < 5; q++) push_max(a.subs[q].vmax, TAr<A>::mag(mx[q]), sizeof(A));
+}
+
 // zero the padding of every row of a padded lattice in a staging buffer
 template <typename A>
 __global__ void k_zero_pads(LatD lat, A* stage) {
@@ -1431,7 +1527,8 @@ static void run_decomp_blk(const DecompArgs& a0, cudaStream_t s) {
   const int64_t items = a.ntiles[0] * a.ntiles[1] * a.ntiles[2];
   if (items == 0) return;
   count_launch();
-  k_decomp_blk<A, VEC><<<(unsigned)((items + 127) / 128), 128, 0, s>>>(a);
+  if (a.retrieve) k_decomp_blk<A, VEC><<<(unsigned)((items + 127) / 128), 128, 0, s>>>(a);
+  else k_decomp_fwd<A, VEC><<<(unsigned)((items + 127) / 128), 128, 0, s>>>(a);
 }
 
 void launch_tile_decomp(int vk, const DecompArgs& a, cudaStream_t s) {
