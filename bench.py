@@ -119,6 +119,25 @@ class Clocks:
                 "samples": len(self.samples)}
 
 
+def max_over_ranks(ms, world, device):
+    """The timed region's milliseconds, the maximum over the ranks of the
+    process group (every rank refactors and retrieves its own field, so the
+    job ends when the slowest rank does)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(nbytes_per_rank, world, ms):
+    """Whole-job throughput: every rank's field refactored and retrieved
+    (2 x its bytes) within the slowest rank's time."""
+    return world * 2 * nbytes_per_rank / (ms * 1e-3) / 1e9
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -194,11 +213,7 @@ def run_pcr(args):
     torch.cuda.synchronize()
     prof = pcr.profile_read(reset=True)
     pcr.profile_enable(False)
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
 
     # e2e through the public API with host buffers (pinned), copies inside
     xh = torch.from_numpy(X).pin_memory()
@@ -228,7 +243,7 @@ def run_pcr(args):
         return
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6400.0)
-    value = world * 2 * nbytes / (ms * 1e-3) / 1e9
+    value = whole_job_gbs(nbytes, world, ms)
     # per-stage shares and the dominant stage's roofline
     total_prof = sum(v[0] for v in prof.values()) or 1.0
     stages = {k: {"ms_per_step": v[0] / psteps, "launches_per_step": v[1] / psteps,
