@@ -175,9 +175,10 @@ void pcr_refactor_graph_free(pcr_refactor_graph* g);
  * (value kind, direction, degree, level grid) on a stream that is not being
  * captured times every candidate with CUDA events and keeps the fastest;
  * later launches use the table (enable(0) keeps using it without adding).
- * read: up to max_entries entries, keys = 6 int64 per entry (value kind
- * PCR-internal 0 f32 / 1 f64 / 2 fixed point, retrieve 0/1, degree, level
- * grid lengths m0, m1, m2), choice (0 general tile kernel, -1 marching with
+ * read: up to max_entries entries, keys = 7 int64 per entry (value kind
+ * PCR-internal 0 f32 / 1 f64 / 2 fixed point, retrieve 0/1, degree,
+ * interpolation 0 per-level / 1 per-region, level grid lengths m0, m1, m2),
+ * choice (0 general tile kernel, -1 marching with
  * the default chunk, k > 0 marching with k-plane chunks), ms (the winner's
  * time); *n_out = entries in the table; reset clears it afterwards. */
 pcr_status pcr_autotune_enable(int enable);

@@ -438,15 +438,15 @@ def autotune(enable=True):
 
 
 def autotune_table(reset=False):
-    """Tuned entries: {(kind, retrieve, degree, m0, m1, m2): (choice, ms)}."""
+    """Tuned entries: {(kind, retrieve, degree, interp, m0, m1, m2): (choice, ms)}."""
     n = C.c_int()
     _check(_lib.pcr_autotune_read(0, None, None, None, C.byref(n), 0))
     k = n.value
-    keys = (C.c_int64 * (6 * max(k, 1)))()
+    keys = (C.c_int64 * (7 * max(k, 1)))()
     ch = (C.c_int * max(k, 1))()
     ms = (C.c_double * max(k, 1))()
     _check(_lib.pcr_autotune_read(k, keys, ch, ms, C.byref(n), 1 if reset else 0))
-    return {tuple(keys[6 * i:6 * i + 6]): (ch[i], ms[i]) for i in range(min(k, n.value))}
+    return {tuple(keys[7 * i:7 * i + 7]): (ch[i], ms[i]) for i in range(min(k, n.value))}
 
 
 def retrieve_batch(handles, plans, outs, stream=None):

@@ -799,7 +799,7 @@ template <> struct MaxAbs<int64_t> {
 // region 1 starts (1,0,0) step (2,2,2), region 2 (0,1,0) step (1,2,2),
 // region 3 (0,0,1) step (1,1,2) (checked by the launcher).
 // Arithmetic: the 1-D rules of the general tile kernel (same expressions).
-template <typename A, int DEG, bool RET, int T1, int T2>
+template <typename A, int DEG, bool RET, bool IPR, int T1, int T2>
 __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
   constexpr int NT = 256;
   constexpr int HR = DEG - 1;            // reach beyond the tile along i1, i2
@@ -977,7 +977,8 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
 #pragma unroll
       for (int it = 0; it < N1; it++) {
         int ci, cj, r, c;
-        const bool ok = p1pt(it, ci, cj, r, c) && in_tile(r, c) && r < m1 && c < m2;
+        // per-region retrieval rebuilds halo points too: their c_hat as well
+        const bool ok = p1pt(it, ci, cj, r, c) && (IPR || in_tile(r, c)) && r >= 0 && c >= 0 && r < m1 && c < m2;
         h1[it] = ok ? g1[B1 + (int64_t)(r >> 1) * rp1 + (c >> 1)] : A(0);
       }
     }
@@ -998,7 +999,7 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
 #pragma unroll
       for (int it = 0; it < N2; it++) {
         int ri, cj, r, c;
-        const bool ok = p2pt(it, ri, cj, r, c) && in_tile(r, c) && r < m1 && c < m2;
+        const bool ok = p2pt(it, ri, cj, r, c) && (IPR || in_tile(r, c)) && r >= 0 && c >= 0 && r < m1 && c < m2;
         h2[it] = ok ? g2[B2 + (int64_t)(r >> 1) * rp2 + (c >> 1)] : A(0);
       }
     }
@@ -1094,7 +1095,10 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
             Xo[r - b1][c - b2] = TAr<A>::add(W, c1[it]);
           }
         }
-        Pe[2 * ci][cj + PAD] = W;
+        // later passes read predictions (per-level), or originals /
+        // reconstructed values (per-region refactor / retrieval)
+        if (!IPR) Pe[2 * ci][cj + PAD] = W;
+        else if (RET) Pe[2 * ci][cj + PAD] = TAr<A>::add(W, c1[it]);
       }
       __syncthreads();
     }
@@ -1116,7 +1120,7 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
             auto at = [&](int k) -> A { return Pe[pr + (k - r)][pc]; };
             W = rule<A>(r, m1, DEG, at);
           }
-          Pe[pr][pc] = W;
+          if (!IPR) Pe[pr][pc] = W;
           continue;
         }
         float2 W;   // columns pc, pc + 1 (pc even)
@@ -1144,7 +1148,7 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
             Xo[r - b1][c + 2 - b2] = TAr<A>::add(W.y, c2[2 * it + 1]);
           }
         }
-        *reinterpret_cast<float2*>(&Pe[pr][pc]) = W;
+        if (!IPR) *reinterpret_cast<float2*>(&Pe[pr][pc]) = W;
       }
     } else {
       const int64_t B2 = base2(i0);
@@ -1169,7 +1173,8 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
             Xo[r - b1][c - b2] = TAr<A>::add(W, c2[it]);
           }
         }
-        Pe[pr][cj + PAD] = W;
+        if (!IPR) Pe[pr][cj + PAD] = W;
+        else if (RET) Pe[pr][cj + PAD] = TAr<A>::add(W, c2[it]);
       }
     }
     __syncthreads();
@@ -1297,7 +1302,7 @@ static void run_tile_kind(const TileArgs& a, cudaStream_t s) {
   }
 }
 
-template <typename A, int DEG, bool RET, int T1, int T2>
+template <typename A, int DEG, bool RET, bool PR, int T1, int T2>
 static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force) {
   TileArgs a = a0;
   const bool box = a.bhi[0] != 0;
@@ -1328,10 +1333,10 @@ static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force) {
   a.ntiles[0] = (zend - zlo + zc - 1) / zc;
   static bool attr = false;
   if (!attr) {   // shared memory for several CTAs per SM
-    cudaFuncSetAttribute(k_level0_march<A, DEG, RET, T1, T2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_level0_march<A, DEG, RET, PR, T1, T2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr = true;
   }
-  k_level0_march<A, DEG, RET, T1, T2><<<(unsigned)(a.ntiles[0] * cols), 256, 0, s>>>(a, (int)zc);
+  k_level0_march<A, DEG, RET, PR, T1, T2><<<(unsigned)(a.ntiles[0] * cols), 256, 0, s>>>(a, (int)zc);
 }
 
 // the plane-marching kernel covers level 0 of 3-D per-level schemes in a
@@ -1339,7 +1344,8 @@ static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force) {
 template <typename A>
 static bool march_applies(const TileArgs& a) {
   constexpr int VEC = 16 / sizeof(A);
-  if (a.d != 3 || a.interp != 0 || a.order[0] != 0 || a.order[1] != 1 || a.order[2] != 2) return false;
+  // per-level, or per-region in pass order (0, 1, 2): the same region lattices
+  if (a.d != 3 || a.order[0] != 0 || a.order[1] != 1 || a.order[2] != 2) return false;
   if (a.degree != 1 && a.degree != 3) return false;
   if (a.stride[2] != 1 || a.stride[1] != a.m[2] || a.stride[0] != a.m[1] * a.m[2]) return false;
   if (a.m[2] % VEC != 0 || ((uintptr_t)a.src % 16) != 0 || ((uintptr_t)a.dst % 16) != 0) return false;
@@ -1356,12 +1362,23 @@ static bool march_applies(const TileArgs& a) {
 template <typename A>
 static void march_launch(const TileArgs& a, cudaStream_t s, int zc) {
   constexpr int T1 = 16, T2 = sizeof(A) == 4 ? 128 : 64;
+  const bool pr = a.interp != 0;
   if (a.retrieve) {
-    if (a.degree == 3) run_level0_march<A, 3, true, T1, T2>(a, s, zc);
-    else run_level0_march<A, 1, true, T1, T2>(a, s, zc);
+    if (a.degree == 3) {
+      if (pr) run_level0_march<A, 3, true, true, T1, T2>(a, s, zc);
+      else run_level0_march<A, 3, true, false, T1, T2>(a, s, zc);
+    } else {
+      if (pr) run_level0_march<A, 1, true, true, T1, T2>(a, s, zc);
+      else run_level0_march<A, 1, true, false, T1, T2>(a, s, zc);
+    }
   } else {
-    if (a.degree == 3) run_level0_march<A, 3, false, T1, T2>(a, s, zc);
-    else run_level0_march<A, 1, false, T1, T2>(a, s, zc);
+    if (a.degree == 3) {
+      if (pr) run_level0_march<A, 3, false, true, T1, T2>(a, s, zc);
+      else run_level0_march<A, 3, false, false, T1, T2>(a, s, zc);
+    } else {
+      if (pr) run_level0_march<A, 1, false, true, T1, T2>(a, s, zc);
+      else run_level0_march<A, 1, false, false, T1, T2>(a, s, zc);
+    }
   }
 }
 
@@ -1380,12 +1397,13 @@ static void march_launch(const TileArgs& a, cudaStream_t s, int zc) {
 // repeated, so the timing runs leave the same outputs behind.
 namespace {
 struct TuneKey {
-  int vk, ret, deg;
+  int vk, ret, deg, interp;
   int64_t m0, m1, m2;
   bool operator<(const TuneKey& o) const {
     if (vk != o.vk) return vk < o.vk;
     if (ret != o.ret) return ret < o.ret;
     if (deg != o.deg) return deg < o.deg;
+    if (interp != o.interp) return interp < o.interp;
     if (m0 != o.m0) return m0 < o.m0;
     if (m1 != o.m1) return m1 < o.m1;
     return m2 < o.m2;
@@ -1437,7 +1455,7 @@ TuneVal tune(const TileArgs& a, cudaStream_t s) {
 template <typename A>
 bool launch_tuned(int vk, const TileArgs& a, cudaStream_t s) {
   if (!march_applies<A>(a)) return false;
-  const TuneKey key{vk, a.retrieve, a.degree, a.m[0], a.m[1], a.m[2]};
+  const TuneKey key{vk, a.retrieve, a.degree, a.interp, a.m[0], a.m[1], a.m[2]};
   int choice = -1;
   bool have = false;
   {
@@ -1472,8 +1490,8 @@ int autotune_entries(int max_entries, int64_t* keys, int* choice, double* ms) {
     if (k < max_entries) {
       const TuneKey& t = kv.first;
       if (keys) {
-        const int64_t v[6] = {t.vk, t.ret, t.deg, t.m0, t.m1, t.m2};
-        for (int i = 0; i < 6; i++) keys[6 * k + i] = v[i];
+        const int64_t v[7] = {t.vk, t.ret, t.deg, t.interp, t.m0, t.m1, t.m2};
+        for (int i = 0; i < 7; i++) keys[7 * k + i] = v[i];
       }
       if (choice) choice[k] = kv.second.choice;
       if (ms) ms[k] = kv.second.ms;

@@ -16,6 +16,7 @@ CASES = [
     ((40, 52, 67), np.float32, dict(interp="level", degree="cubic", decomp_axis=2)),
     ((36, 33, 132), np.float32, dict(interp="level", degree="linear")),
     ((31, 36, 41), np.float32, dict(interp="region", degree="cubic", order=(2, 0, 1), decomp_axis=1)),
+    ((36, 40, 68), np.float32, dict(interp="region", degree="cubic", decomp_axis=2)),
     ((34, 40, 66), np.float64, dict(interp="level", degree="cubic", decomp_axis=2)),
     ((130, 257), np.float32, dict(interp="level", degree="cubic")),
 ]

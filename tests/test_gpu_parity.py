@@ -48,6 +48,11 @@ CASES = [
     # B not a multiple of 4 with whole 4096-value segments: plane rows of
     # later streams start off 16-byte boundaries
     ((40, 52, 70), np.float32, dict(interp="level", degree="cubic", decomp_axis=2, nplanes=6)),
+    # per-region in pass order (0, 1, 2) on rows of whole 16-byte vectors:
+    # the plane-marching kernel with original / reconstructed sources
+    ((36, 40, 68), np.float32, dict(interp="region", degree="cubic", decomp_axis=2)),
+    ((34, 30, 64), np.float32, dict(mode="psnr", interp="region", degree="linear")),
+    ((20, 24, 34), np.float64, dict(interp="region", degree="cubic")),
 ]
 
 
