@@ -1156,64 +1156,224 @@ const std::vector<Unit>& cached_units(const pcr_handle* h, bool linf) {
   return h->units[linf];
 }
 
-// L-infinity composition (Composer::linf) with the partial results of the
-// coarser levels kept: a step that changes streams of level l only needs
-// levels l .. 0 again.  Same operations in the same order as linf().
-struct LinfEval {
+// Composer::linf and Composer::l2 with the partial results of the coarser
+// levels kept: a step that changes streams of level l only needs levels
+// l .. 0 again.  Every bound is computed with the same operations in the same
+// order as the composer's, so the plans match it exactly.
+struct BoundEval {
+  struct Group {            // one region of a level for the L2 chain
+    int region;
+    std::vector<int> items; // streams in (sub, stream) order
+    bool decomposed;
+    double f1, f2, rfac, rcnt;
+  };
   const Composer& c;
   int L;
-  std::vector<std::vector<int>> ids;         // stream ids per level (stream order)
-  std::vector<double> E_in;                  // E entering each level for the current errors
-  // each level's region sums for the current errors: a step changes one
-  // level's streams, so the other levels' sums are reused as they are
-  std::vector<std::vector<std::pair<int, double>>> reg_cur;
-  mutable std::vector<std::pair<int, double>> reg;
-  explicit LinfEval(const Composer& comp) : c(comp), L(comp.m.L) {
+  bool l2;
+  std::vector<std::vector<int>> ids;     // stream ids per level (stream order)
+  std::vector<std::vector<int>> slot;    // per stream of a level: its region's slot (first appearance)
+  std::vector<int> nslot;
+  std::vector<std::vector<int>> by_id;   // slots in ascending region id
+  std::vector<std::vector<Group>> grp;   // per level, ascending region id
+  std::vector<double> lfac, lcnt;        // per level: level factor, sqrt(point count)
+  double top_cnt = 0;
+  // kept state for the current errors
+  std::vector<double> E_in, N_in, csum;
+  std::vector<std::vector<double>> acc, cn;
+  std::vector<char> acc_ok, cn_ok;
+  std::vector<double> tacc, tcn;
+
+  BoundEval(const Composer& comp, bool use_l2) : c(comp), L(comp.m.L), l2(use_l2) {
     ids.resize(L);
-    for (int l = 0; l < L; l++) ids[l] = c.by_level.at(l);
-    E_in.assign(L, 0.0);
-    reg_cur.resize(L);
-  }
-  void region_errors(int level, const std::vector<double>& err, std::vector<std::pair<int, double>>& out) const {
-    out.clear();
-    for (int i : ids[level]) {
-      const int r = c.st[i].region;
-      bool found = false;
-      for (auto& pr : out)
-        if (pr.first == r) {
-          pr.second = pr.second + err[i];
-          found = true;
+    slot.resize(L);
+    nslot.assign(L, 0);
+    by_id.resize(L);
+    grp.resize(L);
+    lfac.assign(L, 0.0);
+    lcnt.assign(L, 0.0);
+    for (int l = 0; l < L; l++) {
+      ids[l] = c.by_level.at(l);
+      std::vector<int> regs;
+      for (int i : ids[l]) {
+        const int r = c.st[i].region;
+        int k = 0;
+        while (k < (int)regs.size() && regs[k] != r) k++;
+        if (k == (int)regs.size()) regs.push_back(r);
+        slot[l].push_back(k);
+      }
+      nslot[l] = (int)regs.size();
+      std::vector<int> o(regs.size());
+      for (size_t k = 0; k < o.size(); k++) o[k] = (int)k;
+      std::sort(o.begin(), o.end(), [&](int a, int b) { return regs[a] < regs[b]; });
+      by_id[l] = o;
+      if (!l2 || l == L - 1) continue;
+      std::map<int, std::vector<std::pair<int, int>>> groups;
+      for (int i : ids[l]) groups[c.st[i].region].push_back({c.st[i].sub, i});
+      for (auto& g : groups) {
+        auto items = g.second;
+        std::sort(items.begin(), items.end());
+        Group G;
+        G.region = g.first;
+        for (auto& it : items) G.items.push_back(it.second);
+        G.decomposed = items[0].first != 0;
+        G.f1 = G.f2 = 0.0;
+        if (G.decomposed) {
+          const auto f = c.m.decomp_factors.at(g.first);
+          G.f1 = f.first;
+          G.f2 = f.second;
         }
-      if (!found) out.push_back({r, 0.0 + err[i]});
+        G.rfac = G.rcnt = 0.0;
+        if (c.m.interp != 0) {
+          G.rfac = c.m.region_factor.at({l, g.first});
+          G.rcnt = std::sqrt((double)c.m.region_counts.at({l, g.first}));
+        }
+        grp[l].push_back(G);
+      }
+      if (c.m.interp == 0) {
+        lfac[l] = c.m.level_factor.at(l);
+        lcnt[l] = std::sqrt((double)c.m.level_counts.at(l));
+      }
+    }
+    if (l2) top_cnt = std::sqrt((double)c.m.level_counts.at(L - 1));
+    E_in.assign(L, 0.0);
+    N_in.assign(L, 0.0);
+    csum.assign(L, 0.0);
+    acc.resize(L);
+    cn.resize(L);
+    for (int l = 0; l < L; l++) {
+      acc[l].assign(nslot[l], 0.0);
+      cn[l].assign(grp[l].size(), 0.0);
+    }
+    acc_ok.assign(L, 0);
+    cn_ok.assign(L, 0);
+  }
+
+  // region sums in stream order (Composer::region_errors)
+  void sums(int l, const std::vector<double>& err, double* out) const {
+    for (int k = 0; k < nslot[l]; k++) out[k] = 0.0;
+    const auto& s = slot[l];
+    const auto& id = ids[l];
+    for (size_t j = 0; j < id.size(); j++) out[s[j]] = out[s[j]] + err[id[j]];
+  }
+  double sum_vals(int l, const double* a) const {
+    double s = 0.0;
+    for (int k = 0; k < nslot[l]; k++) s += a[k];
+    return s;
+  }
+  // Composer::level_step; the running maximum equals its max over the list
+  double level_step(int l, double E, const double* a, double rho) const {
+    if (c.m.interp == 0) {
+      double e = a[0];
+      for (int k = 0; k < nslot[l]; k++) e = std::max(e, a[k]);
+      return c.lam_d * E + e + rho;
+    }
+    double base = E;
+    for (int k : by_id[l]) base = std::max(base, c.lam * base + a[k] + rho);
+    return base;
+  }
+  // per-region norms of one level (Composer::l2)
+  void norms(int l, const std::vector<double>& sq, double* out, double& cs) const {
+    const auto& gs = grp[l];
+    for (size_t g = 0; g < gs.size(); g++) {
+      const Group& G = gs[g];
+      if (!G.decomposed) {
+        out[g] = std::sqrt(sq[G.items[0]]);
+      } else {
+        const double n1 = std::sqrt(sq[G.items[0]]);
+        const double n2 = std::sqrt(sq[G.items[1]]) + G.f1 * n1;
+        const double n3 = std::sqrt(sq[G.items[2]]) + G.f2 * std::sqrt(n1 * n1 + n2 * n2);
+        out[g] = std::sqrt(n1 * n1 + n2 * n2 + n3 * n3);
+      }
+    }
+    if (c.m.interp == 0) {
+      double s = 0.0;
+      for (size_t g = 0; g < gs.size(); g++) s += out[g] * out[g];
+      cs = std::sqrt(s);
     }
   }
   double top(const std::vector<double>& err) const { return err[ids[L - 1][0]] + (L - 1 >= 1 ? c.m.h : 0.0); }
-  // bound with the errors `err`, of which only level `from`'s streams may
-  // differ from the kept state; `keep` makes `err` the kept state
-  double eval_from(int from, const std::vector<double>& err, bool keep) {
-    if (L == 1) return (top(err) + c.rho0(0.0, 0.0)) * kMargin;
-    double E;
-    int level;
-    if (from >= L - 1) {
-      E = top(err);
-      level = L - 2;
-    } else {
-      E = E_in[from];
-      level = from;
+
+  // bound for the errors err / sq, of which only level `from`'s streams may
+  // differ from the kept state; `keep` makes them the kept state
+  double eval_from(int from, const std::vector<double>& err, const std::vector<double>& sq, bool keep) {
+    if (L == 1) {
+      if (!l2) return (top(err) + c.rho0(0.0, 0.0)) * kMargin;
+      double N = std::sqrt(sq[ids[0][0]]);
+      N += c.rho0(0.0, 0.0) * std::sqrt((double)c.m.level_counts.at(0));
+      return (N * N) * kMargin;
     }
-    for (; level >= 0; level--) {
-      const std::vector<std::pair<int, double>>* rg;
-      if (level == from || reg_cur[level].empty()) {
-        region_errors(level, err, keep ? reg_cur[level] : reg);
-        rg = keep ? &reg_cur[level] : &reg;
+    const int start = std::min(from, L - 2);
+    // the L-infinity chain (for L2: down to the rounding term of level 0)
+    double E = from >= L - 1 ? top(err) : E_in[from];
+    double rho_0 = 0.0;
+    for (int level = start; level >= 0; level--) {
+      const double* a;
+      if (level == from || !acc_ok[level]) {
+        double* o;
+        if (keep) {
+          o = acc[level].data();
+          acc_ok[level] = 1;
+        } else {
+          tacc.resize(nslot[level]);
+          o = tacc.data();
+        }
+        sums(level, err, o);
+        a = o;
       } else {
-        rg = &reg_cur[level];
+        a = acc[level].data();
       }
       if (keep) E_in[level] = E;
-      const double rho = level == 0 ? c.rho0(E, Composer::sum_vals(*rg)) : c.rho_fix;
-      E = c.level_step(E, *rg, rho);
+      if (level == 0) {
+        rho_0 = c.rho0(E, sum_vals(0, a));
+        if (l2) break;
+        E = level_step(0, E, a, rho_0);
+      } else {
+        E = level_step(level, E, a, c.rho_fix);
+      }
     }
-    return E * kMargin;
+    if (!l2) return E * kMargin;
+    double N;
+    if (from >= L - 1) {
+      N = std::sqrt(sq[ids[L - 1][0]]);
+      N += c.m.h * top_cnt;
+    } else {
+      N = N_in[from];
+    }
+    for (int level = start; level >= 0; level--) {
+      const double rho = level == 0 ? rho_0 : c.rho_fix;
+      const double* a;
+      double cs;
+      if (level == from || !cn_ok[level]) {
+        double* o;
+        if (keep) {
+          o = cn[level].data();
+          cn_ok[level] = 1;
+        } else {
+          tcn.resize(grp[level].size());
+          o = tcn.data();
+        }
+        norms(level, sq, o, cs);
+        if (keep) csum[level] = cs;
+        a = o;
+      } else {
+        a = cn[level].data();
+        cs = csum[level];
+      }
+      if (keep) N_in[level] = N;
+      if (c.m.interp == 0) {
+        const double t = lfac[level] * N + cs + rho * lcnt[level];
+        N = std::sqrt(N * N + t * t);
+      } else {
+        double T = N * N;
+        const auto& gs = grp[level];
+        for (size_t g = 0; g < gs.size(); g++) {
+          const double t = gs[g].rfac * std::sqrt(T) + a[g] + rho * gs[g].rcnt;
+          T += t * t;
+        }
+        N = std::sqrt(T);
+      }
+    }
+    return (N * N) * kMargin;
   }
 };
 
@@ -1228,13 +1388,10 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
     err[i] = h->tabs[i].maxerr[0];
     sq[i] = h->tabs[i].sq[0];
   }
-  LinfEval le(h->comp);
+  BoundEval be(h->comp, !linf);
   std::vector<int> unit_level(units.size());
   for (size_t ui = 0; ui < units.size(); ui++) unit_level[ui] = h->geo[units[ui].ids[0]].level;
-  auto evaluate = [&](int level, bool keep) {
-    if (linf) return le.eval_from(level, err, keep);
-    return h->comp.l2(sq, err);
-  };
+  auto evaluate = [&](int level, bool keep) { return be.eval_from(level, err, sq, keep); };
   std::vector<std::pair<int, double>> reg;
   auto unit_value = [&](const Unit& u) {
     if (u.ids.size() == 1) return linf ? err[u.ids[0]] : sq[u.ids[0]];
@@ -1311,7 +1468,7 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
       best_bnd = fb_bnd;
     }
     apply(units[best_u].steps[pos[best_u]]);
-    if (linf) le.eval_from(unit_level[best_u], err, true);   // refresh the kept partial results
+    be.eval_from(unit_level[best_u], err, sq, true);   // refresh the kept partial results
     bound = best_bnd;
     pos[best_u]++;
   }

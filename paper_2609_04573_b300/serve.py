@@ -47,7 +47,7 @@ class Request:
 class Server:
     """Continuous-batching retrieval server over resident handles."""
 
-    def __init__(self, handles, mem_budget=8 << 30, max_batch=32, streams=2, device=None):
+    def __init__(self, handles, mem_budget=8 << 30, max_batch=32, streams=2, device=None, start=True):
         self.handles = list(handles)
         self.budget = int(mem_budget)
         self.max_batch = max_batch
@@ -61,8 +61,15 @@ class Server:
         self._need = [h.retrieve_scratch_bytes() + h.out_bytes for h in self.handles]
         # a box retrieval reconstructs into a field-sized buffer before copying the box
         self._worker = threading.Thread(target=self._run, daemon=True)
-        self._worker.start()
         self.batches = 0
+        if start:
+            self._worker.start()
+
+    def start(self):
+        """Start the worker of a server made with start=False (requests
+        submitted before then wait in the queue and are batched together)."""
+        if self._worker.ident is None:
+            self._worker.start()
 
     def submit(self, field_id, target, box=None):
         r = Request(field_id, target, box, t_submit=time.perf_counter())
@@ -71,6 +78,8 @@ class Server:
 
     def close(self):
         self._stop = True
+        if self._worker.ident is None:   # never started: serve what is queued, then stop
+            self._worker.start()
         self._worker.join()
 
     # ---- worker -----------------------------------------------------------

@@ -63,9 +63,10 @@ def test_server_results_equal_single_retrievals():
         want.append(out[tuple(slice(lo, hi) for lo, hi in box)] if box else out)
     torch.cuda.synchronize()
     budget = 3 * max(h.retrieve_scratch_bytes() + h.out_bytes for h in hs)
-    srv = Server(hs, mem_budget=budget, max_batch=4, streams=2)
-    live = []
-    for f, t, box in reqs:
+    srv = Server(hs, mem_budget=budget, max_batch=4, streams=2, start=False)
+    live = [srv.submit(f, t, box) for f, t, box in reqs[:8]]   # queued before the worker runs
+    srv.start()
+    for f, t, box in reqs[8:]:
         live.append(srv.submit(f, t, box))
         time.sleep(rng.random() * 0.002)
     got = [r.future.result(timeout=60) for r in live]
