@@ -35,11 +35,11 @@ TARGET = ("rel", 1e-4)
 WORKLOAD = "grf_k-5/3_512^3_f32"
 METRIC = "refactor & retrieve GB/s (fraction of HBM roofline) at stated eb/PSNR vs CPU oracle"
 
-# DRAM traffic per launch of the dominant kernel, from the committed ncu
-# summary (profiles/encode_float_grf384.md: 357.9 MB at 384^3, scaled by the
-# level-0 value count to 512^3); absent when the kernel changed after that
-# capture or the run's size differs.
-TRAFFIC_PER_LAUNCH = {("encode_float", 512): 849.0e6}
+# DRAM traffic per launch of the dominant kernel, from a committed ncu
+# summary under profiles/ (scaled by the level-0 value count when captured on
+# a smaller field); absent when the kernel changed after that capture or the
+# run's size differs.
+TRAFFIC_PER_LAUNCH = {}
 
 
 def parse():

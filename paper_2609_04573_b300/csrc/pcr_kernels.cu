@@ -630,8 +630,9 @@ __device__ __forceinline__ double scale2d(double x, int k) {
   return (k >= -1022 && k <= 1023) ? __dmul_rn(x, __longlong_as_double((long long)(k + 1023) << 52)) : ldexp(x, k);
 }
 
-template <typename VT, int W>
-__device__ __forceinline__ code_t<W> quantize(VT v, const StreamD& s, const QParams& qp, bool& neg) {
+// S: any type with the stream's B and enc (StreamD, or a register copy)
+template <typename VT, int W, typename S>
+__device__ __forceinline__ code_t<W> quantize(VT v, const S& s, const QParams& qp, bool& neg) {
   using C = code_t<W>;
   const int B = s.B;
   const C M = (C)nb_mask(B);
@@ -1267,6 +1268,260 @@ void launch_copy_raw(int vk, const FieldD& f, const LatD& lat, const void* vals,
   else k_copy_raw<double><<<grid_for(n), 256, 0, s>>>(f, lat, (const double*)vals, (double*)out);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent encoder for FP32 streams with 32-bit codes (Sec. V-C bitplanes,
+// Sec. VI-A encodings).  Same planes, sign sub-streams, counts and tables as
+// k_encode; organised for throughput:
+//  * each CTA loops over work items; the next segment's 16 KB of values is
+//    copied into shared memory with cp.async while the current one is coded;
+//  * sign ranks come from the transposed planes: F_k = D_k & ~(D_0 | .. |
+//    D_{k-1}) marks the elements first significant at plane k; the word's
+//    signs sorted by (plane, element) are one warp OR-reduction, and lane k
+//    appends its slice of that word to plane k's per-warp bit string;
+//  * plane words leave in 16-byte stores from rows of 132 words.
+// ---------------------------------------------------------------------------
+constexpr int kEncRow = kSegWords + 4;            // pbuf row (16-byte multiple, bank-spread)
+
+// x * 2^k as two multiplies by normal powers of two, chosen per stream so
+// that the first product is exact whenever the result can reach 1: for k in
+// [-126, 127] (2^k, 1); above, (2^127, 2^(k-127)); below, (2^(k+126), 2^-126).
+// Truncated to an integer this equals scale2f(x, k) for every |x| < 2^E.
+struct Scale2 {
+  float m1, m2;
+};
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }   // k in [-126, 127]
+__device__ __forceinline__ Scale2 scale_pair(int k) {
+  if (k > 127) return {pow2f(127), pow2f(k - 127)};
+  if (k < -126) return {pow2f(k + 126), pow2f(-126)};
+  return {pow2f(k), 1.0f};
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// start the copy of one segment's staged values (zero fill past the stream)
+__device__ __forceinline__ void enc_fetch(uint32_t* buf, const float* stage, int64_t e0, int64_t n_pad) {
+  const int64_t avail = n_pad - e0;              // elements of the stream from e0 (multiple of 32)
+  for (int c = threadIdx.x; c < kSegElems / 4; c += kThreads) {
+    const bool ok = (int64_t)c * 4 < avail;
+    cp_async16(buf + c * 4, ok ? (const void*)(stage + e0 + c * 4) : (const void*)(stage), ok ? 16 : 0);
+  }
+}
+
+// sign bit-string of plane `lane` in this warp: index of word i in the
+// warp's 32 x 16 buffer (swizzled so that lanes flushing the same word index
+// hit different banks)
+__device__ __forceinline__ int sb_index(int lane, int i) { return lane * 16 + (i ^ ((lane >> 1) & 15)); }
+
+constexpr int kEncDynSmem = (2 * kSegElems + 32 * kEncRow) * 4;   // two input buffers + plane rows
+
+__global__ void __launch_bounds__(kThreads, 4) k_encode_f32(const StreamD* __restrict__ streams,
+                                                            const WorkItem* __restrict__ items, int nitems) {
+  extern __shared__ __align__(16) uint32_t enc_dyn[];
+  uint32_t* const pbuf = enc_dyn + 2 * kSegElems;
+  __shared__ uint32_t sbuf[kSegWords + 64];
+  __shared__ uint32_t wcnt[kWarps][32];
+  __shared__ uint32_t woff[kWarps][32];
+  __shared__ uint32_t poff[33];
+  __shared__ uint32_t pnz[32];
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const TrC tc = tr_consts(lane);
+  const uint32_t lt = (1u << lane) - 1u;
+
+  int item = blockIdx.x;
+  if (item >= nitems) return;
+  if (threadIdx.x < 32) pnz[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < kSegWords + 64; i += kThreads) sbuf[i] = 0;
+  // the current item's stream fields needed to fetch it, and the next one's
+  WorkItem it = items[item];
+  {
+    const StreamD& s0 = streams[it.stream];
+    enc_fetch(enc_dyn, (const float*)s0.stage, (int64_t)it.seg * kSegElems, s0.n_pad);
+    cp_async_commit();
+  }
+  int nitem = item + gridDim.x;
+  WorkItem nit = nitem < nitems ? items[nitem] : WorkItem{0, 0};
+  const float* nstage = nullptr;
+  int64_t nn_pad = 0;
+  if (nitem < nitems) {
+    nstage = (const float*)streams[nit.stream].stage;
+    nn_pad = streams[nit.stream].n_pad;
+  }
+
+  for (int cur = 0; item < nitems; cur ^= 1) {
+    // (A) the next item's values start moving; the one after is located
+    if (nitem < nitems) enc_fetch(enc_dyn + (cur ^ 1) * kSegElems, nstage, (int64_t)nit.seg * kSegElems, nn_pad);
+    cp_async_commit();
+    const int item2 = nitem + gridDim.x;
+    WorkItem it2{0, 0};
+    const float* stage2 = nullptr;
+    int64_t n_pad2 = 0;
+    if (item2 < nitems) {
+      it2 = items[item2];
+      stage2 = (const float*)streams[it2.stream].stage;
+      n_pad2 = streams[it2.stream].n_pad;
+    }
+    const StreamD& s = streams[it.stream];
+    const int B = s.B;
+    const bool generic = s.enc == 1;
+    const QParams qp = qparams(s);
+    // quantisation (the arithmetic of quantize<float, 32>) with per-item constants
+    const Scale2 sc = scale_pair(generic ? B - qp.E : B - 3 - qp.E);
+    const uint32_t M = (uint32_t)nb_mask(B);
+    const int64_t e0 = (int64_t)it.seg * kSegElems;
+    const int nw = (int)min((int64_t)kSegWords, (s.n_pad - e0) / 32);
+
+    // (B) this item's values have landed (S1)
+    cp_async_wait<1>();
+    __syncthreads();
+
+    // (C) code this warp's 16 words
+    uint32_t* wbuf = enc_dyn + cur * kSegElems + warp * kWordsPerWarp * 32;
+    float v[kWordsPerWarp];
+#pragma unroll
+    for (int jj = 0; jj < kWordsPerWarp; jj++) v[jj] = __uint_as_float(wbuf[jj * 32 + lane]);
+    __syncwarp();                       // the warp's region now holds its sign bit-strings
+    uint32_t acc = 0, fill = 0, wpos = 0, count = 0, nz = 0;
+    uint32_t pw[4];
+#pragma unroll
+    for (int jj = 0; jj < kWordsPerWarp; jj++) {
+      const bool neg = v[jj] < 0.0f;
+      uint32_t q;
+      if (generic) {
+        q = __float2uint_rz(__fmul_rn(__fmul_rn(fabsf(v[jj]), sc.m1), sc.m2));
+      } else {
+        const int sv = __float2int_rz(__fmul_rn(__fmul_rn(v[jj], sc.m1), sc.m2));
+        q = ((uint32_t)sv + M) ^ M;
+      }
+      if (qp.zero) q = 0;
+      const uint32_t xr = q << (32 - B);
+      const uint32_t x = __brev(xr);                     // bit t = plane t (from the top)
+      const uint32_t D = transpose32c(x, tc);             // lane k: plane k of the 32 values
+      uint32_t sl = D;
+      if (!generic) {
+        const uint32_t up = __shfl_up_sync(FULL, D, 1);
+        sl = lane ? D ^ up : D;
+      }
+      pw[jj & 3] = sl;
+      if ((jj & 3) == 3 && lane < B)
+        *reinterpret_cast<uint4*>(&pbuf[lane * kEncRow + warp * kWordsPerWarp + (jj & ~3)]) =
+            make_uint4(pw[0], pw[1], pw[2], pw[3]);
+      nz += sl != 0;
+      if (generic) {
+        // planes above k that hold a one, per element (inclusive prefix OR)
+        uint32_t inc = D;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) inc |= __shfl_up_sync(FULL, inc, o);
+        uint32_t exc = __shfl_up_sync(FULL, inc, 1);
+        exc = lane ? exc : 0u;
+        const uint32_t F = D & ~exc;                     // first significant at plane `lane`
+        const uint32_t cnt = __popc(F), start = __popc(exc);
+        // this element's place in the word's signs sorted by (plane, element)
+        const int pe = __clz(xr) & 31;                   // its plane (any lane when q == 0)
+        const uint32_t Fp = __shfl_sync(FULL, F, pe);
+        const uint32_t sp = __shfl_sync(FULL, start, pe);
+        const uint32_t dest = sp + __popc(Fp & lt);
+        const uint32_t sorted = __reduce_or_sync(FULL, (neg && xr) ? (1u << dest) : 0u);
+        // lane k: its plane's slice [start, start + cnt), appended to the plane's bit-string
+        const uint32_t bits = __funnelshift_rc(sorted, 0u, start) & __funnelshift_lc(~0u, 0u, cnt);
+        acc |= bits << fill;
+        const uint32_t nf = fill + cnt;
+        if (nf >= 32) {
+          wbuf[sb_index(lane, wpos)] = acc;
+          wpos++;
+          acc = __funnelshift_rc(bits, 0u, 32 - fill);   // the part that did not fit (none if fill == 0)
+        }
+        fill = nf & 31;
+        count += cnt;
+      }
+    }
+    if (generic) {
+      if (fill) wbuf[sb_index(lane, wpos)] = acc;
+      wcnt[warp][lane] = count;
+    }
+    if (lane < B && nz) atomicAdd(&pnz[lane], nz);
+    __syncthreads();   // S2
+    // (D) sign layout of the segment, then each plane's bit-strings in place
+    if (generic) {
+      if (warp == 0) sign_layout32(wcnt, woff, poff, B, lane);
+      __syncthreads();   // S3
+      if (count) {
+        const uint32_t O = poff[lane] * 32 + woff[warp][lane];
+        const uint32_t sh = O & 31, base = O >> 5, nwd = (count + 31) >> 5;
+        for (uint32_t i = 0; i < nwd; i++) {
+          const uint32_t w = wbuf[sb_index(lane, i)];
+          atomicOr(&sbuf[base + i], w << sh);
+          if (sh) {
+            const uint32_t hi = w >> (32 - sh);
+            if (hi) atomicOr(&sbuf[base + i + 1], hi);
+          }
+        }
+      }
+      __syncthreads();   // S4
+      uint32_t* dst = s.signs + (int64_t)it.seg * s.slot_words;
+      for (int i = threadIdx.x; i < (int)poff[B]; i += kThreads) dst[i] = sbuf[i];
+      if (threadIdx.x < B) {
+        const uint32_t c = wcnt[0][threadIdx.x];
+        s.sign_counts[(int64_t)it.seg * B + threadIdx.x] = c;
+        if (c) atomicAdd(&s.plane_nz[B + threadIdx.x], (c + 31) >> 5);
+      }
+    }
+    // (E) plane words, four at a time where the rows allow it
+    {
+      const int64_t w0 = (int64_t)it.seg * kSegWords;
+      const bool vec = ((s.words & 3) == 0) && ((((uintptr_t)s.planes) & 15) == 0);
+      for (int c = threadIdx.x; c < B * (kSegWords / 4); c += kThreads) {
+        const int k = c >> 5, j = (c & 31) * 4;
+        if (j >= nw) continue;
+        const uint4 w4 = *reinterpret_cast<const uint4*>(&pbuf[k * kEncRow + j]);
+        uint32_t* g = s.planes + (int64_t)k * s.words + w0 + j;
+        if (vec && j + 4 <= nw) {
+          *reinterpret_cast<uint4*>(g) = w4;
+        } else {
+          g[0] = w4.x;
+          if (j + 1 < nw) g[1] = w4.y;
+          if (j + 2 < nw) g[2] = w4.z;
+          if (j + 3 < nw) g[3] = w4.w;
+        }
+      }
+      if (threadIdx.x < B && pnz[threadIdx.x]) atomicAdd(&s.plane_nz[threadIdx.x], pnz[threadIdx.x]);
+    }
+    // (F) every read of this item's shared memory is done (S5): clear for the next
+    __syncthreads();
+    if (threadIdx.x < 32) pnz[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < kSegWords + 64; i += kThreads) sbuf[i] = 0;
+    item = nitem;
+    it = nit;
+    nitem = item2;
+    nit = it2;
+    nstage = stage2;
+    nn_pad = n_pad2;
+  }
+  cp_async_wait<0>();
+}
+
+// persistent grid of k_encode_f32: the CTAs that fit on the device at once
+static int enc_f32_grid(int nitems) {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& g = cached[dev & 63];
+  if (g == 0) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_encode_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncDynSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_encode_f32, kThreads, kEncDynSmem);
+    g = max(1, sms * max(per, 1));
+  }
+  return min(nitems, g);
+}
+
 // vk: value kind of the streams in this work list; w64: FP64-field word path
 void launch_encode(int vk, int w64, int pairs, const StreamD* d_streams, const WorkItem* d_items,
                    int nitems, cudaStream_t s) {
@@ -1274,7 +1529,10 @@ void launch_encode(int vk, int w64, int pairs, const StreamD* d_streams, const W
   count_launch();
 #define ENC(VT, W, P) k_encode<VT, W, P><<<nitems, kThreads, 0, s>>>(d_streams, d_items)
   if (!w64) {
-    if (vk == VK_F32) { if (pairs) ENC(float, 32, true); else ENC(float, 32, false); }
+    if (vk == VK_F32) {
+      if (pairs) ENC(float, 32, true);
+      else k_encode_f32<<<enc_f32_grid(nitems), kThreads, kEncDynSmem, s>>>(d_streams, d_items, nitems);
+    }
     else { if (pairs) ENC(int64_t, 32, true); else ENC(int64_t, 32, false); }
   } else {
     if (vk == VK_F64) { if (pairs) ENC(double, 64, true); else ENC(double, 64, false); }
