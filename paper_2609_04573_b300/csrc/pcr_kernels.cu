@@ -630,6 +630,21 @@ __device__ __forceinline__ double scale2d(double x, int k) {
   return (k >= -1022 && k <= 1023) ? __dmul_rn(x, __longlong_as_double((long long)(k + 1023) << 52)) : ldexp(x, k);
 }
 
+// x * 2^k as two multiplies by normal powers of two, chosen per stream so
+// that the first product is exact whenever the result can reach 1: for k in
+// [-126, 127] (2^k, 1); above, (2^127, 2^(k-127)); below, (2^(k+126), 2^-126).
+// Truncated to an integer this equals scale2f(x, k) for every |x| < 2^E;
+// applied to a dequantised integer (>= 1 or 0) it rounds once, as scale2f.
+struct Scale2 {
+  float m1, m2;
+};
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }   // k in [-126, 127]
+__device__ __forceinline__ Scale2 scale_pair(int k) {
+  if (k > 127) return {pow2f(127), pow2f(k - 127)};
+  if (k < -126) return {pow2f(k + 126), pow2f(-126)};
+  return {pow2f(k), 1.0f};
+}
+
 // S: any type with the stream's B and enc (StreamD, or a register copy)
 template <typename VT, int W, typename S>
 __device__ __forceinline__ code_t<W> quantize(VT v, const S& s, const QParams& qp, bool& neg) {
@@ -970,12 +985,11 @@ __device__ __forceinline__ uint32_t transpose32c(uint32_t x, const TrC& c) {
 // (used by the decoder; the encoder measured faster with sign_record).
 __device__ __forceinline__ uint32_t sign_rank32(uint32_t d, int p, bool neg, int B, uint32_t& ctr, int lane,
                                                 uint32_t lt) {
+  // inclusive prefix OR over the lanes (a lane below o gets its own value
+  // back from the shuffle, which leaves the OR unchanged)
   uint32_t incl = d;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(FULL, incl, o);
-    incl |= lane >= o ? t : 0u;
-  }
+  for (int o = 1; o < 32; o <<= 1) incl |= __shfl_up_sync(FULL, incl, o);
   uint32_t excl = __shfl_up_sync(FULL, incl, 1);
   excl = lane ? excl : 0u;
   const uint32_t F = d & ~excl;
@@ -1125,6 +1139,12 @@ __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__
   uint32_t pbase = 0;
   if (W == 32 && generic && lane < B) pbase = poff[lane] * 32 + woff[warp][lane];
   VT* op = out + e0 + (int64_t)warp * kWordsPerWarp * 32 + lane;
+  [[maybe_unused]] Scale2 dq{1.0f, 1.0f};
+  [[maybe_unused]] uint32_t nbm = 0;
+  if constexpr (std::is_same<VT, float>::value && W == 32) {
+    dq = scale_pair(generic ? s.E - B : s.E - B + 3);
+    nbm = (uint32_t)nb_mask(B);
+  }
 #pragma unroll
   for (int jj = 0; jj < kWordsPerWarp; jj++) {
     const int j = warp * kWordsPerWarp + jj;
@@ -1144,7 +1164,18 @@ __global__ void __launch_bounds__(kThreads) k_decode(const StreamD* __restrict__
       const uint32_t bit = poff[p] * 32 + woff[warp][p] + ((r >> 7) & 8191);
       neg = (sbuf[bit >> 5] >> (bit & 31)) & 1u;
     }
-    op[jj * 32] = dequantize<VT, W>(qs[jj], neg, s);
+    if constexpr (std::is_same<VT, float>::value && W == 32) {
+      // dequantize<float, 32> with the stream's scaling as two multipliers
+      if (generic) {
+        const float mag = __fmul_rn(__fmul_rn(__uint2float_rn((uint32_t)qs[jj]), dq.m1), dq.m2);
+        op[jj * 32] = neg ? -mag : mag;
+      } else {
+        const int64_t val = (int64_t)((uint64_t)((uint32_t)qs[jj] ^ nbm)) - (int64_t)nbm;
+        op[jj * 32] = __fmul_rn(__fmul_rn(__int2float_rn((int)val), dq.m1), dq.m2);
+      }
+    } else {
+      op[jj * 32] = dequantize<VT, W>(qs[jj], neg, s);
+    }
   }
 }
 
@@ -1282,19 +1313,6 @@ void launch_copy_raw(int vk, const FieldD& f, const LatD& lat, const void* vals,
 // ---------------------------------------------------------------------------
 constexpr int kEncRow = kSegWords + 4;            // pbuf row (16-byte multiple, bank-spread)
 
-// x * 2^k as two multiplies by normal powers of two, chosen per stream so
-// that the first product is exact whenever the result can reach 1: for k in
-// [-126, 127] (2^k, 1); above, (2^127, 2^(k-127)); below, (2^(k+126), 2^-126).
-// Truncated to an integer this equals scale2f(x, k) for every |x| < 2^E.
-struct Scale2 {
-  float m1, m2;
-};
-__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }   // k in [-126, 127]
-__device__ __forceinline__ Scale2 scale_pair(int k) {
-  if (k > 127) return {pow2f(127), pow2f(k - 127)};
-  if (k < -126) return {pow2f(k + 126), pow2f(-126)};
-  return {pow2f(k), 1.0f};
-}
 
 __device__ __forceinline__ void cp_async16(uint32_t* smem, const void* gmem, int src_bytes) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
