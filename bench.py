@@ -39,7 +39,7 @@ METRIC = "refactor & retrieve GB/s (fraction of HBM roofline) at stated eb/PSNR 
 # summary under profiles/ (scaled by the level-0 value count when captured on
 # a smaller field); absent when the kernel changed after that capture or the
 # run's size differs.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {("encode_float", 512): 843.5e6}   # profiles/encode_f32_grf384.md
 
 
 def parse():
