@@ -130,6 +130,57 @@ def test_encode_oracle_coefficients_bit_exact(kind, enc, B):
             assert int(got["pairs"][a, b]) == int(C[a, b])
 
 
+@pytest.mark.parametrize("enc,B,lg", [(1, 32, -120), (2, 32, -120), (1, 7, -130), (2, 4, 126),
+                                      (1, 1, 126), (1, 32, 126), (2, 32, 0)])
+def test_encode_f32_without_pairs_bit_exact(enc, B, lg):
+    """FP32 streams without pair tables (the persistent encoder): planes,
+    signs and counts bit-exact, down to subnormal values (scaling 2^k with
+    k > 127) and up to near the largest float (k at or below -126 for small
+    B), over whole segments and a ragged last one."""
+    pcr = _pcr()
+    from oracle import bitplane as bp
+    rng = np.random.default_rng(1000 + enc * 100 + B + lg)
+    n = 5 * 4096 + 160
+    v = rng.standard_normal(n) * np.exp(rng.uniform(-12, 0, n)) * 2.0 ** lg
+    v = np.clip(v, -3.0e38, 3.0e38).astype(np.float32)
+    v[::7] = 0
+    v[4096:8192] = 0                          # a segment with no significant value
+    encname = "generic" if enc == 1 else "negabinary"
+    e = bp.encode(v, False, B, encname, False)
+    got = pcr.debug_encode(torch.from_numpy(v).cuda(), 0, B, enc, False)
+    assert np.array_equal(got["planes"], e["planes"])
+    assert list(got["plane_nz"]) == e["plane_nz"]
+    if enc == 1:
+        assert np.array_equal(got["sign_counts"].astype(np.int64), e["sign_counts"])
+        for g in range(got["sign_counts"].shape[0]):
+            want = np.concatenate(e["signs"][g])
+            assert np.array_equal(got["signs"][g, :want.size], want)
+
+
+@pytest.mark.parametrize("lg,kw", [(-120, dict(interp="level", degree="cubic", decomp_axis=2)),
+                                   (-120, dict(mode="psnr", interp="level", degree="cubic")),
+                                   (100, dict(interp="level", degree="cubic", decomp_axis=2))])
+def test_extreme_magnitude_fields_parity(lg, kw):
+    """Fields of tiny (subnormal coefficients) and huge magnitude: streams,
+    plans and retrievals equal the oracle's (quantisation scale 2^k outside
+    the normal range on one side, dequantisation on the other)."""
+    pcr = _pcr()
+    X = (grf((33, 40, 64), 77, np.float64) * 2.0 ** lg).astype(np.float32)
+    sch = pcr.Scheme(**kw)
+    h_or = oracle.refactor(X, oracle_scheme(sch, X.ndim))
+    h = pcr.refactor(torch.from_numpy(X).cuda(), sch)
+    torch.cuda.synchronize()
+    compare_streams(h, h_or)
+    targets = [OTarget("rel", v) for v in (1e-2, 1e-5)] + [OTarget("psnr", v) for v in (60.0,)]
+    for t in targets:
+        pl_or = oracle.plan(h_or, t)
+        pl = h.plan(pcr.Target(t.kind, t.value), allow_unsat=True)
+        assert pl.planes == pl_or["b"] and pl.bound == pl_or["bound"]
+        x_or, _ = oracle.retrieve(h_or, pl_or)
+        out, _ = h.retrieve(pl)
+        assert np.array_equal(out.cpu().numpy(), x_or), f"retrieval differs for {t}"
+
+
 def test_serialize_round_trip():
     pcr = _pcr()
     X = grf((20, 24, 33), 7, np.float32)
