@@ -1524,6 +1524,131 @@ __global__ void __launch_bounds__(kThreads, 4) k_encode_f32(const StreamD* __res
   cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------------------
+// Decoder for streams with 32-bit codes: one warp per segment, one pass, no
+// shared memory (Sec. V-C bitplanes, Sec. VI-A encodings).  Lane k reads
+// plane k's words of the segment directly (16-byte loads where the rows
+// allow) and, for the generic encoding, plane k's sign sub-stream through a
+// two-word bit reader.  Per word, the planes give F_k (values first
+// significant at plane k, a prefix OR over lanes); the lanes' sign slices
+// laid side by side in plane order are one warp OR-reduction, from which
+// each value takes its bit at (values of lower planes) + (rank in F_k).
+// ---------------------------------------------------------------------------
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) k_decode_w32(const StreamD* __restrict__ streams,
+                                                         const WorkItem* __restrict__ items, int nitems) {
+  const int lane = threadIdx.x & 31;
+  const int item = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  if (item >= nitems) return;                       // whole warps
+  const WorkItem it = items[item];
+  const StreamD& s = streams[it.stream];
+  const int B = s.B, b = s.b;
+  const bool generic = s.enc == 1;
+  const int64_t e0 = (int64_t)it.seg * kSegElems;
+  const int nw = (int)min((int64_t)kSegWords, (s.n_pad - e0) / 32);
+  const int64_t w0 = (int64_t)it.seg * kSegWords;
+  VT* out = (VT*)s.stage + e0 + lane;
+  const TrC tc = tr_consts(lane);
+  const uint32_t lt = (1u << lane) - 1u;
+
+  // this lane's plane row (planes >= b, and planes with no nonzero word in
+  // the stream, read as zeros)
+  const bool has = lane < b && s.plane_nz[lane] != 0;
+  const uint32_t* row = s.planes + (int64_t)(has ? lane : 0) * s.words + w0;
+  const bool vec = ((s.words & 3) == 0) && ((((uintptr_t)s.planes) & 15) == 0);
+
+  // this lane's sign sub-stream: first word = exclusive prefix of the
+  // planes' word counts over the lanes
+  uint32_t win = 0, nxt = 0, pos = 0, idx = 2, nwords = 0;
+  const uint32_t* sp = s.signs + (int64_t)it.seg * s.slot_words;
+  if (generic) {
+    const uint32_t cntk = lane < B ? s.sign_counts[(int64_t)it.seg * B + lane] : 0u;
+    const uint32_t words = (cntk + 31) >> 5;
+    uint32_t inc = words;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL, inc, o);
+      inc += lane >= o ? t : 0u;
+    }
+    sp += inc - words;
+    nwords = lane < b ? words : 0u;
+    if (nwords > 0) win = __ldg(sp);
+    if (nwords > 1) nxt = __ldg(sp + 1);
+  }
+  // dequantisation constants (dequantize<VT, 32>)
+  [[maybe_unused]] Scale2 dq{1.0f, 1.0f};
+  const uint32_t nbm = (uint32_t)nb_mask(B);
+  if constexpr (std::is_same<VT, float>::value) dq = scale_pair(generic ? s.E - B : s.E - B + 3);
+
+  auto load4 = [&](int j) -> uint4 {
+    if (!has || j >= nw) return make_uint4(0u, 0u, 0u, 0u);
+    if (vec && j + 4 <= nw) return __ldg(reinterpret_cast<const uint4*>(row + j));
+    uint4 g;
+    g.x = __ldg(row + j);
+    g.y = j + 1 < nw ? __ldg(row + j + 1) : 0u;
+    g.z = j + 2 < nw ? __ldg(row + j + 2) : 0u;
+    g.w = j + 3 < nw ? __ldg(row + j + 3) : 0u;
+    return g;
+  };
+
+  uint4 g = load4(0);
+  for (int j4 = 0; j4 < nw; j4 += 4) {
+    const uint4 gn = load4(j4 + 4);                 // next group in flight
+#pragma unroll
+    for (int e4 = 0; e4 < 4; e4++) {
+      const int j = j4 + e4;
+      if (j >= nw) break;
+      uint32_t xl = e4 == 0 ? g.x : e4 == 1 ? g.y : e4 == 2 ? g.z : g.w;
+      if (!generic) {                               // negabinary planes are stored XOR-differenced
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(FULL, xl, o);
+          if (lane >= o) xl ^= t;
+        }
+        if (lane >= b) xl = 0;
+      }
+      const uint32_t q = __brev(transpose32c(xl, tc)) >> (32 - B);
+      bool neg = false;
+      if (generic) {
+        uint32_t inc = xl;                          // a one in planes 0..lane
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) inc |= __shfl_up_sync(FULL, inc, o);
+        uint32_t exc = __shfl_up_sync(FULL, inc, 1);
+        exc = lane ? exc : 0u;
+        const uint32_t F = xl & ~exc;
+        const uint32_t cnt = __popc(F), start = __popc(exc);
+        // the next cnt bits of this plane's signs
+        const uint32_t slice = __funnelshift_r(win, nxt, pos) & __funnelshift_lc(~0u, 0u, cnt);
+        pos += cnt;
+        if (pos >= 32) {
+          win = nxt;
+          nxt = idx < nwords ? __ldg(sp + idx) : 0u;
+          idx++;
+          pos -= 32;
+        }
+        const uint32_t sorted = __reduce_or_sync(FULL, slice << (start & 31));
+        const uint32_t xr = q << (32 - B);
+        const int pe = __clz(xr) & 31;
+        const uint32_t Fp = __shfl_sync(FULL, F, pe);
+        const uint32_t spp = __shfl_sync(FULL, start, pe);
+        neg = xr && ((sorted >> (spp + __popc(Fp & lt))) & 1u);
+      }
+      if constexpr (std::is_same<VT, float>::value) {
+        if (generic) {
+          const float mag = __fmul_rn(__fmul_rn(__uint2float_rn(q), dq.m1), dq.m2);
+          out[(int64_t)j * 32] = neg ? -mag : mag;
+        } else {
+          const int64_t val = (int64_t)((uint64_t)(q ^ nbm)) - (int64_t)nbm;
+          out[(int64_t)j * 32] = __fmul_rn(__fmul_rn(__int2float_rn((int)val), dq.m1), dq.m2);
+        }
+      } else {
+        out[(int64_t)j * 32] = dequantize<VT, 32>(q, neg, s);
+      }
+    }
+    g = gn;
+  }
+}
+
 // persistent grid of k_encode_f32: the CTAs that fit on the device at once
 static int enc_f32_grid(int nitems) {
   static int cached[64] = {0};
@@ -1564,8 +1689,9 @@ void launch_decode(int vk, int w64, const StreamD* d_streams, const WorkItem* d_
   if (nitems == 0) return;
   count_launch();
   if (!w64) {
-    if (vk == VK_F32) k_decode<float, 32><<<nitems, kThreads, 0, s>>>(d_streams, d_items);
-    else k_decode<int64_t, 32><<<nitems, kThreads, 0, s>>>(d_streams, d_items);
+    const int grid = (nitems + kWarps - 1) / kWarps;   // one warp per segment
+    if (vk == VK_F32) k_decode_w32<float><<<grid, kThreads, 0, s>>>(d_streams, d_items, nitems);
+    else k_decode_w32<int64_t><<<grid, kThreads, 0, s>>>(d_streams, d_items, nitems);
   } else {
     if (vk == VK_F64) k_decode<double, 64><<<nitems, kThreads, 0, s>>>(d_streams, d_items);
     else k_decode<int64_t, 64><<<nitems, kThreads, 0, s>>>(d_streams, d_items);
