@@ -39,7 +39,7 @@ METRIC = "refactor & retrieve GB/s (fraction of HBM roofline) at stated eb/PSNR 
 # summary under profiles/ (scaled by the level-0 value count when captured on
 # a smaller field); absent when the kernel changed after that capture or the
 # run's size differs.
-TRAFFIC_PER_LAUNCH = {("encode_float", 512): 843.5e6}   # profiles/encode_f32_grf384.md
+TRAFFIC_PER_LAUNCH = {("encode_float", 512): 843.5e6}   # k_encode_f32 at 384^3: 355.8 MB x 2.370
 
 
 def parse():
@@ -366,7 +366,7 @@ RETRIEVE_STAGES = {"decode_float", "decode_fixed", "recompose", "recon_coarsest"
 
 
 def algorithmic_bytes(stage, shape, w, pl):
-    """Algorithmic DRAM bytes of one launch of a stage (defined in the design doc):
+    """Algorithmic DRAM bytes of one launch of a stage:
     interp_level0 (refactor): read the field, write level-0 coefficients;
     recon_level0: read coarse values and level-0 coefficients, write field;
     decompose / recompose: read and write the decomposed region values;

@@ -129,6 +129,28 @@ pcr_status pcr_refactor(const void* d_field, int ndim, const int64_t* dims, int 
                         const pcr_scheme* scheme, const pcr_allocator* alloc,
                         void* cuda_stream, pcr_handle** out);
 
+/* ---- asynchronous refactor (pipelining of independent fields) ----------
+ * begin: arguments as pcr_refactor.  Allocates the handle's buffers and
+ *   scratch (stream-ordered, through `alloc`), enqueues every kernel and the
+ *   small read-backs of the statistics into pinned host memory on
+ *   `cuda_stream`, records an event and returns without waiting.  The field
+ *   must stay unchanged at `d_field` until the job's work has run.  While a
+ *   job is pending the host may plan, retrieve or begin other jobs; work
+ *   enqueued later on the same stream runs after this job's kernels.
+ * end: waits for the job's event, builds the host tables (Sec. V-C error
+ *   tables) and returns the handle in *out (the caller owns it and frees it
+ *   with pcr_free).  The job is consumed whatever the outcome.
+ * job_free: abandons a job without a handle; waits for its work first.
+ * The handle equals the one pcr_refactor returns for the same field.
+ * Errors: as pcr_refactor; PCR_ERR_OOM also when pinned host memory for the
+ *   read-backs cannot be allocated. */
+typedef struct pcr_refactor_job pcr_refactor_job;
+pcr_status pcr_refactor_begin(const void* d_field, int ndim, const int64_t* dims, int dtype,
+                              const pcr_scheme* scheme, const pcr_allocator* alloc,
+                              void* cuda_stream, pcr_refactor_job** out);
+pcr_status pcr_refactor_end(pcr_refactor_job* job, pcr_handle** out);
+void pcr_refactor_job_free(pcr_refactor_job* job);
+
 /* Batched form: n independent fields refactored with one work list per
  * kernel (one launch per pipeline stage for the whole batch).  Arrays are
  * length n; fields may have different shapes and dtypes. */
@@ -137,7 +159,7 @@ pcr_status pcr_refactor_batch(int n, const void* const* d_fields, const int* ndi
                               const pcr_scheme* schemes, const pcr_allocator* alloc,
                               void* cuda_stream, pcr_handle** outs);
 
-/* ---- batched refactor captured in one CUDA graph (spec batching) --
+/* ---- batched refactor captured in one CUDA graph ----------------------
  * For batches refactored again and again with the same shapes (variables of
  * successive timesteps): the whole batch -- every kernel, memset and the
  * small uploads and read-backs -- is captured once into one CUDA graph and
@@ -167,7 +189,7 @@ pcr_status pcr_refactor_graph_info(const pcr_refactor_graph* g, int64_t* nodes, 
                                    int64_t* arena_bytes);
 void pcr_refactor_graph_free(pcr_refactor_graph* g);
 
-/* ---- autotuner of the level-interpolation schedule (spec tuning;
+/* ---- autotuner of the level-interpolation schedule (GPU tuning;
  * the paper tunes its interpolation choices, Sec. VI-A, but not GPU tiles) -
  * Where a level can run either the general tile kernel or the plane-marching
  * kernel, and the marching kernel's plane chunk sets its grid, all choices

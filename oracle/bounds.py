@@ -9,7 +9,7 @@ coefficient decomposition, the level's error is the maximum over regions, and
 error, merging steps with equal error, into segments with an error list M_0.
 Sec. VI-B: the interpreter picks how many bitplanes to retrieve.
 
-Readings (the paper gives estimates; the benchmark spec asks for a guarantee):
+Readings (the paper gives estimates; these bounds are guarantees):
 * L-infinity: per-level E_l = Lam^d E_{l+1} + e_l + rho_l; per-region
   F_r = Lam max(E_{l+1}, F_1..F_{r-1}) + e_{l,r} + rho_l, E_l = max(E_{l+1}, F_r);
   Lam = 1.25 (cubic: sum of |weights| of every boundary rule) or 1 (linear).

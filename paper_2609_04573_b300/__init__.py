@@ -73,6 +73,9 @@ class _Allocator(C.Structure):
 _vp, _i64p = C.c_void_p, C.POINTER(C.c_int64)
 _sigs = {
     "pcr_refactor": [_vp, C.c_int, _i64p, C.c_int, C.POINTER(_Scheme), C.POINTER(_Allocator), _vp, C.POINTER(_vp)],
+    "pcr_refactor_begin": [_vp, C.c_int, _i64p, C.c_int, C.POINTER(_Scheme), C.POINTER(_Allocator), _vp,
+                           C.POINTER(_vp)],
+    "pcr_refactor_end": [_vp, C.POINTER(_vp)],
     "pcr_refactor_batch": [C.c_int, C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(_i64p), C.POINTER(C.c_int),
                            C.POINTER(_Scheme), C.POINTER(_Allocator), _vp, C.POINTER(_vp)],
     "pcr_plan": [_vp, C.POINTER(_Target), C.POINTER(_Plan)],
@@ -115,6 +118,8 @@ _lib.pcr_free.argtypes = [_vp]
 _lib.pcr_free.restype = None
 _lib.pcr_refactor_graph_free.argtypes = [_vp]
 _lib.pcr_refactor_graph_free.restype = None
+_lib.pcr_refactor_job_free.argtypes = [_vp]
+_lib.pcr_refactor_job_free.restype = None
 _lib.pcr_buffer_free.argtypes = [_vp]
 _lib.pcr_buffer_free.restype = None
 _lib.pcr_last_error.argtypes = []
@@ -122,7 +127,8 @@ _lib.pcr_last_error.restype = C.c_char_p
 
 # exported symbols (checked by the CPU tests against include/pcr.h)
 EXPORTS = sorted(list(_sigs) + ["pcr_free", "pcr_buffer_free", "pcr_last_error", "pcr_profile_enable",
-                                "pcr_profile_read", "pcr_launch_count", "pcr_refactor_graph_free"])
+                                "pcr_profile_read", "pcr_launch_count", "pcr_refactor_graph_free",
+                                "pcr_refactor_job_free"])
 
 
 def _check(st):
@@ -363,6 +369,43 @@ def refactor(x, scheme=None, stream=None):
                              C.byref(scheme.c(x.dim())), C.byref(_ALLOCATOR), _stream_ptr(stream),
                              C.byref(out)))
     return Handle(out.value, x.shape, x.dtype, x.device)
+
+
+class RefactorJob:
+    """A refactor enqueued with refactor_async; result() waits for it and
+    returns the Handle.  Keeps the field tensor alive until then."""
+
+    def __init__(self, ptr, x):
+        self._p = C.c_void_p(ptr)
+        self._x = x
+
+    def result(self):
+        if not self._p or not self._p.value:
+            raise RuntimeError("job already consumed")
+        out = C.c_void_p()
+        p, self._p = self._p, C.c_void_p(None)
+        _check(_lib.pcr_refactor_end(p, C.byref(out)))
+        x, self._x = self._x, None
+        return Handle(out.value, x.shape, x.dtype, x.device)
+
+    def __del__(self):
+        if getattr(self, "_p", None) and self._p.value:
+            _lib.pcr_refactor_job_free(self._p)
+            self._p = C.c_void_p(None)
+
+
+def refactor_async(x, scheme=None, stream=None):
+    """Enqueue the refactor of x and return a RefactorJob without waiting:
+    the host can plan and retrieve other fields meanwhile."""
+    scheme = scheme or Scheme()
+    if not (x.is_cuda and x.is_contiguous() and x.dtype in _DT and x.dim() in (2, 3)):
+        raise ValueError("refactor expects a contiguous 2-D/3-D float32/float64 CUDA tensor")
+    dims = (C.c_int64 * x.dim())(*x.shape)
+    out = C.c_void_p()
+    _check(_lib.pcr_refactor_begin(C.c_void_p(x.data_ptr()), x.dim(), dims, _DT[x.dtype],
+                                   C.byref(scheme.c(x.dim())), C.byref(_ALLOCATOR), _stream_ptr(stream),
+                                   C.byref(out)))
+    return RefactorJob(out.value, x)
 
 
 def refactor_batch(xs: Sequence[torch.Tensor], schemes, stream=None):

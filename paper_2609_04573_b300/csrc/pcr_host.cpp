@@ -1776,8 +1776,11 @@ static pcr_status alloc_handle_buffers(pcr_handle* h, cudaStream_t s) {
   p += b_nz;
   h->d_items_all = (WorkItem*)p;
   h->items_ready = false;
-  // unused tails of sign slots stay zero, so containers are deterministic
+  // unused tails of sign slots stay zero, and so do the sign counts of
+  // streams without sign sub-streams (negabinary), so a handle's contents
+  // never depend on what the allocator handed back
   if (h->sign_area_words) CUDA_TRY(cudaMemsetAsync(h->d_signs, 0, h->sign_area_words * 4, s));
+  if (h->scnt_words) CUDA_TRY(cudaMemsetAsync(h->d_scnt, 0, h->scnt_words * 4, s));
   return PCR_OK;
 }
 
@@ -1812,6 +1815,7 @@ struct BatchLayout {
 // same roles are played by pinned buffers that outlive the graph (`pinned`).
 struct BatchStage {
   bool pinned = false;
+  bool pinned_out = false;   // only the read-backs (st, vm, pairs, nz) are pinned, set by the caller
   FieldStats* st_init = nullptr;
   StreamD* sd = nullptr;
   WorkItem* items = nullptr;
@@ -1934,7 +1938,7 @@ static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* 
     }
   CUDA_TRY(cudaGetLastError());
   // read-back of the statistics the host tables need
-  if (!io.pinned) {
+  if (!io.pinned && !io.pinned_out) {
     io.v_st.resize(n);
     io.st = io.v_st.data();
     io.v_vm.resize(std::max<size_t>(L.nv, 1));
@@ -2059,6 +2063,123 @@ extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, con
   for (int k = 0; k < n; k++) outs[k] = own[k].release();
   return PCR_OK;
 }
+
+// ---------------------------------------------------------------------------
+// asynchronous refactor: enqueue now, finish the host tables later
+// ---------------------------------------------------------------------------
+// pinned read-back blocks, kept for reuse by later jobs (a block is only
+// returned once the copies into it have completed)
+static std::mutex g_pin_mu;
+static std::vector<std::pair<size_t, void*>> g_pin_free;
+
+static void* pin_acquire(size_t bytes, size_t& got) {
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    for (size_t i = 0; i < g_pin_free.size(); i++)
+      if (g_pin_free[i].first >= bytes) {
+        void* p = g_pin_free[i].second;
+        got = g_pin_free[i].first;
+        g_pin_free.erase(g_pin_free.begin() + (long)i);
+        return p;
+      }
+  }
+  const size_t sz = (bytes + 65535) & ~size_t(65535);
+  void* p = nullptr;
+  if (cudaMallocHost(&p, sz) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  got = sz;
+  return p;
+}
+
+static void pin_release(void* p, size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back({bytes, p});
+}
+
+struct pcr_refactor_job {
+  Mem mem;
+  cudaStream_t s = nullptr;
+  std::unique_ptr<pcr_handle> own;
+  std::vector<pcr_handle*> hs;
+  std::unique_ptr<BatchLayout> layout;
+  BatchStage io;
+  Scratch sc{nullptr, nullptr, {}};
+  std::unique_ptr<ScratchBlock> blk;
+  void* pin = nullptr;
+  size_t pin_bytes = 0;
+  cudaEvent_t done = nullptr;
+  bool enqueued = false;
+  ~pcr_refactor_job() {
+    // nothing the job owns is released while its copies or kernels may run
+    if (done) cudaEventSynchronize(done);
+    else if (enqueued) cudaStreamSynchronize(s);
+    blk.reset();
+    if (done) cudaEventDestroy(done);
+    if (pin) pin_release(pin, pin_bytes);
+  }
+};
+
+extern "C" pcr_status pcr_refactor_begin(const void* d_field, int ndim, const int64_t* dims, int dtype,
+                                         const pcr_scheme* scheme, const pcr_allocator* alloc, void* cuda_stream,
+                                         pcr_refactor_job** out) {
+  if (!out || !d_field || !dims || !scheme) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  std::unique_ptr<pcr_refactor_job> j(new pcr_refactor_job());
+  j->s = (cudaStream_t)cuda_stream;
+  j->mem = make_mem(alloc);
+  const void* f[1] = {d_field};
+  const int nd[1] = {ndim};
+  const int64_t* dm[1] = {dims};
+  const int dt[1] = {dtype};
+  std::vector<std::unique_ptr<pcr_handle>> own;
+  pcr_status e = make_batch_handles(1, f, nd, dm, dt, scheme, j->mem, j->s, own);
+  if (e) return e;
+  j->own = std::move(own[0]);
+  j->hs.push_back(j->own.get());
+  j->layout.reset(new BatchLayout(j->hs));
+  const BatchLayout& L = *j->layout;
+  // pinned targets of the read-backs, so that the enqueue does not wait
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t b_st = sizeof(FieldStats), b_vm = 8 * std::max<size_t>(L.nv, 1),
+               b_pr = 8 * std::max<size_t>(L.npairs, 1), b_nz = 4 * std::max<size_t>(L.nnz, 1);
+  j->pin = pin_acquire(al(b_st) + al(b_vm) + al(b_pr) + al(b_nz), j->pin_bytes);
+  if (!j->pin) return fail(PCR_ERR_OOM, "pinned read-back allocation failed");
+  char* p = (char*)j->pin;
+  j->io.pinned_out = true;
+  j->io.st = (FieldStats*)p;
+  p += al(b_st);
+  j->io.vm = (unsigned long long*)p;
+  p += al(b_vm);
+  j->io.pairs = (uint64_t*)p;
+  p += al(b_pr);
+  j->io.nz = (uint32_t*)p;
+  j->sc.mem = &j->mem;
+  j->sc.s = j->s;
+  j->blk.reset(new ScratchBlock(&j->mem, j->s, 256 * 8 + refactor_scratch_bytes(j->own.get()), j->sc));
+  if (!j->blk->p) return fail(PCR_ERR_OOM, "scratch allocation failed");
+  j->enqueued = true;
+  e = enqueue_batch(j->hs, f, j->s, j->sc, L, j->io, false);
+  if (e) return e;
+  CUDA_TRY(cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventRecord(j->done, j->s));
+  *out = j.release();
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_refactor_end(pcr_refactor_job* job, pcr_handle** out) {
+  if (!job || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  std::unique_ptr<pcr_refactor_job> j(job);   // consumed, whatever the outcome
+  CUDA_TRY(cudaEventSynchronize(j->done));
+  pcr_status e = finish_batch(j->hs, *j->layout, j->io);
+  if (e) return e;
+  *out = j->own.release();
+  return PCR_OK;
+}
+
+extern "C" void pcr_refactor_job_free(pcr_refactor_job* job) { delete job; }
 
 // ---------------------------------------------------------------------------
 // batched refactor captured in one CUDA graph

@@ -1,7 +1,7 @@
 """CUDA path vs CPU oracle, element by element, on seeded inputs that span
 several 4096-element segments, ragged row tails and the degenerate cases.
 
-Bars (the benchmark spec): quantised integers, bitplanes, sign sub-streams and integer
+Bars: quantised integers, bitplanes, sign sub-streams and integer
 table sums bit-exact; coefficients equal because both sides evaluate the same
 expression trees in the same precision; every retrieval within its bound.
 """
