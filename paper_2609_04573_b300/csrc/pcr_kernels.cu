@@ -1530,9 +1530,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_encode_f32(const StreamD* __res
 // plane k's words of the segment directly (16-byte loads where the rows
 // allow) and, for the generic encoding, plane k's sign sub-stream through a
 // two-word bit reader.  Per word, the planes give F_k (values first
-// significant at plane k, a prefix OR over lanes); the lanes' sign slices
-// laid side by side in plane order are one warp OR-reduction, from which
-// each value takes its bit at (values of lower planes) + (rank in F_k).
+// significant at plane k, a prefix OR over lanes) and lane k takes the
+// next |F_k| bits of its sign sub-stream; a value first significant at
+// plane k reads its sign from lane k's slice at its rank in F_k.
 // ---------------------------------------------------------------------------
 template <typename VT>
 __global__ void __launch_bounds__(kThreads) k_decode_w32(const StreamD* __restrict__ streams,
@@ -1616,7 +1616,7 @@ __global__ void __launch_bounds__(kThreads) k_decode_w32(const StreamD* __restri
         uint32_t exc = __shfl_up_sync(FULL, inc, 1);
         exc = lane ? exc : 0u;
         const uint32_t F = xl & ~exc;
-        const uint32_t cnt = __popc(F), start = __popc(exc);
+        const uint32_t cnt = __popc(F);
         // the next cnt bits of this plane's signs
         const uint32_t slice = __funnelshift_r(win, nxt, pos) & __funnelshift_lc(~0u, 0u, cnt);
         pos += cnt;
@@ -1626,12 +1626,13 @@ __global__ void __launch_bounds__(kThreads) k_decode_w32(const StreamD* __restri
           idx++;
           pos -= 32;
         }
-        const uint32_t sorted = __reduce_or_sync(FULL, slice << (start & 31));
+        // a value's sign: bit (its rank among the values first significant
+        // at its plane) of that plane's slice
         const uint32_t xr = q << (32 - B);
         const int pe = __clz(xr) & 31;
         const uint32_t Fp = __shfl_sync(FULL, F, pe);
-        const uint32_t spp = __shfl_sync(FULL, start, pe);
-        neg = xr && ((sorted >> (spp + __popc(Fp & lt))) & 1u);
+        const uint32_t Sp = __shfl_sync(FULL, slice, pe);
+        neg = xr && ((Sp >> __popc(Fp & lt)) & 1u);
       }
       if constexpr (std::is_same<VT, float>::value) {
         if (generic) {
