@@ -141,7 +141,10 @@ pcr_status pcr_refactor(const void* d_field, int ndim, const int64_t* dims, int 
  *   tables) and returns the handle in *out (the caller owns it and frees it
  *   with pcr_free).  The job is consumed whatever the outcome.
  * job_free: abandons a job without a handle; waits for its work first.
- * The handle equals the one pcr_refactor returns for the same field.
+ * The handle equals the one pcr_refactor returns for the same field.  Its
+ *   buffers come from `alloc` on `cuda_stream` and go back there at
+ *   pcr_free without waiting: work on other streams that reads the handle
+ *   (a retrieval on a second stream) must have completed before pcr_free.
  * Errors: as pcr_refactor; PCR_ERR_OOM also when pinned host memory for the
  *   read-backs cannot be allocated. */
 typedef struct pcr_refactor_job pcr_refactor_job;

@@ -396,7 +396,9 @@ class RefactorJob:
 
 def refactor_async(x, scheme=None, stream=None):
     """Enqueue the refactor of x and return a RefactorJob without waiting:
-    the host can plan and retrieve other fields meanwhile."""
+    the host can plan and retrieve other fields meanwhile.  The handle's
+    buffers belong to `stream`'s allocator pool: when it is retrieved on
+    another stream, keep the Handle alive until that retrieval has run."""
     scheme = scheme or Scheme()
     if not (x.is_cuda and x.is_contiguous() and x.dtype in _DT and x.dim() in (2, 3)):
         raise ValueError("refactor expects a contiguous 2-D/3-D float32/float64 CUDA tensor")
