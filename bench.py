@@ -195,7 +195,7 @@ def run_pcr(args):
 
     rstream = torch.cuda.Stream()
 
-    def run_pipelined(k):
+    def run_pipelined(k, sch=None):
         """k steps, step i+1's refactor enqueued before step i's tables are
         finished, planned and retrieved: the host work of one step overlaps
         the GPU work of the next.  Refactors run on `stream`, retrievals on
@@ -203,11 +203,12 @@ def run_pcr(args):
         A handle is released only once its retrieval has run (its buffers
         belong to the refactor stream's allocator pool).  Exactly k
         refactors and k retrievals; `stream` waits for `rstream` at the end."""
+        sch = sch or scheme
         pending = collections.deque()
-        job = pcr.refactor_async(x, scheme, stream=stream)
+        job = pcr.refactor_async(x, sch, stream=stream)
         hk = plk = None
         for i in range(k):
-            nxt = pcr.refactor_async(x, scheme, stream=stream) if i + 1 < k else None
+            nxt = pcr.refactor_async(x, sch, stream=stream) if i + 1 < k else None
             hk = job.result()
             plk = hk.plan(target)
             hk.retrieve(plk, out=out, stream=rstream)
@@ -257,24 +258,18 @@ def run_pcr(args):
     ms = max_over_ranks(ms, world, dev)
 
     # the configuration's other interpolation scheme (per-region cubic with
-    # the same decomposition), timed the same way on fewer steps
+    # the same decomposition), pipelined the same way on fewer steps
     sch_r = pcr.Scheme(mode="eb", interp="region", degree="cubic", decomp_axis=2)
 
-    def step_r():
-        hr = pcr.refactor(x, sch_r)
-        hr.retrieve(hr.plan(target), out=out)
-        return hr
-    for _ in range(args.warmup):
-        hr = step_r()
+    run_pipelined(args.warmup, sch_r)
     torch.cuda.synchronize()
-    err_r = (out.double() - x.double()).abs().max().item()
     nr = max(10, args.steps // 4)
     er0, er1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     er0.record(stream)
-    for _ in range(nr):
-        hr = step_r()
+    run_pipelined(nr, sch_r)
     er1.record(stream)
     torch.cuda.synchronize()
+    err_r = (out.double() - x.double()).abs().max().item()
     ms_r = er0.elapsed_time(er1) / nr
     per_region = {"ms_per_step": ms_r, "value": whole_job_gbs(nbytes, 1, ms_r), "unit": "GB/s",
                   "bound_respected_full_size": bool(err_r <= TARGET[1] * (xmax - xmin)), "max_err": err_r}
