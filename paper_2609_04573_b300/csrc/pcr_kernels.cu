@@ -1591,62 +1591,76 @@ __global__ void __launch_bounds__(kThreads) k_decode_w32(const StreamD* __restri
     return g;
   };
 
-  uint4 g = load4(0);
-  for (int j4 = 0; j4 < nw; j4 += 4) {
-    const uint4 gn = load4(j4 + 4);                 // next group in flight
+  // the word loop, instantiated per encoding and for whole / ragged segments
+  // (neither test then runs per word)
+  auto words = [&](auto gen_tag, auto whole_tag) {
+    constexpr bool GEN = decltype(gen_tag)::value;
+    constexpr bool WHOLE = decltype(whole_tag)::value;
+    const int nwl = WHOLE ? kSegWords : nw;
+    uint4 g = load4(0);
+    for (int j4 = 0; j4 < nwl; j4 += 4) {
+      const uint4 gn = load4(j4 + 4);               // next group in flight
 #pragma unroll
-    for (int e4 = 0; e4 < 4; e4++) {
-      const int j = j4 + e4;
-      if (j >= nw) break;
-      uint32_t xl = e4 == 0 ? g.x : e4 == 1 ? g.y : e4 == 2 ? g.z : g.w;
-      if (!generic) {                               // negabinary planes are stored XOR-differenced
+      for (int e4 = 0; e4 < 4; e4++) {
+        const int j = j4 + e4;
+        if (!WHOLE && j >= nwl) break;
+        uint32_t xl = e4 == 0 ? g.x : e4 == 1 ? g.y : e4 == 2 ? g.z : g.w;
+        if constexpr (!GEN) {                       // negabinary planes are stored XOR-differenced
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t t = __shfl_up_sync(FULL, xl, o);
-          if (lane >= o) xl ^= t;
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, xl, o);
+            if (lane >= o) xl ^= t;
+          }
+          if (lane >= b) xl = 0;
         }
-        if (lane >= b) xl = 0;
-      }
-      const uint32_t q = __brev(transpose32c(xl, tc)) >> (32 - B);
-      bool neg = false;
-      if (generic) {
-        uint32_t inc = xl;                          // a one in planes 0..lane
+        const uint32_t q = __brev(transpose32c(xl, tc)) >> (32 - B);
+        bool neg = false;
+        if constexpr (GEN) {
+          uint32_t inc = xl;                        // a one in planes 0..lane
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) inc |= __shfl_up_sync(FULL, inc, o);
-        uint32_t exc = __shfl_up_sync(FULL, inc, 1);
-        exc = lane ? exc : 0u;
-        const uint32_t F = xl & ~exc;
-        const uint32_t cnt = __popc(F);
-        // the next cnt bits of this plane's signs
-        const uint32_t slice = __funnelshift_r(win, nxt, pos) & __funnelshift_lc(~0u, 0u, cnt);
-        pos += cnt;
-        if (pos >= 32) {
-          win = nxt;
-          nxt = idx < nwords ? __ldg(sp + idx) : 0u;
-          idx++;
-          pos -= 32;
+          for (int o = 1; o < 32; o <<= 1) inc |= __shfl_up_sync(FULL, inc, o);
+          uint32_t exc = __shfl_up_sync(FULL, inc, 1);
+          exc = lane ? exc : 0u;
+          const uint32_t F = xl & ~exc;
+          const uint32_t cnt = __popc(F);
+          // the next cnt bits of this plane's signs
+          const uint32_t slice = __funnelshift_r(win, nxt, pos) & __funnelshift_lc(~0u, 0u, cnt);
+          pos += cnt;
+          if (pos >= 32) {
+            win = nxt;
+            nxt = idx < nwords ? __ldg(sp + idx) : 0u;
+            idx++;
+            pos -= 32;
+          }
+          // a value's sign: bit (its rank among the values first significant
+          // at its plane) of that plane's slice
+          const uint32_t xr = q << (32 - B);
+          const int pe = __clz(xr) & 31;
+          const uint32_t Fp = __shfl_sync(FULL, F, pe);
+          const uint32_t Sp = __shfl_sync(FULL, slice, pe);
+          neg = xr && ((Sp >> __popc(Fp & lt)) & 1u);
         }
-        // a value's sign: bit (its rank among the values first significant
-        // at its plane) of that plane's slice
-        const uint32_t xr = q << (32 - B);
-        const int pe = __clz(xr) & 31;
-        const uint32_t Fp = __shfl_sync(FULL, F, pe);
-        const uint32_t Sp = __shfl_sync(FULL, slice, pe);
-        neg = xr && ((Sp >> __popc(Fp & lt)) & 1u);
-      }
-      if constexpr (std::is_same<VT, float>::value) {
-        if (generic) {
-          const float mag = __fmul_rn(__fmul_rn(__uint2float_rn(q), dq.m1), dq.m2);
-          out[(int64_t)j * 32] = neg ? -mag : mag;
+        if constexpr (std::is_same<VT, float>::value) {
+          if constexpr (GEN) {
+            const float mag = __fmul_rn(__fmul_rn(__uint2float_rn(q), dq.m1), dq.m2);
+            out[(int64_t)j * 32] = neg ? -mag : mag;
+          } else {
+            const int64_t val = (int64_t)((uint64_t)(q ^ nbm)) - (int64_t)nbm;
+            out[(int64_t)j * 32] = __fmul_rn(__fmul_rn(__int2float_rn((int)val), dq.m1), dq.m2);
+          }
         } else {
-          const int64_t val = (int64_t)((uint64_t)(q ^ nbm)) - (int64_t)nbm;
-          out[(int64_t)j * 32] = __fmul_rn(__fmul_rn(__int2float_rn((int)val), dq.m1), dq.m2);
+          out[(int64_t)j * 32] = dequantize<VT, 32>(q, neg, s);
         }
-      } else {
-        out[(int64_t)j * 32] = dequantize<VT, 32>(q, neg, s);
       }
+      g = gn;
     }
-    g = gn;
+  };
+  if (generic) {
+    if (nw == kSegWords) words(std::true_type{}, std::true_type{});
+    else words(std::true_type{}, std::false_type{});
+  } else {
+    if (nw == kSegWords) words(std::false_type{}, std::true_type{});
+    else words(std::false_type{}, std::false_type{});
   }
 }
 
