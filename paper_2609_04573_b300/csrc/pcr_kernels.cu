@@ -1406,59 +1406,65 @@ __global__ void __launch_bounds__(kThreads, 4) k_encode_f32(const StreamD* __res
     for (int jj = 0; jj < kWordsPerWarp; jj++) v[jj] = __uint_as_float(wbuf[jj * 32 + lane]);
     __syncwarp();                       // the warp's region now holds its sign bit-strings
     uint32_t acc = 0, fill = 0, wpos = 0, count = 0, nz = 0;
-    uint32_t pw[4];
+    // the word loop, instantiated per encoding (the test then runs once)
+    auto words = [&](auto gen_tag) {
+      constexpr bool GEN = decltype(gen_tag)::value;
+      uint32_t pw[4];
 #pragma unroll
-    for (int jj = 0; jj < kWordsPerWarp; jj++) {
-      const bool neg = v[jj] < 0.0f;
-      uint32_t q;
-      if (generic) {
-        q = __float2uint_rz(__fmul_rn(__fmul_rn(fabsf(v[jj]), sc.m1), sc.m2));
-      } else {
-        const int sv = __float2int_rz(__fmul_rn(__fmul_rn(v[jj], sc.m1), sc.m2));
-        q = ((uint32_t)sv + M) ^ M;
-      }
-      if (qp.zero) q = 0;
-      const uint32_t xr = q << (32 - B);
-      const uint32_t x = __brev(xr);                     // bit t = plane t (from the top)
-      const uint32_t D = transpose32c(x, tc);             // lane k: plane k of the 32 values
-      uint32_t sl = D;
-      if (!generic) {
-        const uint32_t up = __shfl_up_sync(FULL, D, 1);
-        sl = lane ? D ^ up : D;
-      }
-      pw[jj & 3] = sl;
-      if ((jj & 3) == 3 && lane < B)
-        *reinterpret_cast<uint4*>(&pbuf[lane * kEncRow + warp * kWordsPerWarp + (jj & ~3)]) =
-            make_uint4(pw[0], pw[1], pw[2], pw[3]);
-      nz += sl != 0;
-      if (generic) {
-        // planes above k that hold a one, per element (inclusive prefix OR)
-        uint32_t inc = D;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) inc |= __shfl_up_sync(FULL, inc, o);
-        uint32_t exc = __shfl_up_sync(FULL, inc, 1);
-        exc = lane ? exc : 0u;
-        const uint32_t F = D & ~exc;                     // first significant at plane `lane`
-        const uint32_t cnt = __popc(F), start = __popc(exc);
-        // this element's place in the word's signs sorted by (plane, element)
-        const int pe = __clz(xr) & 31;                   // its plane (any lane when q == 0)
-        const uint32_t Fp = __shfl_sync(FULL, F, pe);
-        const uint32_t sp = __shfl_sync(FULL, start, pe);
-        const uint32_t dest = sp + __popc(Fp & lt);
-        const uint32_t sorted = __reduce_or_sync(FULL, (neg && xr) ? (1u << dest) : 0u);
-        // lane k: its plane's slice [start, start + cnt), appended to the plane's bit-string
-        const uint32_t bits = __funnelshift_rc(sorted, 0u, start) & __funnelshift_lc(~0u, 0u, cnt);
-        acc |= bits << fill;
-        const uint32_t nf = fill + cnt;
-        if (nf >= 32) {
-          wbuf[sb_index(lane, wpos)] = acc;
-          wpos++;
-          acc = __funnelshift_rc(bits, 0u, 32 - fill);   // the part that did not fit (none if fill == 0)
+      for (int jj = 0; jj < kWordsPerWarp; jj++) {
+        const bool neg = v[jj] < 0.0f;
+        uint32_t q;
+        if constexpr (GEN) {
+          q = __float2uint_rz(__fmul_rn(__fmul_rn(fabsf(v[jj]), sc.m1), sc.m2));
+        } else {
+          const int sv = __float2int_rz(__fmul_rn(__fmul_rn(v[jj], sc.m1), sc.m2));
+          q = ((uint32_t)sv + M) ^ M;
         }
-        fill = nf & 31;
-        count += cnt;
+        if (qp.zero) q = 0;
+        const uint32_t xr = q << (32 - B);
+        const uint32_t x = __brev(xr);                   // bit t = plane t (from the top)
+        const uint32_t D = transpose32c(x, tc);           // lane k: plane k of the 32 values
+        uint32_t sl = D;
+        if constexpr (!GEN) {
+          const uint32_t up = __shfl_up_sync(FULL, D, 1);
+          sl = lane ? D ^ up : D;
+        }
+        pw[jj & 3] = sl;
+        if ((jj & 3) == 3 && lane < B)
+          *reinterpret_cast<uint4*>(&pbuf[lane * kEncRow + warp * kWordsPerWarp + (jj & ~3)]) =
+              make_uint4(pw[0], pw[1], pw[2], pw[3]);
+        nz += sl != 0;
+        if constexpr (GEN) {
+          // planes above k that hold a one, per element (inclusive prefix OR)
+          uint32_t inc = D;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) inc |= __shfl_up_sync(FULL, inc, o);
+          uint32_t exc = __shfl_up_sync(FULL, inc, 1);
+          exc = lane ? exc : 0u;
+          const uint32_t F = D & ~exc;                   // first significant at plane `lane`
+          const uint32_t cnt = __popc(F), start = __popc(exc);
+          // this element's place in the word's signs sorted by (plane, element)
+          const int pe = __clz(xr) & 31;                 // its plane (any lane when q == 0)
+          const uint32_t Fp = __shfl_sync(FULL, F, pe);
+          const uint32_t sp = __shfl_sync(FULL, start, pe);
+          const uint32_t dest = sp + __popc(Fp & lt);
+          const uint32_t sorted = __reduce_or_sync(FULL, (neg && xr) ? (1u << dest) : 0u);
+          // lane k: its plane's slice [start, start + cnt), appended to the plane's bit-string
+          const uint32_t bits = __funnelshift_rc(sorted, 0u, start) & __funnelshift_lc(~0u, 0u, cnt);
+          acc |= bits << fill;
+          const uint32_t nf = fill + cnt;
+          if (nf >= 32) {
+            wbuf[sb_index(lane, wpos)] = acc;
+            wpos++;
+            acc = __funnelshift_rc(bits, 0u, 32 - fill);   // the part that did not fit (none if fill == 0)
+          }
+          fill = nf & 31;
+          count += cnt;
+        }
       }
-    }
+    };
+    if (generic) words(std::true_type{});
+    else words(std::false_type{});
     if (generic) {
       if (fill) wbuf[sb_index(lane, wpos)] = acc;
       wcnt[warp][lane] = count;
