@@ -40,7 +40,7 @@ METRIC = "refactor & retrieve GB/s (fraction of HBM roofline) at stated eb/PSNR 
 # summary under profiles/ (scaled by the level-0 value count when captured on
 # a smaller field); absent when the kernel changed after that capture or the
 # run's size differs.
-TRAFFIC_PER_LAUNCH = {("encode_float", 512): 843.5e6}   # k_encode_f32 at 384^3: 355.8 MB x 2.370
+TRAFFIC_PER_LAUNCH = {("encode_float", 512): 844.4e6}   # k_encode_f32 at 384^3: 356.3 MB x 2.370
 
 
 def parse():
