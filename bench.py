@@ -65,38 +65,114 @@ def dist_env():
 
 
 class Clocks:
-    """nvidia-smi samples during the timed region.
+    """SM clock and throttle reasons sampled during the timed region.
 
-    Each query stalls this process's CUDA calls for tens of milliseconds, so
-    the sampler polls every 500 ms and the default timed region (200 steps,
-    about a second) holds a few samples at a few percent of its time."""
+    NVML (the driver's library, through ctypes) is read in-process from a
+    background thread (one clock and one reason query per sample, no
+    subprocess), on the device this process computes on (matched by UUID, so
+    the NVML index is right under CUDA_VISIBLE_DEVICES).  __enter__ returns only after the first
+    sample has been taken; __exit__ takes one more after the region.  Without
+    NVML the nvidia-smi loop is the fallback."""
 
-    def __init__(self, index):
-        self.index = index
-        self.samples = []
+    PERIOD_S = 0.02
+    NAMES = ["sw_power_cap", "hw_slowdown", "sw_thermal_slowdown", "hw_thermal_slowdown"]
+
+    def __init__(self, device_index):
+        self.device_index = device_index
+        self.samples = []          # (sm_mhz, sm_max_mhz, [reason names])
+        self.source = None
+        self.nvml_error = None
+        self._stop = threading.Event()
+        self._thread = None
+        self._nv = None
+        self._h = None
         self.proc = None
 
+    # NVML clock-event reason bits (nvml.h): sw power cap, hw slowdown, sw
+    # thermal, hw thermal
+    MASKS = [0x4, 0x8, 0x20, 0x40]
+    NVML_CLOCK_SM = 1
+
+    def _nvml_handle(self):
+        """NVML through ctypes (libnvidia-ml ships with the driver)."""
+        import ctypes as C
+        import torch
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+        props = torch.cuda.get_device_properties(self.device_index)
+        h = C.c_void_p()
+        uuid = ("GPU-" + str(props.uuid)).encode()
+        if lib.nvmlDeviceGetHandleByUUID(C.c_char_p(uuid), C.byref(h)) != 0:
+            bus = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0".encode()
+            if lib.nvmlDeviceGetHandleByPciBusId_v2(C.c_char_p(bus), C.byref(h)) != 0:
+                raise RuntimeError("no NVML handle for this device")
+        return lib, h
+
+    def _sample_nvml(self):
+        import ctypes as C
+        lib, h = self._nv, self._h
+        sm, mx, bits = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        if (lib.nvmlDeviceGetClockInfo(h, self.NVML_CLOCK_SM, C.byref(sm)) or
+                lib.nvmlDeviceGetMaxClockInfo(h, self.NVML_CLOCK_SM, C.byref(mx)) or
+                lib.nvmlDeviceGetCurrentClocksEventReasons(h, C.byref(bits))):
+            raise RuntimeError("NVML query failed")
+        self.samples.append((float(sm.value), float(mx.value),
+                             [n for n, m in zip(self.NAMES, self.MASKS) if bits.value & m]))
+
+    def _loop(self):
+        while not self._stop.wait(self.PERIOD_S):
+            try:
+                self._sample_nvml()
+            except Exception:
+                return
+
     def __enter__(self):
-        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-             "clocks_event_reasons.sw_power_cap")
+        try:
+            self._nv, self._h = self._nvml_handle()
+            self._sample_nvml()
+            self.source = "nvml"
+            self._thread = threading.Thread(target=self._loop, daemon=True)
+            self._thread.start()
+            return self
+        except Exception as e:
+            self._nv = None
+            self.nvml_error = f"{type(e).__name__}: {e}"
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.sw_power_cap,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.hw_thermal_slowdown")
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                 "-lms", "500"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
+                ["nvidia-smi", "-i", str(self.device_index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._thread = threading.Thread(target=self._read_smi, daemon=True)
+            self._thread.start()
+            self.source = "nvidia-smi"
+            t0 = time.time()
+            while not self.samples and time.time() - t0 < 10:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
-        time.sleep(0.3)
         return self
 
-    def _read(self):
+    def _read_smi(self):
         for line in self.proc.stdout:
-            self.samples.append([x.strip() for x in line.split(",")])
+            s = [x.strip() for x in line.split(",")]
+            try:
+                self.samples.append((float(s[0]), float(s[1]),
+                                     [n for n, v in zip(self.NAMES, s[2:6]) if v.lower() == "active"]))
+            except (ValueError, IndexError):
+                pass
 
     def __exit__(self, *exc):
-        if self.proc:
+        if self._nv is not None:
+            self._stop.set()
+            self._thread.join(timeout=2)
+            try:
+                self._sample_nvml()
+            except Exception:
+                pass
+        elif self.proc:
             time.sleep(0.25)
             self.proc.terminate()
             try:
@@ -106,18 +182,12 @@ class Clocks:
 
     def summary(self):
         if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = set()
-        for s in self.samples:
-            for n, v in zip(names, s[3:7]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(self.samples)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        reasons = sorted({r for s in self.samples for r in s[2]})
+        return {"sm_mhz": statistics.median(s[0] for s in self.samples),
+                "sm_max_mhz": max(s[1] for s in self.samples), "reasons": reasons,
+                "samples": len(self.samples), "source": self.source,
+                **({"nvml_error": self.nvml_error} if self.nvml_error else {})}
 
 
 def max_over_ranks(ms, world, device):
