@@ -246,22 +246,28 @@ pcr_status pcr_retrieve_scratch_bytes(const pcr_handle* h, size_t* bytes);
 
 /* ---- retrieval without device allocation -------------------------------- */
 /* Same plans, same kernels and the same output as pcr_retrieve, for callers
- * that must not allocate device memory: code that enqueues work while a
- * stream is being captured into a CUDA graph (cudaMalloc is not permitted
- * there), applications whose own pool or arena owns all device memory, and
- * latency-bound loops where cudaMalloc / cudaFree would synchronise the device.
- * Every temporary buffer of the call is carved out of one fixed 32 MiB array
- * compiled into the library (PCR_STATIC_SCRATCH_BYTES); each GPU that loads
- * the library holds that array until the process exits.  Nothing is
- * allocated: no cudaMalloc / cudaMallocAsync / cudaFree and no call to the
- * handle's allocator.  Every byte of the array that a call reads is written
- * earlier in the same call, so nothing needs clearing between calls.
+ * that must not allocate device memory: applications whose own pool or arena
+ * owns all device memory, hosts that forbid libraries to allocate on their
+ * behalf, and latency-bound loops where cudaMalloc / cudaFree would
+ * synchronise the device.  Every temporary buffer of the call is carved out
+ * of one fixed 32 MiB array compiled into the library
+ * (PCR_STATIC_SCRATCH_BYTES); each GPU that loads the library holds that
+ * array until the process exits.  Nothing is allocated: no cudaMalloc /
+ * cudaMallocAsync / cudaFree and no call to the handle's allocator.  Every
+ * byte of the array that a call reads is written earlier in the same call,
+ * so nothing needs clearing between calls.
  *   - A retrieval needing more scratch than the array holds returns
  *     PCR_ERR_UNSUPPORTED with the required size in pcr_last_error() (with
  *     FP32 and coefficient decomposition the limit is about 3.5 M points).
+ *   - The current device must be the one the handle was created on
+ *     (PCR_ERR_INVALID_ARG otherwise): the array is per device.
  *   - The first call on a device looks the array's device address up with
  *     cudaGetSymbolAddress (device-wide set-up): make that first call on each
  *     device before any stream capture begins.
+ *   - The call copies its per-call stream descriptors (and, for a handle from
+ *     pcr_deserialize, its work list) from host memory that lives only for
+ *     the call, so a stream that is being captured is refused with
+ *     PCR_ERR_UNSUPPORTED.
  *   - All calls share the one array, so calls that can run at the same time
  *     on the GPU (different streams, or host threads without ordering) race
  *     and corrupt each other; calls enqueued on one stream are ordered.

@@ -17,8 +17,29 @@ Readings (the paper gives estimates; these bounds are guarantees):
   per-level predictions have unit weight sum).
 * L2 (PSNR): ||P e||_2 <= sqrt(||P^T P||_inf) ||e||_2 per 1-D pass, with the
   row sum computed exactly for every line length; tensor passes multiply.
-* rho_l: rounding allowance (first-order error analysis of the canonical
-  expressions, times 1.01); fixed-point levels lose < one quantum per floor.
+* Rounding at level 0 (field dtype, unit roundoff u): the coarse values
+  enter as the fixed-point reconstruction rounded once to the field dtype
+  (error <= u Y, added to the incoming error); every level-0 point then
+  carries rho_0 = G u (Pr + Y + Cr) + s, with
+  Y = M + Lam^d (E_1 + sum e_0) bounding |x'| and the retrieval's inputs;
+  Pr the rounding of the prediction in refactoring and in retrieval: one
+  pass (per-region) rounds at most kappa (M + Y); per-level pass k rounds at
+  most kappa V_k, which the later d - k passes multiply by Lam^(d-k), where
+  pass 1 reads coarse values (V_1 = M, retrieval Y) and pass k >= 2 also
+  earlier passes' predictions, each bounded by Lam^(k-1) times that and also
+  by M + C0c (1 + 2u) (a prediction W at a level-0 point satisfies
+  |W| <= |x| + |c| / (1 - u)), retrieval Y + C0c (1 + 2u);
+  Y the final addition; Cr the coefficient side, with C0c = max |c| over
+  level 0 and Dm = max |value| of the decomposition's sub-levels S2, S3:
+  c = x - P rounded once (C0c), negabinary dequantisation (C0c); with
+  decomposition, per sub-level S2 its forward difference (Dm), the two
+  linear predictions (2 C0c) and the addition (C0c), and S3 its forward
+  difference (Dm), the two 2-pass bilinear predictions (4 C0c), the
+  addition (C0c) and the S2 points it reads: Cr = 9 C0c + 2 Dm generic,
+  10 C0c + 4 Dm negabinary (dequantisation of S1, S2, S3); s the subnormal
+  floor; G = 1.0001 the second-order terms.  kappa = worst rounding of one 1-D rule per unit input:
+  2.875 cubic (2.75 inside, 2.875 at the edges, see interp._F), 1 linear.
+  Fixed-point levels lose < one quantum per floor.
 * Greedy planner: take the step with the largest bound decrease per byte
   until the bound meets the target (the paper uses greedy for PMGARD and a DP
   / best-first search for its own modes; greedy is this build's reading).
@@ -28,9 +49,12 @@ import math
 import numpy as np
 
 LAMBDA = {"linear": 1.0, "cubic": 1.25}
-KAPPA = {"linear": 1.0, "cubic": 3.625}
+KAPPA = {"linear": 1.0, "cubic": 2.875}
 U_W = {"f32": 2.0 ** -24, "f64": 2.0 ** -53}
+# 256 times the largest absolute rounding error of a subnormal result
+SUBNORMAL = {"f32": 2.0 ** -142, "f64": 2.0 ** -1067}
 MARGIN = 1.000000001
+ROUND2 = 1.0001      # second-order rounding terms (n u < 1e-4 for the chains here)
 
 
 def _up(x):
@@ -159,20 +183,53 @@ class Composer:
         for _ in range(self.d - 1):
             lam_d1 *= self.lam
         self.lam_d = lam_d1 * self.lam
-        self.pf = (self.d * kap * lam_d1) if meta["interp"] == "level" else kap
         self.rho_fix = (2.0 * self.d * lam_d1 + 2.0) * self.h
+        neg = 1.0 if meta["encoding"] == "negabinary" else 0.0
+        self.C0c = meta["C0c"]
+        if meta["decomp_axis"] >= 0:
+            self.cr = (9.0 + neg) * self.C0c + (2.0 + 2.0 * neg) * meta["Dm"]
+        else:
+            self.cr = (1.0 + neg) * self.C0c
+        self.sub = SUBNORMAL[meta["dtype"]]
+        self.kap = kap
         # stream groups
         self.by_level = {}
         for i, s in enumerate(streams):
             self.by_level.setdefault(s["level"], []).append(i)
 
     # ---- L-infinity -------------------------------------------------------
+    def _mag(self, E1, e0sum):
+        """Y: bound on |x'| and on the inputs of the retrieval's level-0
+        prediction."""
+        return self.M + self.lam_d * (E1 + e0sum)
+
+    def _pred_rounding(self, Y):
+        """Pr: rounding of the level-0 prediction, refactoring + retrieval."""
+        M, lam, d = self.M, self.lam, self.d
+        if self.m["interp"] != "level":
+            return self.kap * (M + Y)
+        cap = self.C0c * (1.0 + 2.0 * self.uw)
+        acc = 0.0
+        lk = 1.0                       # Lam^(k-1)
+        for k in range(d):
+            vr = M if k == 0 else min(lk * M, M + cap)
+            vt = Y if k == 0 else min(lk * Y, Y + cap)
+            prop = 1.0                 # Lam^(d-k), later passes
+            for _ in range(d - 1 - k):
+                prop *= lam
+            acc += prop * (vr + vt)
+            lk *= lam
+        return self.kap * acc
+
     def rho0(self, E1, e0sum):
         if self.L == 1:
             return MARGIN * 1.01 * self.uw * self.C0
-        V = self.M + self.lam_d * E1 + e0sum
-        return 1.01 * self.uw * (2.0 * self.pf * V + self.lam_d * V + 2.0 * V
-                                 + 12.0 * self.C0)
+        Y = self._mag(E1, e0sum)
+        return ROUND2 * self.uw * (self._pred_rounding(Y) + Y + self.cr) + self.sub
+
+    def conv(self, E1, e0sum):
+        """Rounding of the fixed-point coarse values to the field dtype."""
+        return ROUND2 * self.uw * self._mag(E1, e0sum)
 
     def region_errors(self, level, err):
         """e_{l,r} per region (sum of sub-streams); region 0 = whole level."""
@@ -192,6 +249,7 @@ class Composer:
             reg = self.region_errors(level, err)
             if level == 0:
                 rho = self.rho0(E, sum(reg.values()))
+                E = E + self.conv(E, sum(reg.values()))
             else:
                 rho = self.rho_fix
             if self.m["interp"] == "level":
@@ -245,6 +303,8 @@ class Composer:
         E1, e0 = self._e1_and_e0(err)
         for level in range(L - 2, -1, -1):
             rho = self.rho0(E1, e0) if level == 0 else self.rho_fix
+            if level == 0:
+                N = N + self.conv(E1, e0) * math.sqrt(m["n"] - cnt[0])
             groups = {}
             for i in self.by_level[level]:
                 s = self.st[i]

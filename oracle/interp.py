@@ -26,7 +26,15 @@ outside the line:
   constant  a[j-1]
 Floating point evaluates exactly the expression trees in ``_F`` (left to right,
 no fused multiply-add); fixed point evaluates the integer numerator and floors
-the division by a power of two (arithmetic right shift).
+the division by a power of two (arithmetic right shift).  The floating-point
+trees are written to round little: with inputs bounded by V and unit
+roundoff u, the cubic rule as mean + correction,
+  s1 = a[j-1] + a[j+1],  s2 = a[j-3] + a[j+3],  s1 / 2 + (s1 - s2) / 16,
+rounds s1 (weight 9/16, |s1| <= 2V), s2 (1/16, 2V), s1 - s2 (1/16, 4V) and the
+sum (|result| <= 1.25 V): at most 2.75 u V; the edge rule as
+  0.75 a[j+1] + (0.375 a[j-1] - 0.125 a[j+3])
+rounds 0.75 a (0.75 V), 0.375 a (0.375 V), the difference (0.5 V) and the sum
+(1.25 V): 2.875 u V; the linear rule rounds a + b once: u V.
 """
 import numpy as np
 
@@ -39,19 +47,21 @@ class _F:
     def __init__(self, dt):
         self.dt = dt
         self.c = {k: dt.type(v) for k, v in
-                  dict(h=0.5, e=0.125, s=0.0625, three=3.0, six=6.0, nine=9.0).items()}
+                  dict(h=0.5, e=0.125, s=0.0625, q3=0.375, q6=0.75).items()}
 
     def lin(self, a, b):
         return (a + b) * self.c["h"]
 
     def cubic(self, m3, m1, p1, p3):
-        return ((m1 + p1) * self.c["nine"] - (m3 + p3)) * self.c["s"]
+        s1 = m1 + p1
+        s2 = m3 + p3
+        return s1 * self.c["h"] + (s1 - s2) * self.c["s"]
 
     def left(self, m1, p1, p3):
-        return ((self.c["three"] * m1 + self.c["six"] * p1) - p3) * self.c["e"]
+        return p1 * self.c["q6"] + (m1 * self.c["q3"] - p3 * self.c["e"])
 
     def right(self, m3, m1, p1):
-        return ((self.c["six"] * m1 + self.c["three"] * p1) - m3) * self.c["e"]
+        return m1 * self.c["q6"] + (p1 * self.c["q3"] - m3 * self.c["e"])
 
 
 class _I:

@@ -89,7 +89,9 @@ def _scatter(stream, vals, dst):
         off += lat.n_pad
 
 
-def refactor(X, scheme=Scheme()):
+def refactor(X, scheme=Scheme(), trace=None):
+    """Alg. 1.  ``trace`` (a dict, optional) receives the level-0 coefficient
+    array ``c`` and the decomposed values ``d`` (for tests)."""
     X = np.asarray(X)
     assert X.ndim in (2, 3) and min(X.shape) >= 2
     dt = X.dtype
@@ -135,6 +137,8 @@ def refactor(X, scheme=Scheme()):
                 sl = region_lattice(shape3, 0, order, r).slices()
                 Df[sl] = decompose(Cf[sl].copy(), uv)
 
+    if trace is not None:
+        trace["c"], trace["d"] = Cf.copy(), Df.copy()
     streams = []
     for s in geo.streams:
         src = Ci if s.is_int else (Df if s.sub > 0 else Cf)
@@ -147,12 +151,19 @@ def refactor(X, scheme=Scheme()):
                             n_real=s.n_real, n_pad=s.n_pad, is_int=s.is_int,
                             enc=enc, tab=tab, geo=s))
 
-    C0 = M if L == 1 else float(np.abs(Cf[level_points_mask(shape3, order)]).max())
+    # C0c: max |c| over the level-0 coefficients; Dm: max |value| of the
+    # decomposition's predicted sub-levels (S2, S3); C0: max over both
+    C0c = M if L == 1 else float(np.abs(Cf[level_points_mask(shape3, order)]).max())
+    Dm = 0.0
+    for s in streams:
+        if s["level"] == 0 and not s["is_int"] and s["sub"] >= 2:
+            Dm = max(Dm, s["enc"]["quant"]["vmax"])
+    C0 = C0c
     for s in streams:
         if s["level"] == 0 and not s["is_int"]:
             C0 = max(C0, s["enc"]["quant"]["vmax"])
     meta = dict(L=L, d=len(order), degree=scheme.degree, interp=scheme.interp,
-                dtype=dtag, h=h, G=G, M=M, C0=C0, R=xmax - xmin, xmin=xmin,
+                dtype=dtag, h=h, G=G, M=M, C0=C0, C0c=C0c, Dm=Dm, R=xmax - xmin, xmin=xmin,
                 xmax=xmax, n=X3.size, B=B, encoding=encoding, order=order,
                 decomp_axis=dax, shape3=shape3, shape=X.shape, mode=scheme.mode)
     _add_factors(meta, geo)
@@ -217,9 +228,11 @@ def plan(handle, target):
     return dict(b=b, bound=bound, satisfied=ok, bytes=total, kind=target.kind)
 
 
-def retrieve(handle, target_or_plan):
+def retrieve(handle, target_or_plan, trace=None):
     """Alg. 2: decode the planned planes, recompose level 0, reconstruct
-    coarse -> fine.  Returns (x', plan)."""
+    coarse -> fine.  Returns (x', plan).  ``trace`` (a dict, optional)
+    receives the decoded level-0 coefficients ``c_hat`` (recomposed) and
+    decoded sub-level values ``d_hat`` (for tests)."""
     pl = target_or_plan if isinstance(target_or_plan, dict) else plan(handle, target_or_plan)
     meta = handle["meta"]
     dt = handle["dtype"]
@@ -239,6 +252,8 @@ def retrieve(handle, target_or_plan):
         for r in range(1, len(order) + 1):
             sl = region_lattice(shape3, 0, order, r).slices()
             Cf[sl] = recompose(Df[sl].copy(), uv)
+    if trace is not None:
+        trace["c_hat"], trace["d_hat"] = Cf.copy(), Df.copy()
     Xi = np.zeros(shape3, dtype=np.int64)
     cl = coarse_lattice(shape3, L).slices()
     Xi[cl] = Ci[cl]

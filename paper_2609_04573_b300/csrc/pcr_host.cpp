@@ -483,10 +483,13 @@ struct Tab {
 };
 
 constexpr double kMargin = 1.000000001;
+constexpr double kRound2 = 1.0001;   // second-order rounding terms
 
 struct Meta {
   int L = 1, d = 1, degree = 3, interp = 0, dtype = 0, decomp = -1;
+  int enc = 1;   // 1 generic, 2 negabinary
   double h = 0, M = 0, C0 = 0, R = 0;
+  double C0c = 0, Dm = 0;   // max |c| at level 0; max |S2 / S3 value|
   int64_t n = 0;
   std::map<int, int64_t> level_counts;
   std::map<std::pair<int, int>, int64_t> region_counts;
@@ -499,32 +502,78 @@ struct SRef {
   int level, region, sub;
 };
 
+// Rounding at level 0 (field dtype, unit roundoff u).  The coarse values are
+// the fixed-point reconstruction rounded once to the field dtype: conv() =
+// G u Y joins the incoming error.  Every level-0 point then carries
+// rho0() = G u (Pr + Y + Cr) + sub, with Y = M + Lam^d (E_1 + sum e_0)
+// bounding |x'| and the retrieval's prediction inputs:
+//   Pr     rounding of the prediction in refactoring and in retrieval: one
+//          per-region pass rounds at most kappa (M + Y); per-level pass k
+//          rounds at most kappa V_k, multiplied by Lam^(d-k) in the later
+//          passes; pass 1 reads coarse values (V_1 = M; retrieval Y), pass
+//          k >= 2 also earlier predictions, bounded by Lam^(k-1) V_1 and by
+//          M + C0c (1 + 2u) (|W| <= |x| + |c| / (1 - u) at a level-0 point;
+//          retrieval Y + C0c (1 + 2u)); kappa = 2.875 cubic (the rule forms of
+//          the kernels), 1 linear;
+//   Y      the final addition x' = P + c_hat;
+//   Cr     the coefficient side, with C0c = max |c| over level 0 and Dm =
+//          max |value| of the decomposition's sub-levels S2, S3: c = x - P
+//          rounded once (C0c), negabinary dequantisation (C0c); with
+//          decomposition S2's forward difference (Dm), two linear
+//          predictions (2 C0c) and addition (C0c), S3's forward difference
+//          (Dm), two 2-pass bilinear predictions (4 C0c), addition (C0c) and
+//          the S2 points it reads: 9 C0c + 2 Dm generic, 10 C0c + 4 Dm
+//          negabinary (dequantisation of S1, S2, S3);
+//   sub    256 times the largest absolute error of a subnormal result;
+//   G      1.0001, the second-order terms.
 struct Composer {
   Meta m;
   std::vector<SRef> st;
   std::map<int, std::vector<int>> by_level;
-  double lam, uw, lam_d, pf, rho_fix;
+  double lam, uw, lam_d, rho_fix, cr, sub, kap;
 
   void init(const Meta& meta, const std::vector<SRef>& streams) {
     m = meta;
     st = streams;
     lam = m.degree == 3 ? 1.25 : 1.0;
     uw = m.dtype == PCR_F32 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
-    const double kap = m.degree == 3 ? 3.625 : 1.0;
+    kap = m.degree == 3 ? 2.875 : 1.0;
     double lam_d1 = 1.0;
     for (int i = 0; i < m.d - 1; i++) lam_d1 *= lam;
     lam_d = lam_d1 * lam;
-    pf = m.interp == 0 ? ((double)m.d * kap * lam_d1) : kap;
     rho_fix = (2.0 * (double)m.d * lam_d1 + 2.0) * m.h;
+    const double neg = m.enc == 2 ? 1.0 : 0.0;
+    cr = m.decomp >= 0 ? (9.0 + neg) * m.C0c + (2.0 + 2.0 * neg) * m.Dm : (1.0 + neg) * m.C0c;
+    sub = m.dtype == PCR_F32 ? std::ldexp(1.0, -142) : std::ldexp(1.0, -1067);
     by_level.clear();
     for (size_t i = 0; i < st.size(); i++) by_level[st[i].level].push_back((int)i);
   }
 
+  double mag(double E1, double e0sum) const { return m.M + lam_d * (E1 + e0sum); }
+
+  double pred_rounding(double Y) const {
+    if (m.interp != 0) return kap * (m.M + Y);
+    const double cap = m.C0c * (1.0 + 2.0 * uw);
+    double acc = 0.0, lk = 1.0;
+    for (int k = 0; k < m.d; k++) {
+      const double vr = k == 0 ? m.M : std::min(lk * m.M, m.M + cap);
+      const double vt = k == 0 ? Y : std::min(lk * Y, Y + cap);
+      double prop = 1.0;
+      for (int j = 0; j < m.d - 1 - k; j++) prop *= lam;
+      acc += prop * (vr + vt);
+      lk *= lam;
+    }
+    return kap * acc;
+  }
+
   double rho0(double E1, double e0sum) const {
     if (m.L == 1) return kMargin * 1.01 * uw * m.C0;
-    const double V = m.M + lam_d * E1 + e0sum;
-    return 1.01 * uw * (2.0 * pf * V + lam_d * V + 2.0 * V + 12.0 * m.C0);
+    const double Y = mag(E1, e0sum);
+    return kRound2 * uw * (pred_rounding(Y) + Y + cr) + sub;
   }
+
+  // rounding of the fixed-point coarse values to the field dtype
+  double conv(double E1, double e0sum) const { return kRound2 * uw * mag(E1, e0sum); }
 
   // region -> summed error, in order of first appearance (stream order)
   std::vector<std::pair<int, double>> region_errors(int level, const std::vector<double>& err) const {
@@ -573,6 +622,7 @@ struct Composer {
     for (int level = L - 2; level >= 0; level--) {
       auto reg = region_errors(level, err);
       const double rho = level == 0 ? rho0(E, sum_vals(reg)) : rho_fix;
+      if (level == 0) E = E + conv(E, sum_vals(reg));
       E = level_step(E, reg, rho);
     }
     return E * kMargin;
@@ -602,6 +652,7 @@ struct Composer {
     e1_e0(err, E1, e0);
     for (int level = L - 2; level >= 0; level--) {
       const double rho = level == 0 ? rho0(E1, e0) : rho_fix;
+      if (level == 0) N = N + conv(E1, e0) * std::sqrt((double)(m.n - m.level_counts.at(0)));
       std::map<int, std::vector<std::pair<int, int>>> groups;
       for (int i : by_level.at(level)) groups[st[i].region].push_back({st[i].sub, i});
       std::map<int, double> cnorm;
@@ -785,6 +836,7 @@ struct pcr_handle {
   std::vector<int> order;
   int L = 1, B = 32, enc = 1, decomp = -1;
   double xmin = 0, xmax = 0, M = 0, h = 0, C0 = 0;
+  double C0c = 0;   // max |c| over the level-0 coefficients (before decomposition)
   int G = 0;
   std::vector<SGeo> geo;
   std::vector<int> E, sh;
@@ -818,6 +870,7 @@ struct pcr_handle {
   size_t items_n[2] = {0, 0};
   bool items_ready = false;
   void* d_block = nullptr;   // one allocation holding planes, signs, counts and the work list
+  int device = -1;           // CUDA device holding d_block (current device at allocation)
   ~pcr_handle() {
     if (d_block) mem.free(d_block, 0);
   }
@@ -1071,9 +1124,14 @@ void build_meta(pcr_handle* h) {
   m.interp = h->sch.interp;
   m.dtype = h->dtype;
   m.decomp = h->decomp;
+  m.enc = h->enc;
   m.h = h->h;
   m.M = h->M;
   m.C0 = h->C0;
+  m.C0c = h->C0c;
+  m.Dm = 0.0;
+  for (size_t i = 0; i < h->geo.size(); i++)
+    if (h->geo[i].level == 0 && !h->geo[i].is_fix && h->geo[i].sub >= 2) m.Dm = std::max(m.Dm, h->vmax[i]);
   m.R = h->xmax - h->xmin;
   m.n = h->n3[0] * h->n3[1] * h->n3[2];
   m.level_counts.clear();
@@ -1176,7 +1234,7 @@ struct BoundEval {
   std::vector<std::vector<int>> by_id;   // slots in ascending region id
   std::vector<std::vector<Group>> grp;   // per level, ascending region id
   std::vector<double> lfac, lcnt;        // per level: level factor, sqrt(point count)
-  double top_cnt = 0;
+  double top_cnt = 0, n2grid = 0;
   // kept state for the current errors
   std::vector<double> E_in, N_in, csum;
   std::vector<std::vector<double>> acc, cn;
@@ -1235,6 +1293,7 @@ struct BoundEval {
       }
     }
     if (l2) top_cnt = std::sqrt((double)c.m.level_counts.at(L - 1));
+    if (l2 && L >= 2) n2grid = std::sqrt((double)(c.m.n - c.m.level_counts.at(0)));
     E_in.assign(L, 0.0);
     N_in.assign(L, 0.0);
     csum.assign(L, 0.0);
@@ -1305,7 +1364,7 @@ struct BoundEval {
     const int start = std::min(from, L - 2);
     // the L-infinity chain (for L2: down to the rounding term of level 0)
     double E = from >= L - 1 ? top(err) : E_in[from];
-    double rho_0 = 0.0;
+    double rho_0 = 0.0, conv_0 = 0.0;
     for (int level = start; level >= 0; level--) {
       const double* a;
       if (level == from || !acc_ok[level]) {
@@ -1325,8 +1384,9 @@ struct BoundEval {
       if (keep) E_in[level] = E;
       if (level == 0) {
         rho_0 = c.rho0(E, sum_vals(0, a));
+        conv_0 = c.conv(E, sum_vals(0, a));
         if (l2) break;
-        E = level_step(0, E, a, rho_0);
+        E = level_step(0, E + conv_0, a, rho_0);
       } else {
         E = level_step(level, E, a, c.rho_fix);
       }
@@ -1341,6 +1401,8 @@ struct BoundEval {
     }
     for (int level = start; level >= 0; level--) {
       const double rho = level == 0 ? rho_0 : c.rho_fix;
+      if (level == 0 && keep) N_in[0] = N;
+      if (level == 0) N = N + conv_0 * n2grid;
       const double* a;
       double cs;
       if (level == from || !cn_ok[level]) {
@@ -1359,7 +1421,7 @@ struct BoundEval {
         a = cn[level].data();
         cs = csum[level];
       }
-      if (keep) N_in[level] = N;
+      if (keep && level > 0) N_in[level] = N;
       if (c.m.interp == 0) {
         const double t = lfac[level] * N + cs + rho * lcnt[level];
         N = std::sqrt(N * N + t * t);
@@ -1721,6 +1783,7 @@ static pcr_status finish_refactor(pcr_handle* h, const FieldStats& st, const std
   double c0;
   std::memcpy(&c0, &st.c0, 8);
   h->C0 = h->L == 1 ? h->M : c0;
+  h->C0c = h->C0;
   for (int i = 0; i < ns; i++) {
     const SGeo& g = h->geo[i];
     const unsigned long long v = vm[i];
@@ -1744,6 +1807,7 @@ static pcr_status finish_refactor(pcr_handle* h, const FieldStats& st, const std
       if (dv > 0) std::frexp(dv, &E);
       h->E[i] = E;
       if (g.level == 0 && h->L >= 2) h->C0 = std::max(h->C0, dv);
+      if (g.level == 0 && h->L >= 2 && g.sub <= 1) h->C0c = std::max(h->C0c, dv);
     }
     const int64_t nseg = (g.n_pad() + kSegElems - 1) / kSegElems;
     h->plane_nz[i].assign(nz.begin() + h->nz_off[i], nz.begin() + h->nz_off[i] + h->B);
@@ -1763,6 +1827,7 @@ static pcr_status alloc_handle_buffers(pcr_handle* h, cudaStream_t s) {
   const size_t b_pl = al(h->plane_words * 4), b_sg = al(std::max<size_t>(h->sign_area_words, 1) * 4),
                b_sc = al(std::max<size_t>(h->scnt_words, 1) * 4), b_nz = al(h->nz_words * 4),
                b_it = al(std::max<size_t>(items, 1) * sizeof(WorkItem));
+  CUDA_TRY(cudaGetDevice(&h->device));
   h->d_block = h->mem.alloc(b_pl + b_sg + b_sc + b_nz + b_it + 256, s);
   if (!h->d_block) return fail(PCR_ERR_OOM, "handle allocation failed");
   char* p = (char*)(((uintptr_t)h->d_block + 255) & ~uintptr_t(255));
@@ -2808,6 +2873,19 @@ extern "C" pcr_status pcr_retrieve_scratch_bytes(const pcr_handle* h, size_t* by
 extern "C" pcr_status pcr_retrieve_static(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out,
                                           void* cuda_stream) {
   if (!h || !plan || !d_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // the scratch array is per device: it must be the one holding the handle
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != h->device)
+    return fail(PCR_ERR_INVALID_ARG, "current device " + std::to_string(dev) + " is not the handle's device " +
+                                         std::to_string(h->device));
+  // the call uploads its stream descriptors (and, for handles without a kept
+  // work list, the work list) from host memory that does not outlive it
+  cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+  CUDA_TRY(cudaStreamIsCapturing(s, &cap_st));
+  if (cap_st != cudaStreamCaptureStatusNone)
+    return fail(PCR_ERR_UNSUPPORTED, "pcr_retrieve_static does not accept a stream that is being captured");
   size_t cap = 0;
   std::string why;
   char* base = (char*)static_scratch(&cap, &why);
@@ -2816,7 +2894,6 @@ extern "C" pcr_status pcr_retrieve_static(const pcr_handle* h, const pcr_retriev
   if (need > cap)
     return fail(PCR_ERR_UNSUPPORTED, "retrieval needs " + std::to_string(need) +
                                          " bytes of scratch; the static array holds " + std::to_string(cap));
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   Mem mem = h->mem;
   Scratch sc{&mem, s, {}};
   sc.bump = base;
@@ -2961,7 +3038,7 @@ struct Reader {
     return q;
   }
 };
-const uint64_t kMagic = 0x3130524350ull;  // "PCR01"
+const uint64_t kMagic = 0x3230524350ull;  // "PCR02"
 }  // namespace
 
 extern "C" pcr_status pcr_serialize(const pcr_handle* h, void** buf, size_t* len) {
@@ -2978,6 +3055,7 @@ extern "C" pcr_status pcr_serialize(const pcr_handle* h, void** buf, size_t* len
   hd.put(h->xmax);
   hd.put(h->G);
   hd.put(h->C0);
+  hd.put(h->C0c);
   const int ns = (int)h->geo.size();
   for (int i = 0; i < ns; i++) {
     hd.put(h->vmax[i]);
@@ -3043,6 +3121,7 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
   h->xmax = hr.get<double>();
   h->G = hr.get<int>();
   h->C0 = hr.get<double>();
+  h->C0c = hr.get<double>();
   h->M = std::max(std::fabs(h->xmin), std::fabs(h->xmax));
   h->h = std::ldexp(1.0, h->G - kFixBits);
   const int ns = (int)h->geo.size();

@@ -330,7 +330,6 @@ def test_int64_to_float32_single_rounding():
     v = (1 << 60) + (1 << 36) + 1          # just above a float32 tie
     f = from_fixed(np.array([v], np.int64), 40, np.dtype(np.float32))[0]
     exact = Fraction(v)
-    lo = Fraction(float(np.float32(np.nextafter(np.float32(2.0 ** 60), np.float32(0))))) if False else None
     cands = [np.float32(2.0 ** 60), np.nextafter(np.float32(2.0 ** 60), np.float32(np.inf))]
     best = min(cands, key=lambda c: abs(Fraction(float(c)) - exact))
     assert f == best
@@ -453,9 +452,50 @@ def test_max_ordering_segments_descend_and_merge_equal_steps():
             final[i] = nb
 
 
-def test_psnr_definition_and_bitrate():
-    """Sec. III-A PSNR = 20 log10(range / RMSE); Sec. VII bitrate = 8 S / n."""
-    X = np.array([[0.0, 1.0], [2.0, 4.0]])
-    Y = X + np.array([[0.1, -0.1], [0.1, -0.1]])
-    rmse = math.sqrt(np.mean((X - Y) ** 2))
-    assert abs(20 * math.log10(4.0 / rmse) - 20 * math.log10(40.0)) < 1e-12
+def test_psnr_plan_meets_definition():
+    """Sec. III-A: PSNR = 20 log10((max x - min x) / RMSE).  The planner's SSE
+    bound for a PSNR target must imply that PSNR by the definition, and the
+    retrieved field's PSNR, computed here from the definition in FP64, must
+    reach it."""
+    X = grf((24, 20, 28), 23, np.float32)
+    X64 = X.astype(np.float64)
+    h = oracle.refactor(X, Scheme(mode="psnr", interp="region", degree="cubic"))
+    R = float(X64.max() - X64.min())
+    for p in (40.0, 70.0, 100.0):
+        xr, pl = oracle.retrieve(h, Target("psnr", p))
+        assert pl["satisfied"]
+        sse = float(np.sum((xr.astype(np.float64) - X64) ** 2))
+        assert sse <= pl["bound"]
+        assert 20 * math.log10(R / math.sqrt(pl["bound"] / X.size)) >= p
+        assert 20 * math.log10(R / math.sqrt(sse / X.size)) >= p
+
+
+def _golden_streams():
+    streams, cur = [], None
+    for line in open(f"{GOLDEN}/stream_bytes.txt"):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "stream":
+            cur = dict(enc=f[1], B=int(f[2]), n=int(f[3]), vals={})
+            streams.append(cur)
+        elif f[0] == "value":
+            cur["vals"][int(f[1])] = int(f[2])
+        elif f[0] == "range":            # elements lo .. hi-1 all hold one value
+            for i in range(int(f[1]), int(f[2])):
+                cur["vals"][i] = int(f[3])
+        elif f[0] == "expect":
+            cur["expect"] = [int(x) for x in f[1:]]
+    return streams
+
+
+def test_stream_bytes_hand_counted():
+    """bytes(b) equals hand-counted tables (tests/golden/stream_bytes.txt):
+    zero planes are free, sign words of planes < b only, counted per sign
+    segment; negabinary XOR can make a digit plane free."""
+    for st in _golden_streams():
+        vals = np.zeros(st["n"], dtype=np.int64)
+        for i, v in st["vals"].items():
+            vals[i] = v
+        enc = bp.encode(vals, True, st["B"], st["enc"], False)
+        assert bp.stream_bytes(enc, st["B"], st["n"] // WORD) == st["expect"]
