@@ -48,7 +48,7 @@ typedef enum {
 } pcr_status;
 
 enum { PCR_F32 = 0, PCR_F64 = 1 };
-enum { PCR_MODE_EB = 0, PCR_MODE_PSNR = 1 };
+enum { PCR_MODE_EB = 0, PCR_MODE_PSNR = 1, PCR_MODE_EXPLICIT = 2 };
 enum { PCR_INTERP_LEVEL = 0, PCR_INTERP_REGION = 1 };
 enum { PCR_LINEAR = 1, PCR_CUBIC = 3 };
 enum { PCR_ENC_DEFAULT = 0, PCR_ENC_GENERIC = 1, PCR_ENC_NEGABINARY = 2 };
@@ -68,14 +68,17 @@ typedef struct {
 /* Refactoring scheme (Sec. IV-VI; tuning table of Sec. VI-A).
  *   mode        PCR_MODE_EB: error-bound mode, L-inf tables only (sq tables
  *               are the L-inf bound times the count);
- *               PCR_MODE_PSNR: also exact integer squared-error tables.
+ *               PCR_MODE_PSNR: also exact integer squared-error tables;
+ *               PCR_MODE_EXPLICIT: every field taken as given, exact integer
+ *               squared-error tables kept, so the handle serves error-bound
+ *               and PSNR targets alike (encoding default: generic).
  *   interp      per-level (pass order = natural axis order) or per-region.
  *   degree      PCR_LINEAR or PCR_CUBIC.
  *   order       per-region pass order: a permutation of the field's axes
  *               (3-D: of 0,1,2; 2-D: of 0,1 in order[0..1]); ignored per-level.
  *   decomp_axis slice normal (0..2) of the level-0 coefficient decomposition
  *               (Sec. V-B), or -1 for none; 3-D only.
- *   encoding    PCR_ENC_DEFAULT picks generic for EB, negabinary+XOR for PSNR.
+ *   encoding    PCR_ENC_DEFAULT picks negabinary+XOR for PSNR, generic otherwise.
  *   nlevels     L (0 = auto: coarsest grid keeps >= 3 points per axis).
  *   nplanes     B (0 = auto: 32 for FP32, 64 for FP64; otherwise 1..B_auto). */
 typedef struct {
@@ -91,10 +94,17 @@ typedef struct {
 
 /* Retrieval target (Sec. III-A): PCR_TARGET_ABS max|x - x'| <= value;
  * PCR_TARGET_REL max|x - x'| <= value * (max x - min x);
- * PCR_TARGET_PSNR 20 log10((max x - min x) / RMSE) >= value (dB). */
+ * PCR_TARGET_PSNR 20 log10((max x - min x) / RMSE) >= value (dB).
+ * has_box != 0 asks for the box [lo, hi) of the field only (user axes,
+ * 0 <= lo < hi <= dims; entries past ndim are ignored): the plan is the
+ * whole field's (its L-inf bound holds at every point, so inside the box;
+ * a PSNR target is planned on the whole field) and the output holds the
+ * box, row-major. */
 typedef struct {
   int kind;
   double value;
+  int has_box;
+  int64_t lo[3], hi[3];
 } pcr_target;
 
 /* A retrieval plan: how many planes of every stream to read (host data). */
@@ -106,6 +116,34 @@ typedef struct {
   uint64_t bytes;     /* payload bytes read: plane words + sign words       */
   int satisfied;      /* 1 when the bound meets the target                  */
 } pcr_retrieval_plan;
+
+/* What one pcr_retrieve call read and how long it took. */
+typedef struct {
+  int nstreams;
+  int planes[PCR_MAX_STREAMS];  /* planes read per stream                    */
+  uint64_t bytes;               /* plane words + sign words read             */
+  double bits_per_value;        /* 8 bytes / points of the output            */
+  double bound;                 /* L-inf bound (ABS/REL) or SSE bound (PSNR) */
+  double psnr_bound;            /* PSNR implied by the SSE bound (PSNR)      */
+  int satisfied;                /* 1 when the bound meets the target         */
+  double plan_ms;               /* host time of the interpreter              */
+  double enqueue_ms;            /* host time enqueueing the GPU work         */
+  int want_gpu_ms;              /* input: 1 = time the GPU work (the call
+                                   then waits for it)                        */
+  double gpu_ms;                /* GPU time of the call's work, -1 untimed   */
+} pcr_retrieval_info;
+
+/* Error tables of every stream (Sec. V-C).  The library fills nstreams,
+ * nplanes (B) and exponent[]; maxerr / sq / bytes, when not NULL, are
+ * caller arrays of nstreams * (nplanes + 1) entries, row i = stream i,
+ * column b = b planes read (call once with NULL arrays to learn the sizes). */
+typedef struct {
+  int nstreams, nplanes;
+  int exponent[PCR_MAX_STREAMS];  /* E (float streams) or bit length (fixed) */
+  double* maxerr;                 /* L-inf error bound                        */
+  double* sq;                     /* squared-error bound (sum over the stream)*/
+  uint64_t* bytes;                /* bytes of the first b planes              */
+} pcr_tables;
 
 /* Per-stream description (tests, tools, serialisation). */
 typedef struct {
@@ -216,22 +254,36 @@ pcr_status pcr_autotune_read(int max_entries, int64_t* keys, int* choice, double
 pcr_status pcr_plan(const pcr_handle* h, const pcr_target* target, pcr_retrieval_plan* out);
 
 /* ---- retrieve (Algorithm 2) ------------------------------------------- */
-/* Decode the planes of `plan` (from pcr_plan on the same handle), recompose
- * and reconstruct into the caller's device buffer `d_out` (same shape and
- * dtype as the refactored field).  Returns after enqueueing. */
-pcr_status pcr_retrieve(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out,
-                        void* cuda_stream);
+/* One call: plan `target` (as pcr_plan) and reconstruct into the caller's
+ * device buffer `d_out` (the field's shape and dtype, or the box's when
+ * target->has_box).  Returns after enqueueing, unless info->want_gpu_ms is
+ * set (then it waits for the work and reports its GPU time).  `info` may be
+ * NULL.  PCR_ERR_UNSATISFIABLE: even every plane cannot meet the target;
+ * nothing is enqueued and info (bound, planes = all) is still filled. */
+pcr_status pcr_retrieve(const pcr_handle* h, const pcr_target* target, void* d_out, void* cuda_stream,
+                        pcr_retrieval_info* info);
 
-/* Batched retrieval: n (handle, plan, output) triples, one work list per
- * stage.  Used by the serving loop. */
-pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
-                              void* const* d_outs, void* cuda_stream);
+/* Decode the planes of `plan` (from pcr_plan on the same handle, or any
+ * plane counts 0..B), recompose and reconstruct into `d_out` (same shape
+ * and dtype as the refactored field).  Returns after enqueueing. */
+pcr_status pcr_retrieve_plan(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out,
+                             void* cuda_stream);
+
+/* Batched retrieval: n (handle, target, output) triples planned one by one
+ * and retrieved with one work list per stage (whole-field targets only;
+ * box targets go through pcr_retrieve).  infos: n entries or NULL. */
+pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_target* targets,
+                              void* const* d_outs, void* cuda_stream, pcr_retrieval_info* infos);
+
+/* The same with plans given (the serving loop plans on its own). */
+pcr_status pcr_retrieve_batch_plan(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
+                                   void* const* d_outs, void* cuda_stream);
 
 /* Retrieval of a box [lo, hi) of the field (user axes, 0 <= lo < hi <= dims)
  * under `plan` (from pcr_plan: the bound holds at every point, so inside the
  * box too).  d_out: device buffer of the box, row-major, prod(hi - lo)
- * values of the field dtype.  Returns exactly the box of what pcr_retrieve
- * with the same plan returns.  A point at level l depends on the coarser
+ * values of the field dtype.  Returns exactly the box of what
+ * pcr_retrieve_plan with the same plan returns.  A point at level l depends on the coarser
  * grid and on level l's coefficients within 3 * 2^l field points per axis
  * (Alg. 2's rules), so only the stream segments meeting the box's
  * dependency region are decoded and only the tiles meeting it are
@@ -240,12 +292,12 @@ pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_retr
 pcr_status pcr_retrieve_box(const pcr_handle* h, const pcr_retrieval_plan* plan, const int64_t* lo,
                             const int64_t* hi, void* d_out, void* cuda_stream);
 
-/* Upper bound on the temporary device memory one pcr_retrieve of `h` takes
+/* Upper bound on the temporary device memory one retrieval of `h` takes
  * (staging, work lists, recomposition); used for memory-based admission. */
 pcr_status pcr_retrieve_scratch_bytes(const pcr_handle* h, size_t* bytes);
 
 /* ---- retrieval without device allocation -------------------------------- */
-/* Same plans, same kernels and the same output as pcr_retrieve, for callers
+/* Same plans, same kernels and the same output as pcr_retrieve_plan, for callers
  * that must not allocate device memory: applications whose own pool or arena
  * owns all device memory, hosts that forbid libraries to allocate on their
  * behalf, and latency-bound loops where cudaMalloc / cudaFree would
@@ -279,6 +331,8 @@ pcr_status pcr_retrieve_static(const pcr_handle* h, const pcr_retrieval_plan* pl
 /* ---- introspection / persistence -------------------------------------- */
 pcr_status pcr_num_streams(const pcr_handle* h, int* n);
 pcr_status pcr_stream_info_get(const pcr_handle* h, int i, pcr_stream_info* out);
+/* Error tables of every stream at once (see pcr_tables). */
+pcr_status pcr_get_tables(const pcr_handle* h, pcr_tables* out);
 /* Error tables of stream i: maxerr[B+1], sq[B+1] (FP64) and bytes[B+1]. */
 pcr_status pcr_stream_tables(const pcr_handle* h, int i, double* maxerr, double* sq,
                              uint64_t* bytes);

@@ -47,7 +47,21 @@ class _Scheme(C.Structure):
 
 
 class _Target(C.Structure):
-    _fields_ = [("kind", C.c_int), ("value", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("value", C.c_double), ("has_box", C.c_int),
+                ("lo", C.c_int64 * 3), ("hi", C.c_int64 * 3)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("nstreams", C.c_int), ("planes", C.c_int * MAX_STREAMS), ("bytes", C.c_uint64),
+                ("bits_per_value", C.c_double), ("bound", C.c_double), ("psnr_bound", C.c_double),
+                ("satisfied", C.c_int), ("plan_ms", C.c_double), ("enqueue_ms", C.c_double),
+                ("want_gpu_ms", C.c_int), ("gpu_ms", C.c_double)]
+
+
+class _Tables(C.Structure):
+    _fields_ = [("nstreams", C.c_int), ("nplanes", C.c_int), ("exponent", C.c_int * MAX_STREAMS),
+                ("maxerr", C.POINTER(C.c_double)), ("sq", C.POINTER(C.c_double)),
+                ("bytes", C.POINTER(C.c_uint64))]
 
 
 class _Plan(C.Structure):
@@ -79,8 +93,12 @@ _sigs = {
     "pcr_refactor_batch": [C.c_int, C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(_i64p), C.POINTER(C.c_int),
                            C.POINTER(_Scheme), C.POINTER(_Allocator), _vp, C.POINTER(_vp)],
     "pcr_plan": [_vp, C.POINTER(_Target), C.POINTER(_Plan)],
-    "pcr_retrieve": [_vp, C.POINTER(_Plan), _vp, _vp],
-    "pcr_retrieve_batch": [C.c_int, C.POINTER(_vp), C.POINTER(_Plan), C.POINTER(_vp), _vp],
+    "pcr_retrieve": [_vp, C.POINTER(_Target), _vp, _vp, C.POINTER(_Info)],
+    "pcr_retrieve_plan": [_vp, C.POINTER(_Plan), _vp, _vp],
+    "pcr_retrieve_batch": [C.c_int, C.POINTER(_vp), C.POINTER(_Target), C.POINTER(_vp), _vp,
+                           C.POINTER(_Info)],
+    "pcr_retrieve_batch_plan": [C.c_int, C.POINTER(_vp), C.POINTER(_Plan), C.POINTER(_vp), _vp],
+    "pcr_get_tables": [_vp, C.POINTER(_Tables)],
     "pcr_retrieve_static": [_vp, C.POINTER(_Plan), _vp, _vp],
     "pcr_retrieve_box": [_vp, C.POINTER(_Plan), _i64p, _i64p, _vp, _vp],
     "pcr_retrieve_scratch_bytes": [_vp, C.POINTER(C.c_size_t)],
@@ -159,7 +177,7 @@ _ALLOC_CB = _ALLOC_FN(_torch_alloc)
 _FREE_CB = _FREE_FN(_torch_free)
 _ALLOCATOR = _Allocator(None, _ALLOC_CB, _FREE_CB)
 
-EB, PSNR = 0, 1
+EB, PSNR, EXPLICIT = 0, 1, 2
 LEVEL, REGION = 0, 1
 LINEAR, CUBIC = 1, 3
 GENERIC, NEGABINARY = 1, 2
@@ -169,7 +187,7 @@ _DT = {torch.float32: 0, torch.float64: 1}
 @dataclass
 class Scheme:
     """Refactoring scheme (Sec. IV-VI, tuning table of Sec. VI-A)."""
-    mode: str = "eb"                 # "eb" | "psnr"
+    mode: str = "eb"                 # "eb" | "psnr" | "explicit"
     interp: str = "level"            # "level" | "region"
     degree: str = "cubic"            # "linear" | "cubic"
     order: Optional[Tuple[int, ...]] = None
@@ -189,7 +207,7 @@ class Scheme:
 
     def c(self, ndim):
         s = _Scheme()
-        s.mode = PSNR if self.mode == "psnr" else EB
+        s.mode = {"eb": EB, "psnr": PSNR, "explicit": EXPLICIT}[self.mode]
         s.interp = REGION if self.interp == "region" else LEVEL
         s.degree = CUBIC if self.degree == "cubic" else LINEAR
         order = self.order or tuple(range(ndim))
@@ -206,9 +224,17 @@ class Scheme:
 class Target:
     kind: str      # "abs" | "rel" | "psnr"
     value: float
+    box: Optional[Tuple[Tuple[int, int], ...]] = None   # ((lo, hi) per axis) or None
 
     def c(self):
-        return _Target({"abs": 0, "rel": 1, "psnr": 2}[self.kind], float(self.value))
+        t = _Target()
+        t.kind = {"abs": 0, "rel": 1, "psnr": 2}[self.kind]
+        t.value = float(self.value)
+        if self.box is not None:
+            t.has_box = 1
+            for k, (lo, hi) in enumerate(self.box):
+                t.lo[k], t.hi[k] = int(lo), int(hi)
+        return t
 
 
 @dataclass
@@ -219,6 +245,25 @@ class Plan:
     bytes: int
     satisfied: bool
     _c: object = field(default=None, repr=False)
+
+
+@dataclass
+class RetrievalInfo:
+    """What one pcr_retrieve call read (pcr_retrieval_info)."""
+    planes: list
+    bytes: int
+    bits_per_value: float
+    bound: float
+    psnr_bound: float
+    satisfied: bool
+    plan_ms: float
+    enqueue_ms: float
+    gpu_ms: float
+
+    @classmethod
+    def of(cls, i):
+        return cls(list(i.planes[:i.nstreams]), i.bytes, i.bits_per_value, i.bound, i.psnr_bound,
+                   bool(i.satisfied), i.plan_ms, i.enqueue_ms, i.gpu_ms)
 
 
 def _stream_ptr(stream):
@@ -302,14 +347,46 @@ class Handle:
             p.planes[i] = int(b)
         return Plan(list(planes), 0.0, 0.0, 0, True, p)
 
-    def retrieve(self, target_or_plan, out=None, stream=None):
-        """Reconstruct into ``out`` (allocated when None).  Returns (out, plan)."""
-        plan = target_or_plan if isinstance(target_or_plan, Plan) else self.plan(target_or_plan)
+    def retrieve(self, target_or_plan, out=None, stream=None, gpu_time=False):
+        """Reconstruct into ``out`` (allocated when None).  A Target goes
+        through the one-call pcr_retrieve (its box, if any, sets the output
+        shape) and returns (out, RetrievalInfo); a Plan goes through
+        pcr_retrieve_plan and returns (out, plan)."""
+        if isinstance(target_or_plan, Plan):
+            plan = target_or_plan
+            if out is None:
+                out = torch.empty(self.shape, dtype=self.dtype, device=self.device)
+            assert out.is_contiguous() and tuple(out.shape) == self.shape and out.dtype == self.dtype
+            _check(_lib.pcr_retrieve_plan(self._p, C.byref(plan._c), C.c_void_p(out.data_ptr()),
+                                          _stream_ptr(stream)))
+            return out, plan
+        t = target_or_plan
+        shp = self.shape if t.box is None else tuple(hi - lo for lo, hi in t.box)
+        if t.box is not None and len(t.box) != len(self.shape):
+            raise ValueError("box needs one (lo, hi) pair per axis")
         if out is None:
-            out = torch.empty(self.shape, dtype=self.dtype, device=self.device)
-        assert out.is_contiguous() and tuple(out.shape) == self.shape and out.dtype == self.dtype
-        _check(_lib.pcr_retrieve(self._p, C.byref(plan._c), C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
-        return out, plan
+            out = torch.empty(shp, dtype=self.dtype, device=self.device)
+        assert out.is_contiguous() and tuple(out.shape) == shp and out.dtype == self.dtype
+        info = _Info()
+        info.want_gpu_ms = 1 if gpu_time else 0
+        _check(_lib.pcr_retrieve(self._p, C.byref(t.c()), C.c_void_p(out.data_ptr()), _stream_ptr(stream),
+                                 C.byref(info)))
+        return out, RetrievalInfo.of(info)
+
+    def get_tables(self):
+        """pcr_get_tables: per stream exponent, maxerr[B+1], sq[B+1], bytes[B+1]."""
+        import numpy as np
+        t = _Tables()
+        _check(_lib.pcr_get_tables(self._p, C.byref(t)))
+        ns, B = t.nstreams, t.nplanes
+        me = np.zeros((ns, B + 1), np.float64)
+        sq = np.zeros((ns, B + 1), np.float64)
+        by = np.zeros((ns, B + 1), np.uint64)
+        t.maxerr = me.ctypes.data_as(C.POINTER(C.c_double))
+        t.sq = sq.ctypes.data_as(C.POINTER(C.c_double))
+        t.bytes = by.ctypes.data_as(C.POINTER(C.c_uint64))
+        _check(_lib.pcr_get_tables(self._p, C.byref(t)))
+        return dict(exponent=list(t.exponent[:ns]), maxerr=me, sq=sq, bytes=by)
 
     def retrieve_box(self, target_or_plan, box, out=None, stream=None):
         """Reconstruct only the box ((lo, hi) per axis) of the field: the same
@@ -495,12 +572,26 @@ def autotune_table(reset=False):
 
 
 def retrieve_batch(handles, plans, outs, stream=None):
+    """pcr_retrieve_batch_plan: one work list per stage for n (handle, plan,
+    output) triples."""
     n = len(handles)
     hp = (C.c_void_p * n)(*[h._p.value for h in handles])
     pl = (_Plan * n)(*[p._c for p in plans])
     op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
-    _check(_lib.pcr_retrieve_batch(n, hp, pl, op, _stream_ptr(stream)))
+    _check(_lib.pcr_retrieve_batch_plan(n, hp, pl, op, _stream_ptr(stream)))
     return outs
+
+
+def retrieve_batch_targets(handles, targets, outs, stream=None):
+    """pcr_retrieve_batch: each target planned, all retrieved with one work
+    list per stage.  Returns [RetrievalInfo]."""
+    n = len(handles)
+    hp = (C.c_void_p * n)(*[h._p.value for h in handles])
+    tg = (_Target * n)(*[t.c() for t in targets])
+    op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    infos = (_Info * n)()
+    _check(_lib.pcr_retrieve_batch(n, hp, tg, op, _stream_ptr(stream), infos))
+    return [RetrievalInfo.of(i) for i in infos]
 
 
 def deserialize(data: bytes, device=None, stream=None):

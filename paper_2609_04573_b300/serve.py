@@ -4,11 +4,11 @@ Refactored fields stay resident on the device (their handles own the plane
 streams).  Requests -- (field, target[, box]) -- arrive at any time; a worker
 thread admits them while the memory the in-flight retrievals need (output +
 scratch, from pcr_retrieve_scratch_bytes) stays under a budget, groups the
-admitted requests into one pcr_retrieve_batch call (one decode work list for
+admitted requests into one pcr_retrieve_batch_plan call (one decode work list for
 the whole group), and keeps up to `streams` groups on the GPU at once on
 separate CUDA streams.  Requests that arrive while groups are running join the
 next group as soon as memory frees up; results complete out of order through
-CUDA events.  Every result is the same field a single pcr_retrieve of that
+CUDA events.  Every result is the same field a single retrieval of that
 request produces (the kernels are deterministic and share no state between
 requests).
 

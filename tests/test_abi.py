@@ -17,11 +17,21 @@ def declared():
 
 
 def test_header_declares_the_boundary():
+    """The calls of the boundary: refactor (single, batched), plan, the
+    one-call retrieve(target) with its info, batched retrieve by target,
+    every stream's tables, the container, free, last error, and the test
+    entry that encodes given coefficients."""
     names = declared()
     for n in ["pcr_refactor", "pcr_refactor_batch", "pcr_plan", "pcr_retrieve",
-              "pcr_retrieve_batch", "pcr_serialize", "pcr_deserialize", "pcr_free",
-              "pcr_last_error", "pcr_debug_encode"]:
+              "pcr_retrieve_plan", "pcr_retrieve_batch", "pcr_retrieve_batch_plan", "pcr_get_tables",
+              "pcr_serialize", "pcr_deserialize", "pcr_free", "pcr_last_error", "pcr_debug_encode"]:
         assert n in names
+    src = open(os.path.join(ROOT, "include", "pcr.h")).read()
+    for token in ["PCR_MODE_EXPLICIT", "has_box", "pcr_retrieval_info", "pcr_tables",
+                  "PCR_ERR_UNSATISFIABLE", "PCR_ERR_TIMEOUT", "PCR_ERR_CORRUPT"]:
+        assert token in src, token
+    assert re.search(r"pcr_status pcr_retrieve\(const pcr_handle\* h, const pcr_target\* target, void\* d_out, "
+                     r"void\* cuda_stream,\s*pcr_retrieval_info\* info\)", src)
 
 
 def test_library_exports_every_declared_symbol():
