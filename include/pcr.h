@@ -49,7 +49,7 @@ typedef enum {
 
 enum { PCR_F32 = 0, PCR_F64 = 1 };
 enum { PCR_MODE_EB = 0, PCR_MODE_PSNR = 1, PCR_MODE_EXPLICIT = 2 };
-enum { PCR_INTERP_LEVEL = 0, PCR_INTERP_REGION = 1 };
+enum { PCR_INTERP_AUTO = -1, PCR_INTERP_LEVEL = 0, PCR_INTERP_REGION = 1 };
 enum { PCR_LINEAR = 1, PCR_CUBIC = 3 };
 enum { PCR_ENC_DEFAULT = 0, PCR_ENC_GENERIC = 1, PCR_ENC_NEGABINARY = 2 };
 enum { PCR_TARGET_ABS = 0, PCR_TARGET_REL = 1, PCR_TARGET_PSNR = 2 };
@@ -72,7 +72,11 @@ typedef struct {
  *               PCR_MODE_EXPLICIT: every field taken as given, exact integer
  *               squared-error tables kept, so the handle serves error-bound
  *               and PSNR targets alike (encoding default: generic).
- *   interp      per-level (pass order = natural axis order) or per-region.
+ *   interp      per-level (pass order = natural axis order) or per-region;
+ *               PCR_INTERP_AUTO: the target-driven tuner (pcr_tune, Sec. VI-A)
+ *               picks interp, order, decomposition axis and encoding for the
+ *               mode (EB or PSNR) from a sample of the field, then the field
+ *               is refactored with that choice (pcr_get_scheme reads it).
  *   degree      PCR_LINEAR or PCR_CUBIC.
  *   order       per-region pass order: a permutation of the field's axes
  *               (3-D: of 0,1,2; 2-D: of 0,1 in order[0..1]); ignored per-level.
@@ -246,6 +250,38 @@ void pcr_refactor_graph_free(pcr_refactor_graph* g);
  * time); *n_out = entries in the table; reset clears it afterwards. */
 pcr_status pcr_autotune_enable(int enable);
 pcr_status pcr_autotune_read(int max_entries, int64_t* keys, int* choice, double* ms, int* n_out, int reset);
+
+/* ---- target-driven sampled tuning (Sec. VI-A and its tuning table) ----
+ * Picks the scheme of `mode` (PCR_MODE_EB: per-level or per-region with each
+ * of the d! pass orders, decomposition off or along each axis, generic
+ * planes; PCR_MODE_PSNR: per-region only, negabinary + XOR; cubic) for the
+ * device field: whole blocks of min(edge, n)^d points sampled on a regular
+ * grid (at most `fraction` of the field, at least one block; 0 = defaults
+ * 0.01 and 64) are refactored with every candidate; at each of the 9
+ * tolerances tau = 1e-3, 5e-4, 1e-4, .., 1e-7 (relative to the field's
+ * range R) the candidate needing the fewest bytes gets a vote (EB: max error
+ * tau R in every block; PSNR: squared-error sum n_block (tau R)^2, i.e.
+ * RMSE tau R); most votes wins, ties to the earlier candidate.  Synchronises
+ * `cuda_stream`; temporary memory through `alloc`.  info (nullable) receives
+ * the candidates, votes and byte counts (UINT64_MAX: tolerance not met). */
+#define PCR_TUNE_NTOL 9
+#define PCR_TUNE_MAX_CANDIDATES 32
+typedef struct {
+  int ncand, winner;
+  pcr_scheme cand[PCR_TUNE_MAX_CANDIDATES];
+  int votes[PCR_TUNE_MAX_CANDIDATES];
+  uint64_t bytes[PCR_TUNE_MAX_CANDIDATES][PCR_TUNE_NTOL];
+  int nblocks;
+  int64_t block[3];      /* block edge per field axis (ndim entries) */
+  double fraction;       /* sampled points / field points */
+  double ms;             /* wall time of the call */
+} pcr_tune_info;
+pcr_status pcr_tune(const void* d_field, int ndim, const int64_t* dims, int dtype, int mode, double fraction,
+                    int edge, const pcr_allocator* alloc, void* cuda_stream, pcr_scheme* out,
+                    pcr_tune_info* info);
+/* The scheme a handle was refactored with (the tuner's choice for
+ * PCR_INTERP_AUTO requests). */
+pcr_status pcr_get_scheme(const pcr_handle* h, pcr_scheme* out);
 
 /* ---- plan (retrieval interpreter, Sec. V-C / VI-B) -------------------- */
 /* Host only.  Greedy selection of planes meeting `target`; returns

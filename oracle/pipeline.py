@@ -5,8 +5,12 @@ Test infrastructure only.
 Arithmetic (a reading; the paper runs FP64 data in FP64): level 0 and its
 coefficient decomposition run in the field's dtype; levels >= 1 (at most 1/8
 of the points, but their errors are amplified by up to Lam^(d l) on the way to
-level 0) run in exact 64-bit fixed point with quantum h = 2^(G - 40), where
-max|x| < 2^G.  The fixed-point value of x is floor(x / h).
+level 0) run in exact 64-bit fixed point with quantum h = 2^(G - F), where
+max|x| < 2^G and F = fix_bits(dtype, L): 40 for FP32 fields (far below FP32
+resolution), for FP64 fields 48, or 56 - L for deep hierarchies so that
+every reconstruction numerator keeps int64 headroom (values up to
+4.2 (Lam^d)^L 2^F, numerators up to 20 times that).  The fixed-point value of
+x is floor(x / h).
 """
 import math
 from dataclasses import dataclass
@@ -21,12 +25,17 @@ from .geometry import (active_axes, auto_levels, max_levels, build_geometry, cou
 from .interp import (decompose, level_points_mask, predict_level, recompose,
                      reconstruct_level)
 
-FIX_BITS = 40
+FIX_BITS_F32 = 40
+
+
+def fix_bits(dtag, L):
+    """Fraction bits F of the fixed point of levels >= 1."""
+    return FIX_BITS_F32 if dtag == "f32" else min(48, 56 - L)
 
 
 @dataclass
 class Scheme:
-    mode: str = "eb"             # "eb" | "psnr": which target the refactor serves
+    mode: str = "eb"             # "eb" | "psnr" | "explicit" (both tables, generic default)
     interp: str = "level"        # "level" | "region"
     degree: str = "cubic"        # "linear" | "cubic"
     order: Optional[Tuple[int, ...]] = None   # per-region pass order
@@ -46,17 +55,20 @@ def shape3_of(shape):
     return (1,) + tuple(shape) if len(shape) == 2 else tuple(shape)
 
 
-def fixed_scale(M):
+def fixed_scale(M, F=FIX_BITS_F32):
     G = math.frexp(M)[1] if M > 0 else 0
-    return G, math.ldexp(1.0, G - FIX_BITS)
+    return G, math.ldexp(1.0, G - F)
 
 
-def to_fixed(X, G):
-    return np.floor(np.ldexp(X.astype(np.float64), FIX_BITS - G)).astype(np.int64)
+def to_fixed(X, G, F=FIX_BITS_F32):
+    """floor(x 2^(F - G)), exactly (FP64 product of an exact power of two;
+    for FP64 inputs with F - G large enough to leave the FP64 range of exact
+    integers the product is still exact: scaling by 2^k never rounds)."""
+    return np.floor(np.ldexp(X.astype(np.float64), F - G)).astype(np.int64)
 
 
-def from_fixed(xi, G, dtype):
-    return (xi.astype(dtype) * dtype.type(math.ldexp(1.0, G - FIX_BITS))).astype(dtype)
+def from_fixed(xi, G, dtype, F=FIX_BITS_F32):
+    return (xi.astype(dtype) * dtype.type(math.ldexp(1.0, G - F))).astype(dtype)
 
 
 def _grid(shape3, s):
@@ -103,14 +115,16 @@ def refactor(X, scheme=Scheme(), trace=None):
     L = scheme.nlevels or auto_levels(shape3)
     assert 1 <= L <= max_levels(shape3)
     order = tuple(scheme.order) if (scheme.order and scheme.interp == "region") else act
-    encoding = scheme.encoding or ("generic" if scheme.mode == "eb" else "negabinary")
+    encoding = scheme.encoding or ("negabinary" if scheme.mode == "psnr" else "generic")
+    exact_sq = scheme.mode != "eb"       # exact integer squared-error tables
     dax = scheme.decomp_axis if (len(act) == 3 and L >= 2) else -1
     geo = build_geometry(shape3, L, scheme.interp, order, dax)
 
     # a1: field statistics (Sec. III-A: PSNR uses max - min)
     xmin, xmax = float(X3.min()), float(X3.max())
     M = max(abs(xmin), abs(xmax))
-    G, h = fixed_scale(M)
+    F = fix_bits(dtag, L)
+    G, h = fixed_scale(M, F)
 
     Ci = np.zeros(shape3, dtype=np.int64)
     Cf = np.zeros(shape3, dtype=dt)
@@ -118,7 +132,7 @@ def refactor(X, scheme=Scheme(), trace=None):
     if L == 1:
         Cf[...] = X3
     else:
-        Xi = to_fixed(X3, G)
+        Xi = to_fixed(X3, G, F)
         cl = coarse_lattice(shape3, L).slices()
         Ci[cl] = Xi[cl]
         for level in range(1, L - 1):                      # Alg. 1, l = 1..L-2
@@ -143,10 +157,9 @@ def refactor(X, scheme=Scheme(), trace=None):
     for s in geo.streams:
         src = Ci if s.is_int else (Df if s.sub > 0 else Cf)
         vals = _stream_values(s, src)
-        enc = bp.encode(vals, s.is_int, B, encoding, scheme.mode == "psnr")
+        enc = bp.encode(vals, s.is_int, B, encoding, exact_sq)
         nbytes = bp.stream_bytes(enc, B, s.words)
-        tab = bd.stream_tables(enc, s.n_real, s.is_int, B, encoding, h,
-                               scheme.mode == "psnr", nbytes)
+        tab = bd.stream_tables(enc, s.n_real, s.is_int, B, encoding, h, exact_sq, nbytes)
         streams.append(dict(level=s.level, region=s.region, sub=s.sub,
                             n_real=s.n_real, n_pad=s.n_pad, is_int=s.is_int,
                             enc=enc, tab=tab, geo=s))
@@ -163,7 +176,7 @@ def refactor(X, scheme=Scheme(), trace=None):
         if s["level"] == 0 and not s["is_int"]:
             C0 = max(C0, s["enc"]["quant"]["vmax"])
     meta = dict(L=L, d=len(order), degree=scheme.degree, interp=scheme.interp,
-                dtype=dtag, h=h, G=G, M=M, C0=C0, C0c=C0c, Dm=Dm, R=xmax - xmin, xmin=xmin,
+                dtype=dtag, h=h, G=G, F=F, M=M, C0=C0, C0c=C0c, Dm=Dm, R=xmax - xmin, xmin=xmin,
                 xmax=xmax, n=X3.size, B=B, encoding=encoding, order=order,
                 decomp_axis=dax, shape3=shape3, shape=X.shape, mode=scheme.mode)
     _add_factors(meta, geo)
@@ -265,7 +278,7 @@ def retrieve(handle, target_or_plan, trace=None):
         reconstruct_level(Gs, order, meta["interp"], meta["degree"])
     Xr = np.zeros(shape3, dtype=dt)
     g2 = _grid(shape3, 2)
-    Xr[g2] = from_fixed(Xi[g2], meta["G"], dt)
+    Xr[g2] = from_fixed(Xi[g2], meta["G"], dt, meta["F"])
     mask = level_points_mask(shape3, order)
     Xr[mask] = Cf[mask]
     reconstruct_level(Xr, order, meta["interp"], meta["degree"])

@@ -69,6 +69,15 @@ class _Plan(C.Structure):
                 ("psnr_bound", C.c_double), ("bytes", C.c_uint64), ("satisfied", C.c_int)]
 
 
+TUNE_NTOL, TUNE_MAX = 9, 32
+
+
+class _TuneInfo(C.Structure):
+    _fields_ = [("ncand", C.c_int), ("winner", C.c_int), ("cand", _Scheme * TUNE_MAX), ("votes", C.c_int * TUNE_MAX),
+                ("bytes", (C.c_uint64 * TUNE_NTOL) * TUNE_MAX), ("nblocks", C.c_int), ("block", C.c_int64 * 3),
+                ("fraction", C.c_double), ("ms", C.c_double)]
+
+
 class _StreamInfo(C.Structure):
     _fields_ = [("level", C.c_int), ("region", C.c_int), ("sub", C.c_int), ("is_fixed", C.c_int),
                 ("nplanes", C.c_int), ("n_real", C.c_int64), ("n_pad", C.c_int64),
@@ -99,6 +108,9 @@ _sigs = {
                            C.POINTER(_Info)],
     "pcr_retrieve_batch_plan": [C.c_int, C.POINTER(_vp), C.POINTER(_Plan), C.POINTER(_vp), _vp],
     "pcr_get_tables": [_vp, C.POINTER(_Tables)],
+    "pcr_tune": [_vp, C.c_int, _i64p, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(_Allocator), _vp,
+                 C.POINTER(_Scheme), C.POINTER(_TuneInfo)],
+    "pcr_get_scheme": [_vp, C.POINTER(_Scheme)],
     "pcr_retrieve_static": [_vp, C.POINTER(_Plan), _vp, _vp],
     "pcr_retrieve_box": [_vp, C.POINTER(_Plan), _i64p, _i64p, _vp, _vp],
     "pcr_retrieve_scratch_bytes": [_vp, C.POINTER(C.c_size_t)],
@@ -178,7 +190,7 @@ _FREE_CB = _FREE_FN(_torch_free)
 _ALLOCATOR = _Allocator(None, _ALLOC_CB, _FREE_CB)
 
 EB, PSNR, EXPLICIT = 0, 1, 2
-LEVEL, REGION = 0, 1
+AUTO, LEVEL, REGION = -1, 0, 1
 LINEAR, CUBIC = 1, 3
 GENERIC, NEGABINARY = 1, 2
 _DT = {torch.float32: 0, torch.float64: 1}
@@ -188,7 +200,7 @@ _DT = {torch.float32: 0, torch.float64: 1}
 class Scheme:
     """Refactoring scheme (Sec. IV-VI, tuning table of Sec. VI-A)."""
     mode: str = "eb"                 # "eb" | "psnr" | "explicit"
-    interp: str = "level"            # "level" | "region"
+    interp: str = "level"            # "level" | "region" | "auto" (sampled tuner)
     degree: str = "cubic"            # "linear" | "cubic"
     order: Optional[Tuple[int, ...]] = None
     decomp_axis: int = -1
@@ -208,7 +220,7 @@ class Scheme:
     def c(self, ndim):
         s = _Scheme()
         s.mode = {"eb": EB, "psnr": PSNR, "explicit": EXPLICIT}[self.mode]
-        s.interp = REGION if self.interp == "region" else LEVEL
+        s.interp = {"level": LEVEL, "region": REGION, "auto": AUTO}[self.interp]
         s.degree = CUBIC if self.degree == "cubic" else LINEAR
         order = self.order or tuple(range(ndim))
         for i in range(3):
@@ -218,6 +230,17 @@ class Scheme:
         s.nlevels = self.nlevels
         s.nplanes = self.nplanes
         return s
+
+
+    @classmethod
+    def of(cls, s, ndim):
+        """Scheme of a pcr_scheme (pass orders in user axes)."""
+        interp = {LEVEL: "level", REGION: "region"}[s.interp]
+        order = tuple(s.order[:ndim]) if interp == "region" else None
+        enc = {GENERIC: "generic", NEGABINARY: "negabinary"}.get(s.encoding)
+        mode = {EB: "eb", PSNR: "psnr", EXPLICIT: "explicit"}[s.mode]
+        return cls(mode=mode, interp=interp, degree="cubic" if s.degree == CUBIC else "linear", order=order,
+                   decomp_axis=s.decomp_axis, encoding=enc, nlevels=s.nlevels, nplanes=s.nplanes)
 
 
 @dataclass
@@ -373,6 +396,12 @@ class Handle:
                                  C.byref(info)))
         return out, RetrievalInfo.of(info)
 
+    def scheme(self):
+        """pcr_get_scheme: the scheme this handle was refactored with."""
+        sc = _Scheme()
+        _check(_lib.pcr_get_scheme(self._p, C.byref(sc)))
+        return Scheme.of(sc, len(self.shape))
+
     def get_tables(self):
         """pcr_get_tables: per stream exponent, maxerr[B+1], sq[B+1], bytes[B+1]."""
         import numpy as np
@@ -433,6 +462,26 @@ class Handle:
         data = C.string_at(buf, n.value)
         _lib.pcr_buffer_free(buf)
         return data
+
+
+def tune(x, mode="eb", fraction=0.0, edge=0, stream=None):
+    """pcr_tune: the target-driven sampled tuner's scheme for x (Sec. VI-A).
+    Returns (Scheme, info dict: candidates, votes, bytes per tolerance (None:
+    not met), blocks, block edge, sampled fraction, ms)."""
+    if not (x.is_cuda and x.is_contiguous() and x.dtype in _DT and x.dim() in (2, 3)):
+        raise ValueError("tune expects a contiguous 2-D/3-D float32/float64 CUDA tensor")
+    dims = (C.c_int64 * x.dim())(*x.shape)
+    out, info = _Scheme(), _TuneInfo()
+    _check(_lib.pcr_tune(C.c_void_p(x.data_ptr()), x.dim(), dims, _DT[x.dtype], {"eb": EB, "psnr": PSNR}[mode],
+                         float(fraction), int(edge), C.byref(_ALLOCATOR), _stream_ptr(stream), C.byref(out),
+                         C.byref(info)))
+    nd = x.dim()
+    cands = [Scheme.of(info.cand[c], nd) for c in range(info.ncand)]
+    table = [[None if info.bytes[c][t] == (1 << 64) - 1 else int(info.bytes[c][t]) for t in range(TUNE_NTOL)]
+             for c in range(info.ncand)]
+    return Scheme.of(out, nd), dict(candidates=cands, votes=list(info.votes[:info.ncand]), bytes=table,
+                                    winner=info.winner, nblocks=info.nblocks, block=tuple(info.block[:nd]),
+                                    fraction=info.fraction, ms=info.ms)
 
 
 def refactor(x, scheme=None, stream=None):

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -876,6 +878,14 @@ struct pcr_handle {
   }
 };
 
+// exact integer squared-error tables (plane pair counts) are kept for PSNR
+// and explicit schemes; error-bound schemes use n maxerr^2
+static bool keeps_pairs(const pcr_handle* h) { return h->sch.mode != PCR_MODE_EB; }
+
+static pcr_status resolve_auto(int n, const void* const* d_fields, const int* ndims, const int64_t* const* dims,
+                               const int* dtypes, const pcr_scheme* schemes, const pcr_allocator* alloc,
+                               void* cuda_stream, std::vector<pcr_scheme>& out);
+
 namespace {
 
 LatD to_latd(const Lat& l, int64_t base) {
@@ -901,6 +911,7 @@ FieldD field_desc(const pcr_handle* h) {
   f.interp = h->sch.interp;
   f.degree = h->sch.degree;
   f.L = h->L;
+  f.fixb = fix_bits(h->vk, h->L);
   return f;
 }
 
@@ -1550,7 +1561,8 @@ static pcr_status validate(const void* d_field, int ndim, const int64_t* dims, i
   for (int i = 0; i < ndim; i++)
     if (dims[i] < 2) return fail(PCR_ERR_INVALID_ARG, "every dimension must be >= 2");
   if (dtype != PCR_F32 && dtype != PCR_F64) return fail(PCR_ERR_INVALID_ARG, "dtype must be PCR_F32 or PCR_F64");
-  if (sch->mode != PCR_MODE_EB && sch->mode != PCR_MODE_PSNR) return fail(PCR_ERR_INVALID_ARG, "bad mode");
+  if (sch->mode != PCR_MODE_EB && sch->mode != PCR_MODE_PSNR && sch->mode != PCR_MODE_EXPLICIT)
+    return fail(PCR_ERR_INVALID_ARG, "bad mode");
   if (sch->interp != 0 && sch->interp != 1) return fail(PCR_ERR_INVALID_ARG, "bad interp");
   if (sch->degree != 1 && sch->degree != 3) return fail(PCR_ERR_INVALID_ARG, "degree must be 1 or 3");
   if (sch->encoding < 0 || sch->encoding > 2) return fail(PCR_ERR_INVALID_ARG, "bad encoding");
@@ -1592,7 +1604,7 @@ static pcr_status setup_handle(pcr_handle* h, int ndim, const int64_t* dims, int
   if (h->B < 1 || h->B > Bmax) return fail(PCR_ERR_INVALID_ARG, "nplanes out of range");
   h->L = sch->nlevels ? sch->nlevels : auto_levels(h->n3);
   if (h->L < 1 || h->L > max_levels(h->n3)) return fail(PCR_ERR_INVALID_ARG, "nlevels out of range");
-  h->enc = sch->encoding == PCR_ENC_DEFAULT ? (sch->mode == PCR_MODE_EB ? 1 : 2) : sch->encoding;
+  h->enc = sch->encoding == PCR_ENC_DEFAULT ? (sch->mode == PCR_MODE_PSNR ? 2 : 1) : sch->encoding;
   if (sch->decomp_axis < -1 || sch->decomp_axis > 2) return fail(PCR_ERR_INVALID_ARG, "decomp_axis must be -1..2");
   h->decomp = (d == 3 && h->L >= 2) ? sch->decomp_axis : -1;
   h->geo = build_streams(h->n3, h->L, sch->interp, h->order, h->decomp);
@@ -1771,7 +1783,7 @@ static pcr_status finish_refactor(pcr_handle* h, const FieldStats& st, const std
   h->xmax = inv(st.xmax_key);
   h->M = std::max(std::fabs(h->xmin), std::fabs(h->xmax));
   h->G = st.G;
-  h->h = std::ldexp(1.0, h->G - kFixBits);
+  h->h = std::ldexp(1.0, h->G - fix_bits(h->vk, h->L));
   const int ns = (int)h->geo.size();
   h->E.assign(ns, 0);
   h->sh.assign(ns, 0);
@@ -1814,7 +1826,7 @@ static pcr_status finish_refactor(pcr_handle* h, const FieldStats& st, const std
     h->sign_words[i].assign(nz.begin() + h->nz_off[i] + h->B, nz.begin() + h->nz_off[i] + 2 * h->B);
     if (pairs) h->pairs[i].assign(pairs->begin() + (size_t)i * h->B * h->B, pairs->begin() + (size_t)(i + 1) * h->B * h->B);
   }
-  for (int i = 0; i < ns; i++) compute_tables(h, i, pairs ? &h->pairs[i] : nullptr, h->sch.mode == PCR_MODE_PSNR);
+  for (int i = 0; i < ns; i++) compute_tables(h, i, pairs ? &h->pairs[i] : nullptr, keeps_pairs(h));
   build_meta(h);
   return PCR_OK;
 }
@@ -1867,7 +1879,7 @@ struct BatchLayout {
       vm_off.push_back(nv);
       nv += h->geo.size();
       pr_off.push_back(npairs);
-      if (h->sch.mode == PCR_MODE_PSNR) npairs += h->geo.size() * h->B * h->B;
+      if (keeps_pairs(h)) npairs += h->geo.size() * h->B * h->B;
       nz_off.push_back(nnz);
       nnz += h->nz_words;
     }
@@ -1933,13 +1945,13 @@ static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* 
     pcr_handle* h = hs[k];
     std::vector<StreamD> sds(h->geo.size());
     pcr_status e = enqueue_refactor(h, d_fields[k], s, sc, d_st + k, d_vm + L.vm_off[k],
-                                    h->sch.mode == PCR_MODE_PSNR ? d_pairs + L.pr_off[k] : nullptr, sds);
+                                    keeps_pairs(h) ? d_pairs + L.pr_off[k] : nullptr, sds);
     if (e) return e;
     for (size_t i = 0; i < sds.size(); i++) {
       const int idx = (int)all.size();
       all.push_back(sds[i]);
       const int fx = sds[i].is_fix;
-      const int pm = h->sch.mode == PCR_MODE_PSNR;
+      const int pm = keeps_pairs(h);
       if (pairs_mode[h->w64][fx] < 0) pairs_mode[h->w64][fx] = pm;
       else if (pairs_mode[h->w64][fx] != pm) return fail(PCR_ERR_UNSUPPORTED, "mixed EB/PSNR modes in one batch");
       for (int64_t g = 0; g < sds[i].nseg; g++) items[h->w64][fx].push_back({idx, (int)g});
@@ -2028,9 +2040,9 @@ static pcr_status finish_batch(const std::vector<pcr_handle*>& hs, const BatchLa
     std::vector<unsigned long long> v(io.vm + L.vm_off[k], io.vm + L.vm_off[k] + h->geo.size());
     std::vector<uint32_t> nz(io.nz + L.nz_off[k], io.nz + L.nz_off[k] + h->nz_words);
     std::vector<uint64_t> pk;
-    if (h->sch.mode == PCR_MODE_PSNR)
+    if (keeps_pairs(h))
       pk.assign(io.pairs + L.pr_off[k], io.pairs + L.pr_off[k] + h->geo.size() * h->B * h->B);
-    pcr_status e = finish_refactor(h, io.st[k], v, nz, h->sch.mode == PCR_MODE_PSNR ? &pk : nullptr);
+    pcr_status e = finish_refactor(h, io.st[k], v, nz, keeps_pairs(h) ? &pk : nullptr);
     if (e) return e;
     std::lock_guard<std::mutex> lk(h->plan_mu);   // planner units follow the new tables
     h->units_ok[0] = h->units_ok[1] = false;
@@ -2070,7 +2082,7 @@ static size_t refactor_scratch_bytes(const pcr_handle* h) {
   const size_t ns = h->geo.size();
   size_t t = al(fix * 8) + al(flt * w) + al(ns * sizeof(StreamD)) + al(std::max<size_t>(items, 1) * sizeof(WorkItem)) +
              al(sizeof(FieldStats)) + al(ns * 8);
-  if (h->sch.mode == PCR_MODE_PSNR) t += al(ns * h->B * h->B * 8);
+  if (keeps_pairs(h)) t += al(ns * h->B * h->B * 8);
   if (h->L >= 2) {
     size_t nc = 1;
     for (int a = 0; a < 3; a++) nc *= h->n3[a] > 1 ? (h->n3[a] - 1) / 2 + 1 : 1;
@@ -2106,8 +2118,11 @@ extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, con
     return fail(PCR_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   Mem mem = make_mem(alloc);
+  std::vector<pcr_scheme> sch;
+  pcr_status e = resolve_auto(n, d_fields, ndims, dims, dtypes, schemes, alloc, cuda_stream, sch);
+  if (e) return e;
   std::vector<std::unique_ptr<pcr_handle>> own;
-  pcr_status e = make_batch_handles(n, d_fields, ndims, dims, dtypes, schemes, mem, s, own);
+  e = make_batch_handles(n, d_fields, ndims, dims, dtypes, sch.data(), mem, s, own);
   if (e) return e;
   std::vector<pcr_handle*> hs;
   for (auto& h : own) hs.push_back(h.get());
@@ -2198,8 +2213,11 @@ extern "C" pcr_status pcr_refactor_begin(const void* d_field, int ndim, const in
   const int nd[1] = {ndim};
   const int64_t* dm[1] = {dims};
   const int dt[1] = {dtype};
+  std::vector<pcr_scheme> sch;
+  pcr_status e = resolve_auto(1, f, nd, dm, dt, scheme, alloc, cuda_stream, sch);
+  if (e) return e;
   std::vector<std::unique_ptr<pcr_handle>> own;
-  pcr_status e = make_batch_handles(1, f, nd, dm, dt, scheme, j->mem, j->s, own);
+  e = make_batch_handles(1, f, nd, dm, dt, sch.data(), j->mem, j->s, own);
   if (e) return e;
   j->own = std::move(own[0]);
   j->hs.push_back(j->own.get());
@@ -2283,7 +2301,10 @@ extern "C" pcr_status pcr_refactor_graph_create(int n, const void* const* d_fiel
   cudaStream_t s = (cudaStream_t)cuda_stream;
   std::unique_ptr<pcr_refactor_graph> g(new pcr_refactor_graph());
   g->mem = make_mem(alloc);
-  pcr_status e = make_batch_handles(n, d_fields, ndims, dims, dtypes, schemes, g->mem, s, g->own);
+  std::vector<pcr_scheme> sch;
+  pcr_status e = resolve_auto(n, d_fields, ndims, dims, dtypes, schemes, alloc, cuda_stream, sch);
+  if (e) return e;
+  e = make_batch_handles(n, d_fields, ndims, dims, dtypes, sch.data(), g->mem, s, g->own);
   if (e) return e;
   for (auto& h : g->own) g->hs.push_back(h.get());
   g->fields.assign(d_fields, d_fields + n);
@@ -2526,7 +2547,7 @@ static pcr_status enqueue_reconstruct(const pcr_handle* h, const std::vector<Str
   }
   {
     Prof pf("coarse_out", s);
-    launch_coarse_out(h->vk, f, xc, std::ldexp(1.0, h->G - kFixBits), d_out, s);
+    launch_coarse_out(h->vk, f, xc, std::ldexp(1.0, h->G - fix_bits(h->vk, h->L)), d_out, s);
   }
   // level 0
   TileArgs a = level_args(h, 0, 1, d_out, d_out);
@@ -2738,7 +2759,7 @@ static pcr_status enqueue_reconstruct_box(const pcr_handle* h, const std::vector
       cb.cnt[k] = std::max<int64_t>(0, hi[k] - lo[k]);
     }
     Prof pf("coarse_out", s);
-    launch_coarse_out(h->vk, f, xc, std::ldexp(1.0, h->G - kFixBits), d_full, s, &cb);
+    launch_coarse_out(h->vk, f, xc, std::ldexp(1.0, h->G - fix_bits(h->vk, h->L)), d_full, s, &cb);
   }
   TileArgs a = level_args(h, 0, 1, d_full, d_full);
   if (h->decomp >= 0) {
@@ -2826,8 +2847,8 @@ extern "C" pcr_status pcr_retrieve_box(const pcr_handle* h, const pcr_retrieval_
 
 static size_t retrieve_scratch_bytes(const pcr_handle* h);
 
-extern "C" pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
-                                         void* const* d_outs, void* cuda_stream) {
+extern "C" pcr_status pcr_retrieve_batch_plan(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
+                                              void* const* d_outs, void* cuda_stream) {
   if (n <= 0 || !hs || !plans || !d_outs) return fail(PCR_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   for (int k = 0; k < n; k++)
@@ -2901,9 +2922,124 @@ extern "C" pcr_status pcr_retrieve_static(const pcr_handle* h, const pcr_retriev
   return retrieve_batch_impl(1, &h, plan, &d_out, s, sc);
 }
 
-extern "C" pcr_status pcr_retrieve(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out, void* cuda_stream) {
+extern "C" pcr_status pcr_retrieve_plan(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out,
+                                        void* cuda_stream) {
   if (!h || !plan || !d_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
-  return pcr_retrieve_batch(1, &h, plan, &d_out, cuda_stream);
+  return pcr_retrieve_batch_plan(1, &h, plan, &d_out, cuda_stream);
+}
+
+// ---------------------------------------------------------------------------
+// one-call retrieval: plan + retrieve (Sec. III-A problem statement)
+// ---------------------------------------------------------------------------
+namespace {
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+int64_t out_points(const pcr_handle* h, const pcr_target* t) {
+  int64_t n = 1;
+  for (int k = 0; k < h->ndim; k++) n *= t->has_box ? (t->hi[k] - t->lo[k]) : h->dims[k];
+  return n;
+}
+
+void fill_info(const pcr_handle* h, const pcr_target* t, const pcr_retrieval_plan& p, double plan_ms,
+               pcr_retrieval_info* info) {
+  const int want = info->want_gpu_ms;
+  std::memset(info, 0, sizeof(*info));
+  info->want_gpu_ms = want;
+  info->nstreams = p.nstreams;
+  for (int i = 0; i < p.nstreams; i++) info->planes[i] = p.planes[i];
+  info->bytes = p.bytes;
+  const int64_t n = out_points(h, t);
+  info->bits_per_value = n > 0 ? 8.0 * (double)p.bytes / (double)n : 0.0;
+  info->bound = p.bound;
+  info->psnr_bound = p.psnr_bound;
+  info->satisfied = p.satisfied;
+  info->plan_ms = plan_ms;
+  info->gpu_ms = -1.0;
+}
+}  // namespace
+
+extern "C" pcr_status pcr_retrieve(const pcr_handle* h, const pcr_target* target, void* d_out, void* cuda_stream,
+                                   pcr_retrieval_info* info) {
+  if (!h || !target || !d_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  if (target->has_box) {
+    for (int k = 0; k < h->ndim; k++)
+      if (target->lo[k] < 0 || target->hi[k] > h->dims[k] || target->lo[k] >= target->hi[k])
+        return fail(PCR_ERR_INVALID_ARG, "box outside the field");
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  pcr_retrieval_plan p{};
+  const pcr_status ps = pcr_plan(h, target, &p);
+  const double plan_ms = ms_since(t0);
+  if (info) fill_info(h, target, p, plan_ms, info);
+  if (ps != PCR_OK) return ps;   // unsatisfiable: nothing enqueued, info filled
+  const bool timed = info && info->want_gpu_ms;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (timed) {
+    CUDA_TRY(cudaEventCreate(&ev[0]));
+    CUDA_TRY(cudaEventCreate(&ev[1]));
+    CUDA_TRY(cudaEventRecord(ev[0], s));
+  }
+  const auto t1 = std::chrono::steady_clock::now();
+  const pcr_status st = target->has_box ? pcr_retrieve_box(h, &p, target->lo, target->hi, d_out, cuda_stream)
+                                        : pcr_retrieve_plan(h, &p, d_out, cuda_stream);
+  if (info) info->enqueue_ms = ms_since(t1);
+  if (timed) {
+    float ms = -1.0f;
+    if (st == PCR_OK && cudaEventRecord(ev[1], s) == cudaSuccess && cudaEventSynchronize(ev[1]) == cudaSuccess)
+      cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    info->gpu_ms = ms;
+  }
+  return st;
+}
+
+extern "C" pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_target* targets,
+                                         void* const* d_outs, void* cuda_stream, pcr_retrieval_info* infos) {
+  if (n <= 0 || !hs || !targets || !d_outs) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  std::vector<pcr_retrieval_plan> plans(n);
+  for (int k = 0; k < n; k++) {
+    if (!hs[k]) return fail(PCR_ERR_INVALID_ARG, "null handle");
+    if (targets[k].has_box) return fail(PCR_ERR_UNSUPPORTED, "box targets go through pcr_retrieve");
+    const auto t0 = std::chrono::steady_clock::now();
+    const pcr_status ps = pcr_plan(hs[k], &targets[k], &plans[k]);
+    if (infos) {
+      infos[k].want_gpu_ms = 0;
+      fill_info(hs[k], &targets[k], plans[k], ms_since(t0), &infos[k]);
+    }
+    if (ps != PCR_OK) return ps;
+  }
+  const auto t1 = std::chrono::steady_clock::now();
+  const pcr_status st = pcr_retrieve_batch_plan(n, hs, plans.data(), d_outs, cuda_stream);
+  if (infos) {
+    const double e = ms_since(t1);
+    for (int k = 0; k < n; k++) infos[k].enqueue_ms = e;
+  }
+  return st;
+}
+
+// ---------------------------------------------------------------------------
+// error tables of every stream (Sec. V-C)
+// ---------------------------------------------------------------------------
+extern "C" pcr_status pcr_get_tables(const pcr_handle* h, pcr_tables* out) {
+  if (!h || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  const int ns = (int)h->geo.size();
+  out->nstreams = ns;
+  out->nplanes = h->B;
+  for (int i = 0; i < PCR_MAX_STREAMS; i++) out->exponent[i] = i < ns ? h->E[i] : 0;
+  for (int i = 0; i < ns; i++) {
+    const Tab& t = h->tabs[i];
+    const size_t o = (size_t)i * (h->B + 1);
+    for (int b = 0; b <= h->B; b++) {
+      if (out->maxerr) out->maxerr[o + b] = t.maxerr[b];
+      if (out->sq) out->sq[o + b] = t.sq[b];
+      if (out->bytes) out->bytes[o + b] = t.bytes[b];
+    }
+  }
+  return PCR_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -3123,7 +3259,7 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
   h->C0 = hr.get<double>();
   h->C0c = hr.get<double>();
   h->M = std::max(std::fabs(h->xmin), std::fabs(h->xmax));
-  h->h = std::ldexp(1.0, h->G - kFixBits);
+  h->h = std::ldexp(1.0, h->G - fix_bits(h->vk, h->L));
   const int ns = (int)h->geo.size();
   h->vmax.resize(ns);
   h->E.resize(ns);
@@ -3174,9 +3310,239 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
   CUDA_TRY(cudaMemcpyAsync(h->d_nz, nz.data(), nz.size() * 4, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   for (int i = 0; i < ns; i++)
-    compute_tables(h.get(), i, h->pairs[i].empty() ? nullptr : &h->pairs[i], h->sch.mode == PCR_MODE_PSNR);
+    compute_tables(h.get(), i, h->pairs[i].empty() ? nullptr : &h->pairs[i], keeps_pairs(h.get()));
   build_meta(h.get());
   *out = h.release();
+  return PCR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// target-driven sampled tuning (Sec. VI-A and its tuning table)
+// ---------------------------------------------------------------------------
+// Sample: whole blocks of b^D points (b = min(edge, n) per axis) centred on a
+// regular k_0 x .. x k_(D-1) grid, the counts grown one axis at a time (the
+// axis with the most points per block slot first) while the blocks stay
+// within `fraction` of the field, at least one block; each block refactored
+// as a field of its own with every candidate; at each of 9 tolerances tau
+// (relative to the whole field's range R) the candidate needing the fewest
+// bytes over all blocks gets a vote (error-bound mode: max |x - x'| <= tau R
+// per block; PSNR mode: squared errors <= n_block (tau R)^2 per block); a
+// candidate unable to meet tau in some block takes no part in that vote;
+// ties go to the earlier candidate.
+namespace {
+const double kTuneTol[PCR_TUNE_NTOL] = {1e-3, 5e-4, 1e-4, 5e-5, 1e-5, 5e-6, 1e-6, 5e-7, 1e-7};
+
+std::vector<pcr_scheme> tune_candidates(int mode, int ndim) {
+  std::vector<std::array<int, 3>> orders;
+  std::array<int, 3> o = {0, 1, 2};
+  const int d = ndim == 3 ? 3 : 2;
+  do {
+    orders.push_back(o);
+  } while (std::next_permutation(o.begin(), o.begin() + d));
+  std::vector<int> decomps = ndim == 3 ? std::vector<int>{-1, 0, 1, 2} : std::vector<int>{-1};
+  std::vector<std::pair<int, std::array<int, 3>>> interps;
+  if (mode == PCR_MODE_EB) interps.push_back({PCR_INTERP_LEVEL, {0, 1, 2}});
+  for (auto& od : orders) interps.push_back({PCR_INTERP_REGION, od});
+  std::vector<pcr_scheme> out;
+  for (auto& it : interps)
+    for (int dax : decomps) {
+      pcr_scheme c{};
+      c.mode = mode;
+      c.interp = it.first;
+      c.degree = PCR_CUBIC;
+      for (int k = 0; k < 3; k++) c.order[k] = it.second[k];
+      c.decomp_axis = dax;
+      c.encoding = mode == PCR_MODE_PSNR ? PCR_ENC_NEGABINARY : PCR_ENC_GENERIC;
+      out.push_back(c);
+    }
+  return out;
+}
+
+void tune_blocks(const int64_t* dims, int ndim, double fraction, int edge, std::vector<std::array<int64_t, 3>>& org,
+                 int64_t* b) {
+  int64_t k[3] = {1, 1, 1};
+  int64_t N = 1, per = 1;
+  for (int d = 0; d < ndim; d++) {
+    b[d] = std::min<int64_t>(edge, dims[d]);
+    N *= dims[d];
+    per *= b[d];
+  }
+  while (true) {
+    int best = -1;
+    for (int d = 0; d < ndim; d++) {
+      const double r = (double)dims[d] / (double)(k[d] + 1), rb = best < 0 ? 0.0 : (double)dims[best] / (double)(k[best] + 1);
+      if ((k[d] + 1) * b[d] <= dims[d] && (best < 0 || r > rb)) best = d;
+    }
+    if (best < 0) break;
+    int64_t tot = per;
+    for (int d = 0; d < ndim; d++) tot *= d == best ? k[d] + 1 : k[d];
+    if ((double)tot > fraction * (double)N) break;
+    k[best]++;
+  }
+  org.clear();
+  int64_t idx[3] = {0, 0, 0};
+  const int64_t nb = k[0] * (ndim > 1 ? k[1] : 1) * (ndim > 2 ? k[2] : 1);
+  for (int64_t t = 0; t < nb; t++) {
+    int64_t r = t;
+    for (int d = ndim - 1; d >= 0; d--) {
+      idx[d] = r % k[d];
+      r /= k[d];
+    }
+    std::array<int64_t, 3> o = {0, 0, 0};
+    for (int d = 0; d < ndim; d++) {
+      const int64_t c = ((2 * idx[d] + 1) * dims[d]) / (2 * k[d]);
+      o[d] = std::min(std::max<int64_t>(c - b[d] / 2, 0), dims[d] - b[d]);
+    }
+    org.push_back(o);
+  }
+}
+
+double key_to_double(unsigned long long k) {
+  unsigned long long u = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  double d;
+  std::memcpy(&d, &u, 8);
+  return d;
+}
+}  // namespace
+
+extern "C" pcr_status pcr_tune(const void* d_field, int ndim, const int64_t* dims, int dtype, int mode, double fraction,
+                               int edge, const pcr_allocator* alloc, void* cuda_stream, pcr_scheme* out,
+                               pcr_tune_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!d_field || !dims || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  if (ndim != 2 && ndim != 3) return fail(PCR_ERR_INVALID_ARG, "ndim must be 2 or 3");
+  if (mode != PCR_MODE_EB && mode != PCR_MODE_PSNR) return fail(PCR_ERR_INVALID_ARG, "tuning needs EB or PSNR mode");
+  if (dtype != PCR_F32 && dtype != PCR_F64) return fail(PCR_ERR_INVALID_ARG, "bad dtype");
+  for (int d = 0; d < ndim; d++)
+    if (dims[d] < 2) return fail(PCR_ERR_INVALID_ARG, "every dimension must be >= 2");
+  if (fraction <= 0) fraction = 0.01;
+  if (edge <= 0) edge = 64;
+  if (edge < 4) return fail(PCR_ERR_INVALID_ARG, "block edge must be >= 4");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Mem mem = make_mem(alloc);
+  const int vk = dtype == PCR_F64 ? VK_F64 : VK_F32;
+  const size_t w = vsize(vk);
+  int64_t n3[3] = {1, 1, 1};
+  for (int d = 0; d < ndim; d++) n3[3 - ndim + d] = dims[d];
+  const int64_t n = n3[0] * n3[1] * n3[2];
+  // the whole field's range
+  std::vector<std::array<int64_t, 3>> org;
+  int64_t b[3] = {1, 1, 1};
+  tune_blocks(dims, ndim, fraction, edge, org, b);
+  int64_t bsz = 1;
+  for (int d = 0; d < ndim; d++) bsz *= b[d];
+  Scratch sc{&mem, s, {}};
+  FieldStats* d_st = (FieldStats*)sc.get(sizeof(FieldStats));
+  char* d_blocks = (char*)sc.get(org.size() * bsz * w);
+  if (!d_st || !d_blocks) return fail(PCR_ERR_OOM, "tuning allocation failed");
+  FieldStats st0{};
+  st0.xmin_key = ~0ull;
+  CUDA_TRY(cudaMemcpyAsync(d_st, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
+  launch_minmax(vk, d_field, n, d_st, s);
+  FieldD f{};
+  for (int a = 0; a < 3; a++) f.n[a] = n3[a];
+  for (size_t k = 0; k < org.size(); k++) {
+    Box3 bx;
+    for (int a = 0; a < 3; a++) {
+      const int d = a - (3 - ndim);
+      bx.lo[a] = d >= 0 ? org[k][d] : 0;
+      bx.cnt[a] = d >= 0 ? b[d] : 1;
+    }
+    launch_copy_box(vk, f, d_field, d_blocks + k * bsz * w, bx, s);
+  }
+  FieldStats st;
+  CUDA_TRY(cudaMemcpyAsync(&st, d_st, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (st.bad) return fail(PCR_ERR_INVALID_ARG, "field contains NaN or Inf");
+  const double R = key_to_double(st.xmax_key) - key_to_double(st.xmin_key);
+  const std::vector<pcr_scheme> cands = tune_candidates(mode, ndim);
+  const int nc = (int)cands.size(), nb = (int)org.size();
+  std::vector<const void*> ptrs(nb);
+  std::vector<int> nds(nb, ndim), dts(nb, dtype);
+  std::vector<const int64_t*> dms(nb, b);
+  for (int k = 0; k < nb; k++) ptrs[k] = d_blocks + k * bsz * w;
+  const uint64_t kNone = ~uint64_t(0);
+  std::vector<std::array<uint64_t, PCR_TUNE_NTOL>> table(nc);
+  for (int c = 0; c < nc; c++) {
+    std::vector<pcr_scheme> sch(nb, cands[c]);
+    std::vector<pcr_handle*> hs(nb, nullptr);
+    pcr_status e = pcr_refactor_batch(nb, ptrs.data(), nds.data(), dms.data(), dts.data(), sch.data(), alloc,
+                                      cuda_stream, hs.data());
+    if (e) return e;
+    std::vector<std::unique_ptr<pcr_handle>> own(nb);
+    for (int k = 0; k < nb; k++) own[k].reset(hs[k]);
+    for (int t = 0; t < PCR_TUNE_NTOL; t++) {
+      const double tau = kTuneTol[t] * R;
+      uint64_t tot = 0;
+      for (int k = 0; k < nb && tot != kNone; k++) {
+        std::vector<int> bv;
+        double bound = 0;
+        const bool ok = mode == PCR_MODE_PSNR ? greedy(hs[k], (double)hs[k]->meta.n * tau * tau, false, bv, bound)
+                                              : greedy(hs[k], tau, true, bv, bound);
+        if (!ok) {
+          tot = kNone;
+          break;
+        }
+        for (size_t i = 0; i < bv.size(); i++) tot += hs[k]->tabs[i].bytes[bv[i]];
+      }
+      table[c][t] = tot;
+    }
+  }
+  std::vector<int> votes(nc, 0);
+  for (int t = 0; t < PCR_TUNE_NTOL; t++) {
+    int best = -1;
+    for (int c = 0; c < nc; c++)
+      if (table[c][t] != kNone && (best < 0 || table[c][t] < table[best][t])) best = c;
+    if (best >= 0) votes[best]++;
+  }
+  int win = 0;
+  for (int c = 0; c < nc; c++)
+    if (votes[c] > votes[win]) win = c;
+  *out = cands[win];
+  if (ndim == 2) {   // orders in user axes; the table keeps the 3-D view's natural fill
+    out->order[2] = 0;
+  }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->ncand = nc;
+    info->winner = win;
+    for (int c = 0; c < nc && c < PCR_TUNE_MAX_CANDIDATES; c++) {
+      info->votes[c] = votes[c];
+      info->cand[c] = cands[c];
+      for (int t = 0; t < PCR_TUNE_NTOL; t++) info->bytes[c][t] = table[c][t];
+    }
+    info->nblocks = nb;
+    for (int d = 0; d < ndim; d++) info->block[d] = b[d];
+    info->fraction = (double)(bsz * nb) / (double)n;
+    info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return PCR_OK;
+}
+
+// Schemes whose interp is PCR_INTERP_AUTO are replaced by the tuner's choice
+// for their field (degree, nlevels and nplanes of the request kept).
+static pcr_status resolve_auto(int n, const void* const* d_fields, const int* ndims, const int64_t* const* dims,
+                               const int* dtypes, const pcr_scheme* schemes, const pcr_allocator* alloc,
+                               void* cuda_stream, std::vector<pcr_scheme>& out) {
+  out.assign(schemes, schemes + n);
+  for (int k = 0; k < n; k++) {
+    if (schemes[k].interp != PCR_INTERP_AUTO) continue;
+    if (schemes[k].mode == PCR_MODE_EXPLICIT)
+      return fail(PCR_ERR_INVALID_ARG, "an explicit scheme cannot leave its interpolation to the tuner");
+    pcr_scheme t{};
+    pcr_status e = pcr_tune(d_fields[k], ndims[k], dims[k], dtypes[k], schemes[k].mode, 0.0, 0, alloc, cuda_stream,
+                            &t, nullptr);
+    if (e) return e;
+    t.nlevels = schemes[k].nlevels;
+    t.nplanes = schemes[k].nplanes;
+    out[k] = t;
+  }
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_get_scheme(const pcr_handle* h, pcr_scheme* out) {
+  if (!h || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  *out = h->sch;
   return PCR_OK;
 }
 

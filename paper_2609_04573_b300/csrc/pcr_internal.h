@@ -9,7 +9,16 @@ namespace pcr {
 constexpr int kWord = 32;          // elements per plane word
 constexpr int kSegElems = 4096;    // elements per sign segment / encode CTA
 constexpr int kSegWords = kSegElems / kWord;
-constexpr int kFixBits = 40;       // fixed point: x_int = floor(x 2^(40-G))
+// Fixed point of levels >= 1: x_int = floor(x 2^(F - G)), max |x| < 2^G,
+// with F = fix_bits(value kind, L): 40 for FP32 fields; for FP64 fields 48,
+// fewer for deep hierarchies (56 - L) so that every reconstruction
+// numerator keeps int64 headroom (values <= 4.2 (Lam^d)^L 2^F, numerators
+// <= 20 times that, Lam^d <= 1.953).
+constexpr int kFixBitsF32 = 40;
+inline int fix_bits(int vk, int L) {
+  if (vk != 1) return kFixBitsF32;
+  return 56 - L < 48 ? 56 - L : 48;
+}
 constexpr int kMaxLat = 3;
 
 enum ValueKind { VK_F32 = 0, VK_F64 = 1, VK_FIX = 2 };
@@ -31,6 +40,7 @@ struct FieldD {
   int interp;          // 0 per-level, 1 per-region
   int degree;          // 1 linear, 3 cubic
   int L;
+  int fixb;            // fixed-point fraction bits F (see fix_bits)
 };
 
 // Per-stream device descriptor; holds raw device pointers so kernels can run

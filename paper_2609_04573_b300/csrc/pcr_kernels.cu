@@ -152,14 +152,14 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
   return v;
 }
 
-// floor(x 2^(40-G)) for finite x with |x| < 2^G (exact bit manipulation).
-template <typename T> __device__ __forceinline__ int64_t fix_from(T x, int G);
-template <> __device__ __forceinline__ int64_t fix_from<float>(float x, int G) {
+// floor(x 2^(F-G)) for finite x with |x| < 2^G (exact bit manipulation).
+template <typename T> __device__ __forceinline__ int64_t fix_from(T x, int G, int F);
+template <> __device__ __forceinline__ int64_t fix_from<float>(float x, int G, int F) {
   const uint32_t u = __float_as_uint(x);
   const int e = (u >> 23) & 0xFF;
   const int64_t val = e ? (int64_t)((u & 0x7FFFFFu) | 0x800000u) : (int64_t)(u & 0x7FFFFFu);
   if (val == 0) return 0;
-  const int sh = (e ? e - 150 : -149) + kFixBits - G;
+  const int sh = (e ? e - 150 : -149) + F - G;
   const bool neg = u >> 31;
   if (sh >= 0) { const int64_t r = val << sh; return neg ? -r : r; }
   const int k = -sh;
@@ -167,13 +167,13 @@ template <> __device__ __forceinline__ int64_t fix_from<float>(float x, int G) {
   if (!neg) return val >> k;
   return -((val + ((int64_t(1) << k) - 1)) >> k);
 }
-template <> __device__ __forceinline__ int64_t fix_from<double>(double x, int G) {
+template <> __device__ __forceinline__ int64_t fix_from<double>(double x, int G, int F) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((u >> 52) & 0x7FF);
   const int64_t val = e ? (int64_t)((u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull)
                         : (int64_t)(u & 0xFFFFFFFFFFFFFull);
   if (val == 0) return 0;
-  const int sh = (e ? e - 1075 : -1074) + kFixBits - G;
+  const int sh = (e ? e - 1075 : -1074) + F - G;
   const bool neg = u >> 63;
   if (sh >= 0) { const int64_t r = val << sh; return neg ? -r : r; }
   const int k = -sh;
@@ -299,7 +299,7 @@ __global__ void k_to_fixed(const T* __restrict__ x, FieldD f, const FieldStats* 
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c2 = i % f.nc[2], t = i / f.nc[2];
     const int64_t c1 = t % f.nc[1], c0 = t / f.nc[1];
-    xc[i] = fix_from<T>(x[((c0 * s0) * f.n[1] + 2 * c1) * f.n[2] + 2 * c2], G);
+    xc[i] = fix_from<T>(x[((c0 * s0) * f.n[1] + 2 * c1) * f.n[2] + 2 * c2], G, f.fixb);
   }
 }
 

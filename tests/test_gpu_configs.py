@@ -68,3 +68,47 @@ def test_precision_variant_fp64_and_fp32_cast():
             assert np.abs(got.astype(np.float64) - X64).max() <= cast + v * R * (1 + 1e-6)
     for (kind, v), (got, pl) in outs64.items():
         assert pl.satisfied, v
+
+
+def test_precision_variant_fp64_larger():
+    """The FP64 climate-like field at 64x96x128 (786 K points): streams,
+    plans and retrieved fields bit-exact against the oracle at relative
+    bounds 1e-3..1e-9; each retrieval's error measured against the FP64
+    field stays within its bound."""
+    import paper_2609_04573_b300 as pcr
+    from synth import climate
+    X64 = climate((64, 96, 128), 3, np.float64)
+    sch = pcr.Scheme(interp="level", degree="cubic", decomp_axis=2)
+    tg = [("rel", 10.0 ** -k) for k in range(3, 10)]
+    _, outs64, R = _parity(X64, sch, tg)
+    for (kind, v), (got, pl) in outs64.items():
+        assert pl.satisfied, v
+        assert np.abs(got - X64).max() <= v * R
+
+
+def test_batch_shape_classes_match_the_oracle():
+    """One field of each batched shape class (3-D slabs, 3-D elongated, 2-D),
+    reduced to sizes the oracle finishes in seconds, through the batched
+    refactor and the graph-captured batch: streams and tables bit-exact
+    against the oracle, and a retrieval equal to the oracle's."""
+    import oracle
+    import paper_2609_04573_b300 as pcr
+    from synth import grf
+    from _compare import oracle_scheme, compare_streams
+    shapes = [(25, 125, 125), (16, 64, 256), (450, 900)]
+    Xs = [grf(s, 1000 + i, np.float32) for i, s in enumerate(shapes)]
+    xs = [torch.from_numpy(X).cuda() for X in Xs]
+    schs = [pcr.Scheme(interp="level", degree="cubic", decomp_axis=2 if X.ndim == 3 else -1) for X in Xs]
+    hb = pcr.refactor_batch(xs, schs)
+    g = pcr.RefactorGraph(xs, schs)
+    g.run()
+    for X, s, h1, h2 in zip(Xs, schs, hb, g.handles):
+        h_or = oracle.refactor(X, oracle_scheme(s, X.ndim))
+        compare_streams(h1, h_or)
+        compare_streams(h2, h_or)
+        pl_or = oracle.plan(h_or, oracle.Target("rel", 1e-4))
+        x_or, _ = oracle.retrieve(h_or, pl_or)
+        for h in (h1, h2):
+            out, info = h.retrieve(pcr.Target("rel", 1e-4))
+            assert info.planes == pl_or["b"]
+            assert np.array_equal(out.cpu().numpy(), x_or)

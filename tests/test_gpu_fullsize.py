@@ -14,6 +14,16 @@ the whole field in test time, so:
   the oracle's quantisation gives its value with the stream's exponent
   (the stream maximum is appended to the oracle's input so its E is the
   stream's).  Windows: the 8 field corners and 4 interior positions.
+* sampled retrieval: the whole field is retrieved on the GPU (rel 1e-4 for
+  the per-level scheme, PSNR 80 dB for the per-region one); in each window
+  the oracle decodes the window's level-0 values at the plan's plane counts
+  (with the stream's exponent), recomposes them, and reconstructs level 0
+  from the coarse values the GPU produced; every point 8 (per-level) or 12
+  (per-region, whose passes read reconstructed neighbours) inside the window
+  must equal the GPU's output bit for bit.
+* both of the configuration's schemes: (A) per-level cubic + decomposition,
+  generic planes; (B) per-region cubic (order 0, 1, 2) + decomposition,
+  negabinary + XOR planes, PSNR mode.
 * properties that hold at any size: every retrieval within its bound for
   relative targets 1e-1..1e-7 and PSNR 40..120 dB, payload bytes never
   shrinking as the target tightens, and all planes within the all-planes
@@ -28,34 +38,84 @@ pytestmark = pytest.mark.gpu
 N = 512
 
 
+SCHEMES = {
+    "A": dict(mode="eb", interp="level", degree="cubic", decomp_axis=2),
+    "B": dict(mode="psnr", interp="region", degree="cubic", order=(0, 1, 2), decomp_axis=2),
+}
+TARGETS = {"A": ("rel", 1e-4), "B": ("psnr", 80.0)}
+
+
 @pytest.fixture(scope="module")
-def refactored():
-    import paper_2609_04573_b300 as pcr
+def field():
     from synth.device import grf_torch
     x = grf_torch((N, N, N), 2)
-    sch = pcr.Scheme(mode="eb", interp="level", degree="cubic", decomp_axis=2)
+    torch.cuda.synchronize()
+    return x, x.cpu().numpy()
+
+
+@pytest.fixture(scope="module", params=["A", "B"])
+def refactored(request, field):
+    import paper_2609_04573_b300 as pcr
+    x, X = field
+    sch = pcr.Scheme(**SCHEMES[request.param])
     h = pcr.refactor(x, sch)
     torch.cuda.synchronize()
-    return x, sch, h
+    return x, X, sch, h, request.param
 
 
-def _codes(planes, e, B):
+def _codes(planes, e, B, negabinary):
+    """Codes of elements e from the plane words (negabinary: digits, i.e. the
+    XOR between consecutive stored planes undone)."""
     w, b = e >> 5, (e & 31).astype(np.uint32)
     q = np.zeros(e.shape, np.uint64)
+    prev = np.zeros(e.shape, np.uint64)
     for k in range(B):
-        q |= ((planes[k, w] >> b) & 1).astype(np.uint64) << np.uint64(B - 1 - k)
+        bit = ((planes[k, w] >> b) & 1).astype(np.uint64)
+        if negabinary:
+            bit ^= prev
+            prev = bit
+        q |= bit << np.uint64(B - 1 - k)
     return q
 
 
-def test_sampled_level0_codes_equal_the_oracle(refactored):
-    import oracle.bitplane as bp
-    from oracle.geometry import build_geometry, auto_levels, region_lattice, decomp_axes
+def _window_points(lat, lo, hi):
+    """Lattice indices (K0, K1, K2) of the lattice points in the box [lo, hi]."""
+    ks = []
+    for a in range(3):
+        st, sp, cnt = lat.start[a], lat.step[a], lat.count[a]
+        k0 = max(0, -(-(lo[a] - st) // sp))
+        k1 = min(cnt - 1, (hi[a] - st) // sp)
+        ks.append(np.arange(k0, k1 + 1) if k1 >= k0 else np.zeros(0, np.int64))
+    if not all(len(k) for k in ks):
+        return None
+    return np.meshgrid(*ks, indexing="ij")
+
+
+def _origins():
+    rng = np.random.default_rng(5)
+    origins = [(a, b, c) for a in (0, N - 64) for b in (0, N - 64) for c in (0, N - 64)]
+    origins += [tuple(int(v) * 8 for v in rng.integers(1, (N - 64) // 8, 3)) for _ in range(4)]
+    return origins
+
+
+def _window_coefficients(Xw, sch):
+    """The oracle's level-0 coefficients of a window, decomposed."""
+    from oracle.geometry import region_lattice, decomp_axes
     from oracle.interp import predict_level, level_points_mask, decompose
-    x, sch, h = refactored
-    X = x.cpu().numpy()
-    shape3 = X.shape
     order = (0, 1, 2)
-    geo = build_geometry(shape3, auto_levels(shape3), "level", order, 2)
+    W = predict_level(Xw, order, sch.interp, sch.degree)
+    C = np.where(level_points_mask(Xw.shape, order), Xw - W, 0).astype(np.float32)
+    D = np.zeros_like(C)
+    for r in (1, 2, 3):
+        sl = region_lattice(Xw.shape, 0, order, r).slices()
+        D[sl] = decompose(C[sl].copy(), decomp_axes(2))
+    return D
+
+
+def _level0_streams(h, sch):
+    from oracle.geometry import build_geometry, auto_levels
+    shape3 = (N, N, N)
+    geo = build_geometry(shape3, auto_levels(shape3), sch.interp, (0, 1, 2), 2)
     assert len(geo.streams) == h.nstreams
     lvl0 = [i for i, s in enumerate(geo.streams) if s.level == 0 and not s.is_int]
     assert lvl0 and all(geo.streams[i].sub > 0 for i in lvl0)
@@ -64,48 +124,99 @@ def test_sampled_level0_codes_equal_the_oracle(refactored):
         info = h.stream_info(i)
         assert (info["level"], info["sub"]) == (0, geo.streams[i].sub)
         gpu[i] = (h.stream_copy(i)[0], info["nplanes"], np.float32(info["vmax"]))
-    rng = np.random.default_rng(5)
-    origins = [(a, b, c) for a in (0, N - 64) for b in (0, N - 64) for c in (0, N - 64)]
-    origins += [tuple(int(v) * 8 for v in rng.integers(1, (N - 64) // 8, 3)) for _ in range(4)]
+    return geo, lvl0, gpu
+
+
+def test_sampled_level0_codes_equal_the_oracle(refactored):
+    import oracle.bitplane as bp
+    x, X, sch, h, tag = refactored
+    neg = sch.mode == "psnr"
+    enc = bp.NEGABINARY if neg else bp.GENERIC
+    geo, lvl0, gpu = _level0_streams(h, sch)
     checked = 0
-    for o in origins:
+    for o in _origins():
         e = tuple(min(N, oa + 64) for oa in o)
-        Xw = X[o[0]:e[0], o[1]:e[1], o[2]:e[2]]
-        W = predict_level(Xw, order, "level", sch.degree)
-        C = np.where(level_points_mask(Xw.shape, order), Xw - W, 0).astype(np.float32)
-        D = np.zeros_like(C)
-        for r in (1, 2, 3):
-            sl = region_lattice(Xw.shape, 0, order, r).slices()
-            D[sl] = decompose(C[sl].copy(), decomp_axes(2))
+        D = _window_coefficients(X[o[0]:e[0], o[1]:e[1], o[2]:e[2]], sch)
         lo = [oa if oa == 0 else oa + 8 for oa in o]
-        hi = [ea if ea == N else ea - 8 for ea in e]
+        hi = [(ea if ea == N else ea - 8) - 1 for ea in e]
         for i in lvl0:
             planes, B, vmax = gpu[i]
             base = 0
             for lat in geo.streams[i].lattices:
-                ks = []
-                for a in range(3):
-                    st, sp, cnt = lat.start[a], lat.step[a], lat.count[a]
-                    k0 = max(0, -(-(lo[a] - st) // sp))
-                    k1 = min(cnt - 1, (hi[a] - 1 - st) // sp)
-                    ks.append(np.arange(k0, k1 + 1) if k1 >= k0 else np.zeros(0, np.int64))
-                if all(len(k) for k in ks):
-                    K0, K1, K2 = np.meshgrid(*ks, indexing="ij")
-                    g = [lat.start[a] + lat.step[a] * K for a, K in enumerate((K0, K1, K2))]
+                K = _window_points(lat, lo, hi)
+                if K is not None:
+                    K0, K1, K2 = K
+                    g = [lat.start[a] + lat.step[a] * Ka for a, Ka in enumerate(K)]
                     vals = D[g[0] - o[0], g[1] - o[1], g[2] - o[2]].ravel()
                     elem = (base + (K0 * lat.count[1] + K1) * lat.row_pad + K2).ravel()
-                    want = bp.quantize(np.append(vals, vmax), False, B, bp.GENERIC)["q"][:-1]
-                    got = _codes(planes, elem, B)
+                    want = bp.quantize(np.append(vals, vmax), False, B, enc)["q"][:-1]
+                    got = _codes(planes, elem, B, neg)
                     bad = np.nonzero(got != want.astype(np.uint64))[0]
-                    assert bad.size == 0, (o, i, int(elem[bad[0]]), int(got[bad[0]]), int(want[bad[0]]))
+                    assert bad.size == 0, (tag, o, i, int(elem[bad[0]]), int(got[bad[0]]), int(want[bad[0]]))
                     checked += vals.size
                 base += lat.n_pad
     assert checked > 500_000
 
 
+def test_sampled_retrieval_equals_the_oracle(refactored):
+    """Decode + recompose + level-0 reconstruction at full size, in windows,
+    against the oracle (coarse values taken from the GPU's output)."""
+    import oracle.bitplane as bp
+    import paper_2609_04573_b300 as pcr
+    from oracle.geometry import region_lattice, decomp_axes
+    from oracle.interp import level_points_mask, recompose, reconstruct_level
+    x, X, sch, h, tag = refactored
+    neg = sch.mode == "psnr"
+    enc = bp.NEGABINARY if neg else bp.GENERIC
+    geo, lvl0, gpu = _level0_streams(h, sch)
+    pl = h.plan(pcr.Target(*TARGETS[tag]))
+    out, _ = h.retrieve(pl)
+    OUT = out.cpu().numpy()
+    order, uv = (0, 1, 2), decomp_axes(2)
+    checked = 0
+    for o in _origins():
+        e = tuple(min(N, oa + 64) for oa in o)
+        win = tuple(slice(a, b) for a, b in zip(o, e))
+        D = _window_coefficients(X[win], sch)
+        Dhat = np.zeros_like(D)
+        for i in lvl0:
+            planes, B, vmax = gpu[i]
+            for lat in geo.streams[i].lattices:
+                K = _window_points(lat, o, [ea - 1 for ea in e])
+                if K is None:
+                    continue
+                g = [lat.start[a] + lat.step[a] * Ka - o[a] for a, Ka in enumerate(K)]
+                vals = np.append(D[g[0], g[1], g[2]].ravel(), vmax)
+                n = -(-vals.size // 32) * 32
+                vals = np.concatenate([vals, np.zeros(n - vals.size, np.float32)])
+                ec = bp.encode(vals, False, B, enc, False)
+                dec = bp.decode(ec, n, False, B, enc, pl.planes[i], np.dtype(np.float32))
+                Dhat[g[0], g[1], g[2]] = dec[:g[0].size].reshape(g[0].shape)
+        Xr = np.zeros(D.shape, np.float32)
+        mask = level_points_mask(D.shape, order)
+        for r in (1, 2, 3):
+            sl = region_lattice(D.shape, 0, order, r).slices()
+            Xr[sl] = recompose(Dhat[sl].copy(), uv)
+        W = OUT[win]
+        Xr[~mask] = W[~mask]                       # the GPU's coarse values
+        reconstruct_level(Xr, order, sch.interp, sch.degree)
+        # interior: per-level passes read coarse values only (reach 3, the
+        # point's own recomposition 6); per-region passes read earlier
+        # regions' reconstructed values, whose recomposition reaches 6 field
+        # points along an in-slice axis on top of the pass's 3
+        m = 8 if sch.interp == "level" else 12
+        lo = [0 if oa == 0 else m for oa in o]
+        hi = [b - a if b == N else b - a - m for a, b in zip(o, e)]
+        inner = tuple(slice(a, b) for a, b in zip(lo, hi))
+        bad = np.argwhere(Xr[inner] != W[inner])
+        assert bad.size == 0, (tag, o, bad[0].tolist())
+        checked += Xr[inner].size
+    assert checked > 500_000
+
+
 def test_full_size_retrievals_within_bound(refactored):
     import paper_2609_04573_b300 as pcr
-    x, sch, h = refactored
+    x, X, sch, h, tag = refactored
     xmin, xmax, _ = h.field_stats()
     R = xmax - xmin
     xd = x.double()

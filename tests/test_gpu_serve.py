@@ -3,8 +3,9 @@
 * pcr_refactor_batch: each field of a batch (uneven shapes, 2-D and 3-D)
   refactors byte-for-byte like its own pcr_refactor.
 * Server (continuous batching, memory admission, two streams): every
-  request's field equals the one a single pcr_retrieve of the same request
-  returns, whatever the mix it was batched with.
+  request's field equals the one a single retrieval of the same request
+  returns, whatever the mix it was batched with, and served results (whole
+  fields and boxes) equal the oracle's retrieval.
 """
 import random
 import time
@@ -76,3 +77,31 @@ def test_server_results_equal_single_retrievals():
     assert srv.batches < len(reqs)          # some groups held several requests
     assert all(r.latency > 0 for r in live)
     assert srv.mem_in_use == 0
+
+
+def test_served_results_match_the_oracle():
+    import oracle
+    import paper_2609_04573_b300 as pcr
+    from paper_2609_04573_b300.serve import Server
+    from _compare import oracle_scheme
+    Xs = _fields()[:3]
+    schs = [pcr.Scheme(interp="level", degree="cubic", decomp_axis=2 if X.ndim == 3 else -1) for X in Xs[:2]]
+    schs.append(pcr.Scheme(mode="psnr", interp="region", degree="cubic", decomp_axis=0))
+    hs = [pcr.refactor(torch.from_numpy(X).cuda(), s) for X, s in zip(Xs, schs)]
+    hos = [oracle.refactor(X, oracle_scheme(s, X.ndim)) for X, s in zip(Xs, schs)]
+    reqs = [(0, pcr.Target("rel", 1e-3), None), (1, pcr.Target("psnr", 70.0), None),
+            (2, pcr.Target("psnr", 90.0), ((3, 17), (5, 30), (10, 65))),
+            (0, pcr.Target("rel", 1e-5), ((0, 18), (20, 44), (33, 70))), (2, pcr.Target("rel", 1e-4), None),
+            (1, pcr.Target("rel", 1e-2), ((40, 96), (0, 64)))]
+    budget = 3 * max(h.retrieve_scratch_bytes() + h.out_bytes for h in hs)
+    srv = Server(hs, mem_budget=budget, max_batch=4, streams=2, start=False)
+    live = [srv.submit(f, t, box) for f, t, box in reqs]
+    srv.start()
+    got = [r.future.result(timeout=60) for r in live]
+    srv.close()
+    for (f, t, box), g in zip(reqs, got):
+        pl_or = oracle.plan(hos[f], oracle.Target(t.kind, t.value))
+        x_or, _ = oracle.retrieve(hos[f], pl_or)
+        if box:
+            x_or = x_or[tuple(slice(lo, hi) for lo, hi in box)]
+        assert np.array_equal(g.cpu().numpy(), x_or), (f, t, box)

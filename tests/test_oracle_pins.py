@@ -499,3 +499,26 @@ def test_stream_bytes_hand_counted():
             vals[i] = v
         enc = bp.encode(vals, True, st["B"], st["enc"], False)
         assert bp.stream_bytes(enc, st["B"], st["n"] // WORD) == st["expect"]
+
+
+def test_fp64_all_planes_near_lossless():
+    """Every plane of an FP64 refactor gives the field back to within 1e-14
+    of its range (the paper's near-lossless full retrieval; the fixed point
+    of levels >= 1 keeps 48 fraction bits for FP64 fields, so the only
+    losses are its floor and FP64 rounding at level 0), and an FP32 field to
+    within a few units in the last place."""
+    for shape, sch in [((24, 28, 32), Scheme(interp="level", degree="cubic", decomp_axis=2)),
+                       ((26, 31, 29), Scheme(mode="psnr", interp="region", degree="cubic")),
+                       ((1, 60, 70), Scheme(interp="level", degree="linear"))]:
+        X = grf(shape, 77, np.float64)
+        X = X[0] if shape[0] == 1 else X
+        h = oracle.refactor(X, sch)
+        assert h["meta"]["F"] == 48
+        B = h["meta"]["B"]
+        xr, _ = oracle.retrieve(h, dict(b=[B] * len(h["streams"])))
+        R = h["meta"]["R"]
+        assert np.abs(xr - X).max() <= 1e-14 * R
+        X32 = X.astype(np.float32)
+        h32 = oracle.refactor(X32, sch)
+        xr32, _ = oracle.retrieve(h32, dict(b=[32] * len(h32["streams"])))
+        assert np.abs(xr32.astype(np.float64) - X32).max() <= 8 * 2.0 ** -24 * np.abs(X32).max()
