@@ -48,8 +48,18 @@ void launch_encode(int vk, int w64, int pairs, const StreamD* d_streams, const W
 void launch_decode(int vk, int w64, const StreamD* d_streams, const WorkItem* d_items, int nitems,
                    cudaStream_t s);
 void launch_tile_interp(int vk, const TileArgs& a, cudaStream_t s);
+void launch_tile_interp_multi(int vk, const TileArgs* args, int n, cudaStream_t s);
 void launch_tile_decomp(int vk, const DecompArgs& a, cudaStream_t s);
-void launch_zero_pads(int vk, const LatD& lat, void* stage, cudaStream_t s);
+void launch_zero_pads_multi(const int* vks, const LatD* lats, void* const* stages, int n, cudaStream_t s);
+void launch_tile_decomp_multi(int vk, const DecompArgs* das, int n, cudaStream_t s);
+// batched forms over the fields of a batch (pcr_kernels.cu)
+void launch_stats_multi(int vk, const void* const* xs, const int64_t* ns, FieldStats* const* sts, int n,
+                        cudaStream_t s);
+void launch_to_fixed_multi(int vk, const void* const* xs, const FieldD* fs, const FieldStats* const* sts,
+                           int64_t* const* xcs, int n, cudaStream_t s);
+void launch_coarsest_multi(const FieldD* fs, const int* levels, const LatD* lats, const int64_t* const* xcs,
+                           int64_t* const* outs, unsigned long long* const* vmaxs, int n, cudaStream_t s);
+void launch_words_multi(const WordsItem* items, int n, cudaStream_t s);
 }  // namespace pcr
 
 using namespace pcr;
@@ -1010,11 +1020,6 @@ void level_regions(const pcr_handle* h, int level, const std::vector<StreamD>& s
   }
 }
 
-void zero_stream_pads(const pcr_handle* h, const StreamD& sd, int kind, cudaStream_t s) {
-  for (int k = 0; k < sd.nlat; k++)
-    if (sd.lat[k].row_pad > sd.lat[k].count[2]) launch_zero_pads(kind, sd.lat[k], sd.stage, s);
-}
-
 // sub-level lattices of a decomposed region in its compact coordinates
 void decomp_subs(const pcr_handle* h, int region, const std::vector<StreamD>& sds, DecompArgs& a) {
   int u = -1, v = -1;
@@ -1665,15 +1670,47 @@ struct Scratch {
   }
 };
 
-// Enqueue the whole refactor of one handle (geometry already set up) with its
-// device outputs allocated; `st` receives field stats, `vmax` per-stream maxima.
-static pcr_status enqueue_refactor(pcr_handle* h, const void* d_field, cudaStream_t s, Scratch& sc,
-                                   FieldStats* d_st, unsigned long long* d_vmax, unsigned long long* d_pairs,
-                                   std::vector<StreamD>& sds) {
+// The refactor of one field, prepared on the host: its scratch carved, its
+// stream descriptors filled and the arguments of every stage's launch
+// recorded.  The stages of a batch then go out stage by stage across all its
+// fields (enqueue_stages), each stage in as few launches as the batched
+// kernels' parameter blocks allow.
+struct FieldWork {
+  pcr_handle* h = nullptr;
+  const void* x = nullptr;
+  FieldD f{};
+  FieldStats* st = nullptr;
+  int64_t n = 0;
+  int64_t* xc = nullptr;   // fixed-point 2-grid (L >= 2)
+  bool has_l0 = false;     // level 0 predicted from the original values
+  TileArgs l0{};
+  // coarsest level: fixed point (L >= 2) or the raw values (L = 1)
+  bool coarse_fix = false;
+  int coarse_level = 0;
+  LatD coarse_lat{};
+  void* coarse_stage = nullptr;
+  unsigned long long* coarse_vmax = nullptr;
+  std::vector<TileArgs> fixed;     // levels L-2 .. 1 (fixed point)
+  std::vector<DecompArgs> dec;     // decomposed level-0 regions
+  std::vector<int> pad_vk;         // row padding of every stream's staging
+  std::vector<LatD> pad_lat;
+  std::vector<void*> pad_stage;
+};
+
+// Scratch and launch arguments of one handle's refactor (geometry already
+// set up, device outputs allocated); `st` receives field stats, `vmax`
+// per-stream maxima.  Nothing is launched.
+static pcr_status prepare_refactor(pcr_handle* h, const void* d_field, Scratch& sc, FieldStats* d_st,
+                                   unsigned long long* d_vmax, unsigned long long* d_pairs,
+                                   std::vector<StreamD>& sds, FieldWork& w) {
   const int ns = (int)h->geo.size();
-  const int64_t n = h->n3[0] * h->n3[1] * h->n3[2];
   const FieldD f = field_desc(h);
-  const size_t w = vsize(h->vk);
+  const size_t vb = vsize(h->vk);
+  w.h = h;
+  w.x = d_field;
+  w.f = f;
+  w.st = d_st;
+  w.n = h->n3[0] * h->n3[1] * h->n3[2];
   // staging
   size_t fix_elems = 0, flt_elems = 0;
   std::vector<size_t> soff(ns);
@@ -1687,27 +1724,18 @@ static pcr_status enqueue_refactor(pcr_handle* h, const void* d_field, cudaStrea
     }
   }
   int64_t* st_fix = (int64_t*)sc.get(fix_elems * 8);
-  char* st_flt = (char*)sc.get(flt_elems * w);
+  char* st_flt = (char*)sc.get(flt_elems * vb);
   if (!st_fix || !st_flt) return fail(PCR_ERR_OOM, "staging allocation failed");
-  {
-    Prof pf("stats", s);
-    launch_minmax(h->vk, d_field, n, d_st, s);
-  }
-  int64_t* xc = nullptr;
   if (h->L >= 2) {
-    xc = (int64_t*)sc.get((size_t)f.nc[0] * f.nc[1] * f.nc[2] * 8);
-    if (!xc) return fail(PCR_ERR_OOM, "staging allocation failed");
-    {
-      Prof pf("to_fixed", s);
-      launch_to_fixed(h->vk, d_field, f, d_st, xc, s);
-    }
+    w.xc = (int64_t*)sc.get((size_t)f.nc[0] * f.nc[1] * f.nc[2] * 8);
+    if (!w.xc) return fail(PCR_ERR_OOM, "staging allocation failed");
   }
   // region compact arrays for the decomposition
   std::vector<void*> comp(4, nullptr);
   if (h->decomp >= 0)
     for (int r = 1; r <= f.d; r++) {
       const Lat R = region_lat(h->n3, 0, h->order, r);
-      comp[r] = sc.get((size_t)R.n_real() * w);
+      comp[r] = sc.get((size_t)R.n_real() * vb);
       if (!comp[r]) return fail(PCR_ERR_OOM, "staging allocation failed");
     }
   unsigned long long* c0 = &d_st->c0;
@@ -1716,20 +1744,12 @@ static pcr_status enqueue_refactor(pcr_handle* h, const void* d_field, cudaStrea
     sds[i] = stream_desc(h, i);
     sds[i].vmax = d_vmax + i;
     sds[i].pairs = d_pairs ? d_pairs + (size_t)i * h->B * h->B : nullptr;
-    sds[i].stage = g.is_fix ? (void*)(st_fix + soff[i]) : (void*)(st_flt + soff[i] * w);
+    sds[i].stage = g.is_fix ? (void*)(st_fix + soff[i]) : (void*)(st_flt + soff[i] * vb);
   }
-  // coarsest level (raw) and the L = 1 case
-  {
-    const SGeo& g = h->geo[0];
-    const LatD ld = to_latd(g.lats[0], 0);
-    Prof pf("coarsest", s);
-    if (g.is_fix) launch_coef_fixed(f, g.level, 1, ld, xc, (int64_t*)sds[0].stage, sds[0].vmax, s);
-    else launch_raw_stage(h->vk, f, ld, d_field, sds[0].stage, sds[0].vmax, s);
-  }
-  // levels L-2 .. 1 in fixed point (Alg. 1 loop), level 0 in the field dtype
-  for (int level = h->L - 2; level >= 0; level--) {
-    TileArgs a = level_args(h, level, 0, level == 0 ? d_field : (const void*)xc, nullptr);
-    if (level == 0 && h->decomp >= 0) {
+  // level 0 (Alg. 1 predicts it from the original values)
+  if (h->L >= 2) {
+    TileArgs a = level_args(h, 0, 0, d_field, nullptr);
+    if (h->decomp >= 0) {
       for (int r = 1; r <= f.d; r++) {
         const Lat R = region_lat(h->n3, 0, h->order, r);
         // max |c| over level 0 for the rounding allowance, taken while the
@@ -1738,41 +1758,155 @@ static pcr_status enqueue_refactor(pcr_handle* h, const void* d_field, cudaStrea
         a.reg[r - 1].vmax_double = 1;
       }
     } else {
-      level_regions(h, level, sds, a);
+      level_regions(h, 0, sds, a);
     }
-    {
-      Prof pf(level == 0 ? "interp_level0" : "interp_fixed_levels", s);
-      launch_tile_interp(level == 0 ? h->vk : VK_FIX, a, s);
-    }
+    w.has_l0 = true;
+    w.l0 = a;
   }
+  // coarsest level (raw) and the L = 1 case
   {
-    Prof pf("zero_pads", s);
-    for (int i = 1; i < ns; i++)
-      if (h->geo[i].sub == 0) zero_stream_pads(h, sds[i], h->geo[i].is_fix ? VK_FIX : h->vk, s);
+    const SGeo& g = h->geo[0];
+    w.coarse_fix = g.is_fix;
+    w.coarse_level = g.level;
+    w.coarse_lat = to_latd(g.lats[0], 0);
+    w.coarse_stage = sds[0].stage;
+    w.coarse_vmax = sds[0].vmax;
   }
-  if (h->decomp >= 0) {
+  // levels L-2 .. 1 in fixed point (Alg. 1 loop); each reads only the
+  // fixed-point copy of the field, so they are independent grids
+  for (int level = h->L - 2; level >= 1; level--) {
+    TileArgs a = level_args(h, level, 0, (const void*)w.xc, nullptr);
+    level_regions(h, level, sds, a);
+    w.fixed.push_back(a);
+  }
+  if (h->decomp >= 0)
     for (int r = 1; r <= f.d; r++) {
       DecompArgs da{};
       decomp_subs(h, r, sds, da);
       da.retrieve = 0;
       da.comp = comp[r];
       da.c0 = nullptr;   // max |c| taken by the level-0 prediction
-      {
-        Prof pf(da.retrieve ? "recompose" : "decompose", s);
-        launch_tile_decomp(h->vk, da, s);
+      da.err = &d_st->timeout;
+      w.dec.push_back(da);
+    }
+  // the row padding of every stream's staging (the kernels above write only
+  // real elements, so this may run in any order with them)
+  for (int i = 1; i < ns; i++)
+    for (int k = 0; k < sds[i].nlat; k++)
+      if (sds[i].lat[k].row_pad > sds[i].lat[k].count[2]) {
+        w.pad_vk.push_back(h->geo[i].is_fix ? VK_FIX : h->vk);
+        w.pad_lat.push_back(sds[i].lat[k]);
+        w.pad_stage.push_back(sds[i].stage);
+      }
+  return PCR_OK;
+}
+
+// The coefficient stages of a batch's refactors, stage by stage across the
+// fields: statistics, level-0 prediction, fixed-point copy, coarsest level,
+// fixed-point levels, decomposition, row padding.  Within a stage the
+// fields' grids are independent; each stage reads only what earlier stages
+// wrote.
+static void enqueue_stages(const std::vector<FieldWork>& ws, cudaStream_t s) {
+  const int vks[2] = {VK_F32, VK_F64};
+  {
+    Prof pf("stats", s);
+    for (int vk : vks) {
+      std::vector<const void*> xs;
+      std::vector<int64_t> ns;
+      std::vector<FieldStats*> sts;
+      for (const FieldWork& w : ws)
+        if (w.h->vk == vk) {
+          xs.push_back(w.x);
+          ns.push_back(w.n);
+          sts.push_back(w.st);
+        }
+      if (!xs.empty()) launch_stats_multi(vk, xs.data(), ns.data(), sts.data(), (int)xs.size(), s);
+    }
+  }
+  {
+    Prof pf("interp_level0", s);
+    for (int vk : vks) {
+      std::vector<TileArgs> l0;
+      for (const FieldWork& w : ws)
+        if (w.h->vk == vk && w.has_l0) l0.push_back(w.l0);
+      launch_tile_interp_multi(vk, l0.data(), (int)l0.size(), s);
+    }
+  }
+  {
+    Prof pf("to_fixed", s);
+    for (int vk : vks) {
+      std::vector<const void*> xs;
+      std::vector<FieldD> fs;
+      std::vector<const FieldStats*> sts;
+      std::vector<int64_t*> xcs;
+      for (const FieldWork& w : ws)
+        if (w.h->vk == vk && w.xc) {
+          xs.push_back(w.x);
+          fs.push_back(w.f);
+          sts.push_back(w.st);
+          xcs.push_back(w.xc);
+        }
+      if (!xs.empty()) launch_to_fixed_multi(vk, xs.data(), fs.data(), sts.data(), xcs.data(), (int)xs.size(), s);
+    }
+  }
+  {
+    Prof pf("coarsest", s);
+    std::vector<FieldD> fs;
+    std::vector<int> levels;
+    std::vector<LatD> lats;
+    std::vector<const int64_t*> xcs;
+    std::vector<int64_t*> outs;
+    std::vector<unsigned long long*> vms;
+    for (const FieldWork& w : ws) {
+      if (w.coarse_fix) {
+        fs.push_back(w.f);
+        levels.push_back(w.coarse_level);
+        lats.push_back(w.coarse_lat);
+        xcs.push_back(w.xc);
+        outs.push_back((int64_t*)w.coarse_stage);
+        vms.push_back(w.coarse_vmax);
+      } else {
+        launch_raw_stage(w.h->vk, w.f, w.coarse_lat, w.x, w.coarse_stage, w.coarse_vmax, s);
       }
     }
-    Prof pf("zero_pads", s);
-    for (int i = 1; i < ns; i++)
-      if (h->geo[i].sub != 0) zero_stream_pads(h, sds[i], h->vk, s);
+    if (!fs.empty())
+      launch_coarsest_multi(fs.data(), levels.data(), lats.data(), xcs.data(), outs.data(), vms.data(),
+                            (int)fs.size(), s);
   }
-  return PCR_OK;
+  {
+    std::vector<TileArgs> lv;
+    for (const FieldWork& w : ws) lv.insert(lv.end(), w.fixed.begin(), w.fixed.end());
+    Prof pf("interp_fixed_levels", s);
+    launch_tile_interp_multi(VK_FIX, lv.data(), (int)lv.size(), s);
+  }
+  {
+    Prof pf("decompose", s);
+    for (int vk : vks) {
+      std::vector<DecompArgs> das;
+      for (const FieldWork& w : ws)
+        if (w.h->vk == vk) das.insert(das.end(), w.dec.begin(), w.dec.end());
+      if (!das.empty()) launch_tile_decomp_multi(vk, das.data(), (int)das.size(), s);
+    }
+  }
+  {
+    std::vector<int> pv;
+    std::vector<LatD> pl;
+    std::vector<void*> ps;
+    for (const FieldWork& w : ws) {
+      pv.insert(pv.end(), w.pad_vk.begin(), w.pad_vk.end());
+      pl.insert(pl.end(), w.pad_lat.begin(), w.pad_lat.end());
+      ps.insert(ps.end(), w.pad_stage.begin(), w.pad_stage.end());
+    }
+    Prof pf("zero_pads", s);
+    launch_zero_pads_multi(pv.data(), pl.data(), ps.data(), (int)pv.size(), s);
+  }
 }
 
 static pcr_status finish_refactor(pcr_handle* h, const FieldStats& st, const std::vector<unsigned long long>& vm,
                                   const std::vector<uint32_t>& nz,
                                   const std::vector<uint64_t>* pairs) {
   if (st.bad) return fail(PCR_ERR_INVALID_ARG, "field contains NaN or Inf");
+  if (st.timeout) return fail(PCR_ERR_TIMEOUT, "a device wait of the refactor gave up");
   auto inv = [](unsigned long long k) {
     unsigned long long u = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
     double d;
@@ -1933,19 +2067,30 @@ static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* 
   CUDA_TRY(cudaMemcpyAsync(d_st, io.st_init, sizeof(FieldStats) * n, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemsetAsync(d_vm, 0, L.nv * 8, s));
   if (L.npairs) CUDA_TRY(cudaMemsetAsync(d_pairs, 0, L.npairs * 8, s));
-  for (int k = 0; k < n; k++) {
-    CUDA_TRY(cudaMemsetAsync(hs[k]->d_nz, 0, hs[k]->nz_words * 4, s));
-    if (clear_signs && hs[k]->sign_area_words) CUDA_TRY(cudaMemsetAsync(hs[k]->d_signs, 0, hs[k]->sign_area_words * 4, s));
+  // every handle's plane counts (and, when asked, sign slots and counts)
+  // zeroed in one launch
+  {
+    std::vector<WordsItem> z;
+    for (int k = 0; k < n; k++) {
+      z.push_back({hs[k]->d_nz, nullptr, (int64_t)hs[k]->nz_words});
+      if (clear_signs) {
+        z.push_back({hs[k]->d_signs, nullptr, (int64_t)hs[k]->sign_area_words});
+        z.push_back({hs[k]->d_scnt, nullptr, (int64_t)hs[k]->scnt_words});
+      }
+    }
+    launch_words_multi(z.data(), (int)z.size(), s);
   }
-  // coefficient stages per field; encode work lists for the whole batch
+  // coefficient stages of every field, stage by stage; encode work lists
+  // for the whole batch
+  std::vector<FieldWork> ws(n);
   std::vector<StreamD> all;
   std::vector<WorkItem> items[2][2];  // [w64][fixed?]
   int pairs_mode[2][2] = {{-1, -1}, {-1, -1}};
   for (int k = 0; k < n; k++) {
     pcr_handle* h = hs[k];
     std::vector<StreamD> sds(h->geo.size());
-    pcr_status e = enqueue_refactor(h, d_fields[k], s, sc, d_st + k, d_vm + L.vm_off[k],
-                                    keeps_pairs(h) ? d_pairs + L.pr_off[k] : nullptr, sds);
+    pcr_status e = prepare_refactor(h, d_fields[k], sc, d_st + k, d_vm + L.vm_off[k],
+                                    keeps_pairs(h) ? d_pairs + L.pr_off[k] : nullptr, sds, ws[k]);
     if (e) return e;
     for (size_t i = 0; i < sds.size(); i++) {
       const int idx = (int)all.size();
@@ -1957,11 +2102,15 @@ static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* 
       for (int64_t g = 0; g < sds[i].nseg; g++) items[h->w64][fx].push_back({idx, (int)g});
     }
   }
-  // each handle's whole-retrieval work list, kept on the device
+  enqueue_stages(ws, s);
+  // each handle's whole-retrieval work list, kept on the device (one upload
+  // for the batch, scattered by one launch)
+  std::vector<WorkItem> li;
+  std::vector<std::pair<pcr_handle*, size_t>> li_at;
   for (int k = 0; k < n; k++) {
     pcr_handle* h = hs[k];
     if (h->items_ready) continue;
-    std::vector<WorkItem> li;
+    const size_t at = li.size();
     for (int fx = 0; fx < 2; fx++) {
       h->items_n[fx] = 0;
       for (int i = 0; i < (int)h->geo.size(); i++) {
@@ -1971,9 +2120,27 @@ static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* 
         h->items_n[fx] += nseg;
       }
     }
-    if (li.empty()) continue;
-    CUDA_TRY(cudaMemcpyAsync(h->d_items_all, li.data(), li.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
-    h->items_ready = true;
+    if (li.size() > at) li_at.push_back({h, at});
+  }
+  if (!li.empty()) {
+    static_assert(sizeof(WorkItem) % 4 == 0, "work items are whole words");
+    if (li_at.size() == 1) {
+      CUDA_TRY(cudaMemcpyAsync(li_at[0].first->d_items_all, li.data(), li.size() * sizeof(WorkItem),
+                               cudaMemcpyHostToDevice, s));
+    } else {
+      WorkItem* d_li = (WorkItem*)sc.get(li.size() * sizeof(WorkItem));
+      if (!d_li) return fail(PCR_ERR_OOM, "work list allocation failed");
+      CUDA_TRY(cudaMemcpyAsync(d_li, li.data(), li.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+      std::vector<WordsItem> cp;
+      for (size_t q = 0; q < li_at.size(); q++) {
+        const size_t end = q + 1 < li_at.size() ? li_at[q + 1].second : li.size();
+        cp.push_back({(uint32_t*)li_at[q].first->d_items_all, (const uint32_t*)(d_li + li_at[q].second),
+                      (int64_t)((end - li_at[q].second) * sizeof(WorkItem) / 4)});
+      }
+      launch_words_multi(cp.data(), (int)cp.size(), s);
+    }
+    // (a copy from pageable memory has read its source when the call returns)
+    for (auto& q : li_at) q.first->items_ready = true;
   }
   size_t nit = 0;
   for (int a = 0; a < 2; a++)
@@ -2028,8 +2195,16 @@ static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* 
   CUDA_TRY(cudaMemcpyAsync(io.st, d_st, sizeof(FieldStats) * n, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(io.vm, d_vm, L.nv * 8, cudaMemcpyDeviceToHost, s));
   if (L.npairs) CUDA_TRY(cudaMemcpyAsync(io.pairs, d_pairs, L.npairs * 8, cudaMemcpyDeviceToHost, s));
-  for (int k = 0; k < n; k++)
-    CUDA_TRY(cudaMemcpyAsync(io.nz + L.nz_off[k], hs[k]->d_nz, hs[k]->nz_words * 4, cudaMemcpyDeviceToHost, s));
+  if (n == 1) {
+    CUDA_TRY(cudaMemcpyAsync(io.nz, hs[0]->d_nz, hs[0]->nz_words * 4, cudaMemcpyDeviceToHost, s));
+  } else {   // the handles' plane counts gathered by one launch, read back by one copy
+    uint32_t* d_nz = (uint32_t*)sc.get(std::max<size_t>(L.nnz, 1) * 4);
+    if (!d_nz) return fail(PCR_ERR_OOM, "statistics allocation failed");
+    std::vector<WordsItem> cp;
+    for (int k = 0; k < n; k++) cp.push_back({d_nz + L.nz_off[k], hs[k]->d_nz, (int64_t)hs[k]->nz_words});
+    launch_words_multi(cp.data(), (int)cp.size(), s);
+    CUDA_TRY(cudaMemcpyAsync(io.nz, d_nz, L.nnz * 4, cudaMemcpyDeviceToHost, s));
+  }
   return PCR_OK;
 }
 
@@ -2083,6 +2258,8 @@ static size_t refactor_scratch_bytes(const pcr_handle* h) {
   size_t t = al(fix * 8) + al(flt * w) + al(ns * sizeof(StreamD)) + al(std::max<size_t>(items, 1) * sizeof(WorkItem)) +
              al(sizeof(FieldStats)) + al(ns * 8);
   if (keeps_pairs(h)) t += al(ns * h->B * h->B * 8);
+  // its share of the batch's work-list upload and plane-count gather
+  t += al(std::max<size_t>(items, 1) * sizeof(WorkItem)) + al(std::max<size_t>(h->nz_words, 1) * 4);
   if (h->L >= 2) {
     size_t nc = 1;
     for (int a = 0; a < 3; a++) nc *= h->n3[a] > 1 ? (h->n3[a] - 1) / 2 + 1 : 1;

@@ -103,6 +103,40 @@ struct TileArgs {
   int64_t tlo[3];
 };
 
+// items of one batched (multi-field) launch of the per-field kernels
+constexpr int kMaxBatchItems = 128;
+
+// a range of 32-bit words to zero (src null) or copy, one item of a batched
+// launch
+struct WordsItem {
+  uint32_t* dst;
+  const uint32_t* src;
+  int64_t words;
+};
+
+#ifdef __CUDACC__
+// item of a batched launch that owns this block: the last i < n with
+// first[i] <= blockIdx.x (first[] ascending, first[0] = 0)
+__device__ __forceinline__ int batch_find(const int64_t* first, int n) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= (int64_t)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+#endif
+
+// independent tile-kernel launches fused into one (the refactor's levels
+// >= 1, or one level of several fields); first[i]: first block of args[i]
+constexpr int kMaxTileBatch = 56;
+struct TileBatch {
+  int n;
+  int64_t first[kMaxTileBatch + 1];
+  TileArgs args[kMaxTileBatch];
+};
+
 // one sub-level lattice part of a decomposed region, in the region's compact
 // coordinates, with its padded stream staging
 struct DecompSub {
@@ -123,6 +157,7 @@ struct DecompArgs {
   // first block per axis set by the launcher
   int64_t blo[3], bhi[3], tlo[3];
   unsigned long long* c0;  // decompose: running max |c| (bits of a double)
+  int* err;                // set to 1 when a bounded device wait gives up (may be null)
 };
 
 // an index box: points lo + [0, cnt) per axis
@@ -141,6 +176,7 @@ struct FieldStats {
   unsigned long long c0;                   // max |c| at level 0 (double bits)
   int G;                                   // max|x| < 2^G
   int bad;                                 // non-finite input seen
+  int timeout;                             // a bounded device wait gave up
 };
 
 // Device address of the library's fixed scratch array on the current device

@@ -212,8 +212,12 @@ __device__ __forceinline__ int64_t lat_padded_index(const LatD& l, const int64_t
 // --------------------------------------------------------------------------
 // a1: field statistics
 // --------------------------------------------------------------------------
+// min, max and finiteness of x[0 .. n) by the threads tid = 0 .. nth - 1 of
+// the blocks that share this field (a grid, or the field's blocks of a
+// batched launch)
 template <typename T>
-__global__ void k_minmax(const T* __restrict__ x, int64_t n, FieldStats* st) {
+__device__ __forceinline__ void minmax_body(const T* __restrict__ x, int64_t n, FieldStats* st, int64_t tid,
+                                            int64_t nth) {
   __shared__ unsigned long long rlo[32], rhi[32];
   __shared__ int rbad;
   if (threadIdx.x == 0) rbad = 0;
@@ -224,7 +228,6 @@ __global__ void k_minmax(const T* __restrict__ x, int64_t n, FieldStats* st) {
     lo = v < lo ? v : lo;
     hi = v > hi ? v : hi;
   };
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
   int64_t tail = 0;
   if (((uintptr_t)x & 15) == 0) {   // 16-byte vectors, four loads in flight
     using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
@@ -275,9 +278,46 @@ __global__ void k_minmax(const T* __restrict__ x, int64_t n, FieldStats* st) {
   }
 }
 
+template <typename T>
+__global__ void k_minmax(const T* __restrict__ x, int64_t n, FieldStats* st) {
+  minmax_body<T>(x, n, st, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// batched forms: one launch for the fields of a batch (blocks first[i] ..
+// first[i + 1] - 1 belong to item i)
+// ---------------------------------------------------------------------------
+struct MinmaxBatch {
+  int n;
+  int64_t first[kMaxBatchItems + 1];
+  const void* x[kMaxBatchItems];
+  int64_t cnt[kMaxBatchItems];
+  FieldStats* st[kMaxBatchItems];
+};
+static_assert(sizeof(MinmaxBatch) <= 32764, "kernel parameter block");
+
+template <typename T>
+__global__ void k_minmax_multi(const __grid_constant__ MinmaxBatch b) {
+  const int i = batch_find(b.first, b.n);
+  const int64_t nblk = b.first[i + 1] - b.first[i];
+  minmax_body<T>(reinterpret_cast<const T*>(b.x[i]), b.cnt[i], b.st[i],
+                 (blockIdx.x - b.first[i]) * (int64_t)blockDim.x + threadIdx.x, nblk * blockDim.x);
+}
+
 __device__ __forceinline__ double dkey_inv(unsigned long long k) {
   unsigned long long u = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
   return __longlong_as_double((long long)u);
+}
+
+__global__ void k_stats_finalize_multi(const __grid_constant__ MinmaxBatch b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= b.n) return;
+  FieldStats* st = b.st[i];
+  const double lo = dkey_inv(st->xmin_key), hi = dkey_inv(st->xmax_key);
+  const double M = fmax(fabs(lo), fabs(hi));
+  int G = 0;
+  if (M > 0) frexp(M, &G);
+  st->G = G;
 }
 
 __global__ void k_stats_finalize(FieldStats* st) {
@@ -290,17 +330,39 @@ __global__ void k_stats_finalize(FieldStats* st) {
 
 // fixed-point copy of the 2-grid (coarse points of level 0)
 template <typename T>
-__global__ void k_to_fixed(const T* __restrict__ x, FieldD f, const FieldStats* st,
-                           int64_t* __restrict__ xc) {
+__device__ __forceinline__ void to_fixed_body(const T* __restrict__ x, const FieldD& f, const FieldStats* st,
+                                              int64_t* __restrict__ xc, int64_t tid, int64_t nth) {
   const int G = st->G;
   const int64_t n = f.nc[0] * f.nc[1] * f.nc[2];
   const int s0 = f.n[0] > 1 ? 2 : 1;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = tid; i < n; i += nth) {
     const int64_t c2 = i % f.nc[2], t = i / f.nc[2];
     const int64_t c1 = t % f.nc[1], c0 = t / f.nc[1];
     xc[i] = fix_from<T>(x[((c0 * s0) * f.n[1] + 2 * c1) * f.n[2] + 2 * c2], G, f.fixb);
   }
+}
+
+template <typename T>
+__global__ void k_to_fixed(const T* __restrict__ x, FieldD f, const FieldStats* st, int64_t* __restrict__ xc) {
+  to_fixed_body<T>(x, f, st, xc, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
+struct ToFixedBatch {
+  int n;
+  int64_t first[kMaxBatchItems + 1];
+  const void* x[kMaxBatchItems];
+  FieldD f[kMaxBatchItems];
+  const FieldStats* st[kMaxBatchItems];
+  int64_t* xc[kMaxBatchItems];
+};
+static_assert(sizeof(ToFixedBatch) <= 32764, "kernel parameter block");
+
+template <typename T>
+__global__ void k_to_fixed_multi(const __grid_constant__ ToFixedBatch b) {
+  const int i = batch_find(b.first, b.n);
+  const int64_t nblk = b.first[i + 1] - b.first[i];
+  to_fixed_body<T>(reinterpret_cast<const T*>(b.x[i]), b.f[i], b.st[i], b.xc[i],
+                   (blockIdx.x - b.first[i]) * (int64_t)blockDim.x + threadIdx.x, nblk * blockDim.x);
 }
 
 // --------------------------------------------------------------------------
@@ -319,8 +381,9 @@ __device__ __forceinline__ LevelGrid level_grid(const FieldD& f, int level) {
 }
 
 // fixed-point levels >= 1: values from the 2-grid copy; raw = coarsest level
-__global__ void k_coef_fixed(FieldD f, int level, int raw, LatD lat, const int64_t* __restrict__ xc,
-                             int64_t* __restrict__ out, unsigned long long* vmax) {
+__device__ __forceinline__ void coef_fixed_body(const FieldD& f, int level, int raw, const LatD& lat,
+                                                const int64_t* __restrict__ xc, int64_t* __restrict__ out,
+                                                unsigned long long* vmax, int64_t tid, int64_t nth) {
   const LevelGrid g = level_grid(f, level);
   const int64_t half = g.s >> 1;
   const int64_t n = lat.count[0] * lat.count[1] * lat.row_pad;
@@ -328,8 +391,7 @@ __global__ void k_coef_fixed(FieldD f, int level, int raw, LatD lat, const int64
     return xc[((a0 * (f.n[0] > 1 ? half : 0)) * f.nc[1] + a1 * half) * f.nc[2] + a2 * half];
   };
   unsigned long long mx = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = tid; i < n; i += nth) {
     int64_t p[3];
     int64_t c = 0;
     if (lat_coords(lat, i, p)) {
@@ -343,6 +405,31 @@ __global__ void k_coef_fixed(FieldD f, int level, int raw, LatD lat, const int64
   }
   mx = warp_max(mx);
   if ((threadIdx.x & 31) == 0 && mx) atomicMax(vmax, mx);
+}
+
+__global__ void k_coef_fixed(FieldD f, int level, int raw, LatD lat, const int64_t* __restrict__ xc,
+                             int64_t* __restrict__ out, unsigned long long* vmax) {
+  coef_fixed_body(f, level, raw, lat, xc, out, vmax, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                  (int64_t)gridDim.x * blockDim.x);
+}
+
+struct CoefFixedBatch {
+  int n;
+  int64_t first[kMaxBatchItems + 1];
+  FieldD f[kMaxBatchItems];
+  LatD lat[kMaxBatchItems];
+  int level[kMaxBatchItems];
+  const int64_t* xc[kMaxBatchItems];
+  int64_t* out[kMaxBatchItems];
+  unsigned long long* vmax[kMaxBatchItems];
+};
+static_assert(sizeof(CoefFixedBatch) <= 32764, "kernel parameter block");
+
+__global__ void k_coef_fixed_multi(const __grid_constant__ CoefFixedBatch b) {
+  const int i = batch_find(b.first, b.n);
+  const int64_t nblk = b.first[i + 1] - b.first[i];
+  coef_fixed_body(b.f[i], b.level[i], 1, b.lat[i], b.xc[i], b.out[i], b.vmax[i],
+                  (blockIdx.x - b.first[i]) * (int64_t)blockDim.x + threadIdx.x, nblk * blockDim.x);
 }
 
 // level 0 in the field dtype.  compact != 0: write the region's compact
@@ -1202,6 +1289,133 @@ void launch_minmax(int vk, const void* x, int64_t n, FieldStats* st, cudaStream_
   if (vk == VK_F32) k_minmax<float><<<g, 512, 0, s>>>((const float*)x, n, st);
   else k_minmax<double><<<g, 512, 0, s>>>((const double*)x, n, st);
   k_stats_finalize<<<1, 1, 0, s>>>(st);
+}
+
+// zeroing (src null) or copying of many word ranges in one launch
+constexpr int kMaxWordsItems = 512;
+struct WordsBatch {
+  int n;
+  int64_t first[kMaxWordsItems + 1];
+  WordsItem it[kMaxWordsItems];
+};
+static_assert(sizeof(WordsBatch) <= 32764, "kernel parameter block");
+
+__global__ void __launch_bounds__(256) k_words_multi(const __grid_constant__ WordsBatch b) {
+  const int i = batch_find(b.first, b.n);
+  const WordsItem& t = b.it[i];
+  const int64_t nblk = b.first[i + 1] - b.first[i];
+  for (int64_t e = (blockIdx.x - b.first[i]) * (int64_t)blockDim.x + threadIdx.x; e < t.words;
+       e += nblk * (int64_t)blockDim.x)
+    t.dst[e] = t.src ? t.src[e] : 0u;
+}
+
+void launch_words_multi(const WordsItem* items, int n, cudaStream_t s) {
+  int k = 0;
+  while (k < n) {
+    WordsBatch b{};
+    int64_t tot = 0;
+    for (; k < n && b.n < kMaxWordsItems; k++) {
+      if (items[k].words <= 0) continue;
+      b.first[b.n] = tot;
+      b.it[b.n++] = items[k];
+      tot += std::min<int64_t>((items[k].words + 255) / 256, 148 * 4);
+    }
+    b.first[b.n] = tot;
+    if (!tot) continue;
+    count_launch();
+    k_words_multi<<<(unsigned)tot, 256, 0, s>>>(b);
+  }
+}
+
+// ---- batched launchers: items of one value kind, split into launches of at
+// most kMaxBatchItems; each item gets blocks in proportion to its size (a
+// single item takes the one-field kernel)
+void launch_to_fixed(int vk, const void* x, const FieldD& f, const FieldStats* st, int64_t* xc, cudaStream_t s);
+void launch_coef_fixed(const FieldD& f, int level, int raw, const LatD& lat, const int64_t* xc, int64_t* out,
+                       unsigned long long* vmax, cudaStream_t s);
+
+static int64_t blocks_for(int64_t n, int threads = 256, int64_t cap = 148 * 8) {
+  return std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, cap));
+}
+
+void launch_stats_multi(int vk, const void* const* xs, const int64_t* ns, FieldStats* const* sts, int n,
+                        cudaStream_t s) {
+  if (n == 1) {
+    launch_minmax(vk, xs[0], ns[0], sts[0], s);
+    return;
+  }
+  for (int k0 = 0; k0 < n; k0 += kMaxBatchItems) {
+    MinmaxBatch b{};
+    int64_t tot = 0;
+    for (int k = k0; k < n && b.n < kMaxBatchItems; k++) {
+      b.first[b.n] = tot;
+      b.x[b.n] = xs[k];
+      b.cnt[b.n] = ns[k];
+      b.st[b.n] = sts[k];
+      b.n++;
+      tot += blocks_for(ns[k], 512, 148 * 4);
+    }
+    b.first[b.n] = tot;
+    count_launch();
+    count_launch();
+    if (vk == VK_F32) k_minmax_multi<float><<<(unsigned)tot, 512, 0, s>>>(b);
+    else k_minmax_multi<double><<<(unsigned)tot, 512, 0, s>>>(b);
+    k_stats_finalize_multi<<<(b.n + 63) / 64, 64, 0, s>>>(b);
+  }
+}
+
+void launch_to_fixed_multi(int vk, const void* const* xs, const FieldD* fs, const FieldStats* const* sts,
+                           int64_t* const* xcs, int n, cudaStream_t s) {
+  if (n == 1) {
+    launch_to_fixed(vk, xs[0], fs[0], sts[0], xcs[0], s);
+    return;
+  }
+  for (int k0 = 0; k0 < n; k0 += kMaxBatchItems) {
+    ToFixedBatch b{};
+    int64_t tot = 0;
+    for (int k = k0; k < n && b.n < kMaxBatchItems; k++) {
+      b.first[b.n] = tot;
+      b.x[b.n] = xs[k];
+      b.f[b.n] = fs[k];
+      b.st[b.n] = sts[k];
+      b.xc[b.n] = xcs[k];
+      b.n++;
+      tot += blocks_for(fs[k].nc[0] * fs[k].nc[1] * fs[k].nc[2]);
+    }
+    b.first[b.n] = tot;
+    count_launch();
+    if (vk == VK_F32) k_to_fixed_multi<float><<<(unsigned)tot, 256, 0, s>>>(b);
+    else k_to_fixed_multi<double><<<(unsigned)tot, 256, 0, s>>>(b);
+  }
+}
+
+void launch_coarsest_multi(const FieldD* fs, const int* levels, const LatD* lats, const int64_t* const* xcs,
+                           int64_t* const* outs, unsigned long long* const* vmaxs, int n, cudaStream_t s) {
+  if (n == 1) {
+    launch_coef_fixed(fs[0], levels[0], 1, lats[0], xcs[0], outs[0], vmaxs[0], s);
+    return;
+  }
+  for (int k0 = 0; k0 < n; k0 += kMaxBatchItems) {
+    CoefFixedBatch b{};
+    int64_t tot = 0;
+    for (int k = k0; k < n && b.n < kMaxBatchItems; k++) {
+      const int64_t m = lats[k].count[0] * lats[k].count[1] * lats[k].row_pad;
+      if (!m) continue;
+      b.first[b.n] = tot;
+      b.f[b.n] = fs[k];
+      b.lat[b.n] = lats[k];
+      b.level[b.n] = levels[k];
+      b.xc[b.n] = xcs[k];
+      b.out[b.n] = outs[k];
+      b.vmax[b.n] = vmaxs[k];
+      b.n++;
+      tot += blocks_for(m);
+    }
+    b.first[b.n] = tot;
+    if (!tot) continue;
+    count_launch();
+    k_coef_fixed_multi<<<(unsigned)tot, 256, 0, s>>>(b);
+  }
 }
 
 void launch_to_fixed(int vk, const void* x, const FieldD& f, const FieldStats* st, int64_t* xc,

@@ -21,6 +21,10 @@
 #include <map>
 #include <cstdint>
 #include <type_traits>
+#include <vector>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "pcr_internal.h"
 
@@ -234,7 +238,7 @@ __device__ __forceinline__ void tile_pass(const TileArgs& a, A* __restrict__ S, 
 }
 
 template <typename A, int T0, int T1, int T2, int H0, int H>
-__global__ void __launch_bounds__(256) k_tile_interp(TileArgs a) {
+__device__ __forceinline__ void tile_interp_body(const TileArgs& a, unsigned bid) {
   // the x extent of the staged box starts 4 points (not H) before the tile so
   // that, for float fields whose rows are 16-byte multiples, every staged row
   // is loaded with aligned 16-byte vectors
@@ -243,7 +247,6 @@ __global__ void __launch_bounds__(256) k_tile_interp(TileArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   A* S = reinterpret_cast<A*>(smem_raw);
 
-  unsigned bid = blockIdx.x;
   const unsigned nt2 = (unsigned)a.ntiles[2], nt1 = (unsigned)a.ntiles[1];
   const int b2 = (int)(bid % nt2 + a.tlo[2]) * T2;
   bid /= nt2;
@@ -333,6 +336,20 @@ __global__ void __launch_bounds__(256) k_tile_interp(TileArgs a) {
                                                  retrieve, dst);
     __syncthreads();
   }
+}
+
+template <typename A, int T0, int T1, int T2, int H0, int H>
+__global__ void __launch_bounds__(256) k_tile_interp(TileArgs a) {
+  tile_interp_body<A, T0, T1, T2, H0, H>(a, blockIdx.x);
+}
+
+// Several independent level grids (the levels >= 1 of a refactor, or of
+// several fields) in one launch: the tiles of args[i] are blocks
+// first[i] .. first[i + 1] - 1.
+template <typename A, int T0, int T1, int T2, int H0, int H>
+__global__ void __launch_bounds__(256) k_tile_interp_multi(const __grid_constant__ TileBatch b) {
+  const int i = batch_find(b.first, b.n);
+  tile_interp_body<A, T0, T1, T2, H0, H>(b.args[i], blockIdx.x - (unsigned)b.first[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -649,42 +666,21 @@ __global__ void __launch_bounds__(128) k_decomp_blk(DecompArgs a) {
     }
 }
 
-// Decomposition only (same values as k_decomp_blk's forward direction):
-// the 2-grid of the block's neighbourhood stays in registers while S1/S2 are
-// written, then each S3 point is loaded and predicted on its own, so fewer
-// vectors are live at once and more CTAs fit on an SM.
-template <typename A, int VEC>
-__global__ void __launch_bounds__(128, 6) k_decomp_fwd(DecompArgs a) {
+// The forward decomposition of one 4 x 4 in-slice block (block indices ab,
+// bb) at VEC consecutive points along the normal (starting at k2): S1 / S2 /
+// S3 values written to their sub-level rows, their magnitudes folded into
+// mx.  `ld(r, du, dv)` loads the block's point (du, dv), du, dv in 0..4 (the
+// next 4-grid lines included); vu / vv flag the points inside the array.
+// Same arithmetic as k_decomp_blk's forward direction.
+template <typename A, int VEC, typename LD>
+__device__ __forceinline__ void decomp_fwd_block(const DecompArgs& a, unsigned ab, unsigned bb, int64_t k2,
+                                                 const bool* vu, const bool* vv, LD ld, A* mx) {
   using V = VecT<A, VEC>;
-  const unsigned nvec = (unsigned)a.ntiles[2], nbb = (unsigned)a.ntiles[1], nab = (unsigned)a.ntiles[0];
-  const unsigned item = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned iv = item % nvec + (unsigned)a.tlo[2], rest = item / nvec;
-  const unsigned bb = rest % nbb + (unsigned)a.tlo[1], ab = rest / nbb + (unsigned)a.tlo[0];
-  const bool live = rest / nbb < nab;
-  const int cu = (int)a.cnt[0], cv = (int)a.cnt[1];
-  const int64_t cw = a.cnt[2];
-  const int u0 = 4 * (int)ab, v0 = 4 * (int)bb;
-  const int64_t k2 = (int64_t)iv * VEC;
-  const A* __restrict__ comp = reinterpret_cast<const A*>(a.comp);
-  bool vu[5], vv[5];
-#pragma unroll
-  for (int d = 0; d < 5; d++) {
-    vu[d] = live && u0 + d < cu;
-    vv[d] = live && v0 + d < cv;
-  }
   auto srow = [&](int sl, int du, int dv) -> A* {
     const DecompSub& sb = a.subs[sl];
     const int64_t ui = ((int64_t)ab << (2 - blk_lu(sl))) + ((du - blk_su(sl)) >> blk_lu(sl));
     const int64_t vi = ((int64_t)bb << (2 - blk_lv(sl))) + ((dv - blk_sv(sl)) >> blk_lv(sl));
     return reinterpret_cast<A*>(sb.stage) + sb.base + (ui * sb.count[1] + vi) * sb.row_pad + k2;
-  };
-  auto ld = [&](int du, int dv) {
-    V r;
-    if (vu[du] && vv[dv]) vld<A, VEC>(r, comp + ((int64_t)(u0 + du) * cv + (v0 + dv)) * cw + k2);
-    else
-#pragma unroll
-      for (int e = 0; e < VEC; e++) r.v[e] = A(0);
-    return r;
   };
   auto lin = [](const V& p, const V& q) {
     V r;
@@ -697,8 +693,7 @@ __global__ void __launch_bounds__(128, 6) k_decomp_fwd(DecompArgs a) {
 #pragma unroll
   for (int i = 0; i < 3; i++)
 #pragma unroll
-    for (int j = 0; j < 3; j++) g[i][j] = ld(2 * i, 2 * j);
-  A mx[5] = {A(0), A(0), A(0), A(0), A(0)};
+    for (int j = 0; j < 3; j++) ld(g[i][j], 2 * i, 2 * j);
   auto emit = [&](int sl, int du, int dv, const V& x, const V& w, bool sub) {
     V d = x;
     if (sub)
@@ -739,23 +734,340 @@ __global__ void __launch_bounds__(128, 6) k_decomp_fwd(DecompArgs a) {
         if (!vv[dv + 1]) w = lo;
         else w = lin(lo, uc ? G(du, dv + 1) : pass_u1(du, dv + 1));
       }
-      emit(blk_slot(du, dv), du, dv, ld(du, dv), w, true);
+      V x;
+      ld(x, du, dv);
+      emit(blk_slot(du, dv), du, dv, x, w, true);
     }
+}
+
+// Decomposition only (same values as k_decomp_blk's forward direction):
+// the 2-grid of the block's neighbourhood stays in registers while S1/S2 are
+// written, then each S3 point is loaded and predicted on its own, so fewer
+// vectors are live at once and more CTAs fit on an SM.
+template <typename A, int VEC>
+__device__ __forceinline__ void decomp_fwd_body(const DecompArgs& a, unsigned item) {
+  using V = VecT<A, VEC>;
+  const unsigned nvec = (unsigned)a.ntiles[2], nbb = (unsigned)a.ntiles[1], nab = (unsigned)a.ntiles[0];
+  const unsigned iv = item % nvec + (unsigned)a.tlo[2], rest = item / nvec;
+  const unsigned bb = rest % nbb + (unsigned)a.tlo[1], ab = rest / nbb + (unsigned)a.tlo[0];
+  const bool live = rest / nbb < nab;
+  const int cu = (int)a.cnt[0], cv = (int)a.cnt[1];
+  const int64_t cw = a.cnt[2];
+  const int u0 = 4 * (int)ab, v0 = 4 * (int)bb;
+  const int64_t k2 = (int64_t)iv * VEC;
+  const A* __restrict__ comp = reinterpret_cast<const A*>(a.comp);
+  bool vu[5], vv[5];
+#pragma unroll
+  for (int d = 0; d < 5; d++) {
+    vu[d] = live && u0 + d < cu;
+    vv[d] = live && v0 + d < cv;
+  }
+  auto ld = [&](V& r, int du, int dv) {
+    if (vu[du] && vv[dv]) vld<A, VEC>(r, comp + ((int64_t)(u0 + du) * cv + (v0 + dv)) * cw + k2);
+    else
+#pragma unroll
+      for (int e = 0; e < VEC; e++) r.v[e] = A(0);
+  };
+  A mx[5] = {A(0), A(0), A(0), A(0), A(0)};
+  decomp_fwd_block<A, VEC>(a, ab, bb, k2, vu, vv, ld, mx);
 #pragma unroll
   for (int q = 0; q < 5; q++) push_max(a.subs[q].vmax, TAr<A>::mag(mx[q]), sizeof(A));
 }
 
-// zero the padding of every row of a padded lattice in a staging buffer
-template <typename A>
-__global__ void k_zero_pads(LatD lat, A* stage) {
-  const int64_t padw = lat.row_pad - lat.count[2];
-  const int64_t rows = lat.count[0] * lat.count[1];
-  const int64_t n = rows * padw;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / padw, c = i % padw;
-    stage[lat.base + r * lat.row_pad + lat.count[2] + c] = A(0);
+template <typename A, int VEC>
+__global__ void __launch_bounds__(128, 6) k_decomp_fwd(DecompArgs a) {
+  decomp_fwd_body<A, VEC>(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// the forward decomposition of several regions in one launch: item i owns
+// blocks first[i] .. first[i + 1] - 1
+constexpr int kMaxDecompFwdBatch = 40;
+struct DecompBatch {
+  int n;
+  int64_t first[kMaxDecompFwdBatch + 1];
+  DecompArgs a[kMaxDecompFwdBatch];
+};
+static_assert(sizeof(DecompBatch) <= 32764, "kernel parameter block");
+
+template <typename A, int VEC>
+__global__ void __launch_bounds__(128, 6) k_decomp_fwd_multi(const __grid_constant__ DecompBatch b) {
+  const int i = batch_find(b.first, b.n);
+  decomp_fwd_body<A, VEC>(b.a[i], (blockIdx.x - (unsigned)b.first[i]) * blockDim.x + threadIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Forward decomposition with TMA-staged tiles (FP32, slices normal to the
+// fastest axis, rows a multiple of 4 values).  A persistent CTA walks tiles
+// of 16 x 16 in-slice points x 32 points along the normal; each tile and its
+// next 4-grid lines (17 x 17 x 32 values) arrive in shared memory by one
+// cp.async.bulk.tensor copy, completed on an mbarrier, while the previous
+// tile is decomposed (two stages).  One thread per (4 x 4 block, normal
+// point): reads its 5 x 5 neighbourhood from shared memory (a warp = 32
+// consecutive normal points: conflict-free) and writes its 16 values to the
+// sub-level rows (a warp writes 128 contiguous bytes per row).  Waits are
+// bounded: on a timeout the CTA records it in *a.err, waits (bounded) for
+// the copy it still has in flight and returns.
+// ---------------------------------------------------------------------------
+constexpr int kDtU = 16, kDtV = 16, kDtW = 32;
+constexpr int kDtBox = (kDtU + 1) * (kDtV + 1) * kDtW;          // floats per stage
+constexpr int kDtSmem = 2 * kDtBox * 4 + 64 + 128;              // two stages + two mbarriers + alignment
+constexpr int kDtSpin = 1 << 22;                                // bounded mbarrier polls
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < kDtSpin; i++) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Tile sources of the kernel below: one region (Dt1), or the regions of a
+// batch of fields (DtBatch: item i owns tiles first[i] .. first[i + 1] - 1).
+struct Dt1 {
+  const CUtensorMap* tm;
+  const DecompArgs* a;
+  int ntu, ntv, ntw;
+  __device__ int item(int) const { return 0; }
+  __device__ int first(int) const { return 0; }
+  __device__ const CUtensorMap* map(int) const { return tm; }
+  __device__ const DecompArgs& args(int) const { return *a; }
+  __device__ int nv(int) const { return ntv; }
+  __device__ int nw(int) const { return ntw; }
+};
+
+constexpr int kMaxDecompBatch = 32;
+struct DecompTmaBatch {
+  CUtensorMap tm[kMaxDecompBatch];
+  DecompArgs a[kMaxDecompBatch];
+  int n;
+  int first[kMaxDecompBatch + 1];
+  int ntv[kMaxDecompBatch], ntw[kMaxDecompBatch];
+};
+
+struct DtBatch {
+  const DecompTmaBatch* b;
+  __device__ int item(int t) const {
+    int i = 0;
+    while (i + 1 < b->n && t >= b->first[i + 1]) i++;
+    return i;
+  }
+  __device__ int first(int i) const { return b->first[i]; }
+  __device__ const CUtensorMap* map(int i) const { return &b->tm[i]; }
+  __device__ const DecompArgs& args(int i) const { return b->a[i]; }
+  __device__ int nv(int i) const { return b->ntv[i]; }
+  __device__ int nw(int i) const { return b->ntw[i]; }
+};
+
+template <class S>
+__device__ __forceinline__ void decomp_tma_body(const S& src, int ntiles) {
+  extern __shared__ __align__(128) float dsm_raw[];
+  // stages on 128-byte boundaries (tensor copies land there)
+  float* dsm = dsm_raw + ((128 - (smem_u32(dsm_raw) & 127)) & 127) / 4;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + 2 * kDtBox);
+  const int tid = threadIdx.x;
+  if ((int)blockIdx.x >= ntiles) return;
+  const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int t, int buf) {   // thread 0
+    const int it = src.item(t), lt = t - src.first(it), ntw = src.nw(it), ntv = src.nv(it);
+    const int tw = lt % ntw, r = lt / ntw, tv = r % ntv, tu = r / ntv;
+    const uint32_t bar = buf ? bar1 : bar0;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(kDtBox * 4) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
+        ::"r"(smem_u32(dsm + buf * kDtBox)), "l"(reinterpret_cast<uint64_t>(src.map(it))), "r"(tw * kDtW),
+        "r"(tv * kDtV), "r"(tu * kDtU), "r"(bar)
+        : "memory");
+  };
+  float mx[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  int cur = src.item(blockIdx.x);   // item whose maxima mx holds
+  uint32_t par = 0;                 // bit b: phase of stage b's next completion
+  int buf = 0;
+  if (tid == 0) issue(blockIdx.x, 0);
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+    const int tn = t + gridDim.x;
+    if (tid == 0 && tn < ntiles) issue(tn, buf ^ 1);   // that stage was released by the last barrier
+    const bool ok = mbar_wait(buf ? bar1 : bar0, (par >> buf) & 1);
+    if (__syncthreads_or(!ok)) {   // the whole CTA gives up together
+      if (tid == 0) atomicExch(src.args(cur).err, 1);
+      if (tn < ntiles) mbar_wait(buf ? bar0 : bar1, (par >> (buf ^ 1)) & 1);
+      return;
+    }
+    par ^= 1u << buf;
+    const int it = src.item(t);
+    if (it != cur) {   // the maxima so far belong to the previous item
+#pragma unroll
+      for (int q = 0; q < 5; q++) {
+        push_max(src.args(cur).subs[q].vmax, TAr<float>::mag(mx[q]), 4);
+        mx[q] = 0.f;
+      }
+      cur = it;
+    }
+    const DecompArgs& a = src.args(it);
+    const int lt = t - src.first(it), ntw = src.nw(it), ntv = src.nv(it);
+    const int tw = lt % ntw, r = lt / ntw, tv = r % ntv, tu = r / ntv;
+    const int cu = (int)a.cnt[0], cv = (int)a.cnt[1];
+    const int64_t cw = a.cnt[2];
+    const float* st = dsm + buf * kDtBox;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      const int i = tid + 256 * k;
+      const int w = i & 31, blk = i >> 5;
+      const int ub = (blk >> 2) * 4, vb = (blk & 3) * 4;
+      const int U0 = tu * kDtU + ub, V0 = tv * kDtV + vb;
+      const int64_t W = (int64_t)tw * kDtW + w;
+      const bool live = U0 < cu && V0 < cv && W < cw;
+      bool vu[5], vv[5];
+#pragma unroll
+      for (int d = 0; d < 5; d++) {
+        vu[d] = live && U0 + d < cu;
+        vv[d] = live && V0 + d < cv;
+      }
+      auto ld = [&](VecT<float, 1>& rv, int du, int dv) {
+        rv.v[0] = st[((ub + du) * (kDtV + 1) + (vb + dv)) * kDtW + w];
+      };
+      if (live) decomp_fwd_block<float, 1>(a, (unsigned)(U0 >> 2), (unsigned)(V0 >> 2), W, vu, vv, ld, mx);
+    }
+    __syncthreads();   // every read of this stage done: it may be refilled
+  }
+#pragma unroll
+  for (int q = 0; q < 5; q++) push_max(src.args(cur).subs[q].vmax, TAr<float>::mag(mx[q]), 4);
+}
+
+__global__ void __launch_bounds__(256, 2) k_decomp_tma(const __grid_constant__ CUtensorMap tm,
+                                                       const __grid_constant__ DecompArgs a, int ntu, int ntv,
+                                                       int ntw) {
+  decomp_tma_body(Dt1{&tm, &a, ntu, ntv, ntw}, ntu * ntv * ntw);
+}
+
+__global__ void __launch_bounds__(256, 2) k_decomp_tma_multi(const __grid_constant__ DecompTmaBatch b) {
+  decomp_tma_body(DtBatch{&b}, b.first[b.n]);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// the TMA form applies to a whole array, FP32, slices normal to the fastest
+// axis, 16-byte row strides and a tensor map the driver accepts
+static bool decomp_tma_applies(const DecompArgs& a) {
+  return !a.retrieve && a.n == 2 && a.bhi[0] == 0 && a.cnt[2] % 4 == 0 && a.err && ((uintptr_t)a.comp & 15) == 0;
+}
+
+// tensor map of a region's compact array: boxes of kDtW x (kDtV + 1) x
+// (kDtU + 1) values, zero fill beyond the array
+static bool decomp_tensor_map(const DecompArgs& a, CUtensorMap& tm) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const int64_t cu = a.cnt[0], cv = a.cnt[1], cw = a.cnt[2];
+  const cuuint64_t gdim[3] = {(cuuint64_t)cw, (cuuint64_t)cv, (cuuint64_t)cu};
+  const cuuint64_t gstride[2] = {(cuuint64_t)cw * 4, (cuuint64_t)(cw * cv) * 4};
+  const cuuint32_t box[3] = {kDtW, kDtV + 1, kDtU + 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.comp, gdim, gstride, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// resident CTAs of the TMA kernels on this device (both forms take the same
+// shared memory and registers per CTA)
+static int decomp_tma_grid_cap() {
+  static int grid_cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& per_dev = grid_cache[dev & 63];
+  if (per_dev == 0) {
+    int sms = 0, per = 0, per_m = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_decomp_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kDtSmem);
+    cudaFuncSetAttribute(k_decomp_tma_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, kDtSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_decomp_tma, 256, kDtSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_m, k_decomp_tma_multi, 256, kDtSmem);
+    per_dev = std::max(1, sms * std::max(std::min(per, per_m), 1));
+  }
+  return per_dev;
+}
+
+static bool run_decomp_tma(const DecompArgs& a, cudaStream_t s) {
+  if (!decomp_tma_applies(a)) return false;
+  const int64_t cu = a.cnt[0], cv = a.cnt[1], cw = a.cnt[2];
+  if (cu <= 0 || cv <= 0 || cw <= 0) return true;   // nothing to do
+  CUtensorMap tm;
+  if (!decomp_tensor_map(a, tm)) return false;
+  const int ntu = (int)((cu + kDtU - 1) / kDtU), ntv = (int)((cv + kDtV - 1) / kDtV),
+            ntw = (int)((cw + kDtW - 1) / kDtW);
+  const int64_t ntiles = (int64_t)ntu * ntv * ntw;
+  const int grid = (int)std::min<int64_t>(ntiles, decomp_tma_grid_cap());
+  count_launch();
+  k_decomp_tma<<<grid, 256, kDtSmem, s>>>(tm, a, ntu, ntv, ntw);
+  return true;
+}
+
+// several regions (of one field or of a batch's fields) in shared TMA
+// launches; items the TMA form does not take go one by one
+static void run_decomp_tma_multi(const DecompArgs* das, int n, cudaStream_t s, std::vector<int>& rest) {
+  std::vector<int> tk;
+  for (int k = 0; k < n; k++) {
+    if (decomp_tma_applies(das[k])) tk.push_back(k);
+    else rest.push_back(k);
+  }
+  if (tk.size() == 1) {
+    if (!run_decomp_tma(das[tk[0]], s)) rest.push_back(tk[0]);
+    return;
+  }
+  static_assert(sizeof(DecompTmaBatch) <= 32764, "kernel parameter block");
+  size_t k = 0;
+  while (k < tk.size()) {
+    DecompTmaBatch b{};
+    int tot = 0;
+    for (; k < tk.size() && b.n < kMaxDecompBatch; k++) {
+      const DecompArgs& a = das[tk[k]];
+      const int64_t cu = a.cnt[0], cv = a.cnt[1], cw = a.cnt[2];
+      if (cu <= 0 || cv <= 0 || cw <= 0) continue;
+      if (!decomp_tensor_map(a, b.tm[b.n])) {
+        rest.push_back(tk[k]);
+        continue;
+      }
+      const int ntu = (int)((cu + kDtU - 1) / kDtU), ntv = (int)((cv + kDtV - 1) / kDtV),
+                ntw = (int)((cw + kDtW - 1) / kDtW);
+      b.a[b.n] = a;
+      b.first[b.n] = tot;
+      b.ntv[b.n] = ntv;
+      b.ntw[b.n] = ntw;
+      b.n++;
+      tot += ntu * ntv * ntw;
+    }
+    b.first[b.n] = tot;
+    if (!tot) continue;
+    count_launch();
+    k_decomp_tma_multi<<<std::min(tot, decomp_tma_grid_cap()), 256, kDtSmem, s>>>(b);
   }
 }
+
 
 // max |c| over a region's compact array (level-0 rounding term)
 // running maximum of |c|: floating point in the value type, fixed point as
@@ -804,7 +1116,7 @@ template <> struct MaxAbs<int64_t> {
 // region 3 (0,0,1) step (1,1,2) (checked by the launcher).
 // Arithmetic: the 1-D rules of the general tile kernel (same expressions).
 template <typename A, int DEG, bool RET, bool IPR, int T1, int T2>
-__global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
+__device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, unsigned bid) {
   constexpr int NT = 256;
   constexpr int HR = DEG - 1;            // reach beyond the tile along i1, i2
   constexpr int PR = T1 + 2 * HR + 1;    // Pe rows: i1 in [b1 - HR, b1 + T1 + HR]
@@ -836,7 +1148,6 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
 
   const int m0 = (int)a.m[0], m1 = (int)a.m[1], m2 = (int)a.m[2];
   const int64_t s0 = a.stride[0], s1 = a.stride[1];
-  unsigned bid = blockIdx.x;
   const unsigned nt2 = (unsigned)a.ntiles[2], nt1 = (unsigned)a.ntiles[1];
   const int b2 = (int)(bid % nt2 + a.tlo[2]) * T2;
   bid /= nt2;
@@ -1266,6 +1577,27 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
   }
 }
 
+template <typename A, int DEG, bool RET, bool IPR, int T1, int T2>
+__global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
+  level0_march_body<A, DEG, RET, IPR, T1, T2>(a, zc, blockIdx.x);
+}
+
+// the plane-marching kernel over several fields (or fixed-point levels) in
+// one launch: item i owns blocks first[i] .. first[i + 1] - 1
+struct MarchBatch {
+  int n;
+  int64_t first[kMaxTileBatch + 1];
+  int zc[kMaxTileBatch];
+  TileArgs args[kMaxTileBatch];
+};
+static_assert(sizeof(MarchBatch) <= 32764 && sizeof(TileBatch) <= 32764, "kernel parameter block");
+
+template <typename A, int DEG, bool RET, bool IPR, int T1, int T2>
+__global__ void __launch_bounds__(256, 4) k_level0_march_multi(const __grid_constant__ MarchBatch b) {
+  const int i = batch_find(b.first, b.n);
+  level0_march_body<A, DEG, RET, IPR, T1, T2>(b.args[i], b.zc[i], blockIdx.x - (unsigned)b.first[i]);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -1290,6 +1622,58 @@ static void run_tile(const TileArgs& a0, cudaStream_t s) {
   k_tile_interp<A, T0, T1, T2, H0, H><<<(unsigned)nb, 256, smem, s>>>(a);
 }
 
+// independent grids of one kernel shape in as few launches as the batch
+// parameter block allows
+template <typename A, int T0, int T1, int T2, int H0, int H>
+static void run_tile_multi(const std::vector<TileArgs>& v, cudaStream_t s) {
+  const size_t smem = sizeof(A) * (T0 + 2 * H0) * (T1 + 2 * H) * (T2 + 8);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tile_interp_multi<A, T0, T1, T2, H0, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr = true;
+  }
+  const int64_t T[3] = {T0, T1, T2};
+  size_t k = 0;
+  while (k < v.size()) {
+    TileBatch b{};
+    int64_t tot = 0;
+    for (; k < v.size() && b.n < kMaxTileBatch; k++) {
+      TileArgs a = v[k];
+      int64_t nb = 1;
+      for (int q = 0; q < 3; q++) {
+        const int64_t lo = a.bhi[0] ? a.blo[q] : 0, hi = a.bhi[0] ? a.bhi[q] : a.m[q];
+        a.tlo[q] = lo / T[q];
+        a.ntiles[q] = hi > lo ? (hi + T[q] - 1) / T[q] - a.tlo[q] : 0;
+        nb *= a.ntiles[q];
+      }
+      if (!nb) continue;
+      b.first[b.n] = tot;
+      b.args[b.n++] = a;
+      tot += nb;
+    }
+    b.first[b.n] = tot;
+    if (!tot) continue;
+    count_launch();
+    k_tile_interp_multi<A, T0, T1, T2, H0, H><<<(unsigned)tot, 256, smem, s>>>(b);
+  }
+}
+
+template <typename A>
+static void run_tile_kind_multi(const std::vector<TileArgs>& all, cudaStream_t s) {
+  std::vector<TileArgs> g[2][2];   // [3-D][cubic]
+  for (const TileArgs& a : all) g[a.m[0] > 1][a.degree == 3].push_back(a);
+  constexpr bool wide = sizeof(A) == 4;
+  if (!g[1][1].empty()) {
+    if (wide) run_tile_multi<A, 8, 8, 64, 3, 3>(g[1][1], s); else run_tile_multi<A, 4, 4, 64, 3, 3>(g[1][1], s);
+  }
+  if (!g[1][0].empty()) {
+    if (wide) run_tile_multi<A, 8, 8, 64, 1, 1>(g[1][0], s); else run_tile_multi<A, 4, 4, 64, 1, 1>(g[1][0], s);
+  }
+  if (!g[0][1].empty()) run_tile_multi<A, 1, 32, 64, 0, 3>(g[0][1], s);
+  if (!g[0][0].empty()) run_tile_multi<A, 1, 32, 64, 0, 1>(g[0][0], s);
+}
+
 template <typename A>
 static void run_tile_kind(const TileArgs& a, cudaStream_t s) {
   const bool is3 = a.m[0] > 1;
@@ -1306,12 +1690,14 @@ static void run_tile_kind(const TileArgs& a, cudaStream_t s) {
   }
 }
 
-template <typename A, int DEG, bool RET, bool PR, int T1, int T2>
-static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force) {
-  TileArgs a = a0;
+// grid of the plane-marching kernel for one level: column tiles covering the
+// box (or the grid) and chunks of zc planes; returns the block count (0:
+// nothing to do) with a.ntiles / a.tlo set
+template <int T1, int T2>
+static int64_t march_grid(TileArgs& a, int zc_force, int& zc_out) {
   const bool box = a.bhi[0] != 0;
   const int64_t T[3] = {1, T1, T2};
-  for (int k = 1; k < 3; k++) {   // column tiles covering the box (or the grid)
+  for (int k = 1; k < 3; k++) {
     const int64_t lo = box ? a.blo[k] : 0, hi = box ? a.bhi[k] : a.m[k];
     a.tlo[k] = lo / T[k];
     a.ntiles[k] = hi > lo ? (hi + T[k] - 1) / T[k] - a.tlo[k] : 0;
@@ -1320,8 +1706,7 @@ static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force) {
   // planes)
   const int64_t zlo = box ? (a.blo[0] & ~int64_t(1)) : 0, zend = box ? a.bhi[0] : a.m[0];
   a.tlo[0] = zlo;
-  if (zend <= zlo || !a.ntiles[1] || !a.ntiles[2]) return;
-  count_launch();
+  if (zend <= zlo || !a.ntiles[1] || !a.ntiles[2]) return 0;
   // plane chunks (default): about eight full waves of 4 CTAs per SM, so the
   // last wave is not a sparse tail; at least 8 planes so the ring warm-up
   // (three coarse-plane loads) stays a small share of a chunk
@@ -1335,12 +1720,59 @@ static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force) {
     zc = std::max<int64_t>(8, (zc + 1) & ~int64_t(1));
   }
   a.ntiles[0] = (zend - zlo + zc - 1) / zc;
+  zc_out = (int)zc;
+  return a.ntiles[0] * cols;
+}
+
+template <typename A, int DEG, bool RET, bool PR, int T1, int T2>
+static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force) {
+  TileArgs a = a0;
+  int zc = 0;
+  const int64_t nb = march_grid<T1, T2>(a, zc_force, zc);
+  if (!nb) return;
+  count_launch();
   static bool attr = false;
   if (!attr) {   // shared memory for several CTAs per SM
     cudaFuncSetAttribute(k_level0_march<A, DEG, RET, PR, T1, T2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr = true;
   }
-  k_level0_march<A, DEG, RET, PR, T1, T2><<<(unsigned)(a.ntiles[0] * cols), 256, 0, s>>>(a, (int)zc);
+  k_level0_march<A, DEG, RET, PR, T1, T2><<<(unsigned)nb, 256, 0, s>>>(a, zc);
+}
+
+// levels of one marching-kernel shape (value kind, degree, direction,
+// interpolation) in shared launches; zcs[i]: the plane chunk of item i
+// (<= 0: the default); a single item takes the one-level kernel
+template <typename A, int DEG, bool RET, bool PR, int T1, int T2>
+static void run_level0_march_multi(const std::vector<TileArgs>& v, const std::vector<int>& zcs, cudaStream_t s) {
+  if (v.size() == 1) {
+    run_level0_march<A, DEG, RET, PR, T1, T2>(v[0], s, zcs[0]);
+    return;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_level0_march_multi<A, DEG, RET, PR, T1, T2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         100);
+    attr = true;
+  }
+  size_t k = 0;
+  while (k < v.size()) {
+    MarchBatch b{};
+    int64_t tot = 0;
+    for (; k < v.size() && b.n < kMaxTileBatch; k++) {
+      TileArgs a = v[k];
+      int zc = 0;
+      const int64_t nb = march_grid<T1, T2>(a, zcs[k], zc);
+      if (!nb) continue;
+      b.first[b.n] = tot;
+      b.zc[b.n] = zc;
+      b.args[b.n++] = a;
+      tot += nb;
+    }
+    b.first[b.n] = tot;
+    if (!tot) continue;
+    count_launch();
+    k_level0_march_multi<A, DEG, RET, PR, T1, T2><<<(unsigned)tot, 256, 0, s>>>(b);
+  }
 }
 
 // the plane-marching kernel covers level 0 of 3-D per-level schemes in a
@@ -1456,9 +1888,10 @@ TuneVal tune(const TileArgs& a, cudaStream_t s) {
   return best;
 }
 
+// the schedule of a level the marching kernel applies to (timing the
+// candidates first when tuning is on and the level is untuned)
 template <typename A>
-bool launch_tuned(int vk, const TileArgs& a, cudaStream_t s) {
-  if (!march_applies<A>(a)) return false;
+int tuned_choice(int vk, const TileArgs& a, cudaStream_t s) {
   const TuneKey key{vk, a.retrieve, a.degree, a.interp, a.m[0], a.m[1], a.m[2]};
   int choice = -1;
   bool have = false;
@@ -1480,8 +1913,14 @@ bool launch_tuned(int vk, const TileArgs& a, cudaStream_t s) {
       choice = v.choice;
     }
   }
-  run_choice<A>(a, s, choice);
-  return true;
+  return choice;
+}
+
+template <typename A>
+int launch_tuned(int vk, const TileArgs& a, cudaStream_t s) {
+  if (!march_applies<A>(a)) return -1;
+  run_choice<A>(a, s, tuned_choice<A>(vk, a, s));
+  return 1;
 }
 }  // namespace
 
@@ -1510,10 +1949,46 @@ void clear_autotune() {
   g_tune.clear();
 }
 
+// independent grids (no grid reads another's output): those the schedule
+// gives the marching kernel in shared launches per kernel shape, the rest in
+// shared launches of the tile kernel
+template <typename A>
+static void launch_multi_kind(int vk, const TileArgs* args, int n, cudaStream_t s) {
+  constexpr int T1 = 16, T2 = sizeof(A) == 4 ? 128 : 64;
+  std::vector<TileArgs> rest, mv[2][2];   // marching refactor levels [cubic][per-region]
+  std::vector<int> mz[2][2];
+  for (int i = 0; i < n; i++) {
+    const TileArgs& a = args[i];
+    const int c = march_applies<A>(a) ? tuned_choice<A>(vk, a, s) : 0;
+    if (c == 0) {
+      rest.push_back(a);
+    } else if (a.retrieve) {
+      march_launch<A>(a, s, c);
+    } else {
+      mv[a.degree == 3][a.interp != 0].push_back(a);
+      mz[a.degree == 3][a.interp != 0].push_back(c);
+    }
+  }
+  if (!mv[1][0].empty()) run_level0_march_multi<A, 3, false, false, T1, T2>(mv[1][0], mz[1][0], s);
+  if (!mv[1][1].empty()) run_level0_march_multi<A, 3, false, true, T1, T2>(mv[1][1], mz[1][1], s);
+  if (!mv[0][0].empty()) run_level0_march_multi<A, 1, false, false, T1, T2>(mv[0][0], mz[0][0], s);
+  if (!mv[0][1].empty()) run_level0_march_multi<A, 1, false, true, T1, T2>(mv[0][1], mz[0][1], s);
+  run_tile_kind_multi<A>(rest, s);
+}
+
+void launch_tile_interp_multi(int vk, const TileArgs* args, int n, cudaStream_t s) {
+  if (n <= 0) return;
+  if (vk == VK_F32) launch_multi_kind<float>(vk, args, n, s);
+  else if (vk == VK_F64) launch_multi_kind<double>(vk, args, n, s);
+  else launch_multi_kind<int64_t>(vk, args, n, s);
+}
+
 void launch_tile_interp(int vk, const TileArgs& a, cudaStream_t s) {
-  if (vk == VK_F32 && launch_tuned<float>(vk, a, s)) return;
-  if (vk == VK_F64 && launch_tuned<double>(vk, a, s)) return;
-  if (vk == VK_FIX && launch_tuned<int64_t>(vk, a, s)) return;   // a contiguous fixed-point level (level 1)
+  int r = -1;
+  if (vk == VK_F32) r = launch_tuned<float>(vk, a, s);
+  else if (vk == VK_F64) r = launch_tuned<double>(vk, a, s);
+  else if (vk == VK_FIX) r = launch_tuned<int64_t>(vk, a, s);   // a contiguous fixed-point level (level 1)
+  if (r > 0) return;
   if (vk == VK_F32) run_tile_kind<float>(a, s);
   else if (vk == VK_F64) run_tile_kind<double>(a, s);
   else run_tile_kind<int64_t>(a, s);
@@ -1536,17 +2011,45 @@ static void run_decomp(const DecompArgs& a0, cudaStream_t s) {
   k_tile_decomp<A, N, T0, T1, T2><<<(unsigned)nb, 256, smem, s>>>(a);
 }
 
-template <typename A, int VEC>
-static void run_decomp_blk(const DecompArgs& a0, cudaStream_t s) {
-  DecompArgs a = a0;
+// 4 x 4 blocks and vectors covering the box (or the array): sets a.tlo and
+// a.ntiles, returns the thread items
+template <int VEC>
+static int64_t decomp_blk_grid(DecompArgs& a) {
   const bool box = a.bhi[0] != 0;
   const int64_t T[3] = {4, 4, VEC};
-  for (int k = 0; k < 3; k++) {   // 4 x 4 blocks and vectors covering the box (or the array)
+  for (int k = 0; k < 3; k++) {
     const int64_t lo = box ? a.blo[k] : 0, hi = box ? std::min(a.bhi[k], a.cnt[k]) : a.cnt[k];
     a.tlo[k] = lo / T[k];
     a.ntiles[k] = hi > lo ? (k == 2 ? hi / T[k] + (hi % T[k] != 0) : (hi + T[k] - 1) / T[k]) - a.tlo[k] : 0;
   }
-  const int64_t items = a.ntiles[0] * a.ntiles[1] * a.ntiles[2];
+  return a.ntiles[0] * a.ntiles[1] * a.ntiles[2];
+}
+
+template <typename A, int VEC>
+static void run_decomp_fwd_multi(const std::vector<DecompArgs>& v, cudaStream_t s) {
+  size_t k = 0;
+  while (k < v.size()) {
+    DecompBatch b{};
+    int64_t tot = 0;
+    for (; k < v.size() && b.n < kMaxDecompFwdBatch; k++) {
+      DecompArgs a = v[k];
+      const int64_t items = decomp_blk_grid<VEC>(a);
+      if (!items) continue;
+      b.first[b.n] = tot;
+      b.a[b.n++] = a;
+      tot += (items + 127) / 128;
+    }
+    b.first[b.n] = tot;
+    if (!tot) continue;
+    count_launch();
+    k_decomp_fwd_multi<A, VEC><<<(unsigned)tot, 128, 0, s>>>(b);
+  }
+}
+
+template <typename A, int VEC>
+static void run_decomp_blk(const DecompArgs& a0, cudaStream_t s) {
+  DecompArgs a = a0;
+  const int64_t items = decomp_blk_grid<VEC>(a);
   if (items == 0) return;
   count_launch();
   if (a.retrieve) k_decomp_blk<A, VEC><<<(unsigned)((items + 127) / 128), 128, 0, s>>>(a);
@@ -1556,7 +2059,9 @@ static void run_decomp_blk(const DecompArgs& a0, cudaStream_t s) {
 void launch_tile_decomp(int vk, const DecompArgs& a, cudaStream_t s) {
   // tiles are multiples of 4 along the in-slice axes
   if (vk == VK_F32) {
-    if (a.n == 2 && a.cnt[2] % 4 == 0) run_decomp_blk<float, 4>(a, s);
+    if (a.n == 2 && a.cnt[2] % 4 == 0) {
+      if (!run_decomp_tma(a, s)) run_decomp_blk<float, 4>(a, s);
+    }
     else if (a.n == 2) run_decomp_blk<float, 1>(a, s);
     else if (a.n == 1) run_decomp<float, 1, 16, 4, 64>(a, s);
     else run_decomp<float, 0, 4, 16, 64>(a, s);
@@ -1568,16 +2073,86 @@ void launch_tile_decomp(int vk, const DecompArgs& a, cudaStream_t s) {
   }
 }
 
-void launch_zero_pads(int vk, const LatD& lat, void* stage, cudaStream_t s) {
-  const int64_t n = lat.count[0] * lat.count[1] * (lat.row_pad - lat.count[2]);
-  if (n <= 0) return;
-  count_launch();
-  int g = (int)((n + 255) / 256);
-  if (g > 148 * 16) g = 148 * 16;
-  if (vk == VK_F32) k_zero_pads<float><<<g, 256, 0, s>>>(lat, (float*)stage);
-  else if (vk == VK_F64) k_zero_pads<double><<<g, 256, 0, s>>>(lat, (double*)stage);
-  else k_zero_pads<int64_t><<<g, 256, 0, s>>>(lat, (int64_t*)stage);
+// forward decompositions of several regions: the TMA form's in shared
+// launches, the other slices-normal-to-the-fastest-axis ones in shared
+// launches per value type and vector width, the rest one by one
+void launch_tile_decomp_multi(int vk, const DecompArgs* das, int n, cudaStream_t s) {
+  std::vector<int> rest;
+  if (vk == VK_F32) run_decomp_tma_multi(das, n, s, rest);
+  else
+    for (int k = 0; k < n; k++) rest.push_back(k);
+  std::vector<DecompArgs> g[4];   // F32 x4, F32 x1, F64 x2, F64 x1
+  std::vector<int> one;
+  for (int k : rest) {
+    const DecompArgs& a = das[k];
+    if (a.retrieve || a.n != 2) one.push_back(k);
+    else if (vk == VK_F32) g[a.cnt[2] % 4 == 0 ? 0 : 1].push_back(a);
+    else g[a.cnt[2] % 2 == 0 ? 2 : 3].push_back(a);
+  }
+  for (int q = 0; q < 4; q++) {
+    if (g[q].size() == 1) {
+      launch_tile_decomp(vk, g[q][0], s);
+    } else if (!g[q].empty()) {
+      if (q == 0) run_decomp_fwd_multi<float, 4>(g[q], s);
+      else if (q == 1) run_decomp_fwd_multi<float, 1>(g[q], s);
+      else if (q == 2) run_decomp_fwd_multi<double, 2>(g[q], s);
+      else run_decomp_fwd_multi<double, 1>(g[q], s);
+    }
+  }
+  for (int k : one) launch_tile_decomp(vk, das[k], s);
 }
+
+// the row padding of many lattices (any value kinds) zeroed in one launch:
+// item i owns blocks first[i] .. first[i + 1] - 1 and writes 32-bit words
+constexpr int kMaxPadItems = 512;
+struct PadItem {
+  uint32_t* p;         // first padding word of the lattice's first row
+  int64_t rows;        // rows of the lattice
+  int64_t row_words;   // words from one row's padding to the next
+  int64_t padw;        // padding words per row
+};
+struct PadBatch {
+  int n;
+  int64_t first[kMaxPadItems + 1];
+  PadItem it[kMaxPadItems];
+};
+
+__global__ void __launch_bounds__(256) k_zero_pads_multi(const __grid_constant__ PadBatch b) {
+  const int lo = batch_find(b.first, b.n);
+  const PadItem& t = b.it[lo];
+  const int64_t n = t.rows * t.padw;
+  const int64_t nblk = b.first[lo + 1] - b.first[lo];
+  for (int64_t e = (blockIdx.x - b.first[lo]) * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += nblk * (int64_t)blockDim.x) {
+    const int64_t r = e / t.padw, c = e % t.padw;
+    t.p[r * t.row_words + c] = 0u;
+  }
+}
+
+void launch_zero_pads_multi(const int* vks, const LatD* lats, void* const* stages, int n, cudaStream_t s) {
+  static_assert(sizeof(PadBatch) <= 32764, "kernel parameter block");
+  int k = 0;
+  while (k < n) {
+    PadBatch b{};
+    int64_t tot = 0;
+    for (; k < n && b.n < kMaxPadItems; k++) {
+      const LatD& l = lats[k];
+      const int w = vks[k] == VK_F32 ? 1 : 2;
+      const int64_t padw = (l.row_pad - l.count[2]) * w, rows = l.count[0] * l.count[1];
+      if (padw <= 0 || rows <= 0) continue;
+      const int64_t blocks = std::min<int64_t>((rows * padw + 255) / 256, 148 * 4);
+      b.first[b.n] = tot;
+      b.it[b.n] = {reinterpret_cast<uint32_t*>(stages[k]) + (l.base + l.count[2]) * w, rows, l.row_pad * w, padw};
+      b.n++;
+      tot += blocks;
+    }
+    b.first[b.n] = tot;
+    if (!tot) continue;
+    count_launch();
+    k_zero_pads_multi<<<(unsigned)tot, 256, 0, s>>>(b);
+  }
+}
+
 
 
 }  // namespace pcr
