@@ -60,6 +60,7 @@ void launch_to_fixed_multi(int vk, const void* const* xs, const FieldD* fs, cons
 void launch_coarsest_multi(const FieldD* fs, const int* levels, const LatD* lats, const int64_t* const* xcs,
                            int64_t* const* outs, unsigned long long* const* vmaxs, int n, cudaStream_t s);
 void launch_words_multi(const WordsItem* items, int n, cudaStream_t s);
+void launch_finalize_multi(FieldStats* const* sts, int n, cudaStream_t s);
 }  // namespace pcr
 
 using namespace pcr;
@@ -1809,13 +1810,15 @@ static pcr_status prepare_refactor(pcr_handle* h, const void* d_field, Scratch& 
 static void enqueue_stages(const std::vector<FieldWork>& ws, cudaStream_t s) {
   const int vks[2] = {VK_F32, VK_F64};
   {
+    // fields without a level 0 (L = 1): a statistics pass of their own; the
+    // others' statistics are taken while their level 0 is predicted
     Prof pf("stats", s);
     for (int vk : vks) {
       std::vector<const void*> xs;
       std::vector<int64_t> ns;
       std::vector<FieldStats*> sts;
       for (const FieldWork& w : ws)
-        if (w.h->vk == vk) {
+        if (w.h->vk == vk && !w.has_l0) {
           xs.push_back(w.x);
           ns.push_back(w.n);
           sts.push_back(w.st);
@@ -1828,9 +1831,16 @@ static void enqueue_stages(const std::vector<FieldWork>& ws, cudaStream_t s) {
     for (int vk : vks) {
       std::vector<TileArgs> l0;
       for (const FieldWork& w : ws)
-        if (w.h->vk == vk && w.has_l0) l0.push_back(w.l0);
+        if (w.h->vk == vk && w.has_l0) {
+          l0.push_back(w.l0);
+          l0.back().stats = w.st;
+        }
       launch_tile_interp_multi(vk, l0.data(), (int)l0.size(), s);
     }
+    std::vector<FieldStats*> fin;
+    for (const FieldWork& w : ws)
+      if (w.has_l0) fin.push_back(w.st);
+    if (!fin.empty()) launch_finalize_multi(fin.data(), (int)fin.size(), s);
   }
   {
     Prof pf("to_fixed", s);

@@ -84,6 +84,8 @@ struct TileRegion {
   int vmax_double;            // 1: the slot holds the bits of a double (field statistics' max |c|)
 };
 
+struct FieldStats;
+
 // arguments of the tiled interpolation kernel (one level, all regions)
 struct TileArgs {
   int64_t m[3];        // level-grid lengths (1 along an inactive axis)
@@ -101,6 +103,10 @@ struct TileArgs {
   int64_t blo[3], bhi[3];
   // set by the launchers: first tile per axis (plane-marching: first plane)
   int64_t tlo[3];
+  // refactor of level 0: the field's statistics (min, max, finiteness),
+  // taken by the plane-marching kernel as it reads the field, else by a
+  // separate pass the launcher adds (null: not wanted)
+  FieldStats* stats;
 };
 
 // items of one batched (multi-field) launch of the per-field kernels
@@ -130,7 +136,7 @@ __device__ __forceinline__ int batch_find(const int64_t* first, int n) {
 
 // independent tile-kernel launches fused into one (the refactor's levels
 // >= 1, or one level of several fields); first[i]: first block of args[i]
-constexpr int kMaxTileBatch = 56;
+constexpr int kMaxTileBatch = 54;
 struct TileBatch {
   int n;
   int64_t first[kMaxTileBatch + 1];
@@ -178,6 +184,62 @@ struct FieldStats {
   int bad;                                 // non-finite input seen
   int timeout;                             // a bounded device wait gave up
 };
+
+#ifdef __CUDACC__
+// fixed-point value -> value type (v * scale, scale a power of two)
+template <typename T> __device__ __forceinline__ T from_fix(int64_t v, T scale);
+template <> __device__ __forceinline__ float from_fix<float>(int64_t v, float scale) {
+  return __fmul_rn(__ll2float_rn(v), scale);
+}
+template <> __device__ __forceinline__ double from_fix<double>(int64_t v, double scale) {
+  return __dmul_rn(__ll2double_rn(v), scale);
+}
+
+// order-preserving key of a double (unsigned comparison = numeric order)
+__device__ __forceinline__ unsigned long long dkey(double x) {
+  unsigned long long u = __double_as_longlong(x);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// a block's minimum, maximum and non-finite flag merged into the field's
+// statistics; every thread of the block calls it
+__device__ __forceinline__ void stats_push_block(FieldStats* st, double lo, double hi, int bad) {
+  __shared__ unsigned long long rlo[32], rhi[32];
+  __shared__ int rbad;
+  unsigned long long klo = dkey(lo), khi = dkey(hi);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xFFFFFFFFu, klo, o), b = __shfl_xor_sync(0xFFFFFFFFu, khi, o);
+    klo = a < klo ? a : klo;
+    khi = b > khi ? b : khi;
+  }
+  bad = __any_sync(0xFFFFFFFFu, bad);
+  if (threadIdx.x == 0) rbad = 0;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    rlo[threadIdx.x >> 5] = klo;
+    rhi[threadIdx.x >> 5] = khi;
+    if (bad) rbad = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x >> 5;
+    klo = threadIdx.x < nw ? rlo[threadIdx.x] : ~0ull;
+    khi = threadIdx.x < nw ? rhi[threadIdx.x] : 0ull;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long a = __shfl_xor_sync(0xFFFFFFFFu, klo, o), b = __shfl_xor_sync(0xFFFFFFFFu, khi, o);
+      klo = a < klo ? a : klo;
+      khi = b > khi ? b : khi;
+    }
+    if (threadIdx.x == 0) {
+      atomicMin(&st->xmin_key, klo);
+      atomicMax(&st->xmax_key, khi);
+      if (rbad) st->bad = 1;
+    }
+  }
+}
+#endif
 
 // Device address of the library's fixed scratch array on the current device
 // (looked up once per device with cudaGetSymbolAddress); nullptr and a

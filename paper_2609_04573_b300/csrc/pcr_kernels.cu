@@ -127,11 +127,6 @@ __device__ __forceinline__ T predict(const int64_t* q, const int64_t* m, const i
 // --------------------------------------------------------------------------
 // helpers
 // --------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long dkey(double x) {
-  unsigned long long u = __double_as_longlong(x);
-  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
-}
-
 template <typename T> __device__ __forceinline__ unsigned long long absbits(T v);
 template <> __device__ __forceinline__ unsigned long long absbits<float>(float v) {
   return __float_as_uint(fabsf(v));
@@ -182,14 +177,6 @@ template <> __device__ __forceinline__ int64_t fix_from<double>(double x, int G,
   return -((val + ((int64_t(1) << k) - 1)) >> k);
 }
 
-template <typename T> __device__ __forceinline__ T from_fix(int64_t v, T scale);
-template <> __device__ __forceinline__ float from_fix<float>(int64_t v, float scale) {
-  return __fmul_rn(__ll2float_rn(v), scale);
-}
-template <> __device__ __forceinline__ double from_fix<double>(int64_t v, double scale) {
-  return __dmul_rn(__ll2double_rn(v), scale);
-}
-
 // lattice element -> field coordinates; returns false for row padding
 __device__ __forceinline__ bool lat_coords(const LatD& l, int64_t idx, int64_t* p) {
   const int64_t col = idx % l.row_pad;
@@ -218,9 +205,6 @@ __device__ __forceinline__ int64_t lat_padded_index(const LatD& l, const int64_t
 template <typename T>
 __device__ __forceinline__ void minmax_body(const T* __restrict__ x, int64_t n, FieldStats* st, int64_t tid,
                                             int64_t nth) {
-  __shared__ unsigned long long rlo[32], rhi[32];
-  __shared__ int rbad;
-  if (threadIdx.x == 0) rbad = 0;
   T lo = x[0], hi = x[0];
   int bad = 0;
   auto take = [&](T v) {
@@ -245,37 +229,7 @@ __device__ __forceinline__ void minmax_body(const T* __restrict__ x, int64_t n, 
     tail = nv * (16 / (int64_t)sizeof(T));
   }
   for (int64_t i = tail + tid; i < n; i += nth) take(x[i]);
-  unsigned long long klo = dkey((double)lo), khi = dkey((double)hi);
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    unsigned long long a = __shfl_xor_sync(FULL, klo, o), b = __shfl_xor_sync(FULL, khi, o);
-    klo = a < klo ? a : klo;
-    khi = b > khi ? b : khi;
-  }
-  bad = __any_sync(FULL, bad);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) {
-    rlo[threadIdx.x >> 5] = klo;
-    rhi[threadIdx.x >> 5] = khi;
-    if (bad) rbad = 1;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int nw = blockDim.x >> 5;
-    klo = threadIdx.x < nw ? rlo[threadIdx.x] : ~0ull;
-    khi = threadIdx.x < nw ? rhi[threadIdx.x] : 0ull;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      unsigned long long a = __shfl_xor_sync(FULL, klo, o), b = __shfl_xor_sync(FULL, khi, o);
-      klo = a < klo ? a : klo;
-      khi = b > khi ? b : khi;
-    }
-    if (threadIdx.x == 0) {
-      atomicMin(&st->xmin_key, klo);
-      atomicMax(&st->xmax_key, khi);
-      if (rbad) st->bad = 1;
-    }
-  }
+  stats_push_block(st, (double)lo, (double)hi, bad);
 }
 
 template <typename T>
@@ -1338,10 +1292,15 @@ static int64_t blocks_for(int64_t n, int threads = 256, int64_t cap = 148 * 8) {
   return std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, cap));
 }
 
-void launch_stats_multi(int vk, const void* const* xs, const int64_t* ns, FieldStats* const* sts, int n,
-                        cudaStream_t s) {
+// minimum / maximum / finiteness of several fields (no exponent yet)
+void launch_minmax_multi(int vk, const void* const* xs, const int64_t* ns, FieldStats* const* sts, int n,
+                         cudaStream_t s) {
   if (n == 1) {
-    launch_minmax(vk, xs[0], ns[0], sts[0], s);
+    count_launch();
+    int g = grid_for(ns[0], 512);
+    if (g > 148 * 4) g = 148 * 4;
+    if (vk == VK_F32) k_minmax<float><<<g, 512, 0, s>>>((const float*)xs[0], ns[0], sts[0]);
+    else k_minmax<double><<<g, 512, 0, s>>>((const double*)xs[0], ns[0], sts[0]);
     return;
   }
   for (int k0 = 0; k0 < n; k0 += kMaxBatchItems) {
@@ -1357,11 +1316,30 @@ void launch_stats_multi(int vk, const void* const* xs, const int64_t* ns, FieldS
     }
     b.first[b.n] = tot;
     count_launch();
-    count_launch();
     if (vk == VK_F32) k_minmax_multi<float><<<(unsigned)tot, 512, 0, s>>>(b);
     else k_minmax_multi<double><<<(unsigned)tot, 512, 0, s>>>(b);
+  }
+}
+
+// the exponent G of each field from its completed minimum and maximum
+void launch_finalize_multi(FieldStats* const* sts, int n, cudaStream_t s) {
+  if (n == 1) {
+    count_launch();
+    k_stats_finalize<<<1, 1, 0, s>>>(sts[0]);
+    return;
+  }
+  for (int k0 = 0; k0 < n; k0 += kMaxBatchItems) {
+    MinmaxBatch b{};
+    for (int k = k0; k < n && b.n < kMaxBatchItems; k++) b.st[b.n++] = sts[k];
+    count_launch();
     k_stats_finalize_multi<<<(b.n + 63) / 64, 64, 0, s>>>(b);
   }
+}
+
+void launch_stats_multi(int vk, const void* const* xs, const int64_t* ns, FieldStats* const* sts, int n,
+                        cudaStream_t s) {
+  launch_minmax_multi(vk, xs, ns, sts, n, s);
+  launch_finalize_multi(sts, n, s);
 }
 
 void launch_to_fixed_multi(int vk, const void* const* xs, const FieldD* fs, const FieldStats* const* sts,

@@ -32,6 +32,10 @@ namespace pcr {
 
 #define FULLMASK 0xFFFFFFFFu
 
+// minimum / maximum / finiteness of whole fields (pcr_kernels.cu)
+void launch_minmax_multi(int vk, const void* const* xs, const int64_t* ns, FieldStats* const* sts, int n,
+                         cudaStream_t s);
+
 // 1-D interpolation rules, same expressions as the codec file's (rounding:
 // cubic <= 2.75 u V, edges <= 2.875 u V, mean <= u V for inputs bounded by V)
 template <typename T> struct TAr;
@@ -1167,6 +1171,20 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
   auto base3 = [&](int i0) { return a.reg[2].base + (int64_t)i0 * a.reg[2].count[1] * rp3; };
   using MX = MaxAbs<A>;
   typename MX::T mx1 = 0, mx2 = 0, mx3 = 0;
+  // refactor of a field's level 0: its statistics as the planes arrive
+  // (minimum, maximum, and a sum of x - x that turns NaN at the first
+  // non-finite value), kept per thread in shared memory: the kernel is
+  // register-bound
+  constexpr bool STATS = !RET && !std::is_same<A, int64_t>::value;
+  __shared__ A sst[3][STATS ? NT : 1];
+  const bool st_on = STATS && a.stats != nullptr;
+  if constexpr (STATS) {
+    if (st_on) {
+      sst[0][tid] = A(INFINITY);
+      sst[1][tid] = A(-INFINITY);
+      sst[2][tid] = A(0);
+    }
+  }
 
   // point sets of the passes (thread-strided)
   auto p1pt = [&](int it, int& ci, int& cj, int& r, int& c) {
@@ -1257,7 +1275,44 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
       }
     }
   };
+  auto plane_stats = [&]() {   // the in-tile values of the plane in pv
+    A lo = sst[0][tid], hi = sst[1][tid], nz = sst[2][tid];
+    // min / max ignore NaN; nz = fma(x, 0, nz) stays 0 while every x is finite
+    auto take = [&](A x) {
+      if constexpr (std::is_same<A, float>::value) {
+        lo = fminf(lo, x);
+        hi = fmaxf(hi, x);
+        nz = __fmaf_rn(x, 0.0f, nz);
+      } else if constexpr (std::is_same<A, double>::value) {
+        lo = fmin(lo, x);
+        hi = fmax(hi, x);
+        nz = __fma_rn(x, 0.0, nz);
+      }
+    };
+#pragma unroll
+    for (int it = 0; it < NLV; it++) {
+      const int i = tid + NT * it;
+      const int pr = i / NV, v = i - pr * NV;
+      if (i >= PR * NV || pr < HR || pr >= HR + T1 || b1 - HR + pr >= m1) continue;
+      const int c0 = b2 - XL + v * VEC;
+      if (c0 < b2 || c0 >= b2 + T2) continue;   // vectors lie wholly inside or outside the tile's columns
+      if (c0 + VEC <= m2) {
+#pragma unroll
+        for (int k = 0; k < VEC; k++) take(pv[it].v[k]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < VEC; k++)
+          if (c0 + k < m2) take(pv[it].v[k]);
+      }
+    }
+    sst[0][tid] = lo;
+    sst[1][tid] = hi;
+    sst[2][tid] = nz;
+  };
   auto store_plane = [&]() {
+    if constexpr (STATS) {
+      if (st_on) plane_stats();
+    }
 #pragma unroll
     for (int it = 0; it < NLV; it++) {
       const int i = tid + NT * it;
@@ -1566,6 +1621,12 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
       }
     }
     __syncthreads();
+  }
+  if constexpr (STATS) {
+    if (st_on) {
+      const A nz = sst[2][tid];
+      stats_push_block(a.stats, (double)sst[0][tid], (double)sst[1][tid], nz != A(0));
+    }
   }
   if (!RET) {
     const unsigned long long m[3] = {MX::bits(mx1), MX::bits(mx2), MX::bits(mx3)};
@@ -1957,10 +2018,18 @@ static void launch_multi_kind(int vk, const TileArgs* args, int n, cudaStream_t 
   constexpr int T1 = 16, T2 = sizeof(A) == 4 ? 128 : 64;
   std::vector<TileArgs> rest, mv[2][2];   // marching refactor levels [cubic][per-region]
   std::vector<int> mz[2][2];
+  std::vector<const void*> sx;            // statistics the tile kernel does not take
+  std::vector<int64_t> sn;
+  std::vector<FieldStats*> ss;
   for (int i = 0; i < n; i++) {
     const TileArgs& a = args[i];
     const int c = march_applies<A>(a) ? tuned_choice<A>(vk, a, s) : 0;
     if (c == 0) {
+      if (a.stats && !a.retrieve) {
+        sx.push_back(a.src);
+        sn.push_back(a.m[0] * a.m[1] * a.m[2]);
+        ss.push_back(a.stats);
+      }
       rest.push_back(a);
     } else if (a.retrieve) {
       march_launch<A>(a, s, c);
@@ -1973,6 +2042,7 @@ static void launch_multi_kind(int vk, const TileArgs* args, int n, cudaStream_t 
   if (!mv[1][1].empty()) run_level0_march_multi<A, 3, false, true, T1, T2>(mv[1][1], mz[1][1], s);
   if (!mv[0][0].empty()) run_level0_march_multi<A, 1, false, false, T1, T2>(mv[0][0], mz[0][0], s);
   if (!mv[0][1].empty()) run_level0_march_multi<A, 1, false, true, T1, T2>(mv[0][1], mz[0][1], s);
+  if (!sx.empty()) launch_minmax_multi(vk, sx.data(), sn.data(), ss.data(), (int)sx.size(), s);
   run_tile_kind_multi<A>(rest, s);
 }
 
