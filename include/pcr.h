@@ -221,6 +221,9 @@ pcr_status pcr_refactor_batch(int n, const void* const* d_fields, const int* ndi
  * handle: the k-th handle, owned by the graph (do not pcr_free it); valid
  *   until pcr_refactor_graph_free, its contents replaced by every run.
  * info: graph nodes, kernels per run, scratch arena bytes (any may be NULL).
+ * times: of the last run, the graph's device time (CUDA events around the
+ *   launch, ms) and the host finish of the tables (ms); zeros before the
+ *   first run (either may be NULL).
  * Errors: as pcr_refactor_batch; PCR_ERR_CUDA when capture or instantiation
  *   fails. */
 typedef struct pcr_refactor_graph pcr_refactor_graph;
@@ -232,6 +235,7 @@ pcr_status pcr_refactor_graph_run(pcr_refactor_graph* g, void* cuda_stream);
 pcr_status pcr_refactor_graph_handle(const pcr_refactor_graph* g, int k, const pcr_handle** out);
 pcr_status pcr_refactor_graph_info(const pcr_refactor_graph* g, int64_t* nodes, int64_t* kernels,
                                    int64_t* arena_bytes);
+pcr_status pcr_refactor_graph_times(const pcr_refactor_graph* g, double* gpu_ms, double* host_ms);
 void pcr_refactor_graph_free(pcr_refactor_graph* g);
 
 /* ---- autotuner of the level-interpolation schedule (GPU tuning;

@@ -130,6 +130,7 @@ _sigs = {
     "pcr_refactor_graph_run": [_vp, _vp],
     "pcr_refactor_graph_handle": [_vp, C.c_int, C.POINTER(_vp)],
     "pcr_refactor_graph_info": [_vp, _i64p, _i64p, _i64p],
+    "pcr_refactor_graph_times": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "pcr_autotune_enable": [C.c_int],
     "pcr_autotune_read": [C.c_int, _i64p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int],
 }
@@ -596,6 +597,13 @@ class RefactorGraph:
         a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
         _check(_lib.pcr_refactor_graph_info(self._g, C.byref(a), C.byref(b), C.byref(c)))
         return {"nodes": a.value, "kernels": b.value, "arena_bytes": c.value}
+
+    def times(self):
+        """Of the last run: the graph's device time and the host finish of
+        the tables, in ms."""
+        g, h = C.c_double(), C.c_double()
+        _check(_lib.pcr_refactor_graph_times(self._g, C.byref(g), C.byref(h)))
+        return {"gpu_ms": g.value, "host_ms": h.value}
 
     def __del__(self):
         if getattr(self, "_g", None) and self._g.value:

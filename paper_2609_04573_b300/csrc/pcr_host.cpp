@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -16,6 +17,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -1671,6 +1673,14 @@ struct Scratch {
   }
 };
 
+// elements per row of a decomposed region's compact array in the refactor:
+// FP32 with slices normal to the fastest axis rounds rows up to 16 bytes
+// (the TMA-staged decomposition needs 16-byte row strides); else dense
+static int64_t comp_pitch(const pcr_handle* h, const Lat& R) {
+  const int64_t cw = R.count[2];
+  return (h->vk == VK_F32 && h->decomp == 2) ? (cw + 3) & ~int64_t(3) : cw;
+}
+
 // The refactor of one field, prepared on the host: its scratch carved, its
 // stream descriptors filled and the arguments of every stage's launch
 // recorded.  The stages of a batch then go out stage by stage across all its
@@ -1731,12 +1741,15 @@ static pcr_status prepare_refactor(pcr_handle* h, const void* d_field, Scratch& 
     w.xc = (int64_t*)sc.get((size_t)f.nc[0] * f.nc[1] * f.nc[2] * 8);
     if (!w.xc) return fail(PCR_ERR_OOM, "staging allocation failed");
   }
-  // region compact arrays for the decomposition
+  // region compact arrays for the decomposition (rows pitched to 16 bytes
+  // where the TMA-staged decomposition can then take them)
   std::vector<void*> comp(4, nullptr);
+  std::vector<int64_t> pitch(4, 0);
   if (h->decomp >= 0)
     for (int r = 1; r <= f.d; r++) {
       const Lat R = region_lat(h->n3, 0, h->order, r);
-      comp[r] = sc.get((size_t)R.n_real() * vb);
+      pitch[r] = comp_pitch(h, R);
+      comp[r] = sc.get((size_t)(R.count[0] * R.count[1] * pitch[r]) * vb);
       if (!comp[r]) return fail(PCR_ERR_OOM, "staging allocation failed");
     }
   unsigned long long* c0 = &d_st->c0;
@@ -1755,7 +1768,7 @@ static pcr_status prepare_refactor(pcr_handle* h, const void* d_field, Scratch& 
         const Lat R = region_lat(h->n3, 0, h->order, r);
         // max |c| over level 0 for the rounding allowance, taken while the
         // coefficients are formed
-        a.reg[r - 1] = tile_region(h, R, 0, R.count[2], 0, comp[r], c0);
+        a.reg[r - 1] = tile_region(h, R, 0, pitch[r], 0, comp[r], c0);
         a.reg[r - 1].vmax_double = 1;
       }
     } else {
@@ -1786,6 +1799,7 @@ static pcr_status prepare_refactor(pcr_handle* h, const void* d_field, Scratch& 
       decomp_subs(h, r, sds, da);
       da.retrieve = 0;
       da.comp = comp[r];
+      da.pitch = pitch[r];
       da.c0 = nullptr;   // max |c| taken by the level-0 prediction
       da.err = &d_st->timeout;
       w.dec.push_back(da);
@@ -2218,9 +2232,42 @@ static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* 
   return PCR_OK;
 }
 
-// host tables of every handle from a completed batch's read-backs
+// f(k) for k in [0, n) on up to 16 host threads (the caller's included):
+// independent per-field host work of a batch.  Returns the failing status
+// of the lowest k, with its message.
+template <class F>
+static pcr_status parallel_for(int n, F f) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nt = std::max(1, std::min(n, std::min(16, hw ? (int)hw : 1)));
+  if (nt == 1 || n < 4) {
+    for (int k = 0; k < n; k++) {
+      pcr_status e = f(k);
+      if (e) return e;
+    }
+    return PCR_OK;
+  }
+  std::vector<pcr_status> st(n, PCR_OK);
+  std::vector<std::string> msg(n);
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (int k; (k = next.fetch_add(1)) < n;) {
+      st[k] = f(k);
+      if (st[k]) msg[k] = g_err;   // this thread's message
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; t++) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+  for (int k = 0; k < n; k++)
+    if (st[k]) return fail(st[k], msg[k]);
+  return PCR_OK;
+}
+
+// host tables of every handle from a completed batch's read-backs (the
+// handles are independent: several at a time)
 static pcr_status finish_batch(const std::vector<pcr_handle*>& hs, const BatchLayout& L, const BatchStage& io) {
-  for (size_t k = 0; k < hs.size(); k++) {
+  return parallel_for((int)hs.size(), [&](int k) -> pcr_status {
     pcr_handle* h = hs[k];
     std::vector<unsigned long long> v(io.vm + L.vm_off[k], io.vm + L.vm_off[k] + h->geo.size());
     std::vector<uint32_t> nz(io.nz + L.nz_off[k], io.nz + L.nz_off[k] + h->nz_words);
@@ -2231,8 +2278,8 @@ static pcr_status finish_batch(const std::vector<pcr_handle*>& hs, const BatchLa
     if (e) return e;
     std::lock_guard<std::mutex> lk(h->plan_mu);   // planner units follow the new tables
     h->units_ok[0] = h->units_ok[1] = false;
-  }
-  return PCR_OK;
+    return PCR_OK;
+  });
 }
 
 static pcr_status make_batch_handles(int n, const void* const* d_fields, const int* ndims,
@@ -2276,7 +2323,10 @@ static size_t refactor_scratch_bytes(const pcr_handle* h) {
     t += al(nc * 8);
   }
   if (h->decomp >= 0)
-    for (int r = 1; r <= (int)h->order.size(); r++) t += al((size_t)region_lat(h->n3, 0, h->order, r).n_real() * w);
+    for (int r = 1; r <= (int)h->order.size(); r++) {
+      const Lat R = region_lat(h->n3, 0, h->order, r);
+      t += al((size_t)(R.count[0] * R.count[1] * comp_pitch(h, R)) * w);
+    }
   return t + 256;
 }
 
@@ -2469,7 +2519,11 @@ struct pcr_refactor_graph {
   cudaGraphExec_t exec = nullptr;
   long long kernels = 0;
   size_t nodes = 0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  double gpu_ms = 0.0, host_ms = 0.0;   // of the last run
   ~pcr_refactor_graph() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (cap) cudaStreamDestroy(cap);
@@ -2570,10 +2624,27 @@ extern "C" pcr_status pcr_refactor_graph_create(int n, const void* const* d_fiel
 extern "C" pcr_status pcr_refactor_graph_run(pcr_refactor_graph* g, void* cuda_stream) {
   if (!g) return fail(PCR_ERR_INVALID_ARG, "null graph");
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  for (cudaEvent_t& e : g->ev)
+    if (!e) CUDA_TRY(cudaEventCreate(&e));
+  CUDA_TRY(cudaEventRecord(g->ev[0], s));
   CUDA_TRY(cudaGraphLaunch(g->exec, s));
+  CUDA_TRY(cudaEventRecord(g->ev[1], s));
   add_launches(g->kernels);
   CUDA_TRY(cudaStreamSynchronize(s));
-  return finish_batch(g->hs, *g->layout, g->io);
+  float ms = 0.0f;
+  CUDA_TRY(cudaEventElapsedTime(&ms, g->ev[0], g->ev[1]));
+  g->gpu_ms = ms;
+  const auto t0 = std::chrono::steady_clock::now();
+  const pcr_status e = finish_batch(g->hs, *g->layout, g->io);
+  g->host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return e;
+}
+
+extern "C" pcr_status pcr_refactor_graph_times(const pcr_refactor_graph* g, double* gpu_ms, double* host_ms) {
+  if (!g) return fail(PCR_ERR_INVALID_ARG, "null graph");
+  if (gpu_ms) *gpu_ms = g->gpu_ms;
+  if (host_ms) *host_ms = g->host_ms;
+  return PCR_OK;
 }
 
 extern "C" pcr_status pcr_refactor_graph_handle(const pcr_refactor_graph* g, int k, const pcr_handle** out) {
@@ -3066,7 +3137,10 @@ static size_t retrieve_scratch_bytes(const pcr_handle* h) {
     t += al(nc * 8);
   }
   if (h->decomp >= 0)
-    for (int r = 1; r <= (int)h->order.size(); r++) t += al((size_t)region_lat(h->n3, 0, h->order, r).n_real() * w);
+    for (int r = 1; r <= (int)h->order.size(); r++) {
+      const Lat R = region_lat(h->n3, 0, h->order, r);
+      t += al((size_t)(R.count[0] * R.count[1] * comp_pitch(h, R)) * w);
+    }
   return t + 256;
 }
 

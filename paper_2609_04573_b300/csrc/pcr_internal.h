@@ -164,6 +164,7 @@ struct DecompArgs {
   int64_t blo[3], bhi[3], tlo[3];
   unsigned long long* c0;  // decompose: running max |c| (bits of a double)
   int* err;                // set to 1 when a bounded device wait gives up (may be null)
+  int64_t pitch;           // elements per compact row (0: cnt[2]); forward decomposition only
 };
 
 // an index box: points lo + [0, cnt) per axis

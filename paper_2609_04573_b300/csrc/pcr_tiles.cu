@@ -756,7 +756,7 @@ __device__ __forceinline__ void decomp_fwd_body(const DecompArgs& a, unsigned it
   const unsigned bb = rest % nbb + (unsigned)a.tlo[1], ab = rest / nbb + (unsigned)a.tlo[0];
   const bool live = rest / nbb < nab;
   const int cu = (int)a.cnt[0], cv = (int)a.cnt[1];
-  const int64_t cw = a.cnt[2];
+  const int64_t cw = a.cnt[2], pw = a.pitch ? a.pitch : cw;
   const int u0 = 4 * (int)ab, v0 = 4 * (int)bb;
   const int64_t k2 = (int64_t)iv * VEC;
   const A* __restrict__ comp = reinterpret_cast<const A*>(a.comp);
@@ -767,7 +767,7 @@ __device__ __forceinline__ void decomp_fwd_body(const DecompArgs& a, unsigned it
     vv[d] = live && v0 + d < cv;
   }
   auto ld = [&](V& r, int du, int dv) {
-    if (vu[du] && vv[dv]) vld<A, VEC>(r, comp + ((int64_t)(u0 + du) * cv + (v0 + dv)) * cw + k2);
+    if (vu[du] && vv[dv]) vld<A, VEC>(r, comp + ((int64_t)(u0 + du) * cv + (v0 + dv)) * pw + k2);
     else
 #pragma unroll
       for (int e = 0; e < VEC; e++) r.v[e] = A(0);
@@ -979,7 +979,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // the TMA form applies to a whole array, FP32, slices normal to the fastest
 // axis, 16-byte row strides and a tensor map the driver accepts
 static bool decomp_tma_applies(const DecompArgs& a) {
-  return !a.retrieve && a.n == 2 && a.bhi[0] == 0 && a.cnt[2] % 4 == 0 && a.err && ((uintptr_t)a.comp & 15) == 0;
+  const int64_t pw = a.pitch ? a.pitch : a.cnt[2];
+  return !a.retrieve && a.n == 2 && a.bhi[0] == 0 && pw % 4 == 0 && a.err && ((uintptr_t)a.comp & 15) == 0;
 }
 
 // tensor map of a region's compact array: boxes of kDtW x (kDtV + 1) x
@@ -987,9 +988,9 @@ static bool decomp_tma_applies(const DecompArgs& a) {
 static bool decomp_tensor_map(const DecompArgs& a, CUtensorMap& tm) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
-  const int64_t cu = a.cnt[0], cv = a.cnt[1], cw = a.cnt[2];
+  const int64_t cu = a.cnt[0], cv = a.cnt[1], cw = a.cnt[2], pw = a.pitch ? a.pitch : cw;
   const cuuint64_t gdim[3] = {(cuuint64_t)cw, (cuuint64_t)cv, (cuuint64_t)cu};
-  const cuuint64_t gstride[2] = {(cuuint64_t)cw * 4, (cuuint64_t)(cw * cv) * 4};
+  const cuuint64_t gstride[2] = {(cuuint64_t)pw * 4, (cuuint64_t)(pw * cv) * 4};
   const cuuint32_t box[3] = {kDtW, kDtV + 1, kDtU + 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.comp, gdim, gstride, box, estr,
@@ -2129,9 +2130,8 @@ static void run_decomp_blk(const DecompArgs& a0, cudaStream_t s) {
 void launch_tile_decomp(int vk, const DecompArgs& a, cudaStream_t s) {
   // tiles are multiples of 4 along the in-slice axes
   if (vk == VK_F32) {
-    if (a.n == 2 && a.cnt[2] % 4 == 0) {
-      if (!run_decomp_tma(a, s)) run_decomp_blk<float, 4>(a, s);
-    }
+    if (a.n == 2 && run_decomp_tma(a, s)) return;   // forward, whole array, 16-byte row pitch
+    if (a.n == 2 && a.cnt[2] % 4 == 0) run_decomp_blk<float, 4>(a, s);
     else if (a.n == 2) run_decomp_blk<float, 1>(a, s);
     else if (a.n == 1) run_decomp<float, 1, 16, 4, 64>(a, s);
     else run_decomp<float, 0, 4, 16, 64>(a, s);
@@ -2156,7 +2156,7 @@ void launch_tile_decomp_multi(int vk, const DecompArgs* das, int n, cudaStream_t
   for (int k : rest) {
     const DecompArgs& a = das[k];
     if (a.retrieve || a.n != 2) one.push_back(k);
-    else if (vk == VK_F32) g[a.cnt[2] % 4 == 0 ? 0 : 1].push_back(a);
+    else if (vk == VK_F32) g[a.cnt[2] % 4 == 0 ? 0 : 1].push_back(a);   // whole vectors per row
     else g[a.cnt[2] % 2 == 0 ? 2 : 3].push_back(a);
   }
   for (int q = 0; q < 4; q++) {
