@@ -299,12 +299,13 @@ def _stream_ptr(stream):
 class Handle:
     """Refactored field: device streams + host tables (owned by the library)."""
 
-    def __init__(self, ptr, shape, dtype, device, owner=None):
+    def __init__(self, ptr, shape, dtype, device, owner=None, allocator=None):
         self._p = C.c_void_p(ptr)
         self.shape = tuple(shape)
         self.dtype = dtype
         self.device = device
         self._owner = owner   # a RefactorGraph owns its handles; keep it alive
+        self._alloc = allocator   # a caller's allocator frees the handle's memory: keep it alive
 
     def __del__(self):
         if getattr(self, "_owner", None) is None and getattr(self, "_p", None) and self._p.value:
@@ -485,17 +486,27 @@ def tune(x, mode="eb", fraction=0.0, edge=0, stream=None):
                                     fraction=info.fraction, ms=info.ms)
 
 
-def refactor(x, scheme=None, stream=None):
-    """Refactor a contiguous CUDA float32/float64 tensor (2-D or 3-D)."""
+def _alloc_ref(allocator):
+    """A caller's pcr_allocator (an object with a `.c` _Allocator, or the
+    struct itself), else torch's caching allocator."""
+    if allocator is None:
+        return C.byref(_ALLOCATOR)
+    return C.byref(getattr(allocator, "c", allocator))
+
+
+def refactor(x, scheme=None, stream=None, allocator=None):
+    """Refactor a contiguous CUDA float32/float64 tensor (2-D or 3-D).
+    `allocator`: device memory for the handle and the call's scratch
+    (default: torch's caching allocator)."""
     scheme = scheme or Scheme()
     if not (x.is_cuda and x.is_contiguous() and x.dtype in _DT and x.dim() in (2, 3)):
         raise ValueError("refactor expects a contiguous 2-D/3-D float32/float64 CUDA tensor")
     dims = (C.c_int64 * x.dim())(*x.shape)
     out = C.c_void_p()
     _check(_lib.pcr_refactor(C.c_void_p(x.data_ptr()), x.dim(), dims, _DT[x.dtype],
-                             C.byref(scheme.c(x.dim())), C.byref(_ALLOCATOR), _stream_ptr(stream),
+                             C.byref(scheme.c(x.dim())), _alloc_ref(allocator), _stream_ptr(stream),
                              C.byref(out)))
-    return Handle(out.value, x.shape, x.dtype, x.device)
+    return Handle(out.value, x.shape, x.dtype, x.device, allocator=allocator)
 
 
 class RefactorJob:
@@ -537,8 +548,9 @@ def refactor_async(x, scheme=None, stream=None):
     return RefactorJob(out.value, x)
 
 
-def refactor_batch(xs: Sequence[torch.Tensor], schemes, stream=None):
-    """One work list per pipeline stage for all fields (batched form)."""
+def refactor_batch(xs: Sequence[torch.Tensor], schemes, stream=None, allocator=None):
+    """Every pipeline stage in one launch (or a few) across all fields
+    (batched form)."""
     n = len(xs)
     if not isinstance(schemes, (list, tuple)):
         schemes = [schemes] * n
@@ -549,9 +561,9 @@ def refactor_batch(xs: Sequence[torch.Tensor], schemes, stream=None):
     dts = (C.c_int * n)(*[_DT[x.dtype] for x in xs])
     sch = (_Scheme * n)(*[s.c(x.dim()) for s, x in zip(schemes, xs)])
     outs = (C.c_void_p * n)()
-    _check(_lib.pcr_refactor_batch(n, ptrs, nd, dims, dts, sch, C.byref(_ALLOCATOR),
+    _check(_lib.pcr_refactor_batch(n, ptrs, nd, dims, dts, sch, _alloc_ref(allocator),
                                    _stream_ptr(stream), outs))
-    return [Handle(outs[i], x.shape, x.dtype, x.device) for i, x in enumerate(xs)]
+    return [Handle(outs[i], x.shape, x.dtype, x.device, allocator=allocator) for i, x in enumerate(xs)]
 
 
 def _batch_args(xs, schemes):
@@ -574,14 +586,15 @@ class RefactorGraph:
     Creation refactors once (autotuning the level schedule) so `handles` are
     valid right away; every run replaces their contents."""
 
-    def __init__(self, xs: Sequence[torch.Tensor], schemes, stream=None):
+    def __init__(self, xs: Sequence[torch.Tensor], schemes, stream=None, allocator=None):
         for x in xs:
             if not (x.is_cuda and x.is_contiguous() and x.dtype in _DT and x.dim() in (2, 3)):
                 raise ValueError("RefactorGraph expects contiguous 2-D/3-D float32/float64 CUDA tensors")
         self._xs = list(xs)
+        self._alloc = allocator   # kept alive: the graph frees its arena through it
         n, ptrs, nd, dims, _keep, dts, sch = _batch_args(xs, schemes)
         self._g = C.c_void_p()
-        _check(_lib.pcr_refactor_graph_create(n, ptrs, nd, dims, dts, sch, C.byref(_ALLOCATOR),
+        _check(_lib.pcr_refactor_graph_create(n, ptrs, nd, dims, dts, sch, _alloc_ref(allocator),
                                               _stream_ptr(stream), C.byref(self._g)))
         self.handles = []
         for i, x in enumerate(xs):

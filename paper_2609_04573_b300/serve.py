@@ -15,6 +15,11 @@ requests).
 Box requests are retrieved with pcr_retrieve_box on the group's stream: only
 the box's dependency region is decoded and reconstructed, and the result is
 the box of the whole-field retrieval under the same plan.
+
+A request can be cancelled (Request.cancel) until its group is launched: it
+is then dropped from the group, its memory is not charged and its future
+stays cancelled.  A request whose plan fails gets the exception on its
+future; the rest of its group runs.
 """
 import queue
 import threading
@@ -43,6 +48,10 @@ class Request:
     def latency(self):
         return self.t_done - self.t_submit
 
+    def cancel(self):
+        """True if the request will not run (cancelled before its launch)."""
+        return self.future.cancel()
+
 
 class Server:
     """Continuous-batching retrieval server over resident handles."""
@@ -62,6 +71,7 @@ class Server:
         # a box retrieval reconstructs into a field-sized buffer before copying the box
         self._worker = threading.Thread(target=self._run, daemon=True)
         self.batches = 0
+        self.cancelled = 0
         if start:
             self._worker.start()
 
@@ -129,6 +139,9 @@ class Server:
         hs, plans, outs, boxes = [], [], [], []
         live = []
         for r in group:
+            if not r.future.set_running_or_notify_cancel():   # cancelled while queued
+                self.cancelled += 1
+                continue
             h = self.handles[r.field_id]
             try:
                 p = h.plan(r.target, allow_unsat=True)
@@ -148,6 +161,7 @@ class Server:
                 boxes.append((r, h, p))
         if not live:
             return
+        mem = sum(self._need_of(r) for r in live)   # the requests that run
         with torch.cuda.stream(stream):
             if hs:
                 retrieve_batch(hs, plans, outs, stream=stream)
