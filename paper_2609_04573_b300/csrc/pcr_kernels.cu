@@ -1498,11 +1498,13 @@ void launch_copy_raw(int vk, const FieldD& f, const LatD& lat, const void* vals,
 }
 
 // ---------------------------------------------------------------------------
-// Persistent encoder for FP32 streams with 32-bit codes (Sec. V-C bitplanes,
-// Sec. VI-A encodings).  Same planes, sign sub-streams, counts and tables as
-// k_encode; organised for throughput:
-//  * each CTA loops over work items; the next segment's 16 KB of values is
-//    copied into shared memory with cp.async while the current one is coded;
+// Persistent encoder for streams with 32-bit codes whose tables need no
+// plane-pair counts: FP32 streams and fixed-point streams (Sec. V-C
+// bitplanes, Sec. VI-A encodings).  Same planes, sign sub-streams, counts
+// and tables as k_encode; organised for throughput:
+//  * each CTA loops over work items; the next segment's values (16 KB FP32,
+//    32 KB fixed point) are copied into shared memory with cp.async while the
+//    current one is coded;
 //  * sign ranks come from the transposed planes: F_k = D_k & ~(D_0 | .. |
 //    D_{k-1}) marks the elements first significant at plane k; the word's
 //    signs sorted by (plane, element) are one warp OR-reduction, and lane k
@@ -1521,11 +1523,13 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // start the copy of one segment's staged values (zero fill past the stream)
-__device__ __forceinline__ void enc_fetch(uint32_t* buf, const float* stage, int64_t e0, int64_t n_pad) {
+template <typename VT>
+__device__ __forceinline__ void enc_fetch(uint32_t* buf, const VT* stage, int64_t e0, int64_t n_pad) {
+  constexpr int PER = 16 / sizeof(VT);           // values per 16-byte chunk
   const int64_t avail = n_pad - e0;              // elements of the stream from e0 (multiple of 32)
-  for (int c = threadIdx.x; c < kSegElems / 4; c += kThreads) {
-    const bool ok = (int64_t)c * 4 < avail;
-    cp_async16(buf + c * 4, ok ? (const void*)(stage + e0 + c * 4) : (const void*)(stage), ok ? 16 : 0);
+  for (int c = threadIdx.x; c < kSegElems / PER; c += kThreads) {
+    const bool ok = (int64_t)c * PER < avail;
+    cp_async16(buf + c * 4, ok ? (const void*)(stage + e0 + c * PER) : (const void*)(stage), ok ? 16 : 0);
   }
 }
 
@@ -1534,12 +1538,16 @@ __device__ __forceinline__ void enc_fetch(uint32_t* buf, const float* stage, int
 // hit different banks)
 __device__ __forceinline__ int sb_index(int lane, int i) { return lane * 16 + (i ^ ((lane >> 1) & 15)); }
 
-constexpr int kEncDynSmem = (2 * kSegElems + 32 * kEncRow) * 4;   // two input buffers + plane rows
+// two input buffers + plane rows (value type VT: 4 or 8 bytes)
+template <typename VT>
+constexpr int enc_dyn_smem() { return (2 * kSegElems * (int)(sizeof(VT) / 4) + 32 * kEncRow) * 4; }
 
-__global__ void __launch_bounds__(kThreads, 4) k_encode_f32(const StreamD* __restrict__ streams,
+template <typename VT>
+__global__ void __launch_bounds__(kThreads, 4) k_encode_w32(const StreamD* __restrict__ streams,
                                                             const WorkItem* __restrict__ items, int nitems) {
+  constexpr int VW = sizeof(VT) / 4;   // 32-bit words per staged value
   extern __shared__ __align__(16) uint32_t enc_dyn[];
-  uint32_t* const pbuf = enc_dyn + 2 * kSegElems;
+  uint32_t* const pbuf = enc_dyn + 2 * kSegElems * VW;
   __shared__ uint32_t sbuf[kSegWords + 64];
   __shared__ uint32_t wcnt[kWarps][32];
   __shared__ uint32_t woff[kWarps][32];
@@ -1558,37 +1566,39 @@ __global__ void __launch_bounds__(kThreads, 4) k_encode_f32(const StreamD* __res
   WorkItem it = items[item];
   {
     const StreamD& s0 = streams[it.stream];
-    enc_fetch(enc_dyn, (const float*)s0.stage, (int64_t)it.seg * kSegElems, s0.n_pad);
+    enc_fetch(enc_dyn, (const VT*)s0.stage, (int64_t)it.seg * kSegElems, s0.n_pad);
     cp_async_commit();
   }
   int nitem = item + gridDim.x;
   WorkItem nit = nitem < nitems ? items[nitem] : WorkItem{0, 0};
-  const float* nstage = nullptr;
+  const VT* nstage = nullptr;
   int64_t nn_pad = 0;
   if (nitem < nitems) {
-    nstage = (const float*)streams[nit.stream].stage;
+    nstage = (const VT*)streams[nit.stream].stage;
     nn_pad = streams[nit.stream].n_pad;
   }
 
   for (int cur = 0; item < nitems; cur ^= 1) {
     // (A) the next item's values start moving; the one after is located
-    if (nitem < nitems) enc_fetch(enc_dyn + (cur ^ 1) * kSegElems, nstage, (int64_t)nit.seg * kSegElems, nn_pad);
+    if (nitem < nitems)
+      enc_fetch(enc_dyn + (cur ^ 1) * kSegElems * VW, nstage, (int64_t)nit.seg * kSegElems, nn_pad);
     cp_async_commit();
     const int item2 = nitem + gridDim.x;
     WorkItem it2{0, 0};
-    const float* stage2 = nullptr;
+    const VT* stage2 = nullptr;
     int64_t n_pad2 = 0;
     if (item2 < nitems) {
       it2 = items[item2];
-      stage2 = (const float*)streams[it2.stream].stage;
+      stage2 = (const VT*)streams[it2.stream].stage;
       n_pad2 = streams[it2.stream].n_pad;
     }
     const StreamD& s = streams[it.stream];
     const int B = s.B;
     const bool generic = s.enc == 1;
     const QParams qp = qparams(s);
-    // quantisation (the arithmetic of quantize<float, 32>) with per-item constants
-    const Scale2 sc = scale_pair(generic ? B - qp.E : B - 3 - qp.E);
+    // quantisation (the arithmetic of quantize<VT, 32>) with per-item constants
+    [[maybe_unused]] Scale2 sc{1.0f, 1.0f};
+    if constexpr (std::is_same<VT, float>::value) sc = scale_pair(generic ? B - qp.E : B - 3 - qp.E);
     const uint32_t M = (uint32_t)nb_mask(B);
     const int64_t e0 = (int64_t)it.seg * kSegElems;
     const int nw = (int)min((int64_t)kSegWords, (s.n_pad - e0) / 32);
@@ -1598,10 +1608,27 @@ __global__ void __launch_bounds__(kThreads, 4) k_encode_f32(const StreamD* __res
     __syncthreads();
 
     // (C) code this warp's 16 words
-    uint32_t* wbuf = enc_dyn + cur * kSegElems + warp * kWordsPerWarp * 32;
-    float v[kWordsPerWarp];
+    uint32_t* wbuf = enc_dyn + (cur * kSegElems + warp * kWordsPerWarp * 32) * VW;
+    // FP32: the values; fixed point: the codes and signs right away (the
+    // arithmetic of quantize<int64_t, 32>), 32 bits per value in registers
+    [[maybe_unused]] float v[std::is_same<VT, float>::value ? kWordsPerWarp : 1];
+    [[maybe_unused]] uint32_t qv[std::is_same<VT, float>::value ? 1 : kWordsPerWarp];
+    [[maybe_unused]] uint32_t negm = 0;
+    if constexpr (std::is_same<VT, float>::value) {
 #pragma unroll
-    for (int jj = 0; jj < kWordsPerWarp; jj++) v[jj] = __uint_as_float(wbuf[jj * 32 + lane]);
+      for (int jj = 0; jj < kWordsPerWarp; jj++) v[jj] = __uint_as_float(wbuf[jj * 32 + lane]);
+    } else {
+      const int64_t* wv = reinterpret_cast<const int64_t*>(wbuf);
+#pragma unroll
+      for (int jj = 0; jj < kWordsPerWarp; jj++) {
+        const int64_t x = wv[jj * 32 + lane];
+        const bool ng = x < 0;
+        const uint64_t mag = (uint64_t)(ng ? -x : x) >> qp.sh;
+        const int64_t sv = ng ? -(int64_t)mag : (int64_t)mag;
+        qv[jj] = generic ? (uint32_t)mag : (((uint32_t)sv + M) ^ M);
+        negm |= (uint32_t)ng << jj;
+      }
+    }
     __syncwarp();                       // the warp's region now holds its sign bit-strings
     uint32_t acc = 0, fill = 0, wpos = 0, count = 0, nz = 0;
     // the word loop, instantiated per encoding (the test then runs once)
@@ -1610,13 +1637,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_encode_f32(const StreamD* __res
       uint32_t pw[4];
 #pragma unroll
       for (int jj = 0; jj < kWordsPerWarp; jj++) {
-        const bool neg = v[jj] < 0.0f;
+        bool neg;
         uint32_t q;
-        if constexpr (GEN) {
-          q = __float2uint_rz(__fmul_rn(__fmul_rn(fabsf(v[jj]), sc.m1), sc.m2));
+        if constexpr (std::is_same<VT, float>::value) {
+          neg = v[jj] < 0.0f;
+          if constexpr (GEN) {
+            q = __float2uint_rz(__fmul_rn(__fmul_rn(fabsf(v[jj]), sc.m1), sc.m2));
+          } else {
+            const int sv = __float2int_rz(__fmul_rn(__fmul_rn(v[jj], sc.m1), sc.m2));
+            q = ((uint32_t)sv + M) ^ M;
+          }
         } else {
-          const int sv = __float2int_rz(__fmul_rn(__fmul_rn(v[jj], sc.m1), sc.m2));
-          q = ((uint32_t)sv + M) ^ M;
+          neg = (negm >> jj) & 1u;
+          q = qv[jj];
         }
         if (qp.zero) q = 0;
         const uint32_t xr = q << (32 - B);
@@ -1868,8 +1901,9 @@ __global__ void __launch_bounds__(kThreads) k_decode_w32(const StreamD* __restri
   }
 }
 
-// persistent grid of k_encode_f32: the CTAs that fit on the device at once
-static int enc_f32_grid(int nitems) {
+// persistent grid of k_encode_w32: the CTAs that fit on the device at once
+template <typename VT>
+static int enc_w32_grid(int nitems) {
   static int cached[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1877,8 +1911,8 @@ static int enc_f32_grid(int nitems) {
   if (g == 0) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_encode_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncDynSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_encode_f32, kThreads, kEncDynSmem);
+    cudaFuncSetAttribute(k_encode_w32<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, enc_dyn_smem<VT>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_encode_w32<VT>, kThreads, enc_dyn_smem<VT>());
     g = max(1, sms * max(per, 1));
   }
   return min(nitems, g);
@@ -1893,9 +1927,15 @@ void launch_encode(int vk, int w64, int pairs, const StreamD* d_streams, const W
   if (!w64) {
     if (vk == VK_F32) {
       if (pairs) ENC(float, 32, true);
-      else k_encode_f32<<<enc_f32_grid(nitems), kThreads, kEncDynSmem, s>>>(d_streams, d_items, nitems);
+      else
+        k_encode_w32<float><<<enc_w32_grid<float>(nitems), kThreads, enc_dyn_smem<float>(), s>>>(d_streams, d_items,
+                                                                                                 nitems);
+    } else {
+      if (pairs) ENC(int64_t, 32, true);
+      else
+        k_encode_w32<int64_t><<<enc_w32_grid<int64_t>(nitems), kThreads, enc_dyn_smem<int64_t>(), s>>>(
+            d_streams, d_items, nitems);
     }
-    else { if (pairs) ENC(int64_t, 32, true); else ENC(int64_t, 32, false); }
   } else {
     if (vk == VK_F64) { if (pairs) ENC(double, 64, true); else ENC(double, 64, false); }
     else { if (pairs) ENC(int64_t, 64, true); else ENC(int64_t, 64, false); }
