@@ -1673,6 +1673,101 @@ struct Scratch {
   }
 };
 
+// ---------------------------------------------------------------------------
+// a second stream beside a call's stream: the fixed-point coarse levels
+// (1/8 of the points, small latency-bound kernels) run beside the level-0
+// coefficient work, forked after the work both need and joined before the
+// work that needs both
+// ---------------------------------------------------------------------------
+struct SideLane {
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static pcr_status lane_create(SideLane& l) {
+  CUDA_TRY(cudaStreamCreateWithFlags(&l.st, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&l.fork, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&l.join, cudaEventDisableTiming));
+  return PCR_OK;
+}
+
+static void lane_destroy(SideLane& l) {
+  if (l.join) cudaEventDestroy(l.join);
+  if (l.fork) cudaEventDestroy(l.fork);
+  if (l.st) cudaStreamDestroy(l.st);
+  l = SideLane();
+}
+
+// lanes are taken for the enqueue of one call (its events must not be
+// re-recorded by another thread meanwhile) and returned afterwards, kept per
+// (device, main stream) so that calls on different streams do not queue
+// their side work behind each other's; work an earlier call left queued on
+// a lane's stream only delays the next user of that lane
+static std::mutex g_lane_mu;
+static std::map<std::pair<int, cudaStream_t>, std::vector<SideLane>> g_lane_free;
+
+class Fork {
+ public:
+  // `fixed`: a lane owned by the caller (a graph being captured); else a
+  // pooled one, unless the stream is being captured (then no fork).  With
+  // stage tracing on there is no fork either: per-stage CUDA-event times
+  // are only meaningful for stages that do not share the GPU.
+  Fork(cudaStream_t main, const SideLane* fixed = nullptr) : main_(main) {
+    if (g_prof_on) return;
+    if (fixed) {
+      lane_ = *fixed;
+      return;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(main, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      cudaGetLastError();
+      return;
+    }
+    cudaGetDevice(&dev_);
+    {
+      std::lock_guard<std::mutex> lk(g_lane_mu);
+      auto& v = g_lane_free[{dev_, main_}];
+      if (!v.empty()) {
+        lane_ = v.back();
+        v.pop_back();
+      }
+    }
+    if (!lane_.st && lane_create(lane_) != PCR_OK) {
+      lane_destroy(lane_);
+      cudaGetLastError();
+    }
+    pooled_ = lane_.st != nullptr;
+  }
+  ~Fork() {
+    if (open_) join();   // an error path: the main stream still waits for the side work
+    if (pooled_) {
+      std::lock_guard<std::mutex> lk(g_lane_mu);
+      g_lane_free[{dev_, main_}].push_back(lane_);
+    }
+  }
+  cudaStream_t side() const { return open_ ? lane_.st : main_; }
+  pcr_status fork() {
+    if (!lane_.st) return PCR_OK;
+    CUDA_TRY(cudaEventRecord(lane_.fork, main_));
+    CUDA_TRY(cudaStreamWaitEvent(lane_.st, lane_.fork, 0));
+    open_ = true;
+    return PCR_OK;
+  }
+  pcr_status join() {
+    if (!open_) return PCR_OK;
+    open_ = false;
+    CUDA_TRY(cudaEventRecord(lane_.join, lane_.st));
+    CUDA_TRY(cudaStreamWaitEvent(main_, lane_.join, 0));
+    return PCR_OK;
+  }
+
+ private:
+  cudaStream_t main_;
+  SideLane lane_;
+  int dev_ = 0;
+  bool pooled_ = false, open_ = false;
+};
+
 // elements per row of a decomposed region's compact array in the refactor:
 // FP32 with slices normal to the fastest axis rounds rows up to 16 bytes
 // (the TMA-staged decomposition needs 16-byte row strides); else dense
@@ -1817,11 +1912,11 @@ static pcr_status prepare_refactor(pcr_handle* h, const void* d_field, Scratch& 
 }
 
 // The coefficient stages of a batch's refactors, stage by stage across the
-// fields: statistics, level-0 prediction, fixed-point copy, coarsest level,
-// fixed-point levels, decomposition, row padding.  Within a stage the
-// fields' grids are independent; each stage reads only what earlier stages
-// wrote.
-static void enqueue_stages(const std::vector<FieldWork>& ws, cudaStream_t s) {
+// fields; within a stage the fields' grids are independent, and each stage
+// reads only what earlier stages wrote.
+// Level 0 and what every later stage needs: statistics, level-0 prediction,
+// the exponent, the row padding of every staging.
+static void stages_level0(const std::vector<FieldWork>& ws, cudaStream_t s) {
   const int vks[2] = {VK_F32, VK_F64};
   {
     // fields without a level 0 (L = 1): a statistics pass of their own; the
@@ -1856,6 +1951,24 @@ static void enqueue_stages(const std::vector<FieldWork>& ws, cudaStream_t s) {
       if (w.has_l0) fin.push_back(w.st);
     if (!fin.empty()) launch_finalize_multi(fin.data(), (int)fin.size(), s);
   }
+  {
+    std::vector<int> pv;
+    std::vector<LatD> pl;
+    std::vector<void*> ps;
+    for (const FieldWork& w : ws) {
+      pv.insert(pv.end(), w.pad_vk.begin(), w.pad_vk.end());
+      pl.insert(pl.end(), w.pad_lat.begin(), w.pad_lat.end());
+      ps.insert(ps.end(), w.pad_stage.begin(), w.pad_stage.end());
+    }
+    Prof pf("zero_pads", s);
+    launch_zero_pads_multi(pv.data(), pl.data(), ps.data(), (int)pv.size(), s);
+  }
+}
+
+// The fixed-point coarse levels: fixed-point copy, coarsest level, levels
+// L-2 .. 1 (after stages_level0: they need the exponent).
+static void stages_fixed(const std::vector<FieldWork>& ws, cudaStream_t s) {
+  const int vks[2] = {VK_F32, VK_F64};
   {
     Prof pf("to_fixed", s);
     for (int vk : vks) {
@@ -1903,6 +2016,11 @@ static void enqueue_stages(const std::vector<FieldWork>& ws, cudaStream_t s) {
     Prof pf("interp_fixed_levels", s);
     launch_tile_interp_multi(VK_FIX, lv.data(), (int)lv.size(), s);
   }
+}
+
+// The level-0 decomposition (after stages_level0).
+static void stages_float(const std::vector<FieldWork>& ws, cudaStream_t s) {
+  const int vks[2] = {VK_F32, VK_F64};
   {
     Prof pf("decompose", s);
     for (int vk : vks) {
@@ -1911,18 +2029,6 @@ static void enqueue_stages(const std::vector<FieldWork>& ws, cudaStream_t s) {
         if (w.h->vk == vk) das.insert(das.end(), w.dec.begin(), w.dec.end());
       if (!das.empty()) launch_tile_decomp_multi(vk, das.data(), (int)das.size(), s);
     }
-  }
-  {
-    std::vector<int> pv;
-    std::vector<LatD> pl;
-    std::vector<void*> ps;
-    for (const FieldWork& w : ws) {
-      pv.insert(pv.end(), w.pad_vk.begin(), w.pad_vk.end());
-      pl.insert(pl.end(), w.pad_lat.begin(), w.pad_lat.end());
-      ps.insert(ps.end(), w.pad_stage.begin(), w.pad_stage.end());
-    }
-    Prof pf("zero_pads", s);
-    launch_zero_pads_multi(pv.data(), pl.data(), ps.data(), (int)pv.size(), s);
   }
 }
 
@@ -2073,7 +2179,8 @@ struct BatchStage {
 // read-back of its statistics; no synchronisation.  `clear_signs` zeroes the
 // sign slots first (a replayed graph must not keep an earlier run's tails).
 static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* const* d_fields, cudaStream_t s,
-                                Scratch& sc, const BatchLayout& L, BatchStage& io, bool clear_signs) {
+                                Scratch& sc, const BatchLayout& L, BatchStage& io, bool clear_signs,
+                                const SideLane* lane = nullptr) {
   const int n = (int)hs.size();
   FieldStats* d_st = (FieldStats*)sc.get(sizeof(FieldStats) * n);
   unsigned long long* d_vm = (unsigned long long*)sc.get(L.nv * 8);
@@ -2126,7 +2233,58 @@ static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* 
       for (int64_t g = 0; g < sds[i].nseg; g++) items[h->w64][fx].push_back({idx, (int)g});
     }
   }
-  enqueue_stages(ws, s);
+  size_t nit = 0;
+  for (int a = 0; a < 2; a++)
+    for (int b = 0; b < 2; b++) nit += items[a][b].size();
+  io.used_sd = all.size();
+  io.used_items = nit;
+  StreamD* d_sd = (StreamD*)sc.get(all.size() * sizeof(StreamD));
+  WorkItem* d_items = (WorkItem*)sc.get(std::max<size_t>(nit, 1) * sizeof(WorkItem));
+  if (!d_sd || !d_items) return fail(PCR_ERR_OOM, "work list allocation failed");
+  if (!io.pinned) {
+    io.v_sd = all;
+    io.sd = io.v_sd.data();
+    io.v_items.resize(std::max<size_t>(nit, 1));
+    io.items = io.v_items.data();
+  } else if (all.size() > io.cap_sd || nit > io.cap_items) {
+    return fail(PCR_ERR_INVALID_ARG, "batch work list larger than its staging");
+  } else {
+    std::memcpy(io.sd, all.data(), all.size() * sizeof(StreamD));
+  }
+  size_t off = 0;
+  for (int a = 0; a < 2; a++)
+    for (int b = 0; b < 2; b++) {
+      if (items[a][b].empty()) continue;
+      std::memcpy(io.items + off, items[a][b].data(), items[a][b].size() * sizeof(WorkItem));
+      off += items[a][b].size();
+    }
+  CUDA_TRY(cudaMemcpyAsync(d_sd, io.sd, all.size() * sizeof(StreamD), cudaMemcpyHostToDevice, s));
+  if (nit) CUDA_TRY(cudaMemcpyAsync(d_items, io.items, nit * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+  // level 0 on the call's stream; then the fixed-point coarse levels and
+  // their encode beside the decomposition and the level-0 encode
+  stages_level0(ws, s);
+  {
+    Fork fk(s, lane);
+    pcr_status e = fk.fork();
+    if (e) return e;
+    const cudaStream_t sf = fk.side();
+    stages_fixed(ws, sf);
+    stages_float(ws, s);
+    off = 0;
+    for (int a = 0; a < 2; a++)
+      for (int b = 0; b < 2; b++) {
+        if (items[a][b].empty()) continue;
+        const int vk = b ? VK_FIX : (a ? VK_F64 : VK_F32);
+        const cudaStream_t es = b ? sf : s;
+        {
+          Prof pf(b ? "encode_fixed" : "encode_float", es);
+          launch_encode(vk, a, pairs_mode[a][b] > 0, d_sd, d_items + off, (int)items[a][b].size(), es);
+        }
+        off += items[a][b].size();
+      }
+    e = fk.join();
+    if (e) return e;
+  }
   // each handle's whole-retrieval work list, kept on the device (one upload
   // for the batch, scattered by one launch)
   std::vector<WorkItem> li;
@@ -2166,44 +2324,6 @@ static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* 
     // (a copy from pageable memory has read its source when the call returns)
     for (auto& q : li_at) q.first->items_ready = true;
   }
-  size_t nit = 0;
-  for (int a = 0; a < 2; a++)
-    for (int b = 0; b < 2; b++) nit += items[a][b].size();
-  io.used_sd = all.size();
-  io.used_items = nit;
-  StreamD* d_sd = (StreamD*)sc.get(all.size() * sizeof(StreamD));
-  WorkItem* d_items = (WorkItem*)sc.get(std::max<size_t>(nit, 1) * sizeof(WorkItem));
-  if (!d_sd || !d_items) return fail(PCR_ERR_OOM, "work list allocation failed");
-  if (!io.pinned) {
-    io.v_sd = all;
-    io.sd = io.v_sd.data();
-    io.v_items.resize(std::max<size_t>(nit, 1));
-    io.items = io.v_items.data();
-  } else if (all.size() > io.cap_sd || nit > io.cap_items) {
-    return fail(PCR_ERR_INVALID_ARG, "batch work list larger than its staging");
-  } else {
-    std::memcpy(io.sd, all.data(), all.size() * sizeof(StreamD));
-  }
-  size_t off = 0;
-  for (int a = 0; a < 2; a++)
-    for (int b = 0; b < 2; b++) {
-      if (items[a][b].empty()) continue;
-      std::memcpy(io.items + off, items[a][b].data(), items[a][b].size() * sizeof(WorkItem));
-      off += items[a][b].size();
-    }
-  CUDA_TRY(cudaMemcpyAsync(d_sd, io.sd, all.size() * sizeof(StreamD), cudaMemcpyHostToDevice, s));
-  if (nit) CUDA_TRY(cudaMemcpyAsync(d_items, io.items, nit * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
-  off = 0;
-  for (int a = 0; a < 2; a++)
-    for (int b = 0; b < 2; b++) {
-      if (items[a][b].empty()) continue;
-      const int vk = b ? VK_FIX : (a ? VK_F64 : VK_F32);
-      {
-        Prof pf(b ? "encode_fixed" : "encode_float", s);
-        launch_encode(vk, a, pairs_mode[a][b] > 0, d_sd, d_items + off, (int)items[a][b].size(), s);
-      }
-      off += items[a][b].size();
-    }
   CUDA_TRY(cudaGetLastError());
   // read-back of the statistics the host tables need
   if (!io.pinned && !io.pinned_out) {
@@ -2521,9 +2641,11 @@ struct pcr_refactor_graph {
   size_t nodes = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   double gpu_ms = 0.0, host_ms = 0.0;   // of the last run
+  SideLane lane;                        // the captured fork's second stream
   ~pcr_refactor_graph() {
     for (cudaEvent_t e : ev)
       if (e) cudaEventDestroy(e);
+    lane_destroy(lane);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (cap) cudaStreamDestroy(cap);
@@ -2596,6 +2718,8 @@ extern "C" pcr_status pcr_refactor_graph_create(int n, const void* const* d_fiel
   g->io.nz = (uint32_t*)p;
   // 3. capture the whole batch on a stream of its own (tracing off while capturing)
   CUDA_TRY(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking));
+  e = lane_create(g->lane);
+  if (e) return e;
   CUDA_TRY(cudaStreamSynchronize(s));
   const bool prof = g_prof_on;
   g_prof_on = false;
@@ -2605,7 +2729,7 @@ extern "C" pcr_status pcr_refactor_graph_create(int n, const void* const* d_fiel
     Scratch sc{&g->mem, g->cap, {}};
     sc.bump = (char*)(((uintptr_t)g->arena + 255) & ~uintptr_t(255));
     sc.cap = need;
-    e = enqueue_batch(g->hs, d_fields, g->cap, sc, L, g->io, true);
+    e = enqueue_batch(g->hs, d_fields, g->cap, sc, L, g->io, true, &g->lane);
   }
   cudaGraph_t graph = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(g->cap, &graph);
@@ -2760,15 +2884,23 @@ static pcr_status enqueue_retrieve_one(const pcr_handle* h, const pcr_retrieval_
   return PCR_OK;
 }
 
-static pcr_status enqueue_reconstruct(const pcr_handle* h, const std::vector<StreamD>& sds, void* d_out,
-                                      cudaStream_t s, Scratch& sc) {
+// Reconstruction up to level 0 (Alg. 2): the level-0 recomposition on `s`
+// (after the float decode there), the fixed-point coarse levels and the
+// coarse points of the output on `sf` (after the fixed-point decode there);
+// `l0` receives the level-0 pass, which needs both.
+struct ReconL0 {
+  bool on = false;
+  TileArgs a{};
+};
+
+static pcr_status enqueue_reconstruct_coarse(const pcr_handle* h, const std::vector<StreamD>& sds, void* d_out,
+                                             cudaStream_t s, cudaStream_t sf, Scratch& sc, ReconL0& l0) {
   const FieldD f = field_desc(h);
   const size_t w = vsize(h->vk);
+  l0.on = false;
   if (h->L == 1) {
-    {
-      Prof pf("copy_raw", s);
-      launch_copy_raw(h->vk, f, to_latd(h->geo[0].lats[0], 0), sds[0].stage, d_out, s);
-    }
+    Prof pf("copy_raw", s);
+    launch_copy_raw(h->vk, f, to_latd(h->geo[0].lats[0], 0), sds[0].stage, d_out, s);
     return PCR_OK;
   }
   // level-0 recomposition (Alg. 2)
@@ -2782,30 +2914,26 @@ static pcr_status enqueue_reconstruct(const pcr_handle* h, const std::vector<Str
       decomp_subs(h, r, sds, da);
       da.retrieve = 1;
       da.comp = comp[r];
-      {
-        Prof pf(da.retrieve ? "recompose" : "decompose", s);
-        launch_tile_decomp(h->vk, da, s);
-      }
+      Prof pf("recompose", s);
+      launch_tile_decomp(h->vk, da, s);
     }
   }
   // coarse levels in fixed point: raw coarsest, then L-2 .. 1
   int64_t* xc = (int64_t*)sc.get((size_t)f.nc[0] * f.nc[1] * f.nc[2] * 8);
   if (!xc) return fail(PCR_ERR_OOM, "staging allocation failed");
   {
-    Prof pf("recon_coarsest", s);
-    launch_recon_fixed(f, h->L - 1, 1, to_latd(h->geo[0].lats[0], 0), (const int64_t*)sds[0].stage, xc, s);
+    Prof pf("recon_coarsest", sf);
+    launch_recon_fixed(f, h->L - 1, 1, to_latd(h->geo[0].lats[0], 0), (const int64_t*)sds[0].stage, xc, sf);
   }
   for (int level = h->L - 2; level >= 1; level--) {
     TileArgs a = level_args(h, level, 1, xc, xc);
     level_regions(h, level, sds, a);
-    {
-      Prof pf("recon_fixed_levels", s);
-      launch_tile_interp(VK_FIX, a, s);
-    }
+    Prof pf("recon_fixed_levels", sf);
+    launch_tile_interp(VK_FIX, a, sf);
   }
   {
-    Prof pf("coarse_out", s);
-    launch_coarse_out(h->vk, f, xc, std::ldexp(1.0, h->G - fix_bits(h->vk, h->L)), d_out, s);
+    Prof pf("coarse_out", sf);
+    launch_coarse_out(h->vk, f, xc, std::ldexp(1.0, h->G - fix_bits(h->vk, h->L)), d_out, sf);
   }
   // level 0
   TileArgs a = level_args(h, 0, 1, d_out, d_out);
@@ -2817,18 +2945,49 @@ static pcr_status enqueue_reconstruct(const pcr_handle* h, const std::vector<Str
   } else {
     level_regions(h, 0, sds, a);
   }
-  {
-    Prof pf("recon_level0", s);
-    launch_tile_interp(h->vk, a, s);
-  }
+  l0.on = true;
+  l0.a = a;
   return PCR_OK;
 }
 
+static void enqueue_reconstruct_l0(const pcr_handle* h, const ReconL0& l0, cudaStream_t s) {
+  if (!l0.on) return;
+  Prof pf("recon_level0", s);
+  launch_tile_interp(h->vk, l0.a, s);
+}
+
+// `fork`: the fixed-point chain (decode, coarse levels, coarse output) runs
+// on a second stream beside the float decode and recomposition
 static pcr_status retrieve_batch_impl(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
-                                      void* const* d_outs, cudaStream_t s, Scratch& sc) {
+                                      void* const* d_outs, cudaStream_t s, Scratch& sc, bool fork = true) {
   std::vector<std::vector<StreamD>> sds(n);
   std::vector<StreamD> all;
   std::vector<WorkItem> items[2][2];
+  // decodes (fixed point on the side stream), then the reconstruction up to
+  // level 0, then, joined, every level 0
+  auto run = [&](auto decode_all) -> pcr_status {
+    std::unique_ptr<Fork> fk;
+    if (fork) fk.reset(new Fork(s));
+    if (fk) {
+      pcr_status e = fk->fork();
+      if (e) return e;
+    }
+    const cudaStream_t sf = fk ? fk->side() : s;
+    pcr_status e = decode_all(sf);
+    if (e) return e;
+    std::vector<ReconL0> l0(n);
+    for (int k = 0; k < n; k++) {
+      e = enqueue_reconstruct_coarse(hs[k], sds[k], d_outs[k], s, sf, sc, l0[k]);
+      if (e) return e;
+    }
+    if (fk) {
+      e = fk->join();
+      if (e) return e;
+    }
+    for (int k = 0; k < n; k++) enqueue_reconstruct_l0(hs[k], l0[k], s);
+    CUDA_TRY(cudaGetLastError());
+    return PCR_OK;
+  };
   if (n == 1 && hs[0]->items_ready) {   // one handle: its kept work list
     const pcr_handle* h = hs[0];
     std::vector<int> kinds;
@@ -2837,20 +2996,20 @@ static pcr_status retrieve_batch_impl(int n, const pcr_handle* const* hs, const 
     StreamD* d_sd = (StreamD*)sc.get(sds[0].size() * sizeof(StreamD));
     if (!d_sd) return fail(PCR_ERR_OOM, "work list allocation failed");
     CUDA_TRY(cudaMemcpyAsync(d_sd, sds[0].data(), sds[0].size() * sizeof(StreamD), cudaMemcpyHostToDevice, s));
-    size_t off = 0;
-    for (int fx = 0; fx < 2; fx++) {
-      if (!h->items_n[fx]) continue;
-      const int vk = fx ? VK_FIX : h->vk;
-      {
-        Prof pf(fx ? "decode_fixed" : "decode_float", s);
-        launch_decode(vk, h->w64, d_sd, h->d_items_all + off, (int)h->items_n[fx], s);
+    return run([&](cudaStream_t sf) -> pcr_status {
+      size_t off = 0;
+      for (int fx = 0; fx < 2; fx++) {
+        if (!h->items_n[fx]) continue;
+        const int vk = fx ? VK_FIX : h->vk;
+        const cudaStream_t ds = fx ? sf : s;
+        {
+          Prof pf(fx ? "decode_fixed" : "decode_float", ds);
+          launch_decode(vk, h->w64, d_sd, h->d_items_all + off, (int)h->items_n[fx], ds);
+        }
+        off += h->items_n[fx];
       }
-      off += h->items_n[fx];
-    }
-    e = enqueue_reconstruct(h, sds[0], d_outs[0], s, sc);
-    if (e) return e;
-    CUDA_TRY(cudaGetLastError());
-    return PCR_OK;
+      return PCR_OK;
+    });
   }
   for (int k = 0; k < n; k++) {
     std::vector<int> kinds;
@@ -2876,19 +3035,23 @@ static pcr_status retrieve_batch_impl(int n, const pcr_handle* const* hs, const 
       if (items[a][b].empty()) continue;
       CUDA_TRY(cudaMemcpyAsync(d_items + off, items[a][b].data(), items[a][b].size() * sizeof(WorkItem),
                                cudaMemcpyHostToDevice, s));
-      const int vk = b ? VK_FIX : (a ? VK_F64 : VK_F32);
-      {
-        Prof pf(b ? "decode_fixed" : "decode_float", s);
-        launch_decode(vk, a, d_sd, d_items + off, (int)items[a][b].size(), s);
-      }
       off += items[a][b].size();
     }
-  for (int k = 0; k < n; k++) {
-    pcr_status e = enqueue_reconstruct(hs[k], sds[k], d_outs[k], s, sc);
-    if (e) return e;
-  }
-  CUDA_TRY(cudaGetLastError());
-  return PCR_OK;
+  return run([&](cudaStream_t sf) -> pcr_status {
+    size_t o = 0;
+    for (int a = 0; a < 2; a++)
+      for (int b = 0; b < 2; b++) {
+        if (items[a][b].empty()) continue;
+        const int vk = b ? VK_FIX : (a ? VK_F64 : VK_F32);
+        const cudaStream_t ds = b ? sf : s;
+        {
+          Prof pf(b ? "decode_fixed" : "decode_float", ds);
+          launch_decode(vk, a, d_sd, d_items + o, (int)items[a][b].size(), ds);
+        }
+        o += items[a][b].size();
+      }
+    return PCR_OK;
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -3180,7 +3343,7 @@ extern "C" pcr_status pcr_retrieve_static(const pcr_handle* h, const pcr_retriev
   Scratch sc{&mem, s, {}};
   sc.bump = base;
   sc.cap = cap;
-  return retrieve_batch_impl(1, &h, plan, &d_out, s, sc);
+  return retrieve_batch_impl(1, &h, plan, &d_out, s, sc, false);
 }
 
 extern "C" pcr_status pcr_retrieve_plan(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out,
