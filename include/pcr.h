@@ -253,6 +253,12 @@ void pcr_refactor_graph_free(pcr_refactor_graph* g);
  * the default chunk, k > 0 marching with k-plane chunks), ms (the winner's
  * time); *n_out = entries in the table; reset clears it afterwards. */
 pcr_status pcr_autotune_enable(int enable);
+/* Pin one schedule: `key` = the 7 int64 of an entry (as pcr_autotune_read
+ * gives them), `choice` one of the candidates (0, 8, 16, 32, 64, -1);
+ * every later launch of that level grid uses it (a level the marching
+ * kernel cannot take runs the general tile kernel whatever the choice).
+ * PCR_ERR_INVALID_ARG for an unknown key field or choice. */
+pcr_status pcr_autotune_set(const int64_t* key, int choice);
 pcr_status pcr_autotune_read(int max_entries, int64_t* keys, int* choice, double* ms, int* n_out, int reset);
 
 /* ---- target-driven sampled tuning (Sec. VI-A and its tuning table) ----

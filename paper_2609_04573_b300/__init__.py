@@ -131,6 +131,7 @@ _sigs = {
     "pcr_refactor_graph_handle": [_vp, C.c_int, C.POINTER(_vp)],
     "pcr_refactor_graph_info": [_vp, _i64p, _i64p, _i64p],
     "pcr_refactor_graph_times": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "pcr_autotune_set": [_i64p, C.c_int],
     "pcr_autotune_enable": [C.c_int],
     "pcr_autotune_read": [C.c_int, _i64p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int],
 }
@@ -627,6 +628,13 @@ class RefactorGraph:
 def autotune(enable=True):
     """Level-schedule autotuner on/off (pcr_autotune_enable)."""
     _check(_lib.pcr_autotune_enable(1 if enable else 0))
+
+
+def autotune_pin(key, choice):
+    """Pin the schedule of one level grid: key = (kind, retrieve, degree,
+    interp, m0, m1, m2) as autotune_table gives it (pcr_autotune_set)."""
+    k = (C.c_int64 * 7)(*key)
+    _check(_lib.pcr_autotune_set(k, int(choice)))
 
 
 def autotune_table(reset=False):

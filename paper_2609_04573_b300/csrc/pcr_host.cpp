@@ -2793,6 +2793,12 @@ extern "C" pcr_status pcr_autotune_enable(int enable) {
   return PCR_OK;
 }
 
+extern "C" pcr_status pcr_autotune_set(const int64_t* key, int choice) {
+  if (!key) return fail(PCR_ERR_INVALID_ARG, "null key");
+  if (!autotune_pin(key, choice)) return fail(PCR_ERR_INVALID_ARG, "unknown key field or schedule choice");
+  return PCR_OK;
+}
+
 extern "C" pcr_status pcr_autotune_read(int max_entries, int64_t* keys, int* choice, double* ms, int* n_out,
                                         int reset) {
   if (!n_out) return fail(PCR_ERR_INVALID_ARG, "null argument");

@@ -254,6 +254,7 @@ long long launch_count();
 void add_launches(long long n);
 // autotuner of the level-interpolation schedule (pcr_tiles.cu)
 int set_autotune(int on);   // returns the previous setting
+bool autotune_pin(const int64_t* key, int choice);   // false: unknown key field or choice
 int autotune_entries(int max_entries, int64_t* keys, int* choice, double* ms);
 void clear_autotune();
 

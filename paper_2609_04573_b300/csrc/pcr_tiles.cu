@@ -1988,6 +1988,20 @@ int launch_tuned(int vk, const TileArgs& a, cudaStream_t s) {
 
 int set_autotune(int on) { return g_tune_on.exchange(on ? 1 : 0); }
 
+// pin one entry of the table (ms recorded as 0): every later launch of that
+// (value kind, direction, degree, interpolation, level grid) uses `choice`
+bool autotune_pin(const int64_t* key, int choice) {
+  bool known = false;
+  for (int c : kTuneCand) known = known || c == choice;
+  if (!known || key[0] < 0 || key[0] > 2 || key[1] < 0 || key[1] > 1 || (key[2] != 1 && key[2] != 3) ||
+      key[3] < 0 || key[3] > 1)
+    return false;
+  const TuneKey k{(int)key[0], (int)key[1], (int)key[2], (int)key[3], key[4], key[5], key[6]};
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[k] = TuneVal{choice, 0.0f};
+  return true;
+}
+
 int autotune_entries(int max_entries, int64_t* keys, int* choice, double* ms) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   int k = 0;
