@@ -464,12 +464,31 @@ def build_units(comp, tabs, kind):
     return units
 
 
-def greedy(comp, tabs, target, kind):
-    """Greedy interpreter: returns (planes per stream, bound, satisfied)."""
+def greedy(comp, tabs, target, kind, have=None):
+    """Greedy interpreter: returns (planes per stream, bound, satisfied).
+
+    ``have`` (incremental invocation, the progressive retrieval of Sec. III-A
+    reusing fetched planes): planes already fetched per stream.  The plan
+    starts there and never drops a plane; a step costs only the bytes of the
+    planes it adds beyond what is fetched, and steps whose planes are all
+    fetched are passed over.  Without ``have`` every step costs its
+    staircase increment (the same number when nothing is fetched)."""
     n = len(tabs)
-    b = [0] * n
+    b = list(have) if have is not None else [0] * n
     units = build_units(comp, tabs, kind)
     pos = [0] * len(units)
+    if have is not None:
+        for ui, u in enumerate(units):
+            while pos[ui] < len(u.steps) and all(nb <= b[i] for i, nb in u.steps[pos[ui]][0]):
+                pos[ui] += 1
+
+    def step_cost(upd, db, bb):
+        if have is None:
+            return db
+        top = {}
+        for i, nb in upd:
+            top[i] = max(top.get(i, 0), nb)
+        return sum(tabs[i]["bytes"][max(nb, bb[i])] - tabs[i]["bytes"][bb[i]] for i, nb in top.items())
 
     def evaluate(bb):
         err = [tabs[i]["maxerr"][bb[i]] for i in range(n)]
@@ -496,9 +515,10 @@ def greedy(comp, tabs, target, kind):
             if pos[ui] >= len(u.steps):
                 continue
             upd, db, _ = u.steps[pos[ui]]
+            db = step_cost(upd, db, b)
             trial = list(b)
             for i, nb in upd:
-                trial[i] = nb
+                trial[i] = nb if have is None else max(trial[i], nb)
             nbnd = evaluate(trial)
             gain = bound - nbnd
             ratio = math.inf if db == 0 else gain / db

@@ -223,19 +223,22 @@ def _add_factors(meta, geo):
     meta["decomp_factors"] = df
 
 
-def plan(handle, target):
-    """Retrieval interpreter: planes per stream for a target."""
+def plan(handle, target, have=None):
+    """Retrieval interpreter: planes per stream for a target.  ``have``: a
+    plan whose planes are already fetched (incremental invocation, see
+    bounds.greedy); the result contains it."""
     meta = handle["meta"]
     tabs = [s["tab"] for s in handle["streams"]]
     comp = handle["comp"]
+    hb = have["b"] if isinstance(have, dict) else have
     if target.kind in ("abs", "rel"):
         tau = target.value * (meta["R"] if target.kind == "rel" else 1.0)
-        b, bound, ok = bd.greedy(comp, tabs, tau, "linf")
+        b, bound, ok = bd.greedy(comp, tabs, tau, "linf", hb)
         psnr = None
     else:
         ratio = meta["R"] / (10.0 ** (target.value / 20.0))
         sse_max = meta["n"] * ratio * ratio
-        b, bound, ok = bd.greedy(comp, tabs, sse_max, "l2")
+        b, bound, ok = bd.greedy(comp, tabs, sse_max, "l2", hb)
         psnr = None
     total = sum(t["bytes"][bi] for t, bi in zip(tabs, b))
     return dict(b=b, bound=bound, satisfied=ok, bytes=total, kind=target.kind)
