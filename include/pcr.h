@@ -298,6 +298,17 @@ pcr_status pcr_get_scheme(const pcr_handle* h, pcr_scheme* out);
  * PCR_ERR_UNSATISFIABLE (plan still filled with all planes) when the bound
  * with every plane exceeds the target. */
 pcr_status pcr_plan(const pcr_handle* h, const pcr_target* target, pcr_retrieval_plan* out);
+/* Incremental invocation (progressive refinement, Sec. III-A: a retrieval
+ * refines an earlier one and re-uses the planes it fetched): plan `target`
+ * starting from `have` (a plan of this handle whose planes the caller
+ * holds).  The result contains `have` stream by stream; the greedy steps
+ * are ranked by the bytes they add beyond `have`, and steps whose planes
+ * `have` already holds are passed over.  out->bytes is the whole plan's
+ * size; the bytes to fetch are out->bytes - have->bytes.  From an empty
+ * plan it equals pcr_plan.  Errors: as pcr_plan; PCR_ERR_INVALID_ARG when
+ * `have` does not match the handle (stream count, plane counts). */
+pcr_status pcr_plan_more(const pcr_handle* h, const pcr_target* target, const pcr_retrieval_plan* have,
+                         pcr_retrieval_plan* out);
 
 /* ---- retrieve (Algorithm 2) ------------------------------------------- */
 /* One call: plan `target` (as pcr_plan) and reconstruct into the caller's

@@ -102,6 +102,7 @@ _sigs = {
     "pcr_refactor_batch": [C.c_int, C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(_i64p), C.POINTER(C.c_int),
                            C.POINTER(_Scheme), C.POINTER(_Allocator), _vp, C.POINTER(_vp)],
     "pcr_plan": [_vp, C.POINTER(_Target), C.POINTER(_Plan)],
+    "pcr_plan_more": [_vp, C.POINTER(_Target), C.POINTER(_Plan), C.POINTER(_Plan)],
     "pcr_retrieve": [_vp, C.POINTER(_Target), _vp, _vp, C.POINTER(_Info)],
     "pcr_retrieve_plan": [_vp, C.POINTER(_Plan), _vp, _vp],
     "pcr_retrieve_batch": [C.c_int, C.POINTER(_vp), C.POINTER(_Target), C.POINTER(_vp), _vp,
@@ -359,9 +360,15 @@ class Handle:
         _check(_lib.pcr_max_ordering(self._p, arr, C.byref(n)))
         return list(arr)
 
-    def plan(self, target, allow_unsat=False):
+    def plan(self, target, allow_unsat=False, have=None):
+        """Planes per stream for `target` (pcr_plan).  `have`: a Plan whose
+        planes are already fetched; the result contains it and is ranked by
+        the bytes it adds (pcr_plan_more)."""
         p = _Plan()
-        st = _lib.pcr_plan(self._p, C.byref(target.c()), C.byref(p))
+        if have is None:
+            st = _lib.pcr_plan(self._p, C.byref(target.c()), C.byref(p))
+        else:
+            st = _lib.pcr_plan_more(self._p, C.byref(target.c()), C.byref(have._c), C.byref(p))
         if st != OK and not (st == ERR_UNSAT and allow_unsat):
             _check(st)
         return Plan(list(p.planes[:p.nstreams]), p.bound, p.psnr_bound, p.bytes, bool(p.satisfied), p)
@@ -623,6 +630,25 @@ class RefactorGraph:
         if getattr(self, "_g", None) and self._g.value:
             _lib.pcr_refactor_graph_free(self._g)
             self._g = C.c_void_p(None)
+
+
+class Progressive:
+    """A progressive retrieval session over one handle (Sec. III-A
+    refinement): each refine() plans the new target from the planes fetched
+    so far (pcr_plan_more), retrieves, and reports the bytes it added."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.plan = None
+        self.fetched = 0
+
+    def refine(self, target, out=None, stream=None):
+        p = self.handle.plan(target, allow_unsat=True, have=self.plan)
+        added = p.bytes - (self.plan.bytes if self.plan is not None else 0)
+        out, _ = self.handle.retrieve(p, out=out, stream=stream)
+        self.plan = p
+        self.fetched += added
+        return out, p, added
 
 
 def autotune(enable=True):

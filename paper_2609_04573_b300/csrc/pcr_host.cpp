@@ -1458,17 +1458,51 @@ struct BoundEval {
   }
 };
 
-// greedy interpreter: largest bound decrease per byte until the target holds
-bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, double& bound) {
+// greedy interpreter: largest bound decrease per byte until the target holds.
+// `have` (incremental invocation, Sec. III-A progressive refinement): planes
+// already fetched per stream; the plan starts there and never drops a plane,
+// a step costs only the bytes of planes not yet fetched, and steps whose
+// planes are all fetched are passed over.
+bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, double& bound,
+            const std::vector<int>* have = nullptr) {
   const int n = (int)h->tabs.size();
-  b.assign(n, 0);
+  if (have) b = *have;
+  else b.assign(n, 0);
   const std::vector<Unit>& units = cached_units(h, linf);
   std::vector<size_t> pos(units.size(), 0);
   std::vector<double> err(n), sq(n);
   for (int i = 0; i < n; i++) {
-    err[i] = h->tabs[i].maxerr[0];
-    sq[i] = h->tabs[i].sq[0];
+    err[i] = h->tabs[i].maxerr[b[i]];
+    sq[i] = h->tabs[i].sq[b[i]];
   }
+  if (have)
+    for (size_t ui = 0; ui < units.size(); ui++)
+      for (; pos[ui] < units[ui].steps.size(); pos[ui]++) {
+        bool covered = true;
+        for (auto& up : units[ui].steps[pos[ui]].upd) covered = covered && up.second <= b[up.first];
+        if (!covered) break;
+      }
+  // bytes a step adds to the current plan
+  std::vector<std::pair<int, int>> top;
+  auto step_cost = [&](const Step& st) -> uint64_t {
+    if (!have) return st.db;
+    top.clear();
+    for (auto& up : st.upd) {
+      bool found = false;
+      for (auto& tp : top)
+        if (tp.first == up.first) {
+          tp.second = std::max(tp.second, up.second);
+          found = true;
+        }
+      if (!found) top.push_back(up);
+    }
+    uint64_t c = 0;
+    for (auto& tp : top) {
+      const int i = tp.first;
+      c += h->tabs[i].bytes[std::max(tp.second, b[i])] - h->tabs[i].bytes[b[i]];
+    }
+    return c;
+  };
   BoundEval be(h->comp, !linf);
   std::vector<int> unit_level(units.size());
   for (size_t ui = 0; ui < units.size(); ui++) unit_level[ui] = h->geo[units[ui].ids[0]].level;
@@ -1497,9 +1531,10 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
     saved.clear();
     for (auto& up : st.upd) {
       saved.push_back({up.first, b[up.first]});
-      b[up.first] = up.second;
-      err[up.first] = h->tabs[up.first].maxerr[up.second];
-      sq[up.first] = h->tabs[up.first].sq[up.second];
+      const int nb = have ? std::max(b[up.first], up.second) : up.second;
+      b[up.first] = nb;
+      err[up.first] = h->tabs[up.first].maxerr[nb];
+      sq[up.first] = h->tabs[up.first].sq[nb];
     }
   };
   auto undo = [&]() {
@@ -1518,6 +1553,7 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
       const Unit& u = units[ui];
       if (pos[ui] >= u.steps.size()) continue;
       const Step& st = u.steps[pos[ui]];
+      const uint64_t db = step_cost(st);
       const double own0 = unit_value(u);
       apply(st);
       const double nb = evaluate(unit_level[ui], false);
@@ -1525,8 +1561,8 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
       undo();
       const double gain = bound - nb;
       const double inf = std::numeric_limits<double>::infinity();
-      const double ratio = st.db == 0 ? inf : gain / (double)st.db;
-      if (gain > 0 || st.db == 0) {
+      const double ratio = db == 0 ? inf : gain / (double)db;
+      if (gain > 0 || db == 0) {
         if (!have_best || ratio > best_r) {
           have_best = true;
           best_r = ratio;
@@ -1535,7 +1571,7 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
         }
       }
       const double own = (own0 - own1) * u.weight;
-      const double fr = st.db == 0 ? inf : own / (double)st.db;
+      const double fr = db == 0 ? inf : own / (double)db;
       if (!have_fb || fr > fb_r) {
         have_fb = true;
         fb_r = fr;
@@ -2821,8 +2857,8 @@ extern "C" pcr_status pcr_refactor(const void* d_field, int ndim, const int64_t*
 // ---------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------
-extern "C" pcr_status pcr_plan(const pcr_handle* h, const pcr_target* t, pcr_retrieval_plan* out) {
-  if (!h || !t || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+static pcr_status plan_impl(const pcr_handle* h, const pcr_target* t, const std::vector<int>* have,
+                            pcr_retrieval_plan* out) {
   if (!(t->value >= 0) || !std::isfinite(t->value)) return fail(PCR_ERR_INVALID_ARG, "bad target value");
   std::vector<int> b;
   double bound = 0;
@@ -2831,12 +2867,12 @@ extern "C" pcr_status pcr_plan(const pcr_handle* h, const pcr_target* t, pcr_ret
   std::memset(out, 0, sizeof(*out));
   if (t->kind == PCR_TARGET_ABS || t->kind == PCR_TARGET_REL) {
     const double tau = t->value * (t->kind == PCR_TARGET_REL ? R : 1.0);
-    ok = greedy(h, tau, true, b, bound);
+    ok = greedy(h, tau, true, b, bound, have);
     out->psnr_bound = 0;
   } else if (t->kind == PCR_TARGET_PSNR) {
     const double ratio = R / std::pow(10.0, t->value / 20.0);
     const double sse_max = (double)h->meta.n * ratio * ratio;
-    ok = greedy(h, sse_max, false, b, bound);
+    ok = greedy(h, sse_max, false, b, bound, have);
     const double rmse = std::sqrt(bound / (double)h->meta.n);
     out->psnr_bound = rmse > 0 ? 20.0 * std::log10(R / rmse) : std::numeric_limits<double>::infinity();
   } else {
@@ -2853,6 +2889,24 @@ extern "C" pcr_status pcr_plan(const pcr_handle* h, const pcr_target* t, pcr_ret
   out->satisfied = ok ? 1 : 0;
   if (!ok) return fail(PCR_ERR_UNSATISFIABLE, "target tighter than the all-planes bound");
   return PCR_OK;
+}
+
+extern "C" pcr_status pcr_plan(const pcr_handle* h, const pcr_target* t, pcr_retrieval_plan* out) {
+  if (!h || !t || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  return plan_impl(h, t, nullptr, out);
+}
+
+extern "C" pcr_status pcr_plan_more(const pcr_handle* h, const pcr_target* t, const pcr_retrieval_plan* have,
+                                    pcr_retrieval_plan* out) {
+  if (!h || !t || !have || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  const int ns = (int)h->tabs.size();
+  if (have->nstreams != ns) return fail(PCR_ERR_INVALID_ARG, "plan does not match the handle");
+  std::vector<int> hv(ns);
+  for (int i = 0; i < ns; i++) {
+    if (have->planes[i] < 0 || have->planes[i] > h->B) return fail(PCR_ERR_INVALID_ARG, "plan plane count out of range");
+    hv[i] = have->planes[i];
+  }
+  return plan_impl(h, t, &hv, out);
 }
 
 // ---------------------------------------------------------------------------
