@@ -353,6 +353,7 @@ def run_pcr(args):
     # progressive retrieval across the configuration's targets (plan +
     # retrieve of the per-level handle, event-timed, 5 repetitions each)
     retrievals = sweep(pcr, h, x, out, stream, R)
+    progressive = progressive_leg(pcr, h, x, out, R)
 
     # e2e through the public API with host buffers (pinned), every step's
     # copies inside the timed region: the field in from pinned host memory,
@@ -445,7 +446,7 @@ def run_pcr(args):
                                  "retrieve": ((pl.bytes + 4 * n) / (retrieve_ms * 1e-3) / 1e9) / hbm
                                  if retrieve_ms else None},
         "retrieve_bytes_per_elem": pl.bytes / n, "bound_respected_full_size": bool(bound_ok),
-        "max_err": err, "roofline": roof, "stages": stages,
+        "max_err": err, "roofline": roof, "stages": stages, "progressive": progressive,
         "e2e": {"value": world * 2 * nbytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms,
                 "pipelined": "upload of step i+1 and download of step i-1 overlap step i (two copy streams)"},
@@ -487,6 +488,28 @@ def sweep(pcr, h, x, out, stream, R, targets=SWEEP, reps=5):
                     "bytes_per_value": plr.bytes / x.numel(), "satisfied": bool(plr.satisfied),
                     "within_target": bool(ok) if plr.satisfied else None, "max_err": e})
     return res
+
+
+def progressive_leg(pcr, h, x, out, R, values=(1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6)):
+    """A progressive session over the headline handle (Progressive.refine:
+    each tighter relative target planned from the planes already fetched):
+    per refinement the bytes it adds, the retrieval time and the error; and
+    the one-shot plan of the last target for comparison."""
+    import torch
+    sess = pcr.Progressive(h)
+    rows = []
+    for v in values:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o, pl, added = sess.refine(pcr.Target("rel", v), out=out)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e = (o.double() - x.double()).abs().max().item()
+        rows.append({"target": f"rel {v:g}", "added_bytes": added, "plan_bytes": pl.bytes,
+                     "satisfied": bool(pl.satisfied), "ms": dt * 1e3,
+                     "within_target": (e <= v * R) if pl.satisfied else None})
+    one = h.plan(pcr.Target("rel", values[-1]), allow_unsat=True)
+    return {"refinements": rows, "session_bytes": sess.fetched, "one_shot_bytes_last_target": one.bytes}
 
 
 def precision_leg(pcr, dev):
