@@ -310,6 +310,33 @@ pcr_status pcr_plan(const pcr_handle* h, const pcr_target* target, pcr_retrieval
 pcr_status pcr_plan_more(const pcr_handle* h, const pcr_target* target, const pcr_retrieval_plan* have,
                          pcr_retrieval_plan* out);
 
+/* ---- block sharding of one field (Sec. VII: independent blocks) -------
+ * A field split along axis 0 into slabs, each refactored as a field of its
+ * own (on this GPU or on the ranks that hold them), retrieved for one
+ * whole-field target:
+ * plan_global: plans[k] for hs[k] (n blocks of one field).  abs / rel
+ *   targets: relative to the whole field's range (max of the blocks'
+ *   maxima minus min of their minima); every block planned by pcr_plan for
+ *   that absolute tolerance; *bound = the largest block bound.  PSNR: one
+ *   budget N (R 10^(-psnr/20))^2 of squared errors (N points in all
+ *   blocks) spent by one greedy over every block's planning units (the step
+ *   with the largest decrease of its own block's L2 bound per byte; ties to
+ *   the earlier block, then the earlier unit); *bound = the blocks' summed
+ *   bound, plans[k].bound each block's.  One block gives its pcr_plan.
+ *   Errors: as pcr_plan (PCR_ERR_UNSATISFIABLE: some block cannot meet its
+ *   share even with every plane; the plans are still filled).
+ * export_plan_state: what the planner needs of a handle (statistics and
+ *   per-stream tables, no planes) as a host buffer (free with
+ *   pcr_buffer_free) that another process can import.
+ * import_plan_state: a planning-only handle from such a buffer: it plans
+ *   (pcr_plan, pcr_plan_more, pcr_plan_global) but holds no planes, so
+ *   retrievals, stream copies and pcr_serialize return PCR_ERR_UNSUPPORTED.
+ *   PCR_ERR_CORRUPT on a bad magic, length or checksum. */
+pcr_status pcr_plan_global(int n, const pcr_handle* const* hs, const pcr_target* target,
+                           pcr_retrieval_plan* plans, double* bound, int* satisfied);
+pcr_status pcr_export_plan_state(const pcr_handle* h, void** buf, size_t* len);
+pcr_status pcr_import_plan_state(const void* buf, size_t len, pcr_handle** out);
+
 /* ---- retrieve (Algorithm 2) ------------------------------------------- */
 /* One call: plan `target` (as pcr_plan) and reconstruct into the caller's
  * device buffer `d_out` (the field's shape and dtype, or the box's when

@@ -103,6 +103,10 @@ _sigs = {
                            C.POINTER(_Scheme), C.POINTER(_Allocator), _vp, C.POINTER(_vp)],
     "pcr_plan": [_vp, C.POINTER(_Target), C.POINTER(_Plan)],
     "pcr_plan_more": [_vp, C.POINTER(_Target), C.POINTER(_Plan), C.POINTER(_Plan)],
+    "pcr_plan_global": [C.c_int, C.POINTER(_vp), C.POINTER(_Target), C.POINTER(_Plan), C.POINTER(C.c_double),
+                        C.POINTER(C.c_int)],
+    "pcr_export_plan_state": [_vp, C.POINTER(_vp), C.POINTER(C.c_size_t)],
+    "pcr_import_plan_state": [_vp, C.c_size_t, C.POINTER(_vp)],
     "pcr_retrieve": [_vp, C.POINTER(_Target), _vp, _vp, C.POINTER(_Info)],
     "pcr_retrieve_plan": [_vp, C.POINTER(_Plan), _vp, _vp],
     "pcr_retrieve_batch": [C.c_int, C.POINTER(_vp), C.POINTER(_Target), C.POINTER(_vp), _vp,
@@ -373,6 +377,15 @@ class Handle:
             _check(st)
         return Plan(list(p.planes[:p.nstreams]), p.bound, p.psnr_bound, p.bytes, bool(p.satisfied), p)
 
+    def export_plan_state(self):
+        """What the planner needs of this handle (no planes), as bytes."""
+        buf, n = C.c_void_p(), C.c_size_t()
+        _check(_lib.pcr_export_plan_state(self._p, C.byref(buf), C.byref(n)))
+        try:
+            return C.string_at(buf, n.value)
+        finally:
+            _lib.pcr_buffer_free(buf)
+
     def plan_from_planes(self, planes):
         p = _Plan()
         p.nstreams = len(planes)
@@ -630,6 +643,32 @@ class RefactorGraph:
         if getattr(self, "_g", None) and self._g.value:
             _lib.pcr_refactor_graph_free(self._g)
             self._g = C.c_void_p(None)
+
+
+def import_plan_state(data, shape, dtype=torch.float32):
+    """A planning-only Handle from export_plan_state bytes (plans, no
+    retrieval)."""
+    buf = C.create_string_buffer(data, len(data))
+    out = C.c_void_p()
+    _check(_lib.pcr_import_plan_state(buf, len(data), C.byref(out)))
+    return Handle(out.value, shape, dtype, None)
+
+
+def plan_global(handles, target):
+    """Plans of the blocks of one field for a whole-field target
+    (pcr_plan_global): (plans, bound, satisfied)."""
+    n = len(handles)
+    hp = (C.c_void_p * n)(*[h._p.value for h in handles])
+    pl = (_Plan * n)()
+    bnd, sat = C.c_double(), C.c_int()
+    st = _lib.pcr_plan_global(n, hp, C.byref(target.c()), pl, C.byref(bnd), C.byref(sat))
+    if st not in (OK, ERR_UNSAT):
+        _check(st)
+    plans = []
+    for k in range(n):
+        c = _Plan.from_buffer_copy(pl[k])
+        plans.append(Plan(list(c.planes[:c.nstreams]), c.bound, c.psnr_bound, c.bytes, bool(c.satisfied), c))
+    return plans, bnd.value, bool(sat.value)
 
 
 class Progressive:

@@ -2891,6 +2891,172 @@ static pcr_status plan_impl(const pcr_handle* h, const pcr_target* t, const std:
   return PCR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// one target for several blocks of a field (axis-0 slabs refactored one by
+// one, Sec. VII): error bounds per block at the field's absolute tolerance;
+// PSNR with one squared-error budget spent by one greedy over every block's
+// units (the largest decrease of its own block's L2 bound per byte, ties to
+// the earlier block then unit; when nothing lowers a bound, the largest
+// decrease of the stream's own squared-error entry times the unit's weight
+// per byte); one block gives the block's own plan
+// ---------------------------------------------------------------------------
+namespace {
+struct BlockPlan {
+  const pcr_handle* h;
+  std::vector<int> b;
+  std::vector<double> err, sq;
+  std::unique_ptr<BoundEval> be;
+  const std::vector<Unit>* units;
+  std::vector<size_t> pos;
+  std::vector<int> unit_level;
+  double E = 0;
+};
+}  // namespace
+
+static bool greedy_l2_global(std::vector<BlockPlan>& bp, double budget, double& total) {
+  for (BlockPlan& p : bp) {
+    const int n = (int)p.h->tabs.size();
+    p.b.assign(n, 0);
+    p.err.resize(n);
+    p.sq.resize(n);
+    for (int i = 0; i < n; i++) {
+      p.err[i] = p.h->tabs[i].maxerr[0];
+      p.sq[i] = p.h->tabs[i].sq[0];
+    }
+    p.be.reset(new BoundEval(p.h->comp, true));
+    p.units = &cached_units(p.h, false);
+    p.pos.assign(p.units->size(), 0);
+    p.unit_level.resize(p.units->size());
+    for (size_t ui = 0; ui < p.units->size(); ui++) p.unit_level[ui] = p.h->geo[(*p.units)[ui].ids[0]].level;
+    p.E = p.be->eval_from(p.h->L - 1, p.err, p.sq, true);
+  }
+  total = 0.0;
+  for (BlockPlan& p : bp) total += p.E;
+  std::vector<std::pair<int, int>> saved;
+  auto apply = [&](BlockPlan& p, const Step& st) {
+    saved.clear();
+    for (auto& up : st.upd) {
+      saved.push_back({up.first, p.b[up.first]});
+      p.b[up.first] = up.second;
+      p.err[up.first] = p.h->tabs[up.first].maxerr[up.second];
+      p.sq[up.first] = p.h->tabs[up.first].sq[up.second];
+    }
+  };
+  auto undo = [&](BlockPlan& p) {
+    for (auto it = saved.rbegin(); it != saved.rend(); ++it) {
+      p.b[it->first] = it->second;
+      p.err[it->first] = p.h->tabs[it->first].maxerr[it->second];
+      p.sq[it->first] = p.h->tabs[it->first].sq[it->second];
+    }
+  };
+  const double inf = std::numeric_limits<double>::infinity();
+  while (total > budget) {
+    bool have_best = false, have_fb = false;
+    double best_r = 0, fb_r = 0, best_e = 0, fb_e = 0;
+    size_t best_k = 0, best_u = 0, fb_k = 0, fb_u = 0;
+    for (size_t k = 0; k < bp.size(); k++) {
+      BlockPlan& p = bp[k];
+      for (size_t ui = 0; ui < p.units->size(); ui++) {
+        const Unit& u = (*p.units)[ui];
+        if (p.pos[ui] >= u.steps.size()) continue;
+        const Step& st = u.steps[p.pos[ui]];
+        const int i0 = u.ids[0];
+        const double own0 = p.sq[i0];
+        apply(p, st);
+        const double ne = p.be->eval_from(p.unit_level[ui], p.err, p.sq, false);
+        const double own1 = p.sq[i0];
+        undo(p);
+        const double gain = p.E - ne;
+        const double ratio = st.db == 0 ? inf : gain / (double)st.db;
+        if (gain > 0 || st.db == 0) {
+          if (!have_best || ratio > best_r) {
+            have_best = true;
+            best_r = ratio;
+            best_k = k;
+            best_u = ui;
+            best_e = ne;
+          }
+        }
+        const double own = (own0 - own1) * u.weight;
+        const double fr = st.db == 0 ? inf : own / (double)st.db;
+        if (!have_fb || fr > fb_r) {
+          have_fb = true;
+          fb_r = fr;
+          fb_k = k;
+          fb_u = ui;
+          fb_e = ne;
+        }
+      }
+    }
+    if (!have_best) {
+      if (!have_fb) return false;
+      best_k = fb_k;
+      best_u = fb_u;
+      best_e = fb_e;
+    }
+    BlockPlan& p = bp[best_k];
+    apply(p, (*p.units)[best_u].steps[p.pos[best_u]]);
+    p.be->eval_from(p.unit_level[best_u], p.err, p.sq, true);   // refresh the kept partial results
+    p.pos[best_u]++;
+    total = total - p.E + best_e;
+    p.E = best_e;
+  }
+  return true;
+}
+
+extern "C" pcr_status pcr_plan_global(int n, const pcr_handle* const* hs, const pcr_target* t,
+                                      pcr_retrieval_plan* plans, double* bound, int* satisfied) {
+  if (n <= 0 || !hs || !t || !plans) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  for (int k = 0; k < n; k++)
+    if (!hs[k]) return fail(PCR_ERR_INVALID_ARG, "null handle");
+  if (!(t->value >= 0) || !std::isfinite(t->value)) return fail(PCR_ERR_INVALID_ARG, "bad target value");
+  double lo = hs[0]->xmin, hi = hs[0]->xmax;
+  int64_t N = 0;
+  for (int k = 0; k < n; k++) {
+    lo = std::min(lo, hs[k]->xmin);
+    hi = std::max(hi, hs[k]->xmax);
+    N += hs[k]->meta.n;
+  }
+  const double R = hi - lo;
+  bool ok = true;
+  double bnd = 0;
+  if (t->kind == PCR_TARGET_ABS || t->kind == PCR_TARGET_REL) {
+    const double tau = t->value * (t->kind == PCR_TARGET_REL ? R : 1.0);
+    const pcr_target ta{PCR_TARGET_ABS, tau, 0, {0, 0, 0}, {0, 0, 0}};
+    for (int k = 0; k < n; k++) {
+      const pcr_status e = plan_impl(hs[k], &ta, nullptr, &plans[k]);
+      if (e && e != PCR_ERR_UNSATISFIABLE) return e;
+      ok = ok && plans[k].satisfied;
+      bnd = k ? std::max(bnd, plans[k].bound) : plans[k].bound;
+    }
+  } else if (t->kind == PCR_TARGET_PSNR) {
+    const double ratio = R / std::pow(10.0, t->value / 20.0);
+    const double budget = (double)N * ratio * ratio;
+    std::vector<BlockPlan> bp(n);
+    for (int k = 0; k < n; k++) bp[k].h = hs[k];
+    ok = greedy_l2_global(bp, budget, bnd);
+    for (int k = 0; k < n; k++) {
+      pcr_retrieval_plan& o = plans[k];
+      std::memset(&o, 0, sizeof(o));
+      o.nstreams = (int)bp[k].b.size();
+      uint64_t bytes = 0;
+      for (int i = 0; i < o.nstreams; i++) {
+        o.planes[i] = bp[k].b[i];
+        bytes += hs[k]->tabs[i].bytes[bp[k].b[i]];
+      }
+      o.bytes = bytes;
+      o.bound = bp[k].E;
+      o.satisfied = ok ? 1 : 0;
+    }
+  } else {
+    return fail(PCR_ERR_INVALID_ARG, "bad target kind");
+  }
+  if (bound) *bound = bnd;
+  if (satisfied) *satisfied = ok ? 1 : 0;
+  if (!ok) return fail(PCR_ERR_UNSATISFIABLE, "target tighter than the all-planes bound of some block");
+  return PCR_OK;
+}
+
 extern "C" pcr_status pcr_plan(const pcr_handle* h, const pcr_target* t, pcr_retrieval_plan* out) {
   if (!h || !t || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   return plan_impl(h, t, nullptr, out);
@@ -3020,6 +3186,8 @@ static void enqueue_reconstruct_l0(const pcr_handle* h, const ReconL0& l0, cudaS
 // on a second stream beside the float decode and recomposition
 static pcr_status retrieve_batch_impl(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
                                       void* const* d_outs, cudaStream_t s, Scratch& sc, bool fork = true) {
+  for (int k = 0; k < n; k++)
+    if (!hs[k]->d_block) return fail(PCR_ERR_UNSUPPORTED, "a planning-only handle holds no planes");
   std::vector<std::vector<StreamD>> sds(n);
   std::vector<StreamD> all;
   std::vector<WorkItem> items[2][2];
@@ -3260,6 +3428,7 @@ static pcr_status enqueue_reconstruct_box(const pcr_handle* h, const std::vector
 extern "C" pcr_status pcr_retrieve_box(const pcr_handle* h, const pcr_retrieval_plan* plan, const int64_t* lo,
                                        const int64_t* hi, void* d_out, void* cuda_stream) {
   if (!h || !plan || !lo || !hi || !d_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  if (!h->d_block) return fail(PCR_ERR_UNSUPPORTED, "a planning-only handle holds no planes");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   // user axes -> the internal 3-D view (2-D fields are 1 x n0 x n1)
   FBox B0{{0, 0, 0}, {1, 1, 1}};
@@ -3575,6 +3744,7 @@ extern "C" pcr_status pcr_field_stats(const pcr_handle* h, double* xmin, double*
 extern "C" pcr_status pcr_stream_copy(const pcr_handle* h, int i, uint32_t* planes_host, uint32_t* signs_host,
                                       uint32_t* sign_counts_host, uint64_t* pairs_host) {
   if (!h || i < 0 || i >= (int)h->geo.size()) return fail(PCR_ERR_INVALID_ARG, "bad stream index");
+  if (!h->d_block) return fail(PCR_ERR_UNSUPPORTED, "a planning-only handle holds no planes");
   const int64_t words = h->geo[i].n_pad() / 32;
   const int64_t nseg = (h->geo[i].n_pad() + kSegElems - 1) / kSegElems;
   if (planes_host) CUDA_TRY(cudaMemcpy(planes_host, h->d_planes + h->plane_off[i], (size_t)h->B * words * 4, cudaMemcpyDeviceToHost));
@@ -3661,12 +3831,10 @@ struct Reader {
 const uint64_t kMagic = 0x3230524350ull;  // "PCR02"
 }  // namespace
 
-extern "C" pcr_status pcr_serialize(const pcr_handle* h, void** buf, size_t* len) {
-  if (!h || !buf || !len) return fail(PCR_ERR_INVALID_ARG, "null argument");
-  Writer w;
-  w.put(kMagic);
-  // header section
-  Writer hd;
+// what a handle's tables and planner need: dims, dtype, scheme, field
+// statistics, per stream its maximum, exponent, shift, nonzero-plane counts,
+// sign counts per segment and plane-pair counts
+static pcr_status write_header(const pcr_handle* h, Writer& hd) {
   hd.put(h->ndim);
   for (int i = 0; i < 3; i++) hd.put(h->dims[i]);
   hd.put(h->dtype);
@@ -3692,6 +3860,17 @@ extern "C" pcr_status pcr_serialize(const pcr_handle* h, void** buf, size_t* len
     hd.put(np);
     hd.raw(h->pairs[i].data(), np * 8);
   }
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_serialize(const pcr_handle* h, void** buf, size_t* len) {
+  if (!h || !buf || !len) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  if (!h->d_block) return fail(PCR_ERR_UNSUPPORTED, "a planning-only handle holds no planes");
+  Writer w;
+  w.put(kMagic);
+  Writer hd;
+  pcr_status e = write_header(h, hd);
+  if (e) return e;
   w.put((uint64_t)hd.buf.size());
   w.put(crc32(hd.buf.data(), hd.buf.size()));
   w.raw(hd.buf.data(), hd.buf.size());
@@ -3714,19 +3893,7 @@ extern "C" pcr_status pcr_serialize(const pcr_handle* h, void** buf, size_t* len
   return PCR_OK;
 }
 
-extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_allocator* alloc, void* cuda_stream,
-                                      pcr_handle** out) {
-  if (!buf || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  Reader r{(const uint8_t*)buf, len};
-  if (r.get<uint64_t>() != kMagic || !r.ok) return fail(PCR_ERR_CORRUPT, "bad magic");
-  const uint64_t hl = r.get<uint64_t>();
-  const uint32_t hc = r.get<uint32_t>();
-  const uint8_t* hp = r.take(hl);
-  if (!r.ok || crc32(hp, hl) != hc) return fail(PCR_ERR_CORRUPT, "header checksum or length mismatch");
-  Reader hr{hp, hl};
-  std::unique_ptr<pcr_handle> h(new pcr_handle());
-  h->mem = make_mem(alloc);
+static pcr_status read_header(Reader& hr, pcr_handle* h, std::vector<std::vector<uint32_t>>& scnts) {
   const int ndim = hr.get<int>();
   int64_t dims[3];
   for (int i = 0; i < 3; i++) dims[i] = hr.get<int64_t>();
@@ -3735,7 +3902,7 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
   if (!hr.ok) return fail(PCR_ERR_CORRUPT, "truncated header");
   pcr_status e = validate((const void*)1, ndim, dims, dtype, &sch);
   if (e) return fail(PCR_ERR_CORRUPT, std::string("invalid header: ") + g_err);
-  e = setup_handle(h.get(), ndim, dims, dtype, &sch);
+  e = setup_handle(h, ndim, dims, dtype, &sch);
   if (e) return fail(PCR_ERR_CORRUPT, std::string("invalid header: ") + g_err);
   h->xmin = hr.get<double>();
   h->xmax = hr.get<double>();
@@ -3749,7 +3916,7 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
   h->E.resize(ns);
   h->sh.resize(ns);
   h->plane_nz.resize(ns);
-  std::vector<std::vector<uint32_t>> scnts(ns);
+  scnts.assign(ns, {});
   h->sign_words.assign(ns, std::vector<uint32_t>(h->B, 0));
   h->pairs.resize(ns);
   h->tabs.resize(ns);
@@ -3769,6 +3936,27 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
     h->pairs[i].resize(np);
     for (auto& x : h->pairs[i]) x = hr.get<uint64_t>();
   }
+  if (!hr.ok || hr.o != hr.n) return fail(PCR_ERR_CORRUPT, "header length mismatch");
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_allocator* alloc, void* cuda_stream,
+                                      pcr_handle** out) {
+  if (!buf || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Reader r{(const uint8_t*)buf, len};
+  if (r.get<uint64_t>() != kMagic || !r.ok) return fail(PCR_ERR_CORRUPT, "bad magic");
+  const uint64_t hl = r.get<uint64_t>();
+  const uint32_t hc = r.get<uint32_t>();
+  const uint8_t* hp = r.take(hl);
+  if (!r.ok || crc32(hp, hl) != hc) return fail(PCR_ERR_CORRUPT, "header checksum or length mismatch");
+  Reader hr{hp, hl};
+  std::unique_ptr<pcr_handle> h(new pcr_handle());
+  h->mem = make_mem(alloc);
+  std::vector<std::vector<uint32_t>> scnts;
+  pcr_status e = read_header(hr, h.get(), scnts);
+  if (e) return e;
+  const int ns = (int)h->geo.size();
   if (!hr.ok || hr.o != hl) return fail(PCR_ERR_CORRUPT, "header length mismatch");
   const uint64_t npw = r.get<uint64_t>();
   const uint32_t pc = r.get<uint32_t>();
@@ -3794,6 +3982,54 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
   CUDA_TRY(cudaMemcpyAsync(h->d_nz, nz.data(), nz.size() * 4, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   for (int i = 0; i < ns; i++)
+    compute_tables(h.get(), i, h->pairs[i].empty() ? nullptr : &h->pairs[i], keeps_pairs(h.get()));
+  build_meta(h.get());
+  *out = h.release();
+  return PCR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// planning state: what the interpreter needs, without planes (block
+// sharding: ranks exchange their blocks' states and plan the whole field)
+// ---------------------------------------------------------------------------
+const uint64_t kPlanMagic = 0x3230534C50ull;  // "PLS02"
+
+extern "C" pcr_status pcr_export_plan_state(const pcr_handle* h, void** buf, size_t* len) {
+  if (!h || !buf || !len) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  if (!h->d_block) return fail(PCR_ERR_UNSUPPORTED, "a planning-only handle is exported by its owner");
+  Writer w;
+  w.put(kPlanMagic);
+  Writer hd;
+  pcr_status e = write_header(h, hd);
+  if (e) return e;
+  w.put((uint64_t)hd.buf.size());
+  w.put(crc32(hd.buf.data(), hd.buf.size()));
+  w.raw(hd.buf.data(), hd.buf.size());
+  void* out = std::malloc(w.buf.size());
+  if (!out) return fail(PCR_ERR_OOM, "host allocation failed");
+  std::memcpy(out, w.buf.data(), w.buf.size());
+  *buf = out;
+  *len = w.buf.size();
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_import_plan_state(const void* buf, size_t len, pcr_handle** out) {
+  if (!buf || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  Reader r{(const uint8_t*)buf, len};
+  if (r.get<uint64_t>() != kPlanMagic || !r.ok) return fail(PCR_ERR_CORRUPT, "bad magic");
+  const uint64_t hl = r.get<uint64_t>();
+  const uint32_t hc = r.get<uint32_t>();
+  const uint8_t* hp = r.take(hl);
+  if (!r.ok || crc32(hp, hl) != hc) return fail(PCR_ERR_CORRUPT, "header checksum or length mismatch");
+  if (r.o != len) return fail(PCR_ERR_CORRUPT, "trailing bytes");
+  Reader hr{hp, hl};
+  std::unique_ptr<pcr_handle> h(new pcr_handle());
+  h->mem = make_mem(nullptr);
+  std::vector<std::vector<uint32_t>> scnts;
+  pcr_status e = read_header(hr, h.get(), scnts);
+  if (e) return e;
+  for (int i = 0; i < (int)h->geo.size(); i++)
     compute_tables(h.get(), i, h->pairs[i].empty() ? nullptr : &h->pairs[i], keeps_pairs(h.get()));
   build_meta(h.get());
   *out = h.release();
