@@ -50,9 +50,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pcr", choices=["pcr", "reference"])
     ap.add_argument("--size", type=int, default=512, help="cube edge (default 512)")
-    ap.add_argument("--mode", default="headline", choices=["headline", "batch", "serve"],
+    ap.add_argument("--mode", default="headline", choices=["headline", "batch", "serve", "shard"],
                     help="headline (default): the 512^3 step; batch: 96 uneven fields, one "
-                         "batched refactor vs sequential calls; serve: continuous-batching server")
+                         "batched refactor vs sequential calls; serve: continuous-batching server; "
+                         "shard: one 1024x512x512 field as 256x512x512 blocks planned together")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the batch/serve workload")
     return ap.parse_args()
 
@@ -706,6 +707,72 @@ def run_batch(args):
                       "first_fields_identical": same}))
 
 
+def run_shard(args):
+    """Block sharding (the paper's per-block scaling setup: 256x512x512
+    blocks): one 1024x512x512 FP32 GRF refactored as four axis-0 blocks on
+    this GPU (ShardedField), planned together for whole-field targets and
+    retrieved into one output; the same field refactored whole for
+    comparison.  Under torchrun every rank holds its blocks of a field of
+    world x 4 blocks and plans through distributed_plans (states exchanged
+    over a gloo group)."""
+    import torch
+    import torch.distributed as dist
+    import paper_2609_04573_b300 as pcr
+    from paper_2609_04573_b300.shard import ShardedField, distributed_plans
+    from synth.device import grf_torch
+    rank, world, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    nb = 4
+    shape = (256 * nb, 512, 512)
+    x = grf_torch(shape, 7)
+    nbytes = x.numel() * 4
+    sch = pcr.Scheme(interp="level", degree="cubic", decomp_axis=2)
+    targets = [("rel", 1e-4), ("psnr", 80.0)]
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            r = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) / reps, r
+
+    t_ref, sf = timed(lambda: ShardedField(x, nb, sch))
+    t_whole, hw = timed(lambda: pcr.refactor(x, sch))
+    out = torch.empty_like(x)
+    rows = []
+    for kind, v in targets:
+        tg = pcr.Target(kind, v)
+        t0 = time.perf_counter()
+        pls, bound, ok = sf.plan(tg)
+        t_plan = time.perf_counter() - t0
+        t_ret, _ = timed(lambda: sf.retrieve(pls, out=out))
+        d = out.double() - x.double()
+        R = (x.max() - x.min()).item()
+        err = d.abs().max().item()
+        mse = (d ** 2).mean().item()
+        pw = hw.plan(tg, allow_unsat=True)
+        rows.append({"target": f"{kind} {v:g}", "satisfied": ok, "bytes": sum(p.bytes for p in pls),
+                     "bytes_whole_field_plan": pw.bytes, "plan_ms": t_plan * 1e3,
+                     "retrieve_gbs": nbytes / t_ret / 1e9, "max_err_rel": err / R,
+                     "psnr_db": 20 * math.log10(R / math.sqrt(mse)) if mse > 0 else None})
+    res = {"mode": "shard", "field": list(shape), "blocks": nb, "block": [256, 512, 512],
+           "refactor_blocks_gbs": nbytes / t_ref / 1e9, "refactor_whole_gbs": nbytes / t_whole / 1e9,
+           "targets": rows}
+    if world > 1:
+        if not dist.is_initialized():
+            dist.init_process_group("gloo")
+        local_blocks = [(rank * nb + i, h) for i, h in enumerate(sf.handles)]
+        t0 = time.perf_counter()
+        plans, bound, ok = distributed_plans(local_blocks, pcr.Target("psnr", 80.0))
+        res["distributed"] = {"world": world, "blocks": world * nb, "plan_ms": (time.perf_counter() - t0) * 1e3,
+                              "satisfied": ok}
+    if rank == 0:
+        print(json.dumps(res))
+
+
 def run_serve(args):
     """Resident refactored fields, Poisson arrivals of mixed-tolerance
     requests (half whole-field, half 128^3 boxes), continuous batching with
@@ -773,6 +840,8 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.mode == "batch":
         run_batch(a)
+    elif a.mode == "shard":
+        run_shard(a)
     elif a.mode == "serve":
         run_serve(a)
     else:
