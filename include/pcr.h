@@ -332,6 +332,29 @@ pcr_status pcr_plan_more(const pcr_handle* h, const pcr_target* target, const pc
  *   (pcr_plan, pcr_plan_more, pcr_plan_global) but holds no planes, so
  *   retrievals, stream copies and pcr_serialize return PCR_ERR_UNSUPPORTED.
  *   PCR_ERR_CORRUPT on a bad magic, length or checksum. */
+/* ---- lossless coding of plane words (Sec. V: bitplane encoding then
+ * lossless compression) -------------------------------------------------
+ * Every plane of every 4096-value segment of a stream is coded on its own:
+ * nothing when it has no one-bit, else the Rice code of the zero runs
+ * before its ones (parameter k the largest value <= 15 with m 2^k <= n - m,
+ * m ones in n bits), else -- when that code is not shorter -- the raw words;
+ * one header word per segment and plane (mode, k, m, payload words).
+ * Planes with no nonzero word in a stream are not stored.
+ * packed_tables: bytes[i * (B + 1) + b] = stored bytes of stream i's first
+ *   b planes coded (plus their sign words, as in the raw tables); computed
+ *   on the GPU on first use (synchronises the device's default stream).
+ * serialize_packed: a container like pcr_serialize with the planes stored
+ *   coded; pcr_deserialize reads both kinds (it decodes the planes on the
+ *   GPU; a header out of range or a code that does not decode into its
+ *   segment is PCR_ERR_CORRUPT).
+ * Planning-only handles: PCR_ERR_UNSUPPORTED. */
+pcr_status pcr_packed_tables(const pcr_handle* h, uint64_t* bytes);
+/* Test entry: the coded form of one segment's plane (nwords <= 128 words at
+ * d_words in device memory): *header and the payload words (room for 128)
+ * into host memory, *npayload their count. */
+pcr_status pcr_debug_pack(const uint32_t* d_words, int nwords, uint32_t* header, uint32_t* payload, int* npayload);
+pcr_status pcr_serialize_packed(const pcr_handle* h, void** buf, size_t* len);
+
 pcr_status pcr_plan_global(int n, const pcr_handle* const* hs, const pcr_target* target,
                            pcr_retrieval_plan* plans, double* bound, int* satisfied);
 pcr_status pcr_export_plan_state(const pcr_handle* h, void** buf, size_t* len);

@@ -17,9 +17,9 @@ bits, bit e of plane word j being value 32 j + e -- is coded on its own:
   RAW, the plane words themselves.
 
 Stored per segment and plane: one header word (mode in bits 0-1: 0 ZERO,
-1 RICE, 2 RAW; k in bits 2-5; m in bits 6-18) and the payload: RICE the
-code bits packed least significant bit first into ceil(bits / 32) words,
-RAW the segment's plane words.  A plane with no nonzero word in the whole
+1 RICE, 2 RAW; k in bits 2-5; m in bits 6-18; payload words in bits 19-27)
+and the payload: RICE the code bits packed least significant bit first
+into ceil(bits / 32) words, RAW the segment's plane words.  A plane with no nonzero word in the whole
 stream is not stored (as in the raw byte tables); its packed size is 0.
 Packed bytes of a plane: the sum over its segments of 4 (header) + 4 x
 payload words.
@@ -67,10 +67,10 @@ def encode_segment(words):
         code.extend((g >> (k - 1 - t)) & 1 for t in range(k))
         prev = int(q)
     if len(code) >= n:
-        return RAW | (k << 2) | (m << 6), words.copy()
+        return RAW | (k << 2) | (m << 6) | (words.size << 19), words.copy()
     pad = (-len(code)) % 32
     payload = _words_of(np.array(code + [0] * pad, dtype=np.uint32))
-    return RICE | (k << 2) | (m << 6), payload
+    return RICE | (k << 2) | (m << 6) | (payload.size << 19), payload
 
 
 def _decode_rice(bits, k, m, n):
@@ -93,7 +93,7 @@ def _decode_rice(bits, k, m, n):
 
 def decode(header, payload, nwords):
     """Plane words of one segment from its header and payload."""
-    mode, k, m = header & 3, (header >> 2) & 15, header >> 6
+    mode, k, m = header & 3, (header >> 2) & 15, (header >> 6) & 0x1FFF
     if mode == ZERO:
         return np.zeros(nwords, np.uint32)
     if mode == RAW:

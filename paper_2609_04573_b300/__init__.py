@@ -106,6 +106,9 @@ _sigs = {
     "pcr_plan_global": [C.c_int, C.POINTER(_vp), C.POINTER(_Target), C.POINTER(_Plan), C.POINTER(C.c_double),
                         C.POINTER(C.c_int)],
     "pcr_export_plan_state": [_vp, C.POINTER(_vp), C.POINTER(C.c_size_t)],
+    "pcr_packed_tables": [_vp, C.POINTER(C.c_uint64)],
+    "pcr_debug_pack": [_vp, C.c_int, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_int)],
+    "pcr_serialize_packed": [_vp, C.POINTER(_vp), C.POINTER(C.c_size_t)],
     "pcr_import_plan_state": [_vp, C.c_size_t, C.POINTER(_vp)],
     "pcr_retrieve": [_vp, C.POINTER(_Target), _vp, _vp, C.POINTER(_Info)],
     "pcr_retrieve_plan": [_vp, C.POINTER(_Plan), _vp, _vp],
@@ -376,6 +379,28 @@ class Handle:
         if st != OK and not (st == ERR_UNSAT and allow_unsat):
             _check(st)
         return Plan(list(p.planes[:p.nstreams]), p.bound, p.psnr_bound, p.bytes, bool(p.satisfied), p)
+
+    def packed_tables(self):
+        """Stored bytes of each stream's first b planes with the planes
+        coded losslessly: list per stream of B + 1 entries."""
+        ns, B = self.nstreams, self.stream_info(0)["nplanes"]
+        out = (C.c_uint64 * (ns * (B + 1)))()
+        _check(_lib.pcr_packed_tables(self._p, out))
+        return [list(out[i * (B + 1):(i + 1) * (B + 1)]) for i in range(ns)]
+
+    def packed_bytes(self, plan):
+        """Stored bytes of a plan's planes and signs with the planes coded."""
+        t = self.packed_tables()
+        return sum(t[i][b] for i, b in enumerate(plan.planes))
+
+    def serialize_packed(self):
+        """Container bytes with the planes coded losslessly."""
+        buf, n = C.c_void_p(), C.c_size_t()
+        _check(_lib.pcr_serialize_packed(self._p, C.byref(buf), C.byref(n)))
+        try:
+            return C.string_at(buf, n.value)
+        finally:
+            _lib.pcr_buffer_free(buf)
 
     def export_plan_state(self):
         """What the planner needs of this handle (no planes), as bytes."""

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpcr.so")
-SOURCES = ["pcr_kernels.cu", "pcr_tiles.cu", "pcr_static.cu", "pcr_host.cpp"]
+SOURCES = ["pcr_kernels.cu", "pcr_tiles.cu", "pcr_static.cu", "pcr_pack.cu", "pcr_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC,-O3",
          "-I", os.path.join(ROOT, "include")]

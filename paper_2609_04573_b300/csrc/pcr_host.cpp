@@ -63,6 +63,12 @@ void launch_coarsest_multi(const FieldD* fs, const int* levels, const LatD* lats
                            int64_t* const* outs, unsigned long long* const* vmaxs, int n, cudaStream_t s);
 void launch_words_multi(const WordsItem* items, int n, cudaStream_t s);
 void launch_finalize_multi(FieldStats* const* sts, int n, cudaStream_t s);
+// lossless coding of plane words (pcr_pack.cu)
+void launch_pack_sizes(const PackTask* tasks, int ntasks, uint32_t* headers, uint32_t* pwords, cudaStream_t s);
+void launch_pack_write(const PackTask* tasks, int ntasks, const uint32_t* headers, const uint64_t* offsets,
+                       uint32_t* out, cudaStream_t s);
+void launch_unpack(const PackTask* tasks, int ntasks, const uint32_t* headers, const uint64_t* offsets,
+                   const uint32_t* in, int* err, cudaStream_t s);
 }  // namespace pcr
 
 using namespace pcr;
@@ -877,6 +883,9 @@ struct pcr_handle {
   mutable std::mutex plan_mu;
   mutable bool units_ok[2] = {false, false};
   mutable std::vector<Unit> units[2];
+  // lossless-coded plane sizes (bytes per stream and plane), built on first use
+  mutable bool packed_ok = false;
+  mutable std::vector<std::vector<uint64_t>> packed;
   // work list of a whole retrieval (every segment of every stream; stream
   // numbers local to the handle), float streams then fixed-point streams;
   // built by the refactor while its kernels run, reused by every
@@ -3828,7 +3837,8 @@ struct Reader {
     return q;
   }
 };
-const uint64_t kMagic = 0x3230524350ull;  // "PCR02"
+const uint64_t kMagic = 0x3230524350ull;        // "PCR02": planes stored raw
+const uint64_t kPackedMagic = 0x3250524350ull;  // "PCRP2": planes stored coded (pcr_serialize_packed)
 }  // namespace
 
 // what a handle's tables and planner need: dims, dtype, scheme, field
@@ -3940,12 +3950,16 @@ static pcr_status read_header(Reader& hr, pcr_handle* h, std::vector<std::vector
   return PCR_OK;
 }
 
+static void pack_tasks(const pcr_handle* h, uint32_t* planes, std::vector<PackTask>& tasks);
+
 extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_allocator* alloc, void* cuda_stream,
                                       pcr_handle** out) {
   if (!buf || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   Reader r{(const uint8_t*)buf, len};
-  if (r.get<uint64_t>() != kMagic || !r.ok) return fail(PCR_ERR_CORRUPT, "bad magic");
+  const uint64_t magic = r.get<uint64_t>();
+  if (!r.ok || (magic != kMagic && magic != kPackedMagic)) return fail(PCR_ERR_CORRUPT, "bad magic");
+  const bool packed = magic == kPackedMagic;
   const uint64_t hl = r.get<uint64_t>();
   const uint32_t hc = r.get<uint32_t>();
   const uint8_t* hp = r.take(hl);
@@ -3957,11 +3971,43 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
   pcr_status e = read_header(hr, h.get(), scnts);
   if (e) return e;
   const int ns = (int)h->geo.size();
-  if (!hr.ok || hr.o != hl) return fail(PCR_ERR_CORRUPT, "header length mismatch");
-  const uint64_t npw = r.get<uint64_t>();
-  const uint32_t pc = r.get<uint32_t>();
-  const uint8_t* pp = r.take(npw * 4);
-  if (!r.ok || npw != h->plane_words || crc32(pp, npw * 4) != pc) return fail(PCR_ERR_CORRUPT, "plane section mismatch");
+  const uint8_t* pp = nullptr;   // raw planes
+  uint64_t npw = 0;
+  std::vector<PackTask> tasks;   // coded planes: per task header, payload offsets
+  const uint32_t* heads = nullptr;
+  const uint32_t* pay = nullptr;
+  std::vector<uint64_t> off;
+  if (!packed) {
+    npw = r.get<uint64_t>();
+    const uint32_t pc = r.get<uint32_t>();
+    pp = r.take(npw * 4);
+    if (!r.ok || npw != h->plane_words || crc32(pp, npw * 4) != pc)
+      return fail(PCR_ERR_CORRUPT, "plane section mismatch");
+  } else {
+    pack_tasks(h.get(), nullptr, tasks);
+    const uint64_t nt = r.get<uint64_t>();
+    const uint32_t hcrc = r.get<uint32_t>();
+    heads = (const uint32_t*)r.take(nt * 4);
+    if (!r.ok || nt != tasks.size() || crc32(heads, nt * 4) != hcrc)
+      return fail(PCR_ERR_CORRUPT, "coded plane headers mismatch");
+    // every header must describe its segment: mode, ones, payload length
+    off.assign(nt + 1, 0);
+    for (size_t t = 0; t < nt; t++) {
+      uint32_t hw;
+      std::memcpy(&hw, (const uint8_t*)heads + 4 * t, 4);
+      const int64_t w0 = (int64_t)tasks[t].seg * kSegWords;
+      const uint32_t nw = (uint32_t)std::min<int64_t>(kSegWords, tasks[t].words - w0);
+      const uint32_t mode = hw & 3, m = (hw >> 6) & 0x1FFF, pw = hw >> 19;
+      const bool good = (mode == 0 && hw == 0) || (mode == 2 && pw == nw) ||
+                        (mode == 1 && m >= 1 && m <= 32 * nw && pw >= 1 && pw <= nw);
+      if (!good) return fail(PCR_ERR_CORRUPT, "coded plane header out of range");
+      off[t + 1] = off[t] + pw;
+    }
+    const uint64_t np = r.get<uint64_t>();
+    const uint32_t pcrc = r.get<uint32_t>();
+    pay = (const uint32_t*)r.take(np * 4);
+    if (!r.ok || np != off[nt] || crc32(pay, np * 4) != pcrc) return fail(PCR_ERR_CORRUPT, "coded plane payload mismatch");
+  }
   const uint64_t nsw = r.get<uint64_t>();
   const uint32_t sgc = r.get<uint32_t>();
   const uint8_t* sp = r.take(nsw * 4);
@@ -3970,7 +4016,32 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
   if (r.o != len) return fail(PCR_ERR_CORRUPT, "trailing bytes");
   e = alloc_handle_buffers(h.get(), s);
   if (e) return e;
-  CUDA_TRY(cudaMemcpyAsync(h->d_planes, pp, npw * 4, cudaMemcpyHostToDevice, s));
+  if (!packed) {
+    CUDA_TRY(cudaMemcpyAsync(h->d_planes, pp, npw * 4, cudaMemcpyHostToDevice, s));
+  } else if (!tasks.empty()) {
+    // planes with no nonzero word are not stored: zero, then decode the rest
+    CUDA_TRY(cudaMemsetAsync(h->d_planes, 0, h->plane_words * 4, s));
+    pack_tasks(h.get(), h->d_planes, tasks);   // the same tasks, now over this handle's planes
+    const size_t nt = tasks.size();
+    Scratch sc{&h->mem, s, {}};
+    PackTask* d_t = (PackTask*)sc.get(nt * sizeof(PackTask));
+    uint32_t* d_h = (uint32_t*)sc.get(nt * 4);
+    uint64_t* d_o = (uint64_t*)sc.get((nt + 1) * 8);
+    uint32_t* d_p = (uint32_t*)sc.get(std::max<uint64_t>(off[nt], 1) * 4);
+    int* d_err = (int*)sc.get(sizeof(int));
+    if (!d_t || !d_h || !d_o || !d_p || !d_err) return fail(PCR_ERR_OOM, "unpacking allocation failed");
+    CUDA_TRY(cudaMemcpyAsync(d_t, tasks.data(), nt * sizeof(PackTask), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d_h, heads, nt * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d_o, off.data(), (nt + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (off[nt]) CUDA_TRY(cudaMemcpyAsync(d_p, pay, off[nt] * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    launch_unpack(d_t, (int)nt, d_h, d_o, d_p, d_err, s);
+    CUDA_TRY(cudaGetLastError());
+    int err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (err) return fail(PCR_ERR_CORRUPT, "coded plane payload does not decode");
+  }
   if (nsw) CUDA_TRY(cudaMemcpyAsync(h->d_signs, sp, nsw * 4, cudaMemcpyHostToDevice, s));
   std::vector<uint32_t> scnt, nz;
   for (int i = 0; i < ns; i++) {
@@ -4033,6 +4104,182 @@ extern "C" pcr_status pcr_import_plan_state(const void* buf, size_t len, pcr_han
     compute_tables(h.get(), i, h->pairs[i].empty() ? nullptr : &h->pairs[i], keeps_pairs(h.get()));
   build_meta(h.get());
   *out = h.release();
+  return PCR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// lossless coding of plane words (Sec. V): every nonzero plane of every
+// stream coded per 4096-value segment (pcr_pack.cu); sizes for the tables,
+// and a container whose planes are stored coded
+// ---------------------------------------------------------------------------
+// tasks in (stream, plane, segment) order over the planes with a nonzero word
+static void pack_tasks(const pcr_handle* h, uint32_t* planes, std::vector<PackTask>& tasks) {
+  tasks.clear();
+  for (int i = 0; i < (int)h->geo.size(); i++) {
+    const int64_t words = h->geo[i].n_pad() / 32;
+    const int nseg = (int)((words + kSegWords - 1) / kSegWords);
+    for (int k = 0; k < h->B; k++) {
+      if (!h->plane_nz[i][k]) continue;
+      for (int g = 0; g < nseg; g++) tasks.push_back({planes + h->plane_off[i] + (size_t)k * words, words, g});
+    }
+  }
+}
+
+// headers and payload words of every task of a live handle (synchronous)
+static pcr_status pack_headers(const pcr_handle* h, const std::vector<PackTask>& tasks, cudaStream_t s,
+                               std::vector<uint32_t>& headers, std::vector<uint32_t>& pwords) {
+  const size_t nt = tasks.size();
+  headers.assign(nt, 0);
+  pwords.assign(nt, 0);
+  if (!nt) return PCR_OK;
+  Mem mem = h->mem;
+  Scratch sc{&mem, s, {}};
+  PackTask* d_t = (PackTask*)sc.get(nt * sizeof(PackTask));
+  uint32_t* d_h = (uint32_t*)sc.get(nt * 4);
+  uint32_t* d_w = (uint32_t*)sc.get(nt * 4);
+  if (!d_t || !d_h || !d_w) return fail(PCR_ERR_OOM, "packing allocation failed");
+  CUDA_TRY(cudaMemcpyAsync(d_t, tasks.data(), nt * sizeof(PackTask), cudaMemcpyHostToDevice, s));
+  launch_pack_sizes(d_t, (int)nt, d_h, d_w, s);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(headers.data(), d_h, nt * 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(pwords.data(), d_w, nt * 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_packed_tables(const pcr_handle* h, uint64_t* bytes) {
+  if (!h || !bytes) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  if (!h->d_block) return fail(PCR_ERR_UNSUPPORTED, "a planning-only handle holds no planes");
+  const int ns = (int)h->geo.size();
+  {
+    std::lock_guard<std::mutex> lk(h->plan_mu);
+    if (!h->packed_ok) {
+      std::vector<PackTask> tasks;
+      pack_tasks(h, h->d_planes, tasks);
+      std::vector<uint32_t> hd, pw;
+      pcr_status e = pack_headers(h, tasks, nullptr, hd, pw);
+      if (e) return e;
+      h->packed.assign(ns, std::vector<uint64_t>(h->B, 0));
+      size_t t = 0;
+      for (int i = 0; i < ns; i++) {
+        const int64_t words = h->geo[i].n_pad() / 32;
+        const int nseg = (int)((words + kSegWords - 1) / kSegWords);
+        for (int k = 0; k < h->B; k++) {
+          if (!h->plane_nz[i][k]) continue;
+          for (int g = 0; g < nseg; g++, t++) h->packed[i][k] += 4 + 4 * (uint64_t)pw[t];
+        }
+      }
+      h->packed_ok = true;
+    }
+  }
+  const bool nb = h->enc == 2;
+  for (int i = 0; i < ns; i++) {
+    uint64_t acc = 0;
+    bytes[(size_t)i * (h->B + 1)] = 0;
+    for (int k = 0; k < h->B; k++) {
+      acc += h->packed[i][k];
+      if (!nb) acc += 4 * (uint64_t)h->sign_words[i][k];
+      bytes[(size_t)i * (h->B + 1) + k + 1] = acc;
+    }
+  }
+  return PCR_OK;
+}
+
+// test entry: the coded form of one segment's plane words (at most 128
+// words in device memory): header and payload words (payload: room for 128)
+extern "C" pcr_status pcr_debug_pack(const uint32_t* d_words, int nwords, uint32_t* header, uint32_t* payload,
+                                     int* npayload) {
+  if (!d_words || !header || !payload || !npayload || nwords < 1 || nwords > kSegWords)
+    return fail(PCR_ERR_INVALID_ARG, "bad argument");
+  const PackTask tk{const_cast<uint32_t*>(d_words), nwords, 0};
+  PackTask* d_t = nullptr;
+  uint32_t *d_h = nullptr, *d_w = nullptr, *d_p = nullptr;
+  uint64_t* d_o = nullptr;
+  auto release = [&]() {
+    cudaFree(d_t);
+    cudaFree(d_h);
+    cudaFree(d_w);
+    cudaFree(d_p);
+    cudaFree(d_o);
+  };
+  if (cudaMalloc(&d_t, sizeof(PackTask)) != cudaSuccess || cudaMalloc(&d_h, 4) != cudaSuccess ||
+      cudaMalloc(&d_w, 4) != cudaSuccess || cudaMalloc(&d_p, kSegWords * 4) != cudaSuccess ||
+      cudaMalloc(&d_o, 16) != cudaSuccess) {
+    release();
+    cudaGetLastError();
+    return fail(PCR_ERR_OOM, "debug allocation failed");
+  }
+  const uint64_t off[2] = {0, (uint64_t)kSegWords};
+  uint32_t pw = 0;
+  cudaError_t ce = cudaMemcpy(d_t, &tk, sizeof(PackTask), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(d_o, off, 16, cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) {
+    launch_pack_sizes(d_t, 1, d_h, d_w, nullptr);
+    launch_pack_write(d_t, 1, d_h, d_o, d_p, nullptr);
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpy(header, d_h, 4, cudaMemcpyDeviceToHost);
+  if (ce == cudaSuccess) ce = cudaMemcpy(&pw, d_w, 4, cudaMemcpyDeviceToHost);
+  if (ce == cudaSuccess && pw) ce = cudaMemcpy(payload, d_p, pw * 4, cudaMemcpyDeviceToHost);
+  release();
+  if (ce != cudaSuccess) return fail(PCR_ERR_CUDA, cudaGetErrorString(ce));
+  *npayload = (int)pw;
+  return PCR_OK;
+}
+
+extern "C" pcr_status pcr_serialize_packed(const pcr_handle* h, void** buf, size_t* len) {
+  if (!h || !buf || !len) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  if (!h->d_block) return fail(PCR_ERR_UNSUPPORTED, "a planning-only handle holds no planes");
+  Writer w;
+  w.put(kPackedMagic);
+  Writer hd;
+  pcr_status e = write_header(h, hd);
+  if (e) return e;
+  w.put((uint64_t)hd.buf.size());
+  w.put(crc32(hd.buf.data(), hd.buf.size()));
+  w.raw(hd.buf.data(), hd.buf.size());
+  // coded planes: every task's header, then the payloads in task order
+  std::vector<PackTask> tasks;
+  pack_tasks(h, h->d_planes, tasks);
+  std::vector<uint32_t> heads, pw;
+  e = pack_headers(h, tasks, nullptr, heads, pw);
+  if (e) return e;
+  const size_t nt = tasks.size();
+  std::vector<uint64_t> off(nt + 1, 0);
+  for (size_t t = 0; t < nt; t++) off[t + 1] = off[t] + pw[t];
+  std::vector<uint32_t> payload(off[nt]);
+  if (nt && off[nt]) {
+    Mem mem = h->mem;
+    Scratch sc{&mem, nullptr, {}};
+    PackTask* d_t = (PackTask*)sc.get(nt * sizeof(PackTask));
+    uint32_t* d_h = (uint32_t*)sc.get(nt * 4);
+    uint64_t* d_o = (uint64_t*)sc.get((nt + 1) * 8);
+    uint32_t* d_p = (uint32_t*)sc.get(off[nt] * 4);
+    if (!d_t || !d_h || !d_o || !d_p) return fail(PCR_ERR_OOM, "packing allocation failed");
+    CUDA_TRY(cudaMemcpy(d_t, tasks.data(), nt * sizeof(PackTask), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_h, heads.data(), nt * 4, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_o, off.data(), (nt + 1) * 8, cudaMemcpyHostToDevice));
+    launch_pack_write(d_t, (int)nt, d_h, d_o, d_p, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpy(payload.data(), d_p, off[nt] * 4, cudaMemcpyDeviceToHost));
+  }
+  w.put((uint64_t)nt);
+  w.put(crc32(heads.data(), nt * 4));
+  w.raw(heads.data(), nt * 4);
+  w.put((uint64_t)payload.size());
+  w.put(crc32(payload.data(), payload.size() * 4));
+  w.raw(payload.data(), payload.size() * 4);
+  std::vector<uint32_t> signs(h->sign_area_words);
+  if (h->sign_area_words)
+    CUDA_TRY(cudaMemcpy(signs.data(), h->d_signs, h->sign_area_words * 4, cudaMemcpyDeviceToHost));
+  w.put((uint64_t)signs.size());
+  w.put(crc32(signs.data(), signs.size() * 4));
+  w.raw(signs.data(), signs.size() * 4);
+  void* out = std::malloc(w.buf.size());
+  if (!out) return fail(PCR_ERR_OOM, "host allocation failed");
+  std::memcpy(out, w.buf.data(), w.buf.size());
+  *buf = out;
+  *len = w.buf.size();
   return PCR_OK;
 }
 

@@ -112,6 +112,14 @@ struct TileArgs {
 // items of one batched (multi-field) launch of the per-field kernels
 constexpr int kMaxBatchItems = 128;
 
+// one task: stream, plane, segment (plane rows of `words` words, segments of
+// kSegWords words, the last one possibly shorter)
+struct PackTask {
+  uint32_t* plane;         // the plane's row (read by the packer, written by the unpacker)
+  int64_t words;           // words in the row
+  int seg;
+};
+
 // a range of 32-bit words to zero (src null) or copy, one item of a batched
 // launch
 struct WordsItem {

@@ -3,7 +3,8 @@
 * A hand-coded example: ones at bits 0 and 3 of a 4096-bit segment give
   m = 2, k = 10 (the largest k with 2 * 2^k <= 4094), gaps 0 and 2, and the
   22-bit code 0 0000000000 | 0 0000000010, whose only one sits at bit 20 of
-  the first payload word; header 1 | 10 << 2 | 2 << 6.
+  the first payload word; header 1 | 10 << 2 | 2 << 6 | 1 << 19 (one
+  payload word).
 * Round trip on sparse, dense and ragged segments of every density.
 * The Rice code length equals the sum over gaps of (g >> k) + 1 + k,
   counted here from the gaps directly.
@@ -21,7 +22,7 @@ def test_hand_coded_example():
     w = np.zeros(128, np.uint32)
     w[0] = 0b1001
     h, p = ll.encode_segment(w)
-    assert h == 1 | (10 << 2) | (2 << 6)
+    assert h == 1 | (10 << 2) | (2 << 6) | (1 << 19)
     assert p.size == 1 and int(p[0]) == 1 << 20
     assert np.array_equal(ll.decode(h, p, 128), w)
 
@@ -35,7 +36,8 @@ def test_round_trip(density, nwords):
     h, p = ll.encode_segment(w)
     assert np.array_equal(ll.decode(h, p, nwords), w)
     m = int(bits.sum())
-    assert h >> 6 == m if m else h == ll.ZERO
+    assert (h >> 6) & 0x1FFF == m if m else h == ll.ZERO
+    assert h >> 19 == p.size
     if h & 3 == ll.RICE:
         k = (h >> 2) & 15
         pos = np.flatnonzero(bits)
