@@ -471,6 +471,7 @@ def sweep(pcr, h, x, out, stream, R, targets=SWEEP, reps=5):
     whether the retrieved field does."""
     import torch
     res = []
+    ptab = h.packed_tables()
     for kind, v in targets:
         tg = pcr.Target(kind, v)
         plr = h.plan(tg, allow_unsat=True)
@@ -485,8 +486,10 @@ def sweep(pcr, h, x, out, stream, R, targets=SWEEP, reps=5):
         e = d.abs().max().item()
         mse = (d ** 2).mean().item()
         ok = (e <= v * R) if kind == "rel" else (mse == 0 or 20 * math.log10(R / math.sqrt(mse)) >= v)
+        coded = sum(ptab[i][b] for i, b in enumerate(plr.planes))
         res.append({"target": f"{kind} {v:g}", "ms": ea.elapsed_time(eb) / reps, "bytes": plr.bytes,
-                    "bytes_per_value": plr.bytes / x.numel(), "satisfied": bool(plr.satisfied),
+                    "bytes_per_value": plr.bytes / x.numel(), "coded_bytes_per_value": coded / x.numel(),
+                    "satisfied": bool(plr.satisfied),
                     "within_target": bool(ok) if plr.satisfied else None, "max_err": e})
     return res
 
