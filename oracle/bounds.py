@@ -536,3 +536,132 @@ def greedy(comp, tabs, target, kind, have=None):
         _, ui, b, bound = best
         pos[ui] += 1
     return b, bound, True
+
+
+# --------------------------------------------------------------------------
+# best-first search interpreter
+# --------------------------------------------------------------------------
+
+SEARCH_NODES = 4096     # default expansion budget of the search
+
+
+def unit_planes(units, n, have=None):
+    """Per unit u and position p (its first p steps taken): the plane count
+    of each of its streams, {stream: planes}, starting from ``have`` (or
+    zero) the way the greedy applies steps."""
+    out = []
+    for u in units:
+        cur = {i: (have[i] if have is not None else 0) for i in u.ids}
+        seq = [dict(cur)]
+        for upd, _, _ in u.steps:
+            for i, nb in upd:
+                cur[i] = nb if have is None else max(cur[i], nb)
+            seq.append(dict(cur))
+        out.append(seq)
+    return out
+
+
+def best_first(comp, tabs, target, kind, have=None, max_nodes=SEARCH_NODES):
+    """Best-first search for the smallest retrieval meeting the bound
+    (Sec. VI-B: per-level + decomposition uses a best-first search with
+    pruning and incremental invocation; per-region a dynamic program -- both
+    aim at the fewest bytes whose bound meets the target).  Reading: one
+    search for every mode, over the greedy's planning units; a state is the
+    number of steps taken in each unit, its cost the bytes it adds to
+    ``have`` (or to nothing), and the bound is monotone in every unit.
+
+    * incumbent: the greedy plan (always feasible when anything is);
+    * lower positions: unit u needs at least q_u steps, the fewest for which
+      the bound meets the target with every other unit complete; the search
+      starts at q;
+    * uniform-cost order over a tree that reaches every state once (a state
+      only advances units at or after the one its parent advanced); key
+      (cost, push order); a child that meets the target becomes the
+      incumbent when cheaper; children costing at least the incumbent are
+      cut; the search stops when the cheapest open state costs at least the
+      incumbent (the incumbent is then the minimum) or after ``max_nodes``
+      expansions (the best plan found so far).
+
+    Returns (planes, bound, satisfied, info) with info = dict(expanded,
+    optimal, greedy_bytes) (greedy_bytes counted like the cost)."""
+    import heapq
+
+    n = len(tabs)
+    bg, bound_g, ok = greedy(comp, tabs, target, kind, have)
+    base = list(have) if have is not None else [0] * n
+
+    def added(bb):
+        return sum(tabs[i]["bytes"][bb[i]] - tabs[i]["bytes"][base[i]] for i in range(n))
+
+    info = dict(expanded=0, optimal=False, greedy_bytes=added(bg))
+    if not ok:
+        return bg, bound_g, False, info
+    units = build_units(comp, tabs, kind)
+    U = len(units)
+    pls = unit_planes(units, n, have)
+    S = [len(u.steps) for u in units]
+    cost = [[sum(tabs[i]["bytes"][pl[i]] - tabs[i]["bytes"][base[i]] for i in pl) for pl in seq] for seq in pls]
+    start = [0] * U
+    if have is not None:
+        for ui, u in enumerate(units):
+            while start[ui] < S[ui] and all(nb <= base[i] for i, nb in u.steps[start[ui]][0]):
+                start[ui] += 1
+
+    def planes_of(pos):
+        bb = list(base)
+        for ui in range(U):
+            for i, v in pls[ui][pos[ui]].items():
+                bb[i] = v
+        return bb
+
+    def bound_of(pos):
+        bb = planes_of(pos)
+        err = [tabs[i]["maxerr"][bb[i]] for i in range(n)]
+        if kind == "linf":
+            return comp.linf(err)
+        return comp.l2([tabs[i]["sq"][bb[i]] for i in range(n)], err)
+
+    q = []
+    for ui in range(U):
+        pos = list(S)
+        p = start[ui]
+        while True:
+            pos[ui] = p
+            if p == S[ui] or bound_of(pos) <= target:
+                break
+            p += 1
+        q.append(p)
+    best_b, best_bound, c_best = bg, bound_g, info["greedy_bytes"]
+    c0 = sum(cost[ui][q[ui]] for ui in range(U))
+    if c0 >= c_best:
+        info["optimal"] = True
+        return best_b, best_bound, True, info
+    v = bound_of(q)
+    if v <= target:
+        info["optimal"] = True
+        return planes_of(q), v, True, info
+    heap = [(c0, 0, tuple(q), 0)]
+    seq = 1
+    while heap:
+        c, _, pos, lu = heapq.heappop(heap)
+        if c >= c_best:
+            break
+        if info["expanded"] >= max_nodes:
+            return best_b, best_bound, True, info
+        info["expanded"] += 1
+        for ui in range(lu, U):
+            p = pos[ui]
+            if p >= S[ui]:
+                continue
+            nc = c + cost[ui][p + 1] - cost[ui][p]
+            if nc >= c_best:
+                continue
+            child = pos[:ui] + (p + 1,) + pos[ui + 1:]
+            v = bound_of(child)
+            if v <= target:
+                best_b, best_bound, c_best = planes_of(child), v, nc
+            else:
+                heapq.heappush(heap, (nc, seq, child, ui))
+                seq += 1
+    info["optimal"] = True
+    return best_b, best_bound, True, info

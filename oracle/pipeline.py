@@ -223,25 +223,31 @@ def _add_factors(meta, geo):
     meta["decomp_factors"] = df
 
 
-def plan(handle, target, have=None):
+def plan(handle, target, have=None, search=None):
     """Retrieval interpreter: planes per stream for a target.  ``have``: a
     plan whose planes are already fetched (incremental invocation, see
-    bounds.greedy); the result contains it."""
+    bounds.greedy); the result contains it.  ``search``: None for the
+    greedy, else the expansion budget of the best-first search
+    (bounds.best_first; its statistics under "search")."""
     meta = handle["meta"]
     tabs = [s["tab"] for s in handle["streams"]]
     comp = handle["comp"]
     hb = have["b"] if isinstance(have, dict) else have
     if target.kind in ("abs", "rel"):
-        tau = target.value * (meta["R"] if target.kind == "rel" else 1.0)
-        b, bound, ok = bd.greedy(comp, tabs, tau, "linf", hb)
-        psnr = None
+        goal, kind = target.value * (meta["R"] if target.kind == "rel" else 1.0), "linf"
     else:
         ratio = meta["R"] / (10.0 ** (target.value / 20.0))
-        sse_max = meta["n"] * ratio * ratio
-        b, bound, ok = bd.greedy(comp, tabs, sse_max, "l2", hb)
-        psnr = None
+        goal, kind = meta["n"] * ratio * ratio, "l2"
+    info = None
+    if search is None:
+        b, bound, ok = bd.greedy(comp, tabs, goal, kind, hb)
+    else:
+        b, bound, ok, info = bd.best_first(comp, tabs, goal, kind, hb, search)
     total = sum(t["bytes"][bi] for t, bi in zip(tabs, b))
-    return dict(b=b, bound=bound, satisfied=ok, bytes=total, kind=target.kind)
+    out = dict(b=b, bound=bound, satisfied=ok, bytes=total, kind=target.kind)
+    if info is not None:
+        out["search"] = info
+    return out
 
 
 def retrieve(handle, target_or_plan, trace=None):
