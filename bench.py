@@ -487,10 +487,23 @@ def sweep(pcr, h, x, out, stream, R, targets=SWEEP, reps=5):
         mse = (d ** 2).mean().item()
         ok = (e <= v * R) if kind == "rel" else (mse == 0 or 20 * math.log10(R / math.sqrt(mse)) >= v)
         coded = sum(ptab[i][b] for i, b in enumerate(plr.planes))
-        res.append({"target": f"{kind} {v:g}", "ms": ea.elapsed_time(eb) / reps, "bytes": plr.bytes,
-                    "bytes_per_value": plr.bytes / x.numel(), "coded_bytes_per_value": coded / x.numel(),
-                    "satisfied": bool(plr.satisfied),
-                    "within_target": bool(ok) if plr.satisfied else None, "max_err": e})
+        row = {"target": f"{kind} {v:g}", "ms": ea.elapsed_time(eb) / reps, "bytes": plr.bytes,
+               "bytes_per_value": plr.bytes / x.numel(), "coded_bytes_per_value": coded / x.numel(),
+               "satisfied": bool(plr.satisfied),
+               "within_target": bool(ok) if plr.satisfied else None, "max_err": e}
+        if plr.satisfied:
+            # the best-first search interpreter on the same target: its plan
+            # retrieved once and checked the same way
+            pls, info = h.plan_search(tg)
+            h.retrieve(pls, out=out)
+            torch.cuda.synchronize()
+            d = out.double() - x.double()
+            es, mses = d.abs().max().item(), (d ** 2).mean().item()
+            oks = (es <= v * R) if kind == "rel" else (mses == 0 or 20 * math.log10(R / math.sqrt(mses)) >= v)
+            row["search"] = {"bytes": pls.bytes, "bytes_per_value": pls.bytes / x.numel(),
+                             "vs_greedy": pls.bytes / plr.bytes, "expanded": info["expanded"],
+                             "optimal": info["optimal"], "plan_ms": info["plan_ms"], "within_target": bool(oks)}
+        res.append(row)
     return res
 
 

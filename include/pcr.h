@@ -310,6 +310,34 @@ pcr_status pcr_plan(const pcr_handle* h, const pcr_target* target, pcr_retrieval
 pcr_status pcr_plan_more(const pcr_handle* h, const pcr_target* target, const pcr_retrieval_plan* have,
                          pcr_retrieval_plan* out);
 
+/* Best-first search interpreter (Sec. VI-B: per-level + decomposition is
+ * planned by a best-first search with pruning and incremental invocation,
+ * per-region by a dynamic program; both seek the fewest bytes whose bound
+ * meets the target).  One search serves every mode: over the greedy's
+ * planning units (the steps pcr_plan takes), a state is the number of steps
+ * taken per unit and costs the bytes it adds to `have`.  The greedy plan is
+ * the first incumbent; each unit starts at the fewest steps that meet the
+ * target with every other unit complete; states are expanded cheapest
+ * first (ties: the earlier pushed), each reached once (a child advances
+ * units at or after the one its parent advanced); a child meeting the
+ * target replaces a dearer incumbent; children costing at least the
+ * incumbent are cut.  The search ends when the cheapest open state costs at
+ * least the incumbent (the plan is then the minimum over unit positions:
+ * info->optimal = 1) or after `max_nodes` expansions (the best plan found).
+ * The plan never costs more than pcr_plan's (pcr_plan_more's with `have`).
+ * have: NULL or a plan of this handle whose planes the caller holds (as
+ * pcr_plan_more).  info (may be NULL): expansions, whether the minimum was
+ * proved, the greedy's bytes beyond `have`, host milliseconds.  Errors: as
+ * pcr_plan_more; PCR_ERR_INVALID_ARG for max_nodes < 0. */
+typedef struct {
+  int64_t expanded;       /* states expanded                                 */
+  int optimal;            /* 1 when the plan is proved the minimum           */
+  uint64_t greedy_bytes;  /* bytes the greedy plan adds beyond `have`        */
+  double plan_ms;         /* host time of the search                         */
+} pcr_search_info;
+pcr_status pcr_plan_search(const pcr_handle* h, const pcr_target* target, const pcr_retrieval_plan* have,
+                           int64_t max_nodes, pcr_retrieval_plan* out, pcr_search_info* info);
+
 /* ---- block sharding of one field (Sec. VII: independent blocks) -------
  * A field split along axis 0 into slabs, each refactored as a field of its
  * own (on this GPU or on the ranks that hold them), retrieved for one

@@ -567,20 +567,24 @@ def best_first(comp, tabs, target, kind, have=None, max_nodes=SEARCH_NODES):
     pruning and incremental invocation; per-region a dynamic program -- both
     aim at the fewest bytes whose bound meets the target).  Reading: one
     search for every mode, over the greedy's planning units; a state is the
-    number of steps taken in each unit, its cost the bytes it adds to
-    ``have`` (or to nothing), and the bound is monotone in every unit.
+    number of steps taken in each unit (positions), its cost the bytes it
+    adds to ``have`` (or to nothing); the bound is monotone in every unit.
 
-    * incumbent: the greedy plan (always feasible when anything is);
     * lower positions: unit u needs at least q_u steps, the fewest for which
-      the bound meets the target with every other unit complete; the search
-      starts at q;
-    * uniform-cost order over a tree that reaches every state once (a state
-      only advances units at or after the one its parent advanced); key
-      (cost, push order); a child that meets the target becomes the
-      incumbent when cheaper; children costing at least the incumbent are
-      cut; the search stops when the cheapest open state costs at least the
-      incumbent (the incumbent is then the minimum) or after ``max_nodes``
-      expansions (the best plan found so far).
+      the bound meets the target with every other unit complete;
+    * incumbent: the greedy plan, at its positions (per unit the last
+      position with the greedy's planes), improved by local moves until none
+      applies: for each unit in turn, drop its last step while that is
+      cheaper and meets the target; then for each ordered pair of units
+      (a, b), move one step from a to b when that is cheaper and meets the
+      target;
+    * uniform-cost order from q over a tree that reaches every state once
+      (a state only advances units at or after the one its parent
+      advanced); key (cost, push order); a child that meets the target
+      becomes the incumbent when cheaper; children costing at least the
+      incumbent are cut; the search stops when the cheapest open state
+      costs at least the incumbent (the incumbent is then the minimum) or
+      after ``max_nodes`` expansions (the best plan found so far).
 
     Returns (planes, bound, satisfied, info) with info = dict(expanded,
     optimal, greedy_bytes) (greedy_bytes counted like the cost)."""
@@ -631,7 +635,45 @@ def best_first(comp, tabs, target, kind, have=None, max_nodes=SEARCH_NODES):
                 break
             p += 1
         q.append(p)
-    best_b, best_bound, c_best = bg, bound_g, info["greedy_bytes"]
+
+    # the greedy's positions, then local moves
+    pos = []
+    for ui in range(U):
+        p = 0
+        for k in range(S[ui] + 1):
+            if all(bg[i] == v for i, v in pls[ui][k].items()):
+                p = k
+        pos.append(p)
+    c_best, best_bound = info["greedy_bytes"], bound_g
+    changed = True
+    while changed:
+        changed = False
+        for a in range(U):
+            while pos[a] > max(start[a], q[a]):
+                t = list(pos)
+                t[a] -= 1
+                ct = c_best - cost[a][pos[a]] + cost[a][t[a]]
+                if ct >= c_best:
+                    break
+                v = bound_of(t)
+                if v > target:
+                    break
+                pos, c_best, best_bound, changed = t, ct, v, True
+        for a in range(U):
+            for b2 in range(U):
+                if b2 == a or pos[a] <= max(start[a], q[a]) or pos[b2] >= S[b2]:
+                    continue
+                t = list(pos)
+                t[a] -= 1
+                t[b2] += 1
+                ct = c_best - cost[a][pos[a]] + cost[a][t[a]] - cost[b2][pos[b2]] + cost[b2][t[b2]]
+                if ct >= c_best:
+                    continue
+                v = bound_of(t)
+                if v <= target:
+                    pos, c_best, best_bound, changed = t, ct, v, True
+    best_b = planes_of(pos)
+
     c0 = sum(cost[ui][q[ui]] for ui in range(U))
     if c0 >= c_best:
         info["optimal"] = True

@@ -72,6 +72,13 @@ class _Plan(C.Structure):
 TUNE_NTOL, TUNE_MAX = 9, 32
 
 
+class _SearchInfo(C.Structure):
+    _fields_ = [("expanded", C.c_int64), ("optimal", C.c_int), ("greedy_bytes", C.c_uint64), ("plan_ms", C.c_double)]
+
+
+SEARCH_NODES = 4096
+
+
 class _TuneInfo(C.Structure):
     _fields_ = [("ncand", C.c_int), ("winner", C.c_int), ("cand", _Scheme * TUNE_MAX), ("votes", C.c_int * TUNE_MAX),
                 ("bytes", (C.c_uint64 * TUNE_NTOL) * TUNE_MAX), ("nblocks", C.c_int), ("block", C.c_int64 * 3),
@@ -103,6 +110,8 @@ _sigs = {
                            C.POINTER(_Scheme), C.POINTER(_Allocator), _vp, C.POINTER(_vp)],
     "pcr_plan": [_vp, C.POINTER(_Target), C.POINTER(_Plan)],
     "pcr_plan_more": [_vp, C.POINTER(_Target), C.POINTER(_Plan), C.POINTER(_Plan)],
+    "pcr_plan_search": [_vp, C.POINTER(_Target), C.POINTER(_Plan), C.c_int64, C.POINTER(_Plan),
+                        C.POINTER(_SearchInfo)],
     "pcr_plan_global": [C.c_int, C.POINTER(_vp), C.POINTER(_Target), C.POINTER(_Plan), C.POINTER(C.c_double),
                         C.POINTER(C.c_int)],
     "pcr_export_plan_state": [_vp, C.POINTER(_vp), C.POINTER(C.c_size_t)],
@@ -379,6 +388,19 @@ class Handle:
         if st != OK and not (st == ERR_UNSAT and allow_unsat):
             _check(st)
         return Plan(list(p.planes[:p.nstreams]), p.bound, p.psnr_bound, p.bytes, bool(p.satisfied), p)
+
+    def plan_search(self, target, max_nodes=SEARCH_NODES, have=None, allow_unsat=False):
+        """Best-first search interpreter (pcr_plan_search): (Plan, info) with
+        info = dict(expanded, optimal, greedy_bytes, plan_ms); never more
+        bytes than plan(target, have=have)."""
+        p, info = _Plan(), _SearchInfo()
+        st = _lib.pcr_plan_search(self._p, C.byref(target.c()), C.byref(have._c) if have is not None else None,
+                                  int(max_nodes), C.byref(p), C.byref(info))
+        if st != OK and not (st == ERR_UNSAT and allow_unsat):
+            _check(st)
+        pl = Plan(list(p.planes[:p.nstreams]), p.bound, p.psnr_bound, p.bytes, bool(p.satisfied), p)
+        return pl, dict(expanded=info.expanded, optimal=bool(info.optimal), greedy_bytes=info.greedy_bytes,
+                        plan_ms=info.plan_ms)
 
     def packed_tables(self):
         """Stored bytes of each stream's first b planes with the planes

@@ -2,6 +2,7 @@
 // error tables, bound composition, max ordering, the greedy planner, the
 // container and the C ABI (include/pcr.h).  Section references are to
 // arXiv 2609.04573 (ProAICD).
+#include <queue>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1382,6 +1383,12 @@ struct BoundEval {
 
   // bound for the errors err / sq, of which only level `from`'s streams may
   // differ from the kept state; `keep` makes them the kept state
+  // the bound of arbitrary errors, nothing kept or reused
+  double eval_all(const std::vector<double>& err, const std::vector<double>& sq) {
+    std::fill(acc_ok.begin(), acc_ok.end(), 0);
+    std::fill(cn_ok.begin(), cn_ok.end(), 0);
+    return eval_from(L - 1, err, sq, false);
+  }
   double eval_from(int from, const std::vector<double>& err, const std::vector<double>& sq, bool keep) {
     if (L == 1) {
       if (!l2) return (top(err) + c.rho0(0.0, 0.0)) * kMargin;
@@ -1598,6 +1605,204 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
     bound = best_bnd;
     pos[best_u]++;
   }
+  return true;
+}
+
+// Best-first search for the fewest bytes whose bound meets the target
+// (Sec. VI-B: best-first search with pruning and incremental invocation for
+// per-level + decomposition, a dynamic program for per-region; both look for
+// the smallest retrieval under the bound).  One search for every mode, over
+// the greedy's planning units: a state is the number of steps taken in each
+// unit, its cost the bytes it adds to `have` (or to nothing); the bound is
+// monotone in every unit.  The greedy plan is the first incumbent; unit u
+// starts at q_u, the fewest steps meeting the target with every other unit
+// complete; states are expanded cheapest first (key: cost, then push
+// order) over a tree that reaches every state once (a child advances only
+// units at or after the one its parent advanced); a child that meets the
+// target becomes the incumbent when cheaper, children costing at least the
+// incumbent are cut, and the search ends when the cheapest open state costs
+// at least the incumbent (proved minimum) or after max_nodes expansions.
+struct SearchStats {
+  int64_t expanded = 0;
+  int optimal = 0;
+  uint64_t greedy_bytes = 0;
+};
+
+bool search_plan(const pcr_handle* h, double target, bool linf, const std::vector<int>* have, int64_t max_nodes,
+                 std::vector<int>& b, double& bound, SearchStats& ss) {
+  const int n = (int)h->tabs.size();
+  std::vector<int> base = have ? *have : std::vector<int>(n, 0);
+  const bool ok = greedy(h, target, linf, b, bound, have);
+  auto added = [&](const std::vector<int>& bb) {
+    uint64_t c = 0;
+    for (int i = 0; i < n; i++) c += h->tabs[i].bytes[bb[i]] - h->tabs[i].bytes[base[i]];
+    return c;
+  };
+  ss = SearchStats();
+  ss.greedy_bytes = added(b);
+  if (!ok) return false;
+  const std::vector<Unit>& units = cached_units(h, linf);
+  const int U = (int)units.size();
+  // planes of each unit's streams after p steps, and the bytes they add
+  std::vector<std::vector<std::vector<std::pair<int, int>>>> pl(U);
+  std::vector<std::vector<uint64_t>> cost(U);
+  std::vector<int> S(U), start(U, 0);
+  for (int u = 0; u < U; u++) {
+    const Unit& un = units[u];
+    S[u] = (int)un.steps.size();
+    std::vector<std::pair<int, int>> cur;
+    for (int i : un.ids) cur.push_back({i, base[i]});
+    auto push = [&]() {
+      pl[u].push_back(cur);
+      uint64_t c = 0;
+      for (auto& pr : cur) c += h->tabs[pr.first].bytes[pr.second] - h->tabs[pr.first].bytes[base[pr.first]];
+      cost[u].push_back(c);
+    };
+    push();
+    for (const Step& st : un.steps) {
+      for (auto& up : st.upd)
+        for (auto& pr : cur)
+          if (pr.first == up.first) pr.second = have ? std::max(pr.second, up.second) : up.second;
+      push();
+    }
+    if (have)
+      while (start[u] < S[u]) {
+        bool covered = true;
+        for (auto& up : un.steps[start[u]].upd) covered = covered && up.second <= base[up.first];
+        if (!covered) break;
+        start[u]++;
+      }
+  }
+  BoundEval be(h->comp, !linf);
+  std::vector<double> err(n), sq(n);
+  std::vector<int> bb(n);
+  auto planes_of = [&](const uint16_t* pos) {
+    bb = base;
+    for (int u = 0; u < U; u++)
+      for (auto& pr : pl[u][pos[u]]) bb[pr.first] = pr.second;
+  };
+  auto bound_of = [&](const uint16_t* pos) {
+    planes_of(pos);
+    for (int i = 0; i < n; i++) {
+      err[i] = h->tabs[i].maxerr[bb[i]];
+      sq[i] = h->tabs[i].sq[bb[i]];
+    }
+    return be.eval_all(err, sq);
+  };
+  std::vector<uint16_t> q(U), pos(U);
+  for (int u = 0; u < U; u++) {
+    for (int v = 0; v < U; v++) pos[v] = (uint16_t)S[v];
+    int p = start[u];
+    while (true) {
+      pos[u] = (uint16_t)p;
+      if (p == S[u] || bound_of(pos.data()) <= target) break;
+      p++;
+    }
+    q[u] = (uint16_t)p;
+  }
+  // the incumbent: the greedy's positions (per unit the last position with
+  // its planes), improved by local moves until none applies -- drop a unit's
+  // last step, then move one step from unit a to unit b, each taken when it
+  // is cheaper and still meets the target
+  for (int u = 0; u < U; u++) {
+    int p = 0;
+    for (int k = 0; k <= S[u]; k++) {
+      bool eq = true;
+      for (auto& pr : pl[u][k]) eq = eq && b[pr.first] == pr.second;
+      if (eq) p = k;
+    }
+    pos[u] = (uint16_t)p;
+  }
+  uint64_t c_best = ss.greedy_bytes;
+  std::vector<uint16_t> t(U);
+  for (bool changed = true; changed;) {
+    changed = false;
+    for (int a = 0; a < U; a++)
+      while (pos[a] > std::max(start[a], (int)q[a])) {
+        t = pos;
+        t[a]--;
+        const uint64_t ct = c_best - cost[a][pos[a]] + cost[a][t[a]];
+        if (ct >= c_best) break;
+        const double v = bound_of(t.data());
+        if (v > target) break;
+        pos = t;
+        c_best = ct;
+        bound = v;
+        changed = true;
+      }
+    for (int a = 0; a < U; a++)
+      for (int b2 = 0; b2 < U; b2++) {
+        if (b2 == a || pos[a] <= std::max(start[a], (int)q[a]) || pos[b2] >= S[b2]) continue;
+        t = pos;
+        t[a]--;
+        t[b2]++;
+        const int64_t ct = (int64_t)c_best - (int64_t)cost[a][pos[a]] + (int64_t)cost[a][t[a]] -
+                           (int64_t)cost[b2][pos[b2]] + (int64_t)cost[b2][t[b2]];
+        if (ct >= (int64_t)c_best) continue;
+        const double v = bound_of(t.data());
+        if (v <= target) {
+          pos = t;
+          c_best = (uint64_t)ct;
+          bound = v;
+          changed = true;
+        }
+      }
+  }
+  planes_of(pos.data());
+  b = bb;
+  uint64_t c0 = 0;
+  for (int u = 0; u < U; u++) c0 += cost[u][q[u]];
+  if (c0 >= c_best) {
+    ss.optimal = 1;
+    return true;
+  }
+  const double v0 = bound_of(q.data());
+  if (v0 <= target) {
+    planes_of(q.data());
+    b = bb;
+    bound = v0;
+    ss.optimal = 1;
+    return true;
+  }
+  // open states: positions in a pool, heap of (cost, push order, slot, last unit)
+  struct Open {
+    uint64_t cost;
+    int64_t seq;
+    size_t slot;
+    int last;
+  };
+  auto later = [](const Open& a, const Open& o) { return a.cost != o.cost ? a.cost > o.cost : a.seq > o.seq; };
+  std::priority_queue<Open, std::vector<Open>, decltype(later)> heap(later);
+  std::vector<uint16_t> pool(q.begin(), q.end());
+  heap.push({c0, 0, 0, 0});
+  int64_t seq = 1;
+  std::vector<uint16_t> child(U);
+  while (!heap.empty()) {
+    const Open o = heap.top();
+    heap.pop();
+    if (o.cost >= c_best) break;
+    if (ss.expanded >= max_nodes) return true;
+    ss.expanded++;
+    for (int u = o.last; u < U; u++) {
+      const uint16_t* p = &pool[o.slot * U];
+      if (p[u] >= S[u]) continue;
+      const uint64_t nc = o.cost + cost[u][p[u] + 1] - cost[u][p[u]];
+      if (nc >= c_best) continue;
+      std::copy(p, p + U, child.begin());
+      child[u]++;
+      const double v = bound_of(child.data());
+      if (v <= target) {
+        b = bb;
+        bound = v;
+        c_best = nc;
+      } else {
+        const size_t slot = pool.size() / U;
+        pool.insert(pool.end(), child.begin(), child.end());
+        heap.push({nc, seq++, slot, u});
+      }
+    }
+  }
+  ss.optimal = 1;
   return true;
 }
 
@@ -2867,7 +3072,7 @@ extern "C" pcr_status pcr_refactor(const void* d_field, int ndim, const int64_t*
 // plan
 // ---------------------------------------------------------------------------
 static pcr_status plan_impl(const pcr_handle* h, const pcr_target* t, const std::vector<int>* have,
-                            pcr_retrieval_plan* out) {
+                            pcr_retrieval_plan* out, int64_t search_nodes = -1, SearchStats* ss = nullptr) {
   if (!(t->value >= 0) || !std::isfinite(t->value)) return fail(PCR_ERR_INVALID_ARG, "bad target value");
   std::vector<int> b;
   double bound = 0;
@@ -2876,12 +3081,14 @@ static pcr_status plan_impl(const pcr_handle* h, const pcr_target* t, const std:
   std::memset(out, 0, sizeof(*out));
   if (t->kind == PCR_TARGET_ABS || t->kind == PCR_TARGET_REL) {
     const double tau = t->value * (t->kind == PCR_TARGET_REL ? R : 1.0);
-    ok = greedy(h, tau, true, b, bound, have);
+    ok = search_nodes >= 0 ? search_plan(h, tau, true, have, search_nodes, b, bound, *ss)
+                           : greedy(h, tau, true, b, bound, have);
     out->psnr_bound = 0;
   } else if (t->kind == PCR_TARGET_PSNR) {
     const double ratio = R / std::pow(10.0, t->value / 20.0);
     const double sse_max = (double)h->meta.n * ratio * ratio;
-    ok = greedy(h, sse_max, false, b, bound, have);
+    ok = search_nodes >= 0 ? search_plan(h, sse_max, false, have, search_nodes, b, bound, *ss)
+                           : greedy(h, sse_max, false, b, bound, have);
     const double rmse = std::sqrt(bound / (double)h->meta.n);
     out->psnr_bound = rmse > 0 ? 20.0 * std::log10(R / rmse) : std::numeric_limits<double>::infinity();
   } else {
@@ -3082,6 +3289,33 @@ extern "C" pcr_status pcr_plan_more(const pcr_handle* h, const pcr_target* t, co
     hv[i] = have->planes[i];
   }
   return plan_impl(h, t, &hv, out);
+}
+
+extern "C" pcr_status pcr_plan_search(const pcr_handle* h, const pcr_target* t, const pcr_retrieval_plan* have,
+                                      int64_t max_nodes, pcr_retrieval_plan* out, pcr_search_info* info) {
+  if (!h || !t || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  if (max_nodes < 0) return fail(PCR_ERR_INVALID_ARG, "max_nodes must be >= 0");
+  const int ns = (int)h->tabs.size();
+  std::vector<int> hv;
+  if (have) {
+    if (have->nstreams != ns) return fail(PCR_ERR_INVALID_ARG, "plan does not match the handle");
+    hv.resize(ns);
+    for (int i = 0; i < ns; i++) {
+      if (have->planes[i] < 0 || have->planes[i] > h->B)
+        return fail(PCR_ERR_INVALID_ARG, "plan plane count out of range");
+      hv[i] = have->planes[i];
+    }
+  }
+  SearchStats ss;
+  const auto t0 = std::chrono::steady_clock::now();
+  const pcr_status st = plan_impl(h, t, have ? &hv : nullptr, out, max_nodes, &ss);
+  if (info) {
+    info->expanded = ss.expanded;
+    info->optimal = ss.optimal;
+    info->greedy_bytes = ss.greedy_bytes;
+    info->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return st;
 }
 
 // ---------------------------------------------------------------------------
