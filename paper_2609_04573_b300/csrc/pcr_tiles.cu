@@ -247,7 +247,7 @@ __device__ __forceinline__ void tile_interp_body(const TileArgs& a, unsigned bid
   // that, for float fields whose rows are 16-byte multiples, every staged row
   // is loaded with aligned 16-byte vectors
   constexpr int XL = 4;
-  constexpr int S0 = T0 + 2 * H0, S1 = T1 + 2 * H, S2 = T2 + 8;
+  constexpr int S1 = T1 + 2 * H, S2 = T2 + 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   A* S = reinterpret_cast<A*>(smem_raw);
 
@@ -1120,8 +1120,15 @@ template <> struct MaxAbs<int64_t> {
 // region 1 starts (1,0,0) step (2,2,2), region 2 (0,1,0) step (1,2,2),
 // region 3 (0,0,1) step (1,1,2) (checked by the launcher).
 // Arithmetic: the 1-D rules of the general tile kernel (same expressions).
-template <typename A, int DEG, bool RET, bool IPR, int T1, int T2>
-__device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, unsigned bid) {
+// TMA (refactor): the field rows of a plane (tile + halo, PR x (T2 + 8)
+// values, zero beyond the field) arrive in shared memory by one
+// cp.async.bulk.tensor copy issued by thread 0 and completed on an mbarrier;
+// two stages, so plane i0 + 2 is in flight while plane i0 is processed and
+// plane i0 + 1 waits.  Waits are bounded: on a timeout the CTA records it in
+// the field statistics, waits (bounded) for its other copy and returns.
+template <typename A, int DEG, bool RET, bool IPR, int T1, int T2, bool TMA = false>
+__device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, unsigned bid,
+                                                  const CUtensorMap* tm = nullptr) {
   constexpr int NT = 256;
   constexpr int HR = DEG - 1;            // reach beyond the tile along i1, i2
   constexpr int PR = T1 + 2 * HR + 1;    // Pe rows: i1 in [b1 - HR, b1 + T1 + HR]
@@ -1162,6 +1169,36 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
   const A* __restrict__ src = reinterpret_cast<const A*>(a.src);
   A* __restrict__ dst = reinterpret_cast<A*>(a.dst);
   const int tid = threadIdx.x;
+
+  // TMA stages (dynamic shared memory, 128-byte aligned) and their mbarriers
+  static_assert(!TMA || !RET, "TMA staging serves the refactor");
+  constexpr int XW = T2 + 2 * XL;                                    // staged row length
+  constexpr int SST = (PR * XW * (int)sizeof(A) + 127) / 128 * 128;  // bytes per stage
+  [[maybe_unused]] unsigned char* stg = nullptr;
+  [[maybe_unused]] uint32_t bar0 = 0, bar1 = 0, par = 0;
+  if constexpr (TMA) {
+    extern __shared__ __align__(128) unsigned char march_dyn[];
+    stg = march_dyn + ((128 - (smem_u32(march_dyn) & 127)) & 127);
+    bar0 = smem_u32(stg + 2 * SST);
+    bar1 = bar0 + 8;
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar1) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+  }
+  // thread 0: plane p's rows into stage sl
+  [[maybe_unused]] auto issue = [&](int p, int sl) {
+    const uint32_t bar = sl ? bar1 : bar0;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(PR * XW * (int)sizeof(A))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
+        ::"r"(smem_u32(stg + sl * SST)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(b2 - XL), "r"(b1 - HR), "r"(p),
+        "r"(bar)
+        : "memory");
+  };
 
   A* __restrict__ g1 = reinterpret_cast<A*>(a.reg[0].stage);
   A* __restrict__ g2 = reinterpret_cast<A*>(a.reg[1].stage);
@@ -1237,7 +1274,20 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
 
   // ---- prefetch registers
   A rg[N1];                     // coarse values of one even plane (ring points)
-  VecT<A, VEC> pv[RET ? 1 : NLV];   // refactor: field rows of one plane
+  VecT<A, VEC> pv[RET || TMA ? 1 : NLV] = {};   // refactor: field rows of one plane
+  [[maybe_unused]] const A* cur = nullptr;   // TMA: the stage holding the current plane
+  // vector `it` of the current plane (registers, or the TMA stage)
+  auto plane_vec = [&](int it) -> VecT<A, VEC> {
+    if constexpr (TMA) {
+      const int i = tid + NT * it;
+      const int pr = i / NV, v = i - pr * NV;
+      return *reinterpret_cast<const VecT<A, VEC>*>(cur + pr * XW + v * VEC);
+    } else if constexpr (!RET) {
+      return pv[it];
+    } else {
+      return VecT<A, VEC>{};
+    }
+  };
   A h1[RET ? N1 : 1], h2[RET ? N2V : 1], h3[RET ? N3 : 1];   // retrieve: c_hat of one plane
 
   auto fetch_ring = [&](int p) {
@@ -1258,20 +1308,22 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
     }
   };
   auto fetch_plane = [&](int i0) {
+    if constexpr (!TMA) {
 #pragma unroll
-    for (int it = 0; it < NLV; it++) {
-      const int i = tid + NT * it;
-      const int pr = i / NV, v = i - pr * NV;
-      const int r = b1 - HR + pr, c0 = b2 - XL + v * VEC;
-      const bool need = i < PR * NV && ((pr >= HR && pr < HR + T1) || !(r & 1)) && r >= 0 && r < m1 && i0 < m0;
-      if (need && c0 >= 0 && c0 + VEC <= m2) {
-        const A* gp = src + (int64_t)i0 * s0 + (int64_t)r * s1 + c0;
-        vld<A, VEC>(pv[it], gp);
-      } else {
+      for (int it = 0; it < NLV; it++) {
+        const int i = tid + NT * it;
+        const int pr = i / NV, v = i - pr * NV;
+        const int r = b1 - HR + pr, c0 = b2 - XL + v * VEC;
+        const bool need = i < PR * NV && ((pr >= HR && pr < HR + T1) || !(r & 1)) && r >= 0 && r < m1 && i0 < m0;
+        if (need && c0 >= 0 && c0 + VEC <= m2) {
+          const A* gp = src + (int64_t)i0 * s0 + (int64_t)r * s1 + c0;
+          vld<A, VEC>(pv[it], gp);
+        } else {
 #pragma unroll
-        for (int k = 0; k < VEC; k++) {
-          const int c = c0 + k;
-          pv[it].v[k] = (need && c >= 0 && c < m2) ? src[(int64_t)i0 * s0 + (int64_t)r * s1 + c] : A(0);
+          for (int k = 0; k < VEC; k++) {
+            const int c = c0 + k;
+            pv[it].v[k] = (need && c >= 0 && c < m2) ? src[(int64_t)i0 * s0 + (int64_t)r * s1 + c] : A(0);
+          }
         }
       }
     }
@@ -1297,13 +1349,14 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
       if (i >= PR * NV || pr < HR || pr >= HR + T1 || b1 - HR + pr >= m1) continue;
       const int c0 = b2 - XL + v * VEC;
       if (c0 < b2 || c0 >= b2 + T2) continue;   // vectors lie wholly inside or outside the tile's columns
+      const VecT<A, VEC> x = plane_vec(it);
       if (c0 + VEC <= m2) {
 #pragma unroll
-        for (int k = 0; k < VEC; k++) take(pv[it].v[k]);
+        for (int k = 0; k < VEC; k++) take(x.v[k]);
       } else {
 #pragma unroll
         for (int k = 0; k < VEC; k++)
-          if (c0 + k < m2) take(pv[it].v[k]);
+          if (c0 + k < m2) take(x.v[k]);
       }
     }
     sst[0][tid] = lo;
@@ -1322,22 +1375,23 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
       const int r = b1 - HR + pr;
       const bool rows = pr >= HR && pr < HR + T1;
       if (!rows && (r & 1)) continue;
+      const VecT<A, VEC> x = plane_vec(it);
       // element k sits at i2 = b2 - XL + VEC v + k: even k -> Pe, odd k -> Po
       if constexpr (VEC == 4) {
         const int ce = 2 * v - (XL - HR) / 2 + PAD;   // Pe column of element 0 (element 2: ce + 1)
         if (ce >= 0 && ce + 1 < CE + PAD) {
-          *reinterpret_cast<float2*>(&Pe[pr][ce]) = make_float2(pv[it].v[0], pv[it].v[2]);
+          *reinterpret_cast<float2*>(&Pe[pr][ce]) = make_float2(x.v[0], x.v[2]);
         } else {
-          if (ce >= PAD && ce < CE + PAD) Pe[pr][ce] = pv[it].v[0];
-          if (ce + 1 >= PAD && ce + 1 < CE + PAD) Pe[pr][ce + 1] = pv[it].v[2];
+          if (ce >= PAD && ce < CE + PAD) Pe[pr][ce] = x.v[0];
+          if (ce + 1 >= PAD && ce + 1 < CE + PAD) Pe[pr][ce + 1] = x.v[2];
         }
         const int co = 2 * v - XL / 2;                 // Po column of element 1 (element 3: co + 1)
-        if (rows && co >= 0 && co + 1 < CO) *reinterpret_cast<float2*>(&Po[pr - HR][co]) = make_float2(pv[it].v[1], pv[it].v[3]);
+        if (rows && co >= 0 && co + 1 < CO) *reinterpret_cast<float2*>(&Po[pr - HR][co]) = make_float2(x.v[1], x.v[3]);
       } else {
         const int ce = v - (XL - HR) / 2 + PAD;       // element 0 (even)
-        if (ce >= PAD && ce < CE + PAD) Pe[pr][ce] = pv[it].v[0];
+        if (ce >= PAD && ce < CE + PAD) Pe[pr][ce] = x.v[0];
         const int co = v - XL / 2;                    // element 1 (odd)
-        if (rows && co >= 0 && co < CO) Po[pr - HR][co] = pv[it].v[1];
+        if (rows && co >= 0 && co < CO) Po[pr - HR][co] = x.v[1];
       }
     }
   };
@@ -1403,13 +1457,34 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
   store_ring(z0);
   fetch_ring(z0 + 2);
   store_ring(z0 + 2);
-  if (!RET) fetch_plane(z0);
-  else fetch_chat(z0);
+  if constexpr (TMA) {
+    if (tid == 0) {
+      issue(z0, 0);
+      if (z0 + 1 < z1) issue(z0 + 1, 1);
+    }
+  } else if (!RET) {
+    fetch_plane(z0);
+  } else {
+    fetch_chat(z0);
+  }
 
   for (int i0 = z0; i0 < z1; i0++) {
     const bool odd = i0 & 1;
-    // registers -> shared memory: this plane's rows, and (odd planes) the
-    // coarse plane i0 + 3 (the slot of plane i0 - 5)
+    if constexpr (TMA) {   // this plane's rows have landed in stage (i0 - z0) & 1
+      const int sl = (i0 - z0) & 1;
+      const bool ok = mbar_wait(sl ? bar1 : bar0, (par >> sl) & 1);
+      if (__syncthreads_or(!ok)) {   // the whole CTA gives up together
+        if (tid == 0) {
+          if (a.stats) atomicExch(&a.stats->timeout, 1);
+          if (i0 + 1 < z1) mbar_wait(sl ? bar0 : bar1, (par >> (sl ^ 1)) & 1);
+        }
+        return;
+      }
+      par ^= 1u << sl;
+      cur = reinterpret_cast<const A*>(stg + sl * SST);
+    }
+    // registers (or the TMA stage) -> shared memory: this plane's rows, and
+    // (odd planes) the coarse plane i0 + 3 (the slot of plane i0 - 5)
     if (!RET) store_plane();
     if (odd) store_ring(i0 + 3);
     A c1[RET ? N1 : 1], c2[RET ? N2V : 1], c3[RET ? N3 : 1];
@@ -1422,6 +1497,10 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
       for (int it = 0; it < N3; it++) c3[it] = h3[it];
     }
     __syncthreads();
+    // TMA: the stage just read takes plane i0 + 2
+    if constexpr (TMA) {
+      if (tid == 0 && i0 + 2 < z1) issue(i0 + 2, (i0 - z0) & 1);
+    }
     // the next plane's inputs, in flight during this plane's passes
     if (i0 + 1 < z1) {
       if (!RET) fetch_plane(i0 + 1);
@@ -1644,6 +1723,14 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
   level0_march_body<A, DEG, RET, IPR, T1, T2>(a, zc, blockIdx.x);
 }
 
+// refactor with TMA-staged field rows (tm: the field, boxes of
+// (T2 + 8) x (T1 + 2 (DEG - 1) + 1) x 1 values)
+template <typename A, int DEG, bool IPR, int T1, int T2>
+__global__ void __launch_bounds__(256, 4) k_level0_march_tma(const __grid_constant__ CUtensorMap tm,
+                                                             const __grid_constant__ TileArgs a, int zc) {
+  level0_march_body<A, DEG, false, IPR, T1, T2, true>(a, zc, blockIdx.x, &tm);
+}
+
 // the plane-marching kernel over several fields (or fixed-point levels) in
 // one launch: item i owns blocks first[i] .. first[i + 1] - 1
 struct MarchBatch {
@@ -1752,6 +1839,11 @@ static void run_tile_kind(const TileArgs& a, cudaStream_t s) {
   }
 }
 
+// schedule choice: the marching kernel with TMA-staged field rows and the
+// default plane chunking (refactor levels whose statistics it takes; the
+// register-prefetch form elsewhere)
+constexpr int kMarchTma = -2;
+
 // grid of the plane-marching kernel for one level: column tiles covering the
 // box (or the grid) and chunks of zc planes; returns the block count (0:
 // nothing to do) with a.ntiles / a.tlo set
@@ -1786,8 +1878,55 @@ static int64_t march_grid(TileArgs& a, int zc_force, int& zc_out) {
   return a.ntiles[0] * cols;
 }
 
+// tensor map of the field for the TMA form of the marching kernel: boxes of
+// (T2 + 8) x rows x 1 values, zero fill beyond the field (the launcher's
+// contiguity and 16-byte row checks make the strides legal)
+template <typename A>
+static bool march_tensor_map(const TileArgs& a, int T2, int rows, CUtensorMap& tm) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const CUtensorMapDataType dt = std::is_same<A, float>::value    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : std::is_same<A, double>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                                                  : CU_TENSOR_MAP_DATA_TYPE_INT64;
+  const cuuint64_t gdim[3] = {(cuuint64_t)a.m[2], (cuuint64_t)a.m[1], (cuuint64_t)a.m[0]};
+  const cuuint64_t gstride[2] = {(cuuint64_t)a.stride[1] * sizeof(A), (cuuint64_t)a.stride[0] * sizeof(A)};
+  const cuuint32_t box[3] = {(cuuint32_t)(T2 + 8), (cuuint32_t)rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(&tm, dt, 3, const_cast<void*>(a.src), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the TMA form: refactor of a level whose statistics the kernel takes (their
+// record receives a timeout), field base 16-byte aligned (march_applies)
+template <typename A, int DEG, bool PR, int T1, int T2>
+static bool run_level0_march_tma(const TileArgs& a0, cudaStream_t s, int zc_force) {
+  if (a0.retrieve || !a0.stats) return false;
+  constexpr int ROWS = T1 + 2 * (DEG - 1) + 1;
+  constexpr int SST = (ROWS * (T2 + 8) * (int)sizeof(A) + 127) / 128 * 128;
+  constexpr int SMEM = 2 * SST + 128 + 16;
+  CUtensorMap tm;
+  if (!march_tensor_map<A>(a0, T2, ROWS, tm)) return false;
+  TileArgs a = a0;
+  int zc = 0;
+  const int64_t nb = march_grid<T1, T2>(a, zc_force, zc);
+  if (!nb) return true;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_level0_march_tma<A, DEG, PR, T1, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    cudaFuncSetAttribute(k_level0_march_tma<A, DEG, PR, T1, T2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    attr = true;
+  }
+  count_launch();
+  k_level0_march_tma<A, DEG, PR, T1, T2><<<(unsigned)nb, 256, SMEM, s>>>(tm, a, zc);
+  return true;
+}
+
 template <typename A, int DEG, bool RET, bool PR, int T1, int T2>
-static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force) {
+static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force, bool tma = false) {
+  if constexpr (!RET) {
+    if (tma && run_level0_march_tma<A, DEG, PR, T1, T2>(a0, s, zc_force)) return;
+  }
   TileArgs a = a0;
   int zc = 0;
   const int64_t nb = march_grid<T1, T2>(a, zc_force, zc);
@@ -1807,7 +1946,7 @@ static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force) {
 template <typename A, int DEG, bool RET, bool PR, int T1, int T2>
 static void run_level0_march_multi(const std::vector<TileArgs>& v, const std::vector<int>& zcs, cudaStream_t s) {
   if (v.size() == 1) {
-    run_level0_march<A, DEG, RET, PR, T1, T2>(v[0], s, zcs[0]);
+    run_level0_march<A, DEG, RET, PR, T1, T2>(v[0], s, zcs[0], zcs[0] == kMarchTma);
     return;
   }
   static bool attr = false;
@@ -1856,11 +1995,13 @@ static bool march_applies(const TileArgs& a) {
   return true;
 }
 
-// zc > 0: chunks of zc planes; otherwise the default chunking
+// zc > 0: chunks of zc planes; otherwise the default chunking (kMarchTma:
+// with TMA-staged field rows where that form applies)
 template <typename A>
 static void march_launch(const TileArgs& a, cudaStream_t s, int zc) {
   constexpr int T1 = 16, T2 = sizeof(A) == 4 ? 128 : 64;
   const bool pr = a.interp != 0;
+  const bool tma = zc == kMarchTma;
   if (a.retrieve) {
     if (a.degree == 3) {
       if (pr) run_level0_march<A, 3, true, true, T1, T2>(a, s, zc);
@@ -1871,11 +2012,11 @@ static void march_launch(const TileArgs& a, cudaStream_t s, int zc) {
     }
   } else {
     if (a.degree == 3) {
-      if (pr) run_level0_march<A, 3, false, true, T1, T2>(a, s, zc);
-      else run_level0_march<A, 3, false, false, T1, T2>(a, s, zc);
+      if (pr) run_level0_march<A, 3, false, true, T1, T2>(a, s, zc, tma);
+      else run_level0_march<A, 3, false, false, T1, T2>(a, s, zc, tma);
     } else {
-      if (pr) run_level0_march<A, 1, false, true, T1, T2>(a, s, zc);
-      else run_level0_march<A, 1, false, false, T1, T2>(a, s, zc);
+      if (pr) run_level0_march<A, 1, false, true, T1, T2>(a, s, zc, tma);
+      else run_level0_march<A, 1, false, false, T1, T2>(a, s, zc, tma);
     }
   }
 }
@@ -1886,8 +2027,9 @@ static void march_launch(const TileArgs& a, cudaStream_t s, int zc) {
 // Where the marching kernel applies, a level can also run the general tile
 // kernel, and the marching kernel's plane chunk sets its grid; all choices
 // compute the same values (same expression trees).  Choice 0 = general tile
-// kernel, -1 = marching with the default chunking, k > 0 = marching with
-// chunks of k planes.  With tuning on, the first launch of an untuned (value
+// kernel, -1 = marching with the default chunking, kMarchTma (-2, the
+// default) = the same with TMA-staged field rows where that form applies,
+// k > 0 = marching with chunks of k planes.  With tuning on, the first launch of an untuned (value
 // kind, direction, degree, level grid) on a stream that is not being
 // captured times every candidate (CUDA events, the best of two runs after a
 // warm-up) and keeps the fastest; later launches, captured ones included,
@@ -1914,7 +2056,7 @@ struct TuneVal {
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune;
 std::atomic<int> g_tune_on{0};
-constexpr int kTuneCand[] = {0, 8, 16, 32, 64, -1};
+constexpr int kTuneCand[] = {0, 8, 16, 32, 64, -1, kMarchTma};
 
 template <typename A>
 void run_choice(const TileArgs& a, cudaStream_t s, int choice) {
@@ -1955,7 +2097,7 @@ TuneVal tune(const TileArgs& a, cudaStream_t s) {
 template <typename A>
 int tuned_choice(int vk, const TileArgs& a, cudaStream_t s) {
   const TuneKey key{vk, a.retrieve, a.degree, a.interp, a.m[0], a.m[1], a.m[2]};
-  int choice = -1;
+  int choice = kMarchTma;
   bool have = false;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
