@@ -433,9 +433,10 @@ def run_pcr(args):
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "shape": list(shape), "scheme": "per-level cubic + "
+        "config": {"workload": WORKLOAD if shape == FIELD_SHAPE else f"grf_k-5/3_{'x'.join(map(str, shape))}_f32",
+                   "shape": list(shape), "scheme": "per-level cubic + "
                    "coefficient decomposition (axis 2) + generic bitplanes, B=32",
-                   "target": f"{TARGET[0]} {TARGET[1]}", "l2": "inputs larger than L2 (512 MB field)",
+                   "target": f"{TARGET[0]} {TARGET[1]}", "l2": f"inputs larger than L2 ({nbytes >> 20} MB field)",
                    "parallelism": f"replicas x{world}",
                    "pipelined": "step i+1's refactor enqueued before step i's tables are finished, "
                                 "planned and retrieved; refactors and retrievals on two streams; "
