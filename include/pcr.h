@@ -256,6 +256,14 @@ void pcr_refactor_graph_free(pcr_refactor_graph* g);
  * -- k > 0 marching with k-plane chunks), ms (the winner's time); *n_out =
  * entries in the table; reset clears it afterwards. */
 pcr_status pcr_autotune_enable(int enable);
+/* Device status of the current device: *timeouts = 1 when a bounded wait
+ * of a retrieval kernel (TMA-staged level-0 reconstruction) gave up since
+ * the last clear -- the tiles of that CTA were left unwritten -- else 0;
+ * clear != 0 resets it.  Synchronous (waits for the device's pending work
+ * to read it).  pcr_retrieve with want_gpu_ms set checks and clears it
+ * itself and returns PCR_ERR_TIMEOUT.  Refactor waits report through the
+ * refactor's own status. */
+pcr_status pcr_device_status(int* timeouts, int clear);
 /* Pin one schedule: `key` = the 7 int64 of an entry (as pcr_autotune_read
  * gives them), `choice` one of the candidates (0, 8, 16, 32, 64, -1, -2);
  * every later launch of that level grid uses it (a level the marching

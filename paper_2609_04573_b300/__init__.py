@@ -149,6 +149,7 @@ _sigs = {
     "pcr_refactor_graph_info": [_vp, _i64p, _i64p, _i64p],
     "pcr_refactor_graph_times": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "pcr_autotune_set": [_i64p, C.c_int],
+    "pcr_device_status": [C.POINTER(C.c_int), C.c_int],
     "pcr_autotune_enable": [C.c_int],
     "pcr_autotune_read": [C.c_int, _i64p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int],
 }
@@ -740,6 +741,14 @@ class Progressive:
 def autotune(enable=True):
     """Level-schedule autotuner on/off (pcr_autotune_enable)."""
     _check(_lib.pcr_autotune_enable(1 if enable else 0))
+
+
+def device_status(clear=True):
+    """1 when a bounded wait of a retrieval kernel gave up on the current
+    device since the last clear, else 0 (pcr_device_status; synchronous)."""
+    v = C.c_int()
+    _check(_lib.pcr_device_status(C.byref(v), int(clear)))
+    return v.value
 
 
 def autotune_pin(key, choice):

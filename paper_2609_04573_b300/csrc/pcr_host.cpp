@@ -3038,6 +3038,14 @@ extern "C" pcr_status pcr_refactor_graph_info(const pcr_refactor_graph* g, int64
 
 extern "C" void pcr_refactor_graph_free(pcr_refactor_graph* g) { delete g; }
 
+extern "C" pcr_status pcr_device_status(int* timeouts, int clear) {
+  if (!timeouts) return fail(PCR_ERR_INVALID_ARG, "null argument");
+  const int v = read_device_timeouts(clear != 0);
+  if (v < 0) return fail(PCR_ERR_CUDA, "reading the device status failed");
+  *timeouts = v;
+  return PCR_OK;
+}
+
 extern "C" pcr_status pcr_autotune_enable(int enable) {
   set_autotune(enable);
   return PCR_OK;
@@ -3889,6 +3897,10 @@ extern "C" pcr_status pcr_retrieve(const pcr_handle* h, const pcr_target* target
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
     info->gpu_ms = ms;
+    // the call waited for its work: a bounded device wait that gave up
+    // during it is reported here
+    if (st == PCR_OK && read_device_timeouts(true) > 0)
+      return fail(PCR_ERR_TIMEOUT, "a device wait of the retrieval gave up");
   }
   return st;
 }

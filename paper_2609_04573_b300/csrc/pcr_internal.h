@@ -263,6 +263,9 @@ void add_launches(long long n);
 // autotuner of the level-interpolation schedule (pcr_tiles.cu)
 int set_autotune(int on);   // returns the previous setting
 bool autotune_pin(const int64_t* key, int choice);   // false: unknown key field or choice
+// bounded waits of retrieval kernels that gave up on the current device
+// since the last clear (-1: the read failed); clear resets the count
+int read_device_timeouts(bool clear);
 int autotune_entries(int max_entries, int64_t* keys, int* choice, double* ms);
 void clear_autotune();
 

@@ -1128,7 +1128,7 @@ template <> struct MaxAbs<int64_t> {
 // the field statistics, waits (bounded) for its other copy and returns.
 template <typename A, int DEG, bool RET, bool IPR, int T1, int T2, bool TMA = false>
 __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, unsigned bid,
-                                                  const CUtensorMap* tm = nullptr) {
+                                                  const CUtensorMap* tm = nullptr, int* err = nullptr) {
   constexpr int NT = 256;
   constexpr int HR = DEG - 1;            // reach beyond the tile along i1, i2
   constexpr int PR = T1 + 2 * HR + 1;    // Pe rows: i1 in [b1 - HR, b1 + T1 + HR]
@@ -1170,34 +1170,55 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
   A* __restrict__ dst = reinterpret_cast<A*>(a.dst);
   const int tid = threadIdx.x;
 
-  // TMA stages (dynamic shared memory, 128-byte aligned) and their mbarriers
-  static_assert(!TMA || !RET, "TMA staging serves the refactor");
-  constexpr int XW = T2 + 2 * XL;                                    // staged row length
-  constexpr int SST = (PR * XW * (int)sizeof(A) + 127) / 128 * 128;  // bytes per stage
+  // TMA stages (dynamic shared memory, 128-byte aligned) and their mbarriers.
+  // Refactor: a stage holds one plane's field rows (PR x XW values from
+  // (b2 - XL, b1 - HR)); two stages.  Retrieve: a stage holds one plane's
+  // c_hat boxes of the three regions' staging arrays -- region 1 (odd planes)
+  // CR x W12 values from compact (b2 / 2 - 4, (b1 - HR) / 2), region 2
+  // T1 / 2 x W12 from (b2 / 2 - 4, b1 / 2), region 3 T1 x T2 / 2 from
+  // (b2 / 2, b1) -- zero beyond each array; three stages (FP32), two (8-byte
+// values).
+  constexpr int XW = T2 + 2 * XL;                                    // staged row length (refactor)
+  constexpr int W12 = T2 / 2 + 8;                                    // region 1 / 2 box row (retrieve)
+  constexpr int R1B = (CR * W12 * (int)sizeof(A) + 127) / 128 * 128;
+  constexpr int R2B = ((T1 / 2) * W12 * (int)sizeof(A) + 127) / 128 * 128;
+  constexpr int R3B = (T1 * (T2 / 2) * (int)sizeof(A) + 127) / 128 * 128;
+  constexpr int SST = RET ? R1B + R2B + R3B : (PR * XW * (int)sizeof(A) + 127) / 128 * 128;   // bytes per stage
+  constexpr int NSTG = RET && sizeof(A) == 4 ? 3 : 2;   // 8-byte values: two stages keep 4 CTAs per SM
   [[maybe_unused]] unsigned char* stg = nullptr;
-  [[maybe_unused]] uint32_t bar0 = 0, bar1 = 0, par = 0;
+  [[maybe_unused]] uint32_t barb = 0, par = 0;
   if constexpr (TMA) {
     extern __shared__ __align__(128) unsigned char march_dyn[];
     stg = march_dyn + ((128 - (smem_u32(march_dyn) & 127)) & 127);
-    bar0 = smem_u32(stg + 2 * SST);
-    bar1 = bar0 + 8;
+    barb = smem_u32(stg + NSTG * SST);
     if (tid == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar1) : "memory");
+      for (int k = 0; k < NSTG; k++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barb + 8 * k) : "memory");
       asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
   }
-  // thread 0: plane p's rows into stage sl
-  [[maybe_unused]] auto issue = [&](int p, int sl) {
-    const uint32_t bar = sl ? bar1 : bar0;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(PR * XW * (int)sizeof(A))
-                 : "memory");
+  [[maybe_unused]] auto tma3 = [&](const unsigned char* dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
-        ::"r"(smem_u32(stg + sl * SST)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(b2 - XL), "r"(b1 - HR), "r"(p),
-        "r"(bar)
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
+  };
+  // thread 0: plane p's inputs into stage sl
+  [[maybe_unused]] auto issue = [&](int p, int sl) {
+    const uint32_t bar = barb + 8 * sl;
+    unsigned char* d = stg + sl * SST;
+    if constexpr (RET) {
+      const bool o = p & 1;
+      const int bytes = ((o ? CR : 0) * W12 + (T1 / 2) * W12 + T1 * (T2 / 2)) * (int)sizeof(A);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+      if (o) tma3(d, tm, (b2 >> 1) - 4, (b1 - HR) >> 1, p >> 1, bar);
+      tma3(d + R1B, tm + 1, (b2 >> 1) - 4, b1 >> 1, p, bar);
+      tma3(d + R1B + R2B, tm + 2, b2 >> 1, b1, p, bar);
+    } else {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(PR * XW * (int)sizeof(A))
+                   : "memory");
+      tma3(d, tm, b2 - XL, b1 - HR, p, bar);
+    }
   };
 
   A* __restrict__ g1 = reinterpret_cast<A*>(a.reg[0].stage);
@@ -1288,7 +1309,7 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
       return VecT<A, VEC>{};
     }
   };
-  A h1[RET ? N1 : 1], h2[RET ? N2V : 1], h3[RET ? N3 : 1];   // retrieve: c_hat of one plane
+  A h1[RET && !TMA ? N1 : 1], h2[RET && !TMA ? N2V : 1], h3[RET && !TMA ? N3 : 1];   // retrieve: c_hat of one plane
 
   auto fetch_ring = [&](int p) {
 #pragma unroll
@@ -1396,55 +1417,57 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
     }
   };
   auto fetch_chat = [&](int i0) {
-    if (i0 >= z1) return;
-    if (i0 & 1) {
-      const int64_t B1 = base1(i0);
+    if constexpr (!TMA) {
+      if (i0 >= z1) return;
+      if (i0 & 1) {
+        const int64_t B1 = base1(i0);
 #pragma unroll
-      for (int it = 0; it < N1; it++) {
-        int ci, cj, r, c;
-        // per-region retrieval rebuilds halo points too: their c_hat as well
-        const bool ok = p1pt(it, ci, cj, r, c) && (IPR || in_tile(r, c)) && r >= 0 && c >= 0 && r < m1 && c < m2;
-        h1[it] = ok ? g1[B1 + (int64_t)(r >> 1) * rp1 + (c >> 1)] : A(0);
+        for (int it = 0; it < N1; it++) {
+          int ci, cj, r, c;
+          // per-region retrieval rebuilds halo points too: their c_hat as well
+          const bool ok = p1pt(it, ci, cj, r, c) && (IPR || in_tile(r, c)) && r >= 0 && c >= 0 && r < m1 && c < m2;
+          h1[it] = ok ? g1[B1 + (int64_t)(r >> 1) * rp1 + (c >> 1)] : A(0);
+        }
       }
-    }
-    const int64_t B2 = base2(i0), B3 = base3(i0);
-    if constexpr (PAIR2) {
+      const int64_t B2 = base2(i0), B3 = base3(i0);
+      if constexpr (PAIR2) {
 #pragma unroll
-      for (int it = 0; it < N2P; it++) {
-        int ri, cj, r, c;
-        bool pair;
-        float2 t = make_float2(0.0f, 0.0f);
-        // pairs inside the tile: both points (c + 2 < m2 when c < m2)
-        if (p2pair(it, ri, cj, r, c, pair) && pair && in_tile(r, c) && in_tile(r, c + 2) && r < m1 && c < m2)
-          t = *reinterpret_cast<const float2*>(g2 + B2 + (int64_t)(r >> 1) * rp2 + (c >> 1));
-        h2[2 * it] = t.x;
-        h2[2 * it + 1] = t.y;
+        for (int it = 0; it < N2P; it++) {
+          int ri, cj, r, c;
+          bool pair;
+          float2 t = make_float2(0.0f, 0.0f);
+          // pairs inside the tile: both points (c + 2 < m2 when c < m2)
+          if (p2pair(it, ri, cj, r, c, pair) && pair && in_tile(r, c) && in_tile(r, c + 2) && r < m1 && c < m2)
+            t = *reinterpret_cast<const float2*>(g2 + B2 + (int64_t)(r >> 1) * rp2 + (c >> 1));
+          h2[2 * it] = t.x;
+          h2[2 * it + 1] = t.y;
+        }
+      } else {
+#pragma unroll
+        for (int it = 0; it < N2; it++) {
+          int ri, cj, r, c;
+          const bool ok = p2pt(it, ri, cj, r, c) && (IPR || in_tile(r, c)) && r >= 0 && c >= 0 && r < m1 && c < m2;
+          h2[it] = ok ? g2[B2 + (int64_t)(r >> 1) * rp2 + (c >> 1)] : A(0);
+        }
       }
-    } else {
+      if constexpr (PAIR) {
 #pragma unroll
-      for (int it = 0; it < N2; it++) {
-        int ri, cj, r, c;
-        const bool ok = p2pt(it, ri, cj, r, c) && (IPR || in_tile(r, c)) && r >= 0 && c >= 0 && r < m1 && c < m2;
-        h2[it] = ok ? g2[B2 + (int64_t)(r >> 1) * rp2 + (c >> 1)] : A(0);
-      }
-    }
-    if constexpr (PAIR) {
+        for (int pi = 0; pi < N3 / 2; pi++) {
+          int ri, oj, r, c;
+          p3pair(pi, ri, oj, r, c);
+          float2 t = make_float2(0.0f, 0.0f);
+          if (r < m1 && c < m2) t = *reinterpret_cast<const float2*>(g3 + B3 + (int64_t)r * rp3 + (c >> 1));
+          h3[2 * pi] = t.x;
+          h3[2 * pi + 1] = t.y;
+        }
+      } else {
 #pragma unroll
-      for (int pi = 0; pi < N3 / 2; pi++) {
-        int ri, oj, r, c;
-        p3pair(pi, ri, oj, r, c);
-        float2 t = make_float2(0.0f, 0.0f);
-        if (r < m1 && c < m2) t = *reinterpret_cast<const float2*>(g3 + B3 + (int64_t)r * rp3 + (c >> 1));
-        h3[2 * pi] = t.x;
-        h3[2 * pi + 1] = t.y;
-      }
-    } else {
-#pragma unroll
-      for (int it = 0; it < N3; it++) {
-        int ri, oj, r, c;
-        p3pt(it, ri, oj, r, c);
-        const bool ok = r < m1 && c < m2;
-        h3[it] = ok ? g3[B3 + (int64_t)r * rp3 + (c >> 1)] : A(0);
+        for (int it = 0; it < N3; it++) {
+          int ri, oj, r, c;
+          p3pt(it, ri, oj, r, c);
+          const bool ok = r < m1 && c < m2;
+          h3[it] = ok ? g3[B3 + (int64_t)r * rp3 + (c >> 1)] : A(0);
+        }
       }
     }
   };
@@ -1457,11 +1480,10 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
   store_ring(z0);
   fetch_ring(z0 + 2);
   store_ring(z0 + 2);
+  int slot = 0;   // TMA: the stage of the current plane
   if constexpr (TMA) {
-    if (tid == 0) {
-      issue(z0, 0);
-      if (z0 + 1 < z1) issue(z0 + 1, 1);
-    }
+    if (tid == 0)
+      for (int k = 0; k < NSTG && z0 + k < z1; k++) issue(z0 + k, k);
   } else if (!RET) {
     fetch_plane(z0);
   } else {
@@ -1470,25 +1492,27 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
 
   for (int i0 = z0; i0 < z1; i0++) {
     const bool odd = i0 & 1;
-    if constexpr (TMA) {   // this plane's rows have landed in stage (i0 - z0) & 1
-      const int sl = (i0 - z0) & 1;
-      const bool ok = mbar_wait(sl ? bar1 : bar0, (par >> sl) & 1);
+    if constexpr (TMA) {   // this plane's inputs have landed in stage `slot`
+      const bool ok = mbar_wait(barb + 8 * slot, (par >> slot) & 1);
       if (__syncthreads_or(!ok)) {   // the whole CTA gives up together
         if (tid == 0) {
-          if (a.stats) atomicExch(&a.stats->timeout, 1);
-          if (i0 + 1 < z1) mbar_wait(sl ? bar0 : bar1, (par >> (sl ^ 1)) & 1);
+          atomicExch(err, 1);
+          for (int k = 1; k < NSTG && i0 + k < z1; k++) {   // the copies still in flight
+            const int s2 = (slot + k) % NSTG;
+            mbar_wait(barb + 8 * s2, (par >> s2) & 1);
+          }
         }
         return;
       }
-      par ^= 1u << sl;
-      cur = reinterpret_cast<const A*>(stg + sl * SST);
+      par ^= 1u << slot;
+      cur = reinterpret_cast<const A*>(stg + slot * SST);
     }
     // registers (or the TMA stage) -> shared memory: this plane's rows, and
     // (odd planes) the coarse plane i0 + 3 (the slot of plane i0 - 5)
     if (!RET) store_plane();
     if (odd) store_ring(i0 + 3);
-    A c1[RET ? N1 : 1], c2[RET ? N2V : 1], c3[RET ? N3 : 1];
-    if (RET) {
+    A c1[RET && !TMA ? N1 : 1], c2[RET && !TMA ? N2V : 1], c3[RET && !TMA ? N3 : 1];
+    if (RET && !TMA) {
 #pragma unroll
       for (int it = 0; it < N1; it++) c1[it] = h1[it];
 #pragma unroll
@@ -1496,15 +1520,37 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
 #pragma unroll
       for (int it = 0; it < N3; it++) c3[it] = h3[it];
     }
+    // c_hat of pass-1 item (ci, cj), pass-2 item (ri, cj), pass-3 point
+    // (ri, oj): registers, or the regions' boxes in the TMA stage
+    [[maybe_unused]] const A *sb1 = nullptr, *sb2 = nullptr, *sb3 = nullptr;
+    if constexpr (TMA && RET) {
+      sb1 = cur;
+      sb2 = reinterpret_cast<const A*>(reinterpret_cast<const unsigned char*>(cur) + R1B);
+      sb3 = reinterpret_cast<const A*>(reinterpret_cast<const unsigned char*>(cur) + R1B + R2B);
+    }
+    [[maybe_unused]] auto chat1 = [&](int it, int ci, int cj) -> A {
+      if constexpr (TMA && RET) return sb1[ci * W12 + cj - HR / 2 + 4];
+      else return c1[it];
+    };
+    [[maybe_unused]] auto chat2 = [&](int it, int ri, int cj) -> A {
+      if constexpr (TMA && RET) return sb2[ri * W12 + cj - HR / 2 + 4];
+      else return c2[it];
+    };
+    [[maybe_unused]] auto chat3 = [&](int it, int ri, int oj) -> A {
+      if constexpr (TMA && RET) return sb3[ri * (T2 / 2) + oj];
+      else return c3[it];
+    };
     __syncthreads();
-    // TMA: the stage just read takes plane i0 + 2
-    if constexpr (TMA) {
-      if (tid == 0 && i0 + 2 < z1) issue(i0 + 2, (i0 - z0) & 1);
+    // TMA refactor: the stage just read takes plane i0 + 2
+    if constexpr (TMA && !RET) {
+      if (tid == 0 && i0 + 2 < z1) issue(i0 + 2, slot);
     }
     // the next plane's inputs, in flight during this plane's passes
     if (i0 + 1 < z1) {
-      if (!RET) fetch_plane(i0 + 1);
-      else fetch_chat(i0 + 1);
+      if constexpr (!TMA) {
+        if (!RET) fetch_plane(i0 + 1);
+        else fetch_chat(i0 + 1);
+      }
       if (!odd) fetch_ring(i0 + 4);       // needed by plane i0 + 1
     }
     if (!odd && RET) {
@@ -1542,13 +1588,13 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
             g1[B1 + (int64_t)(r >> 1) * rp1 + (c >> 1)] = cv;
             mx1 = MX::upd(mx1, cv);
           } else {
-            Xo[r - b1][c - b2] = TAr<A>::add(W, c1[it]);
+            Xo[r - b1][c - b2] = TAr<A>::add(W, chat1(it, ci, cj));
           }
         }
         // later passes read predictions (per-level), or originals /
         // reconstructed values (per-region refactor / retrieval)
         if (!IPR) Pe[2 * ci][cj + PAD] = W;
-        else if (RET) Pe[2 * ci][cj + PAD] = TAr<A>::add(W, c1[it]);
+        else if (RET) Pe[2 * ci][cj + PAD] = TAr<A>::add(W, chat1(it, ci, cj));
       }
       __syncthreads();
     }
@@ -1620,11 +1666,11 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
             g2[B2 + (int64_t)(r >> 1) * rp2 + (c >> 1)] = cv;
             mx2 = MX::upd(mx2, cv);
           } else {
-            Xo[r - b1][c - b2] = TAr<A>::add(W, c2[it]);
+            Xo[r - b1][c - b2] = TAr<A>::add(W, chat2(it, ri, cj));
           }
         }
         if (!IPR) Pe[pr][cj + PAD] = W;
-        else if (RET) Pe[pr][cj + PAD] = TAr<A>::add(W, c2[it]);
+        else if (RET) Pe[pr][cj + PAD] = TAr<A>::add(W, chat2(it, ri, cj));
       }
     }
     __syncthreads();
@@ -1657,8 +1703,17 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
           *reinterpret_cast<float2*>(g3 + B3 + (int64_t)r * rp3 + (c >> 1)) = make_float2(c0v, c1v);
           mx3 = MX::upd(MX::upd(mx3, c0v), c1v);
         } else {
-          Xo[ri][c - b2] = TAr<A>::add(W0, c3[2 * pi]);
-          Xo[ri][c + 2 - b2] = TAr<A>::add(W1, c3[2 * pi + 1]);
+          A h0, h1v;
+          if constexpr (TMA && RET) {   // adjacent in the region-3 box
+            const float2 t = *reinterpret_cast<const float2*>(&sb3[ri * (T2 / 2) + oj]);
+            h0 = t.x;
+            h1v = t.y;
+          } else {
+            h0 = c3[2 * pi];
+            h1v = c3[2 * pi + 1];
+          }
+          Xo[ri][c - b2] = TAr<A>::add(W0, h0);
+          Xo[ri][c + 2 - b2] = TAr<A>::add(W1, h1v);
         }
       }
     } else {
@@ -1682,12 +1737,17 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
           g3[B3 + (int64_t)r * rp3 + (c >> 1)] = cv;
           mx3 = MX::upd(mx3, cv);
         } else {
-          Xo[ri][c - b2] = TAr<A>::add(W, c3[it]);
+          Xo[ri][c - b2] = TAr<A>::add(W, chat3(it, ri, oj));
         }
       }
     }
     if (RET) {
       __syncthreads();
+      // TMA retrieve: the passes are done with this stage; it takes plane
+      // i0 + NSTG
+      if constexpr (TMA && RET) {
+        if (tid == 0 && i0 + NSTG < z1) issue(i0 + NSTG, slot);
+      }
       // full tile rows of the reconstructed plane
       for (int i = tid; i < T1 * (T2 / VEC); i += NT) {
         const int ri = i / (T2 / VEC), v = i - ri * (T2 / VEC);
@@ -1701,6 +1761,7 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
       }
     }
     __syncthreads();
+    if constexpr (TMA) slot = slot + 1 == NSTG ? 0 : slot + 1;
   }
   if constexpr (STATS) {
     if (st_on) {
@@ -1728,7 +1789,33 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
 template <typename A, int DEG, bool IPR, int T1, int T2>
 __global__ void __launch_bounds__(256, 4) k_level0_march_tma(const __grid_constant__ CUtensorMap tm,
                                                              const __grid_constant__ TileArgs a, int zc) {
-  level0_march_body<A, DEG, false, IPR, T1, T2, true>(a, zc, blockIdx.x, &tm);
+  level0_march_body<A, DEG, false, IPR, T1, T2, true>(a, zc, blockIdx.x, &tm, &a.stats->timeout);
+}
+
+// a bounded wait of a retrieval kernel gave up (read and cleared by
+// read_device_timeouts)
+__device__ int g_dev_timeout = 0;
+
+// tensor maps of the three level-0 regions' staging arrays
+struct MarchMaps {
+  CUtensorMap m[3];
+};
+
+// retrieval with TMA-staged c_hat boxes (mm: regions 1, 2, 3)
+template <typename A, int DEG, bool IPR, int T1, int T2>
+__global__ void __launch_bounds__(256, 4) k_level0_march_tma_ret(const __grid_constant__ MarchMaps mm,
+                                                                 const __grid_constant__ TileArgs a, int zc) {
+  level0_march_body<A, DEG, true, IPR, T1, T2, true>(a, zc, blockIdx.x, mm.m, &g_dev_timeout);
+}
+
+int read_device_timeouts(bool clear) {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_dev_timeout, sizeof(int)) != cudaSuccess) return -1;
+  if (clear && v) {
+    const int z = 0;
+    cudaMemcpyToSymbol(g_dev_timeout, &z, sizeof(int));
+  }
+  return v;
 }
 
 // the plane-marching kernel over several fields (or fixed-point levels) in
@@ -1922,10 +2009,65 @@ static bool run_level0_march_tma(const TileArgs& a0, cudaStream_t s, int zc_forc
   return true;
 }
 
+// tensor map of one level-0 region's staging array ([count0][count1][row_pad]
+// from element `base`): boxes of w x rows x 1 values, zero fill beyond the
+// region's counts; false where the array is not 16-byte aligned or pitched
+template <typename A>
+static bool region_tensor_map(const TileRegion& g, int w, int rows, CUtensorMap& tm) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || !g.stage || g.count[0] <= 0 || g.count[1] <= 0 || g.count[2] <= 0) return false;
+  const char* base = static_cast<const char*>(g.stage) + g.base * (int64_t)sizeof(A);
+  if (((uintptr_t)base & 15) != 0 || (g.row_pad * (int64_t)sizeof(A)) % 16 != 0) return false;
+  const CUtensorMapDataType dt = std::is_same<A, float>::value    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : std::is_same<A, double>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                                                  : CU_TENSOR_MAP_DATA_TYPE_INT64;
+  const cuuint64_t gdim[3] = {(cuuint64_t)g.count[2], (cuuint64_t)g.count[1], (cuuint64_t)g.count[0]};
+  const cuuint64_t gstride[2] = {(cuuint64_t)(g.row_pad * (int64_t)sizeof(A)),
+                                 (cuuint64_t)(g.count[1] * g.row_pad * (int64_t)sizeof(A))};
+  const cuuint32_t box[3] = {(cuuint32_t)w, (cuuint32_t)rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(&tm, dt, 3, const_cast<char*>(base), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the TMA form of the retrieval: every region's staging array takes a
+// tensor map (the level-0 lattices of pass order (0, 1, 2): march_applies)
+template <typename A, int DEG, bool PR, int T1, int T2>
+static bool run_level0_march_tma_ret(const TileArgs& a0, cudaStream_t s, int zc_force) {
+  constexpr int CR = T1 / 2 + DEG, W12 = T2 / 2 + 8;
+  constexpr int R1B = (CR * W12 * (int)sizeof(A) + 127) / 128 * 128;
+  constexpr int R2B = ((T1 / 2) * W12 * (int)sizeof(A) + 127) / 128 * 128;
+  constexpr int R3B = (T1 * (T2 / 2) * (int)sizeof(A) + 127) / 128 * 128;
+  constexpr int NSTG = sizeof(A) == 4 ? 3 : 2;   // as in level0_march_body
+  constexpr int SMEM = NSTG * (R1B + R2B + R3B) + 128 + 8 * NSTG;
+  MarchMaps mm;
+  if (!region_tensor_map<A>(a0.reg[0], W12, CR, mm.m[0]) || !region_tensor_map<A>(a0.reg[1], W12, T1 / 2, mm.m[1]) ||
+      !region_tensor_map<A>(a0.reg[2], T2 / 2, T1, mm.m[2]))
+    return false;
+  TileArgs a = a0;
+  int zc = 0;
+  const int64_t nb = march_grid<T1, T2>(a, zc_force, zc);
+  if (!nb) return true;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_level0_march_tma_ret<A, DEG, PR, T1, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         SMEM);
+    cudaFuncSetAttribute(k_level0_march_tma_ret<A, DEG, PR, T1, T2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         100);
+    attr = true;
+  }
+  count_launch();
+  k_level0_march_tma_ret<A, DEG, PR, T1, T2><<<(unsigned)nb, 256, SMEM, s>>>(mm, a, zc);
+  return true;
+}
+
 template <typename A, int DEG, bool RET, bool PR, int T1, int T2>
 static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force, bool tma = false) {
   if constexpr (!RET) {
     if (tma && run_level0_march_tma<A, DEG, PR, T1, T2>(a0, s, zc_force)) return;
+  } else {
+    if (tma && run_level0_march_tma_ret<A, DEG, PR, T1, T2>(a0, s, zc_force)) return;
   }
   TileArgs a = a0;
   int zc = 0;
@@ -2004,11 +2146,11 @@ static void march_launch(const TileArgs& a, cudaStream_t s, int zc) {
   const bool tma = zc == kMarchTma;
   if (a.retrieve) {
     if (a.degree == 3) {
-      if (pr) run_level0_march<A, 3, true, true, T1, T2>(a, s, zc);
-      else run_level0_march<A, 3, true, false, T1, T2>(a, s, zc);
+      if (pr) run_level0_march<A, 3, true, true, T1, T2>(a, s, zc, tma);
+      else run_level0_march<A, 3, true, false, T1, T2>(a, s, zc, tma);
     } else {
-      if (pr) run_level0_march<A, 1, true, true, T1, T2>(a, s, zc);
-      else run_level0_march<A, 1, true, false, T1, T2>(a, s, zc);
+      if (pr) run_level0_march<A, 1, true, true, T1, T2>(a, s, zc, tma);
+      else run_level0_march<A, 1, true, false, T1, T2>(a, s, zc, tma);
     }
   } else {
     if (a.degree == 3) {

@@ -44,6 +44,7 @@ def test_every_pinned_schedule_matches_the_oracle():
             assert np.array_equal(out.cpu().numpy(), x_or), c
             table = pcr.autotune_table()
             assert all(table[k][0] == c for k in keys), (c, table)
+            assert pcr.device_status() == 0
     finally:
         pcr.autotune_table(reset=True)
 
