@@ -1813,6 +1813,11 @@ size_t vsize(int vk) { return vk == VK_F32 ? 4 : 8; }
 // ---------------------------------------------------------------------------
 // refactor
 // ---------------------------------------------------------------------------
+// the device address of a field's timeout flag (no access: pointer arithmetic)
+static int* timeout_flag(FieldStats* d_st) {
+  return d_st ? reinterpret_cast<int*>(reinterpret_cast<char*>(d_st) + offsetof(FieldStats, timeout)) : nullptr;
+}
+
 static pcr_status validate(const void* d_field, int ndim, const int64_t* dims, int dtype, const pcr_scheme* sch) {
   if (!d_field || !dims || !sch) return fail(PCR_ERR_INVALID_ARG, "null argument");
   if (ndim != 2 && ndim != 3) return fail(PCR_ERR_INVALID_ARG, "ndim must be 2 or 3");
@@ -2136,6 +2141,7 @@ static pcr_status prepare_refactor(pcr_handle* h, const void* d_field, Scratch& 
   for (int level = h->L - 2; level >= 1; level--) {
     TileArgs a = level_args(h, level, 0, (const void*)w.xc, nullptr);
     level_regions(h, level, sds, a);
+    a.err = timeout_flag(w.st);
     w.fixed.push_back(a);
   }
   if (h->decomp >= 0)
@@ -2193,6 +2199,7 @@ static void stages_level0(const std::vector<FieldWork>& ws, cudaStream_t s) {
         if (w.h->vk == vk && w.has_l0) {
           l0.push_back(w.l0);
           l0.back().stats = w.st;
+          l0.back().err = timeout_flag(w.st);
         }
       launch_tile_interp_multi(vk, l0.data(), (int)l0.size(), s);
     }

@@ -107,6 +107,9 @@ struct TileArgs {
   // taken by the plane-marching kernel as it reads the field, else by a
   // separate pass the launcher adds (null: not wanted)
   FieldStats* stats;
+  // set to 1 when a bounded device wait gives up (refactor: the field's
+  // timeout flag; null: the library's device status word)
+  int* err;
 };
 
 // items of one batched (multi-field) launch of the per-field kernels

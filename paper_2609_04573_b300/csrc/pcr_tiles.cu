@@ -1789,7 +1789,7 @@ __global__ void __launch_bounds__(256, 4) k_level0_march(TileArgs a, int zc) {
 template <typename A, int DEG, bool IPR, int T1, int T2>
 __global__ void __launch_bounds__(256, 4) k_level0_march_tma(const __grid_constant__ CUtensorMap tm,
                                                              const __grid_constant__ TileArgs a, int zc) {
-  level0_march_body<A, DEG, false, IPR, T1, T2, true>(a, zc, blockIdx.x, &tm, &a.stats->timeout);
+  level0_march_body<A, DEG, false, IPR, T1, T2, true>(a, zc, blockIdx.x, &tm, a.err);
 }
 
 // a bounded wait of a retrieval kernel gave up (read and cleared by
@@ -1805,7 +1805,7 @@ struct MarchMaps {
 template <typename A, int DEG, bool IPR, int T1, int T2>
 __global__ void __launch_bounds__(256, 4) k_level0_march_tma_ret(const __grid_constant__ MarchMaps mm,
                                                                  const __grid_constant__ TileArgs a, int zc) {
-  level0_march_body<A, DEG, true, IPR, T1, T2, true>(a, zc, blockIdx.x, mm.m, &g_dev_timeout);
+  level0_march_body<A, DEG, true, IPR, T1, T2, true>(a, zc, blockIdx.x, mm.m, a.err ? a.err : &g_dev_timeout);
 }
 
 int read_device_timeouts(bool clear) {
@@ -1984,11 +1984,11 @@ static bool march_tensor_map(const TileArgs& a, int T2, int rows, CUtensorMap& t
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// the TMA form: refactor of a level whose statistics the kernel takes (their
-// record receives a timeout), field base 16-byte aligned (march_applies)
+// the TMA form: refactor of a level with a timeout flag to report a bounded
+// wait that gives up, field base 16-byte aligned (march_applies)
 template <typename A, int DEG, bool PR, int T1, int T2>
 static bool run_level0_march_tma(const TileArgs& a0, cudaStream_t s, int zc_force) {
-  if (a0.retrieve || !a0.stats) return false;
+  if (a0.retrieve || !a0.err) return false;
   constexpr int ROWS = T1 + 2 * (DEG - 1) + 1;
   constexpr int SST = (ROWS * (T2 + 8) * (int)sizeof(A) + 127) / 128 * 128;
   constexpr int SMEM = 2 * SST + 128 + 16;
