@@ -1156,6 +1156,8 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
   __shared__ __align__(16) A Pe[PR][CEP];
   __shared__ __align__(16) A Po[RET ? 1 : T1][CO];
   __shared__ __align__(16) A ring[4][CR][CE];
+  // retrieve: the reconstructed plane, even columns of a tile row in
+  // [0, T2 / 2), odd ones in [T2 / 2, T2) (conflict-free column writes)
   __shared__ __align__(16) A Xo[RET ? T1 : 1][RET ? T2 : 4];
 
   const int m0 = (int)a.m[0], m1 = (int)a.m[1], m2 = (int)a.m[2];
@@ -1561,7 +1563,7 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
         int ci, cj, r, c;
         if (!p1pt(it, ci, cj, r, c)) continue;
         Pe[2 * ci][cj + PAD] = rs[ci][cj];
-        if (in_tile(r, c)) Xo[r - b1][c - b2] = rs[ci][cj];
+        if (in_tile(r, c)) Xo[r - b1][(c - b2) >> 1] = rs[ci][cj];
       }
       __syncthreads();
     }
@@ -1588,7 +1590,7 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
             g1[B1 + (int64_t)(r >> 1) * rp1 + (c >> 1)] = cv;
             mx1 = MX::upd(mx1, cv);
           } else {
-            Xo[r - b1][c - b2] = TAr<A>::add(W, chat1(it, ci, cj));
+            Xo[r - b1][(c - b2) >> 1] = TAr<A>::add(W, chat1(it, ci, cj));
           }
         }
         // later passes read predictions (per-level), or originals /
@@ -1639,9 +1641,6 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
             const A c0v = TAr<A>::sub(x.x, W.x), c1v = TAr<A>::sub(x.y, W.y);
             *reinterpret_cast<float2*>(g2 + B2 + (int64_t)(r >> 1) * rp2 + (c >> 1)) = make_float2(c0v, c1v);
             mx2 = MX::upd(MX::upd(mx2, c0v), c1v);
-          } else {
-            Xo[r - b1][c - b2] = TAr<A>::add(W.x, c2[2 * it]);
-            Xo[r - b1][c + 2 - b2] = TAr<A>::add(W.y, c2[2 * it + 1]);
           }
         }
         if (!IPR) *reinterpret_cast<float2*>(&Pe[pr][pc]) = W;
@@ -1666,7 +1665,7 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
             g2[B2 + (int64_t)(r >> 1) * rp2 + (c >> 1)] = cv;
             mx2 = MX::upd(mx2, cv);
           } else {
-            Xo[r - b1][c - b2] = TAr<A>::add(W, chat2(it, ri, cj));
+            Xo[r - b1][(c - b2) >> 1] = TAr<A>::add(W, chat2(it, ri, cj));
           }
         }
         if (!IPR) Pe[pr][cj + PAD] = W;
@@ -1712,8 +1711,7 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
             h0 = c3[2 * pi];
             h1v = c3[2 * pi + 1];
           }
-          Xo[ri][c - b2] = TAr<A>::add(W0, h0);
-          Xo[ri][c + 2 - b2] = TAr<A>::add(W1, h1v);
+          *reinterpret_cast<float2*>(&Xo[ri][T2 / 2 + oj]) = make_float2(TAr<A>::add(W0, h0), TAr<A>::add(W1, h1v));
         }
       }
     } else {
@@ -1737,7 +1735,7 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
           g3[B3 + (int64_t)r * rp3 + (c >> 1)] = cv;
           mx3 = MX::upd(mx3, cv);
         } else {
-          Xo[ri][c - b2] = TAr<A>::add(W, chat3(it, ri, oj));
+          Xo[ri][T2 / 2 + oj] = TAr<A>::add(W, chat3(it, ri, oj));
         }
       }
     }
@@ -1754,7 +1752,18 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
         const int r = b1 + ri, c0 = b2 + v * VEC;
         if (r >= m1) continue;
         A* gp = dst + (int64_t)i0 * s0 + (int64_t)r * s1 + c0;
-        const VecT<A, VEC> xv = *reinterpret_cast<const VecT<A, VEC>*>(&Xo[ri][v * VEC]);
+        VecT<A, VEC> xv;   // interleave the even and odd halves
+        if constexpr (VEC == 4) {
+          const float2 e = *reinterpret_cast<const float2*>(&Xo[ri][2 * v]);
+          const float2 o = *reinterpret_cast<const float2*>(&Xo[ri][T2 / 2 + 2 * v]);
+          xv.v[0] = e.x;
+          xv.v[1] = o.x;
+          xv.v[2] = e.y;
+          xv.v[3] = o.y;
+        } else {
+          xv.v[0] = Xo[ri][v];
+          xv.v[1] = Xo[ri][T2 / 2 + v];
+        }
         if (c0 + VEC <= m2) vst<A, VEC>(gp, xv);
         else
           for (int k = 0; k < VEC && c0 + k < m2; k++) gp[k] = xv.v[k];
