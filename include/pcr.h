@@ -250,11 +250,12 @@ void pcr_refactor_graph_free(pcr_refactor_graph* g);
  * PCR-internal 0 f32 / 1 f64 / 2 fixed point, retrieve 0/1, degree,
  * interpolation 0 per-level / 1 per-region, level grid lengths m0, m1, m2),
  * choice (0 general tile kernel, -1 marching with the default chunk and
- * register prefetch, -2 marching with the default chunk and the field rows
- * staged by TMA copies -- the refactor of a level whose statistics the
- * kernel takes, register prefetch elsewhere; the schedule of untuned levels
- * -- k > 0 marching with k-plane chunks), ms (the winner's time); *n_out =
- * entries in the table; reset clears it afterwards. */
+ * register prefetch, -2 marching with the default chunk and its inputs
+ * staged by TMA copies where that form applies (register prefetch
+ * elsewhere; the schedule of untuned levels), -3 the same on 16 x 64
+ * columns instead of 16 x 128 (FP32 levels; -2 for other value kinds), k > 0
+ * marching with k-plane chunks), ms (the winner's time); *n_out = entries
+ * in the table; reset clears it afterwards. */
 pcr_status pcr_autotune_enable(int enable);
 /* Device status of the current device: *timeouts = 1 when a bounded wait
  * of a retrieval kernel (TMA-staged level-0 reconstruction) gave up since
@@ -265,7 +266,7 @@ pcr_status pcr_autotune_enable(int enable);
  * refactor's own status. */
 pcr_status pcr_device_status(int* timeouts, int clear);
 /* Pin one schedule: `key` = the 7 int64 of an entry (as pcr_autotune_read
- * gives them), `choice` one of the candidates (0, 8, 16, 32, 64, -1, -2);
+ * gives them), `choice` one of the candidates (0, 8, 16, 32, 64, -1, -2, -3);
  * every later launch of that level grid uses it (a level the marching
  * kernel cannot take runs the general tile kernel whatever the choice).
  * PCR_ERR_INVALID_ARG for an unknown key field or choice. */

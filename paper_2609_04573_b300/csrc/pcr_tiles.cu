@@ -1939,6 +1939,8 @@ static void run_tile_kind(const TileArgs& a, cudaStream_t s) {
 // default plane chunking (refactor levels whose statistics it takes; the
 // register-prefetch form elsewhere)
 constexpr int kMarchTma = -2;
+// the same on 16 x 64 columns (FP32 levels; other value kinds: kMarchTma)
+constexpr int kMarchTmaNarrow = -3;
 
 // grid of the plane-marching kernel for one level: column tiles covering the
 // box (or the grid) and chunks of zc planes; returns the block count (0:
@@ -2146,13 +2148,10 @@ static bool march_applies(const TileArgs& a) {
   return true;
 }
 
-// zc > 0: chunks of zc planes; otherwise the default chunking (kMarchTma:
-// with TMA-staged field rows where that form applies)
-template <typename A>
-static void march_launch(const TileArgs& a, cudaStream_t s, int zc) {
-  constexpr int T1 = 16, T2 = sizeof(A) == 4 ? 128 : 64;
+// one level on the marching kernel with T1 x T2 columns
+template <typename A, int T1, int T2>
+static void march_launch_t(const TileArgs& a, cudaStream_t s, int zc, bool tma) {
   const bool pr = a.interp != 0;
-  const bool tma = zc == kMarchTma;
   if (a.retrieve) {
     if (a.degree == 3) {
       if (pr) run_level0_march<A, 3, true, true, T1, T2>(a, s, zc, tma);
@@ -2172,6 +2171,20 @@ static void march_launch(const TileArgs& a, cudaStream_t s, int zc) {
   }
 }
 
+// zc > 0: chunks of zc planes; otherwise the default chunking (kMarchTma:
+// with TMA-staged inputs where that form applies; kMarchTmaNarrow: the same
+// on 16 x 64 columns for FP32, whose default columns are 16 x 128)
+template <typename A>
+static void march_launch(const TileArgs& a, cudaStream_t s, int zc) {
+  if constexpr (sizeof(A) == 4) {
+    if (zc == kMarchTmaNarrow) {
+      march_launch_t<A, 16, 64>(a, s, zc, true);
+      return;
+    }
+  }
+  march_launch_t<A, 16, sizeof(A) == 4 ? 128 : 64>(a, s, zc, zc == kMarchTma || zc == kMarchTmaNarrow);
+}
+
 // ---------------------------------------------------------------------------
 // autotuner of the level-interpolation schedule
 // ---------------------------------------------------------------------------
@@ -2179,8 +2192,9 @@ static void march_launch(const TileArgs& a, cudaStream_t s, int zc) {
 // kernel, and the marching kernel's plane chunk sets its grid; all choices
 // compute the same values (same expression trees).  Choice 0 = general tile
 // kernel, -1 = marching with the default chunking, kMarchTma (-2, the
-// default) = the same with TMA-staged field rows where that form applies,
-// k > 0 = marching with chunks of k planes.  With tuning on, the first launch of an untuned (value
+// default) = the same with TMA-staged inputs where that form applies,
+// kMarchTmaNarrow (-3) = that on 16 x 64 columns (FP32), k > 0 = marching
+// with chunks of k planes.  With tuning on, the first launch of an untuned (value
 // kind, direction, degree, level grid) on a stream that is not being
 // captured times every candidate (CUDA events, the best of two runs after a
 // warm-up) and keeps the fastest; later launches, captured ones included,
@@ -2207,7 +2221,7 @@ struct TuneVal {
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune;
 std::atomic<int> g_tune_on{0};
-constexpr int kTuneCand[] = {0, 8, 16, 32, 64, -1, kMarchTma};
+constexpr int kTuneCand[] = {0, 8, 16, 32, 64, -1, kMarchTma, kMarchTmaNarrow};
 
 template <typename A>
 void run_choice(const TileArgs& a, cudaStream_t s, int choice) {
@@ -2339,7 +2353,7 @@ static void launch_multi_kind(int vk, const TileArgs* args, int n, cudaStream_t 
         ss.push_back(a.stats);
       }
       rest.push_back(a);
-    } else if (a.retrieve) {
+    } else if (a.retrieve || (c == kMarchTmaNarrow && sizeof(A) == 4)) {
       march_launch<A>(a, s, c);
     } else {
       mv[a.degree == 3][a.interp != 0].push_back(a);

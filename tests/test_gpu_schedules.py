@@ -1,9 +1,9 @@
 """Every level schedule against the oracle.
 
 The autotuner picks, per level grid, the general tile kernel or the plane-
-marching kernel with one of several plane chunks, or with TMA-staged field
-rows (-2; the refactor of level 0, register prefetch elsewhere); all of them
-must compute identical values.  The autotune test checks only the schedule that won, so
+marching kernel with one of several plane chunks, or with TMA-staged
+inputs (-2; -3 on 16 x 64 columns for FP32; register prefetch where the TMA
+form does not apply); all of them must compute identical values.  The autotune test checks only the schedule that won, so
 here each candidate is pinned in turn (pcr_autotune_set) for level 0 (FP32)
 and level 1 (fixed point), in both directions, and the refactored streams
 and the retrieved field are compared with the oracle bit for bit.
@@ -14,7 +14,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-CHOICES = (0, 8, 16, 32, 64, -1, -2)
+CHOICES = (0, 8, 16, 32, 64, -1, -2, -3)
 
 
 def test_every_pinned_schedule_matches_the_oracle():
