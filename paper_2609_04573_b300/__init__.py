@@ -12,6 +12,7 @@ tables (Sec. V-C), bound-driven retrieval (Sec. III-A, Alg. 2).
 """
 import ctypes as C
 import os
+import sys
 from dataclasses import dataclass, field
 from typing import Optional, Sequence, Tuple
 
@@ -201,7 +202,9 @@ def _torch_alloc(ctx, nbytes, stream):
 
 
 def _torch_free(ctx, ptr, stream):
-    if ptr:
+    # at interpreter exit torch's allocator may already be gone: the process
+    # releases the memory anyway
+    if ptr and not sys.is_finalizing():
         torch.cuda.caching_allocator_delete(ptr)
 
 
@@ -327,6 +330,10 @@ class Handle:
         self._alloc = allocator   # a caller's allocator frees the handle's memory: keep it alive
 
     def __del__(self):
+        # nothing is freed while the interpreter exits (the allocator
+        # callbacks would run into a half torn-down torch)
+        if sys.is_finalizing():
+            return
         if getattr(self, "_owner", None) is None and getattr(self, "_p", None) and self._p.value:
             _lib.pcr_free(self._p)
             self._p = C.c_void_p(None)
@@ -596,6 +603,8 @@ class RefactorJob:
         return Handle(out.value, x.shape, x.dtype, x.device)
 
     def __del__(self):
+        if sys.is_finalizing():
+            return
         if getattr(self, "_p", None) and self._p.value:
             _lib.pcr_refactor_job_free(self._p)
             self._p = C.c_void_p(None)
@@ -688,6 +697,8 @@ class RefactorGraph:
         return {"gpu_ms": g.value, "host_ms": h.value}
 
     def __del__(self):
+        if sys.is_finalizing():
+            return
         if getattr(self, "_g", None) and self._g.value:
             _lib.pcr_refactor_graph_free(self._g)
             self._g = C.c_void_p(None)

@@ -1843,6 +1843,26 @@ __global__ void __launch_bounds__(256, 4) k_level0_march_multi(const __grid_cons
   level0_march_body<A, DEG, RET, IPR, T1, T2>(b.args[i], b.zc[i], blockIdx.x - (unsigned)b.first[i]);
 }
 
+// the TMA-staged refactor over several fields (or fixed-point levels) in one
+// launch: item i owns blocks first[i] .. first[i + 1] - 1 and reads its
+// field through tm[i]
+constexpr int kMaxMarchTmaBatch = 40;
+struct MarchTmaBatch {
+  CUtensorMap tm[kMaxMarchTmaBatch];
+  int n;
+  int64_t first[kMaxMarchTmaBatch + 1];
+  int zc[kMaxMarchTmaBatch];
+  TileArgs args[kMaxMarchTmaBatch];
+};
+static_assert(sizeof(MarchTmaBatch) <= 32764, "kernel parameter block");
+
+template <typename A, int DEG, bool IPR, int T1, int T2>
+__global__ void __launch_bounds__(256, 4) k_level0_march_tma_multi(const __grid_constant__ MarchTmaBatch b) {
+  const int i = batch_find(b.first, b.n);
+  level0_march_body<A, DEG, false, IPR, T1, T2, true>(b.args[i], b.zc[i], blockIdx.x - (unsigned)b.first[i], &b.tm[i],
+                                                      b.args[i].err);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -2093,6 +2113,52 @@ static void run_level0_march(const TileArgs& a0, cudaStream_t s, int zc_force, b
   k_level0_march<A, DEG, RET, PR, T1, T2><<<(unsigned)nb, 256, 0, s>>>(a, zc);
 }
 
+template <typename A, int DEG, bool RET, bool PR, int T1, int T2>
+static void run_level0_march_multi_reg(const std::vector<TileArgs>& v, const std::vector<int>& zcs, cudaStream_t s);
+
+// the TMA-staged refactor of several levels in shared launches: items whose
+// schedule is kMarchTma, with a timeout flag and a tensor map the driver
+// accepts; the others are returned in (rest, rest_zc)
+template <typename A, int DEG, bool PR, int T1, int T2>
+static void run_level0_march_tma_multi(const std::vector<TileArgs>& v, const std::vector<int>& zcs, cudaStream_t s,
+                                       std::vector<TileArgs>& rest, std::vector<int>& rest_zc) {
+  constexpr int ROWS = T1 + 2 * (DEG - 1) + 1;
+  constexpr int SST = (ROWS * (T2 + 8) * (int)sizeof(A) + 127) / 128 * 128;
+  constexpr int SMEM = 2 * SST + 128 + 16;
+  static bool attr = false;
+  size_t k = 0;
+  while (k < v.size()) {
+    MarchTmaBatch b{};
+    int64_t tot = 0;
+    for (; k < v.size() && b.n < kMaxMarchTmaBatch; k++) {
+      TileArgs a = v[k];
+      if (zcs[k] != kMarchTma || a.retrieve || !a.err || !march_tensor_map<A>(a, T2, ROWS, b.tm[b.n])) {
+        rest.push_back(v[k]);
+        rest_zc.push_back(zcs[k]);
+        continue;
+      }
+      int zc = 0;
+      const int64_t nb = march_grid<T1, T2>(a, zcs[k], zc);
+      if (!nb) continue;
+      b.first[b.n] = tot;
+      b.zc[b.n] = zc;
+      b.args[b.n++] = a;
+      tot += nb;
+    }
+    b.first[b.n] = tot;
+    if (!tot) continue;
+    if (!attr) {
+      cudaFuncSetAttribute(k_level0_march_tma_multi<A, DEG, PR, T1, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           SMEM);
+      cudaFuncSetAttribute(k_level0_march_tma_multi<A, DEG, PR, T1, T2>,
+                           cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      attr = true;
+    }
+    count_launch();
+    k_level0_march_tma_multi<A, DEG, PR, T1, T2><<<(unsigned)tot, 256, SMEM, s>>>(b);
+  }
+}
+
 // levels of one marching-kernel shape (value kind, degree, direction,
 // interpolation) in shared launches; zcs[i]: the plane chunk of item i
 // (<= 0: the default); a single item takes the one-level kernel
@@ -2102,6 +2168,22 @@ static void run_level0_march_multi(const std::vector<TileArgs>& v, const std::ve
     run_level0_march<A, DEG, RET, PR, T1, T2>(v[0], s, zcs[0], zcs[0] == kMarchTma);
     return;
   }
+  if constexpr (!RET) {   // the TMA form for the items whose schedule and arrays take it
+    std::vector<TileArgs> rv;
+    std::vector<int> rz;
+    run_level0_march_tma_multi<A, DEG, PR, T1, T2>(v, zcs, s, rv, rz);
+    if (rv.size() < v.size()) {
+      if (rv.size() == 1) run_level0_march<A, DEG, RET, PR, T1, T2>(rv[0], s, rz[0], false);
+      else if (!rv.empty()) run_level0_march_multi_reg<A, DEG, RET, PR, T1, T2>(rv, rz, s);
+      return;
+    }
+  }
+  run_level0_march_multi_reg<A, DEG, RET, PR, T1, T2>(v, zcs, s);
+}
+
+// the register-prefetch form of several levels in shared launches
+template <typename A, int DEG, bool RET, bool PR, int T1, int T2>
+static void run_level0_march_multi_reg(const std::vector<TileArgs>& v, const std::vector<int>& zcs, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_level0_march_multi<A, DEG, RET, PR, T1, T2>, cudaFuncAttributePreferredSharedMemoryCarveout,

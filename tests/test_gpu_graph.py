@@ -82,4 +82,4 @@ def test_autotuned_levels_match_the_oracle():
     kinds = {(k[0], k[1]) for k in table}
     assert {(0, 0), (0, 1), (2, 0), (2, 1)} <= kinds, table
     for (choice, ms) in table.values():
-        assert choice in (0, 8, 16, 32, 64, -1) and ms >= 0
+        assert choice in (0, 8, 16, 32, 64, -1, -2, -3) and ms >= 0
