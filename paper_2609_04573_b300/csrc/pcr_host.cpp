@@ -2,6 +2,7 @@
 // error tables, bound composition, max ordering, the greedy planner, the
 // container and the C ABI (include/pcr.h).  Section references are to
 // arXiv 2609.04573 (ProAICD).
+#include <new>
 #include <queue>
 #include <cuda_runtime.h>
 
@@ -142,15 +143,19 @@ struct Prof {
 };
 }  // namespace
 
-extern "C" pcr_status pcr_profile_enable(int enable) {
+extern "C" pcr_status pcr_profile_enable(int enable) try {
   g_prof_on = enable != 0;
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 extern "C" int64_t pcr_launch_count(void) { return launch_count(); }
 
 extern "C" pcr_status pcr_profile_read(int max_entries, char* names, double* ms, int64_t* launches, int* n_out,
-                                       int reset) {
+                                       int reset) try {
   if (!n_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   std::lock_guard<std::mutex> g(g_prof_mu);
   for (auto& r : g_prof_recs) {
@@ -175,6 +180,10 @@ extern "C" pcr_status pcr_profile_read(int max_entries, char* names, double* ms,
   *n_out = k;
   if (reset) g_prof_tot.clear();
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // ---------------------------------------------------------------------------
@@ -2628,12 +2637,23 @@ static pcr_status parallel_for(int n, F f) {
   std::atomic<int> next{0};
   auto work = [&]() {
     for (int k; (k = next.fetch_add(1)) < n;) {
-      st[k] = f(k);
-      if (st[k]) msg[k] = g_err;   // this thread's message
+      try {   // nothing thrown may leave a worker thread
+        st[k] = f(k);
+        if (st[k]) msg[k] = g_err;   // this thread's message
+      } catch (const std::bad_alloc&) {
+        st[k] = PCR_ERR_OOM;
+        msg[k] = "host allocation failed";
+      } catch (...) {
+        st[k] = PCR_ERR_INVALID_ARG;
+        msg[k] = "unexpected host error";
+      }
     }
   };
   std::vector<std::thread> th;
-  for (int t = 1; t < nt; t++) th.emplace_back(work);
+  try {
+    for (int t = 1; t < nt; t++) th.emplace_back(work);
+  } catch (...) {   // fewer threads: this one takes the rest
+  }
   work();
   for (auto& t : th) t.join();
   for (int k = 0; k < n; k++)
@@ -2727,7 +2747,7 @@ struct ScratchBlock {
 
 extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, const int* ndims,
                                          const int64_t* const* dims, const int* dtypes, const pcr_scheme* schemes,
-                                         const pcr_allocator* alloc, void* cuda_stream, pcr_handle** outs) {
+                                         const pcr_allocator* alloc, void* cuda_stream, pcr_handle** outs) try {
   if (n <= 0 || !d_fields || !ndims || !dims || !dtypes || !schemes || !outs)
     return fail(PCR_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -2756,6 +2776,10 @@ extern "C" pcr_status pcr_refactor_batch(int n, const void* const* d_fields, con
   if (e) return e;
   for (int k = 0; k < n; k++) outs[k] = own[k].release();
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // ---------------------------------------------------------------------------
@@ -2817,7 +2841,7 @@ struct pcr_refactor_job {
 
 extern "C" pcr_status pcr_refactor_begin(const void* d_field, int ndim, const int64_t* dims, int dtype,
                                          const pcr_scheme* scheme, const pcr_allocator* alloc, void* cuda_stream,
-                                         pcr_refactor_job** out) {
+                                         pcr_refactor_job** out) try {
   if (!out || !d_field || !dims || !scheme) return fail(PCR_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   std::unique_ptr<pcr_refactor_job> j(new pcr_refactor_job());
@@ -2863,9 +2887,13 @@ extern "C" pcr_status pcr_refactor_begin(const void* d_field, int ndim, const in
   CUDA_TRY(cudaEventRecord(j->done, j->s));
   *out = j.release();
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
-extern "C" pcr_status pcr_refactor_end(pcr_refactor_job* job, pcr_handle** out) {
+extern "C" pcr_status pcr_refactor_end(pcr_refactor_job* job, pcr_handle** out) try {
   if (!job || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   std::unique_ptr<pcr_refactor_job> j(job);   // consumed, whatever the outcome
@@ -2874,6 +2902,10 @@ extern "C" pcr_status pcr_refactor_end(pcr_refactor_job* job, pcr_handle** out) 
   if (e) return e;
   *out = j->own.release();
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 extern "C" void pcr_refactor_job_free(pcr_refactor_job* job) { delete job; }
@@ -2914,7 +2946,7 @@ struct pcr_refactor_graph {
 extern "C" pcr_status pcr_refactor_graph_create(int n, const void* const* d_fields, const int* ndims,
                                                 const int64_t* const* dims, const int* dtypes,
                                                 const pcr_scheme* schemes, const pcr_allocator* alloc,
-                                                void* cuda_stream, pcr_refactor_graph** out) {
+                                                void* cuda_stream, pcr_refactor_graph** out) try {
   if (n <= 0 || !d_fields || !ndims || !dims || !dtypes || !schemes || !out)
     return fail(PCR_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
@@ -3000,9 +3032,13 @@ extern "C" pcr_status pcr_refactor_graph_create(int n, const void* const* d_fiel
   CUDA_TRY(cudaGraphInstantiate(&g->exec, g->graph, 0));
   *out = g.release();
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
-extern "C" pcr_status pcr_refactor_graph_run(pcr_refactor_graph* g, void* cuda_stream) {
+extern "C" pcr_status pcr_refactor_graph_run(pcr_refactor_graph* g, void* cuda_stream) try {
   if (!g) return fail(PCR_ERR_INVALID_ARG, "null graph");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   for (cudaEvent_t& e : g->ev)
@@ -3019,68 +3055,104 @@ extern "C" pcr_status pcr_refactor_graph_run(pcr_refactor_graph* g, void* cuda_s
   const pcr_status e = finish_batch(g->hs, *g->layout, g->io);
   g->host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return e;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
-extern "C" pcr_status pcr_refactor_graph_times(const pcr_refactor_graph* g, double* gpu_ms, double* host_ms) {
+extern "C" pcr_status pcr_refactor_graph_times(const pcr_refactor_graph* g, double* gpu_ms, double* host_ms) try {
   if (!g) return fail(PCR_ERR_INVALID_ARG, "null graph");
   if (gpu_ms) *gpu_ms = g->gpu_ms;
   if (host_ms) *host_ms = g->host_ms;
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
-extern "C" pcr_status pcr_refactor_graph_handle(const pcr_refactor_graph* g, int k, const pcr_handle** out) {
+extern "C" pcr_status pcr_refactor_graph_handle(const pcr_refactor_graph* g, int k, const pcr_handle** out) try {
   if (!g || !out || k < 0 || k >= (int)g->hs.size()) return fail(PCR_ERR_INVALID_ARG, "bad graph or index");
   *out = g->hs[k];
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 extern "C" pcr_status pcr_refactor_graph_info(const pcr_refactor_graph* g, int64_t* nodes, int64_t* kernels,
-                                              int64_t* arena_bytes) {
+                                              int64_t* arena_bytes) try {
   if (!g) return fail(PCR_ERR_INVALID_ARG, "null graph");
   if (nodes) *nodes = (int64_t)g->nodes;
   if (kernels) *kernels = g->kernels;
   if (arena_bytes) *arena_bytes = (int64_t)g->arena_bytes;
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 extern "C" void pcr_refactor_graph_free(pcr_refactor_graph* g) { delete g; }
 
-extern "C" pcr_status pcr_device_status(int* timeouts, int clear) {
+extern "C" pcr_status pcr_device_status(int* timeouts, int clear) try {
   if (!timeouts) return fail(PCR_ERR_INVALID_ARG, "null argument");
   const int v = read_device_timeouts(clear != 0);
   if (v < 0) return fail(PCR_ERR_CUDA, "reading the device status failed");
   *timeouts = v;
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
-extern "C" pcr_status pcr_autotune_enable(int enable) {
+extern "C" pcr_status pcr_autotune_enable(int enable) try {
   set_autotune(enable);
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
-extern "C" pcr_status pcr_autotune_set(const int64_t* key, int choice) {
+extern "C" pcr_status pcr_autotune_set(const int64_t* key, int choice) try {
   if (!key) return fail(PCR_ERR_INVALID_ARG, "null key");
   if (!autotune_pin(key, choice)) return fail(PCR_ERR_INVALID_ARG, "unknown key field or schedule choice");
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 extern "C" pcr_status pcr_autotune_read(int max_entries, int64_t* keys, int* choice, double* ms, int* n_out,
-                                        int reset) {
+                                        int reset) try {
   if (!n_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   *n_out = autotune_entries(max_entries, keys, choice, ms);
   if (reset) clear_autotune();
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 extern "C" pcr_status pcr_refactor(const void* d_field, int ndim, const int64_t* dims, int dtype,
                                    const pcr_scheme* scheme, const pcr_allocator* alloc, void* cuda_stream,
-                                   pcr_handle** out) {
+                                   pcr_handle** out) try {
   if (!out) return fail(PCR_ERR_INVALID_ARG, "null output");
   const void* f[1] = {d_field};
   const int nd[1] = {ndim};
   const int64_t* dm[1] = {dims};
   const int dt[1] = {dtype};
   return pcr_refactor_batch(1, f, nd, dm, dt, scheme, alloc, cuda_stream, out);
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // ---------------------------------------------------------------------------
@@ -3236,7 +3308,7 @@ static bool greedy_l2_global(std::vector<BlockPlan>& bp, double budget, double& 
 }
 
 extern "C" pcr_status pcr_plan_global(int n, const pcr_handle* const* hs, const pcr_target* t,
-                                      pcr_retrieval_plan* plans, double* bound, int* satisfied) {
+                                      pcr_retrieval_plan* plans, double* bound, int* satisfied) try {
   if (n <= 0 || !hs || !t || !plans) return fail(PCR_ERR_INVALID_ARG, "null argument");
   for (int k = 0; k < n; k++)
     if (!hs[k]) return fail(PCR_ERR_INVALID_ARG, "null handle");
@@ -3286,15 +3358,23 @@ extern "C" pcr_status pcr_plan_global(int n, const pcr_handle* const* hs, const 
   if (satisfied) *satisfied = ok ? 1 : 0;
   if (!ok) return fail(PCR_ERR_UNSATISFIABLE, "target tighter than the all-planes bound of some block");
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
-extern "C" pcr_status pcr_plan(const pcr_handle* h, const pcr_target* t, pcr_retrieval_plan* out) {
+extern "C" pcr_status pcr_plan(const pcr_handle* h, const pcr_target* t, pcr_retrieval_plan* out) try {
   if (!h || !t || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   return plan_impl(h, t, nullptr, out);
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 extern "C" pcr_status pcr_plan_more(const pcr_handle* h, const pcr_target* t, const pcr_retrieval_plan* have,
-                                    pcr_retrieval_plan* out) {
+                                    pcr_retrieval_plan* out) try {
   if (!h || !t || !have || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   const int ns = (int)h->tabs.size();
   if (have->nstreams != ns) return fail(PCR_ERR_INVALID_ARG, "plan does not match the handle");
@@ -3304,10 +3384,14 @@ extern "C" pcr_status pcr_plan_more(const pcr_handle* h, const pcr_target* t, co
     hv[i] = have->planes[i];
   }
   return plan_impl(h, t, &hv, out);
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 extern "C" pcr_status pcr_plan_search(const pcr_handle* h, const pcr_target* t, const pcr_retrieval_plan* have,
-                                      int64_t max_nodes, pcr_retrieval_plan* out, pcr_search_info* info) {
+                                      int64_t max_nodes, pcr_retrieval_plan* out, pcr_search_info* info) try {
   if (!h || !t || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   if (max_nodes < 0) return fail(PCR_ERR_INVALID_ARG, "max_nodes must be >= 0");
   const int ns = (int)h->tabs.size();
@@ -3331,6 +3415,10 @@ extern "C" pcr_status pcr_plan_search(const pcr_handle* h, const pcr_target* t, 
     info->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return st;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // ---------------------------------------------------------------------------
@@ -3684,7 +3772,7 @@ static pcr_status enqueue_reconstruct_box(const pcr_handle* h, const std::vector
 }
 
 extern "C" pcr_status pcr_retrieve_box(const pcr_handle* h, const pcr_retrieval_plan* plan, const int64_t* lo,
-                                       const int64_t* hi, void* d_out, void* cuda_stream) {
+                                       const int64_t* hi, void* d_out, void* cuda_stream) try {
   if (!h || !plan || !lo || !hi || !d_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   if (!h->d_block) return fail(PCR_ERR_UNSUPPORTED, "a planning-only handle holds no planes");
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -3751,12 +3839,16 @@ extern "C" pcr_status pcr_retrieve_box(const pcr_handle* h, const pcr_retrieval_
   }
   CUDA_TRY(cudaGetLastError());
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 static size_t retrieve_scratch_bytes(const pcr_handle* h);
 
 extern "C" pcr_status pcr_retrieve_batch_plan(int n, const pcr_handle* const* hs, const pcr_retrieval_plan* plans,
-                                              void* const* d_outs, void* cuda_stream) {
+                                              void* const* d_outs, void* cuda_stream) try {
   if (n <= 0 || !hs || !plans || !d_outs) return fail(PCR_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   for (int k = 0; k < n; k++)
@@ -3768,6 +3860,10 @@ extern "C" pcr_status pcr_retrieve_batch_plan(int n, const pcr_handle* const* hs
   ScratchBlock blk(&mem, s, need, sc);
   if (!blk.p) return fail(PCR_ERR_OOM, "scratch allocation failed");
   return retrieve_batch_impl(n, hs, plans, d_outs, s, sc);
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // bytes of temporary device memory one retrieval of `h` uses (upper bound,
@@ -3794,16 +3890,20 @@ static size_t retrieve_scratch_bytes(const pcr_handle* h) {
   return t + 256;
 }
 
-extern "C" pcr_status pcr_retrieve_scratch_bytes(const pcr_handle* h, size_t* bytes) {
+extern "C" pcr_status pcr_retrieve_scratch_bytes(const pcr_handle* h, size_t* bytes) try {
   if (!h || !bytes) return fail(PCR_ERR_INVALID_ARG, "null argument");
   *bytes = retrieve_scratch_bytes(h);
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // Retrieval whose temporary buffers live in the library's fixed device array
 // (pcr_static.cu); see pcr_retrieve_static in include/pcr.h.
 extern "C" pcr_status pcr_retrieve_static(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out,
-                                          void* cuda_stream) {
+                                          void* cuda_stream) try {
   if (!h || !plan || !d_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   // the scratch array is per device: it must be the one holding the handle
@@ -3831,12 +3931,20 @@ extern "C" pcr_status pcr_retrieve_static(const pcr_handle* h, const pcr_retriev
   sc.bump = base;
   sc.cap = cap;
   return retrieve_batch_impl(1, &h, plan, &d_out, s, sc, false);
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 extern "C" pcr_status pcr_retrieve_plan(const pcr_handle* h, const pcr_retrieval_plan* plan, void* d_out,
-                                        void* cuda_stream) {
+                                        void* cuda_stream) try {
   if (!h || !plan || !d_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   return pcr_retrieve_batch_plan(1, &h, plan, &d_out, cuda_stream);
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // ---------------------------------------------------------------------------
@@ -3872,7 +3980,7 @@ void fill_info(const pcr_handle* h, const pcr_target* t, const pcr_retrieval_pla
 }  // namespace
 
 extern "C" pcr_status pcr_retrieve(const pcr_handle* h, const pcr_target* target, void* d_out, void* cuda_stream,
-                                   pcr_retrieval_info* info) {
+                                   pcr_retrieval_info* info) try {
   if (!h || !target || !d_out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   if (target->has_box) {
     for (int k = 0; k < h->ndim; k++)
@@ -3910,10 +4018,14 @@ extern "C" pcr_status pcr_retrieve(const pcr_handle* h, const pcr_target* target
       return fail(PCR_ERR_TIMEOUT, "a device wait of the retrieval gave up");
   }
   return st;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 extern "C" pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, const pcr_target* targets,
-                                         void* const* d_outs, void* cuda_stream, pcr_retrieval_info* infos) {
+                                         void* const* d_outs, void* cuda_stream, pcr_retrieval_info* infos) try {
   if (n <= 0 || !hs || !targets || !d_outs) return fail(PCR_ERR_INVALID_ARG, "null argument");
   std::vector<pcr_retrieval_plan> plans(n);
   for (int k = 0; k < n; k++) {
@@ -3934,12 +4046,16 @@ extern "C" pcr_status pcr_retrieve_batch(int n, const pcr_handle* const* hs, con
     for (int k = 0; k < n; k++) infos[k].enqueue_ms = e;
   }
   return st;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // ---------------------------------------------------------------------------
 // error tables of every stream (Sec. V-C)
 // ---------------------------------------------------------------------------
-extern "C" pcr_status pcr_get_tables(const pcr_handle* h, pcr_tables* out) {
+extern "C" pcr_status pcr_get_tables(const pcr_handle* h, pcr_tables* out) try {
   if (!h || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   const int ns = (int)h->geo.size();
   out->nstreams = ns;
@@ -3955,18 +4071,26 @@ extern "C" pcr_status pcr_get_tables(const pcr_handle* h, pcr_tables* out) {
     }
   }
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // ---------------------------------------------------------------------------
 // introspection
 // ---------------------------------------------------------------------------
-extern "C" pcr_status pcr_num_streams(const pcr_handle* h, int* n) {
+extern "C" pcr_status pcr_num_streams(const pcr_handle* h, int* n) try {
   if (!h || !n) return fail(PCR_ERR_INVALID_ARG, "null argument");
   *n = (int)h->geo.size();
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
-extern "C" pcr_status pcr_stream_info_get(const pcr_handle* h, int i, pcr_stream_info* o) {
+extern "C" pcr_status pcr_stream_info_get(const pcr_handle* h, int i, pcr_stream_info* o) try {
   if (!h || !o || i < 0 || i >= (int)h->geo.size()) return fail(PCR_ERR_INVALID_ARG, "bad stream index");
   const SGeo& g = h->geo[i];
   o->level = g.level;
@@ -3982,9 +4106,13 @@ extern "C" pcr_status pcr_stream_info_get(const pcr_handle* h, int i, pcr_stream
   o->shift = h->sh[i];
   o->vmax = h->vmax[i];
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
-extern "C" pcr_status pcr_stream_tables(const pcr_handle* h, int i, double* maxerr, double* sq, uint64_t* bytes) {
+extern "C" pcr_status pcr_stream_tables(const pcr_handle* h, int i, double* maxerr, double* sq, uint64_t* bytes) try {
   if (!h || i < 0 || i >= (int)h->geo.size()) return fail(PCR_ERR_INVALID_ARG, "bad stream index");
   const Tab& t = h->tabs[i];
   for (int b = 0; b <= h->B; b++) {
@@ -3993,18 +4121,26 @@ extern "C" pcr_status pcr_stream_tables(const pcr_handle* h, int i, double* maxe
     if (bytes) bytes[b] = t.bytes[b];
   }
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
-extern "C" pcr_status pcr_field_stats(const pcr_handle* h, double* xmin, double* xmax, int* G) {
+extern "C" pcr_status pcr_field_stats(const pcr_handle* h, double* xmin, double* xmax, int* G) try {
   if (!h) return fail(PCR_ERR_INVALID_ARG, "null handle");
   if (xmin) *xmin = h->xmin;
   if (xmax) *xmax = h->xmax;
   if (G) *G = h->G;
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 extern "C" pcr_status pcr_stream_copy(const pcr_handle* h, int i, uint32_t* planes_host, uint32_t* signs_host,
-                                      uint32_t* sign_counts_host, uint64_t* pairs_host) {
+                                      uint32_t* sign_counts_host, uint64_t* pairs_host) try {
   if (!h || i < 0 || i >= (int)h->geo.size()) return fail(PCR_ERR_INVALID_ARG, "bad stream index");
   if (!h->d_block) return fail(PCR_ERR_UNSUPPORTED, "a planning-only handle holds no planes");
   const int64_t words = h->geo[i].n_pad() / 32;
@@ -4016,9 +4152,13 @@ extern "C" pcr_status pcr_stream_copy(const pcr_handle* h, int i, uint32_t* plan
     CUDA_TRY(cudaMemcpy(sign_counts_host, h->d_scnt + h->scnt_off[i], (size_t)nseg * h->B * 4, cudaMemcpyDeviceToHost));
   if (pairs_host && !h->pairs[i].empty()) std::memcpy(pairs_host, h->pairs[i].data(), h->pairs[i].size() * 8);
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
-extern "C" pcr_status pcr_max_ordering(const pcr_handle* h, double* errs, int* n) {
+extern "C" pcr_status pcr_max_ordering(const pcr_handle* h, double* errs, int* n) try {
   if (!h || !n) return fail(PCR_ERR_INVALID_ARG, "null argument");
   if (!h->has_m0) {
     *n = 0;
@@ -4030,6 +4170,10 @@ extern "C" pcr_status pcr_max_ordering(const pcr_handle* h, double* errs, int* n
     for (size_t k = 0; k < h->m0.size(); k++) errs[k + 1] = h->m0[k].val;
   }
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 extern "C" void pcr_free(pcr_handle* h) { delete h; }
@@ -4126,7 +4270,7 @@ static pcr_status write_header(const pcr_handle* h, Writer& hd) {
   return PCR_OK;
 }
 
-extern "C" pcr_status pcr_serialize(const pcr_handle* h, void** buf, size_t* len) {
+extern "C" pcr_status pcr_serialize(const pcr_handle* h, void** buf, size_t* len) try {
   if (!h || !buf || !len) return fail(PCR_ERR_INVALID_ARG, "null argument");
   if (!h->d_block) return fail(PCR_ERR_UNSUPPORTED, "a planning-only handle holds no planes");
   Writer w;
@@ -4154,6 +4298,10 @@ extern "C" pcr_status pcr_serialize(const pcr_handle* h, void** buf, size_t* len
   *buf = out;
   *len = w.buf.size();
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 static pcr_status read_header(Reader& hr, pcr_handle* h, std::vector<std::vector<uint32_t>>& scnts) {
@@ -4206,7 +4354,7 @@ static pcr_status read_header(Reader& hr, pcr_handle* h, std::vector<std::vector
 static void pack_tasks(const pcr_handle* h, uint32_t* planes, std::vector<PackTask>& tasks);
 
 extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_allocator* alloc, void* cuda_stream,
-                                      pcr_handle** out) {
+                                      pcr_handle** out) try {
   if (!buf || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   Reader r{(const uint8_t*)buf, len};
@@ -4310,6 +4458,10 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
   build_meta(h.get());
   *out = h.release();
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // ---------------------------------------------------------------------------
@@ -4318,7 +4470,7 @@ extern "C" pcr_status pcr_deserialize(const void* buf, size_t len, const pcr_all
 // ---------------------------------------------------------------------------
 const uint64_t kPlanMagic = 0x3230534C50ull;  // "PLS02"
 
-extern "C" pcr_status pcr_export_plan_state(const pcr_handle* h, void** buf, size_t* len) {
+extern "C" pcr_status pcr_export_plan_state(const pcr_handle* h, void** buf, size_t* len) try {
   if (!h || !buf || !len) return fail(PCR_ERR_INVALID_ARG, "null argument");
   if (!h->d_block) return fail(PCR_ERR_UNSUPPORTED, "a planning-only handle is exported by its owner");
   Writer w;
@@ -4335,9 +4487,13 @@ extern "C" pcr_status pcr_export_plan_state(const pcr_handle* h, void** buf, siz
   *buf = out;
   *len = w.buf.size();
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
-extern "C" pcr_status pcr_import_plan_state(const void* buf, size_t len, pcr_handle** out) {
+extern "C" pcr_status pcr_import_plan_state(const void* buf, size_t len, pcr_handle** out) try {
   if (!buf || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   Reader r{(const uint8_t*)buf, len};
@@ -4358,6 +4514,10 @@ extern "C" pcr_status pcr_import_plan_state(const void* buf, size_t len, pcr_han
   build_meta(h.get());
   *out = h.release();
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // ---------------------------------------------------------------------------
@@ -4400,7 +4560,7 @@ static pcr_status pack_headers(const pcr_handle* h, const std::vector<PackTask>&
   return PCR_OK;
 }
 
-extern "C" pcr_status pcr_packed_tables(const pcr_handle* h, uint64_t* bytes) {
+extern "C" pcr_status pcr_packed_tables(const pcr_handle* h, uint64_t* bytes) try {
   if (!h || !bytes) return fail(PCR_ERR_INVALID_ARG, "null argument");
   if (!h->d_block) return fail(PCR_ERR_UNSUPPORTED, "a planning-only handle holds no planes");
   const int ns = (int)h->geo.size();
@@ -4436,12 +4596,16 @@ extern "C" pcr_status pcr_packed_tables(const pcr_handle* h, uint64_t* bytes) {
     }
   }
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // test entry: the coded form of one segment's plane words (at most 128
 // words in device memory): header and payload words (payload: room for 128)
 extern "C" pcr_status pcr_debug_pack(const uint32_t* d_words, int nwords, uint32_t* header, uint32_t* payload,
-                                     int* npayload) {
+                                     int* npayload) try {
   if (!d_words || !header || !payload || !npayload || nwords < 1 || nwords > kSegWords)
     return fail(PCR_ERR_INVALID_ARG, "bad argument");
   const PackTask tk{const_cast<uint32_t*>(d_words), nwords, 0};
@@ -4478,9 +4642,13 @@ extern "C" pcr_status pcr_debug_pack(const uint32_t* d_words, int nwords, uint32
   if (ce != cudaSuccess) return fail(PCR_ERR_CUDA, cudaGetErrorString(ce));
   *npayload = (int)pw;
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
-extern "C" pcr_status pcr_serialize_packed(const pcr_handle* h, void** buf, size_t* len) {
+extern "C" pcr_status pcr_serialize_packed(const pcr_handle* h, void** buf, size_t* len) try {
   if (!h || !buf || !len) return fail(PCR_ERR_INVALID_ARG, "null argument");
   if (!h->d_block) return fail(PCR_ERR_UNSUPPORTED, "a planning-only handle holds no planes");
   Writer w;
@@ -4534,6 +4702,10 @@ extern "C" pcr_status pcr_serialize_packed(const pcr_handle* h, void** buf, size
   *buf = out;
   *len = w.buf.size();
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // ---------------------------------------------------------------------------
@@ -4627,7 +4799,7 @@ double key_to_double(unsigned long long k) {
 
 extern "C" pcr_status pcr_tune(const void* d_field, int ndim, const int64_t* dims, int dtype, int mode, double fraction,
                                int edge, const pcr_allocator* alloc, void* cuda_stream, pcr_scheme* out,
-                               pcr_tune_info* info) {
+                               pcr_tune_info* info) try {
   const auto t0 = std::chrono::steady_clock::now();
   if (!d_field || !dims || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   if (ndim != 2 && ndim != 3) return fail(PCR_ERR_INVALID_ARG, "ndim must be 2 or 3");
@@ -4737,6 +4909,10 @@ extern "C" pcr_status pcr_tune(const void* d_field, int ndim, const int64_t* dim
     info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // Schemes whose interp is PCR_INTERP_AUTO are replaced by the tuner's choice
@@ -4760,10 +4936,14 @@ static pcr_status resolve_auto(int n, const void* const* d_fields, const int* nd
   return PCR_OK;
 }
 
-extern "C" pcr_status pcr_get_scheme(const pcr_handle* h, pcr_scheme* out) {
+extern "C" pcr_status pcr_get_scheme(const pcr_handle* h, pcr_scheme* out) try {
   if (!h || !out) return fail(PCR_ERR_INVALID_ARG, "null argument");
   *out = h->sch;
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
 
 // ---------------------------------------------------------------------------
@@ -4772,7 +4952,7 @@ extern "C" pcr_status pcr_get_scheme(const pcr_handle* h, pcr_scheme* out) {
 extern "C" pcr_status pcr_debug_encode(const void* d_vals, int64_t n_pad, int value_kind, int B, int encoding,
                                        int want_pairs, void* cuda_stream, uint32_t* planes_host,
                                        uint32_t* signs_host, uint32_t* sign_counts_host, uint32_t* plane_nz_host,
-                                       uint64_t* pairs_host, double* vmax_host) {
+                                       uint64_t* pairs_host, double* vmax_host) try {
   if (!d_vals || n_pad <= 0 || n_pad % 32) return fail(PCR_ERR_INVALID_ARG, "n_pad must be a positive multiple of 32");
   if (value_kind < 0 || value_kind > 2 || encoding < 1 || encoding > 2) return fail(PCR_ERR_INVALID_ARG, "bad kind");
   const int w64 = value_kind == VK_F64 ? 1 : (value_kind == VK_FIX && B > 32 ? 1 : 0);
@@ -4858,4 +5038,8 @@ extern "C" pcr_status pcr_debug_encode(const void* d_vals, int64_t n_pad, int va
   CUDA_TRY(cudaStreamSynchronize(s));
   if (vmax_host) *vmax_host = vmd;
   return PCR_OK;
+} catch (const std::bad_alloc&) {
+  return fail(PCR_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(PCR_ERR_INVALID_ARG, "unexpected host error");
 }
