@@ -340,7 +340,9 @@ pcr_status pcr_plan_more(const pcr_handle* h, const pcr_target* target, const pc
  * have: NULL or a plan of this handle whose planes the caller holds (as
  * pcr_plan_more).  info (may be NULL): expansions, whether the minimum was
  * proved, the greedy's bytes beyond `have`, host milliseconds.  Errors: as
- * pcr_plan_more; PCR_ERR_INVALID_ARG for max_nodes < 0. */
+ * pcr_plan_more; PCR_ERR_INVALID_ARG for max_nodes < 0; host memory grows
+ * with the budget (about 2 U^2 bytes per expansion for U planning units;
+ * PCR_ERR_OOM when it cannot be had). */
 typedef struct {
   int64_t expanded;       /* states expanded                                 */
   int optimal;            /* 1 when the plan is proved the minimum           */
