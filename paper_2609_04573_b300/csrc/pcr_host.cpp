@@ -1272,6 +1272,7 @@ struct BoundEval {
   std::vector<std::vector<int>> by_id;   // slots in ascending region id
   std::vector<std::vector<Group>> grp;   // per level, ascending region id
   std::vector<double> lfac, lcnt;        // per level: level factor, sqrt(point count)
+  std::vector<int> grp_level, grp_index; // per stream: its L2 group's level and index (-1: none)
   double top_cnt = 0, n2grid = 0;
   // kept state for the current errors
   std::vector<double> E_in, N_in, csum;
@@ -1323,6 +1324,14 @@ struct BoundEval {
           G.rfac = c.m.region_factor.at({l, g.first});
           G.rcnt = std::sqrt((double)c.m.region_counts.at({l, g.first}));
         }
+        for (int i : G.items) {
+          if ((int)grp_level.size() <= i) {
+            grp_level.resize(i + 1, -1);
+            grp_index.resize(i + 1, -1);
+          }
+          grp_level[i] = l;
+          grp_index[i] = (int)grp[l].size();
+        }
         grp[l].push_back(G);
       }
       if (c.m.interp == 0) {
@@ -1368,25 +1377,27 @@ struct BoundEval {
     for (int k : by_id[l]) base = std::max(base, c.lam * base + a[k] + rho);
     return base;
   }
+  // the norm of one region group (Composer::l2)
+  static double group_norm(const Group& G, const std::vector<double>& sq) {
+    if (!G.decomposed) return std::sqrt(sq[G.items[0]]);
+    const double n1 = std::sqrt(sq[G.items[0]]);
+    const double n2 = std::sqrt(sq[G.items[1]]) + G.f1 * n1;
+    const double n3 = std::sqrt(sq[G.items[2]]) + G.f2 * std::sqrt(n1 * n1 + n2 * n2);
+    return std::sqrt(n1 * n1 + n2 * n2 + n3 * n3);
+  }
+  // their root sum of squares (per-level interpolation)
+  void norm_sum(int l, const double* out, double& cs) const {
+    if (c.m.interp == 0) {
+      double s = 0.0;
+      for (size_t g = 0; g < grp[l].size(); g++) s += out[g] * out[g];
+      cs = std::sqrt(s);
+    }
+  }
   // per-region norms of one level (Composer::l2)
   void norms(int l, const std::vector<double>& sq, double* out, double& cs) const {
     const auto& gs = grp[l];
-    for (size_t g = 0; g < gs.size(); g++) {
-      const Group& G = gs[g];
-      if (!G.decomposed) {
-        out[g] = std::sqrt(sq[G.items[0]]);
-      } else {
-        const double n1 = std::sqrt(sq[G.items[0]]);
-        const double n2 = std::sqrt(sq[G.items[1]]) + G.f1 * n1;
-        const double n3 = std::sqrt(sq[G.items[2]]) + G.f2 * std::sqrt(n1 * n1 + n2 * n2);
-        out[g] = std::sqrt(n1 * n1 + n2 * n2 + n3 * n3);
-      }
-    }
-    if (c.m.interp == 0) {
-      double s = 0.0;
-      for (size_t g = 0; g < gs.size(); g++) s += out[g] * out[g];
-      cs = std::sqrt(s);
-    }
+    for (size_t g = 0; g < gs.size(); g++) out[g] = group_norm(gs[g], sq);
+    norm_sum(l, out, cs);
   }
   double top(const std::vector<double>& err) const { return err[ids[L - 1][0]] + (L - 1 >= 1 ? c.m.h : 0.0); }
 
@@ -1398,7 +1409,11 @@ struct BoundEval {
     std::fill(cn_ok.begin(), cn_ok.end(), 0);
     return eval_from(L - 1, err, sq, false);
   }
-  double eval_from(int from, const std::vector<double>& err, const std::vector<double>& sq, bool keep) {
+  // `changed` >= 0: the one stream whose sq may differ from the kept state
+  // (the other groups' norms are taken from it, computed by the same
+  // operations)
+  double eval_from(int from, const std::vector<double>& err, const std::vector<double>& sq, bool keep,
+                   int changed = -1) {
     if (L == 1) {
       if (!l2) return (top(err) + c.rho0(0.0, 0.0)) * kMargin;
       double N = std::sqrt(sq[ids[0][0]]);
@@ -1458,7 +1473,14 @@ struct BoundEval {
           tcn.resize(grp[level].size());
           o = tcn.data();
         }
-        norms(level, sq, o, cs);
+        if (!keep && changed >= 0 && changed < (int)grp_level.size() && cn_ok[level] &&
+            grp_level[changed] == level) {
+          std::copy(cn[level].begin(), cn[level].end(), tcn.begin());
+          o[grp_index[changed]] = group_norm(grp[level][grp_index[changed]], sq);
+          norm_sum(level, o, cs);
+        } else {
+          norms(level, sq, o, cs);
+        }
         if (keep) csum[level] = cs;
         a = o;
       } else {
@@ -1531,7 +1553,7 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
   BoundEval be(h->comp, !linf);
   std::vector<int> unit_level(units.size());
   for (size_t ui = 0; ui < units.size(); ui++) unit_level[ui] = h->geo[units[ui].ids[0]].level;
-  auto evaluate = [&](int level, bool keep) { return be.eval_from(level, err, sq, keep); };
+  auto evaluate = [&](int level, bool keep, int changed = -1) { return be.eval_from(level, err, sq, keep, changed); };
   std::vector<std::pair<int, double>> reg;
   auto unit_value = [&](const Unit& u) {
     if (u.ids.size() == 1) return linf ? err[u.ids[0]] : sq[u.ids[0]];
@@ -1581,7 +1603,7 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
       const uint64_t db = step_cost(st);
       const double own0 = unit_value(u);
       apply(st);
-      const double nb = evaluate(unit_level[ui], false);
+      const double nb = evaluate(unit_level[ui], false, u.ids.size() == 1 ? u.ids[0] : -1);
       const double own1 = unit_value(u);
       undo();
       const double gain = bound - nb;
@@ -3266,7 +3288,7 @@ static bool greedy_l2_global(std::vector<BlockPlan>& bp, double budget, double& 
         const int i0 = u.ids[0];
         const double own0 = p.sq[i0];
         apply(p, st);
-        const double ne = p.be->eval_from(p.unit_level[ui], p.err, p.sq, false);
+        const double ne = p.be->eval_from(p.unit_level[ui], p.err, p.sq, false, u.ids.size() == 1 ? i0 : -1);
         const double own1 = p.sq[i0];
         undo(p);
         const double gain = p.E - ne;

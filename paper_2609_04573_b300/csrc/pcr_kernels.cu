@@ -1542,9 +1542,15 @@ __device__ __forceinline__ int sb_index(int lane, int i) { return lane * 16 + (i
 template <typename VT>
 constexpr int enc_dyn_smem() { return (2 * kSegElems * (int)(sizeof(VT) / 4) + 32 * kEncRow) * 4; }
 
-template <typename VT>
-__global__ void __launch_bounds__(kThreads, 4) k_encode_w32(const StreamD* __restrict__ streams,
-                                                            const WorkItem* __restrict__ items, int nitems) {
+// PAIRS (PSNR-mode streams): also the plane-pair counts of the exact
+// squared-error tables, sum over values of d_a d_c for planes a <= c: per
+// word lane a adds popc(D_a & D_(a+t)) for t = 0..16 (rotated lanes cover
+// every unordered pair once, t = 16 only from the lower half), folded into
+// shared counts per segment and added to the stream's table.
+template <typename VT, bool PAIRS>
+__global__ void __launch_bounds__(kThreads, PAIRS ? 2 : 4) k_encode_w32(const StreamD* __restrict__ streams,
+                                                                        const WorkItem* __restrict__ items,
+                                                                        int nitems) {
   constexpr int VW = sizeof(VT) / 4;   // 32-bit words per staged value
   extern __shared__ __align__(16) uint32_t enc_dyn[];
   uint32_t* const pbuf = enc_dyn + 2 * kSegElems * VW;
@@ -1553,6 +1559,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_encode_w32(const StreamD* __res
   __shared__ uint32_t woff[kWarps][32];
   __shared__ uint32_t poff[33];
   __shared__ uint32_t pnz[32];
+  __shared__ uint32_t pairs_s[PAIRS ? 32 * 33 / 2 : 1];
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const TrC tc = tr_consts(lane);
@@ -1561,6 +1568,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_encode_w32(const StreamD* __res
   int item = blockIdx.x;
   if (item >= nitems) return;
   if (threadIdx.x < 32) pnz[threadIdx.x] = 0;
+  if constexpr (PAIRS)
+    for (int i = threadIdx.x; i < 32 * 33 / 2; i += kThreads) pairs_s[i] = 0;
+  [[maybe_unused]] uint32_t acc_p[PAIRS ? 17 : 1];
+  if constexpr (PAIRS) {
+#pragma unroll
+    for (int t = 0; t < 17; t++) acc_p[t] = 0;
+  }
   for (int i = threadIdx.x; i < kSegWords + 64; i += kThreads) sbuf[i] = 0;
   // the current item's stream fields needed to fetch it, and the next one's
   WorkItem it = items[item];
@@ -1655,6 +1669,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_encode_w32(const StreamD* __res
         const uint32_t xr = q << (32 - B);
         const uint32_t x = __brev(xr);                   // bit t = plane t (from the top)
         const uint32_t D = transpose32c(x, tc);           // lane k: plane k of the 32 values
+        if constexpr (PAIRS) {
+#pragma unroll
+          for (int t = 0; t < 17; t++) acc_p[t] += __popc(D & __shfl_sync(FULL, D, (lane + t) & 31));
+        }
         uint32_t sl = D;
         if constexpr (!GEN) {
           const uint32_t up = __shfl_up_sync(FULL, D, 1);
@@ -1701,6 +1719,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_encode_w32(const StreamD* __res
       wcnt[warp][lane] = count;
     }
     if (lane < B && nz) atomicAdd(&pnz[lane], nz);
+    if constexpr (PAIRS) {
+#pragma unroll
+      for (int t = 0; t < 17; t++) {
+        const int b2 = (lane + t) & 31;
+        if ((t < 16 || lane < 16) && acc_p[t]) atomicAdd(&pairs_s[tri<32>(min(lane, b2), max(lane, b2))], acc_p[t]);
+        acc_p[t] = 0;
+      }
+    }
     __syncthreads();   // S2
     // (D) sign layout of the segment, then each plane's bit-strings in place
     if (generic) {
@@ -1746,10 +1772,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_encode_w32(const StreamD* __res
         }
       }
       if (threadIdx.x < B && pnz[threadIdx.x]) atomicAdd(&s.plane_nz[threadIdx.x], pnz[threadIdx.x]);
+      if constexpr (PAIRS) {
+        for (int i = threadIdx.x; i < 32 * 32; i += kThreads) {
+          const int a = i >> 5, c = i & 31;
+          if (a <= c && c < B && pairs_s[tri<32>(a, c)])
+            atomicAdd(&s.pairs[a * B + c], (unsigned long long)pairs_s[tri<32>(a, c)]);
+        }
+      }
     }
     // (F) every read of this item's shared memory is done (S5): clear for the next
     __syncthreads();
     if (threadIdx.x < 32) pnz[threadIdx.x] = 0;
+    if constexpr (PAIRS)
+      for (int i = threadIdx.x; i < 32 * 33 / 2; i += kThreads) pairs_s[i] = 0;
     for (int i = threadIdx.x; i < kSegWords + 64; i += kThreads) sbuf[i] = 0;
     item = nitem;
     it = nit;
@@ -1902,7 +1937,7 @@ __global__ void __launch_bounds__(kThreads) k_decode_w32(const StreamD* __restri
 }
 
 // persistent grid of k_encode_w32: the CTAs that fit on the device at once
-template <typename VT>
+template <typename VT, bool PAIRS>
 static int enc_w32_grid(int nitems) {
   static int cached[64] = {0};
   int dev = 0;
@@ -1911,8 +1946,8 @@ static int enc_w32_grid(int nitems) {
   if (g == 0) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_encode_w32<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, enc_dyn_smem<VT>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_encode_w32<VT>, kThreads, enc_dyn_smem<VT>());
+    cudaFuncSetAttribute(k_encode_w32<VT, PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize, enc_dyn_smem<VT>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_encode_w32<VT, PAIRS>, kThreads, enc_dyn_smem<VT>());
     g = max(1, sms * max(per, 1));
   }
   return min(nitems, g);
@@ -1924,23 +1959,22 @@ void launch_encode(int vk, int w64, int pairs, const StreamD* d_streams, const W
   if (nitems == 0) return;
   count_launch();
 #define ENC(VT, W, P) k_encode<VT, W, P><<<nitems, kThreads, 0, s>>>(d_streams, d_items)
+#define ENC32(VT, P) \
+  k_encode_w32<VT, P><<<enc_w32_grid<VT, P>(nitems), kThreads, enc_dyn_smem<VT>(), s>>>(d_streams, d_items, nitems)
   if (!w64) {
     if (vk == VK_F32) {
-      if (pairs) ENC(float, 32, true);
-      else
-        k_encode_w32<float><<<enc_w32_grid<float>(nitems), kThreads, enc_dyn_smem<float>(), s>>>(d_streams, d_items,
-                                                                                                 nitems);
+      if (pairs) ENC32(float, true);
+      else ENC32(float, false);
     } else {
-      if (pairs) ENC(int64_t, 32, true);
-      else
-        k_encode_w32<int64_t><<<enc_w32_grid<int64_t>(nitems), kThreads, enc_dyn_smem<int64_t>(), s>>>(
-            d_streams, d_items, nitems);
+      if (pairs) ENC32(int64_t, true);
+      else ENC32(int64_t, false);
     }
   } else {
     if (vk == VK_F64) { if (pairs) ENC(double, 64, true); else ENC(double, 64, false); }
     else { if (pairs) ENC(int64_t, 64, true); else ENC(int64_t, 64, false); }
   }
 #undef ENC
+#undef ENC32
 }
 
 void launch_decode(int vk, int w64, const StreamD* d_streams, const WorkItem* d_items, int nitems,
