@@ -1273,6 +1273,7 @@ struct BoundEval {
   std::vector<std::vector<Group>> grp;   // per level, ascending region id
   std::vector<double> lfac, lcnt;        // per level: level factor, sqrt(point count)
   std::vector<int> grp_level, grp_index; // per stream: its L2 group's level and index (-1: none)
+  std::vector<std::vector<double>> t_pre; // per-region L2 chain, kept: T before each group of a level
   double top_cnt = 0, n2grid = 0;
   // kept state for the current errors
   std::vector<double> E_in, N_in, csum;
@@ -1342,6 +1343,7 @@ struct BoundEval {
     if (l2) top_cnt = std::sqrt((double)c.m.level_counts.at(L - 1));
     if (l2 && L >= 2) n2grid = std::sqrt((double)(c.m.n - c.m.level_counts.at(0)));
     E_in.assign(L, 0.0);
+    t_pre.assign(L, {});
     N_in.assign(L, 0.0);
     csum.assign(L, 0.0);
     acc.resize(L);
@@ -1494,7 +1496,18 @@ struct BoundEval {
       } else {
         double T = N * N;
         const auto& gs = grp[level];
-        for (size_t g = 0; g < gs.size(); g++) {
+        size_t g0 = 0;
+        // one changed group above level 0: the chain before it is the kept
+        // one (the incoming N, the earlier groups and rho are unchanged; at
+        // level 0 rho and the coarse rounding move with every error)
+        if (!keep && changed >= 0 && level == from && level > 0 && changed < (int)grp_level.size() &&
+            grp_level[changed] == level && t_pre.size() > (size_t)level && t_pre[level].size() == gs.size()) {
+          g0 = (size_t)grp_index[changed];
+          T = t_pre[level][g0];
+        }
+        if (keep) t_pre[level].resize(gs.size());
+        for (size_t g = g0; g < gs.size(); g++) {
+          if (keep) t_pre[level][g] = T;
           const double t = gs[g].rfac * std::sqrt(T) + a[g] + rho * gs[g].rcnt;
           T += t * t;
         }
