@@ -451,12 +451,47 @@ struct Big {
     if (rest) m += 1;
     return std::ldexp((double)m, drop);
   }
+  // ceil(sqrt(value)), exact.  A long-double estimate e of sqrt(value)
+  // (64-bit mantissa: relative error below 2^-62) gives the floor root
+  // within e 2^-60 + 2; the bits below that margin are then set one at a
+  // time from a lower bound (r = lo + sum of 2^i with (r + 2^i)^2 <= value),
+  // so only a few multiplications remain.
   Big isqrt_ceil() const {
-    Big r;
-    const int t = (bitlen() + 1) / 2 + 1;
-    for (int i = t; i >= 0; i--) {
+    const int t = bitlen();
+    if (t == 0) return Big();
+    long double v = 0.0L;   // value rounded to 64 bits, then the estimate
+    {
+      const int drop = t > 64 ? t - 64 : 0;
+      uint64_t m = 0;
+      for (int i = t - 1; i >= drop; i--) m = (m << 1) | (uint64_t)bit(i);
+      v = std::ldexp((long double)m, drop);
+    }
+    const long double e = std::sqrt(v);
+    const long double margin = std::ldexp(e, -60) + 4.0L;
+    long double lo_f = std::floor(e - margin);
+    if (lo_f < 0.0L) lo_f = 0.0L;
+    // lo_f as a Big (an integer below 2^96 whose 64-bit mantissa is exact)
+    Big lo;
+    {
+      int ex = 0;
+      const long double fr = std::frexp(lo_f, &ex);   // lo_f = fr 2^ex, fr in [0.5, 1)
+      if (lo_f > 0.0L) {
+        const uint64_t mant = (uint64_t)std::ldexp(fr, 64);
+        const int sh = ex - 64;
+        if (sh >= 0) lo = Big::shl(mant, sh);
+        else lo = Big::from(mant >> (-sh));
+      }
+    }
+    int k = 0;   // bits to settle: the floor root lies in [lo, lo + 2^(k+1))
+    {
+      const long double span = 2.0L * margin + 2.0L;
+      while (std::ldexp(1.0L, k + 1) <= span) k++;
+      k++;
+    }
+    Big r = lo;
+    for (int i = k; i >= 0; i--) {
       Big c = r;
-      c.setbit(i);
+      c.add(Big::shl(1, i));
       if (c.mulb(c).cmp(*this) <= 0) r = c;
     }
     if (r.mulb(r).cmp(*this) < 0) r.add(Big::from(1));
@@ -1122,21 +1157,27 @@ void compute_tables(pcr_handle* h, int i, const std::vector<uint64_t>* pairs, bo
     const int64_t n_real = g.n_real();
     if (psnr && pairs) {
       const auto& C = *pairs;
-      for (int b = 0; b <= B; b++) {
-        Big pos, neg, s1;
-        for (int j = b; j < B; j++)
+      // the sums over planes j, jj >= b, from b = B down: step b adds the
+      // pairs with min(j, jj) = b ((b, b) once, (b, jj) and (jj, b) as one
+      // doubled term); exact integers, so the order does not matter
+      Big pos, neg, s1g;
+      for (int b = B; b >= 0; b--) {
+        if (b < B) {
           for (int jj = b; jj < B; jj++) {
-            const uint64_t c = C[std::min(j, jj) * B + std::max(j, jj)];
+            const uint64_t c = C[b * B + jj];
             if (!c) continue;
-            const int w = 2 * B - 2 - j - jj;
-            Big term = Big::shl(c, w);
-            if (!nb || ((j + jj) % 2 == 0)) pos.add(term);
+            const int w = 2 * B - 2 - b - jj + (jj == b ? 0 : 1);
+            const Big term = Big::shl(c, w);
+            if (!nb || ((b + jj) % 2 == 0)) pos.add(term);
             else neg.add(term);
           }
+          if (!nb) s1g.add(Big::shl(C[b * B + b], B - 1 - b));
+        }
         Big s2 = pos;
         s2.sub(neg);
+        Big s1;
         if (!nb) {
-          for (int j = b; j < B; j++) s1.add(Big::shl(C[j * B + j], B - 1 - j));
+          s1 = s1g;
         } else {
           s1 = s2.mul((uint64_t)n_real).isqrt_ceil();
         }
