@@ -1447,6 +1447,121 @@ struct BoundEval {
   // bound for the errors err / sq, of which only level `from`'s streams may
   // differ from the kept state; `keep` makes them the kept state
   // the bound of arbitrary errors, nothing kept or reused
+  // whether eval_batch applies to stream i: an L2 evaluator, i one of the
+  // streams of a level below the top one (in an L2 group), the kept state
+  // current for every level (it is after any evaluation with keep)
+  bool batch_ok(int i) const {
+    if (!l2 || L < 2 || i < 0 || i >= (int)grp_level.size() || grp_level[i] < 0) return false;
+    for (int l = 0; l <= grp_level[i]; l++)
+      if (!acc_ok[l] || !cn_ok[l]) return false;
+    return true;
+  }
+  // The bounds of n candidates, candidate k being the kept state with stream
+  // st[k]'s error and squared error replaced by nerr[k], nsq[k] (its level
+  // l_k below the top one): eval_from(l_k, ..., false, st[k]) for each, with
+  // the same operations in the same order per candidate, computed side by
+  // side so that the candidates' dependent square-root chains overlap.
+  // err / sq hold the kept state.
+  void eval_batch(int n, const int* st, const double* nerr, const double* nsq, const std::vector<double>& err,
+                  const std::vector<double>& sq, double* out) {
+    b_lvl.resize(n);
+    b_slot.resize(n);
+    b_ssum.resize(n);
+    b_E.resize(n);
+    b_rho.resize(n);
+    b_conv.resize(n);
+    b_N.resize(n);
+    b_gn.resize(n);
+    b_cs.resize(n);
+    int top = 0;
+    for (int k = 0; k < n; k++) {
+      const int i = st[k], l = grp_level[i];
+      b_lvl[k] = l;
+      top = std::max(top, l);
+      // the changed stream's slot sum, in stream order as sums() forms it
+      const auto& idl = ids[l];
+      const auto& sll = slot[l];
+      int si = -1;
+      for (size_t j = 0; j < idl.size(); j++)
+        if (idl[j] == i) si = sll[j];
+      double ssum = 0.0;
+      for (size_t j = 0; j < idl.size(); j++)
+        if (sll[j] == si) ssum = ssum + (idl[j] == i ? nerr[k] : err[idl[j]]);
+      b_slot[k] = si;
+      b_ssum[k] = ssum;
+      b_E[k] = E_in[l];
+      // the changed group's norm (group_norm with sq[i] replaced)
+      const Group& Gi = grp[l][grp_index[i]];
+      auto sqv = [&](int id) { return id == i ? nsq[k] : sq[id]; };
+      if (!Gi.decomposed) {
+        b_gn[k] = std::sqrt(sqv(Gi.items[0]));
+      } else {
+        const double n1 = std::sqrt(sqv(Gi.items[0]));
+        const double n2 = std::sqrt(sqv(Gi.items[1])) + Gi.f1 * n1;
+        const double n3 = std::sqrt(sqv(Gi.items[2])) + Gi.f2 * std::sqrt(n1 * n1 + n2 * n2);
+        b_gn[k] = std::sqrt(n1 * n1 + n2 * n2 + n3 * n3);
+      }
+      if (c.m.interp == 0) {   // the level's root sum of squares with that group replaced
+        double sacc = 0.0;
+        for (size_t g = 0; g < grp[l].size(); g++) {
+          const double v = (int)g == grp_index[i] ? b_gn[k] : cn[l][g];
+          sacc += v * v;
+        }
+        b_cs[k] = std::sqrt(sacc);
+      }
+    }
+    // the L-infinity chain from each candidate's level to level 1, then the
+    // level-0 rounding terms
+    for (int level = top; level >= 1; level--)
+      for (int k = 0; k < n; k++) {
+        if (b_lvl[k] < level) continue;
+        const double* a = acc[level].data();
+        if (b_lvl[k] == level) {
+          tacc.assign(a, a + nslot[level]);
+          tacc[b_slot[k]] = b_ssum[k];
+          a = tacc.data();
+        }
+        b_E[k] = level_step(level, b_E[k], a, c.rho_fix);
+      }
+    for (int k = 0; k < n; k++) {
+      double e0 = 0.0;
+      for (int q = 0; q < nslot[0]; q++) e0 += (b_lvl[k] == 0 && q == b_slot[k]) ? b_ssum[k] : acc[0][q];
+      b_rho[k] = c.rho0(b_E[k], e0);
+      b_conv[k] = c.conv(b_E[k], e0);
+      b_N[k] = N_in[b_lvl[k]];
+    }
+    // the L2 chain from each candidate's level down to level 0
+    for (int level = top; level >= 0; level--) {
+      const auto& gs = grp[level];
+      const int G = (int)gs.size();
+      for (int k = 0; k < n; k++) {
+        if (b_lvl[k] < level) continue;
+        const double rho = level == 0 ? b_rho[k] : c.rho_fix;
+        double N = b_N[k];
+        if (level == 0) N = N + b_conv[k] * n2grid;
+        const bool own = b_lvl[k] == level;
+        const int gi = own ? grp_index[st[k]] : -1;
+        if (c.m.interp == 0) {
+          const double cs = own ? b_cs[k] : csum[level];
+          const double t = lfac[level] * N + cs + rho * lcnt[level];
+          N = std::sqrt(N * N + t * t);
+        } else {
+          double T = N * N;
+          for (int g = 0; g < G; g++) {
+            const double a = g == gi ? b_gn[k] : cn[level][g];
+            const double t = gs[g].rfac * std::sqrt(T) + a + rho * gs[g].rcnt;
+            T += t * t;
+          }
+          N = std::sqrt(T);
+        }
+        b_N[k] = N;
+      }
+    }
+    for (int k = 0; k < n; k++) out[k] = (b_N[k] * b_N[k]) * kMargin;
+  }
+  std::vector<int> b_lvl, b_slot;
+  std::vector<double> b_ssum, b_E, b_rho, b_conv, b_N, b_gn, b_cs;
+
   double eval_all(const std::vector<double>& err, const std::vector<double>& sq) {
     std::fill(acc_ok.begin(), acc_ok.end(), 0);
     std::fill(cn_ok.begin(), cn_ok.end(), 0);
@@ -1646,20 +1761,60 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
     }
   };
   bound = evaluate(h->L - 1, true);
+  // candidates that change one stream below the top level of an L2 plan:
+  // evaluated side by side (BoundEval::eval_batch, the same values as one
+  // by one)
+  std::vector<int> bst, bunit;
+  std::vector<double> berr, bsq, bval, nbv(units.size()), own1v(units.size());
+  std::vector<char> batched(units.size(), 0);
   while (bound > target) {
     bool have_best = false, have_fb = false;
     double best_r = 0, fb_r = 0, best_bnd = 0, fb_bnd = 0;
     size_t best_u = 0, fb_u = 0;
+    bst.clear();
+    bunit.clear();
+    berr.clear();
+    bsq.clear();
+    if (!linf) {
+      for (size_t ui = 0; ui < units.size(); ui++) {
+        batched[ui] = 0;
+        const Unit& u = units[ui];
+        if (pos[ui] >= u.steps.size() || u.ids.size() != 1) continue;
+        const Step& st = u.steps[pos[ui]];
+        const int i = u.ids[0];
+        if (st.upd.size() != 1 || st.upd[0].first != i || !be.batch_ok(i)) continue;
+        const int nbp = have ? std::max(b[i], st.upd[0].second) : st.upd[0].second;
+        bst.push_back(i);
+        bunit.push_back((int)ui);
+        berr.push_back(h->tabs[i].maxerr[nbp]);
+        bsq.push_back(h->tabs[i].sq[nbp]);
+        batched[ui] = 1;
+      }
+      if (!bst.empty()) {
+        bval.resize(bst.size());
+        be.eval_batch((int)bst.size(), bst.data(), berr.data(), bsq.data(), err, sq, bval.data());
+        for (size_t k = 0; k < bst.size(); k++) {
+          nbv[bunit[k]] = bval[k];
+          own1v[bunit[k]] = bsq[k];
+        }
+      }
+    }
     for (size_t ui = 0; ui < units.size(); ui++) {
       const Unit& u = units[ui];
       if (pos[ui] >= u.steps.size()) continue;
       const Step& st = u.steps[pos[ui]];
       const uint64_t db = step_cost(st);
       const double own0 = unit_value(u);
-      apply(st);
-      const double nb = evaluate(unit_level[ui], false, u.ids.size() == 1 ? u.ids[0] : -1);
-      const double own1 = unit_value(u);
-      undo();
+      double nb, own1;
+      if (!linf && batched[ui]) {
+        nb = nbv[ui];
+        own1 = own1v[ui];
+      } else {
+        apply(st);
+        nb = evaluate(unit_level[ui], false, u.ids.size() == 1 ? u.ids[0] : -1);
+        own1 = unit_value(u);
+        undo();
+      }
       const double gain = bound - nb;
       const double inf = std::numeric_limits<double>::infinity();
       const double ratio = db == 0 ? inf : gain / (double)db;
