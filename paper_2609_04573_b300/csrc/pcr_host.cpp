@@ -1315,6 +1315,7 @@ struct BoundEval {
   std::vector<double> lfac, lcnt;        // per level: level factor, sqrt(point count)
   std::vector<int> grp_level, grp_index; // per stream: its L2 group's level and index (-1: none)
   std::vector<std::vector<double>> t_pre; // per-region L2 chain, kept: T before each group of a level
+  std::vector<int> stream_level;          // per stream: its level
   double top_cnt = 0, n2grid = 0;
   // kept state for the current errors
   std::vector<double> E_in, N_in, csum;
@@ -1332,6 +1333,10 @@ struct BoundEval {
     lcnt.assign(L, 0.0);
     for (int l = 0; l < L; l++) {
       ids[l] = c.by_level.at(l);
+      for (int i : ids[l]) {
+        if ((int)stream_level.size() <= i) stream_level.resize(i + 1, -1);
+        stream_level[i] = l;
+      }
       std::vector<int> regs;
       for (int i : ids[l]) {
         const int r = c.st[i].region;
@@ -1451,9 +1456,11 @@ struct BoundEval {
   // streams of a level below the top one (in an L2 group), the kept state
   // current for every level (it is after any evaluation with keep)
   bool batch_ok(int i) const {
-    if (!l2 || L < 2 || i < 0 || i >= (int)grp_level.size() || grp_level[i] < 0) return false;
-    for (int l = 0; l <= grp_level[i]; l++)
-      if (!acc_ok[l] || !cn_ok[l]) return false;
+    if (L < 2 || i < 0 || i >= (int)stream_level.size() || stream_level[i] < 0 || stream_level[i] >= L - 1)
+      return false;
+    if (l2 && (i >= (int)grp_level.size() || grp_level[i] != stream_level[i])) return false;
+    for (int l = 0; l <= stream_level[i]; l++)
+      if (!acc_ok[l] || (l2 && !cn_ok[l])) return false;
     return true;
   }
   // The bounds of n candidates, candidate k being the kept state with stream
@@ -1475,7 +1482,7 @@ struct BoundEval {
     b_cs.resize(n);
     int top = 0;
     for (int k = 0; k < n; k++) {
-      const int i = st[k], l = grp_level[i];
+      const int i = st[k], l = stream_level[i];
       b_lvl[k] = l;
       top = std::max(top, l);
       // the changed stream's slot sum, in stream order as sums() forms it
@@ -1490,6 +1497,7 @@ struct BoundEval {
       b_slot[k] = si;
       b_ssum[k] = ssum;
       b_E[k] = E_in[l];
+      if (!l2) continue;
       // the changed group's norm (group_norm with sq[i] replaced)
       const Group& Gi = grp[l][grp_index[i]];
       auto sqv = [&](int id) { return id == i ? nsq[k] : sq[id]; };
@@ -1528,8 +1536,19 @@ struct BoundEval {
       for (int q = 0; q < nslot[0]; q++) e0 += (b_lvl[k] == 0 && q == b_slot[k]) ? b_ssum[k] : acc[0][q];
       b_rho[k] = c.rho0(b_E[k], e0);
       b_conv[k] = c.conv(b_E[k], e0);
+      if (!l2) {   // the L-infinity bound: level 0's step
+        const double* a = acc[0].data();
+        if (b_lvl[k] == 0) {
+          tacc.assign(a, a + nslot[0]);
+          tacc[b_slot[k]] = b_ssum[k];
+          a = tacc.data();
+        }
+        out[k] = level_step(0, b_E[k] + b_conv[k], a, b_rho[k]) * kMargin;
+        continue;
+      }
       b_N[k] = N_in[b_lvl[k]];
     }
+    if (!l2) return;
     // the L2 chain from each candidate's level down to level 0
     for (int level = top; level >= 0; level--) {
       const auto& gs = grp[level];
@@ -1775,7 +1794,7 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
     bunit.clear();
     berr.clear();
     bsq.clear();
-    if (!linf) {
+    {
       for (size_t ui = 0; ui < units.size(); ui++) {
         batched[ui] = 0;
         const Unit& u = units[ui];
@@ -1788,15 +1807,13 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
         bunit.push_back((int)ui);
         berr.push_back(h->tabs[i].maxerr[nbp]);
         bsq.push_back(h->tabs[i].sq[nbp]);
+        own1v[ui] = linf ? h->tabs[i].maxerr[nbp] : h->tabs[i].sq[nbp];
         batched[ui] = 1;
       }
       if (!bst.empty()) {
         bval.resize(bst.size());
         be.eval_batch((int)bst.size(), bst.data(), berr.data(), bsq.data(), err, sq, bval.data());
-        for (size_t k = 0; k < bst.size(); k++) {
-          nbv[bunit[k]] = bval[k];
-          own1v[bunit[k]] = bsq[k];
-        }
+        for (size_t k = 0; k < bst.size(); k++) nbv[bunit[k]] = bval[k];
       }
     }
     for (size_t ui = 0; ui < units.size(); ui++) {
@@ -1806,7 +1823,7 @@ bool greedy(const pcr_handle* h, double target, bool linf, std::vector<int>& b, 
       const uint64_t db = step_cost(st);
       const double own0 = unit_value(u);
       double nb, own1;
-      if (!linf && batched[ui]) {
+      if (batched[ui]) {
         nb = nbv[ui];
         own1 = own1v[ui];
       } else {
