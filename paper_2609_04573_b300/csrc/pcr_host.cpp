@@ -2803,6 +2803,20 @@ static pcr_status enqueue_batch(const std::vector<pcr_handle*>& hs, const void* 
   // for the batch, scattered by one launch)
   std::vector<WorkItem> li;
   std::vector<std::pair<pcr_handle*, size_t>> li_at;
+  // one handle: its encode work list (floating-point streams, then fixed
+  // point, streams and segments in order) is that list already
+  if (n == 1 && !hs[0]->items_ready && nit) {
+    pcr_handle* h = hs[0];
+    for (int fx = 0; fx < 2; fx++) {
+      h->items_n[fx] = 0;
+      for (int i = 0; i < (int)h->geo.size(); i++)
+        if ((int)h->geo[i].is_fix == fx) h->items_n[fx] += (h->geo[i].n_pad() + kSegElems - 1) / kSegElems;
+    }
+    if ((size_t)(h->items_n[0] + h->items_n[1]) == nit) {
+      CUDA_TRY(cudaMemcpyAsync(h->d_items_all, d_items, nit * sizeof(WorkItem), cudaMemcpyDeviceToDevice, s));
+      h->items_ready = true;
+    }
+  }
   for (int k = 0; k < n; k++) {
     pcr_handle* h = hs[k];
     if (h->items_ready) continue;
