@@ -3475,6 +3475,10 @@ struct BlockPlan {
   std::vector<size_t> pos;
   std::vector<int> unit_level;
   double E = 0;
+  // each unit's next-step bound and own squared error, valid until this
+  // block takes a step (a step elsewhere leaves them unchanged)
+  std::vector<double> cne, cown1;
+  bool cvalid = false;
 };
 }  // namespace
 
@@ -3515,22 +3519,55 @@ static bool greedy_l2_global(std::vector<BlockPlan>& bp, double budget, double& 
     }
   };
   const double inf = std::numeric_limits<double>::infinity();
+  std::vector<int> bst, bunit;
+  std::vector<double> berr, bsq, bval;
   while (total > budget) {
     bool have_best = false, have_fb = false;
     double best_r = 0, fb_r = 0, best_e = 0, fb_e = 0;
     size_t best_k = 0, best_u = 0, fb_k = 0, fb_u = 0;
     for (size_t k = 0; k < bp.size(); k++) {
       BlockPlan& p = bp[k];
+      if (!p.cvalid) {   // this block's candidates: batched where they change one stream
+        const size_t nu = p.units->size();
+        p.cne.assign(nu, 0.0);
+        p.cown1.assign(nu, 0.0);
+        bst.clear();
+        bunit.clear();
+        berr.clear();
+        bsq.clear();
+        for (size_t ui = 0; ui < nu; ui++) {
+          const Unit& u = (*p.units)[ui];
+          if (p.pos[ui] >= u.steps.size()) continue;
+          const Step& st = u.steps[p.pos[ui]];
+          const int i0 = u.ids[0];
+          if (u.ids.size() == 1 && st.upd.size() == 1 && st.upd[0].first == i0 && p.be->batch_ok(i0)) {
+            bst.push_back(i0);
+            bunit.push_back((int)ui);
+            berr.push_back(p.h->tabs[i0].maxerr[st.upd[0].second]);
+            bsq.push_back(p.h->tabs[i0].sq[st.upd[0].second]);
+            p.cown1[ui] = bsq.back();
+            continue;
+          }
+          apply(p, st);
+          p.cne[ui] = p.be->eval_from(p.unit_level[ui], p.err, p.sq, false, u.ids.size() == 1 ? i0 : -1);
+          p.cown1[ui] = p.sq[i0];
+          undo(p);
+        }
+        if (!bst.empty()) {
+          bval.resize(bst.size());
+          p.be->eval_batch((int)bst.size(), bst.data(), berr.data(), bsq.data(), p.err, p.sq, bval.data());
+          for (size_t q = 0; q < bst.size(); q++) p.cne[bunit[q]] = bval[q];
+        }
+        p.cvalid = true;
+      }
       for (size_t ui = 0; ui < p.units->size(); ui++) {
         const Unit& u = (*p.units)[ui];
         if (p.pos[ui] >= u.steps.size()) continue;
         const Step& st = u.steps[p.pos[ui]];
         const int i0 = u.ids[0];
         const double own0 = p.sq[i0];
-        apply(p, st);
-        const double ne = p.be->eval_from(p.unit_level[ui], p.err, p.sq, false, u.ids.size() == 1 ? i0 : -1);
-        const double own1 = p.sq[i0];
-        undo(p);
+        const double ne = p.cne[ui];
+        const double own1 = p.cown1[ui];
         const double gain = p.E - ne;
         const double ratio = st.db == 0 ? inf : gain / (double)st.db;
         if (gain > 0 || st.db == 0) {
@@ -3563,6 +3600,7 @@ static bool greedy_l2_global(std::vector<BlockPlan>& bp, double budget, double& 
     apply(p, (*p.units)[best_u].steps[p.pos[best_u]]);
     p.be->eval_from(p.unit_level[best_u], p.err, p.sq, true);   // refresh the kept partial results
     p.pos[best_u]++;
+    p.cvalid = false;
     total = total - p.E + best_e;
     p.E = best_e;
   }
