@@ -1178,15 +1178,14 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
   // c_hat boxes of the three regions' staging arrays -- region 1 (odd planes)
   // CR x W12 values from compact (b2 / 2 - 4, (b1 - HR) / 2), region 2
   // T1 / 2 x W12 from (b2 / 2 - 4, b1 / 2), region 3 T1 x T2 / 2 from
-  // (b2 / 2, b1) -- zero beyond each array; three stages (FP32), two (8-byte
-// values).
+  // (b2 / 2, b1) -- zero beyond each array; two stages.
   constexpr int XW = T2 + 2 * XL;                                    // staged row length (refactor)
   constexpr int W12 = T2 / 2 + 8;                                    // region 1 / 2 box row (retrieve)
   constexpr int R1B = (CR * W12 * (int)sizeof(A) + 127) / 128 * 128;
   constexpr int R2B = ((T1 / 2) * W12 * (int)sizeof(A) + 127) / 128 * 128;
   constexpr int R3B = (T1 * (T2 / 2) * (int)sizeof(A) + 127) / 128 * 128;
   constexpr int SST = RET ? R1B + R2B + R3B : (PR * XW * (int)sizeof(A) + 127) / 128 * 128;   // bytes per stage
-  constexpr int NSTG = RET && sizeof(A) == 4 ? 3 : 2;   // 8-byte values: two stages keep 4 CTAs per SM
+  constexpr int NSTG = 2;   // (three stages for the retrieval measured no faster)
   [[maybe_unused]] unsigned char* stg = nullptr;
   [[maybe_unused]] uint32_t barb = 0, par = 0;
   if constexpr (TMA) {
@@ -2070,7 +2069,7 @@ static bool run_level0_march_tma_ret(const TileArgs& a0, cudaStream_t s, int zc_
   constexpr int R1B = (CR * W12 * (int)sizeof(A) + 127) / 128 * 128;
   constexpr int R2B = ((T1 / 2) * W12 * (int)sizeof(A) + 127) / 128 * 128;
   constexpr int R3B = (T1 * (T2 / 2) * (int)sizeof(A) + 127) / 128 * 128;
-  constexpr int NSTG = sizeof(A) == 4 ? 3 : 2;   // as in level0_march_body
+  constexpr int NSTG = 2;   // as in level0_march_body
   constexpr int SMEM = NSTG * (R1B + R2B + R3B) + 128 + 8 * NSTG;
   MarchMaps mm;
   if (!region_tensor_map<A>(a0.reg[0], W12, CR, mm.m[0]) || !region_tensor_map<A>(a0.reg[1], W12, T1 / 2, mm.m[1]) ||
