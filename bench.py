@@ -583,7 +583,8 @@ RETRIEVE_STAGES = {"decode_float", "decode_fixed", "recompose", "recon_coarsest"
 def algorithmic_bytes(stage, shape, w, pl):
     """Algorithmic DRAM bytes of one launch of a stage:
     interp_level0 (refactor): read the field, write level-0 coefficients;
-    recon_level0: read coarse values and level-0 coefficients, write field;
+    recon_level0: read level-0 coefficients and the coarse points' fixed-point
+      values (8 bytes each), write field;
     decompose / recompose: read and write the decomposed region values;
     encode_float: read level-0 stream values, write B planes + signs;
     decode_float: read the planned planes + signs, write stream values."""
@@ -591,7 +592,7 @@ def algorithmic_bytes(stage, shape, w, pl):
     n0 = n - math.prod((s + 1) // 2 for s in shape)  # level-0 points (odd somewhere)
     table = {
         "interp_level0": (n * w + n0 * w) / 1,
-        "recon_level0": (n0 * w + n * w) / 1,
+        "recon_level0": n0 * w + (n - n0) * 8 + n * w,
         "decompose": 2 * n0 * w / 3,          # three launches (regions) per step
         "recompose": 2 * n0 * w / 3,
         "encode_float": n0 * w + n0 * 4 + n0 / 8,

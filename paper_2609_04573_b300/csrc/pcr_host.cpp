@@ -41,8 +41,6 @@ void launch_decompose(int vk, const DecompGeo& dg, const LatD& sl, const void* c
 void launch_recompose(int vk, const DecompGeo& dg, const LatD& sl, const void* dec, void* comp, cudaStream_t s);
 void launch_recon_fixed(const FieldD& f, int level, int raw, const LatD& lat, const int64_t* chat, int64_t* xc,
                         cudaStream_t s);
-void launch_coarse_out(int vk, const FieldD& f, const int64_t* xc, double scale, void* out, cudaStream_t s,
-                       const Box3* box = nullptr);
 void launch_copy_box(int vk, const FieldD& f, const void* src, void* dst, const Box3& b, cudaStream_t s);
 void launch_recon_l0(int vk, const FieldD& f, const LatD& lat, int compact, const void* chat, void* out,
                      cudaStream_t s);
@@ -3757,9 +3755,9 @@ static pcr_status enqueue_retrieve_one(const pcr_handle* h, const pcr_retrieval_
 }
 
 // Reconstruction up to level 0 (Alg. 2): the level-0 recomposition on `s`
-// (after the float decode there), the fixed-point coarse levels and the
-// coarse points of the output on `sf` (after the fixed-point decode there);
-// `l0` receives the level-0 pass, which needs both.
+// (after the float decode there), the fixed-point coarse levels on `sf`
+// (after the fixed-point decode there); `l0` receives the level-0 pass,
+// which needs both.
 struct ReconL0 {
   bool on = false;
   TileArgs a{};
@@ -3803,12 +3801,12 @@ static pcr_status enqueue_reconstruct_coarse(const pcr_handle* h, const std::vec
     Prof pf("recon_fixed_levels", sf);
     launch_tile_interp(VK_FIX, a, sf);
   }
-  {
-    Prof pf("coarse_out", sf);
-    launch_coarse_out(h->vk, f, xc, std::ldexp(1.0, h->G - fix_bits(h->vk, h->L)), d_out, sf);
-  }
-  // level 0
+  // level 0, which takes the coarse points from the fixed-point grid: the
+  // marching kernel reads them there, the tile kernels have them written
+  // into the output first
   TileArgs a = level_args(h, 0, 1, d_out, d_out);
+  a.cfix = xc;
+  a.cscale = std::ldexp(1.0, h->G - fix_bits(h->vk, h->L));
   if (h->decomp >= 0) {
     for (int r = 1; r <= f.d; r++) {
       const Lat R = region_lat(h->n3, 0, h->order, r);

@@ -110,6 +110,13 @@ struct TileArgs {
   // set to 1 when a bounded device wait gives up (refactor: the field's
   // timeout flag; null: the library's device status word)
   int* err;
+  // whole-field retrieval of level 0: the coarse points (the 2-grid) come
+  // from the fixed-point copy cfix (x_int, shape ((m - 1) / 2 + 1) per axis,
+  // row-major), each value x_int * cscale rounded once.  The marching kernel
+  // reads its ring there and writes those points with its planes; the other
+  // paths first write them into the output.  Null: the output holds them.
+  const int64_t* cfix;
+  double cscale;
 };
 
 // items of one batched (multi-field) launch of the per-field kernels
@@ -269,6 +276,10 @@ bool autotune_pin(const int64_t* key, int choice);   // false: unknown key field
 // bounded waits of retrieval kernels that gave up on the current device
 // since the last clear (-1: the read failed); clear resets the count
 int read_device_timeouts(bool clear);
+// out[2-grid] = x_int * scale rounded once, over the whole 2-grid or a box
+// of it (pcr_kernels.cu)
+void launch_coarse_out(int vk, const FieldD& f, const int64_t* xc, double scale, void* out, cudaStream_t s,
+                       const Box3* box = nullptr);
 int autotune_entries(int max_entries, int64_t* keys, int* choice, double* ms);
 void clear_autotune();
 

@@ -1312,11 +1312,26 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
   };
   A h1[RET && !TMA ? N1 : 1], h2[RET && !TMA ? N2V : 1], h3[RET && !TMA ? N3 : 1];   // retrieve: c_hat of one plane
 
+  // retrieval: coarse values from the fixed-point 2-grid (rounded as the
+  // coarse-point pass rounds them), else from the output.  The fixed-point
+  // words stay in registers until the ring store, so the loads remain in
+  // flight across the plane's passes.
+  constexpr bool FIXR = RET && !std::is_same<A, int64_t>::value;
+  [[maybe_unused]] const int64_t* __restrict__ cfix = FIXR ? a.cfix : nullptr;
+  [[maybe_unused]] const A csc = FIXR ? A(a.cscale) : A(0);
+  [[maybe_unused]] int64_t rgx[FIXR ? N1 : 1];
+  const int64_t nc1 = (m1 - 1) / 2 + 1, nc2 = (m2 - 1) / 2 + 1;
   auto fetch_ring = [&](int p) {
 #pragma unroll
     for (int it = 0; it < N1; it++) {
       int ci, cj, r, c;
       const bool ok = p1pt(it, ci, cj, r, c) && p >= 0 && p < m0 && r >= 0 && r < m1 && c >= 0 && c < m2;
+      if constexpr (FIXR) {
+        if (cfix) {
+          rgx[it] = ok ? cfix[((int64_t)(p >> 1) * nc1 + (r >> 1)) * nc2 + (c >> 1)] : 0;
+          continue;
+        }
+      }
       rg[it] = ok ? src[(int64_t)p * s0 + (int64_t)r * s1 + c] : A(0);
     }
   };
@@ -1326,7 +1341,14 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
 #pragma unroll
     for (int it = 0; it < N1; it++) {
       int ci, cj, r, c;
-      if (p1pt(it, ci, cj, r, c)) rs[ci][cj] = rg[it];
+      if (!p1pt(it, ci, cj, r, c)) continue;
+      if constexpr (FIXR) {
+        if (cfix) {
+          rs[ci][cj] = from_fix<A>(rgx[it], csc);   // 0 outside the grid
+          continue;
+        }
+      }
+      rs[ci][cj] = rg[it];
     }
   };
   auto fetch_plane = [&](int i0) {
@@ -1923,10 +1945,28 @@ static void run_tile_multi(const std::vector<TileArgs>& v, cudaStream_t s) {
   }
 }
 
+// a retrieval of level 0 whose coarse points are still in fixed point: the
+// tile kernels read them from the output, so they go there first
+template <typename A>
+static void coarse_into_output(const TileArgs& a, cudaStream_t s) {
+  if constexpr (!std::is_same<A, int64_t>::value) {
+    if (!a.retrieve || !a.cfix) return;
+    FieldD f{};
+    for (int k = 0; k < 3; k++) {
+      f.n[k] = a.m[k];
+      f.nc[k] = a.m[k] > 1 ? (a.m[k] - 1) / 2 + 1 : 1;
+    }
+    launch_coarse_out(sizeof(A) == 4 ? VK_F32 : VK_F64, f, a.cfix, a.cscale, a.dst, s);
+  }
+}
+
 template <typename A>
 static void run_tile_kind_multi(const std::vector<TileArgs>& all, cudaStream_t s) {
   std::vector<TileArgs> g[2][2];   // [3-D][cubic]
-  for (const TileArgs& a : all) g[a.m[0] > 1][a.degree == 3].push_back(a);
+  for (const TileArgs& a : all) {
+    coarse_into_output<A>(a, s);
+    g[a.m[0] > 1][a.degree == 3].push_back(a);
+  }
   constexpr bool wide = sizeof(A) == 4;
   if (!g[1][1].empty()) {
     if (wide) run_tile_multi<A, 8, 8, 64, 3, 3>(g[1][1], s); else run_tile_multi<A, 4, 4, 64, 3, 3>(g[1][1], s);
@@ -1940,6 +1980,7 @@ static void run_tile_kind_multi(const std::vector<TileArgs>& all, cudaStream_t s
 
 template <typename A>
 static void run_tile_kind(const TileArgs& a, cudaStream_t s) {
+  coarse_into_output<A>(a, s);
   const bool is3 = a.m[0] > 1;
   const bool cubic = a.degree == 3;
   constexpr bool wide = sizeof(A) == 4;
