@@ -1128,7 +1128,8 @@ template <> struct MaxAbs<int64_t> {
 // the field statistics, waits (bounded) for its other copy and returns.
 template <typename A, int DEG, bool RET, bool IPR, int T1, int T2, bool TMA = false>
 __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, unsigned bid,
-                                                  const CUtensorMap* tm = nullptr, int* err = nullptr) {
+                                                  const CUtensorMap* tm = nullptr, int* err = nullptr,
+                                                  const CUtensorMap* tmr = nullptr) {
   constexpr int NT = 256;
   constexpr int HR = DEG - 1;            // reach beyond the tile along i1, i2
   constexpr int PR = T1 + 2 * HR + 1;    // Pe rows: i1 in [b1 - HR, b1 + T1 + HR]
@@ -1186,14 +1187,24 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
   constexpr int R3B = (T1 * (T2 / 2) * (int)sizeof(A) + 127) / 128 * 128;
   constexpr int SST = RET ? R1B + R2B + R3B : (PR * XW * (int)sizeof(A) + 127) / 128 * 128;   // bytes per stage
   constexpr int NSTG = 2;   // (three stages for the retrieval measured no faster)
+  // retrieval with the coarse ring from the fixed-point 2-grid (tmr set):
+  // each even plane's ring words (CR x RW from 2-grid column (b2 - HR) / 2
+  // rounded down to even, a 16-byte boundary) arrive by one tensor copy
+  // into a buffer after the mbarriers, with an mbarrier of its own
+  constexpr int RW = T2 / 2 + 8;
+  [[maybe_unused]] const bool rtma = TMA && RET && !std::is_same<A, int64_t>::value && tmr != nullptr;
   [[maybe_unused]] unsigned char* stg = nullptr;
-  [[maybe_unused]] uint32_t barb = 0, par = 0;
+  [[maybe_unused]] uint32_t barb = 0, par = 0, rbar = 0, rpar = 0;
+  [[maybe_unused]] const int64_t* rbuf = nullptr;
   if constexpr (TMA) {
     extern __shared__ __align__(128) unsigned char march_dyn[];
     stg = march_dyn + ((128 - (smem_u32(march_dyn) & 127)) & 127);
     barb = smem_u32(stg + NSTG * SST);
+    rbar = barb + 8 * NSTG;
+    rbuf = reinterpret_cast<const int64_t*>(stg + NSTG * SST + 128);
     if (tid == 0) {
-      for (int k = 0; k < NSTG; k++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barb + 8 * k) : "memory");
+      for (int k = 0; k < NSTG + (rtma ? 1 : 0); k++)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barb + 8 * k) : "memory");
       asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
@@ -1220,6 +1231,13 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
                    : "memory");
       tma3(d, tm, b2 - XL, b1 - HR, p, bar);
     }
+  };
+  const int rx = ((b2 - HR) >> 1) & ~1;           // ring box: first 2-grid column (even)
+  const int ro = ((b2 - HR) >> 1) - rx;           // ... and the ring's offset in it (0 or 1)
+  // thread 0: the ring words of even plane p into the ring buffer
+  [[maybe_unused]] auto issue_ring = [&](int p) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(rbar), "r"(CR * RW * 8) : "memory");
+    tma3(reinterpret_cast<const unsigned char*>(rbuf), tmr, rx, (b1 - HR) >> 1, p >> 1, rbar);
   };
 
   A* __restrict__ g1 = reinterpret_cast<A*>(a.reg[0].stage);
@@ -1524,6 +1542,7 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
             const int s2 = (slot + k) % NSTG;
             mbar_wait(barb + 8 * s2, (par >> s2) & 1);
           }
+          if (rtma && odd && i0 + 3 < m0) mbar_wait(rbar, rpar);   // the ring copy issued on plane i0 - 1
         }
         return;
       }
@@ -1533,7 +1552,32 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
     // registers (or the TMA stage) -> shared memory: this plane's rows, and
     // (odd planes) the coarse plane i0 + 3 (the slot of plane i0 - 5)
     if (!RET) store_plane();
-    if (odd) store_ring(i0 + 3);
+    if (rtma) {
+      if (odd && i0 + 3 < m0) {   // ring words of plane i0 + 3 (issued on plane i0 - 1)
+        const bool rok = mbar_wait(rbar, rpar);
+        if (__syncthreads_or(!rok)) {
+          if (tid == 0) {
+            atomicExch(err, 1);
+            for (int k = 1; k < NSTG && i0 + k < z1; k++) {
+              const int s2 = (slot + k) % NSTG;
+              mbar_wait(barb + 8 * s2, (par >> s2) & 1);
+            }
+          }
+          return;
+        }
+        rpar ^= 1u;
+        if constexpr (!std::is_same<A, int64_t>::value) {
+          A(*rs)[CE] = ring[((i0 + 3) >> 1) & 3];
+#pragma unroll
+          for (int it = 0; it < N1; it++) {
+            int ci, cj, r, c;
+            if (p1pt(it, ci, cj, r, c)) rs[ci][cj] = from_fix<A>(rbuf[ci * RW + cj + ro], csc);   // 0 beyond the grid
+          }
+        }
+      }
+    } else if (odd) {
+      store_ring(i0 + 3);
+    }
     A c1[RET && !TMA ? N1 : 1], c2[RET && !TMA ? N2V : 1], c3[RET && !TMA ? N3 : 1];
     if (RET && !TMA) {
 #pragma unroll
@@ -1574,7 +1618,11 @@ __device__ __forceinline__ void level0_march_body(const TileArgs& a, int zc, uns
         if (!RET) fetch_plane(i0 + 1);
         else fetch_chat(i0 + 1);
       }
-      if (!odd) fetch_ring(i0 + 4);       // needed by plane i0 + 1
+      if (rtma) {
+        if (!odd && i0 + 4 < m0 && tid == 0) issue_ring(i0 + 4);   // needed by plane i0 + 1
+      } else if (!odd) {
+        fetch_ring(i0 + 4);               // needed by plane i0 + 1
+      }
     }
     if (!odd && RET) {
       // even plane: the coarse points are the reconstruction already
@@ -1826,16 +1874,19 @@ __global__ void __launch_bounds__(256, 4) k_level0_march_tma(const __grid_consta
 // read_device_timeouts)
 __device__ int g_dev_timeout = 0;
 
-// tensor maps of the three level-0 regions' staging arrays
+// tensor maps of the three level-0 regions' staging arrays and (ring set)
+// of the fixed-point 2-grid the coarse ring comes from
 struct MarchMaps {
-  CUtensorMap m[3];
+  CUtensorMap m[4];
+  int ring;
 };
 
 // retrieval with TMA-staged c_hat boxes (mm: regions 1, 2, 3)
 template <typename A, int DEG, bool IPR, int T1, int T2>
 __global__ void __launch_bounds__(256, 4) k_level0_march_tma_ret(const __grid_constant__ MarchMaps mm,
                                                                  const __grid_constant__ TileArgs a, int zc) {
-  level0_march_body<A, DEG, true, IPR, T1, T2, true>(a, zc, blockIdx.x, mm.m, a.err ? a.err : &g_dev_timeout);
+  level0_march_body<A, DEG, true, IPR, T1, T2, true>(a, zc, blockIdx.x, mm.m, a.err ? a.err : &g_dev_timeout,
+                                                     mm.ring ? &mm.m[3] : nullptr);
 }
 
 int read_device_timeouts(bool clear) {
@@ -2102,6 +2153,22 @@ static bool region_tensor_map(const TileRegion& g, int w, int rows, CUtensorMap&
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// tensor map of the fixed-point 2-grid of a level-0 retrieval (cfix; shape
+// ((m - 1) / 2 + 1) per axis, row-major): boxes of w x rows x 1 words, zero
+// fill beyond the grid; false where its rows are not a multiple of 16 bytes
+static bool ring_tensor_map(const TileArgs& a, int w, int rows, CUtensorMap& tm) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  const int64_t nc[3] = {(a.m[0] - 1) / 2 + 1, (a.m[1] - 1) / 2 + 1, (a.m[2] - 1) / 2 + 1};
+  if (!enc || ((uintptr_t)a.cfix & 15) != 0 || (nc[2] * 8) % 16 != 0) return false;
+  const cuuint64_t gdim[3] = {(cuuint64_t)nc[2], (cuuint64_t)nc[1], (cuuint64_t)nc[0]};
+  const cuuint64_t gstride[2] = {(cuuint64_t)(nc[2] * 8), (cuuint64_t)(nc[1] * nc[2] * 8)};
+  const cuuint32_t box[3] = {(cuuint32_t)w, (cuuint32_t)rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(&tm, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<int64_t*>(a.cfix), gdim, gstride, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // the TMA form of the retrieval: every region's staging array takes a
 // tensor map (the level-0 lattices of pass order (0, 1, 2): march_applies)
 template <typename A, int DEG, bool PR, int T1, int T2>
@@ -2111,11 +2178,16 @@ static bool run_level0_march_tma_ret(const TileArgs& a0, cudaStream_t s, int zc_
   constexpr int R2B = ((T1 / 2) * W12 * (int)sizeof(A) + 127) / 128 * 128;
   constexpr int R3B = (T1 * (T2 / 2) * (int)sizeof(A) + 127) / 128 * 128;
   constexpr int NSTG = 2;   // as in level0_march_body
-  constexpr int SMEM = NSTG * (R1B + R2B + R3B) + 128 + 8 * NSTG;
+  // value kinds whose ring may come from the fixed-point grid: a 128-byte
+  // mbarrier block, then the ring buffer (CR x RW words)
+  constexpr bool FIX = !std::is_same<A, int64_t>::value;
+  constexpr int RW = T2 / 2 + 8;
+  constexpr int SMEM = NSTG * (R1B + R2B + R3B) + 128 + (FIX ? 128 + CR * RW * 8 : 8 * NSTG);
   MarchMaps mm;
   if (!region_tensor_map<A>(a0.reg[0], W12, CR, mm.m[0]) || !region_tensor_map<A>(a0.reg[1], W12, T1 / 2, mm.m[1]) ||
       !region_tensor_map<A>(a0.reg[2], T2 / 2, T1, mm.m[2]))
     return false;
+  mm.ring = FIX && a0.cfix && ring_tensor_map(a0, RW, CR, mm.m[3]);
   TileArgs a = a0;
   int zc = 0;
   const int64_t nb = march_grid<T1, T2>(a, zc_force, zc);
